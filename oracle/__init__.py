@@ -1,0 +1,320 @@
+"""Plain FP64 CPU oracle for the projective-integration PIC hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this package. The
+product path (``paper_1610_01071_gb300``) never imports it and shares no code
+with it; the C source lives in ``pepic_oracle.c`` and every function there cites
+the section, equation or appendix of Cazeaux & Hesthaven it follows.
+
+This module only compiles the C file with gcc and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pepic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+THETA_ONE = 1 << 24
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB_PATH)
+    if not stale:
+        src_m = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "pepic_oracle.h")))
+        stale = os.path.getmtime(_LIB_PATH) < src_m
+    if stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+             "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            P = ctypes.c_void_p
+            sig = {
+                "orc_splitmix64": (u64, [u64]),
+                "orc_fx_shift": (i32, [dbl]),
+                "orc_deposit_fx": (None, [i64, P, P, P, i32, i32, P]),
+                "orc_deposit_f64": (None, [i64, P, P, P, P, i32, P, P]),
+                "orc_cyclic_tridiag": (None, [i32, dbl, P, dbl, P, P]),
+                "orc_newton_pb": (ctypes.c_int, [i32, dbl, i32, P, P, dbl, i32, P]),
+                "orc_efield": (None, [i32, dbl, P, P]),
+                "orc_gather": (dbl, [P, i32, i32, dbl]),
+                "orc_push": (None, [i64, P, P, P, P, i32, dbl, dbl, dbl, dbl]),
+                "orc_restrict_sample": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, P, P]),
+                "orc_dwt_level": (None, [P, i32, P, i32, P, P]),
+                "orc_idwt_level": (None, [P, i32, P, P, i32, P]),
+                "orc_coarsen": (None, [P, i32, P, i32, P, i32]),
+                "orc_refine": (None, [P, i32, P, i32, P, i32]),
+                "orc_ls_slope": (dbl, [i32, dbl, P, i64]),
+                "orc_ls_project": (None, [i32, i32, dbl, dbl, P, P, P]),
+                "orc_ndtri": (dbl, [dbl]),
+                "orc_quiet_start": (None, [i64, i32, P, P, dbl, u64, P, P, P, P]),
+                "orc_lift_profile": (None, [i32, P, P, P]),
+                "orc_burst": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl,
+                                             i32, i32, i32, dbl, i32, i32, P, P]),
+                "orc_pic_steps": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32,
+                                                 i32, i32, dbl, i32, i32, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ------------------------------------------------------------------ filters
+# Orthonormal scaling filters (sum h = sqrt 2). Haar; Daubechies' 4-tap filter
+# from its closed form (two vanishing moments of the wavelet).
+_S3 = np.sqrt(3.0)
+FILTERS = {
+    "haar": np.array([1.0, 1.0]) / np.sqrt(2.0),
+    "d4": np.array([1 + _S3, 3 + _S3, 3 - _S3, 1 - _S3]) / (4 * np.sqrt(2.0)),
+}
+WAVELET_IDS = {0: "haar", 1: "d4"}
+
+
+def splitmix64(x: int) -> int:
+    return int(_load().orc_splitmix64(x & 0xFFFFFFFFFFFFFFFF))
+
+
+def fx_shift(cap: float) -> int:
+    return int(_load().orc_fx_shift(float(cap)))
+
+
+class State:
+    """FP64 particle state (cell, theta, v, w)."""
+
+    def __init__(self, cell, theta, v, w):
+        self.cell = _i32(cell).copy()
+        self.theta = _f64(theta).copy()
+        self.v = _f64(v).copy()
+        self.w = _f64(w).copy()
+
+    @property
+    def n(self):
+        return self.cell.shape[0]
+
+    def copy(self):
+        return State(self.cell, self.theta, self.v, self.w)
+
+
+def deposit_fx(cell, theta, w, ncell, s_w):
+    cell, theta, w = _i32(cell), _f64(theta), _f64(w)
+    rho = np.zeros(ncell, np.int64)
+    _load().orc_deposit_fx(cell.shape[0], _p(cell), _p(theta), _p(w), ncell, s_w, _p(rho))
+    return rho
+
+
+def deposit_f64(cell, theta, w, ncell, vel=None):
+    cell, theta, w = _i32(cell), _f64(theta), _f64(w)
+    dens = np.zeros(ncell)
+    mom = np.zeros(ncell) if vel is not None else None
+    vel_a = _f64(vel) if vel is not None else None
+    _load().orc_deposit_f64(cell.shape[0], _p(cell), _p(theta), _p(w),
+                            _p(vel_a) if vel is not None else None, ncell, _p(dens),
+                            _p(mom) if mom is not None else None)
+    return (dens, mom) if vel is not None else dens
+
+
+def cyclic_tridiag(a, b, c, d):
+    b, d = _f64(b), _f64(d)
+    x = np.zeros_like(b)
+    _load().orc_cyclic_tridiag(b.shape[0], float(a), _p(b), float(c), _p(d), _p(x))
+    return x
+
+
+def newton_pb(n, dx, phi0=None, mode=0, tol=1e-11, maxit=50):
+    n = _f64(n)
+    phi = _f64(phi0).copy() if phi0 is not None else np.log(np.maximum(n, 1e-8))
+    iters = np.zeros(1, np.int32)
+    fail = _load().orc_newton_pb(n.shape[0], float(dx), int(mode), _p(n), _p(phi), float(tol), int(maxit), _p(iters))
+    return phi, int(iters[0]), int(fail)
+
+
+def efield(phi, dx):
+    phi = _f64(phi)
+    E = np.zeros_like(phi)
+    _load().orc_efield(phi.shape[0], float(dx), _p(phi), _p(E))
+    return E
+
+
+def gather(F, cell, theta):
+    """CIC gather of nodal field F at each (cell, theta)."""
+    F = _f64(F)
+    fn = _load().orc_gather
+    return np.array([fn(_p(F), F.shape[0], int(c), float(t)) for c, t in zip(cell, theta)])
+
+
+def push(st: State, E, ncell, dx, dt, qm, kick=1.0):
+    E = _f64(E)
+    _load().orc_push(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(E), ncell, float(dx), float(dt),
+                     float(qm), float(kick))
+
+
+def restrict_sample(st: State, vbar, E0, ncell, dx, tau, qm):
+    vbar, E0 = _f64(vbar), _f64(E0)
+    dens, mom = np.zeros(ncell), np.zeros(ncell)
+    _load().orc_restrict_sample(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell,
+                                float(dx), float(tau), float(qm), _p(dens), _p(mom))
+    return dens, mom
+
+
+def dwt_level(x, wavelet="haar"):
+    h = FILTERS[wavelet]
+    x = _f64(x)
+    a, d = np.zeros(x.shape[0] // 2), np.zeros(x.shape[0] // 2)
+    _load().orc_dwt_level(_p(h), h.shape[0], _p(x), x.shape[0], _p(a), _p(d))
+    return a, d
+
+
+def idwt_level(a, d, wavelet="haar"):
+    h = FILTERS[wavelet]
+    a = _f64(a)
+    d = _f64(d) if d is not None else None
+    x = np.zeros(2 * a.shape[0])
+    _load().orc_idwt_level(_p(h), h.shape[0], _p(a), _p(d) if d is not None else None, a.shape[0], _p(x))
+    return x
+
+
+def coarsen(fine, ncoarse, wavelet="haar"):
+    h = FILTERS[wavelet]
+    fine = _f64(fine)
+    out = np.zeros(ncoarse)
+    _load().orc_coarsen(_p(h), h.shape[0], _p(fine), fine.shape[0], _p(out), ncoarse)
+    return out
+
+
+def refine(coarse, nfine, wavelet="haar"):
+    h = FILTERS[wavelet]
+    coarse = _f64(coarse)
+    out = np.zeros(nfine)
+    _load().orc_refine(_p(h), h.shape[0], _p(coarse), coarse.shape[0], _p(out), nfine)
+    return out
+
+
+def ls_slope(y, dt):
+    y = _f64(y)
+    return float(_load().orc_ls_slope(y.shape[0] - 1, float(dt), _p(y), 1))
+
+
+def ls_project(samples, dt, dT):
+    """samples: [K+1, ncoef]. Returns (coarse, slope)."""
+    s = _f64(samples)
+    K, ncoef = s.shape[0] - 1, s.shape[1]
+    out, slope = np.zeros(ncoef), np.zeros(ncoef)
+    _load().orc_ls_project(K, ncoef, float(dt), float(dT), _p(s), _p(out), _p(slope))
+    return out, slope
+
+
+def ndtri(p):
+    lib = _load()
+    return np.array([lib.orc_ndtri(float(x)) for x in np.atleast_1d(p)])
+
+
+def quiet_start(N, ncell, nprof, uprof, v_th, seed):
+    nprof, uprof = _f64(nprof), _f64(uprof)
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_quiet_start(N, ncell, _p(nprof), _p(uprof), float(v_th), seed & 0xFFFFFFFFFFFFFFFF,
+                            _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def lift_profile(n, m):
+    n = _f64(n).copy()
+    m = _f64(m)
+    u = np.zeros_like(n)
+    _load().orc_lift_profile(n.shape[0], _p(n), _p(m), _p(u))
+    return n, u
+
+
+def burst(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, comoving=True, mode=0, tol=1e-11,
+          maxit=50, vel_at_integer=True):
+    """Runs K steps in place on st; returns (samples [(K+1),2,ncell], phi, fails)."""
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, 2, ncell))
+    fails = _load().orc_burst(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                              float(dt), float(qm), int(K), float(dT), int(comoving), int(mode), int(s_w),
+                              float(tol), int(maxit), int(vel_at_integer), _p(phi), _p(samples))
+    return samples, phi, int(fails)
+
+
+def pic_steps(st: State, ncell, dx, dt, qm, nsteps, s_w, phi, mode=0, tol=1e-11, maxit=50,
+              vel_at_integer=True):
+    phi = _f64(phi).copy()
+    fails = _load().orc_pic_steps(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                  float(dt), float(qm), int(nsteps), int(mode), int(s_w), float(tol),
+                                  int(maxit), int(vel_at_integer), _p(phi))
+    return phi, int(fails)
+
+
+# ------------------------------------------------------------------ composite steps
+
+
+def sine_profile(ncell, L, amplitude):
+    """Section 4.1 initial condition on nodes: n = 1 + d cos(2 pi x/L), u = d cos(2 pi x/L)."""
+    x = np.arange(ncell) * (L / ncell)
+    c = amplitude * np.cos(2 * np.pi * x / L)
+    return 1.0 + c, c
+
+
+def efpi_macro_step(st: State, cfg: dict, phi, vel_at_integer=True):
+    """One forward-Euler projective step (Section 3.1/3.3): burst with co-moving
+    restriction, coarsening, least-squares slope, leap. Returns (coarse [2,nc], samples_c, phi)."""
+    ncell, nc, K = cfg["ncell"], cfg["n_coarse"], cfg["K"]
+    dx = cfg["L"] / ncell
+    samples, phi, fails = burst(st, ncell, dx, cfg["dt"], cfg["qm"], K, cfg["dT"], cfg["s_w"], phi,
+                                comoving=cfg.get("comoving", True), mode=cfg.get("mode", 0),
+                                vel_at_integer=vel_at_integer)
+    wav = cfg.get("wavelet", "haar")
+    cs = np.zeros((K + 1, 2, nc))
+    for p in range(K + 1):
+        for m in range(2):
+            cs[p, m] = coarsen(samples[p, m], nc, wav)
+    coarse, _ = ls_project(cs.reshape(K + 1, 2 * nc), cfg["dt"], cfg["dT"])
+    return coarse.reshape(2, nc), cs, phi
+
+
+def lift(coarse, cfg: dict, seed):
+    """Lifting (Section 3.3 + Appendix C): refine with zero details, clamp, quiet start."""
+    ncell = cfg["ncell"]
+    wav = cfg.get("wavelet", "haar")
+    nf = refine(coarse[0], ncell, wav)
+    mf = refine(coarse[1], ncell, wav)
+    nf, uf = lift_profile(nf, mf)
+    return quiet_start(cfg["N"], ncell, nf, uf, cfg["v_th"], seed)

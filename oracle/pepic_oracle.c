@@ -1,0 +1,435 @@
+/*
+ * Plain FP64 CPU oracle — see pepic_oracle.h for the contract.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the GPU product path.
+ *
+ * Compiled with -O2 -ffp-contract=off so that no multiply-add is fused behind
+ * the reader's back. Every loop is the textbook statement of its step.
+ */
+#include "pepic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define THETA_ONE 16777216.0 /* 2^24: resolution of the in-cell offset in the deposit rule */
+
+uint64_t orc_splitmix64(uint64_t x)
+{
+    /* splitmix64 output function applied to the counter x (Steele, Lea, Flood 2014). */
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+int32_t orc_fx_shift(double cap)
+{
+    int e = 0;
+    double m = frexp(cap, &e); /* cap = m 2^e, m in [0.5, 1) */
+    int ceil_log2 = (m == 0.5) ? e - 1 : e;
+    return 22 - ceil_log2;
+}
+
+static int32_t wrap(int64_t j, int32_t n)
+{
+    int64_t r = j % n;
+    if (r < 0) r += n;
+    return (int32_t)r;
+}
+
+/* ---------------------------------------------------------------- deposit */
+
+void orc_deposit_fx(int64_t n, const int32_t* cell, const double* theta, const double* w,
+                    int32_t ncell, int32_t s_w, int64_t* rho)
+{
+    memset(rho, 0, sizeof(int64_t) * (size_t)ncell);
+    const double wscale = ldexp(1.0, s_w);
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t tq = llrint(theta[p] * THETA_ONE); /* round half to even */
+        int64_t wq = llrint(w[p] * wscale);
+        int64_t qr = wq * tq;
+        int64_t ql = wq * (int64_t)THETA_ONE - qr;
+        int32_t j = cell[p];
+        rho[j] += ql;
+        rho[wrap((int64_t)j + 1, ncell)] += qr;
+    }
+}
+
+void orc_deposit_f64(int64_t n, const int32_t* cell, const double* theta, const double* w,
+                     const double* vel, int32_t ncell, double* dens, double* mom)
+{
+    memset(dens, 0, sizeof(double) * (size_t)ncell);
+    if (mom) memset(mom, 0, sizeof(double) * (size_t)ncell);
+    for (int64_t p = 0; p < n; ++p) {
+        int32_t j = cell[p], j1 = wrap((int64_t)j + 1, ncell);
+        dens[j] += w[p] * (1.0 - theta[p]);
+        dens[j1] += w[p] * theta[p];
+        if (mom) {
+            double wv = w[p] * vel[p];
+            mom[j] += wv * (1.0 - theta[p]);
+            mom[j1] += wv * theta[p];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------- field */
+
+static void thomas(int32_t n, double a, const double* b, double c, const double* d, double* x)
+{
+    double* cp = (double*)malloc(sizeof(double) * (size_t)n);
+    double* dp = (double*)malloc(sizeof(double) * (size_t)n);
+    cp[0] = c / b[0];
+    dp[0] = d[0] / b[0];
+    for (int32_t i = 1; i < n; ++i) {
+        double m = b[i] - a * cp[i - 1];
+        cp[i] = c / m;
+        dp[i] = (d[i] - a * dp[i - 1]) / m;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int32_t i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    free(cp);
+    free(dp);
+}
+
+void orc_cyclic_tridiag(int32_t n, double a, const double* b, double c, const double* d, double* x)
+{
+    /* A = T + u v^T with u = (gamma, 0, .., 0, c)^T, v = (1, 0, .., 0, a/gamma)^T:
+     * the corner entries A[0][n-1] = a and A[n-1][0] = c move into u v^T. */
+    double gamma = -b[0];
+    double* bb = (double*)malloc(sizeof(double) * (size_t)n);
+    double* u = (double*)calloc((size_t)n, sizeof(double));
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(bb, b, sizeof(double) * (size_t)n);
+    bb[0] = b[0] - gamma;
+    bb[n - 1] = b[n - 1] - c * a / gamma;
+    u[0] = gamma;
+    u[n - 1] = c;
+    thomas(n, a, bb, c, d, y);
+    thomas(n, a, bb, c, u, z);
+    double fact = (y[0] + a * y[n - 1] / gamma) / (1.0 + z[0] + a * z[n - 1] / gamma);
+    for (int32_t i = 0; i < n; ++i) x[i] = y[i] - fact * z[i];
+    free(bb);
+    free(u);
+    free(y);
+    free(z);
+}
+
+int orc_newton_pb(int32_t ncell, double dx, int32_t mode, const double* n, double* phi,
+                  double tol, int32_t maxit, int32_t* iters)
+{
+    const double inv_dx2 = 1.0 / (dx * dx);
+    double* b = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* delta = (double*)malloc(sizeof(double) * (size_t)ncell);
+    int status = 1;
+    int32_t it = 0;
+    for (it = 0; it < maxit; ++it) {
+        for (int32_t j = 0; j < ncell; ++j) {
+            double lap = (phi[wrap(j - 1, ncell)] - 2.0 * phi[j] + phi[wrap(j + 1, ncell)]) * inv_dx2;
+            double g = (mode == 0) ? exp(phi[j]) : 1.0 + phi[j];
+            double gp = (mode == 0) ? exp(phi[j]) : 1.0;
+            double F = -lap + g - n[j];
+            b[j] = 2.0 * inv_dx2 + gp;
+            rhs[j] = -F;
+        }
+        orc_cyclic_tridiag(ncell, -inv_dx2, b, -inv_dx2, rhs, delta);
+        double m = 0.0;
+        for (int32_t j = 0; j < ncell; ++j) m = fmax(m, fabs(delta[j]));
+        double scale = (m > 2.0) ? 2.0 / m : 1.0; /* damped step: |update| <= 2 */
+        for (int32_t j = 0; j < ncell; ++j) phi[j] += scale * delta[j];
+        if (m < tol) {
+            status = 0;
+            ++it;
+            break;
+        }
+    }
+    if (iters) *iters = it;
+    free(b);
+    free(rhs);
+    free(delta);
+    return status;
+}
+
+void orc_efield(int32_t ncell, double dx, const double* phi, double* E)
+{
+    for (int32_t j = 0; j < ncell; ++j)
+        E[j] = -(phi[wrap(j + 1, ncell)] - phi[wrap(j - 1, ncell)]) / (2.0 * dx);
+}
+
+double orc_gather(const double* F, int32_t ncell, int32_t cell, double theta)
+{
+    return (1.0 - theta) * F[cell] + theta * F[wrap((int64_t)cell + 1, ncell)];
+}
+
+/* ---------------------------------------------------------------- push */
+
+static void drift(int32_t* cell, double* theta, double shift_cells, int32_t ncell)
+{
+    double s = *theta + shift_cells;
+    double k = floor(s);
+    *theta = s - k;
+    *cell = wrap((int64_t)*cell + (int64_t)k, ncell);
+}
+
+void orc_push(int64_t n, int32_t* cell, double* theta, double* v, const double* E,
+              int32_t ncell, double dx, double dt, double qm, double kick)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double Ep = orc_gather(E, ncell, cell[p], theta[p]);
+        v[p] += kick * qm * dt * Ep;
+        drift(&cell[p], &theta[p], v[p] * dt / dx, ncell);
+    }
+}
+
+void orc_restrict_sample(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                         const double* w, const double* E0, int32_t ncell, double dx,
+                         double tau, double qm, double* dens, double* mom)
+{
+    memset(dens, 0, sizeof(double) * (size_t)ncell);
+    memset(mom, 0, sizeof(double) * (size_t)ncell);
+    for (int64_t p = 0; p < n; ++p) {
+        double E0p = orc_gather(E0, ncell, cell[p], theta[p]);
+        int32_t c = cell[p];
+        double th = theta[p];
+        drift(&c, &th, tau * vbar[p] / dx, ncell);      /* X~ = X + tau V  */
+        double vt = vbar[p] + qm * tau * E0p;            /* V~ = V + qm tau E_n(X) */
+        int32_t c1 = wrap((int64_t)c + 1, ncell);
+        dens[c] += w[p] * (1.0 - th);
+        dens[c1] += w[p] * th;
+        mom[c] += w[p] * vt * (1.0 - th);
+        mom[c1] += w[p] * vt * th;
+    }
+}
+
+/* ---------------------------------------------------------------- wavelets */
+
+void orc_dwt_level(const double* h, int32_t len, const double* x, int32_t n, double* approx, double* detail)
+{
+    for (int32_t k = 0; k < n / 2; ++k) {
+        double a = 0.0, d = 0.0;
+        for (int32_t m = 0; m < len; ++m) {
+            double g = ((m & 1) ? -1.0 : 1.0) * h[len - 1 - m];
+            double xv = x[wrap(2 * (int64_t)k + m, n)];
+            a += h[m] * xv;
+            d += g * xv;
+        }
+        approx[k] = a;
+        if (detail) detail[k] = d;
+    }
+}
+
+void orc_idwt_level(const double* h, int32_t len, const double* approx, const double* detail,
+                    int32_t nhalf, double* x)
+{
+    int32_t n = 2 * nhalf;
+    memset(x, 0, sizeof(double) * (size_t)n);
+    for (int32_t k = 0; k < nhalf; ++k) {
+        for (int32_t m = 0; m < len; ++m) {
+            double g = ((m & 1) ? -1.0 : 1.0) * h[len - 1 - m];
+            x[wrap(2 * (int64_t)k + m, n)] += h[m] * approx[k] + g * (detail ? detail[k] : 0.0);
+        }
+    }
+}
+
+static int32_t ilog2(int32_t n)
+{
+    int32_t l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+void orc_coarsen(const double* h, int32_t len, const double* fine, int32_t nfine,
+                 double* coarse, int32_t ncoarse)
+{
+    double* a = (double*)malloc(sizeof(double) * (size_t)nfine);
+    double* t = (double*)malloc(sizeof(double) * (size_t)nfine);
+    double s = pow(2.0, -0.5 * ilog2(nfine)); /* scaling coefficients at the finest level */
+    for (int32_t j = 0; j < nfine; ++j) a[j] = s * fine[j];
+    for (int32_t n = nfine; n > ncoarse; n /= 2) {
+        orc_dwt_level(h, len, a, n, t, NULL);
+        memcpy(a, t, sizeof(double) * (size_t)(n / 2));
+    }
+    memcpy(coarse, a, sizeof(double) * (size_t)ncoarse);
+    free(a);
+    free(t);
+}
+
+void orc_refine(const double* h, int32_t len, const double* coarse, int32_t ncoarse,
+                double* fine, int32_t nfine)
+{
+    double* a = (double*)malloc(sizeof(double) * (size_t)nfine);
+    double* t = (double*)malloc(sizeof(double) * (size_t)nfine);
+    memcpy(a, coarse, sizeof(double) * (size_t)ncoarse);
+    for (int32_t n = ncoarse; n < nfine; n *= 2) {
+        orc_idwt_level(h, len, a, NULL, n, t);
+        memcpy(a, t, sizeof(double) * (size_t)(2 * n));
+    }
+    double s = pow(2.0, 0.5 * ilog2(nfine));
+    for (int32_t j = 0; j < nfine; ++j) fine[j] = s * a[j];
+    free(a);
+    free(t);
+}
+
+/* ---------------------------------------------------------------- projection */
+
+double orc_ls_slope(int32_t K, double dt, const double* y, int64_t stride)
+{
+    double S0 = 0, S1 = 0, S2 = 0, Sy = 0, Sty = 0;
+    for (int32_t p = 0; p <= K; ++p) {
+        double t = p * dt, yp = y[(int64_t)p * stride];
+        S0 += 1.0;
+        S1 += t;
+        S2 += t * t;
+        Sy += yp;
+        Sty += t * yp;
+    }
+    return (S0 * Sty - S1 * Sy) / (S0 * S2 - S1 * S1);
+}
+
+void orc_ls_project(int32_t K, int32_t ncoef, double dt, double dT, const double* samples,
+                    double* coarse_out, double* slope_out)
+{
+    for (int32_t i = 0; i < ncoef; ++i) {
+        double s = orc_ls_slope(K, dt, samples + i, ncoef);
+        if (slope_out) slope_out[i] = s;
+        coarse_out[i] = samples[(int64_t)K * ncoef + i] + (dT - K * dt) * s;
+    }
+}
+
+/* ---------------------------------------------------------------- lifting */
+
+static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+double orc_ndtri(double p)
+{
+    if (!(p > 0.0 && p < 1.0)) return (p <= 0.0) ? -INFINITY : INFINITY;
+    int upper = p > 0.5;
+    double q = upper ? 1.0 - p : p; /* tail probability, q <= 1/2 */
+    double t = sqrt(-2.0 * log(q));
+    /* Abramowitz & Stegun 26.2.23: upper-tail quantile, |error| < 4.5e-4 */
+    double xq = t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                        (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t);
+    double x = -xq; /* Phi(x) = q */
+    for (int it = 0; it < 8; ++it) {
+        double f = std_normal_cdf(x) - q;
+        double dens = exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+        double step = f / dens;
+        x -= step;
+        if (fabs(step) < 1e-16 * fmax(1.0, fabs(x))) break;
+    }
+    return upper ? -x : x;
+}
+
+static uint32_t brev32(uint32_t x)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 32; ++b) r |= ((x >> b) & 1u) << (31 - b);
+    return r;
+}
+
+void orc_quiet_start(int64_t N, int32_t ncell, const double* nprof, const double* uprof,
+                     double v_th, uint64_t seed, int32_t* cell, double* theta, double* v, double* w)
+{
+    int64_t ppc = N / ncell;
+    uint32_t half = (uint32_t)(2147483648.0 / (double)N);
+    uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t c = (int32_t)(i / ppc);
+        double th = (2.0 * (double)(i % ppc) + 1.0) / (2.0 * (double)ppc);
+        int32_t c1 = wrap((int64_t)c + 1, ncell);
+        double nX = (1.0 - th) * nprof[c] + th * nprof[c1];
+        double uX = (1.0 - th) * uprof[c] + th * uprof[c1];
+        uint32_t B = brev32((uint32_t)i) + half + shift; /* mod 2^32 */
+        double b = ((double)B + 0.5) * 2.3283064365386963e-10; /* 2^-32 */
+        cell[i] = c;
+        theta[i] = th;
+        w[i] = nX / (double)ppc;
+        v[i] = uX + v_th * orc_ndtri(b);
+    }
+}
+
+void orc_lift_profile(int32_t ncell, double* n, const double* m, double* u)
+{
+    double sum0 = 0.0, sum1 = 0.0, nmax = 0.0;
+    int clamped = 0;
+    for (int32_t j = 0; j < ncell; ++j) sum0 += n[j];
+    for (int32_t j = 0; j < ncell; ++j) {
+        if (n[j] < 0.0) {
+            n[j] = 0.0;
+            clamped = 1;
+        }
+        sum1 += n[j];
+    }
+    if (clamped && sum1 > 0.0 && sum0 > 0.0)
+        for (int32_t j = 0; j < ncell; ++j) n[j] *= sum0 / sum1;
+    for (int32_t j = 0; j < ncell; ++j) nmax = fmax(nmax, n[j]);
+    for (int32_t j = 0; j < ncell; ++j) u[j] = (n[j] > 1e-12 * nmax) ? m[j] / n[j] : 0.0;
+}
+
+/* ---------------------------------------------------------------- bursts */
+
+static int field_from_particles(int64_t n, const int32_t* cell, const double* theta, const double* w,
+                                int32_t ncell, double dx, int32_t mode, int32_t s_w, double tol,
+                                int32_t maxit, double* phi, double* E)
+{
+    int64_t* rho = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    double* dens = (double*)malloc(sizeof(double) * (size_t)ncell);
+    orc_deposit_fx(n, cell, theta, w, ncell, s_w, rho);
+    double scale = ldexp(1.0, -(s_w + 24));
+    for (int32_t j = 0; j < ncell; ++j) dens[j] = (double)rho[j] * scale;
+    int32_t iters = 0;
+    int fail = orc_newton_pb(ncell, dx, mode, dens, phi, tol, maxit, &iters);
+    orc_efield(ncell, dx, phi, E);
+    free(rho);
+    free(dens);
+    return fail;
+}
+
+int orc_burst(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+              int32_t ncell, double dx, double dt, double qm, int32_t K, double dT,
+              int32_t comoving, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+              int32_t vel_at_integer, double* phi, double* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)n);
+    int fails = field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell); /* E_n, stored at burst start */
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        /* integer-time velocity: the half kick that takes v to time t_n + p dt */
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = v[i] + (kick - 0.5) * qm * dt * orc_gather(E, ncell, cell[i], theta[i]);
+        double tau = comoving ? dT - p * dt : 0.0;
+        double* dens = samples + (size_t)p * 2 * ncell;
+        orc_restrict_sample(n, cell, theta, vbar, w, E0, ncell, dx, tau, qm, dens, dens + ncell);
+        if (p == K) break;
+        orc_push(n, cell, theta, v, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}
+
+int orc_pic_steps(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+                  int32_t ncell, double dx, double dt, double qm, int32_t nsteps,
+                  int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                  int32_t vel_at_integer, double* phi)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    int fails = 0;
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t s = 0; s < nsteps; ++s) {
+        fails += field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+        orc_push(n, cell, theta, v, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+    }
+    free(E);
+    return fails;
+}

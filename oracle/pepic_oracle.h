@@ -1,0 +1,138 @@
+/*
+ * Plain FP64 CPU oracle for the projective-integration PIC hot path
+ * (Cazeaux & Hesthaven, "Projective multiscale time-integration for
+ * electrostatic particle-in-cell methods").
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library. The GPU product
+ * path never calls it, and it shares no source with the GPU path.
+ *
+ * Every function is a direct, unoptimised statement of one step of the
+ * method, in the paper's order, with the paper's notation where it has one.
+ * Particle states are (cell, theta, v, w) with theta in [0,1) the offset
+ * inside the cell, so that X = (cell + theta) * dx.
+ *
+ * Units: Debye length, ion plasma frequency, sound speed, e, m_i, T_e and
+ * n_0 are 1; ions have charge-to-mass ratio qm; E = -dphi/dx.
+ *
+ * Parity status: every function below is pinned by a closed form, an
+ * invariant, brute force or a library routine in the CPU tests; none is
+ * "parity unpinned" except the nonlinear steepening of the full macro-step,
+ * which the paper only shows in figures that are not available.
+ */
+#ifndef PEPIC_ORACLE_H
+#define PEPIC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Counter-based generator: splitmix64 (Steele, Lea & Flood 2014). */
+uint64_t orc_splitmix64(uint64_t x);
+
+/* Fixed-point scale rule: s = 22 - ceil(log2(cap)), so |value * 2^s| <= 2^22. */
+int32_t orc_fx_shift(double cap);
+
+/* Section 2.2: CIC charge deposit with the deterministic fixed-point rule
+ * theta_q = rn(theta 2^24), w_q = rn(w 2^s_w), q_R = w_q theta_q,
+ * q_L = w_q 2^24 - q_R, summed in int64. Overwrites rho[ncell]. Periodic. */
+void orc_deposit_fx(int64_t n, const int32_t* cell, const double* theta, const double* w,
+                    int32_t ncell, int32_t s_w, int64_t* rho);
+
+/* Plain FP64 CIC deposit of w and of w*vel (vel may be NULL). Overwrites. */
+void orc_deposit_f64(int64_t n, const int32_t* cell, const double* theta, const double* w,
+                     const double* vel, int32_t ncell, double* dens, double* mom);
+
+/* Cyclic tridiagonal solve a x_{j-1} + b_j x_j + c x_{j+1} = d_j (Thomas with
+ * Sherman-Morrison); constant off-diagonals a, c. */
+void orc_cyclic_tridiag(int32_t n, double a, const double* b, double c, const double* d, double* x);
+
+/* Section 3.3, Poisson-Boltzmann: -lambda^2 Lap phi + exp(phi) = n_i/n_0 (lambda = n_0 = 1)
+ * on the periodic nodal grid, solved by Newton. mode 0: exp(phi); mode 1: the
+ * linearised electron response 1 + phi. phi holds the initial guess on entry.
+ * Returns 0 on convergence (max |update| < tol), 1 otherwise; *iters gets the
+ * number of Newton updates applied. */
+int orc_newton_pb(int32_t ncell, double dx, int32_t mode, const double* n, double* phi,
+                  double tol, int32_t maxit, int32_t* iters);
+
+/* E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx), periodic. */
+void orc_efield(int32_t ncell, double dx, const double* phi, double* E);
+
+/* CIC gather of a nodal field at one particle. */
+double orc_gather(const double* F, int32_t ncell, int32_t cell, double theta);
+
+/* Leapfrog kick-drift (Section 2.2): v += kick*qm*dt*E(X); X += v dt; periodic wrap. */
+void orc_push(int64_t n, int32_t* cell, double* theta, double* v, const double* E,
+              int32_t ncell, double dx, double dt, double qm, double kick);
+
+/* Appendix B, restriction along approximate characteristics: with tau = Delta t - p dt,
+ * X~ = X + tau Vbar, V~ = Vbar + qm tau E_n(X); deposits w and w V~ (plain FP64 CIC)
+ * at X~. vbar is the integer-time velocity. Overwrites dens/mom [ncell]. */
+void orc_restrict_sample(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                         const double* w, const double* E0, int32_t ncell, double dx,
+                         double tau, double qm, double* dens, double* mom);
+
+/* Orthonormal periodized filter bank (Appendix A). h has len taps. One analysis level:
+ * approx[k] = sum_m h_m x[(2k+m) mod n], detail[k] = sum_m g_m x[(2k+m) mod n],
+ * g_m = (-1)^m h_{len-1-m}. n even. */
+void orc_dwt_level(const double* h, int32_t len, const double* x, int32_t n, double* approx, double* detail);
+/* One synthesis level, exact inverse of orc_dwt_level. */
+void orc_idwt_level(const double* h, int32_t len, const double* approx, const double* detail,
+                    int32_t nhalf, double* x);
+
+/* Restriction to scaling coefficients: fine values f_j (j < nfine) are taken as
+ * scaling coefficients 2^{-J_f/2} f_j at level J_f, then analysed down to
+ * ncoarse coefficients, details discarded (linear thresholding). */
+void orc_coarsen(const double* h, int32_t len, const double* fine, int32_t nfine,
+                 double* coarse, int32_t ncoarse);
+/* Inverse: synthesis with all details zero, then f_j = 2^{J_f/2} a_j. */
+void orc_refine(const double* h, int32_t len, const double* coarse, int32_t ncoarse,
+                double* fine, int32_t nfine);
+
+/* Section 3.3 extrapolation: least-squares slope of samples y_0..y_K taken at
+ * t_p = p dt, from the normal equations of the line fit. */
+double orc_ls_slope(int32_t K, double dt, const double* y, int64_t stride);
+
+/* Forward-Euler leap from the last sample: c = y_K + (dT - K dt) slope, for ncoef
+ * coefficients stored as samples[p*ncoef + i]. */
+void orc_ls_project(int32_t K, int32_t ncoef, double dt, double dT, const double* samples,
+                    double* coarse_out, double* slope_out);
+
+/* Inverse of the standard normal CDF (start from Abramowitz-Stegun 26.2.23, then
+ * Newton steps on Phi(x) = erfc(-x/sqrt 2)/2). */
+double orc_ndtri(double p);
+
+/* Appendix C quiet start on a nodal profile (n_j, u_j), j < ncell, periodic:
+ * particle i of N = ppc*ncell sits at X/dx = i/ppc + (2 (i mod ppc) + 1)/(2 ppc),
+ * weight w = n(X)/ppc, velocity V = u(X) + v_th Phi^{-1}(b_i) with
+ * b_i = (B_i + 1/2) 2^-32, B_i = brev32(i) + floor(2^31/N) + (splitmix64(seed) >> 32) mod 2^32
+ * (Hammersley second coordinate with a Cranley-Patterson shift). n(X), u(X): linear
+ * interpolation between nodes. */
+void orc_quiet_start(int64_t N, int32_t ncell, const double* nprof, const double* uprof,
+                     double v_th, uint64_t seed, int32_t* cell, double* theta, double* v, double* w);
+
+/* Lifting profile: clamp negative densities to 0 and rescale to keep sum(n) (C18),
+ * u_j = m_j / n_j where n_j > 1e-12 max n, else 0. In place on n; u written. */
+void orc_lift_profile(int32_t ncell, double* n, const double* m, double* u);
+
+/* One resolved PIC burst of K steps with co-moving restriction samples.
+ * State holds v at integer time on entry (vel_at_integer = 1) or at half-integer
+ * time (0). On exit v is at half-integer time. samples: [(K+1)][2][ncell]
+ * (density, momentum). phi is the Newton warm start and is updated.
+ * Returns the number of Newton failures. */
+int orc_burst(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+              int32_t ncell, double dx, double dt, double qm, int32_t K, double dT,
+              int32_t comoving, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+              int32_t vel_at_integer, double* phi, double* samples);
+
+/* Plain PIC: nsteps leapfrog steps (deposit, Newton, gather+push). Same v convention. */
+int orc_pic_steps(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+                  int32_t ncell, double dx, double dt, double qm, int32_t nsteps,
+                  int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                  int32_t vel_at_integer, double* phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

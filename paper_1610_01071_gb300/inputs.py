@@ -1,0 +1,63 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds no arithmetic of the method: it only draws random numbers and
+names the workloads (sizes, amplitudes, seeds). Both the GPU path and the CPU
+oracle consume what it returns.
+
+Workloads (synthetic stand-ins for the paper's ion-acoustic and expansion runs,
+Section 4; normalised units lambda_D = omega_pi = c_s = 1, ion q/m = 1):
+
+* ``iaw_small``  — periodic L=64, 128 cells, 2^17 ions, sine amplitude 0.1,
+  v_th=1, dt=0.1, K=20, M=10, Haar coarse level 16.
+* ``iaw_large``  — ion-wave steepening at scale: periodic 4096 cells (dx=0.5,
+  L=2048), 2^24 ions, amplitude 0.5 on the longest mode, v_th=1, K=20, M=10,
+  50 macro-steps, 256 coarse coefficients per moment.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+WORKLOADS = {
+    "iaw_small": dict(ncell=128, L=64.0, N=1 << 17, amplitude=0.1, v_th=1.0, dt=0.1, K=20, M=10,
+                      n_coarse=16, macro_steps=5, wavelet="haar"),
+    "iaw_large": dict(ncell=4096, L=2048.0, N=1 << 24, amplitude=0.5, v_th=1.0, dt=0.1, K=20, M=10,
+                      n_coarse=256, macro_steps=50, wavelet="haar"),
+}
+
+
+def workload(name: str) -> dict:
+    cfg = dict(WORKLOADS[name])
+    cfg["dT"] = cfg["M"] * cfg["K"] * cfg["dt"]  # macro step = M bursts of K fine steps
+    cfg["qm"] = 1.0
+    return cfg
+
+
+def random_particles(N: int, ncell: int, seed: int, v_th: float = 1.0, sort: bool = True,
+                     w_lo: float = 0.5, w_hi: float = 1.5):
+    """Random FP32 particle state (cell int32, theta f32 in [0,1), v f32, w f32).
+
+    Weights are uniform in [w_lo, w_hi) * ncell/N so that the mean density is ~1.
+    With ``sort`` the cells are non-decreasing (the layout lifting produces)."""
+    rng = np.random.default_rng(seed)
+    cell = rng.integers(0, ncell, N, dtype=np.int64).astype(np.int32)
+    if sort:
+        cell.sort()
+    theta = rng.random(N, dtype=np.float32)
+    v = (rng.standard_normal(N) * v_th).astype(np.float32)
+    w = ((w_lo + (w_hi - w_lo) * rng.random(N)) * (ncell / N)).astype(np.float32)
+    return cell, theta, v, w
+
+
+def random_field(ncell: int, seed: int, amp: float = 0.1):
+    """Smooth random periodic nodal field (a few low Fourier modes), float64."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(ncell) / ncell
+    f = np.zeros(ncell)
+    for m in range(1, 5):
+        f += amp / m * (rng.standard_normal() * np.cos(2 * np.pi * m * x) + rng.standard_normal() * np.sin(2 * np.pi * m * x))
+    return f
+
+
+def random_density(ncell: int, seed: int, amp: float = 0.3):
+    """Positive periodic nodal density around 1 (float64)."""
+    return 1.0 + random_field(ncell, seed, amp)
