@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark: projective-integration PIC on the ion-wave steepening workload at scale
+(periodic, 4096 cells, 2^24 ions, amplitude 0.5, v_th 1, burst K = 20, projective
+ratio M = 10, 256 Haar coefficients per moment).
+
+One benchmark step is one projective macro step (Section 3.1): lift -> 20 fine PIC
+steps with a co-moving restriction sample after each (Appendix B) -> coarsening ->
+least-squares slope -> forward-Euler leap over Delta t = M K dt. ``value`` is the
+fine particle-steps executed per second; the simulated time per wall-second of the
+projective path and of plain (resolved) GPU PIC are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent realisation (replicas, weak
+scaling, no data-path collective); timing is the maximum over ranks.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and simulated time per wall-second, projective vs plain PIC"
+UNIT = "particle-steps/s"
+FUSED_BYTES_PER_PARTICLE = 28  # read cell, theta, v, w (16 B) + write cell, theta, v (12 B)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d and isinstance(d[k], (int, float)):
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the benchmark runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.tmp.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def workload_cfg():
+    from paper_1610_01071_gb300 import inputs
+
+    return inputs.workload("iaw_large")
+
+
+# ------------------------------------------------------------------ oracle (CPU) legs
+
+
+def oracle_macro_step(cfg, n_sample, seed):
+    """One projective macro step of the workload with n_sample particles; returns the
+    number of fine particle-steps done and the wall time."""
+    import numpy as np
+
+    import oracle as orc
+
+    ncell = cfg["ncell"]
+    ocfg = dict(cfg, N=n_sample, s_w=orc.fx_shift(8.0 * ncell / n_sample))
+    nprof, uprof = orc.sine_profile(ncell, cfg["L"], cfg["amplitude"])
+    coarse = np.stack([orc.coarsen(nprof, cfg["n_coarse"]), orc.coarsen(nprof * uprof, cfg["n_coarse"])])
+    t0 = time.perf_counter()
+    st = orc.lift(coarse, ocfg, seed)
+    orc.efpi_macro_step(st, ocfg, np.zeros(ncell))
+    return n_sample * cfg["K"], time.perf_counter() - t0
+
+
+def cpu_baseline(cfg, n_sample=1 << 23):
+    ps, t = oracle_macro_step(cfg, n_sample, seed=1)
+    return {"value": ps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one projective macro step (lift, {cfg['K']}-step burst with co-moving restriction, "
+                       f"coarsening, projection) of the {cfg['ncell']}-cell workload with {n_sample} of its "
+                       f"{cfg['N']} particles, FP64, single thread; {t:.1f} s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload_cfg()
+    n_sample = 1 << 20
+    for _ in range(args.warmup):
+        oracle_macro_step(cfg, n_sample, seed=7)
+    tot_ps, tot_t = 0, 0.0
+    for k in range(args.steps):
+        ps, t = oracle_macro_step(cfg, n_sample, seed=100 + k)
+        tot_ps += ps
+        tot_t += t
+    value = tot_ps / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "iaw_large_oracle_sample", "ncell": cfg["ncell"], "particles": n_sample,
+                       "K": cfg["K"], "M": cfg["M"], "n_coarse": cfg["n_coarse"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one macro step with {n_sample} of {cfg['N']} particles"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1610_01071_gb300 import _binding as pb
+    from paper_1610_01071_gb300 import _build
+
+    _build.build()
+    cfg = workload_cfg()
+    N, K, ncell = cfg["N"], cfg["K"], cfg["ncell"]
+    stream = torch.cuda.Stream(device=dev)
+    c = pb.make_config(ncell, cfg["n_coarse"], K, N, cfg["L"], cfg["dt"], cfg["dT"], qm=cfg["qm"], v_th=cfg["v_th"],
+                       wavelet=cfg["wavelet"], seed=1000 + rank, sort_every=20, newton_tol=1e-10)
+    ctx = pb.Context(c, device=dev, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    with torch.cuda.stream(stream):
+        ctx.load_initial(cfg["amplitude"])
+        for _ in range(args.warmup):
+            ctx.step()
+        if ctx.sync_status() != 0:
+            raise RuntimeError("device status after warm-up: " + pb.load().pe_strerror(ctx.sync_status()).decode())
+        # ---------------- timed region: projective macro steps, inputs resident in HBM
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.profile_read()
+        ctx.profile(True)
+        launches0 = pb.launch_count()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.step()
+        ev1.record(stream)
+        barrier()
+        launches = pb.launch_count() - launches0
+        ctx.profile(False)
+        prof = ctx.profile_read()
+        t_proj = ev0.elapsed_time(ev1) / 1e3
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError("device status after the timed region: " + pb.load().pe_strerror(st).decode())
+        # ---------------- plain (resolved) GPU PIC on the same workload, same context
+        ctx.load_initial(cfg["amplitude"])
+        ctx.pic_steps(max(3, args.warmup) * K)
+        n_plain = max(args.steps, 1) * K
+        barrier()
+        ev0.record(stream)
+        ctx.pic_steps(n_plain)
+        ev1.record(stream)
+        barrier()
+        t_plain = ev0.elapsed_time(ev1) / 1e3
+        # ---------------- end to end through the C ABI with host buffers
+        host = torch.empty((2, cfg["n_coarse"]), dtype=torch.float64).pin_memory()
+        ctx.load_initial(cfg["amplitude"])
+        ctx.get_coarse_host(host)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_coarse_host(host)
+            ctx.step()
+            ctx.get_coarse_host(host)
+        t_e2e = time.perf_counter() - t0
+        barrier()
+    clocks = sampler.stop()
+
+    t_proj_max = max_over_ranks(t_proj)
+    t_plain_max = max_over_ranks(t_plain)
+    t_e2e_max = max_over_ranks(t_e2e)
+    ps_proj = sum_over_ranks(float(N) * K * args.steps)
+    ps_plain = sum_over_ranks(float(N) * n_plain)
+    value = ps_proj / t_proj_max
+    sim_proj = cfg["dT"] * args.steps / t_proj_max
+    sim_plain = cfg["dt"] * n_plain / t_plain_max
+    peak, peak_kind = peak_hbm()
+    push_ms = prof["push_ms"] / max(prof["push_launches"], 1)
+    achieved = FUSED_BYTES_PER_PARTICLE * N / (push_ms / 1e3) / 1e9
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_proj_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "iaw_large", "ncell": ncell, "particles": N, "K": K, "M": cfg["M"],
+                   "n_coarse": cfg["n_coarse"], "wavelet": cfg["wavelet"], "dt": cfg["dt"], "dT": cfg["dT"],
+                   "l2": "inputs larger than L2 (268 MB of particles per realisation), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "sim_time_per_wall_s": {"projective": sim_proj, "plain_pic": sim_plain,
+                                "ratio": sim_proj / sim_plain},
+        "plain_pic": {"value": ps_plain / t_plain_max, "unit": UNIT, "steps": n_plain,
+                      "ms_per_step": 1e3 * t_plain_max / n_plain, "sort_every": 20},
+        "field_solve_us": 1e3 * prof["field_ms"] / max(prof["field_launches"], 1),
+        "roofline": {"kernel": "k_particles<push+sample> (gather, kick, drift, deposit, co-moving sample)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_particle": FUSED_BYTES_PER_PARTICLE, "launch_us": 1e3 * push_ms,
+                     "launches": prof["push_launches"]},
+        "e2e": {"value": ps_proj / t_e2e_max, "unit": UNIT, "h2d_bytes_per_step": 8 * 2 * cfg["n_coarse"],
+                "d2h_bytes_per_step": 8 * 2 * cfg["n_coarse"]},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,290 @@
+/*
+ * pepic.h — C ABI of the GB300 (sm_103a) projective-integration PIC library
+ * (libpepic.so). Method: Cazeaux & Hesthaven, "Projective multiscale
+ * time-integration for electrostatic particle-in-cell methods".
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Units: Debye length, ion plasma frequency, sound speed, e, m_i, T_e, n_0 = 1.
+ * - Periodic domain [0, L) with ncell cells (ncell a power of two, >= 8), nodes
+ *   x_j = j dx, dx = L / ncell.
+ * - A particle is (cell int32, theta float, v float, w float): X = (cell + theta) dx,
+ *   theta in [0, 1). Arrays are structure-of-arrays, device memory, each base
+ *   pointer 16-byte aligned (any torch CUDA allocation is). Any n >= 0 is allowed.
+ * - Fixed-point deposit rule (deterministic, order independent): theta_q =
+ *   rn(theta 2^24), w_q = rn(w 2^s_w), q_R = w_q theta_q, q_L = w_q (2^24 - theta_q),
+ *   summed in int64 at nodes cell and cell+1. Density n_j = rho_j 2^-(s_w+24).
+ *   Momentum uses the same split with m_q = rn(w V 2^s_p). Choose s_w so that
+ *   w 2^s_w <= 2^22 (pe_config.w_cap does this for the context API).
+ * - "stream" is a cudaStream_t (NULL = legacy default stream). All device work is
+ *   asynchronous on it; no entry point allocates or frees device memory: the
+ *   caller owns every buffer.
+ * - Errors: a return value != PE_OK means nothing was launched (bad arguments or a
+ *   launch error). Faults found on the device (particle cell out of range,
+ *   fixed-point overflow, Newton non-convergence) are OR-ed into a caller-owned
+ *   device status word (uint32) as PE_FLAG_* bits and never trap; the caller reads
+ *   it after synchronising (the context API does this in pe_sync_status).
+ */
+#ifndef PEPIC_H
+#define PEPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PE_API __attribute__((visibility("default")))
+#else
+#define PE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define PE_OK 0
+#define PE_EINVAL 1    /* invalid argument (size, alignment, power of two, ...) */
+#define PE_ECUDA 2     /* CUDA runtime error while launching */
+#define PE_ENOCONV 3   /* Newton did not converge within newton_maxit */
+#define PE_EOVERFLOW 4 /* a weight or momentum exceeded its fixed-point range */
+#define PE_ERANGE 5    /* a particle cell index was outside [0, ncell) */
+#define PE_ESTATE 6    /* call out of order for the context state */
+
+#define PE_FLAG_NOCONV 1u
+#define PE_FLAG_OVERFLOW 2u
+#define PE_FLAG_RANGE 4u
+
+#define PE_WAVELET_HAAR 0 /* orthonormal Haar filter */
+#define PE_WAVELET_D4 1   /* Daubechies 4-tap orthonormal filter */
+
+#define PE_POISSON_BOLTZMANN 0  /* -Lap phi + exp(phi) = n   (Section 3.3, Eq. poisson2rescaled) */
+#define PE_POISSON_LINEARIZED 1 /* -Lap phi + 1 + phi = n    (its small-amplitude limit) */
+
+#define PE_PROFILE_SINE 0 /* n = 1 + a cos(2 pi x / L), u = a cos(2 pi x / L) (Section 4.1) */
+
+PE_API const char* pe_strerror(int code);
+PE_API const char* pe_version(void);
+
+/* =================================================================== kernels
+ * Stateless entry points: one hot-path step each, on caller buffers.
+ */
+
+/* Charge deposit, Section 2.2 (particles projected on the nodes with the CIC
+ * shape). rho_fx[ncell] (int64) is overwritten with the fixed-point nodal charge
+ * of the n particles. Exact and independent of particle order. */
+PE_API int pe_deposit(const int32_t* cell, const float* theta, const float* w, int64_t n,
+                      int32_t ncell, int32_t s_w, int64_t* rho_fx, uint32_t* status, void* stream);
+
+/* Field solve, Section 3.3, Eq. (poisson2rescaled) discretised on the nodes:
+ * -(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 + g(phi_j) = n_j with g = exp (mode
+ * PE_POISSON_BOLTZMANN) or 1 + phi (PE_POISSON_LINEARIZED), n_j = rho_fx_j 2^-(s_w+24).
+ * Newton iteration in FP64 from the initial guess in phi[ncell] (in/out), each
+ * update a cyclic tridiagonal solve, damped to |update| <= 2, stopped when
+ * max|update| < tol. Then E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx) into E[ncell]
+ * (FP64) and Ef[ncell] (FP32 copy used by the particle kernels).
+ * diag (device, int32[2], may be NULL) gets {iterations, converged}. Non-convergence
+ * sets PE_FLAG_NOCONV. */
+PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
+                    double tol, int32_t maxit, double* phi, double* E, float* Ef, int32_t* diag,
+                    uint32_t* status, void* stream);
+
+/* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
+ * follows it): each particle, at its integer-time velocity Vbar, is carried to
+ * X~ = X + tau Vbar, V~ = Vbar + qm tau E_n(X), and w and w V~ are deposited
+ * (CIC, fixed point) at X~. tau = Delta t - p delta t (0 disables the frame). */
+typedef struct pe_sample_args {
+    const float* E0f;  /* E_n, the field stored at burst start, float[ncell] */
+    float tau;         /* Delta t - p delta t */
+    float qm;          /* ion charge-to-mass ratio */
+    float inv_dx;      /* 1 / dx */
+    int32_t s_w;       /* density fixed-point shift (pe_push requires the same s_w) */
+    int32_t s_p;       /* momentum fixed-point shift: |w V~| 2^s_p must stay <= 2^22 */
+    int64_t* sample_fx; /* int64[2][ncell]: density then momentum; overwritten */
+} pe_sample_args;
+
+/* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
+ * positions and (if sample != NULL) with the co-moving restriction sample of the
+ * current positions:
+ *   E(X) = (1 - theta) Ef[cell] + theta Ef[cell+1]
+ *   Vbar = v + (kick - 1/2) qm_dt E(X)        (integer-time velocity, sample only)
+ *   v   += kick qm_dt E(X)                      (kick = 1/2 when v is at integer time)
+ *   X   += v dt, periodic; cell/theta/v updated in place.
+ * rho_fx[ncell] is overwritten with the deposit of the pushed particles. */
+PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n,
+                   const float* Ef, int32_t ncell, float dt_over_dx, float qm_dt, float kick,
+                   int32_t s_w, int64_t* rho_fx, const pe_sample_args* sample,
+                   uint32_t* status, void* stream);
+
+/* Restriction sample only (no push), e.g. the last sample p = N_e of a burst:
+ * the same sample as pe_push, with Vbar = v + (kick - 1/2) qm_dt E(X). */
+PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, const float* w,
+                     int64_t n, const float* Ef, int32_t ncell, float qm_dt, float kick,
+                     const pe_sample_args* sample, uint32_t* status, void* stream);
+
+/* Restriction to coarse variables, Section 3.3 and Appendix A (Eq.
+ * ScalingCoeffHistogram): for each of nsamples samples and each moment
+ * (density, momentum) the fine nodal values f_j = sample_fx 2^-(s+24) are taken as
+ * scaling coefficients 2^{-J_f/2} f_j at level J_f = log2(ncell), then the periodized
+ * orthonormal DWT is applied down to n_coarse scaling coefficients; details are
+ * discarded. coarse[nsamples][2][n_coarse] (FP64) is overwritten. */
+PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
+                      int32_t s_p, int32_t wavelet, int32_t n_coarse, double* coarse, void* stream);
+
+/* Projective forward-Euler step, Section 3.3, Eqs. (extrapolation2) and
+ * (leastsquares): slope_i = sum_p 6 (K - 2p) / (K (K+1) (K+2) dt) [c_{K-p,i} - c_{p,i}],
+ * out_i = c_{K,i} + (dT - K dt) slope_i, for ncoef coefficients of samples
+ * c[(K+1)][ncoef]. slope (may be NULL) and out are FP64[ncoef]. */
+PE_API int pe_ls_project(const double* samples, int32_t K, int32_t ncoef, double dt, double dT,
+                         double* out, double* slope, void* stream);
+
+/* Lifting profile, Section 3.3 ("increasing the resolution"): inverse DWT of the
+ * coarse density and momentum coefficients coarse[2][n_coarse] with zero details,
+ * f_j = 2^{J_f/2} a_j; negative densities clamped to 0 and the density rescaled to
+ * keep its sum; u_j = m_j / n_j (0 where n_j <= 1e-12 max n). Writes float
+ * prof_n[ncell], prof_u[ncell]. */
+PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
+                     float* prof_n, float* prof_u, void* stream);
+
+/* Quiet-start loading, Appendix C, on nodal profiles (linear interpolation):
+ * particle i of n = ppc*ncell: cell = i / ppc, theta = (2 (i mod ppc) + 1) / (2 ppc),
+ * w = n(X) / ppc, V = u(X) + v_th Phi^-1(b_i), b_i = (B_i + 1/2) 2^-32 with
+ * B_i = brev32(i) + floor(2^31 / n) + (splitmix64(seed) >> 32) mod 2^32 (Hammersley
+ * second coordinate with a Cranley-Patterson shift). Output is sorted by cell.
+ * If rho_fx != NULL it is overwritten with the charge deposit of the new particles. */
+PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                          int32_t ncell, const float* prof_n, const float* prof_u, float v_th,
+                          uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
+                          void* stream);
+
+/* Sort by cell (counting sort), used by the plain PIC path to keep the deposit's
+ * per-block grids local. Reads (cell, theta, v, w), writes the permuted particles to
+ * the out_* arrays (which must not alias the inputs). scratch: int32[2*ncell + 64].
+ * The order of particles inside a cell is not specified; the multiset is exact. */
+PE_API int pe_sort(const int32_t* cell, const float* theta, const float* v, const float* w,
+                   int64_t n, int32_t ncell, int32_t* out_cell, float* out_theta, float* out_v,
+                   float* out_w, int32_t* scratch, uint32_t* status, void* stream);
+
+/* =================================================================== context
+ * One realisation of the projective-integration cycle (Section 3.1, Figure
+ * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares
+ * slope -> forward-Euler leap of the coarse variables.
+ */
+typedef struct pe_config {
+    int32_t ncell;        /* fine cells, power of two */
+    int32_t n_coarse;     /* coarse coefficients per moment, power of two dividing ncell */
+    int32_t wavelet;      /* PE_WAVELET_* */
+    int32_t K;            /* burst length N_e (fine steps per macro step) */
+    int64_t nparticles;   /* ppc * ncell */
+    double L;             /* domain length */
+    double dt;            /* fine step delta t */
+    double dT;            /* macro step Delta t (>= K dt) */
+    double qm;            /* ion charge-to-mass ratio */
+    double v_th;          /* ion thermal speed used by lifting */
+    int32_t comoving;     /* 1: restriction along approximate characteristics (App. B) */
+    int32_t poisson;      /* PE_POISSON_* */
+    double newton_tol;    /* max |Newton update| to stop (e.g. 1e-10) */
+    int32_t newton_maxit; /* e.g. 30 */
+    int32_t sort_every;   /* plain PIC: sort every this many steps (0 = never) */
+    uint64_t seed;        /* lifting shift seeds: splitmix64(seed + macro step) */
+    double w_cap;         /* largest particle weight (fixed-point range); 0 = 8 ncell / N */
+    double v_cap;         /* largest |V~| in restriction samples; 0 = 32 */
+} pe_config;
+
+typedef struct pe_ctx pe_ctx;
+
+/* Named regions of the caller-allocated device arena. */
+enum pe_buffer {
+    PE_BUF_PARTICLES_A = 0, /* cell i32[N] | theta f32[N] | v f32[N] | w f32[N] */
+    PE_BUF_PARTICLES_B,     /* second bank (sort target) */
+    PE_BUF_RHO,             /* int64[ncell] charge deposit */
+    PE_BUF_PHI,             /* f64[ncell] potential (Newton warm start) */
+    PE_BUF_E,               /* f64[ncell] field */
+    PE_BUF_EF,              /* f32[ncell] field copy for the particle kernels */
+    PE_BUF_E0F,             /* f32[ncell] field at burst start */
+    PE_BUF_SAMPLES_FX,      /* int64[K+1][2][ncell] restriction samples */
+    PE_BUF_COARSE_SAMPLES,  /* f64[K+1][2][n_coarse] */
+    PE_BUF_COARSE,          /* f64[2][n_coarse] current coarse state */
+    PE_BUF_SLOPE,           /* f64[2][n_coarse] last least-squares slope */
+    PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u) */
+    PE_BUF_SORT,            /* int32[2 ncell + 64] sort scratch */
+    PE_BUF_STATUS,          /* uint32[4] status word; int32[2] Newton diag after it */
+    PE_NBUF
+};
+
+typedef struct pe_layout {
+    size_t total_bytes;     /* size of the arena the caller must allocate */
+    size_t offset[PE_NBUF]; /* 256-byte aligned offsets into the arena */
+    size_t bytes[PE_NBUF];
+} pe_layout;
+
+typedef struct pe_diag {
+    int64_t macro_steps;    /* completed projective steps */
+    int64_t fine_steps;     /* fine PIC steps run (bursts + plain PIC) */
+    double time;            /* simulated time */
+    int32_t particle_bank;  /* 0 or 1: which PE_BUF_PARTICLES_* holds the particles */
+    int32_t v_at_integer;   /* 1 if stored v is at integer time (after load/lift) */
+    int32_t s_w, s_p;       /* fixed-point shifts in use */
+    int32_t newton_iters;   /* iterations of the last field solve (after sync) */
+    uint32_t status;        /* device status word (after sync) */
+} pe_diag;
+
+/* Validates cfg and fills the arena layout. PE_EINVAL on a bad configuration. */
+PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out);
+
+/* Binds a context to a caller-allocated device arena of at least
+ * layout.total_bytes (256-byte aligned) and a stream. No device allocation.
+ * The context (host memory) is owned by the library: free it with pe_destroy. */
+PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_bytes, void* stream,
+                     pe_ctx** out);
+PE_API void pe_destroy(pe_ctx* ctx);
+
+/* Initial state at t = 0 from an analytic nodal profile (PE_PROFILE_SINE with the
+ * given amplitude) by the quiet start; also computes the initial coarse state. */
+PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude);
+
+/* Micro-scale evolution (Section 3.1): K fine steps from the current particles with
+ * the co-moving restriction sample of each of the K+1 instants (Appendix B). */
+PE_API int pe_burst(pe_ctx* ctx);
+/* Coarsening of the K+1 samples (pe_coarsen into PE_BUF_COARSE_SAMPLES). */
+PE_API int pe_restrict(pe_ctx* ctx);
+/* Least-squares slope and forward-Euler leap to t + Delta t (pe_ls_project). */
+PE_API int pe_project(pe_ctx* ctx);
+/* Lifting (Section 3.3 + Appendix C): coarse state -> profiles -> quiet start. */
+PE_API int pe_lift(pe_ctx* ctx);
+/* One projective macro step: lift (unless the particles are fresh), burst,
+ * restrict, project. Advances time by Delta t. */
+PE_API int pe_step(pe_ctx* ctx);
+/* Plain (resolved) PIC: nsteps leapfrog steps with deposit + Newton each step,
+ * sorting every sort_every steps. Advances time by nsteps dt. */
+PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps);
+/* Coarse state of the current particles (restriction at integer time, no frame
+ * shift) into host or device memory out[2][n_coarse]. */
+PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device);
+
+/* Copy the coarse state (f64[2][n_coarse]) out of / into the context. */
+PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device);
+PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
+
+/* Synchronises the context's stream and returns PE_OK or the first device fault
+ * (PE_ERANGE, PE_EOVERFLOW, PE_ENOCONV); clears the status word. */
+PE_API int pe_sync_status(pe_ctx* ctx);
+/* Host-side counters (no synchronisation except for newton_iters/status, which are
+ * read after a stream synchronise). */
+PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out);
+
+/* Kernel timing for measurement: while enabled, the context records a pair of CUDA
+ * events on its stream around every particle-kernel launch (pe_push, pe_sample,
+ * pe_quiet_start) and every field solve (pe_field) it issues. pe_profile_read
+ * synchronises, returns the summed elapsed milliseconds and launch counts since the
+ * last read, and resets them. Events are host resources created on first use. */
+PE_API int pe_profile(pe_ctx* ctx, int32_t enable);
+PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
+                           int64_t* field_launches);
+
+/* Number of kernels this library has launched in the process so far. */
+PE_API int64_t pe_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEPIC_H */

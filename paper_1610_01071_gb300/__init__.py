@@ -1,5 +1,12 @@
 """GB300-native projective-integration PIC (Cazeaux & Hesthaven, arXiv:1610.01071).
 
-The compute path is the CUDA library ``libpepic.so`` built from ``csrc/``; the
-Python side only marshals arguments to its C ABI (``include/pepic.h``).
+The compute path is the CUDA library ``libpepic.so`` built from ``csrc/`` for
+sm_103a; this package only marshals arguments to its C ABI (``include/pepic.h``).
+Calls raise if the library is missing: there is no CPU path.
 """
+from . import inputs
+from ._binding import (BUF, Config, Context, PepicError, coarsen, deposit, field, layout, load, ls_project,
+                       make_config, make_sample_args, push, quiet_start, refine, sample, sort)
+
+__all__ = ["BUF", "Config", "Context", "PepicError", "coarsen", "deposit", "field", "inputs", "layout", "load",
+           "ls_project", "make_config", "make_sample_args", "push", "quiet_start", "refine", "sample", "sort"]

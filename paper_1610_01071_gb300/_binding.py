@@ -1,0 +1,360 @@
+"""ctypes binding of libpepic.so (C ABI in include/pepic.h).
+
+Argument marshalling only: torch provides the device memory and the stream, every
+step of the method runs in the CUDA library. There is no CPU fallback: if the
+library is missing, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpepic.so")
+
+PE_OK, PE_EINVAL, PE_ECUDA, PE_ENOCONV, PE_EOVERFLOW, PE_ERANGE, PE_ESTATE = range(7)
+PE_WAVELET = {"haar": 0, "d4": 1}
+PE_POISSON = {"boltzmann": 0, "linearized": 1}
+PE_PROFILE_SINE = 0
+PE_NBUF = 14
+BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
+           coarse=9, slope=10, profile=11, sort=12, status=13)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PepicError(RuntimeError):
+    pass
+
+
+class SampleArgs(ctypes.Structure):
+    _fields_ = [("E0f", ctypes.c_void_p), ("tau", ctypes.c_float), ("qm", ctypes.c_float),
+                ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
+                ("sample_fx", ctypes.c_void_p)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int32), ("n_coarse", ctypes.c_int32), ("wavelet", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("nparticles", ctypes.c_int64), ("L", ctypes.c_double),
+                ("dt", ctypes.c_double), ("dT", ctypes.c_double), ("qm", ctypes.c_double),
+                ("v_th", ctypes.c_double), ("comoving", ctypes.c_int32), ("poisson", ctypes.c_int32),
+                ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int32), ("sort_every", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("total_bytes", ctypes.c_size_t), ("offset", ctypes.c_size_t * PE_NBUF),
+                ("bytes", ctypes.c_size_t * PE_NBUF)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("macro_steps", ctypes.c_int64), ("fine_steps", ctypes.c_int64), ("time", ctypes.c_double),
+                ("particle_bank", ctypes.c_int32), ("v_at_integer", ctypes.c_int32), ("s_w", ctypes.c_int32),
+                ("s_p", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_uint32)]
+
+
+# exported symbol -> (restype, argtypes); the test-suite checks this against include/pepic.h
+P, i32, i64, u64, f32, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_float, ctypes.c_double, ctypes.c_size_t)
+SIGNATURES = {
+    "pe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pe_version": (ctypes.c_char_p, []),
+    "pe_deposit": (ctypes.c_int, [P, P, P, i64, i32, i32, P, P, P]),
+    "pe_field": (ctypes.c_int, [P, i32, f64, i32, i32, f64, i32, P, P, P, P, P, P]),
+    "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
+    "pe_sample": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, ctypes.POINTER(SampleArgs), P, P]),
+    "pe_coarsen": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, P, P]),
+    "pe_ls_project": (ctypes.c_int, [P, i32, i32, f64, f64, P, P, P]),
+    "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
+    "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
+    "pe_sort": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P, P]),
+    "pe_layout_for": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Layout)]),
+    "pe_create": (ctypes.c_int, [ctypes.POINTER(Config), P, sz, P, ctypes.POINTER(P)]),
+    "pe_destroy": (None, [P]),
+    "pe_load_initial": (ctypes.c_int, [P, i32, f64]),
+    "pe_burst": (ctypes.c_int, [P]),
+    "pe_restrict": (ctypes.c_int, [P]),
+    "pe_project": (ctypes.c_int, [P]),
+    "pe_lift": (ctypes.c_int, [P]),
+    "pe_step": (ctypes.c_int, [P]),
+    "pe_pic_steps": (ctypes.c_int, [P, i32]),
+    "pe_measure": (ctypes.c_int, [P, P, i32]),
+    "pe_get_coarse": (ctypes.c_int, [P, P, i32]),
+    "pe_set_coarse": (ctypes.c_int, [P, P, i32]),
+    "pe_sync_status": (ctypes.c_int, [P]),
+    "pe_diagnostics": (ctypes.c_int, [P, ctypes.POINTER(Diag)]),
+    "pe_profile": (ctypes.c_int, [P, i32]),
+    "pe_profile_read": (ctypes.c_int, [P, P, P, P, P]),
+    "pe_launch_count": (i64, []),
+}
+
+
+def launch_count() -> int:
+    return int(load().pe_launch_count())
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpepic.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise PepicError(f"{path} is missing: build it with paper_1610_01071_gb300._build.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc: int, what: str = ""):
+    if rc != PE_OK:
+        msg = load().pe_strerror(rc).decode()
+        raise PepicError(f"{what}: {msg} (code {rc})")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise PepicError("device tensor expected (the library has no CPU path)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _status(status, dev):
+    return status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+
+
+# ------------------------------------------------------------------ stateless kernels
+
+
+def deposit(cell, theta, w, ncell, s_w, rho=None, status=None, stream=None):
+    dev = cell.device
+    rho = rho if rho is not None else torch.empty(ncell, dtype=torch.int64, device=dev)
+    status = _status(status, dev)
+    check(load().pe_deposit(_ptr(cell), _ptr(theta), _ptr(w), cell.numel(), ncell, s_w, _ptr(rho), _ptr(status),
+                            _stream(stream)), "pe_deposit")
+    return rho
+
+
+def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, status=None, stream=None):
+    dev = rho.device
+    E = torch.empty(ncell, dtype=torch.float64, device=dev)
+    Ef = torch.empty(ncell, dtype=torch.float32, device=dev)
+    diag = torch.zeros(2, dtype=torch.int32, device=dev)
+    status = _status(status, dev)
+    check(load().pe_field(_ptr(rho), ncell, float(dx), s_w, PE_POISSON[mode], float(tol), int(maxit), _ptr(phi),
+                          _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status), _stream(stream)), "pe_field")
+    return E, Ef, diag
+
+
+def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx):
+    return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
+                      ctypes.c_void_p(sample_fx.data_ptr()))
+
+
+def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
+         stream=None):
+    dev = cell.device
+    rho = rho if rho is not None else torch.empty(ncell, dtype=torch.int64, device=dev)
+    status = _status(status, dev)
+    sp = ctypes.byref(sample) if sample is not None else None
+    check(load().pe_push(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), ncell,
+                         float(dt_over_dx), float(qm_dt), float(kick), s_w, _ptr(rho), sp, _ptr(status),
+                         _stream(stream)), "pe_push")
+    return rho
+
+
+def sample(cell, theta, v, w, Ef, ncell, qm_dt, kick, args, status=None, stream=None):
+    status = _status(status, cell.device)
+    check(load().pe_sample(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), ncell, float(qm_dt),
+                           float(kick), ctypes.byref(args), _ptr(status), _stream(stream)), "pe_sample")
+
+
+def coarsen(sample_fx, nsamples, ncell, s_w, s_p, n_coarse, wavelet="haar", out=None, stream=None):
+    out = out if out is not None else torch.empty((nsamples, 2, n_coarse), dtype=torch.float64,
+                                                  device=sample_fx.device)
+    check(load().pe_coarsen(_ptr(sample_fx), nsamples, ncell, s_w, s_p, PE_WAVELET[wavelet], n_coarse, _ptr(out),
+                            _stream(stream)), "pe_coarsen")
+    return out
+
+
+def ls_project(samples, dt, dT, stream=None):
+    """samples: [(K+1), ncoef] float64 on the device. Returns (out, slope)."""
+    K, ncoef = samples.shape[0] - 1, samples.shape[1]
+    out = torch.empty(ncoef, dtype=torch.float64, device=samples.device)
+    slope = torch.empty_like(out)
+    check(load().pe_ls_project(_ptr(samples), K, ncoef, float(dt), float(dT), _ptr(out), _ptr(slope),
+                               _stream(stream)), "pe_ls_project")
+    return out, slope
+
+
+def refine(coarse, ncell, wavelet="haar", stream=None):
+    """coarse: [2, n_coarse] float64. Returns float32 (n, u) profiles."""
+    nc = coarse.shape[-1]
+    prof_n = torch.empty(ncell, dtype=torch.float32, device=coarse.device)
+    prof_u = torch.empty_like(prof_n)
+    check(load().pe_refine(_ptr(coarse), nc, PE_WAVELET[wavelet], ncell, _ptr(prof_n), _ptr(prof_u),
+                           _stream(stream)), "pe_refine")
+    return prof_n, prof_u
+
+
+def quiet_start(n, ncell, prof_n, prof_u, v_th, seed, s_w, with_rho=True, status=None, stream=None):
+    dev = prof_n.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    status = _status(status, dev)
+    check(load().pe_quiet_start(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, _ptr(prof_n), _ptr(prof_u),
+                                float(v_th), int(seed) & 0xFFFFFFFFFFFFFFFF, s_w, _ptr(rho), _ptr(status),
+                                _stream(stream)), "pe_quiet_start")
+    return cell, theta, v, w, rho
+
+
+def sort(cell, theta, v, w, ncell, status=None, stream=None):
+    dev = cell.device
+    oc, ot, ov, ow = torch.empty_like(cell), torch.empty_like(theta), torch.empty_like(v), torch.empty_like(w)
+    scratch = torch.empty(2 * ncell + 64, dtype=torch.int32, device=dev)
+    status = _status(status, dev)
+    check(load().pe_sort(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), ncell, _ptr(oc), _ptr(ot),
+                         _ptr(ov), _ptr(ow), _ptr(scratch), _ptr(status), _stream(stream)), "pe_sort")
+    return oc, ot, ov, ow
+
+
+# ------------------------------------------------------------------ context
+
+
+def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
+                poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
+                v_cap=0.0) -> Config:
+    return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
+                  float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
+                  int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap))
+
+
+def layout(cfg: Config) -> Layout:
+    lay = Layout()
+    check(load().pe_layout_for(ctypes.byref(cfg), ctypes.byref(lay)), "pe_layout_for")
+    return lay
+
+
+class Context:
+    """One realisation: a caller-owned device arena (torch) bound to a pe_ctx."""
+
+    def __init__(self, cfg: Config, device="cuda", stream=None):
+        self.cfg = cfg
+        self.lay = layout(cfg)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.arena = torch.empty(self.lay.total_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena.data_ptr()
+        self._pad = (-base) % 256
+        self._h = ctypes.c_void_p()
+        check(load().pe_create(ctypes.byref(cfg), ctypes.c_void_p(base + self._pad), self.lay.total_bytes,
+                               _stream(self.stream), ctypes.byref(self._h)), "pe_create")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pe_destroy(h)
+            self._h = None
+
+    def _call(self, name, *args):
+        check(getattr(load(), name)(self._h, *args), name)
+
+    # -- cycle
+    def load_initial(self, amplitude):
+        self._call("pe_load_initial", PE_PROFILE_SINE, float(amplitude))
+
+    def burst(self):
+        self._call("pe_burst")
+
+    def restrict(self):
+        self._call("pe_restrict")
+
+    def project(self):
+        self._call("pe_project")
+
+    def lift(self):
+        self._call("pe_lift")
+
+    def step(self):
+        self._call("pe_step")
+
+    def pic_steps(self, nsteps):
+        self._call("pe_pic_steps", int(nsteps))
+
+    def measure(self, out=None):
+        out = out if out is not None else torch.empty((2, self.cfg.n_coarse), dtype=torch.float64,
+                                                      device=self.device)
+        self._call("pe_measure", _ptr(out), 1)
+        return out
+
+    def get_coarse(self):
+        out = torch.empty((2, self.cfg.n_coarse), dtype=torch.float64, device=self.device)
+        self._call("pe_get_coarse", _ptr(out), 1)
+        return out
+
+    def set_coarse(self, coarse):
+        c = coarse.to(self.device, torch.float64).contiguous()
+        self._call("pe_set_coarse", _ptr(c), 1)
+
+    def get_coarse_host(self, out):
+        """Copies the coarse state into a (pinned) host tensor [2, n_coarse] through the C ABI."""
+        assert out.device.type == "cpu" and out.dtype == torch.float64 and out.is_contiguous()
+        check(load().pe_get_coarse(self._h, ctypes.c_void_p(out.data_ptr()), 0), "pe_get_coarse")
+        return out
+
+    def set_coarse_host(self, src):
+        assert src.device.type == "cpu" and src.dtype == torch.float64 and src.is_contiguous()
+        check(load().pe_set_coarse(self._h, ctypes.c_void_p(src.data_ptr()), 0), "pe_set_coarse")
+
+    def sync_status(self):
+        return load().pe_sync_status(self._h)
+
+    def diagnostics(self) -> Diag:
+        d = Diag()
+        check(load().pe_diagnostics(self._h, ctypes.byref(d)), "pe_diagnostics")
+        return d
+
+    def profile(self, enable=True):
+        self._call("pe_profile", int(bool(enable)))
+
+    def profile_read(self):
+        """Summed event time (ms) and launch counts of particle kernels and field solves."""
+        pm, pl, fm, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+        check(load().pe_profile_read(self._h, ctypes.byref(pm), ctypes.byref(pl), ctypes.byref(fm),
+                                     ctypes.byref(fl)), "pe_profile_read")
+        return dict(push_ms=pm.value, push_launches=pl.value, field_ms=fm.value, field_launches=fl.value)
+
+    # -- typed views into the arena (for tests and inspection)
+    def view(self, buf: str, dtype, count=None):
+        i = BUF[buf]
+        off = self._pad + self.lay.offset[i]
+        nbytes = self.lay.bytes[i]
+        t = self.arena[off:off + nbytes].view(dtype)
+        return t if count is None else t[:count]
+
+    def particles(self, bank=None):
+        """(cell, theta, v, w) views of the current (or given) particle bank."""
+        if bank is None:
+            bank = self.diagnostics().particle_bank
+        N = self.cfg.nparticles
+        stride = ((4 * N + 255) // 256) * 256
+        off = self._pad + self.lay.offset[BUF["particles_a"] + bank]
+        seg = [self.arena[off + k * stride: off + k * stride + 4 * N] for k in range(4)]
+        return (seg[0].view(torch.int32), seg[1].view(torch.float32), seg[2].view(torch.float32),
+                seg[3].view(torch.float32))

@@ -1,0 +1,536 @@
+// Context API: one realisation of the projective-integration cycle (Section 3.1):
+// lift -> K fine PIC steps with a restriction sample after each -> least-squares
+// slope -> forward-Euler leap of the coarse variables; plus the plain PIC path.
+// Host orchestration only: every step runs in the kernels of the other files.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <vector>
+
+#include "pe_internal.h"
+#include "pepic.h"
+
+namespace pe {
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+int max_smem_optin()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (dev < 0 || dev >= 64) return 48 * 1024;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cache[dev] = v > 0 ? v : 48 * 1024;
+    }
+    return cache[dev];
+}
+
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static int fx_shift(double cap)
+{
+    int e = 0;
+    double m = frexp(cap, &e);
+    return 22 - ((m == 0.5) ? e - 1 : e);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace pe
+
+using namespace pe;
+
+struct pe_ctx {
+    pe_config cfg;
+    pe_layout lay;
+    char* arena;
+    cudaStream_t stream;
+    double dx;
+    int s_w, s_p, nc;
+    int bank;            // which particle bank is current
+    int v_at_integer;    // stored v is at integer time
+    int fresh;           // particles were just loaded/lifted (not yet advanced)
+    int rho_valid;       // rho holds the deposit of the current particles
+    int64_t macro_steps, fine_steps;
+    double time;
+    int32_t* cell[2];
+    float* theta[2];
+    float* v[2];
+    float* w[2];
+    int64_t* rho;
+    double* phi;
+    double* E;
+    float* Ef;
+    float* E0f;
+    int64_t* samples;  // [K+2][2][ncell]; row K+1 is measurement scratch
+    double* csamples;  // [K+2][2][nc]
+    double* coarse;
+    double* slope;
+    float* prof;
+    int32_t* sort;
+    uint32_t* status;
+    int32_t* diag;
+    // kernel timing (pe_profile)
+    int profiling;
+    std::vector<cudaEvent_t>* ev_push;   // start/stop pairs
+    std::vector<cudaEvent_t>* ev_field;
+    size_t n_push, n_field;               // pairs recorded since the last read
+};
+
+#define PE_TRY(x)                   \
+    do {                            \
+        int _rc = (x);              \
+        if (_rc != PE_OK) return _rc; \
+    } while (0)
+
+extern "C" PE_API const char* pe_strerror(int code)
+{
+    switch (code) {
+    case PE_OK: return "ok";
+    case PE_EINVAL: return "invalid argument";
+    case PE_ECUDA: return "CUDA runtime error";
+    case PE_ENOCONV: return "Newton iteration did not converge";
+    case PE_EOVERFLOW: return "fixed-point range exceeded (weight or momentum too large)";
+    case PE_ERANGE: return "particle cell index out of range";
+    case PE_ESTATE: return "call out of order for the context state";
+    default: return "unknown error";
+    }
+}
+
+extern "C" PE_API const char* pe_version(void) { return "pepic 0.1 (sm_103a)"; }
+
+extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
+{
+    if (!cfg || !out) return PE_EINVAL;
+    const pe_config& c = *cfg;
+    if (!is_pow2(c.ncell) || c.ncell < 8 || c.ncell > kFullGridMax) return PE_EINVAL;
+    if (!is_pow2(c.n_coarse) || c.n_coarse > c.ncell) return PE_EINVAL;
+    if (c.K < 1 || c.K > 4096) return PE_EINVAL;
+    if (c.nparticles < c.ncell || c.nparticles % c.ncell != 0 || c.nparticles >= (int64_t(1) << 32)) return PE_EINVAL;
+    if (!(c.L > 0.0) || !(c.dt > 0.0) || !(c.dT >= c.K * c.dt * (1.0 - 1e-12)) || !(c.v_th >= 0.0)) return PE_EINVAL;
+    if (c.wavelet != PE_WAVELET_HAAR && c.wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    if (c.poisson != PE_POISSON_BOLTZMANN && c.poisson != PE_POISSON_LINEARIZED) return PE_EINVAL;
+    if (c.newton_maxit < 1 || !(c.newton_tol > 0.0) || c.sort_every < 0) return PE_EINVAL;
+    if (c.w_cap < 0.0 || c.v_cap < 0.0) return PE_EINVAL;
+    memset(out, 0, sizeof(*out));
+    const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
+    const size_t bank = 4 * align256(4 * N);
+    out->bytes[PE_BUF_PARTICLES_A] = bank;
+    out->bytes[PE_BUF_PARTICLES_B] = bank;
+    out->bytes[PE_BUF_RHO] = 8 * nc;
+    out->bytes[PE_BUF_PHI] = 8 * nc;
+    out->bytes[PE_BUF_E] = 8 * nc;
+    out->bytes[PE_BUF_EF] = 4 * nc;
+    out->bytes[PE_BUF_E0F] = 4 * nc;
+    out->bytes[PE_BUF_SAMPLES_FX] = 8 * 2 * nc * (size_t)(c.K + 2);
+    out->bytes[PE_BUF_COARSE_SAMPLES] = 8 * 2 * ncoef * (size_t)(c.K + 2);
+    out->bytes[PE_BUF_COARSE] = 8 * 2 * ncoef;
+    out->bytes[PE_BUF_SLOPE] = 8 * 2 * ncoef;
+    out->bytes[PE_BUF_PROFILE] = 4 * 2 * nc;
+    out->bytes[PE_BUF_SORT] = 4 * (2 * nc + 64);
+    out->bytes[PE_BUF_STATUS] = 64;
+    size_t off = 0;
+    for (int b = 0; b < PE_NBUF; ++b) {
+        out->offset[b] = off;
+        off += align256(out->bytes[b]);
+    }
+    out->total_bytes = off;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_bytes, void* stream, pe_ctx** out)
+{
+    if (!out) return PE_EINVAL;
+    *out = nullptr;
+    pe_layout lay;
+    PE_TRY(pe_layout_for(cfg, &lay));
+    if (!arena || ((uintptr_t)arena & 255u) || arena_bytes < lay.total_bytes) return PE_EINVAL;
+    pe_ctx* x = (pe_ctx*)calloc(1, sizeof(pe_ctx));
+    if (!x) return PE_EINVAL;
+    x->cfg = *cfg;
+    x->lay = lay;
+    x->arena = (char*)arena;
+    x->stream = (cudaStream_t)stream;
+    x->dx = cfg->L / cfg->ncell;
+    x->nc = cfg->n_coarse;
+    const double w_cap = cfg->w_cap > 0.0 ? cfg->w_cap : 8.0 * cfg->ncell / (double)cfg->nparticles;
+    const double v_cap = cfg->v_cap > 0.0 ? cfg->v_cap : 32.0;
+    x->s_w = fx_shift(w_cap);
+    x->s_p = fx_shift(w_cap * v_cap);
+    const size_t N = (size_t)cfg->nparticles;
+    for (int b = 0; b < 2; ++b) {
+        char* base = x->arena + lay.offset[PE_BUF_PARTICLES_A + b];
+        x->cell[b] = (int32_t*)base;
+        x->theta[b] = (float*)(base + align256(4 * N));
+        x->v[b] = (float*)(base + 2 * align256(4 * N));
+        x->w[b] = (float*)(base + 3 * align256(4 * N));
+    }
+    x->rho = (int64_t*)(x->arena + lay.offset[PE_BUF_RHO]);
+    x->phi = (double*)(x->arena + lay.offset[PE_BUF_PHI]);
+    x->E = (double*)(x->arena + lay.offset[PE_BUF_E]);
+    x->Ef = (float*)(x->arena + lay.offset[PE_BUF_EF]);
+    x->E0f = (float*)(x->arena + lay.offset[PE_BUF_E0F]);
+    x->samples = (int64_t*)(x->arena + lay.offset[PE_BUF_SAMPLES_FX]);
+    x->csamples = (double*)(x->arena + lay.offset[PE_BUF_COARSE_SAMPLES]);
+    x->coarse = (double*)(x->arena + lay.offset[PE_BUF_COARSE]);
+    x->slope = (double*)(x->arena + lay.offset[PE_BUF_SLOPE]);
+    x->prof = (float*)(x->arena + lay.offset[PE_BUF_PROFILE]);
+    x->sort = (int32_t*)(x->arena + lay.offset[PE_BUF_SORT]);
+    x->status = (uint32_t*)(x->arena + lay.offset[PE_BUF_STATUS]);
+    x->diag = (int32_t*)(x->status + 4);
+    if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||
+        cudaMemsetAsync(x->status, 0, 64, x->stream) != cudaSuccess) {
+        free(x);
+        return PE_ECUDA;
+    }
+    *out = x;
+    return PE_OK;
+}
+
+static void destroy_events(std::vector<cudaEvent_t>* v)
+{
+    if (!v) return;
+    for (cudaEvent_t e : *v) cudaEventDestroy(e);
+    delete v;
+}
+
+extern "C" PE_API void pe_destroy(pe_ctx* ctx)
+{
+    if (!ctx) return;
+    destroy_events(ctx->ev_push);
+    destroy_events(ctx->ev_field);
+    free(ctx);
+}
+
+extern "C" PE_API int64_t pe_launch_count(void) { return g_launches.load(); }
+
+// Records the event with index 2*slot (+1 for stop) of the pool, creating it on demand.
+static int record(pe_ctx* x, std::vector<cudaEvent_t>*& pool, size_t slot, int stop)
+{
+    if (!pool) pool = new std::vector<cudaEvent_t>();
+    const size_t i = 2 * slot + (size_t)stop;
+    while (pool->size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return PE_ECUDA;
+        pool->push_back(e);
+    }
+    return cudaEventRecord((*pool)[i], x->stream) == cudaSuccess ? PE_OK : PE_ECUDA;
+}
+
+// Wraps one launch in a start/stop event pair when profiling is on.
+template <class F>
+static int timed(pe_ctx* x, int is_field, F&& launch)
+{
+    if (!x->profiling) return launch();
+    std::vector<cudaEvent_t>*& pool = is_field ? x->ev_field : x->ev_push;
+    size_t& n = is_field ? x->n_field : x->n_push;
+    PE_TRY(record(x, pool, n, 0));
+    PE_TRY(launch());
+    PE_TRY(record(x, pool, n, 1));
+    ++n;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_profile(pe_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return PE_EINVAL;
+    ctx->profiling = enable ? 1 : 0;
+    return PE_OK;
+}
+
+static double sum_pairs(std::vector<cudaEvent_t>* pool, size_t n)
+{
+    double tot = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, (*pool)[2 * k], (*pool)[2 * k + 1]) == cudaSuccess) tot += ms;
+    }
+    return tot;
+}
+
+extern "C" PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
+                                      int64_t* field_launches)
+{
+    if (!ctx) return PE_EINVAL;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (push_ms) *push_ms = ctx->n_push ? sum_pairs(ctx->ev_push, ctx->n_push) : 0.0;
+    if (push_launches) *push_launches = (int64_t)ctx->n_push;
+    if (field_ms) *field_ms = ctx->n_field ? sum_pairs(ctx->ev_field, ctx->n_field) : 0.0;
+    if (field_launches) *field_launches = (int64_t)ctx->n_field;
+    ctx->n_push = ctx->n_field = 0;
+    return PE_OK;
+}
+
+static int field_solve(pe_ctx* x)
+{
+    const pe_config& c = x->cfg;
+    return timed(x, 1, [&] {
+        return pe_field(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.newton_tol, c.newton_maxit, x->phi, x->E,
+                        x->Ef, x->diag, x->status, x->stream);
+    });
+}
+
+static int deposit_current(pe_ctx* x)
+{
+    const int b = x->bank;
+    PE_TRY(pe_deposit(x->cell[b], x->theta[b], x->w[b], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho, x->status,
+                      x->stream));
+    x->rho_valid = 1;
+    return PE_OK;
+}
+
+static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
+{
+    pe_sample_args a;
+    a.E0f = x->E0f;
+    a.tau = (float)tau;
+    a.qm = (float)x->cfg.qm;
+    a.inv_dx = (float)(1.0 / x->dx);
+    a.s_w = x->s_w;
+    a.s_p = x->s_p;
+    a.sample_fx = dst;
+    return a;
+}
+
+static int quiet_start_from_profile(pe_ctx* x, uint64_t seed)
+{
+    const pe_config& c = x->cfg;
+    const int b = x->bank;
+    PE_TRY(timed(x, 0, [&] {
+        return pe_quiet_start(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->prof,
+                              x->prof + c.ncell, (float)c.v_th, seed, x->s_w, x->rho, x->status, x->stream);
+    }));
+    x->rho_valid = 1;
+    x->v_at_integer = 1;
+    x->fresh = 1;
+    return PE_OK;
+}
+
+static uint64_t lift_seed(const pe_ctx* x) { return x->cfg.seed + 0x632BE59BD9B4E019ULL * (uint64_t)(x->macro_steps + 1); }
+
+extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device)
+{
+    if (!ctx || !out) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    if (!x->rho_valid) PE_TRY(deposit_current(x));
+    PE_TRY(field_solve(x));
+    int64_t* dst = x->samples + (size_t)(c.K + 1) * 2 * c.ncell;
+    pe_sample_args a = sample_args(x, 0.0, dst);
+    a.E0f = x->Ef;  // tau = 0: the frame field is not used
+    const int b = x->bank;
+    const float kick = x->v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
+                     &a, x->status, x->stream));
+    double* cdst = x->csamples + (size_t)(c.K + 1) * 2 * x->nc;
+    PE_TRY(pe_coarsen(dst, 1, c.ncell, x->s_w, x->s_p, c.wavelet, x->nc, cdst, x->stream));
+    const size_t bytes = sizeof(double) * 2 * x->nc;
+    if (cudaMemcpyAsync(out, cdst, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (!out_on_device && cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude)
+{
+    if (!ctx || profile != PE_PROFILE_SINE) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    std::vector<float> h(2 * (size_t)c.ncell);
+    for (int j = 0; j < c.ncell; ++j) {
+        const double xj = j * x->dx;
+        const double pert = amplitude * cos(2.0 * M_PI * xj / c.L);
+        h[j] = (float)(1.0 + pert);
+        h[c.ncell + j] = (float)pert;
+    }
+    if (cudaMemcpyAsync(x->prof, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;  // host buffer goes out of scope
+    if (cudaMemsetAsync(x->phi, 0, sizeof(double) * c.ncell, x->stream) != cudaSuccess) return PE_ECUDA;
+    x->bank = 0;
+    x->macro_steps = 0;
+    x->fine_steps = 0;
+    x->time = 0.0;
+    PE_TRY(quiet_start_from_profile(x, c.seed));
+    return pe_measure(x, x->coarse, 1);
+}
+
+extern "C" PE_API int pe_burst(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    const int b = x->bank;
+    if (!x->rho_valid) PE_TRY(deposit_current(x));
+    PE_TRY(field_solve(x));
+    if (cudaMemcpyAsync(x->E0f, x->Ef, sizeof(float) * c.ncell, cudaMemcpyDeviceToDevice, x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    float kick = x->v_at_integer ? 0.5f : 1.0f;
+    const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
+    for (int p = 0; p <= c.K; ++p) {
+        const double tau = c.comoving ? c.dT - p * c.dt : 0.0;
+        pe_sample_args a = sample_args(x, tau, x->samples + (size_t)p * 2 * c.ncell);
+        if (p == c.K) {
+            PE_TRY(timed(x, 0, [&] {
+                return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick,
+                                 &a, x->status, x->stream);
+            }));
+            break;
+        }
+        PE_TRY(timed(x, 0, [&] {
+            return pe_push(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
+                           kick, x->s_w, x->rho, &a, x->status, x->stream);
+        }));
+        PE_TRY(field_solve(x));
+        kick = 1.0f;
+    }
+    x->v_at_integer = 0;
+    x->rho_valid = 1;
+    x->fresh = 0;
+    x->fine_steps += c.K;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_restrict(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    const pe_config& c = ctx->cfg;
+    return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->csamples,
+                      ctx->stream);
+}
+
+extern "C" PE_API int pe_project(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    const pe_config& c = ctx->cfg;
+    PE_TRY(pe_ls_project(ctx->csamples, c.K, 2 * ctx->nc, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
+    ctx->macro_steps += 1;
+    ctx->time += c.dT;
+    ctx->fresh = 0;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_lift(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
+    return quiet_start_from_profile(x, lift_seed(x));
+}
+
+extern "C" PE_API int pe_step(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    if (!ctx->fresh) PE_TRY(pe_lift(ctx));
+    PE_TRY(pe_burst(ctx));
+    PE_TRY(pe_restrict(ctx));
+    return pe_project(ctx);
+}
+
+extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
+{
+    if (!ctx || nsteps < 0) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
+    for (int s = 0; s < nsteps; ++s) {
+        if (c.sort_every > 0 && (x->fine_steps % c.sort_every) == 0 && !x->fresh) {
+            const int b = x->bank, o = 1 - b;
+            PE_TRY(pe_sort(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->cell[o], x->theta[o],
+                           x->v[o], x->w[o], x->sort, x->status, x->stream));
+            x->bank = o;
+        }
+        if (!x->rho_valid) PE_TRY(deposit_current(x));
+        PE_TRY(field_solve(x));
+        const int b = x->bank;
+        const float kick = x->v_at_integer ? 0.5f : 1.0f;
+        PE_TRY(timed(x, 0, [&] {
+            return pe_push(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt, kick,
+                           x->s_w, x->rho, nullptr, x->status, x->stream);
+        }));
+        x->v_at_integer = 0;
+        x->rho_valid = 1;
+        x->fresh = 0;
+        x->fine_steps += 1;
+        x->time += c.dt;
+    }
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device)
+{
+    if (!ctx || !out) return PE_EINVAL;
+    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    if (cudaMemcpyAsync(out, ctx->coarse, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (!out_on_device && cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device)
+{
+    if (!ctx || !in) return PE_EINVAL;
+    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    if (cudaMemcpyAsync(ctx->coarse, in, bytes, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (!in_on_device && cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    ctx->fresh = 0;  // the next step lifts from this state
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_sync_status(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    uint32_t st = 0;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t), ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (st & PE_FLAG_RANGE) return PE_ERANGE;
+    if (st & PE_FLAG_OVERFLOW) return PE_EOVERFLOW;
+    if (st & PE_FLAG_NOCONV) return PE_ENOCONV;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out)
+{
+    if (!ctx || !out) return PE_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->macro_steps = ctx->macro_steps;
+    out->fine_steps = ctx->fine_steps;
+    out->time = ctx->time;
+    out->particle_bank = ctx->bank;
+    out->v_at_integer = ctx->v_at_integer;
+    out->s_w = ctx->s_w;
+    out->s_p = ctx->s_p;
+    int32_t d[2] = {0, 0};
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemcpy(d, ctx->diag, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemcpy(&out->status, ctx->status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
+    out->newton_iters = d[0];
+    return PE_OK;
+}

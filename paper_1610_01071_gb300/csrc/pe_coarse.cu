@@ -1,0 +1,213 @@
+// Coarse-variable kernels (FP64): restriction of the fine moment samples to wavelet
+// scaling coefficients, the least-squares projective leap, and the lifting profile.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pe_common.cuh"
+#include "pe_internal.h"
+
+namespace pe {
+
+// Orthonormal scaling filter (sum h = sqrt 2); the wavelet filter is
+// g_m = (-1)^m h_{len-1-m} and is not needed: details are discarded.
+struct Filter {
+    double h[4];
+    int len;
+};
+
+static Filter make_filter(int wavelet)
+{
+    Filter f{};
+    if (wavelet == PE_WAVELET_D4) {
+        // Daubechies' four-tap filter in closed form: (1+r3, 3+r3, 3-r3, 1-r3) / (4 sqrt 2)
+        const double r3 = sqrt(3.0), den = 4.0 * sqrt(2.0);
+        f.h[0] = (1.0 + r3) / den;
+        f.h[1] = (3.0 + r3) / den;
+        f.h[2] = (3.0 - r3) / den;
+        f.h[3] = (1.0 - r3) / den;
+        f.len = 4;
+    } else {
+        f.h[0] = f.h[1] = 1.0 / sqrt(2.0);
+        f.len = 2;
+    }
+    return f;
+}
+
+// One block per (sample, moment) row: fine values -> level-J_f scaling coefficients ->
+// periodized analysis (approximation branch only) down to n_coarse coefficients.
+__global__ void __launch_bounds__(256) k_coarsen(const long long* fx, int ncell, double scale_n, double scale_m,
+                                                 Filter f, int n_coarse, double* out)
+{
+    extern __shared__ double buf[];
+    double* a = buf;
+    double* b = buf + ncell;
+    const int row = blockIdx.x;
+    const double scale = (row & 1) ? scale_m : scale_n;
+    const long long* src = fx + (size_t)row * ncell;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) a[j] = (double)src[j] * scale;
+    __syncthreads();
+    for (int len = ncell; len > n_coarse; len >>= 1) {
+        const int half = len >> 1;
+        for (int k = threadIdx.x; k < half; k += blockDim.x) {
+            double acc = 0.0;
+            for (int m = 0; m < f.len; ++m) acc += f.h[m] * a[(2 * k + m) & (len - 1)];
+            b[k] = acc;
+        }
+        __syncthreads();
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    for (int k = threadIdx.x; k < n_coarse; k += blockDim.x) out[(size_t)row * n_coarse + k] = a[k];
+}
+
+// Least-squares slope in the paired form of Eq. (leastsquares) and the forward-Euler leap.
+__global__ void k_ls_project(const double* c, int K, int ncoef, double dt, double dT, double* out, double* slope)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncoef) return;
+    const double den = (double)K * (K + 1) * (K + 2) * dt;
+    double s = 0.0;
+    for (int p = 0; 2 * p <= K; ++p)
+        s += 6.0 * (K - 2 * p) / den * (c[(size_t)(K - p) * ncoef + i] - c[(size_t)p * ncoef + i]);
+    if (slope) slope[i] = s;
+    out[i] = c[(size_t)K * ncoef + i] + (dT - K * dt) * s;
+}
+
+__device__ double block_sum_d(double v, double* red)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    return warp_sum(lane < nw ? red[lane] : 0.0);
+}
+
+__device__ double block_max_d(double v, double* red)
+{
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    return warp_max(lane < nw ? red[lane] : -1e300);
+}
+
+// Periodized synthesis with zero details from nin coefficients in a to 2*nin in b.
+__device__ void synth_level(const Filter& f, const double* a, int nin, double* b)
+{
+    const int n = 2 * nin;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double acc = 0.0;
+        for (int m = (i & 1); m < f.len; m += 2) acc += f.h[m] * a[((i - m) & (n - 1)) >> 1];
+        b[i] = acc;
+    }
+}
+
+// Returns the buffer holding the refined values (one of x, y).
+__device__ double* synthesise(const Filter& f, const double* coarse, int nc, int ncell, double* x, double* y,
+                              double scale)
+{
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) x[k] = coarse[k];
+    __syncthreads();
+    double* a = x;
+    double* b = y;
+    for (int len = nc; len < ncell; len <<= 1) {
+        synth_level(f, a, len, b);
+        __syncthreads();
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) a[j] *= scale;
+    __syncthreads();
+    return a;
+}
+
+__global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, Filter f, int ncell, double scale,
+                                                 float* prof_n, float* prof_u)
+{
+    extern __shared__ double buf[];
+    __shared__ double red[32];
+    double* X = buf;
+    double* Y = buf + ncell;
+    double* Z = buf + 2 * ncell;
+    double* nf = synthesise(f, coarse, nc, ncell, X, Y, scale);
+    double* o1 = (nf == X) ? Y : X;
+    // clamp negative densities and keep the total
+    double s0 = 0.0, s1 = 0.0, neg = 0.0;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        const double v = nf[j];
+        s0 += v;
+        s1 += fmax(v, 0.0);
+        neg += (v < 0.0) ? 1.0 : 0.0;
+    }
+    s0 = block_sum_d(s0, red);
+    s1 = block_sum_d(s1, red);
+    neg = block_sum_d(neg, red);
+    const double resc = (neg > 0.0 && s1 > 0.0 && s0 > 0.0) ? s0 / s1 : 1.0;
+    double nmax = 0.0;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        const double v = fmax(nf[j], 0.0) * resc;
+        nf[j] = v;
+        nmax = fmax(nmax, v);
+    }
+    nmax = block_max_d(nmax, red);
+    double* mf = synthesise(f, coarse + nc, nc, ncell, o1, Z, scale);
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        const double n = nf[j];
+        prof_n[j] = (float)n;
+        prof_u[j] = (n > 1e-12 * nmax) ? (float)(mf[j] / n) : 0.0f;
+    }
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w, int32_t s_p,
+                                 int32_t wavelet, int32_t n_coarse, double* coarse, void* stream)
+{
+    if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || nsamples < 1 || !sample_fx || !coarse)
+        return PE_EINVAL;
+    if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    const size_t smem = 2 * sizeof(double) * (size_t)ncell;
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    if (cudaFuncSetAttribute((const void*)k_coarsen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return PE_ECUDA;
+    const double lev = pow(2.0, -0.5 * ilog2(ncell));
+    k_coarsen<<<2 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), ncell,
+                                                                 ldexp(1.0, -(s_w + 24)) * lev,
+                                                                 ldexp(1.0, -(s_p + 24)) * lev, make_filter(wavelet),
+                                                                 n_coarse, coarse);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_ls_project(const double* samples, int32_t K, int32_t ncoef, double dt, double dT, double* out,
+                                    double* slope, void* stream)
+{
+    if (!samples || !out || K < 1 || ncoef < 1 || !(dt > 0.0)) return PE_EINVAL;
+    const int block = 256;
+    k_ls_project<<<(ncoef + block - 1) / block, block, 0, (cudaStream_t)stream>>>(samples, K, ncoef, dt, dT, out, slope);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell, float* prof_n,
+                                float* prof_u, void* stream)
+{
+    if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || !coarse || !prof_n || !prof_u) return PE_EINVAL;
+    if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    const size_t smem = 3 * sizeof(double) * (size_t)ncell;
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    if (cudaFuncSetAttribute((const void*)k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return PE_ECUDA;
+    k_refine<<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
+                                                      pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u);
+    return launch_status();
+}

@@ -1,0 +1,593 @@
+// Particle kernels: charge deposit, leapfrog gather+push fused with the deposit and
+// the co-moving restriction sample, quiet-start loading, and the counting sort.
+//
+// Layout: structure of arrays (cell int32, theta f32, v f32, w f32), read and written
+// as 16-byte vectors of four consecutive particles; each block owns one contiguous
+// chunk of the (cell-sorted) particle array, so its deposits land in a narrow range
+// of nodes: per-lane register windows absorb most of them, the rest go to a
+// block-private int64 grid in shared memory that is flushed once with global atomics.
+// All sums are integers, so the result is exact and independent of order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pe_common.cuh"
+#include "pe_internal.h"
+
+namespace pe {
+
+struct PushParams {
+    int32_t* cell;
+    float* theta;
+    float* v;
+    const float* w;
+    int64_t n;
+    int64_t chunk;
+    const float* Ef;
+    int ncell, mask;
+    float dt_dx, qm_dt, kick, wscale;
+    unsigned long long* rho;  // charge of the pushed particles (PUSH) or current ones (DEPOSIT)
+    int rho_width;
+    const float* E0f;  // restriction sample (SAMPLE)
+    float tau_dx, qm_tau, pscale;
+    unsigned long long* samp_n;
+    unsigned long long* samp_m;
+    int samp_width;
+    uint32_t* status;
+};
+
+enum Mode { kDeposit = 0, kPush = 1, kPushSample = 2, kSample = 3 };
+
+__device__ __forceinline__ int32_t fx_weight(float x, float scale, uint32_t* status)
+{
+    int32_t q = __float2int_rn(x * scale);
+    if (q > (1 << 23) || q < -(1 << 23)) raise_flag(status, PE_FLAG_OVERFLOW);
+    return q;
+}
+
+template <int MODE>
+__device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
+                                        LaneWindow& lw, const SmemGrid& grho, const SmemGrid& gsn,
+                                        const SmemGrid& gsm, int& c_out, float& th_out, float& v_out)
+{
+    c_out = c;
+    th_out = th;
+    v_out = vv;
+    if ((unsigned)c >= (unsigned)P.ncell) {
+        raise_flag(P.status, PE_FLAG_RANGE);
+        return;
+    }
+    const int32_t wq = fx_weight(ww, P.wscale, P.status);
+    if (MODE == kDeposit) {
+        lw.add(c, fx_split(wq, th), grho);
+        return;
+    }
+    const int c1 = (c + 1) & P.mask;
+    const float Ec = __ldg(P.Ef + c), Ec1 = __ldg(P.Ef + c1);
+    const float Ep = fmaf(th, Ec1 - Ec, Ec);  // CIC gather
+    if (MODE == kPushSample || MODE == kSample) {
+        // Appendix B: carry the particle along the approximate characteristic to t_{n+1}
+        const float vbar = fmaf((P.kick - 0.5f) * P.qm_dt, Ep, vv);  // integer-time velocity
+        const float E0c = __ldg(P.E0f + c), E0c1 = __ldg(P.E0f + c1);
+        const float E0p = fmaf(th, E0c1 - E0c, E0c);
+        const float xs = fmaf(P.tau_dx, vbar, th);
+        const float fl = floorf(xs);
+        float ths = xs - fl;
+        int k = (int)fl;
+        if (ths >= 1.0f) {
+            ths = 0.0f;
+            k += 1;
+        }
+        const int cs = (c + k) & P.mask, cs1 = (cs + 1) & P.mask;
+        const float vt = fmaf(P.qm_tau, E0p, vbar);
+        const FxSplit qn = fx_split(wq, ths);
+        const FxSplit qp = fx_split(fx_weight(ww * vt, P.pscale, P.status), ths);
+        gsn.add(cs, qn.left);
+        gsn.add(cs1, qn.right);
+        gsm.add(cs, qp.left);
+        gsm.add(cs1, qp.right);
+    }
+    if (MODE == kPush || MODE == kPushSample) {
+        // Section 2.2 leapfrog: kick with the gathered field, then drift
+        const float vn = fmaf(P.kick * P.qm_dt, Ep, vv);
+        const float s = fmaf(vn, P.dt_dx, th);
+        const float fl = floorf(s);
+        float thn = s - fl;
+        int k = (int)fl;
+        if (thn >= 1.0f) {
+            thn = 0.0f;
+            k += 1;
+        }
+        const int cn = (c + k) & P.mask;
+        c_out = cn;
+        th_out = thn;
+        v_out = vn;
+        lw.add(cn, fx_split(wq, thn), grho);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_particles(PushParams P)
+{
+    extern __shared__ unsigned long long smem[];
+    constexpr bool kRho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
+    constexpr bool kSamp = (MODE == kPushSample || MODE == kSample);
+    constexpr bool kWrite = (MODE == kPush || MODE == kPushSample);
+
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
+
+    SmemGrid grho{smem, P.rho, 0, kRho ? P.rho_width : 0, P.mask};
+    if (kRho && P.rho_width < P.ncell) grho.base = (c_first - 64) & P.mask;
+    unsigned long long* s1 = smem + (kRho ? P.rho_width : 0);
+    SmemGrid gsn{s1, P.samp_n, 0, kSamp ? P.samp_width : 0, P.mask};
+    SmemGrid gsm{s1 + (kSamp ? P.samp_width : 0), P.samp_m, 0, kSamp ? P.samp_width : 0, P.mask};
+    if (kSamp && P.samp_width < P.ncell) {
+        gsn.base = (c_first - P.samp_width / 2) & P.mask;
+        gsm.base = gsn.base;
+    }
+    if (kRho) grho.zero();
+    if (kSamp) {
+        gsn.zero();
+        gsm.zero();
+    }
+    __syncthreads();
+
+    LaneWindow lw;
+    lw.reset((c_first - 1) & P.mask);
+
+    const int64_t g0 = begin >> 2, g1 = end >> 2;  // begin is a multiple of 4
+    const int B = blockDim.x;
+    int4* cell4 = reinterpret_cast<int4*>(P.cell);
+    float4* th4 = reinterpret_cast<float4*>(P.theta);
+    float4* v4 = reinterpret_cast<float4*>(P.v);
+    const float4* w4 = reinterpret_cast<const float4*>(P.w);
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += 2 * B) {
+        const bool two = g + B < g1;
+        int4 ca = cell4[g];
+        float4 ta = th4[g];
+        float4 va = (MODE == kDeposit) ? make_float4(0.f, 0.f, 0.f, 0.f) : v4[g];
+        float4 wa = __ldg(w4 + g);
+        int4 cb = make_int4(0, 0, 0, 0);
+        float4 tb = make_float4(0.f, 0.f, 0.f, 0.f), vb = tb, wb = tb;
+        if (two) {
+            cb = cell4[g + B];
+            tb = th4[g + B];
+            if (MODE != kDeposit) vb = v4[g + B];
+            wb = __ldg(w4 + g + B);
+        }
+        int4 co;
+        float4 to, vo;
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, grho, gsn, gsm, co.x, to.x, vo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, grho, gsn, gsm, co.y, to.y, vo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, grho, gsn, gsm, co.z, to.z, vo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, grho, gsn, gsm, co.w, to.w, vo.w);
+        if (kWrite) {
+            cell4[g] = co;
+            th4[g] = to;
+            v4[g] = vo;
+        }
+        if (two) {
+            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, grho, gsn, gsm, co.x, to.x, vo.x);
+            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, grho, gsn, gsm, co.y, to.y, vo.y);
+            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, grho, gsn, gsm, co.z, to.z, vo.z);
+            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, grho, gsn, gsm, co.w, to.w, vo.w);
+            if (kWrite) {
+                cell4[g + B] = co;
+                th4[g + B] = to;
+                v4[g + B] = vo;
+            }
+        }
+    }
+    for (int64_t i = (g1 << 2) + threadIdx.x; i < end; i += B) {  // ragged tail (< 4 particles)
+        int co;
+        float to, vo;
+        float vi = (MODE == kDeposit) ? 0.f : P.v[i];
+        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, grho, gsn, gsm, co, to, vo);
+        if (kWrite) {
+            P.cell[i] = co;
+            P.theta[i] = to;
+            P.v[i] = vo;
+        }
+    }
+    if (kRho) lw.flush(grho);
+    __syncthreads();
+    if (kRho) grho.flush();
+    if (kSamp) {
+        gsn.flush();
+        gsm.flush();
+    }
+}
+
+// ------------------------------------------------------------------ quiet start
+
+struct LoadParams {
+    int32_t* cell;
+    float* theta;
+    float* v;
+    float* w;
+    int64_t n;
+    int64_t chunk;
+    uint32_t ppc;
+    int ncell, mask;
+    float inv_ppc, two_ppc;
+    const float* prof_n;
+    const float* prof_u;
+    float v_th, wscale;
+    uint32_t half, shift;
+    unsigned long long* rho;
+    int rho_width;
+    uint32_t* status;
+};
+
+__device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+{
+    const uint32_t j = i % P.ppc;
+    c = (int)(i / P.ppc);
+    th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    const int c1 = (c + 1) & P.mask;
+    const float n0 = __ldg(P.prof_n + c), n1 = __ldg(P.prof_n + c1);
+    const float u0 = __ldg(P.prof_u + c), u1 = __ldg(P.prof_u + c1);
+    const float nX = fmaf(th, n1 - n0, n0);
+    const float uX = fmaf(th, u1 - u0, u0);
+    ww = nX * P.inv_ppc;
+    // Hammersley second coordinate (radical inverse in base 2) with a Cranley-Patterson shift
+    const uint32_t Bi = __brev(i) + P.half + P.shift;
+    const bool upper = (Bi & 0x80000000u) != 0u;
+    const uint32_t bs = upper ? ~Bi : Bi;  // distance to the nearer end of (0, 1), in 2^-32 units
+    const float b = fmaf(__uint2float_rn(bs), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float z = normcdfinvf(b);
+    vv = fmaf(P.v_th, upper ? -z : z, uX);
+}
+
+__global__ void __launch_bounds__(512) k_quiet_start(LoadParams P)
+{
+    extern __shared__ unsigned long long smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const bool dep = P.rho != nullptr;
+    const int c_first = (begin < end) ? (int)((uint64_t)begin / P.ppc) : 0;
+    SmemGrid grho{smem, P.rho, 0, dep ? P.rho_width : 0, P.mask};
+    if (dep && P.rho_width < P.ncell) grho.base = (c_first - 64) & P.mask;
+    if (dep) grho.zero();
+    __syncthreads();
+    LaneWindow lw;
+    lw.reset((c_first - 1) & P.mask);
+
+    const int64_t g0 = begin >> 2, g1 = end >> 2;
+    int4* cell4 = reinterpret_cast<int4*>(P.cell);
+    float4* th4 = reinterpret_cast<float4*>(P.theta);
+    float4* v4 = reinterpret_cast<float4*>(P.v);
+    float4* w4 = reinterpret_cast<float4*>(P.w);
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        int4 c;
+        float4 t, vv, ww;
+        const uint32_t i0 = (uint32_t)(g << 2);
+        load_one(P, i0, c.x, t.x, vv.x, ww.x);
+        load_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
+        load_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
+        load_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        cell4[g] = c;
+        th4[g] = t;
+        v4[g] = vv;
+        w4[g] = ww;
+        if (dep) {
+            lw.add(c.x, fx_split(fx_weight(ww.x, P.wscale, P.status), t.x), grho);
+            lw.add(c.y, fx_split(fx_weight(ww.y, P.wscale, P.status), t.y), grho);
+            lw.add(c.z, fx_split(fx_weight(ww.z, P.wscale, P.status), t.z), grho);
+            lw.add(c.w, fx_split(fx_weight(ww.w, P.wscale, P.status), t.w), grho);
+        }
+    }
+    for (int64_t i = (g1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
+        int c;
+        float t, vv, ww;
+        load_one(P, (uint32_t)i, c, t, vv, ww);
+        P.cell[i] = c;
+        P.theta[i] = t;
+        P.v[i] = vv;
+        P.w[i] = ww;
+        if (dep) lw.add(c, fx_split(fx_weight(ww, P.wscale, P.status), t), grho);
+    }
+    if (dep) lw.flush(grho);
+    __syncthreads();
+    if (dep) grho.flush();
+}
+
+// ------------------------------------------------------------------ counting sort
+
+__device__ __forceinline__ void warp_count(unsigned* hist, int c)
+{
+    const unsigned peers = __match_any_sync(__activemask(), c);
+    const int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&hist[c], (unsigned)__popc(peers));
+}
+
+__global__ void __launch_bounds__(512) k_sort_count(const int32_t* cell, int64_t n, int64_t chunk, int ncell,
+                                                    unsigned* counts, uint32_t* status)
+{
+    extern __shared__ unsigned hist[];
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    int64_t begin, end;
+    block_chunk(n, chunk, &begin, &end);
+    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        int c = cell[i];
+        if ((unsigned)c >= (unsigned)ncell) {
+            raise_flag(status, PE_FLAG_RANGE);
+            c = 0;  // keep the particle (it is copied, and flagged)
+        }
+        warp_count(hist, c);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[i], hist[i]);
+}
+
+// Exclusive scan of counts[ncell] into cursor[ncell]; one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_sort_scan(const unsigned* counts, unsigned* cursor, int ncell)
+{
+    __shared__ unsigned part[1024];
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per;
+    unsigned s = 0;
+    for (int i = lo; i < lo + per && i < ncell; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele inclusive scan
+        unsigned t = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int i = lo; i < lo + per && i < ncell; ++i) {
+        cursor[i] = run;
+        run += counts[i];
+    }
+}
+
+__global__ void __launch_bounds__(512) k_sort_scatter(const int32_t* cell, const float* theta, const float* v,
+                                                      const float* w, int64_t n, int64_t chunk, int ncell,
+                                                      unsigned* cursor, int32_t* oc, float* ot, float* ov,
+                                                      float* ow)
+{
+    extern __shared__ unsigned sh[];
+    unsigned* hist = sh;          // count of this block's particles per cell
+    unsigned* base = sh + ncell;  // first output slot of this block per cell
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    int64_t begin, end;
+    block_chunk(n, chunk, &begin, &end);
+    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        int c = cell[i];
+        if ((unsigned)c >= (unsigned)ncell) c = 0;
+        warp_count(hist, c);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+        unsigned h = hist[i];
+        base[i] = h ? atomicAdd(&cursor[i], h) : 0u;
+        hist[i] = 0u;
+    }
+    __syncthreads();
+    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        int c = cell[i];
+        if ((unsigned)c >= (unsigned)ncell) c = 0;
+        const unsigned peers = __match_any_sync(__activemask(), c);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        unsigned first = 0;
+        if (lane == leader) first = atomicAdd(&hist[c], (unsigned)__popc(peers));
+        first = __shfl_sync(peers, first, leader);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        const int64_t dst = (int64_t)base[c] + first + rank;
+        oc[dst] = cell[i];
+        ot[dst] = theta[i];
+        ov[dst] = v[i];
+        ow[dst] = w[i];
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    int64_t c = (n + blocks - 1) / blocks;
+    c = (c + 3) & ~int64_t(3);
+    if (c < 4) c = 4;
+    *chunk = c;
+    int64_t g = (n + c - 1) / c;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <int MODE>
+static int launch_particles(PushParams& P, cudaStream_t s)
+{
+    const int block = 512;
+    const bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
+    const bool samp = (MODE == kPushSample || MODE == kSample);
+    P.rho_width = rho ? (P.ncell <= kFullGridMax ? P.ncell : kWindowNodes) : 0;
+    P.samp_width = samp ? (P.ncell <= kFullGridMax ? P.ncell : kWindowNodes) : 0;
+    size_t smem = sizeof(unsigned long long) * (size_t)(P.rho_width + 2 * P.samp_width);
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    const void* k = (const void*)k_particles<MODE>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return PE_ECUDA;
+    int grid = grid_for(k, block, smem, P.n, &P.chunk);
+    if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
+    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)P.ncell, s) != cudaSuccess)
+        return PE_ECUDA;
+    if (P.n == 0) return PE_OK;
+    k_particles<MODE><<<grid, block, smem, s>>>(P);
+    return launch_status();
+}
+
+static bool particles_ok(const void* a, const void* b, const void* c, const void* d, int64_t n)
+{
+    if (n < 0 || n > (int64_t(1) << 32)) return false;
+    if (n == 0) return true;
+    return a && b && c && d && aligned16(a) && aligned16(b) && aligned16(c) && aligned16(d);
+}
+
+static bool sample_ok(const pe_sample_args* s)
+{
+    return s && s->E0f && s->sample_fx && aligned16(s->sample_fx);
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+extern "C" PE_API int pe_deposit(const int32_t* cell, const float* theta, const float* w, int64_t n, int32_t ncell,
+                                 int32_t s_w, int64_t* rho_fx, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !particles_ok(cell, theta, w, w, n)) return PE_EINVAL;
+    PushParams P{};
+    P.cell = const_cast<int32_t*>(cell);
+    P.theta = const_cast<float*>(theta);
+    P.w = w;
+    P.n = n;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.status = status;
+    return launch_particles<kDeposit>(P, (cudaStream_t)stream);
+}
+
+extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
+                              int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w, int64_t* rho_fx,
+                              const pe_sample_args* sample, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !Ef || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
+    if (sample && (!sample_ok(sample) || sample->s_w != s_w)) return PE_EINVAL;
+    PushParams P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.Ef = Ef;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.dt_dx = dt_over_dx;
+    P.qm_dt = qm_dt;
+    P.kick = kick;
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.status = status;
+    if (sample) {
+        P.E0f = sample->E0f;
+        P.tau_dx = sample->tau * sample->inv_dx;
+        P.qm_tau = sample->qm * sample->tau;
+        P.pscale = ldexpf(1.0f, sample->s_p);
+        P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
+        P.samp_m = P.samp_n + ncell;
+        return launch_particles<kPushSample>(P, (cudaStream_t)stream);
+    }
+    return launch_particles<kPush>(P, (cudaStream_t)stream);
+}
+
+extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
+                                const float* Ef, int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample,
+                                uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !Ef || !particles_ok(cell, theta, v, w, n) || !sample_ok(sample))
+        return PE_EINVAL;
+    PushParams P{};
+    P.cell = const_cast<int32_t*>(cell);
+    P.theta = const_cast<float*>(theta);
+    P.v = const_cast<float*>(v);
+    P.w = w;
+    P.n = n;
+    P.Ef = Ef;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.qm_dt = qm_dt;
+    P.kick = kick;
+    P.wscale = ldexpf(1.0f, sample->s_w);
+    P.status = status;
+    P.E0f = sample->E0f;
+    P.tau_dx = sample->tau * sample->inv_dx;
+    P.qm_tau = sample->qm * sample->tau;
+    P.pscale = ldexpf(1.0f, sample->s_p);
+    P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
+    P.samp_m = P.samp_n + ncell;
+    return launch_particles<kSample>(P, (cudaStream_t)stream);
+}
+
+extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                     const float* prof_n, const float* prof_u, float v_th, uint64_t seed, int32_t s_w,
+                                     int64_t* rho_fx, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !prof_n || !prof_u || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
+    if (n % ncell != 0 || n == 0 || n >= (int64_t(1) << 32)) return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    LoadParams P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.ppc = (uint32_t)(n / ncell);
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.inv_ppc = 1.0f / (float)P.ppc;
+    P.two_ppc = 2.0f * (float)P.ppc;
+    P.prof_n = prof_n;
+    P.prof_u = prof_u;
+    P.v_th = v_th;
+    P.wscale = ldexpf(1.0f, s_w);
+    P.half = (uint32_t)(2147483648.0 / (double)n);
+    // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the shift
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    P.shift = (uint32_t)(z >> 32);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.rho_width = rho_fx ? (ncell <= kFullGridMax ? ncell : kWindowNodes) : 0;
+    P.status = status;
+    const int block = 512;
+    size_t smem = sizeof(unsigned long long) * (size_t)P.rho_width;
+    const void* k = (const void*)k_quiet_start;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return PE_ECUDA;
+    int grid = grid_for(k, block, smem, n, &P.chunk);
+    if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    k_quiet_start<<<grid, block, smem, s>>>(P);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_sort(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
+                              int32_t ncell, int32_t* out_cell, float* out_theta, float* out_v, float* out_w,
+                              int32_t* scratch, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !scratch || !particles_ok(cell, theta, v, w, n) ||
+        !particles_ok(out_cell, out_theta, out_v, out_w, n))
+        return PE_EINVAL;
+    if ((size_t)ncell * 2 * sizeof(unsigned) > (size_t)max_smem_optin()) return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* counts = reinterpret_cast<unsigned*>(scratch);
+    unsigned* cursor = counts + ncell;
+    if (cudaMemsetAsync(counts, 0, sizeof(unsigned) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    if (n == 0) return PE_OK;
+    const int block = 512;
+    int64_t chunk = 0;
+    size_t smem1 = sizeof(unsigned) * (size_t)ncell, smem2 = 2 * smem1;
+    if (cudaFuncSetAttribute((const void*)k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) !=
+            cudaSuccess)
+        return PE_ECUDA;
+    int grid = grid_for((const void*)k_sort_scatter, block, smem2, n, &chunk);
+    k_sort_count<<<grid, block, smem1, s>>>(cell, n, chunk, ncell, counts, status);
+    k_sort_scan<<<1, 1024, 0, s>>>(counts, cursor, ncell);
+    k_sort_scatter<<<grid, block, smem2, s>>>(cell, theta, v, w, n, chunk, ncell, cursor, out_cell, out_theta, out_v,
+                                              out_w);
+    return launch_status(3);
+}

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/pepic.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pepic.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"PE_API\s+[\w\s\*]+?\b(pe_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1610_01071_gb300 import _build
+
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_symbols()
+    for required in ("pe_create", "pe_burst", "pe_restrict", "pe_project", "pe_lift", "pe_step",
+                     "pe_deposit", "pe_field", "pe_push", "pe_sample", "pe_coarsen", "pe_ls_project",
+                     "pe_refine", "pe_quiet_start", "pe_sort"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_the_header(lib):
+    from paper_1610_01071_gb300 import _binding
+
+    assert sorted(_binding.SIGNATURES) == declared_symbols()
+
+
+def test_library_exports_nothing_else(lib):
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_1610_01071_gb300", "libpepic.so")],
+                         capture_output=True, text=True).stdout
+    exported = sorted({l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("pe_")})
+    assert exported == declared_symbols()
+
+
+def test_layout_is_host_only_and_validates(lib):
+    from paper_1610_01071_gb300 import _binding as b
+
+    cfg = b.make_config(4096, 256, 20, 1 << 24, 2048.0, 0.1, 20.0)
+    lay = b.layout(cfg)
+    assert lay.total_bytes >= 2 * 16 * (1 << 24)
+    offs = list(lay.offset)
+    assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+    bad = b.make_config(4000, 256, 20, 1 << 24, 2048.0, 0.1, 20.0)
+    with pytest.raises(b.PepicError):
+        b.layout(bad)
+    assert lib.pe_strerror is not None
