@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "pe_internal.h"
@@ -42,6 +43,50 @@ int max_smem_optin()
         cache[dev] = v > 0 ? v : 48 * 1024;
     }
     return cache[dev];
+}
+
+namespace {
+struct KernelInfo {
+    const void* kernel;
+    int device, block;
+    size_t smem;
+    int value;
+};
+std::mutex g_kmu;
+std::vector<KernelInfo> g_smem_set, g_occ;
+}  // namespace
+
+int ensure_smem(const void* kernel, size_t smem)
+{
+    if (smem <= 48 * 1024) return PE_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
+    std::lock_guard<std::mutex> lk(g_kmu);
+    for (auto& k : g_smem_set)
+        if (k.kernel == kernel && k.device == dev && k.smem >= smem) return PE_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return PE_ECUDA;
+    for (auto& k : g_smem_set)
+        if (k.kernel == kernel && k.device == dev) {
+            k.smem = smem;
+            return PE_OK;
+        }
+    g_smem_set.push_back({kernel, dev, 0, smem, 0});
+    return PE_OK;
+}
+
+int blocks_per_sm(const void* kernel, int block, size_t smem)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(g_kmu);
+    for (auto& k : g_occ)
+        if (k.kernel == kernel && k.device == dev && k.block == block && k.smem == smem) return k.value;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    g_occ.push_back({kernel, dev, block, smem, per_sm});
+    return per_sm;
 }
 
 static std::atomic<long long> g_launches{0};

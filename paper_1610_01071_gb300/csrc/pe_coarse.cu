@@ -177,9 +177,7 @@ extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int
     if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
     const size_t smem = 2 * sizeof(double) * (size_t)ncell;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    if (cudaFuncSetAttribute((const void*)k_coarsen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return PE_ECUDA;
+    if (ensure_smem((const void*)k_coarsen, smem) != PE_OK) return PE_ECUDA;
     const double lev = pow(2.0, -0.5 * ilog2(ncell));
     k_coarsen<<<2 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), ncell,
                                                                  ldexp(1.0, -(s_w + 24)) * lev,
@@ -204,9 +202,7 @@ extern "C" PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t 
     if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
     const size_t smem = 3 * sizeof(double) * (size_t)ncell;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    if (cudaFuncSetAttribute((const void*)k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return PE_ECUDA;
+    if (ensure_smem((const void*)k_refine, smem) != PE_OK) return PE_ECUDA;
     k_refine<<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
                                                       pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u);
     return launch_status();

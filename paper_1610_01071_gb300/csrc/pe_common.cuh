@@ -30,34 +30,68 @@ __device__ __forceinline__ FxSplit fx_split(int32_t q, float theta)
     return {(unsigned long long)l, (unsigned long long)r};
 }
 
-// Block-local copy of a nodal int64 grid in shared memory. Either the full periodic
+// Block-local copy of a nodal int64 grid in shared memory: either the full periodic
 // grid (width == ncell, base == 0) or a window [base, base + width) of it; nodes
-// outside the window go straight to the global grid.
+// outside the window go straight to the global grid with a 64-bit atomic.
+//
+// Each node's int64 sum is kept as three digit counters, value = d0 + d1 2^16 + d2 2^32,
+// with every contribution v split as v mod 2^16, (v >> 16) mod 2^16 and v >> 32
+// (arithmetic). The counters are updated with native 32-bit shared-memory reductions
+// and cannot overflow while a block makes at most 65536 additions to a node whose
+// absolute values sum to less than 2^62 (the launch keeps block chunks at or below
+// 65536 particles, each adding to a node at most once, directly or through a lane
+// window). The flush recombines them exactly: the same integer as a plain int64 sum.
+constexpr int kMaxChunk = 65536;
+
 struct SmemGrid {
-    unsigned long long* s;
+    uint32_t* d0;
+    uint32_t* d1;
+    int32_t* d2;
     unsigned long long* g;
     int base, width, mask;
 
+    // Carves three arrays of `width` counters from s; returns the next free word.
+    __device__ __forceinline__ uint32_t* bind(uint32_t* s, unsigned long long* global, int b, int w, int m)
+    {
+        d0 = s;
+        d1 = s + w;
+        d2 = reinterpret_cast<int32_t*>(s + 2 * w);
+        g = global;
+        base = b;
+        width = w;
+        mask = m;
+        return s + 3 * w;
+    }
+
     __device__ __forceinline__ void add(int node, unsigned long long val) const
     {
-        int idx = (node - base) & mask;
-        if (idx < width)
-            atomicAdd(&s[idx], val);
-        else
+        const int idx = (node - base) & mask;
+        if (idx < width) {
+            const uint32_t a = (uint32_t)val & 0xFFFFu, b = (uint32_t)(val >> 16) & 0xFFFFu;
+            const int32_t c = (int32_t)((long long)val >> 32);
+            if (a) atomicAdd(&d0[idx], a);
+            if (b) atomicAdd(&d1[idx], b);
+            if (c) atomicAdd(&d2[idx], c);
+        } else {
             atomicAdd(&g[node], val);
+        }
     }
 
     __device__ __forceinline__ void zero() const
     {
-        for (int i = threadIdx.x; i < width; i += blockDim.x) s[i] = 0ull;
+        for (int i = threadIdx.x; i < width; i += blockDim.x) {
+            d0[i] = 0u;
+            d1[i] = 0u;
+            d2[i] = 0;
+        }
     }
 
-    // Adds the non-zero entries to the global grid; call after __syncthreads().
+    // Adds the non-zero node sums to the global grid; call after __syncthreads().
     __device__ __forceinline__ void flush() const
     {
         for (int i = threadIdx.x; i < width; i += blockDim.x) {
-            unsigned long long val = s[i];
-            if (val) atomicAdd(&g[(base + i) & mask], val);
+            const long long v = (long long)d0[i] + ((long long)d1[i] << 16) + ((long long)d2[i] << 32);
+            if (v) atomicAdd(&g[(base + i) & mask], (unsigned long long)v);
         }
     }
 };
@@ -100,13 +134,26 @@ struct LaneWindow {
 };
 
 // Contiguous particle range [begin, end) of block b when n particles are split into
-// nblocks chunks whose starts are multiples of 4 (so float4 loads stay aligned).
+// chunks whose starts are multiples of 4 (so float4 loads stay aligned).
 __device__ __forceinline__ void block_chunk(int64_t n, int64_t chunk, int64_t* begin, int64_t* end)
 {
     int64_t b = (int64_t)blockIdx.x * chunk;
     *begin = b < n ? b : n;
     int64_t e = b + chunk;
     *end = e < n ? e : n;
+}
+
+// Contiguous range of 4-particle groups [*g0, *g1) of this warp inside the block's
+// groups [gb0, gb1): warps take consecutive slices (multiples of 32 groups), so the
+// particles a lane visits stay sorted and close in cell index.
+__device__ __forceinline__ void warp_groups(int64_t gb0, int64_t gb1, int64_t* g0, int64_t* g1)
+{
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    int64_t per = (gb1 - gb0 + nw - 1) / nw;
+    per = (per + 31) & ~int64_t(31);
+    int64_t a = gb0 + per * w, b = a + per;
+    *g0 = a < gb1 ? a : gb1;
+    *g1 = b < gb1 ? b : gb1;
 }
 
 __device__ __forceinline__ double warp_max(double v)

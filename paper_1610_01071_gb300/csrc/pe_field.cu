@@ -195,9 +195,7 @@ extern "C" PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, 
     const int T = ncell / 2 < kNewtonThreads ? ncell / 2 : kNewtonThreads;
     const size_t smem = sizeof(double) * (3 * (size_t)ncell + 8 * (size_t)T);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    if (cudaFuncSetAttribute((const void*)k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return PE_ECUDA;
+    if (ensure_smem((const void*)k_newton, smem) != PE_OK) return PE_ECUDA;
     const double nscale = ldexp(1.0, -(s_w + 24));
     k_newton<<<1, T, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode,
                                                    tol, maxit, phi, E, Ef, diag, status);

@@ -22,6 +22,12 @@ int sm_count();
 // Maximum dynamic shared memory per block (opt-in) of the current device.
 int max_smem_optin();
 
+// Raises the kernel's dynamic shared-memory limit to at least smem bytes on the
+// current device (cached, so repeated launches pay nothing).
+int ensure_smem(const void* kernel, size_t smem);
+// Resident blocks per SM for (kernel, block, smem) on the current device (cached).
+int blocks_per_sm(const void* kernel, int block, size_t smem);
+
 // Counts kernel launches (exported through pe_launch_count).
 void note_launches(int n);
 
@@ -33,8 +39,9 @@ inline int launch_status(int kernels = 1)
     return PE_OK;
 }
 
-// Shared-memory grid widths used by the particle kernels (nodes of int64).
-constexpr int kFullGridMax = 8192;  // ncell up to this uses a block-private copy of the whole grid
-constexpr int kWindowNodes = 4096;  // otherwise a window of this many nodes
+// Shared-memory grid widths used by the particle kernels (nodes).
+constexpr int kFullGridMax = 8192;     // largest grid the context API accepts
+constexpr int kRhoWindowNodes = 1024;  // charge deposit: window around the block's cells
+constexpr int kWindowNodes = 4096;     // restriction samples: window (co-moving spread)
 
 }  // namespace pe

@@ -106,9 +106,9 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512) k_particles(PushParams P)
+__global__ void __launch_bounds__(256) k_particles(PushParams P)
 {
-    extern __shared__ unsigned long long smem[];
+    extern __shared__ uint32_t smem[];
     constexpr bool kRho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
     constexpr bool kSamp = (MODE == kPushSample || MODE == kSample);
     constexpr bool kWrite = (MODE == kPush || MODE == kPushSample);
@@ -117,14 +117,13 @@ __global__ void __launch_bounds__(512) k_particles(PushParams P)
     block_chunk(P.n, P.chunk, &begin, &end);
     const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
 
-    SmemGrid grho{smem, P.rho, 0, kRho ? P.rho_width : 0, P.mask};
-    if (kRho && P.rho_width < P.ncell) grho.base = (c_first - 64) & P.mask;
-    unsigned long long* s1 = smem + (kRho ? P.rho_width : 0);
-    SmemGrid gsn{s1, P.samp_n, 0, kSamp ? P.samp_width : 0, P.mask};
-    SmemGrid gsm{s1 + (kSamp ? P.samp_width : 0), P.samp_m, 0, kSamp ? P.samp_width : 0, P.mask};
-    if (kSamp && P.samp_width < P.ncell) {
-        gsn.base = (c_first - P.samp_width / 2) & P.mask;
-        gsm.base = gsn.base;
+    SmemGrid grho{}, gsn{}, gsm{};
+    uint32_t* s = smem;
+    if (kRho) s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+    if (kSamp) {
+        const int sb = P.samp_width < P.ncell ? ((c_first - P.samp_width / 2) & P.mask) : 0;
+        s = gsn.bind(s, P.samp_n, sb, P.samp_width, P.mask);
+        s = gsm.bind(s, P.samp_m, sb, P.samp_width, P.mask);
     }
     if (kRho) grho.zero();
     if (kSamp) {
@@ -133,17 +132,19 @@ __global__ void __launch_bounds__(512) k_particles(PushParams P)
     }
     __syncthreads();
 
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;  // begin is a multiple of 4
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    const int lane = threadIdx.x & 31;
     LaneWindow lw;
-    lw.reset((c_first - 1) & P.mask);
+    lw.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);
 
-    const int64_t g0 = begin >> 2, g1 = end >> 2;  // begin is a multiple of 4
-    const int B = blockDim.x;
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
     float4* v4 = reinterpret_cast<float4*>(P.v);
     const float4* w4 = reinterpret_cast<const float4*>(P.w);
-    for (int64_t g = g0 + threadIdx.x; g < g1; g += 2 * B) {
-        const bool two = g + B < g1;
+    for (int64_t g = g0 + lane; g < g1; g += 64) {
+        const bool two = g + 32 < g1;
         int4 ca = cell4[g];
         float4 ta = th4[g];
         float4 va = (MODE == kDeposit) ? make_float4(0.f, 0.f, 0.f, 0.f) : v4[g];
@@ -151,10 +152,10 @@ __global__ void __launch_bounds__(512) k_particles(PushParams P)
         int4 cb = make_int4(0, 0, 0, 0);
         float4 tb = make_float4(0.f, 0.f, 0.f, 0.f), vb = tb, wb = tb;
         if (two) {
-            cb = cell4[g + B];
-            tb = th4[g + B];
-            if (MODE != kDeposit) vb = v4[g + B];
-            wb = __ldg(w4 + g + B);
+            cb = cell4[g + 32];
+            tb = th4[g + 32];
+            if (MODE != kDeposit) vb = v4[g + 32];
+            wb = __ldg(w4 + g + 32);
         }
         int4 co;
         float4 to, vo;
@@ -173,13 +174,13 @@ __global__ void __launch_bounds__(512) k_particles(PushParams P)
             process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, grho, gsn, gsm, co.z, to.z, vo.z);
             process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, grho, gsn, gsm, co.w, to.w, vo.w);
             if (kWrite) {
-                cell4[g + B] = co;
-                th4[g + B] = to;
-                v4[g + B] = vo;
+                cell4[g + 32] = co;
+                th4[g + 32] = to;
+                v4[g + 32] = vo;
             }
         }
     }
-    for (int64_t i = (g1 << 2) + threadIdx.x; i < end; i += B) {  // ragged tail (< 4 particles)
+    for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {  // ragged tail (< 4 particles)
         int co;
         float to, vo;
         float vi = (MODE == kDeposit) ? 0.f : P.v[i];
@@ -240,26 +241,30 @@ __device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c
     vv = fmaf(P.v_th, upper ? -z : z, uX);
 }
 
-__global__ void __launch_bounds__(512) k_quiet_start(LoadParams P)
+__global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
 {
-    extern __shared__ unsigned long long smem[];
+    extern __shared__ uint32_t smem[];
     int64_t begin, end;
     block_chunk(P.n, P.chunk, &begin, &end);
     const bool dep = P.rho != nullptr;
     const int c_first = (begin < end) ? (int)((uint64_t)begin / P.ppc) : 0;
-    SmemGrid grho{smem, P.rho, 0, dep ? P.rho_width : 0, P.mask};
-    if (dep && P.rho_width < P.ncell) grho.base = (c_first - 64) & P.mask;
-    if (dep) grho.zero();
+    SmemGrid grho{};
+    if (dep) {
+        grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        grho.zero();
+    }
     __syncthreads();
-    LaneWindow lw;
-    lw.reset((c_first - 1) & P.mask);
 
-    const int64_t g0 = begin >> 2, g1 = end >> 2;
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    LaneWindow lw;
+    lw.reset(((int)((uint64_t)(g0 << 2) / P.ppc) - 1) & P.mask);
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
     float4* v4 = reinterpret_cast<float4*>(P.v);
     float4* w4 = reinterpret_cast<float4*>(P.w);
-    for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
         int4 c;
         float4 t, vv, ww;
         const uint32_t i0 = (uint32_t)(g << 2);
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(512) k_quiet_start(LoadParams P)
             lw.add(c.w, fx_split(fx_weight(ww.w, P.wscale, P.status), t.w), grho);
         }
     }
-    for (int64_t i = (g1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
+    for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         int c;
         float t, vv, ww;
         load_one(P, (uint32_t)i, c, t, vv, ww);
@@ -392,13 +397,11 @@ __global__ void __launch_bounds__(512) k_sort_scatter(const int32_t* cell, const
 
 static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk)
 {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t blocks = (int64_t)sm_count() * per_sm;
+    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(kernel, block, smem);
     int64_t c = (n + blocks - 1) / blocks;
     c = (c + 3) & ~int64_t(3);
     if (c < 4) c = 4;
+    if (c > kMaxChunk) c = kMaxChunk;  // keeps the shared-memory digit counters exact
     *chunk = c;
     int64_t g = (n + c - 1) / c;
     return (int)(g < 1 ? 1 : g);
@@ -407,16 +410,15 @@ static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64
 template <int MODE>
 static int launch_particles(PushParams& P, cudaStream_t s)
 {
-    const int block = 512;
+    const int block = 256;
     const bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
     const bool samp = (MODE == kPushSample || MODE == kSample);
-    P.rho_width = rho ? (P.ncell <= kFullGridMax ? P.ncell : kWindowNodes) : 0;
-    P.samp_width = samp ? (P.ncell <= kFullGridMax ? P.ncell : kWindowNodes) : 0;
-    size_t smem = sizeof(unsigned long long) * (size_t)(P.rho_width + 2 * P.samp_width);
+    P.rho_width = rho ? (P.ncell <= kRhoWindowNodes ? P.ncell : kRhoWindowNodes) : 0;
+    P.samp_width = samp ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
+    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = (const void*)k_particles<MODE>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return PE_ECUDA;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = grid_for(k, block, smem, P.n, &P.chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
     if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)P.ncell, s) != cudaSuccess)
@@ -550,13 +552,12 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     z ^= z >> 31;
     P.shift = (uint32_t)(z >> 32);
     P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
-    P.rho_width = rho_fx ? (ncell <= kFullGridMax ? ncell : kWindowNodes) : 0;
+    P.rho_width = rho_fx ? (ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes) : 0;
     P.status = status;
-    const int block = 512;
-    size_t smem = sizeof(unsigned long long) * (size_t)P.rho_width;
+    const int block = 256;
+    size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
     const void* k = (const void*)k_quiet_start;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return PE_ECUDA;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = grid_for(k, block, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start<<<grid, block, smem, s>>>(P);
@@ -579,10 +580,8 @@ extern "C" PE_API int pe_sort(const int32_t* cell, const float* theta, const flo
     const int block = 512;
     int64_t chunk = 0;
     size_t smem1 = sizeof(unsigned) * (size_t)ncell, smem2 = 2 * smem1;
-    if (cudaFuncSetAttribute((const void*)k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute((const void*)k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) !=
-            cudaSuccess)
+    if (ensure_smem((const void*)k_sort_count, smem1) != PE_OK ||
+        ensure_smem((const void*)k_sort_scatter, smem2) != PE_OK)
         return PE_ECUDA;
     int grid = grid_for((const void*)k_sort_scatter, block, smem2, n, &chunk);
     k_sort_count<<<grid, block, smem1, s>>>(cell, n, chunk, ncell, counts, status);
