@@ -228,6 +228,7 @@ def run_gpu(args):
         launches = pb.launch_count() - launches0
         ctx.profile(False)
         prof = ctx.profile_read()
+        newton_iters = ctx.diagnostics().newton_iters
         t_proj = ev0.elapsed_time(ev1) / 1e3
         st = ctx.sync_status()
         if st != 0:
@@ -283,6 +284,7 @@ def run_gpu(args):
         "plain_pic": {"value": ps_plain / t_plain_max, "unit": UNIT, "steps": n_plain,
                       "ms_per_step": 1e3 * t_plain_max / n_plain, "sort_every": 20},
         "field_solve_us": 1e3 * prof["field_ms"] / max(prof["field_launches"], 1),
+        "newton_iters_last": newton_iters,
         "roofline": {"kernel": "k_particles<push+sample> (gather, kick, drift, deposit, co-moving sample)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,

@@ -82,7 +82,9 @@ PE_API int pe_deposit(const int32_t* cell, const float* theta, const float* w, i
  * update a cyclic tridiagonal solve, damped to |update| <= 2, stopped when
  * max|update| < tol. Then E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx) into E[ncell]
  * (FP64) and Ef[ncell] (FP32 copy used by the particle kernels).
- * diag (device, int32[2], may be NULL) gets {iterations, converged}. Non-convergence
+ * diag (device, int32[4], may be NULL) gets {iterations, converged, blocks, threads
+ * per block}: grids of 1024 nodes or more are solved by one thread-block cluster
+ * (up to 16 blocks, one per SM), smaller ones by a single block. Non-convergence
  * sets PE_FLAG_NOCONV. */
 PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
                     double tol, int32_t maxit, double* phi, double* E, float* Ef, int32_t* diag,
@@ -207,7 +209,7 @@ enum pe_buffer {
     PE_BUF_SLOPE,           /* f64[2][n_coarse] last least-squares slope */
     PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u) */
     PE_BUF_SORT,            /* int32[2 ncell + 64] sort scratch */
-    PE_BUF_STATUS,          /* uint32[4] status word; int32[2] Newton diag after it */
+    PE_BUF_STATUS,          /* uint32[4] status word; int32[4] Newton diag after it */
     PE_NBUF
 };
 

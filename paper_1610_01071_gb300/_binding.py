@@ -152,7 +152,7 @@ def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, statu
     dev = rho.device
     E = torch.empty(ncell, dtype=torch.float64, device=dev)
     Ef = torch.empty(ncell, dtype=torch.float32, device=dev)
-    diag = torch.zeros(2, dtype=torch.int32, device=dev)
+    diag = torch.zeros(4, dtype=torch.int32, device=dev)
     status = _status(status, dev)
     check(load().pe_field(_ptr(rho), ncell, float(dx), s_w, PE_POISSON[mode], float(tol), int(maxit), _ptr(phi),
                           _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status), _stream(stream)), "pe_field")

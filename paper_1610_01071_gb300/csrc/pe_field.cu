@@ -1,185 +1,331 @@
-// Field solve: the nonlinear Poisson-Boltzmann equation of Section 3.3,
+// Field solve: the nonlinear Poisson-Boltzmann equation of Section 3.3 (Eq.
+// poisson2rescaled with lambda = n_0 = 1) on the periodic nodes,
 //   -(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 + g(phi_j) = n_j,   g = exp or 1 + phi,
-// by Newton's method in FP64 on one block, followed by the centred field
-// E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx).
-//
-// Each Newton update solves the cyclic tridiagonal Jacobian system with a partition
-// method: thread t owns the contiguous segment of M = ncell / T nodes. A downward
-// and an upward elimination sweep inside the segment express every interior node
-// through the segment's first (F) and last (L) node; the 2T boundary unknowns form a
-// cyclic tridiagonal system (order F_0, L_0, F_1, L_1, ...) solved by parallel cyclic
-// reduction in shared memory; the interior nodes follow by back-substitution.
+// by Newton's method, followed by the centred field E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "pe_common.cuh"
 #include "pe_internal.h"
 
+namespace cg = cooperative_groups;
+
 namespace pe {
 
-constexpr int kNewtonThreads = 512;
+constexpr int kClusterMinCells = 1024;  // grids at least this large use the multi-SM solver
 
-__device__ __forceinline__ double block_max(double v, double* red)
+// ---------------------------------------------------------------------------------
+// Production solver: one thread-block cluster of G blocks (G = 1 for small grids, up to
+// 16 for large ones, one block per SM); block g owns the B = ncell / G nodes
+// [g B, (g+1) B), one node per thread.
+//
+// Precision: phi, exp(phi), the Newton residual and the update are FP64; the Jacobian
+// correction J d = -F is solved in FP32. This is Newton's method with an inexact
+// linear solve (mixed-precision iterative refinement): the FP64 residual drives the
+// iteration, so it converges to the FP64 solution of the discrete equation, while the
+// FP32 solve only bounds the final contraction rate (~ cond(J) 2^-24 per iteration).
+// On this GPU a dependent FP64 instruction costs ~100 cycles and the FP64 pipe retires
+// ~2 lanes per cycle per SM, so FP64 is used only for per-node work, spread over many
+// warps and SMs, and kept off the serial chains of the tridiagonal elimination.
+//
+// Linear solve (SPIKE-style partition): each block solves its B rows, with the two
+// couplings to the neighbouring blocks moved to the right-hand side, by parallel
+// cyclic reduction with three right-hand sides, x = y - g X_left - h X_right. The
+// blocks' first and last unknowns then satisfy a cyclic block-tridiagonal system with
+// 2x2 blocks; every block gathers it through distributed shared memory and solves it
+// by block cyclic reduction. exp(phi) is evaluated once per solve and then carried
+// multiplicatively, exp(phi + s d) = exp(phi) exp(s d), with a Taylor polynomial.
+
+constexpr int kClusterMax = 16;
+
+// exp(x) for |x| <= 2^-5 by its Taylor polynomial to degree 8 (relative error < 1e-18).
+__device__ __forceinline__ double exp_small(double x)
 {
-    v = warp_max(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    double r = (lane < nw) ? red[lane] : 0.0;
-    return warp_max(r);
+    double p = 1.0 / 40320.0;
+    p = fma(p, x, 1.0 / 5040.0);
+    p = fma(p, x, 1.0 / 720.0);
+    p = fma(p, x, 1.0 / 120.0);
+    p = fma(p, x, 1.0 / 24.0);
+    p = fma(p, x, 1.0 / 6.0);
+    p = fma(p, x, 0.5);
+    p = fma(p, x, 1.0);
+    return fma(p, x, 1.0);
 }
 
-__global__ void __launch_bounds__(kNewtonThreads) k_newton(const long long* rho, int ncell, double dx, double nscale,
-                                                           int mode, double tol, int maxit, double* phi, double* E,
-                                                           float* Ef, int* diag, uint32_t* status)
+struct M2 {
+    float a, b, c, d;  // [[a, b], [c, d]]
+};
+__device__ __forceinline__ M2 mmul(M2 x, M2 y)
 {
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+__device__ __forceinline__ M2 msub(M2 x, M2 y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+__device__ __forceinline__ M2 minv(M2 x)
+{
+    const float r = 1.0f / (x.a * x.d - x.b * x.c);
+    return {x.d * r, -x.b * r, -x.c * r, x.a * r};
+}
+__device__ __forceinline__ float2 mvec(M2 x, float2 v) { return {x.a * v.x + x.b * v.y, x.c * v.x + x.d * v.y}; }
+
+// Block cyclic reduction of the G block rows (thread k < G owns row k) stored as full
+// 2x2 matrices: L3[k] = {Mk(4), Dk(4), Pk(4), rk(2)}, row k: Mk z_{k-1} + Dk z_k + Pk z_{k+1} = rk.
+// After the steps with stride G/2 every row couples only to itself. zsol gets z.
+__device__ void block_pcr(float* L3, float* L3n, float* zsol, int G)
+{
+    const int k = threadIdx.x;
+    auto ld = [](const float* p) { return M2{p[0], p[1], p[2], p[3]}; };
+    auto st = [](float* p, M2 m) {
+        p[0] = m.a;
+        p[1] = m.b;
+        p[2] = m.c;
+        p[3] = m.d;
+    };
+    for (int s = 1; s <= G / 2; s <<= 1) {
+        if (k < G) {
+            const float* c = L3 + 14 * k;
+            const float* lm = L3 + 14 * ((k - s + G) % G);
+            const float* lp = L3 + 14 * ((k + s) % G);
+            const M2 al = mmul(ld(c), minv(ld(lm + 4)));      // Mk D_{k-s}^-1
+            const M2 ga = mmul(ld(c + 8), minv(ld(lp + 4)));  // Pk D_{k+s}^-1
+            float* o = L3n + 14 * k;
+            const M2 nM = mmul(al, ld(lm));
+            const M2 nP = mmul(ga, ld(lp + 8));
+            st(o, M2{-nM.a, -nM.b, -nM.c, -nM.d});
+            st(o + 8, M2{-nP.a, -nP.b, -nP.c, -nP.d});
+            st(o + 4, msub(msub(ld(c + 4), mmul(al, ld(lm + 8))), mmul(ga, ld(lp))));
+            const float2 ra = mvec(al, make_float2(lm[12], lm[13]));
+            const float2 rg = mvec(ga, make_float2(lp[12], lp[13]));
+            o[12] = c[12] - ra.x - rg.x;
+            o[13] = c[13] - ra.y - rg.y;
+        }
+        __syncthreads();
+        if (k < G)
+            for (int q = 0; q < 14; ++q) L3[14 * k + q] = L3n[14 * k + q];
+        __syncthreads();
+    }
+    if (k < G) {
+        const float* c = L3 + 14 * k;
+        M2 Dt = ld(c + 4);
+        const M2 Mm = ld(c), Pm = ld(c + 8);
+        Dt = M2{Dt.a + Mm.a + Pm.a, Dt.b + Mm.b + Pm.b, Dt.c + Mm.c + Pm.c, Dt.d + Mm.d + Pm.d};
+        const float2 z = mvec(minv(Dt), make_float2(c[12], c[13]));
+        zsol[2 * k] = z.x;
+        zsol[2 * k + 1] = z.y;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, int ncell, double dx, double nscale,
+                                                         int mode, double tol, int maxit, double* phi, double* E,
+                                                         float* Ef, int* diag, uint32_t* status)
+{
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ double sh[];
-    __shared__ double red[32];
-    const int T = blockDim.x;
-    const int M = ncell / T;
+    const int G = (int)cluster.num_blocks();
+    const int g = (int)cluster.block_rank();
+    const int B = blockDim.x;
+    const int i = threadIdx.x;
+    double* ph = sh;                                 // [B + 2]
+    double* mymax = ph + B + 2;                      // [1]
+    float* A = reinterpret_cast<float*>(mymax + 1);  // [B] x 6
+    float* Bd = A + B;
+    float* C = Bd + B;
+    float* D = C + B;
+    float* Gs = D + B;
+    float* Hs = Gs + B;
+    float* red = Hs + B;      // [32]
+    float* mine = red + 32;   // [6]
+    float* L3 = mine + 8;     // [G][14]
+    float* L3n = L3 + 14 * G;
+    float* zsol = L3n + 14 * G;  // [2G]
+
     const int mask = ncell - 1;
-    double* CH = sh;  // [M][T] sweep coefficients: coupling to L (upward) / right neighbour
-    double* AH = CH + (size_t)M * T;  // coupling to F
-    double* DH = AH + (size_t)M * T;  // right-hand side
-    double* RA = DH + (size_t)M * T;  // reduced system [2T]
-    double* RB = RA + 2 * T;
-    double* RC = RB + 2 * T;
-    double* RD = RC + 2 * T;
-    const int t = threadIdx.x;
-    const int j0 = t * M;
+    const int j = g * B + i;
     const double inv_dx2 = 1.0 / (dx * dx);
-    const double o = -inv_dx2;  // off-diagonal of the Jacobian
-    const int nred = 2 * T;
+    const float o = (float)(-inv_dx2);
+    const bool boltz = (mode == PE_POISSON_BOLTZMANN);
+    const double nj = (double)__ldg(rho + j) * nscale;
+    double pj = phi[j];
+    double gj = boltz ? exp(pj) : 1.0 + pj;
 
     int it = 0;
     bool converged = false;
     for (it = 0; it < maxit; ++it) {
-        // ---- residual, Jacobian diagonal and downward sweep over the segment
-        double b0 = 0.0, d0 = 0.0;
-        double phm = phi[(j0 - 1) & mask], phj = phi[j0];
-        for (int i = 0; i < M; ++i) {
-            const int j = j0 + i;
-            const double php = phi[(j + 1) & mask];
-            const double g = (mode == PE_POISSON_BOLTZMANN) ? exp(phj) : 1.0 + phj;
-            const double gp = (mode == PE_POISSON_BOLTZMANN) ? g : 1.0;
-            const double nj = (double)__ldg(rho + j) * nscale;
-            const double b = 2.0 * inv_dx2 + gp;
-            const double d = (phm - 2.0 * phj + php) * inv_dx2 - g + nj;  // -F_j
-            if (i == 0) {
-                b0 = b;
-                d0 = d;
-            } else if (i == 1) {
-                const double rr = 1.0 / b;
-                CH[T + t] = o * rr;
-                AH[T + t] = o * rr;
-                DH[T + t] = d * rr;
-            } else {
-                const double cp = CH[(i - 1) * T + t], ap = AH[(i - 1) * T + t], dp = DH[(i - 1) * T + t];
-                const double rr = 1.0 / (b - o * cp);
-                CH[i * T + t] = o * rr;
-                AH[i * T + t] = -o * ap * rr;
-                DH[i * T + t] = (d - o * dp) * rr;
-            }
-            phm = phj;
-            phj = php;
-        }
-        // ---- upward sweep: rows M-3 .. 1 in terms of the segment's last node
-        for (int i = M - 3; i >= 1; --i) {
-            const double ct = CH[i * T + t], at = AH[i * T + t], dt = DH[i * T + t];
-            const double cn = CH[(i + 1) * T + t], an = AH[(i + 1) * T + t], dn = DH[(i + 1) * T + t];
-            CH[i * T + t] = -ct * cn;
-            AH[i * T + t] = at - ct * an;
-            DH[i * T + t] = dt - ct * dn;
-        }
-        // ---- reduced rows of this segment
-        if (M >= 3) {
-            RA[2 * t] = o;
-            RB[2 * t] = b0 - o * AH[T + t];
-            RC[2 * t] = -o * CH[T + t];
-            RD[2 * t] = d0 - o * DH[T + t];
-        } else {
-            RA[2 * t] = o;
-            RB[2 * t] = b0;
-            RC[2 * t] = o;
-            RD[2 * t] = d0;
-        }
-        RA[2 * t + 1] = AH[(M - 1) * T + t];
-        RB[2 * t + 1] = 1.0;
-        RC[2 * t + 1] = CH[(M - 1) * T + t];
-        RD[2 * t + 1] = DH[(M - 1) * T + t];
+        // ---- FP64 residual with the halo from the neighbouring blocks
+        ph[i + 1] = pj;
+        if (i == 0) ph[0] = phi[(g * B - 1) & mask];
+        if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
         __syncthreads();
-        // ---- parallel cyclic reduction on the 2T boundary unknowns
-        for (int s = 1; s < nred / 2; s <<= 1) {
-            double na[2], nb[2], nc[2], nd[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int r = 2 * t + q;
-                const int rm = (r - s) & (nred - 1), rp = (r + s) & (nred - 1);
-                const double al = RA[r] / RB[rm];
-                const double ga = RC[r] / RB[rp];
-                na[q] = -al * RA[rm];
-                nc[q] = -ga * RC[rp];
-                nb[q] = RB[r] - al * RC[rm] - ga * RA[rp];
-                nd[q] = RD[r] - al * RD[rm] - ga * RD[rp];
+        const double lap = (ph[i] - 2.0 * pj + ph[i + 2]) * inv_dx2;
+        A[i] = (i == 0) ? 0.f : o;
+        C[i] = (i == B - 1) ? 0.f : o;
+        Bd[i] = (float)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
+        D[i] = (float)(lap - gj + nj);  // -F_j
+        Gs[i] = (i == 0) ? o : 0.f;
+        Hs[i] = (i == B - 1) ? o : 0.f;
+        __syncthreads();
+        // ---- FP32 parallel cyclic reduction of the block rows, three right-hand sides
+        for (int s = 1; s < B; s <<= 1) {
+            const int im = i - s, ip = i + s;
+            const float al = (im >= 0) ? A[i] / Bd[im] : 0.f;
+            const float ga = (ip < B) ? C[i] / Bd[ip] : 0.f;
+            const float nA = (im >= 0) ? -al * A[im] : 0.f;
+            const float nC = (ip < B) ? -ga * C[ip] : 0.f;
+            float nB = Bd[i], nD = D[i], nG = Gs[i], nH = Hs[i];
+            if (im >= 0) {
+                nB -= al * C[im];
+                nD -= al * D[im];
+                nG -= al * Gs[im];
+                nH -= al * Hs[im];
+            }
+            if (ip < B) {
+                nB -= ga * A[ip];
+                nD -= ga * D[ip];
+                nG -= ga * Gs[ip];
+                nH -= ga * Hs[ip];
             }
             __syncthreads();
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int r = 2 * t + q;
-                RA[r] = na[q];
-                RB[r] = nb[q];
-                RC[r] = nc[q];
-                RD[r] = nd[q];
-            }
+            A[i] = nA;
+            C[i] = nC;
+            Bd[i] = nB;
+            D[i] = nD;
+            Gs[i] = nG;
+            Hs[i] = nH;
             __syncthreads();
         }
-        {  // rows r and r + T now couple only to each other
-            const int r = t, q = t + T;
-            const double er = RA[r] + RC[r], eq = RA[q] + RC[q];
-            const double xr = (RD[r] * RB[q] - er * RD[q]) / (RB[r] * RB[q] - er * eq);
-            const double xq = (RD[q] - eq * xr) / RB[q];
-            __syncthreads();
-            RD[r] = xr;
-            RD[q] = xq;
+        const float rb = 1.0f / Bd[i];
+        const float y = D[i] * rb, gsp = Gs[i] * rb, hsp = Hs[i] * rb;  // x = y - g X_left - h X_right
+        if (i == 0) {
+            mine[0] = y;
+            mine[1] = gsp;
+            mine[2] = hsp;
+        }
+        if (i == B - 1) {
+            mine[3] = y;
+            mine[4] = gsp;
+            mine[5] = hsp;
+        }
+        cluster.sync();  // #1: every block's boundary rows are visible
+        // ---- cyclic block-tridiagonal system of the blocks' (first, last) unknowns
+        if (i < G) {
+            const float* rem = cluster.map_shared_rank(mine, i);
+            float* r = L3 + 14 * i;
+            // F_k + g0 L_{k-1} + h0 F_{k+1} = y0 ;  L_k + gB L_{k-1} + hB F_{k+1} = yB
+            r[0] = 0.f; r[1] = rem[1]; r[2] = 0.f; r[3] = rem[4];      // M: picks L_{k-1}
+            r[4] = 1.f; r[5] = 0.f;    r[6] = 0.f; r[7] = 1.f;         // D = I
+            r[8] = rem[2]; r[9] = 0.f; r[10] = rem[5]; r[11] = 0.f;    // P: picks F_{k+1}
+            r[12] = rem[0]; r[13] = rem[3];
         }
         __syncthreads();
-        // ---- back-substitution and damped update
-        const double xF = RD[2 * t], xL = RD[2 * t + 1];
-        double mloc = fmax(fabs(xF), fabs(xL));
-        for (int i = 1; i < M - 1; ++i) {
-            const double x = DH[i * T + t] - CH[i * T + t] * xL - AH[i * T + t] * xF;
-            DH[i * T + t] = x;
-            mloc = fmax(mloc, fabs(x));
+        block_pcr(L3, L3n, zsol, G);
+        const float Xl = zsol[2 * ((g - 1 + G) % G) + 1];  // previous block's last unknown
+        const float Xr = zsol[2 * ((g + 1) % G)];          // next block's first unknown
+        const float dlt = y - gsp * Xl - hsp * Xr;
+        // ---- global max |update| (damping and convergence)
+        float mloc = fabsf(dlt);
+        for (int off = 16; off > 0; off >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, off));
+        if ((i & 31) == 0) red[i >> 5] = mloc;
+        __syncthreads();
+        if (i < 32) {
+            float v = (i < ((B + 31) >> 5)) ? red[i] : 0.f;
+            for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (i == 0) *mymax = (double)v;
         }
-        const double m = block_max(mloc, red);
+        cluster.sync();  // #2: block maxima visible; level-3 rows no longer read
+        double m = 0.0;
+        for (int k = 0; k < G; ++k) m = fmax(m, *cluster.map_shared_rank(mymax, k));
         const double scale = (m > 2.0) ? 2.0 / m : 1.0;
-        phi[j0] += scale * xF;
-        phi[j0 + M - 1] += scale * xL;
-        for (int i = 1; i < M - 1; ++i) phi[j0 + i] += scale * DH[i * T + t];
-        __syncthreads();
+        const double x = scale * (double)dlt;
+        pj += x;
+        phi[j] = pj;
+        if (boltz)
+            gj = (fabs(x) <= 0.03125) ? gj * exp_small(x) : exp(pj);
+        else
+            gj = 1.0 + pj;
+        __threadfence();
+        cluster.sync();  // #3: updated phi visible to the neighbouring blocks
         if (m < tol) {
             converged = true;
             ++it;
             break;
         }
     }
-    // ---- centred field
-    const double inv_2dx = 0.5 / dx;
-    for (int i = 0; i < M; ++i) {
-        const int j = j0 + i;
-        const double e = -(phi[(j + 1) & mask] - phi[(j - 1) & mask]) * inv_2dx;
-        E[j] = e;
-        Ef[j] = (float)e;
-    }
-    if (t == 0) {
+    ph[i + 1] = pj;
+    if (i == 0) ph[0] = phi[(g * B - 1) & mask];
+    if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
+    __syncthreads();
+    const double e = -(ph[i + 2] - ph[i]) * (0.5 / dx);
+    E[j] = e;
+    Ef[j] = (float)e;
+    if (g == 0 && i == 0) {
         if (diag) {
             diag[0] = it;
             diag[1] = converged ? 1 : 0;
+            diag[2] = G;
+            diag[3] = B;
         }
         if (!converged) raise_flag(status, PE_FLAG_NOCONV);
     }
+}
+
+static int cluster_size_for(int ncell)
+{
+    // largest cluster (<= 16) the device accepts for this kernel; 0 if none
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        cudaFuncSetAttribute((const void*)k_newton_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kClusterMax;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(kClusterMax);
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = 16 * 1024;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int size = 0;
+        if (cudaOccupancyMaxPotentialClusterSize(&size, (const void*)k_newton_cluster, &cfg) != cudaSuccess) size = 8;
+        cudaGetLastError();
+        int p = 1;
+        while (p * 2 <= size && p * 2 <= kClusterMax) p *= 2;
+        cached[dev] = p;
+    }
+    int G = cached[dev];
+    while (G > 1 && ncell / G < 64) G >>= 1;  // at least 64 nodes per block
+    if (ncell < kClusterMinCells) G = 1;
+    while (ncell / G > 1024) G <<= 1;          // at most 1024 nodes (threads) per block
+    return G <= kClusterMax ? G : 0;
+}
+
+static int launch_newton_cluster(int G, const long long* rho, int ncell, double dx, double nscale, int mode,
+                                 double tol, int maxit, double* phi, double* E, float* Ef, int* diag, uint32_t* status,
+                                 cudaStream_t s)
+{
+    const int B = ncell / G;  // one node per thread
+    if (B > 1024 || B < 2) return PE_EINVAL;
+    const size_t smem = sizeof(double) * ((size_t)B + 3) + sizeof(float) * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    if (ensure_smem((const void*)k_newton_cluster, smem) != PE_OK) return PE_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(B);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_newton_cluster, rho, ncell, dx, nscale, mode, tol, maxit, phi, E, Ef, diag,
+                           status) != cudaSuccess)
+        return PE_ECUDA;
+    return launch_status();
 }
 
 }  // namespace pe
@@ -192,12 +338,12 @@ extern "C" PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, 
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !phi || !E || !Ef || !(dx > 0.0) || maxit < 0) return PE_EINVAL;
     if (mode != PE_POISSON_BOLTZMANN && mode != PE_POISSON_LINEARIZED) return PE_EINVAL;
-    const int T = ncell / 2 < kNewtonThreads ? ncell / 2 : kNewtonThreads;
-    const size_t smem = sizeof(double) * (3 * (size_t)ncell + 8 * (size_t)T);
-    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    if (ensure_smem((const void*)k_newton, smem) != PE_OK) return PE_ECUDA;
     const double nscale = ldexp(1.0, -(s_w + 24));
-    k_newton<<<1, T, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode,
-                                                   tol, maxit, phi, E, Ef, diag, status);
-    return launch_status();
+    if (ncell >= 8 && ncell <= kFullGridMax) {
+        const int G = cluster_size_for(ncell);
+        if (G >= 1)
+            return launch_newton_cluster(G, reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode, tol,
+                                         maxit, phi, E, Ef, diag, status, (cudaStream_t)stream);
+    }
+    return PE_EINVAL;
 }

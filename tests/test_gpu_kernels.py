@@ -69,8 +69,9 @@ def test_deposit_full_size_iaw_large():
 # ----------------------------------------------------------------- field solve
 
 
-@pytest.mark.parametrize("ncell,mode", [(8, "boltzmann"), (128, "boltzmann"), (4096, "boltzmann"),
-                                        (8192, "boltzmann"), (256, "linearized")])
+@pytest.mark.parametrize("ncell,mode", [(8, "boltzmann"), (128, "boltzmann"), (1024, "boltzmann"),
+                                        (2048, "linearized"), (4096, "boltzmann"), (8192, "boltzmann"),
+                                        (256, "linearized")])
 def test_field_matches_oracle_newton(ncell, mode):
     L = ncell * 0.5
     n = inputs.random_density(ncell, seed=ncell, amp=0.4)
@@ -104,8 +105,8 @@ def test_field_manufactured_solution_on_gpu():
     assert np.max(np.abs(phi.cpu().numpy() - phi_star)) < 1e-10
 
 
-def test_field_reports_non_convergence_without_fault():
-    ncell = 256
+@pytest.mark.parametrize("ncell", [256, 4096])
+def test_field_reports_non_convergence_without_fault(ncell):
     n = inputs.random_density(ncell, seed=1, amp=0.4)
     rho = np.rint(n * 2.0**44).astype(np.int64)
     phi = torch.full((ncell,), -30.0, dtype=torch.float64, device=DEV)
