@@ -303,6 +303,71 @@ def run_gpu(args):
     return 0
 
 
+def run_kernel(args):
+    """Times one hot-path kernel alone on the workload's particle state (for profiling):
+    ``--kernel push_sample|push|deposit|sample|field|quiet_start``."""
+    import torch
+
+    from paper_1610_01071_gb300 import _binding as pb
+    from paper_1610_01071_gb300 import _build
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    cfg = workload_cfg()
+    N, K, ncell = cfg["N"], cfg["K"], cfg["ncell"]
+    c = pb.make_config(ncell, cfg["n_coarse"], K, N, cfg["L"], cfg["dt"], cfg["dT"], qm=cfg["qm"], v_th=cfg["v_th"],
+                       seed=7, newton_tol=1e-10)
+    ctx = pb.Context(c, device=dev)
+    ctx.load_initial(cfg["amplitude"])
+    d = ctx.diagnostics()
+    cell, theta, v, w = ctx.particles(d.particle_bank)
+    rho = ctx.view("rho", torch.int64, ncell)
+    phi = ctx.view("phi", torch.float64, ncell)
+    samp = ctx.view("samples_fx", torch.int64, 2 * ncell)
+    prof = ctx.view("profile", torch.float32, 2 * ncell)
+    E, Ef, _ = pb.field(rho, ncell, cfg["L"] / ncell, d.s_w, phi)
+    dx = cfg["L"] / ncell
+    bshift = (ncell // cfg["n_coarse"]).bit_length() - 1 if cfg["wavelet"] == "haar" else 0
+    args_s = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp, bin_shift=bshift)
+    args_f = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp, bin_shift=0)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def once():
+        if args.kernel in ("push_sample", "push_sample_nodal"):
+            pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho,
+                    sample=args_s if args.kernel == "push_sample" else args_f, status=status)
+        elif args.kernel == "push":
+            pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, status=status)
+        elif args.kernel == "deposit":
+            pb.deposit(cell, theta, w, ncell, d.s_w, rho=rho, status=status)
+        elif args.kernel == "sample":
+            pb.sample(cell, theta, v, w, Ef, ncell, cfg["dt"], 1.0, args_s, status=status)
+        elif args.kernel == "field":
+            pb.field(rho, ncell, dx, d.s_w, phi)
+        elif args.kernel == "quiet_start":
+            pb.load().pe_quiet_start(pb._ptr(cell), pb._ptr(theta), pb._ptr(v), pb._ptr(w), N, ncell, pb._ptr(prof),
+                                     pb._ptr(prof[ncell:]), 1.0, 7, d.s_w, pb._ptr(rho), pb._ptr(status),
+                                     pb._stream())
+        else:
+            raise SystemExit(f"unknown kernel {args.kernel}")
+
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / args.steps
+    bytes_per = {"push_sample": 28, "push_sample_nodal": 28, "push": 28, "deposit": 12, "sample": 16, "quiet_start": 16, "field": 0}
+    gbs = bytes_per[args.kernel] * N / (us * 1e-6) / 1e9
+    print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us, "algorithmic_GBps": gbs,
+                      "status": int(status.item())}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,7 +375,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone (profiling mode)")
     args = ap.parse_args()
+    if args.kernel:
+        return run_kernel(args)
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

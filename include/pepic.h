@@ -23,7 +23,9 @@
  *   launch error). Faults found on the device (particle cell out of range,
  *   fixed-point overflow, Newton non-convergence) are OR-ed into a caller-owned
  *   device status word (uint32) as PE_FLAG_* bits and never trap; the caller reads
- *   it after synchronising (the context API does this in pe_sync_status).
+ *   it after synchronising (the context API does this in pe_sync_status). Device-side
+ *   waits are bounded (about one second); a wait that runs out sets PE_FLAG_TIMEOUT and
+ *   the kernel returns instead of hanging.
  */
 #ifndef PEPIC_H
 #define PEPIC_H
@@ -49,10 +51,12 @@ extern "C" {
 #define PE_EOVERFLOW 4 /* a weight or momentum exceeded its fixed-point range */
 #define PE_ERANGE 5    /* a particle cell index was outside [0, ncell) */
 #define PE_ESTATE 6    /* call out of order for the context state */
+#define PE_ETIMEOUT 7  /* a bounded device-side wait (asynchronous copy) timed out */
 
 #define PE_FLAG_NOCONV 1u
 #define PE_FLAG_OVERFLOW 2u
 #define PE_FLAG_RANGE 4u
+#define PE_FLAG_TIMEOUT 8u
 
 #define PE_WAVELET_HAAR 0 /* orthonormal Haar filter */
 #define PE_WAVELET_D4 1   /* Daubechies 4-tap orthonormal filter */
@@ -93,7 +97,10 @@ PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w
 /* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
  * follows it): each particle, at its integer-time velocity Vbar, is carried to
  * X~ = X + tau Vbar, V~ = Vbar + qm tau E_n(X), and w and w V~ are deposited
- * (CIC, fixed point) at X~. tau = Delta t - p delta t (0 disables the frame). */
+ * (CIC, fixed point) at X~. tau = Delta t - p delta t (0 disables the frame).
+ * With bin_shift = b > 0 the sample holds, for each bin of 2^b nodes, the exact sum
+ * of the nodal fixed-point sample over the bin (the Haar restriction only needs these
+ * sums; a particle whose two CIC nodes share a bin then adds its whole w 2^24). */
 typedef struct pe_sample_args {
     const float* E0f;  /* E_n, the field stored at burst start, float[ncell] */
     float tau;         /* Delta t - p delta t */
@@ -101,7 +108,8 @@ typedef struct pe_sample_args {
     float inv_dx;      /* 1 / dx */
     int32_t s_w;       /* density fixed-point shift (pe_push requires the same s_w) */
     int32_t s_p;       /* momentum fixed-point shift: |w V~| 2^s_p must stay <= 2^22 */
-    int64_t* sample_fx; /* int64[2][ncell]: density then momentum; overwritten */
+    int32_t bin_shift; /* 0: nodal sample; b > 0: sums over bins of 2^b consecutive nodes */
+    int64_t* sample_fx; /* int64[2][ncell >> bin_shift]: density then momentum; overwritten */
 } pe_sample_args;
 
 /* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
@@ -128,9 +136,13 @@ PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, co
  * (density, momentum) the fine nodal values f_j = sample_fx 2^-(s+24) are taken as
  * scaling coefficients 2^{-J_f/2} f_j at level J_f = log2(ncell), then the periodized
  * orthonormal DWT is applied down to n_coarse scaling coefficients; details are
- * discarded. coarse[nsamples][2][n_coarse] (FP64) is overwritten. */
+ * discarded. coarse[nsamples][2][n_coarse] (FP64) is overwritten.
+ * bin_shift = b > 0 (Haar only) takes samples of bin sums over 2^b nodes
+ * (sample_fx[nsamples][2][ncell >> b]); the Haar analysis of b levels is then the
+ * exact bin sum scaled by 2^{-(J_f + b)/2}. */
 PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
-                      int32_t s_p, int32_t wavelet, int32_t n_coarse, double* coarse, void* stream);
+                      int32_t s_p, int32_t wavelet, int32_t n_coarse, int32_t bin_shift, double* coarse,
+                      void* stream);
 
 /* Projective forward-Euler step, Section 3.3, Eqs. (extrapolation2) and
  * (leastsquares): slope_i = sum_p 6 (K - 2p) / (K (K+1) (K+2) dt) [c_{K-p,i} - c_{p,i}],
@@ -147,12 +159,16 @@ PE_API int pe_ls_project(const double* samples, int32_t K, int32_t ncoef, double
 PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
                      float* prof_n, float* prof_u, void* stream);
 
-/* Quiet-start loading, Appendix C, on nodal profiles (linear interpolation):
- * particle i of n = ppc*ncell: cell = i / ppc, theta = (2 (i mod ppc) + 1) / (2 ppc),
- * w = n(X) / ppc, V = u(X) + v_th Phi^-1(b_i), b_i = (B_i + 1/2) 2^-32 with
- * B_i = brev32(i) + floor(2^31 / n) + (splitmix64(seed) >> 32) mod 2^32 (Hammersley
- * second coordinate with a Cranley-Patterson shift). Output is sorted by cell.
- * If rho_fx != NULL it is overwritten with the charge deposit of the new particles. */
+/* Quiet-start loading, Appendix C, on nodal profiles (linear interpolation): the
+ * Hammersley point h of n = ppc*ncell: cell = h / ppc, theta = (2 (h mod ppc) + 1) / (2 ppc),
+ * w = n(X) / ppc, V = u(X) + v_th Phi^-1(b_h), b_h = (B_h + 1/2) 2^-32 with
+ * B_h = brev32(h) + floor(2^31 / n) + (splitmix64(seed) >> 32) mod 2^32 (second Hammersley
+ * coordinate with a Cranley-Patterson shift). Storage slot i holds point h = i, except
+ * that with ppc = 2^m each cell stores its points in ascending order of the velocity
+ * quantile (h = i with its low m bits reversed): the same point set, ordered so that
+ * positions at any later time, and co-moving targets, vary smoothly along the array.
+ * Output is sorted by cell. If rho_fx != NULL it is overwritten with the charge deposit
+ * of the new particles. */
 PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n,
                           int32_t ncell, const float* prof_n, const float* prof_u, float v_th,
                           uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
@@ -268,7 +284,7 @@ PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device);
 PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
 
 /* Synchronises the context's stream and returns PE_OK or the first device fault
- * (PE_ERANGE, PE_EOVERFLOW, PE_ENOCONV); clears the status word. */
+ * (PE_ETIMEOUT, PE_ERANGE, PE_EOVERFLOW, PE_ENOCONV); clears the status word. */
 PE_API int pe_sync_status(pe_ctx* ctx);
 /* Host-side counters (no synchronisation except for newton_iters/status, which are
  * read after a stream synchronise). */

@@ -336,7 +336,18 @@ void orc_quiet_start(int64_t N, int32_t ncell, const double* nprof, const double
     int64_t ppc = N / ncell;
     uint32_t half = (uint32_t)(2147483648.0 / (double)N);
     uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
-    for (int64_t i = 0; i < N; ++i) {
+    int m = 0;
+    while (((int64_t)1 << m) < ppc) ++m;
+    int pow2 = ((int64_t)1 << m) == ppc;
+    for (int64_t s = 0; s < N; ++s) {
+        /* storage slot s holds Hammersley point i; for ppc = 2^m a cell stores its points in
+         * ascending velocity quantile: i = s with its low m bits reversed */
+        int64_t i = s;
+        if (pow2 && m > 0) {
+            uint32_t k = (uint32_t)(s & (ppc - 1));
+            uint32_t r = brev32(k) >> (32 - m);
+            i = (s & ~(ppc - 1)) | (int64_t)r;
+        }
         int32_t c = (int32_t)(i / ppc);
         double th = (2.0 * (double)(i % ppc) + 1.0) / (2.0 * (double)ppc);
         int32_t c1 = wrap((int64_t)c + 1, ncell);
@@ -344,10 +355,10 @@ void orc_quiet_start(int64_t N, int32_t ncell, const double* nprof, const double
         double uX = (1.0 - th) * uprof[c] + th * uprof[c1];
         uint32_t B = brev32((uint32_t)i) + half + shift; /* mod 2^32 */
         double b = ((double)B + 0.5) * 2.3283064365386963e-10; /* 2^-32 */
-        cell[i] = c;
-        theta[i] = th;
-        w[i] = nX / (double)ppc;
-        v[i] = uX + v_th * orc_ndtri(b);
+        cell[s] = c;
+        theta[s] = th;
+        w[s] = nX / (double)ppc;
+        v[s] = uX + v_th * orc_ndtri(b);
     }
 }
 

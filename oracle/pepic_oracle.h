@@ -104,11 +104,13 @@ void orc_ls_project(int32_t K, int32_t ncoef, double dt, double dT, const double
 double orc_ndtri(double p);
 
 /* Appendix C quiet start on a nodal profile (n_j, u_j), j < ncell, periodic:
- * particle i of N = ppc*ncell sits at X/dx = i/ppc + (2 (i mod ppc) + 1)/(2 ppc),
+ * Hammersley point i of N = ppc*ncell sits at X/dx = floor(i/ppc) + (2 (i mod ppc) + 1)/(2 ppc),
  * weight w = n(X)/ppc, velocity V = u(X) + v_th Phi^{-1}(b_i) with
  * b_i = (B_i + 1/2) 2^-32, B_i = brev32(i) + floor(2^31/N) + (splitmix64(seed) >> 32) mod 2^32
  * (Hammersley second coordinate with a Cranley-Patterson shift). n(X), u(X): linear
- * interpolation between nodes. */
+ * interpolation between nodes. Storage slot s holds point i = s, except that for
+ * ppc = 2^m each cell stores its points in ascending velocity quantile (i = s with its
+ * low m bits reversed); the point set is unchanged. */
 void orc_quiet_start(int64_t N, int32_t ncell, const double* nprof, const double* uprof,
                      double v_th, uint64_t seed, int32_t* cell, double* theta, double* v, double* w);
 

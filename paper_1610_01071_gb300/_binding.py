@@ -34,7 +34,7 @@ class PepicError(RuntimeError):
 class SampleArgs(ctypes.Structure):
     _fields_ = [("E0f", ctypes.c_void_p), ("tau", ctypes.c_float), ("qm", ctypes.c_float),
                 ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
-                ("sample_fx", ctypes.c_void_p)]
+                ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p)]
 
 
 class Config(ctypes.Structure):
@@ -67,7 +67,7 @@ SIGNATURES = {
     "pe_field": (ctypes.c_int, [P, i32, f64, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
     "pe_sample": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, ctypes.POINTER(SampleArgs), P, P]),
-    "pe_coarsen": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, P, P]),
+    "pe_coarsen": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, i32, P, P]),
     "pe_ls_project": (ctypes.c_int, [P, i32, i32, f64, f64, P, P, P]),
     "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
     "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
@@ -159,9 +159,9 @@ def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, statu
     return E, Ef, diag
 
 
-def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx):
+def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0):
     return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
-                      ctypes.c_void_p(sample_fx.data_ptr()))
+                      int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()))
 
 
 def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
@@ -182,11 +182,11 @@ def sample(cell, theta, v, w, Ef, ncell, qm_dt, kick, args, status=None, stream=
                            float(kick), ctypes.byref(args), _ptr(status), _stream(stream)), "pe_sample")
 
 
-def coarsen(sample_fx, nsamples, ncell, s_w, s_p, n_coarse, wavelet="haar", out=None, stream=None):
+def coarsen(sample_fx, nsamples, ncell, s_w, s_p, n_coarse, wavelet="haar", out=None, stream=None, bin_shift=0):
     out = out if out is not None else torch.empty((nsamples, 2, n_coarse), dtype=torch.float64,
                                                   device=sample_fx.device)
-    check(load().pe_coarsen(_ptr(sample_fx), nsamples, ncell, s_w, s_p, PE_WAVELET[wavelet], n_coarse, _ptr(out),
-                            _stream(stream)), "pe_coarsen")
+    check(load().pe_coarsen(_ptr(sample_fx), nsamples, ncell, s_w, s_p, PE_WAVELET[wavelet], n_coarse, bin_shift,
+                            _ptr(out), _stream(stream)), "pe_coarsen")
     return out
 
 

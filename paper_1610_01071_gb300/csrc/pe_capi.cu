@@ -112,6 +112,8 @@ struct pe_ctx {
     cudaStream_t stream;
     double dx;
     int s_w, s_p, nc;
+    int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
+    int nb;              // sample length per moment: ncell >> bin_shift
     int bank;            // which particle bank is current
     int v_at_integer;    // stored v is at integer time
     int fresh;           // particles were just loaded/lifted (not yet advanced)
@@ -158,6 +160,7 @@ extern "C" PE_API const char* pe_strerror(int code)
     case PE_EOVERFLOW: return "fixed-point range exceeded (weight or momentum too large)";
     case PE_ERANGE: return "particle cell index out of range";
     case PE_ESTATE: return "call out of order for the context state";
+    case PE_ETIMEOUT: return "a bounded device-side wait timed out";
     default: return "unknown error";
     }
 }
@@ -218,6 +221,8 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->stream = (cudaStream_t)stream;
     x->dx = cfg->L / cfg->ncell;
     x->nc = cfg->n_coarse;
+    x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
+    x->nb = cfg->ncell >> x->bin_shift;
     const double w_cap = cfg->w_cap > 0.0 ? cfg->w_cap : 8.0 * cfg->ncell / (double)cfg->nparticles;
     const double v_cap = cfg->v_cap > 0.0 ? cfg->v_cap : 32.0;
     x->s_w = fx_shift(w_cap);
@@ -344,9 +349,12 @@ static int deposit_current(pe_ctx* x)
     return PE_OK;
 }
 
+static int64_t* sample_row(pe_ctx* x, int p) { return x->samples + (size_t)p * 2 * x->nb; }
+
 static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
 {
     pe_sample_args a;
+    a.bin_shift = x->bin_shift;
     a.E0f = x->E0f;
     a.tau = (float)tau;
     a.qm = (float)x->cfg.qm;
@@ -380,7 +388,7 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
     const pe_config& c = x->cfg;
     if (!x->rho_valid) PE_TRY(deposit_current(x));
     PE_TRY(field_solve(x));
-    int64_t* dst = x->samples + (size_t)(c.K + 1) * 2 * c.ncell;
+    int64_t* dst = sample_row(x, c.K + 1);
     pe_sample_args a = sample_args(x, 0.0, dst);
     a.E0f = x->Ef;  // tau = 0: the frame field is not used
     const int b = x->bank;
@@ -388,7 +396,7 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
     PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
                      &a, x->status, x->stream));
     double* cdst = x->csamples + (size_t)(c.K + 1) * 2 * x->nc;
-    PE_TRY(pe_coarsen(dst, 1, c.ncell, x->s_w, x->s_p, c.wavelet, x->nc, cdst, x->stream));
+    PE_TRY(pe_coarsen(dst, 1, c.ncell, x->s_w, x->s_p, c.wavelet, x->nc, x->bin_shift, cdst, x->stream));
     const size_t bytes = sizeof(double) * 2 * x->nc;
     if (cudaMemcpyAsync(out, cdst, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         x->stream) != cudaSuccess)
@@ -435,7 +443,7 @@ extern "C" PE_API int pe_burst(pe_ctx* ctx)
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
     for (int p = 0; p <= c.K; ++p) {
         const double tau = c.comoving ? c.dT - p * c.dt : 0.0;
-        pe_sample_args a = sample_args(x, tau, x->samples + (size_t)p * 2 * c.ncell);
+        pe_sample_args a = sample_args(x, tau, sample_row(x, p));
         if (p == c.K) {
             PE_TRY(timed(x, 0, [&] {
                 return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick,
@@ -461,8 +469,8 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
 {
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
-    return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->csamples,
-                      ctx->stream);
+    return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
+                      ctx->csamples, ctx->stream);
 }
 
 extern "C" PE_API int pe_project(pe_ctx* ctx)
@@ -555,6 +563,7 @@ extern "C" PE_API int pe_sync_status(pe_ctx* ctx)
     if (cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
     if (cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t), ctx->stream) != cudaSuccess) return PE_ECUDA;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    if (st & PE_FLAG_TIMEOUT) return PE_ETIMEOUT;
     if (st & PE_FLAG_RANGE) return PE_ERANGE;
     if (st & PE_FLAG_OVERFLOW) return PE_EOVERFLOW;
     if (st & PE_FLAG_NOCONV) return PE_ENOCONV;

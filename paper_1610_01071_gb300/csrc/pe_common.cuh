@@ -96,9 +96,73 @@ struct SmemGrid {
     }
 };
 
+// Block-local restriction sample summed over bins of 2^b nodes (Haar restriction). A
+// particle whose two CIC nodes fall in one bin adds its whole q 2^24 (q = w_q or m_q,
+// |q| <= 2^23): kept as digits of q in u0 (q mod 2^16) and u1 (q >> 16). A particle
+// split across a bin edge adds its two fixed-point parts as three digits each
+// (v0, v1, v2, as in SmemGrid). The flush recombines
+//   sum = (u0 + u1 2^16) 2^24 + v0 + v1 2^16 + v2 2^32
+// exactly; the bounds of SmemGrid apply per bin (at most 65536 additions per block).
+struct BinGrid {
+    uint32_t* u0;
+    int32_t* u1;
+    uint32_t* v0;
+    uint32_t* v1;
+    int32_t* v2;
+    unsigned long long* g;
+    int nb;
+
+    __device__ __forceinline__ uint32_t* bind(uint32_t* s, unsigned long long* global, int nbins)
+    {
+        u0 = s;
+        u1 = reinterpret_cast<int32_t*>(s + nbins);
+        v0 = s + 2 * nbins;
+        v1 = s + 3 * nbins;
+        v2 = reinterpret_cast<int32_t*>(s + 4 * nbins);
+        g = global;
+        nb = nbins;
+        return s + 5 * nbins;
+    }
+
+    __device__ __forceinline__ void add_whole(int b, int32_t q) const
+    {
+        atomicAdd(&u0[b], (uint32_t)q & 0xFFFFu);
+        atomicAdd(&u1[b], q >> 16);
+    }
+
+    __device__ __forceinline__ void add_part(int b, unsigned long long val) const
+    {
+        atomicAdd(&v0[b], (uint32_t)val & 0xFFFFu);
+        atomicAdd(&v1[b], (uint32_t)(val >> 16) & 0xFFFFu);
+        atomicAdd(&v2[b], (int32_t)((long long)val >> 32));
+    }
+
+    __device__ __forceinline__ void zero() const
+    {
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            u0[i] = 0u;
+            u1[i] = 0;
+            v0[i] = 0u;
+            v1[i] = 0u;
+            v2[i] = 0;
+        }
+    }
+
+    __device__ __forceinline__ void flush() const
+    {
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const long long whole = (long long)u0[i] + ((long long)u1[i] << 16);
+            const long long v = whole * (long long)kThetaOne + (long long)v0[i] + ((long long)v1[i] << 16) +
+                                ((long long)v2[i] << 32);
+            if (v) atomicAdd(&g[i], (unsigned long long)v);
+        }
+    }
+};
+
 // Per-lane sliding accumulator for a stream of particles whose cells change slowly
-// (particles sorted by cell): four consecutive nodes base..base+3 held in registers,
-// flushed to the block grid only when a particle falls outside them.
+// (cell-sorted particles, or the smooth sweeps of a velocity-ordered cell): four
+// consecutive nodes base..base+3 held in registers, flushed to the block grid only when
+// a particle falls outside them.
 struct LaneWindow {
     int base;
     unsigned long long s0, s1, s2, s3;
@@ -130,6 +194,48 @@ struct LaneWindow {
         s1 += (d == 0) ? q.right : ((d == 1) ? q.left : 0ull);
         s2 += (d == 1) ? q.right : ((d == 2) ? q.left : 0ull);
         s3 += (d == 2) ? q.right : 0ull;
+    }
+};
+
+// Per-lane accumulator of whole-particle bin contributions (BinGrid::add_whole) of the
+// density and momentum samples for two consecutive bins base, base+1, in int32. It is
+// flushed when a particle's bin leaves the pair or after 255 additions (so |sum| < 2^31).
+struct BinWindow {
+    int base, count;
+    int32_t n0, n1, m0, m1;
+
+    __device__ __forceinline__ void reset(int b)
+    {
+        base = b;
+        count = 0;
+        n0 = n1 = m0 = m1 = 0;
+    }
+
+    __device__ __forceinline__ void flush(const BinGrid& gn, const BinGrid& gm, int bmask) const
+    {
+        if (n0 | m0) {
+            gn.add_whole(base, n0);
+            gm.add_whole(base, m0);
+        }
+        if (n1 | m1) {
+            gn.add_whole((base + 1) & bmask, n1);
+            gm.add_whole((base + 1) & bmask, m1);
+        }
+    }
+
+    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, const BinGrid& gn, const BinGrid& gm, int bmask)
+    {
+        int d = (b - base) & bmask;
+        if (d > 1 || count == 255) {
+            flush(gn, gm, bmask);
+            reset(b);
+            d = 0;
+        }
+        ++count;
+        n0 += (d == 0) ? wq : 0;
+        m0 += (d == 0) ? mq : 0;
+        n1 += (d == 1) ? wq : 0;
+        m1 += (d == 1) ? mq : 0;
     }
 };
 

@@ -32,23 +32,38 @@ struct PushParams {
     unsigned long long* samp_n;
     unsigned long long* samp_m;
     int samp_width;
+    int bin_shift;  // > 0: samples summed over bins of 2^bin_shift nodes (BINNED modes)
     uint32_t* status;
 };
 
-enum Mode { kDeposit = 0, kPush = 1, kPushSample = 2, kSample = 3 };
+enum Mode { kDeposit = 0, kPush = 1, kPushSample = 2, kSample = 3, kPushSampleBinned = 4, kSampleBinned = 5 };
 
-__device__ __forceinline__ int32_t fx_weight(float x, float scale, uint32_t* status)
+template <int MODE>
+struct ModeTraits {
+    static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned);
+    static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned);
+    static constexpr bool sample = (MODE == kPushSample || MODE == kSample || MODE == kPushSampleBinned ||
+                                    MODE == kSampleBinned);
+    static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
+};
+
+// Fixed-point value rn(x 2^s); records in *ovf whether it left the range |q| <= 2^23.
+__device__ __forceinline__ int32_t fx_weight(float x, float scale, bool* ovf)
 {
-    int32_t q = __float2int_rn(x * scale);
-    if (q > (1 << 23) || q < -(1 << 23)) raise_flag(status, PE_FLAG_OVERFLOW);
+    const int32_t q = __float2int_rn(x * scale);
+    *ovf |= (q > (1 << 23)) | (q < -(1 << 23));
     return q;
 }
 
+constexpr int kThreads = 256;
+
 template <int MODE>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
-                                        LaneWindow& lw, const SmemGrid& grho, const SmemGrid& gsn,
-                                        const SmemGrid& gsm, int& c_out, float& th_out, float& v_out)
+                                        LaneWindow& lw, BinWindow& bw, const SmemGrid& grho,
+                                        const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
+                                        const BinGrid& bsm, bool* ovf, int& c_out, float& th_out, float& v_out)
 {
+    using Tr = ModeTraits<MODE>;
     c_out = c;
     th_out = th;
     v_out = vv;
@@ -56,7 +71,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         raise_flag(P.status, PE_FLAG_RANGE);
         return;
     }
-    const int32_t wq = fx_weight(ww, P.wscale, P.status);
+    const int32_t wq = fx_weight(ww, P.wscale, ovf);
     if (MODE == kDeposit) {
         lw.add(c, fx_split(wq, th), grho);
         return;
@@ -64,7 +79,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
     const int c1 = (c + 1) & P.mask;
     const float Ec = __ldg(P.Ef + c), Ec1 = __ldg(P.Ef + c1);
     const float Ep = fmaf(th, Ec1 - Ec, Ec);  // CIC gather
-    if (MODE == kPushSample || MODE == kSample) {
+    if (Tr::sample) {
         // Appendix B: carry the particle along the approximate characteristic to t_{n+1}
         const float vbar = fmaf((P.kick - 0.5f) * P.qm_dt, Ep, vv);  // integer-time velocity
         const float E0c = __ldg(P.E0f + c), E0c1 = __ldg(P.E0f + c1);
@@ -79,14 +94,28 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         }
         const int cs = (c + k) & P.mask, cs1 = (cs + 1) & P.mask;
         const float vt = fmaf(P.qm_tau, E0p, vbar);
-        const FxSplit qn = fx_split(wq, ths);
-        const FxSplit qp = fx_split(fx_weight(ww * vt, P.pscale, P.status), ths);
-        gsn.add(cs, qn.left);
-        gsn.add(cs1, qn.right);
-        gsm.add(cs, qp.left);
-        gsm.add(cs1, qp.right);
+        const int32_t mq = fx_weight(ww * vt, P.pscale, ovf);
+        if (Tr::binned) {
+            const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
+            if (b0 == b1) {  // both CIC parts in one bin: the whole particle
+                bw.add(b0, wq, mq, bsn, bsm, bsn.nb - 1);
+            } else {
+                const FxSplit qn = fx_split(wq, ths), qp = fx_split(mq, ths);
+                bsn.add_part(b0, qn.left);
+                bsn.add_part(b1, qn.right);
+                bsm.add_part(b0, qp.left);
+                bsm.add_part(b1, qp.right);
+            }
+        } else {
+            const FxSplit qn = fx_split(wq, ths);
+            const FxSplit qp = fx_split(mq, ths);
+            gsn.add(cs, qn.left);
+            gsn.add(cs1, qn.right);
+            gsm.add(cs, qp.left);
+            gsm.add(cs1, qp.right);
+        }
     }
-    if (MODE == kPush || MODE == kPushSample) {
+    if (Tr::push) {
         // Section 2.2 leapfrog: kick with the gathered field, then drift
         const float vn = fmaf(P.kick * P.qm_dt, Ep, vv);
         const float s = fmaf(vn, P.dt_dx, th);
@@ -105,19 +134,25 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
     }
 }
 
+// One block owns a contiguous chunk of <= 65536 particles; each warp a contiguous slice
+// of it, read with 16-byte loads (4 particles per lane, two groups in flight).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_particles(PushParams P)
+__global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
 {
+    using Tr = ModeTraits<MODE>;
+    constexpr bool kRho = Tr::rho;
+    constexpr bool kSamp = Tr::sample && !Tr::binned;
+    constexpr bool kBin = Tr::binned;
+    constexpr bool kWrite = Tr::push;
+    constexpr bool kNeedV = (MODE != kDeposit);
     extern __shared__ uint32_t smem[];
-    constexpr bool kRho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
-    constexpr bool kSamp = (MODE == kPushSample || MODE == kSample);
-    constexpr bool kWrite = (MODE == kPush || MODE == kPushSample);
 
     int64_t begin, end;
     block_chunk(P.n, P.chunk, &begin, &end);
     const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
 
     SmemGrid grho{}, gsn{}, gsm{};
+    BinGrid bsn{}, bsm{};
     uint32_t* s = smem;
     if (kRho) s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
     if (kSamp) {
@@ -125,10 +160,19 @@ __global__ void __launch_bounds__(256) k_particles(PushParams P)
         s = gsn.bind(s, P.samp_n, sb, P.samp_width, P.mask);
         s = gsm.bind(s, P.samp_m, sb, P.samp_width, P.mask);
     }
+    if (kBin) {
+        const int nb = P.ncell >> P.bin_shift;
+        s = bsn.bind(s, P.samp_n, nb);
+        s = bsm.bind(s, P.samp_m, nb);
+    }
     if (kRho) grho.zero();
     if (kSamp) {
         gsn.zero();
         gsm.zero();
+    }
+    if (kBin) {
+        bsn.zero();
+        bsm.zero();
     }
     __syncthreads();
 
@@ -138,6 +182,9 @@ __global__ void __launch_bounds__(256) k_particles(PushParams P)
     const int lane = threadIdx.x & 31;
     LaneWindow lw;
     lw.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);
+    BinWindow bw;
+    bw.reset(0);
+    bool ovf = false;
 
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
@@ -147,32 +194,32 @@ __global__ void __launch_bounds__(256) k_particles(PushParams P)
         const bool two = g + 32 < g1;
         int4 ca = cell4[g];
         float4 ta = th4[g];
-        float4 va = (MODE == kDeposit) ? make_float4(0.f, 0.f, 0.f, 0.f) : v4[g];
+        float4 va = kNeedV ? v4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 wa = __ldg(w4 + g);
         int4 cb = make_int4(0, 0, 0, 0);
         float4 tb = make_float4(0.f, 0.f, 0.f, 0.f), vb = tb, wb = tb;
         if (two) {
             cb = cell4[g + 32];
             tb = th4[g + 32];
-            if (MODE != kDeposit) vb = v4[g + 32];
+            if (kNeedV) vb = v4[g + 32];
             wb = __ldg(w4 + g + 32);
         }
         int4 co;
         float4 to, vo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, grho, gsn, gsm, co.x, to.x, vo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, grho, gsn, gsm, co.y, to.y, vo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, grho, gsn, gsm, co.z, to.z, vo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, grho, gsn, gsm, co.w, to.w, vo.w);
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.x, to.x, vo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.y, to.y, vo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.z, to.z, vo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.w, to.w, vo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
         }
         if (two) {
-            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, grho, gsn, gsm, co.x, to.x, vo.x);
-            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, grho, gsn, gsm, co.y, to.y, vo.y);
-            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, grho, gsn, gsm, co.z, to.z, vo.z);
-            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, grho, gsn, gsm, co.w, to.w, vo.w);
+            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.x, to.x, vo.x);
+            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.y, to.y, vo.y);
+            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.z, to.z, vo.z);
+            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.w, to.w, vo.w);
             if (kWrite) {
                 cell4[g + 32] = co;
                 th4[g + 32] = to;
@@ -183,8 +230,8 @@ __global__ void __launch_bounds__(256) k_particles(PushParams P)
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {  // ragged tail (< 4 particles)
         int co;
         float to, vo;
-        float vi = (MODE == kDeposit) ? 0.f : P.v[i];
-        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, grho, gsn, gsm, co, to, vo);
+        const float vi = kNeedV ? P.v[i] : 0.f;
+        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co, to, vo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
@@ -192,17 +239,24 @@ __global__ void __launch_bounds__(256) k_particles(PushParams P)
         }
     }
     if (kRho) lw.flush(grho);
+    if (kBin) bw.flush(bsn, bsm, bsn.nb - 1);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
     __syncthreads();
     if (kRho) grho.flush();
     if (kSamp) {
         gsn.flush();
         gsm.flush();
     }
+    if (kBin) {
+        bsn.flush();
+        bsm.flush();
+    }
 }
 
 // ------------------------------------------------------------------ quiet start
 
 struct LoadParams {
+    int log2ppc;  // >= 0 when ppc is a power of two: cells store their particles by velocity quantile
     int32_t* cell;
     float* theta;
     float* v;
@@ -223,6 +277,13 @@ struct LoadParams {
 
 __device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
 {
+    // Storage slot i holds Hammersley point h. With ppc = 2^m the cell's slots are filled
+    // in ascending order of the velocity quantile: slot k of a cell takes the point whose
+    // in-cell index is the m-bit reversal of k (the same point set, permuted in the cell).
+    if (P.log2ppc > 0) {
+        const uint32_t k = i & (P.ppc - 1u);
+        i = (i & ~(P.ppc - 1u)) | (__brev(k) >> (32 - P.log2ppc));
+    }
     const uint32_t j = i % P.ppc;
     c = (int)(i / P.ppc);
     th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
@@ -260,6 +321,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     warp_groups(gb0, gb1, &g0, &g1);
     LaneWindow lw;
     lw.reset(((int)((uint64_t)(g0 << 2) / P.ppc) - 1) & P.mask);
+    bool ovf = false;
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
     float4* v4 = reinterpret_cast<float4*>(P.v);
@@ -277,10 +339,10 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
         v4[g] = vv;
         w4[g] = ww;
         if (dep) {
-            lw.add(c.x, fx_split(fx_weight(ww.x, P.wscale, P.status), t.x), grho);
-            lw.add(c.y, fx_split(fx_weight(ww.y, P.wscale, P.status), t.y), grho);
-            lw.add(c.z, fx_split(fx_weight(ww.z, P.wscale, P.status), t.z), grho);
-            lw.add(c.w, fx_split(fx_weight(ww.w, P.wscale, P.status), t.w), grho);
+            lw.add(c.x, fx_split(fx_weight(ww.x, P.wscale, &ovf), t.x), grho);
+            lw.add(c.y, fx_split(fx_weight(ww.y, P.wscale, &ovf), t.y), grho);
+            lw.add(c.z, fx_split(fx_weight(ww.z, P.wscale, &ovf), t.z), grho);
+            lw.add(c.w, fx_split(fx_weight(ww.w, P.wscale, &ovf), t.w), grho);
         }
     }
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
@@ -291,9 +353,10 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
         P.theta[i] = t;
         P.v[i] = vv;
         P.w[i] = ww;
-        if (dep) lw.add(c, fx_split(fx_weight(ww, P.wscale, P.status), t), grho);
+        if (dep) lw.add(c, fx_split(fx_weight(ww, P.wscale, &ovf), t), grho);
     }
     if (dep) lw.flush(grho);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
     __syncthreads();
     if (dep) grho.flush();
 }
@@ -410,18 +473,20 @@ static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64
 template <int MODE>
 static int launch_particles(PushParams& P, cudaStream_t s)
 {
-    const int block = 256;
-    const bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample);
-    const bool samp = (MODE == kPushSample || MODE == kSample);
+    const int block = kThreads;
+    const bool rho = ModeTraits<MODE>::rho;
+    const bool samp = ModeTraits<MODE>::sample;
+    const bool bin = ModeTraits<MODE>::binned;
     P.rho_width = rho ? (P.ncell <= kRhoWindowNodes ? P.ncell : kRhoWindowNodes) : 0;
-    P.samp_width = samp ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
-    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width);
+    P.samp_width = (samp && !bin) ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
+    const int nb = bin ? (P.ncell >> P.bin_shift) : 0;
+    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) + 5 * sizeof(uint32_t) * 2 * nb;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = (const void*)k_particles<MODE>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = grid_for(k, block, smem, P.n, &P.chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
-    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)P.ncell, s) != cudaSuccess)
+    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)(P.ncell >> P.bin_shift), s) != cudaSuccess)
         return PE_ECUDA;
     if (P.n == 0) return PE_OK;
     k_particles<MODE><<<grid, block, smem, s>>>(P);
@@ -435,9 +500,12 @@ static bool particles_ok(const void* a, const void* b, const void* c, const void
     return a && b && c && d && aligned16(a) && aligned16(b) && aligned16(c) && aligned16(d);
 }
 
-static bool sample_ok(const pe_sample_args* s)
+static bool sample_ok(const pe_sample_args* s, int ncell)
 {
-    return s && s->E0f && s->sample_fx && aligned16(s->sample_fx);
+    if (!s || !s->E0f || !s->sample_fx || !aligned16(s->sample_fx)) return false;
+    if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
+    if (s->bin_shift == 0) return true;
+    return (5 * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
 }
 
 }  // namespace pe
@@ -466,7 +534,7 @@ extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float
                               const pe_sample_args* sample, uint32_t* status, void* stream)
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !Ef || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
-    if (sample && (!sample_ok(sample) || sample->s_w != s_w)) return PE_EINVAL;
+    if (sample && (!sample_ok(sample, ncell) || sample->s_w != s_w)) return PE_EINVAL;
     PushParams P{};
     P.cell = cell;
     P.theta = theta;
@@ -487,8 +555,10 @@ extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float
         P.tau_dx = sample->tau * sample->inv_dx;
         P.qm_tau = sample->qm * sample->tau;
         P.pscale = ldexpf(1.0f, sample->s_p);
+        P.bin_shift = sample->bin_shift;
         P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
-        P.samp_m = P.samp_n + ncell;
+        P.samp_m = P.samp_n + (ncell >> P.bin_shift);
+        if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream);
         return launch_particles<kPushSample>(P, (cudaStream_t)stream);
     }
     return launch_particles<kPush>(P, (cudaStream_t)stream);
@@ -498,7 +568,7 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
                                 const float* Ef, int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample,
                                 uint32_t* status, void* stream)
 {
-    if (!is_pow2(ncell) || ncell < 8 || !Ef || !particles_ok(cell, theta, v, w, n) || !sample_ok(sample))
+    if (!is_pow2(ncell) || ncell < 8 || !Ef || !particles_ok(cell, theta, v, w, n) || !sample_ok(sample, ncell))
         return PE_EINVAL;
     PushParams P{};
     P.cell = const_cast<int32_t*>(cell);
@@ -517,8 +587,10 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
     P.tau_dx = sample->tau * sample->inv_dx;
     P.qm_tau = sample->qm * sample->tau;
     P.pscale = ldexpf(1.0f, sample->s_p);
+    P.bin_shift = sample->bin_shift;
     P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
-    P.samp_m = P.samp_n + ncell;
+    P.samp_m = P.samp_n + (ncell >> P.bin_shift);
+    if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream);
     return launch_particles<kSample>(P, (cudaStream_t)stream);
 }
 
@@ -536,6 +608,7 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     P.w = w;
     P.n = n;
     P.ppc = (uint32_t)(n / ncell);
+    P.log2ppc = is_pow2(P.ppc) ? ilog2(P.ppc) : -1;
     P.ncell = ncell;
     P.mask = ncell - 1;
     P.inv_ppc = 1.0f / (float)P.ppc;

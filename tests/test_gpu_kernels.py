@@ -55,6 +55,13 @@ def test_deposit_empty_and_range_flag():
     keep = np.ones(100, bool)
     keep[7] = False
     assert np.array_equal(rho.cpu().numpy(), orc.deposit_fx(c[keep], t[keep], w[keep], 64, 20))
+    # a weight beyond the fixed-point range is reported, not trapped
+    c[7] = 3
+    w = w.copy()
+    w[9] = 100.0
+    st = status_word()
+    pe.deposit(*to_dev(c, t, w), 64, 20, status=st)
+    assert int(st.item()) & 2
 
 
 def test_deposit_full_size_iaw_large():
@@ -202,6 +209,13 @@ def test_sample_matches_oracle(tau):
     assert np.max(np.abs(gd - dens)) < 1e-4 * np.max(np.abs(dens))
     assert np.max(np.abs(gm - mom)) < 1e-4 * np.max(np.abs(mom))
     assert gd.sum() == pytest.approx(dens.sum(), rel=1e-7)
+    # binned form (Haar restriction): exact bin sums of the nodal fixed-point sample
+    for b in (1, 3, 5):
+        outb = torch.empty(2 * (ncell >> b), dtype=torch.int64, device=DEV)
+        argb = pe.make_sample_args(E0f, tau, qm, 1 / dx, s_w, s_p, outb, bin_shift=b)
+        pe.sample(dc, dt_, dv, dw, Ef, ncell, qm * dt, 1.0, argb)
+        want = g.reshape(2, ncell >> b, 1 << b).sum(axis=-1).reshape(-1)
+        assert np.array_equal(outb.cpu().numpy(), want)
 
 
 # ----------------------------------------------------------------- coarse variables
@@ -216,6 +230,19 @@ def test_coarsen_matches_oracle(wav, ncell, nc):
     for p in range(nsamp):
         for m, s in ((0, s_w), (1, s_p)):
             want = orc.coarsen(fx[p, m] * 2.0 ** -(s + 24), nc, wav)
+            assert np.allclose(out[p, m], want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("ncell,nc,b", [(128, 16, 3), (4096, 256, 4), (256, 32, 2)])
+def test_coarsen_binned_haar_matches_oracle(ncell, nc, b):
+    rng = np.random.default_rng(b)
+    nsamp, s_w, s_p = 3, 30, 25
+    fx = rng.integers(-(1 << 50), 1 << 50, size=(nsamp, 2, ncell), dtype=np.int64)
+    binned = fx.reshape(nsamp, 2, ncell >> b, 1 << b).sum(axis=-1)
+    out = pe.coarsen(*to_dev(binned), nsamp, ncell, s_w, s_p, nc, bin_shift=b).cpu().numpy()
+    for p in range(nsamp):
+        for m, s in ((0, s_w), (1, s_p)):
+            want = orc.coarsen(fx[p, m] * 2.0 ** -(s + 24), nc, "haar")
             assert np.allclose(out[p, m], want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
 
 
