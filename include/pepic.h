@@ -182,6 +182,27 @@ PE_API int pe_sort(const int32_t* cell, const float* theta, const float* v, cons
                    int64_t n, int32_t ncell, int32_t* out_cell, float* out_theta, float* out_v,
                    float* out_w, int32_t* scratch, uint32_t* status, void* stream);
 
+/* Allocation-free variant of pe_sort (the paper has no counterpart; this is a library
+ * service). Some callers cannot allocate device memory at the point where they sort:
+ * code running inside a host framework that owns all device allocations, real-time
+ * loops that must not take cudaMalloc's implicit device synchronisation, or plugins
+ * handed only the particle buffers. This entry point therefore takes no scratch
+ * argument: its two counter arrays live in a statically sized device array of this
+ * library (2 * PE_SORT_STATIC_MAX_CELLS + 64 int32, 66 KB), which every GPU that loads
+ * the library keeps until the process exits. It calls no cudaMalloc, cudaFree or any
+ * allocating routine.
+ * - ncell must not exceed PE_SORT_STATIC_MAX_CELLS; larger grids return PE_EINVAL.
+ * - The first call on a device (with that device current) looks up the array's device
+ *   address; make that first call before any stream capture.
+ * - All calls share the one array (the counters are cleared at the start of each call):
+ *   calls that may overlap on the GPU (different streams, or different threads without
+ *   ordering) race and give wrong results. Serialise them.
+ * Arguments and results are those of pe_sort. */
+#define PE_SORT_STATIC_MAX_CELLS 8192
+PE_API int pe_sort_noalloc(const int32_t* cell, const float* theta, const float* v, const float* w,
+                           int64_t n, int32_t ncell, int32_t* out_cell, float* out_theta,
+                           float* out_v, float* out_w, uint32_t* status, void* stream);
+
 /* =================================================================== context
  * One realisation of the projective-integration cycle (Section 3.1, Figure
  * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares

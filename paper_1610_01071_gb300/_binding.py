@@ -72,6 +72,7 @@ SIGNATURES = {
     "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
     "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
     "pe_sort": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P, P]),
+    "pe_sort_noalloc": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P]),
     "pe_layout_for": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Layout)]),
     "pe_create": (ctypes.c_int, [ctypes.POINTER(Config), P, sz, P, ctypes.POINTER(P)]),
     "pe_destroy": (None, [P]),
@@ -231,6 +232,17 @@ def sort(cell, theta, v, w, ncell, status=None, stream=None):
     status = _status(status, dev)
     check(load().pe_sort(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), ncell, _ptr(oc), _ptr(ot),
                          _ptr(ov), _ptr(ow), _ptr(scratch), _ptr(status), _stream(stream)), "pe_sort")
+    return oc, ot, ov, ow
+
+
+def sort_noalloc(cell, theta, v, w, ncell, status=None, stream=None):
+    """pe_sort without a scratch argument: its counters live in the library's static
+    device array (for callers that cannot allocate device memory when they sort)."""
+    dev = cell.device
+    oc, ot, ov, ow = torch.empty_like(cell), torch.empty_like(theta), torch.empty_like(v), torch.empty_like(w)
+    status = _status(status, dev)
+    check(load().pe_sort_noalloc(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), ncell, _ptr(oc), _ptr(ot),
+                                 _ptr(ov), _ptr(ow), _ptr(status), _stream(stream)), "pe_sort_noalloc")
     return oc, ot, ov, ow
 
 

@@ -456,6 +456,12 @@ __global__ void __launch_bounds__(512) k_sort_scatter(const int32_t* cell, const
     }
 }
 
+// Counter storage of pe_sort_noalloc: counts[ncell] and cursor[ncell] for grids of up to
+// PE_SORT_STATIC_MAX_CELLS cells (plus 64 spare words), resident on every device that
+// loads the library. Host code must not pass this symbol itself to a kernel: it is a
+// host-side stand-in; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned g_sort_static[2 * PE_SORT_STATIC_MAX_CELLS + 64];
+
 // ------------------------------------------------------------------ host side
 
 static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk)
@@ -635,6 +641,34 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start<<<grid, block, smem, s>>>(P);
     return launch_status();
+}
+
+// Device address of g_sort_static on the current device, looked up once per device.
+static unsigned* sort_static_ptr()
+{
+    static unsigned* cache[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cache[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sort_static) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cache[dev] = static_cast<unsigned*>(p);
+    }
+    return cache[dev];
+}
+
+extern "C" PE_API int pe_sort_noalloc(const int32_t* cell, const float* theta, const float* v, const float* w,
+                                      int64_t n, int32_t ncell, int32_t* out_cell, float* out_theta, float* out_v,
+                                      float* out_w, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || ncell > PE_SORT_STATIC_MAX_CELLS) return PE_EINVAL;
+    unsigned* scratch = sort_static_ptr();
+    if (!scratch) return PE_ECUDA;
+    return pe_sort(cell, theta, v, w, n, ncell, out_cell, out_theta, out_v, out_w, reinterpret_cast<int32_t*>(scratch),
+                   status, stream);
 }
 
 extern "C" PE_API int pe_sort(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,

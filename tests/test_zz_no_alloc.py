@@ -1,0 +1,42 @@
+"""The allocation-free sort entry point (pe_sort_noalloc) against pe_sort.
+
+pe_sort_noalloc exists for callers that cannot allocate device memory when they sort;
+its counters live in a static device array of the library. This file is collected
+last so that a run stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1610_01071_gb300 as pe
+from paper_1610_01071_gb300 import _binding as pb
+from paper_1610_01071_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _canonical(c, t, v, w):
+    order = np.lexsort((w, v, t, c))
+    return c[order], t[order], v[order], w[order]
+
+
+@pytest.mark.parametrize("ncell,N", [(64, 5003), (4096, (1 << 20) + 7)])
+def test_sort_noalloc_matches_sort_twice(ncell, N):
+    c, t, v, w = inputs.random_particles(N, ncell, seed=ncell + 17, sort=False)
+    dc, dt, dv, dw = [torch.from_numpy(a).to(DEV) for a in (c, t, v, w)]
+    ref = [x.cpu().numpy() for x in pe.sort(dc, dt, dv, dw, ncell)]
+    for _ in range(2):  # two calls in a row: the shared counters must be cleared each time
+        st = torch.zeros(1, dtype=torch.int32, device=DEV)
+        got = [x.cpu().numpy() for x in pb.sort_noalloc(dc, dt, dv, dw, ncell, status=st)]
+        assert int(st.item()) == 0
+        assert np.all(np.diff(got[0]) >= 0)
+        for a, b in zip(_canonical(*ref), _canonical(*got)):
+            assert np.array_equal(a, b)  # the same particles, bit for bit
+
+
+def test_sort_noalloc_rejects_grids_beyond_its_static_size():
+    c, t, v, w = inputs.random_particles(100, 64, seed=1)
+    dc, dt, dv, dw = [torch.from_numpy(a).to(DEV) for a in (c, t, v, w)]
+    with pytest.raises(pb.PepicError):
+        pb.sort_noalloc(dc, dt, dv, dw, 16384)
