@@ -34,6 +34,20 @@ METRIC = "particle-steps/s and simulated time per wall-second, projective vs pla
 UNIT = "particle-steps/s"
 FUSED_BYTES_PER_PARTICLE = 28  # read cell, theta, v, w (16 B) + write cell, theta, v (12 B)
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per launch of the fused kernel from the ncu capture summarised
+# in profiles/k_particles_push_sample_iaw_large.md, valid while the kernel source hashes to
+# the value it was taken with.
+NCU_TRAFFIC = {"source_hash": "bd51059d80d12247", "bytes": 270.222080e6 + 145.538304e6}
+
+
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("pe_particles.cu", "pe_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1610_01071_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def peak_hbm():
@@ -287,7 +301,8 @@ def run_gpu(args):
         "newton_iters_last": newton_iters,
         "roofline": {"kernel": "k_particles<push+sample> (gather, kick, drift, deposit, co-moving sample)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": NCU_TRAFFIC["bytes"] if kernel_source_hash() == NCU_TRAFFIC["source_hash"] else None,
                      "bytes_per_particle": FUSED_BYTES_PER_PARTICLE, "launch_us": 1e3 * push_ms,
                      "launches": prof["push_launches"]},
         "e2e": {"value": ps_proj / t_e2e_max, "unit": UNIT, "h2d_bytes_per_step": 8 * 2 * cfg["n_coarse"],
