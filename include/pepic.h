@@ -320,6 +320,31 @@ PE_API int pe_profile(pe_ctx* ctx, int32_t enable);
 PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
                            int64_t* field_launches);
 
+/* =================================================================== batch
+ * Ensemble of independent realisations advanced together (the same burst length, fine
+ * and macro steps; any grid of at least 64 cells, any particle count, Haar wavelet).
+ * Each fine step of the whole ensemble is one persistent particle launch over a shared
+ * work list of particle chunks plus one launch of field-solve clusters (one per
+ * realisation); from the second pe_batch_step on, the burst, restriction and
+ * projection of every realisation replay as one captured CUDA graph. Lifting stays
+ * per realisation. Each context keeps its own arena; the batch needs caller-owned
+ * device scratch of pe_batch_scratch_bytes (256-byte aligned) for its descriptors, work
+ * list and the ensemble's charge, field-copy and sample grids. Results are identical,
+ * bit for bit, to pe_step on each context alone. The batch's stream waits for work
+ * queued on each context's stream, and each context's stream waits for the batch. Graph
+ * capture needs a created stream: on the legacy default stream every step runs eagerly. */
+typedef struct pe_batch pe_batch;
+PE_API int pe_batch_scratch_bytes(pe_ctx* const* ctxs, int32_t n, size_t* bytes);
+PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scratch, size_t scratch_bytes, void* stream,
+                           pe_batch** out);
+/* One projective macro step of every realisation (all must have been loaded, or all
+ * advanced by the batch: PE_ESTATE otherwise). */
+PE_API int pe_batch_step(pe_batch* b);
+/* Autotuner: times the batched particle pass (read-only sample form) for particle
+ * chunks of 8192..65536 per block and keeps the fastest; returns it in *chunk. */
+PE_API int pe_batch_tune(pe_batch* b, int64_t* chunk);
+PE_API void pe_batch_destroy(pe_batch* b);
+
 /* Number of kernels this library has launched in the process so far. */
 PE_API int64_t pe_launch_count(void);
 

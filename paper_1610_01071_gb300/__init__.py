@@ -5,8 +5,8 @@ sm_103a; this package only marshals arguments to its C ABI (``include/pepic.h``)
 Calls raise if the library is missing: there is no CPU path.
 """
 from . import inputs
-from ._binding import (BUF, Config, Context, PepicError, coarsen, deposit, field, layout, load, ls_project,
+from ._binding import (BUF, Batch, Config, Context, PepicError, coarsen, deposit, field, layout, load, ls_project,
                        make_config, make_sample_args, push, quiet_start, refine, sample, sort)
 
-__all__ = ["BUF", "Config", "Context", "PepicError", "coarsen", "deposit", "field", "inputs", "layout", "load",
+__all__ = ["BUF", "Batch", "Config", "Context", "PepicError", "coarsen", "deposit", "field", "inputs", "layout", "load",
            "ls_project", "make_config", "make_sample_args", "push", "quiet_start", "refine", "sample", "sort"]

@@ -91,6 +91,11 @@ SIGNATURES = {
     "pe_profile": (ctypes.c_int, [P, i32]),
     "pe_profile_read": (ctypes.c_int, [P, P, P, P, P]),
     "pe_launch_count": (i64, []),
+    "pe_batch_scratch_bytes": (ctypes.c_int, [P, i32, ctypes.POINTER(sz)]),
+    "pe_batch_create": (ctypes.c_int, [P, i32, P, sz, P, ctypes.POINTER(P)]),
+    "pe_batch_step": (ctypes.c_int, [P]),
+    "pe_batch_tune": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+    "pe_batch_destroy": (None, [P]),
 }
 
 
@@ -370,3 +375,37 @@ class Context:
         seg = [self.arena[off + k * stride: off + k * stride + 4 * N] for k in range(4)]
         return (seg[0].view(torch.int32), seg[1].view(torch.float32), seg[2].view(torch.float32),
                 seg[3].view(torch.float32))
+
+
+class Batch:
+    """Ensemble of Context objects advanced together (pe_batch_*)."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        dev = self.contexts[0].device
+        # a created stream (the legacy default stream cannot be captured into a graph)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        self._arr = arr
+        nbytes = ctypes.c_size_t()
+        check(load().pe_batch_scratch_bytes(arr, len(self.contexts), ctypes.byref(nbytes)), "pe_batch_scratch_bytes")
+        self.scratch = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        base = self.scratch.data_ptr()
+        pad = (-base) % 256
+        self._h = ctypes.c_void_p()
+        check(load().pe_batch_create(arr, len(self.contexts), ctypes.c_void_p(base + pad), nbytes.value,
+                                     _stream(self.stream), ctypes.byref(self._h)), "pe_batch_create")
+
+    def step(self):
+        check(load().pe_batch_step(self._h), "pe_batch_step")
+
+    def tune(self):
+        chunk = ctypes.c_int64()
+        check(load().pe_batch_tune(self._h, ctypes.byref(chunk)), "pe_batch_tune")
+        return chunk.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pe_batch_destroy(h)
+            self._h = None

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 
+#include "pe_ctx.h"
 #include "pe_internal.h"
 #include "pepic.h"
 
@@ -105,50 +106,6 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 using namespace pe;
 
-struct pe_ctx {
-    pe_config cfg;
-    pe_layout lay;
-    char* arena;
-    cudaStream_t stream;
-    double dx;
-    int s_w, s_p, nc;
-    int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
-    int nb;              // sample length per moment: ncell >> bin_shift
-    int bank;            // which particle bank is current
-    int v_at_integer;    // stored v is at integer time
-    int fresh;           // particles were just loaded/lifted (not yet advanced)
-    int rho_valid;       // rho holds the deposit of the current particles
-    int64_t macro_steps, fine_steps;
-    double time;
-    int32_t* cell[2];
-    float* theta[2];
-    float* v[2];
-    float* w[2];
-    int64_t* rho;
-    double* phi;
-    double* E;
-    float* Ef;
-    float* E0f;
-    int64_t* samples;  // [K+2][2][ncell]; row K+1 is measurement scratch
-    double* csamples;  // [K+2][2][nc]
-    double* coarse;
-    double* slope;
-    float* prof;
-    int32_t* sort;
-    uint32_t* status;
-    int32_t* diag;
-    // kernel timing (pe_profile)
-    int profiling;
-    std::vector<cudaEvent_t>* ev_push;   // start/stop pairs
-    std::vector<cudaEvent_t>* ev_field;
-    size_t n_push, n_field;               // pairs recorded since the last read
-};
-
-#define PE_TRY(x)                   \
-    do {                            \
-        int _rc = (x);              \
-        if (_rc != PE_OK) return _rc; \
-    } while (0)
 
 extern "C" PE_API const char* pe_strerror(int code)
 {
@@ -380,6 +337,9 @@ static int quiet_start_from_profile(pe_ctx* x, uint64_t seed)
 }
 
 static uint64_t lift_seed(const pe_ctx* x) { return x->cfg.seed + 0x632BE59BD9B4E019ULL * (uint64_t)(x->macro_steps + 1); }
+
+int pe_ctx_field_solve(pe_ctx* x) { return field_solve(x); }
+uint64_t pe_ctx_lift_seed(const pe_ctx* x) { return lift_seed(x); }
 
 extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device)
 {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pe_common.cuh"
 #include "pe_internal.h"
@@ -163,6 +164,59 @@ __global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, F
         prof_n[j] = (float)n;
         prof_u[j] = (n > 1e-12 * nmax) ? (float)(mf[j] / n) : 0.0f;
     }
+}
+
+// Batched restriction + projection for Haar samples summed over coarse bins (one block per
+// realisation): the same arithmetic, in the same order, as pe_coarsen with bin_shift =
+// log2(ncell / n_coarse) followed by pe_ls_project.
+struct ProjDesc {
+    const long long* samp;  // row p of this realisation at samp + p * row_stride: [2][nc]
+    int64_t row_stride;
+    double scale_n, scale_m;
+    double* csamples;  // [K+1][2][nc] coarse samples (may be null)
+    double* coarse;    // [2][nc] projected state
+    double* slope;     // [2][nc]
+    int nc, pad;
+};
+
+__global__ void __launch_bounds__(256) k_restrict_project_batch(const ProjDesc* descs, int K, double dt, double dT)
+{
+    const ProjDesc d = descs[blockIdx.x];
+    const int ncoef = 2 * d.nc;
+    const double den = (double)K * (K + 1) * (K + 2) * dt;
+    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+        const double scale = (i >= d.nc) ? d.scale_m : d.scale_n;
+        double s = 0.0;
+        for (int p = 0; 2 * p <= K; ++p) {
+            const double cK = (double)d.samp[(int64_t)(K - p) * d.row_stride + i] * scale;
+            const double c0 = (double)d.samp[(int64_t)p * d.row_stride + i] * scale;
+            s += 6.0 * (K - 2 * p) / den * (cK - c0);
+        }
+        const double last = (double)d.samp[(int64_t)K * d.row_stride + i] * scale;
+        d.slope[i] = s;
+        d.coarse[i] = last + (dT - K * dt) * s;
+        if (d.csamples)
+            for (int p = 0; p <= K; ++p)
+                d.csamples[(size_t)p * ncoef + i] = (double)d.samp[(int64_t)p * d.row_stride + i] * scale;
+    }
+}
+
+size_t proj_desc_size() { return sizeof(ProjDesc); }
+
+void make_proj_desc(void* out, const int64_t* samp, int64_t row_stride, int ncell, int nc, int s_w, int s_p,
+                    double* csamples, double* coarse, double* slope)
+{
+    const int b = ilog2(ncell / nc);
+    const double lev = pow(2.0, -0.5 * (ilog2(ncell) + b));
+    ProjDesc d{reinterpret_cast<const long long*>(samp), row_stride, ldexp(1.0, -(s_w + 24)) * lev,
+               ldexp(1.0, -(s_p + 24)) * lev, csamples, coarse, slope, nc, 0};
+    memcpy(out, &d, sizeof(d));
+}
+
+int launch_restrict_project_batch(const void* descs, int R, int K, double dt, double dT, cudaStream_t s)
+{
+    k_restrict_project_batch<<<R, 256, 0, s>>>(static_cast<const ProjDesc*>(descs), K, dt, dT);
+    return launch_status();
 }
 
 }  // namespace pe

@@ -5,6 +5,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pe_common.cuh"
 #include "pe_internal.h"
@@ -13,7 +14,7 @@ namespace cg = cooperative_groups;
 
 namespace pe {
 
-constexpr int kClusterMinCells = 1024;  // grids at least this large use the multi-SM solver
+constexpr int kClusterMinCells = 512;  // grids at least this large use the multi-SM solver
 
 // ---------------------------------------------------------------------------------
 // Production solver: one thread-block cluster of G blocks (G = 1 for small grids, up to
@@ -116,16 +117,34 @@ __device__ void block_pcr(float* L3, float* L3n, float* zsol, int G)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, int ncell, double dx, double nscale,
-                                                         int mode, double tol, int maxit, double* phi, double* E,
-                                                         float* Ef, int* diag, uint32_t* status)
+// Parameters of one field solve (one realisation).
+struct FieldDesc {
+    const long long* rho;
+    double* phi;
+    double* E;
+    float* Ef;
+    int* diag;
+    uint32_t* status;
+    double dx, nscale, tol;
+    int ncell, mode, maxit, pad;
+};
+
+// Solver body for the realisation of this cluster: B = ncell / G nodes per block, one per
+// thread; threads at or beyond B (a batched launch sized for a larger grid) only take
+// part in the barriers.
+__device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_group& cluster)
 {
-    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ double sh[];
     const int G = (int)cluster.num_blocks();
     const int g = (int)cluster.block_rank();
-    const int B = blockDim.x;
+    const int ncell = d.ncell;
+    const int B = ncell / G;
     const int i = threadIdx.x;
+    const bool act = i < B;
+    const long long* rho = d.rho;
+    double* phi = d.phi;
+    const double dx = d.dx, nscale = d.nscale, tol = d.tol;
+    const int mode = d.mode, maxit = d.maxit;
     double* ph = sh;                                 // [B + 2]
     double* mymax = ph + B + 2;                      // [1]
     float* A = reinterpret_cast<float*>(mymax + 1);  // [B] x 6
@@ -141,38 +160,42 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, i
     float* zsol = L3n + 14 * G;  // [2G]
 
     const int mask = ncell - 1;
-    const int j = g * B + i;
+    const int j = g * B + (act ? i : 0);
     const double inv_dx2 = 1.0 / (dx * dx);
     const float o = (float)(-inv_dx2);
     const bool boltz = (mode == PE_POISSON_BOLTZMANN);
-    const double nj = (double)__ldg(rho + j) * nscale;
-    double pj = phi[j];
+    const double nj = act ? (double)__ldg(rho + j) * nscale : 0.0;
+    double pj = act ? phi[j] : 0.0;
     double gj = boltz ? exp(pj) : 1.0 + pj;
 
     int it = 0;
     bool converged = false;
     for (it = 0; it < maxit; ++it) {
         // ---- FP64 residual with the halo from the neighbouring blocks
-        ph[i + 1] = pj;
-        if (i == 0) ph[0] = phi[(g * B - 1) & mask];
-        if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
+        if (act) {
+            ph[i + 1] = pj;
+            if (i == 0) ph[0] = phi[(g * B - 1) & mask];
+            if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
+        }
         __syncthreads();
-        const double lap = (ph[i] - 2.0 * pj + ph[i + 2]) * inv_dx2;
-        A[i] = (i == 0) ? 0.f : o;
-        C[i] = (i == B - 1) ? 0.f : o;
-        Bd[i] = (float)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
-        D[i] = (float)(lap - gj + nj);  // -F_j
-        Gs[i] = (i == 0) ? o : 0.f;
-        Hs[i] = (i == B - 1) ? o : 0.f;
+        if (act) {
+            const double lap = (ph[i] - 2.0 * pj + ph[i + 2]) * inv_dx2;
+            A[i] = (i == 0) ? 0.f : o;
+            C[i] = (i == B - 1) ? 0.f : o;
+            Bd[i] = (float)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
+            D[i] = (float)(lap - gj + nj);  // -F_j
+            Gs[i] = (i == 0) ? o : 0.f;
+            Hs[i] = (i == B - 1) ? o : 0.f;
+        }
         __syncthreads();
         // ---- FP32 parallel cyclic reduction of the block rows, three right-hand sides
         for (int s = 1; s < B; s <<= 1) {
-            const int im = i - s, ip = i + s;
+            const int im = act ? i - s : -1, ip = act ? i + s : B;
             const float al = (im >= 0) ? A[i] / Bd[im] : 0.f;
             const float ga = (ip < B) ? C[i] / Bd[ip] : 0.f;
             const float nA = (im >= 0) ? -al * A[im] : 0.f;
             const float nC = (ip < B) ? -ga * C[ip] : 0.f;
-            float nB = Bd[i], nD = D[i], nG = Gs[i], nH = Hs[i];
+            float nB = act ? Bd[i] : 0.f, nD = act ? D[i] : 0.f, nG = act ? Gs[i] : 0.f, nH = act ? Hs[i] : 0.f;
             if (im >= 0) {
                 nB -= al * C[im];
                 nD -= al * D[im];
@@ -186,16 +209,19 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, i
                 nH -= ga * Hs[ip];
             }
             __syncthreads();
-            A[i] = nA;
-            C[i] = nC;
-            Bd[i] = nB;
-            D[i] = nD;
-            Gs[i] = nG;
-            Hs[i] = nH;
+            if (act) {
+                A[i] = nA;
+                C[i] = nC;
+                Bd[i] = nB;
+                D[i] = nD;
+                Gs[i] = nG;
+                Hs[i] = nH;
+            }
             __syncthreads();
         }
-        const float rb = 1.0f / Bd[i];
-        const float y = D[i] * rb, gsp = Gs[i] * rb, hsp = Hs[i] * rb;  // x = y - g X_left - h X_right
+        const float rb = act ? 1.0f / Bd[i] : 0.f;
+        const float y = act ? D[i] * rb : 0.f, gsp = act ? Gs[i] * rb : 0.f,
+                    hsp = act ? Hs[i] * rb : 0.f;  // x = y - g X_left - h X_right
         if (i == 0) {
             mine[0] = y;
             mine[1] = gsp;
@@ -228,7 +254,7 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, i
         if ((i & 31) == 0) red[i >> 5] = mloc;
         __syncthreads();
         if (i < 32) {
-            float v = (i < ((B + 31) >> 5)) ? red[i] : 0.f;
+            float v = (i < ((blockDim.x + 31) >> 5)) ? red[i] : 0.f;
             for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
             if (i == 0) *mymax = (double)v;
         }
@@ -236,9 +262,9 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, i
         double m = 0.0;
         for (int k = 0; k < G; ++k) m = fmax(m, *cluster.map_shared_rank(mymax, k));
         const double scale = (m > 2.0) ? 2.0 / m : 1.0;
-        const double x = scale * (double)dlt;
+        const double x = act ? scale * (double)dlt : 0.0;
         pj += x;
-        phi[j] = pj;
+        if (act) phi[j] = pj;
         if (boltz)
             gj = (fabs(x) <= 0.03125) ? gj * exp_small(x) : exp(pj);
         else
@@ -251,22 +277,40 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(const long long* rho, i
             break;
         }
     }
-    ph[i + 1] = pj;
-    if (i == 0) ph[0] = phi[(g * B - 1) & mask];
-    if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
-    __syncthreads();
-    const double e = -(ph[i + 2] - ph[i]) * (0.5 / dx);
-    E[j] = e;
-    Ef[j] = (float)e;
-    if (g == 0 && i == 0) {
-        if (diag) {
-            diag[0] = it;
-            diag[1] = converged ? 1 : 0;
-            diag[2] = G;
-            diag[3] = B;
-        }
-        if (!converged) raise_flag(status, PE_FLAG_NOCONV);
+    if (act) {
+        ph[i + 1] = pj;
+        if (i == 0) ph[0] = phi[(g * B - 1) & mask];
+        if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
     }
+    __syncthreads();
+    if (act) {
+        const double e = -(ph[i + 2] - ph[i]) * (0.5 / dx);
+        d.E[j] = e;
+        d.Ef[j] = (float)e;
+    }
+    if (g == 0 && i == 0) {
+        if (d.diag) {
+            d.diag[0] = it;
+            d.diag[1] = converged ? 1 : 0;
+            d.diag[2] = G;
+            d.diag[3] = B;
+        }
+        if (!converged) raise_flag(d.status, PE_FLAG_NOCONV);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_newton_cluster(FieldDesc d)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    newton_body(d, cluster);
+}
+
+// One cluster per realisation: cluster c solves descs[c].
+__global__ void __launch_bounds__(1024) k_newton_batch(const FieldDesc* descs)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const FieldDesc d = descs[blockIdx.x / cluster.num_blocks()];
+    newton_body(d, cluster);
 }
 
 static int cluster_size_for(int ncell)
@@ -296,10 +340,32 @@ static int cluster_size_for(int ncell)
         cached[dev] = p;
     }
     int G = cached[dev];
-    while (G > 1 && ncell / G < 64) G >>= 1;  // at least 64 nodes per block
+    while (G > 1 && ncell / G < 32) G >>= 1;  // at least 32 nodes per block
     if (ncell < kClusterMinCells) G = 1;
     while (ncell / G > 1024) G <<= 1;          // at most 1024 nodes (threads) per block
     return G <= kClusterMax ? G : 0;
+}
+
+size_t newton_smem_bytes(int B, int G)
+{
+    return sizeof(double) * ((size_t)B + 3) + sizeof(float) * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+}
+
+static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int nclusters, int block, size_t smem,
+                                         cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(G * nclusters);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
 static int launch_newton_cluster(int G, const long long* rho, int ncell, double dx, double nscale, int mode,
@@ -308,24 +374,48 @@ static int launch_newton_cluster(int G, const long long* rho, int ncell, double 
 {
     const int B = ncell / G;  // one node per thread
     if (B > 1024 || B < 2) return PE_EINVAL;
-    const size_t smem = sizeof(double) * ((size_t)B + 3) + sizeof(float) * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    const size_t smem = newton_smem_bytes(B, G);
     if (ensure_smem((const void*)k_newton_cluster, smem) != PE_OK) return PE_ECUDA;
-    cudaLaunchConfig_t cfg = {};
+    FieldDesc d{rho, phi, E, Ef, diag, status, dx, nscale, tol, ncell, mode, maxit, 0};
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = G;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(B);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, k_newton_cluster, rho, ncell, dx, nscale, mode, tol, maxit, phi, E, Ef, diag,
-                           status) != cudaSuccess)
+    cudaLaunchConfig_t cfg = cluster_config(attr, G, 1, B, smem, s);
+    if (cudaLaunchKernelEx(&cfg, k_newton_cluster, d) != cudaSuccess) return PE_ECUDA;
+    return launch_status();
+}
+
+int newton_cluster_size(int ncell) { return cluster_size_for(ncell); }
+
+// Batched field solves: descs[R] on the device, every grid with the same cluster size G.
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, cudaStream_t s)
+{
+    const int B = max_ncell / G;
+    if (B > 1024 || B < 2 || R < 1) return PE_EINVAL;
+    const size_t smem = newton_smem_bytes(B, G);
+    if (ensure_smem((const void*)k_newton_batch, smem) != PE_OK) return PE_ECUDA;
+    static bool nonportable[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PE_ECUDA;
+    if (G > 8 && !nonportable[dev]) {
+        if (cudaFuncSetAttribute((const void*)k_newton_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+            return PE_ECUDA;
+        nonportable[dev] = true;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(attr, G, R, B, smem, s);
+    if (cudaLaunchKernelEx(&cfg, k_newton_batch, static_cast<const FieldDesc*>(descs)) != cudaSuccess)
         return PE_ECUDA;
     return launch_status();
+}
+
+size_t field_desc_size() { return sizeof(FieldDesc); }
+
+void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, double tol, int maxit,
+                     double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status)
+{
+    FieldDesc d{reinterpret_cast<const long long*>(rho), phi, E, Ef, diag, status, dx, ldexp(1.0, -(s_w + 24)), tol,
+                ncell, mode, maxit, 0};
+    memcpy(out, &d, sizeof(d));
 }
 
 }  // namespace pe

@@ -28,6 +28,31 @@ int ensure_smem(const void* kernel, size_t smem);
 // Resident blocks per SM for (kernel, block, smem) on the current device (cached).
 int blocks_per_sm(const void* kernel, int block, size_t smem);
 
+// Batched field solves (pe_field.cu): descriptor size, descriptor builder, cluster size
+// used for a grid of ncell nodes, and the launch over R realisations of one cluster size.
+size_t field_desc_size();
+void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, double tol, int maxit,
+                     double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status);
+int newton_cluster_size(int ncell);
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, cudaStream_t s);
+
+// Batched particle passes (pe_particles.cu).
+size_t push_desc_size();
+size_t work_item_size();
+void make_push_desc(void* out, int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
+                    int ncell, float dt_dx, float qm_dt, int s_w, int64_t* rho, const float* E0f, double dT, double dt,
+                    float inv_dx, float qm, int comoving, int s_p, int bin_shift, int64_t* samp_base,
+                    int64_t row_stride, uint32_t* status);
+void make_work_item(void* out, int r, int64_t begin, int64_t end);
+int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
+                           unsigned* counter, int max_ncell, int max_nb, cudaStream_t s);
+
+// Batched restriction + projection of Haar-binned samples (pe_coarse.cu).
+size_t proj_desc_size();
+void make_proj_desc(void* out, const int64_t* samp, int64_t row_stride, int ncell, int nc, int s_w, int s_p,
+                    double* csamples, double* coarse, double* slope);
+int launch_restrict_project_batch(const void* descs, int R, int K, double dt, double dT, cudaStream_t s);
+
 // Counts kernel launches (exported through pe_launch_count).
 void note_launches(int n);
 

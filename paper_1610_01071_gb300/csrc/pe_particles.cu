@@ -9,6 +9,7 @@
 // All sums are integers, so the result is exact and independent of order.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pe_common.cuh"
 #include "pe_internal.h"
@@ -34,6 +35,13 @@ struct PushParams {
     int samp_width;
     int bin_shift;  // > 0: samples summed over bins of 2^bin_shift nodes (BINNED modes)
     uint32_t* status;
+    // batched launches: per-step fields derived on the device from these
+    double dT, dt;                     // tau = comoving ? (float)(dT - p dt) : 0, as on the host
+    float inv_dx, qm;
+    int comoving;
+    unsigned long long* samp_base;     // sample row p starts at samp_base + p * row_stride
+    int64_t row_stride;
+    int64_t max_chunk;                 // largest particle chunk per block (<= 65536; 0 = 65536)
 };
 
 enum Mode { kDeposit = 0, kPush = 1, kPushSample = 2, kSample = 3, kPushSampleBinned = 4, kSampleBinned = 5 };
@@ -137,7 +145,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
 // One block owns a contiguous chunk of <= 65536 particles; each warp a contiguous slice
 // of it, read with 16-byte loads (4 particles per lane, two groups in flight).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
+__device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begin, int64_t end, uint32_t* smem)
 {
     using Tr = ModeTraits<MODE>;
     constexpr bool kRho = Tr::rho;
@@ -145,10 +153,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
     constexpr bool kBin = Tr::binned;
     constexpr bool kWrite = Tr::push;
     constexpr bool kNeedV = (MODE != kDeposit);
-    extern __shared__ uint32_t smem[];
 
-    int64_t begin, end;
-    block_chunk(P.n, P.chunk, &begin, &end);
     const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
 
     SmemGrid grho{}, gsn{}, gsm{};
@@ -250,6 +255,51 @@ __global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
     if (kBin) {
         bsn.flush();
         bsm.flush();
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
+{
+    extern __shared__ uint32_t smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    particle_chunk<MODE>(P, begin, end, smem);
+}
+
+// Work item of a batched launch: particles [begin, end) of realisation r.
+struct WorkItem {
+    int64_t begin, end;
+    int r, pad;
+};
+
+// Persistent batched launch over the work items of many realisations: each block takes
+// the next item from a global counter until none are left. Step p and the kick are the
+// same for every realisation; tau and the sample row follow from each descriptor.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 3) k_particles_batch(const PushParams* descs, const WorkItem* items,
+                                                                 int nitems, int p, float kick, unsigned* counter)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = next;
+        __syncthreads();
+        if (it >= nitems) break;
+        const WorkItem wi = items[it];
+        PushParams P = descs[wi.r];
+        P.kick = kick;
+        const float tau = P.comoving ? (float)(P.dT - p * P.dt) : 0.f;
+        P.tau_dx = tau * P.inv_dx;
+        P.qm_tau = P.qm * tau;
+        if (ModeTraits<MODE>::sample) {
+            P.samp_n = P.samp_base + (int64_t)p * P.row_stride;
+            P.samp_m = P.samp_n + (P.ncell >> P.bin_shift);
+        }
+        particle_chunk<MODE>(P, wi.begin, wi.end, smem);
+        __syncthreads();
     }
 }
 
@@ -464,13 +514,14 @@ static __device__ __align__(256) unsigned g_sort_static[2 * PE_SORT_STATIC_MAX_C
 
 // ------------------------------------------------------------------ host side
 
-static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk)
+static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk = 0)
 {
     int64_t blocks = (int64_t)sm_count() * blocks_per_sm(kernel, block, smem);
     int64_t c = (n + blocks - 1) / blocks;
     c = (c + 3) & ~int64_t(3);
     if (c < 4) c = 4;
-    if (c > kMaxChunk) c = kMaxChunk;  // keeps the shared-memory digit counters exact
+    const int64_t cap = (max_chunk > 0 && max_chunk < kMaxChunk) ? (max_chunk & ~int64_t(3)) : kMaxChunk;
+    if (c > cap) c = cap;  // the cap keeps the shared-memory digit counters exact
     *chunk = c;
     int64_t g = (n + c - 1) / c;
     return (int)(g < 1 ? 1 : g);
@@ -490,7 +541,7 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = (const void*)k_particles<MODE>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    int grid = grid_for(k, block, smem, P.n, &P.chunk);
+    int grid = grid_for(k, block, smem, P.n, &P.chunk, P.max_chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
     if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)(P.ncell >> P.bin_shift), s) != cudaSuccess)
         return PE_ECUDA;
@@ -512,6 +563,84 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
     if (s->bin_shift == 0) return true;
     return (5 * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
+}
+
+// ------------------------------------------------------------------ batched launches
+
+size_t push_desc_size() { return sizeof(PushParams); }
+size_t work_item_size() { return sizeof(WorkItem); }
+
+void make_push_desc(void* out, int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
+                    int ncell, float dt_dx, float qm_dt, int s_w, int64_t* rho, const float* E0f, double dT, double dt,
+                    float inv_dx, float qm, int comoving, int s_p, int bin_shift, int64_t* samp_base,
+                    int64_t row_stride, uint32_t* status)
+{
+    PushParams P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.Ef = Ef;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.dt_dx = dt_dx;
+    P.qm_dt = qm_dt;
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho);
+    P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
+    P.E0f = E0f;
+    P.pscale = ldexpf(1.0f, s_p);
+    P.samp_width = 0;
+    P.bin_shift = bin_shift;
+    P.status = status;
+    P.dT = dT;
+    P.dt = dt;
+    P.inv_dx = inv_dx;
+    P.qm = qm;
+    P.comoving = comoving;
+    P.samp_base = reinterpret_cast<unsigned long long*>(samp_base);
+    P.row_stride = row_stride;
+    memcpy(out, &P, sizeof(P));
+}
+
+void make_work_item(void* out, int r, int64_t begin, int64_t end)
+{
+    WorkItem wi{begin, end, r, 0};
+    memcpy(out, &wi, sizeof(wi));
+}
+
+// Grid size (blocks) of a persistent batched launch: every resident block of the GPU.
+int batch_grid(int mode, int max_ncell, int max_nb)
+{
+    const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
+    const void* k = (mode == 0) ? (const void*)k_particles_batch<kPushSampleBinned> : (const void*)k_particles_batch<kSampleBinned>;
+    const size_t smem = 3 * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) + 5 * sizeof(uint32_t) * 2 * max_nb;
+    return sm_count() * blocks_per_sm(k, kThreads, smem);
+}
+
+// mode 0: fused push + binned sample of step p; mode 1: binned sample only.
+int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
+                           unsigned* counter, int max_ncell, int max_nb, cudaStream_t s)
+{
+    const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
+    const size_t smem = 3 * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) + 5 * sizeof(uint32_t) * 2 * max_nb;
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
+    const auto* d = static_cast<const PushParams*>(descs);
+    const auto* it = static_cast<const WorkItem*>(items);
+    if (mode == 0) {
+        const void* k = (const void*)k_particles_batch<kPushSampleBinned>;
+        if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+        const int grid = sm_count() * blocks_per_sm(k, kThreads, smem);
+        k_particles_batch<kPushSampleBinned><<<grid, kThreads, smem, s>>>(d, it, nitems, p, kick, counter);
+    } else {
+        const void* k = (const void*)k_particles_batch<kSampleBinned>;
+        if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+        const int grid = sm_count() * blocks_per_sm(k, kThreads, smem);
+        k_particles_batch<kSampleBinned><<<grid, kThreads, smem, s>>>(d, it, nitems, p, kick, counter);
+    }
+    return launch_status();
 }
 
 }  // namespace pe
