@@ -269,6 +269,8 @@ def run_gpu(args):
             ctx.get_coarse_host(host)
         t_e2e = time.perf_counter() - t0
         barrier()
+        # ---------------- time to solution and accuracy against a resolved plain-PIC run
+        acc = run_accuracy(dev, cfg, pb) if not args.no_accuracy else None
         # ---------------- ensemble of 64 realisations of log-uniform sizes (pe_batch)
         ens = run_ensemble(dev, max(args.steps // 2, 2), 3, rank) if not args.no_ensemble else None
     clocks = sampler.stop()
@@ -312,6 +314,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if acc is not None:
+        line["time_to_solution"] = acc
     if ens is not None:
         t_ens = max_over_ranks(ens["seconds"])
         line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10",
@@ -405,6 +409,48 @@ def ensemble_sizes(count=64, seed=4):
     return out
 
 
+def run_accuracy(dev, cfg, pb):
+    """Time to the ion-wave end time T = macro_steps * Delta t, projective vs plain GPU PIC,
+    and the relative L2 error of the coarse density (Section 4.1.1, Eq. errormeasures)."""
+    import numpy as np
+    import torch
+
+    c = pb.make_config(cfg["ncell"], cfg["n_coarse"], cfg["K"], cfg["N"], cfg["L"], cfg["dt"], cfg["dT"],
+                       qm=cfg["qm"], v_th=cfg["v_th"], wavelet=cfg["wavelet"], seed=11, sort_every=20,
+                       newton_tol=1e-10)
+    steps = cfg["macro_steps"]
+    per = int(round(cfg["dT"] / cfg["dt"]))
+    checks = sorted({max(1, steps // 5), steps // 2, steps})
+    ef, ref = pb.Context(c, device=dev), pb.Context(c, device=dev)
+    ef.load_initial(cfg["amplitude"])
+    ref.load_initial(cfg["amplitude"])
+    got = {}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for m in range(1, steps + 1):
+        ef.step()
+        if m in checks:
+            got[m] = ef.get_coarse()[0].clone()
+    torch.cuda.synchronize(dev)
+    t_proj = time.perf_counter() - t0
+    want = {}
+    t0 = time.perf_counter()
+    done = 0
+    for m in checks:
+        ref.pic_steps((m - done) * per)
+        done = m
+        want[m] = ref.measure()[0].clone()
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    eps = {}
+    for m in checks:
+        a, b = got[m].cpu().numpy(), want[m].cpu().numpy()
+        eps[str(round(m * cfg["dT"]))] = float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
+    return {"T_end": steps * cfg["dT"], "projective_s": t_proj, "plain_pic_s": t_plain,
+            "speedup": t_plain / t_proj, "eps_coarse_density_at_T": eps,
+            "status": [ef.sync_status(), ref.sync_status()]}
+
+
 def run_ensemble(dev, steps, warmup, rank=0):
     """64 realisations advanced by pe_batch (shared launches, replayed CUDA graph)."""
     import torch
@@ -447,6 +493,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--kernel", default=None, help="time one kernel alone (profiling mode)")
     args = ap.parse_args()
     if args.kernel:
