@@ -203,6 +203,43 @@ PE_API int pe_sort_noalloc(const int32_t* cell, const float* theta, const float*
                            int64_t n, int32_t ncell, int32_t* out_cell, float* out_theta,
                            float* out_v, float* out_w, uint32_t* status, void* stream);
 
+/* Diagnostics of a particle state (Section 4's conservation checks and the particle
+ * CFL number). Velocities are taken at integer time, Vbar = v + (kick - 1/2) qm_dt E(X)
+ * with E(X) the CIC gather of Ef (kick = 1/2 when v is already at integer time, 1 when
+ * it is at half-integer time and Ef is the field of the current positions). Each
+ * particle carries charge w dx. The electron free energy is sum (phi e^phi - e^phi + 1) dx
+ * for PE_POISSON_BOLTZMANN and sum phi^2 dx / 2 for PE_POISSON_LINEARIZED: with the ion
+ * kinetic and the field energy it makes the energy that the continuous ion /
+ * Boltzmann-electron system conserves. phi and E (FP64 [ncell]) may be NULL (their
+ * energies are then 0). A particle with cell outside [0, ncell), theta outside [0, 1] or
+ * a non-finite v or w is counted in `invalid`, left out of every sum, and sets
+ * PE_FLAG_RANGE. scratch: PE_MOMENTS_SCRATCH_BYTES of device memory (16-byte aligned);
+ * out: one pe_moments in device memory, written on the stream. Floating-point sums use a
+ * fixed partition for a given n, so repeated calls return identical bits. */
+#define PE_MOMENTS_SCRATCH_BYTES 49152
+typedef struct pe_moments {
+    int64_t charge_fx;          /* sum_p rn(w 2^s_w) 2^24: equals the sum of the deposit */
+    int64_t invalid;            /* particles left out (see above) */
+    double charge_fixed_point;  /* charge_fx 2^-(s_w+24) dx */
+    double charge;              /* sum w dx */
+    double momentum;            /* sum w Vbar dx */
+    double kinetic;             /* sum w Vbar^2 dx / 2 */
+    double field_energy;        /* sum E_j^2 dx / 2 */
+    double electron_energy;     /* see above */
+    double total_energy;        /* kinetic + field + electron */
+    double max_speed;           /* max |Vbar| */
+    double cfl;                 /* max_speed dt / dx */
+} pe_moments;
+PE_API int pe_compute_moments(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
+                      const float* Ef, const double* phi, const double* E, int32_t ncell, double dx, double dt,
+                      float qm_dt, float kick, int32_t s_w, int32_t mode, void* scratch, pe_moments* out,
+                      uint32_t* status, void* stream);
+
+/* Error measure of Section 4.1.1 between two coarse states (or any FP64 vectors):
+ * out = sqrt( sum_i (a_i - b_i)^2 / sum_i (a_i^2 + b_i^2) ), 0 when both vanish. a, b, out
+ * in device memory; one block, fixed summation order. */
+PE_API int pe_rel_l2(const double* a, const double* b, int64_t n, double* out, void* stream);
+
 /* =================================================================== context
  * One realisation of the projective-integration cycle (Section 3.1, Figure
  * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares
@@ -247,6 +284,8 @@ enum pe_buffer {
     PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u) */
     PE_BUF_SORT,            /* int32[2 ncell + 64] sort scratch */
     PE_BUF_STATUS,          /* uint32[4] status word; int32[4] Newton diag after it */
+    PE_BUF_DIAG,            /* pe_moments scratch + one pe_moments result */
+    PE_BUF_SURROGATE,       /* f64[2][n_coarse] surrogate slope + gate result */
     PE_NBUF
 };
 
@@ -300,6 +339,9 @@ PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps);
  * shift) into host or device memory out[2][n_coarse]. */
 PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device);
 
+/* Least-squares slope (f64[2][n_coarse]) of the last macro step (or the accepted surrogate
+ * slope), into host or device memory. */
+PE_API int pe_get_slope(pe_ctx* ctx, double* out, int32_t out_on_device);
 /* Copy the coarse state (f64[2][n_coarse]) out of / into the context. */
 PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device);
 PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
@@ -307,6 +349,11 @@ PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
 /* Synchronises the context's stream and returns PE_OK or the first device fault
  * (PE_ETIMEOUT, PE_ERANGE, PE_EOVERFLOW, PE_ENOCONV); clears the status word. */
 PE_API int pe_sync_status(pe_ctx* ctx);
+/* Conserved quantities of the current particles at the current time (pe_compute_moments
+ * with the field of the current positions; deposits and solves it first, which also
+ * refreshes the Newton warm start, as pe_measure does). out: host (synchronises) or
+ * device memory. */
+PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out_on_device);
 /* Host-side counters (no synchronisation except for newton_iters/status, which are
  * read after a stream synchronise). */
 PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out);
@@ -344,6 +391,112 @@ PE_API int pe_batch_step(pe_batch* b);
  * chunks of 8192..65536 per block and keeps the fastest; returns it in *chunk. */
 PE_API int pe_batch_tune(pe_batch* b, int64_t* chunk);
 PE_API void pe_batch_destroy(pe_batch* b);
+
+/* =================================================================== learned surrogate
+ * A multilayer perceptron that predicts the least-squares slope of the coarse variables
+ * (Section 3.3, Eq. (leastsquares)) from the coarse state at the start of a burst, so that
+ * a gated macro step (pe_step_surrogate) can replace most of the resolved burst. Linear
+ * layers W_l [d_{l+1}][d_l] with bias, GELU (erf form, GELU(z) = z Phi(z)) after every
+ * layer but the last. Inputs and targets are z-scored per component (pe_mlp_fit_norm).
+ * Arithmetic: BF16 weights and activations on the tensor cores with FP32 accumulation,
+ * FP32 bias, activation, loss and Adam state (master weights FP32, mirrored to BF16 after
+ * every update). Training: mean squared error of the normalised outputs, Adam with bias
+ * correction. All dims must be multiples of 64 (64..4096); training batches a multiple of
+ * 32. Like the context API, the network lives in a caller-owned device arena (no
+ * allocation) and runs on the stream given at creation. */
+#define PE_MLP_MAX_LAYERS 8
+enum pe_mlp_buffer {
+    PE_MLP_PARAMS = 0,  /* f32[nparams]: W_1, b_1, W_2, b_2, ... (flat) */
+    PE_MLP_PARAMS_BF16, /* bf16 mirror of the parameters */
+    PE_MLP_GRADS,       /* f32[nparams] gradients of the last pe_mlp_grad / training step */
+    PE_MLP_ADAM_M,      /* f32[nparams] first moments */
+    PE_MLP_ADAM_V,      /* f32[nparams] second moments */
+    PE_MLP_NORM,        /* f32[4][dmax] mu_in, sd_in, mu_out, sd_out; statistics scratch; step, loss */
+    PE_MLP_WORK,        /* batch workspace (activations, gradients) for max_batch rows */
+    PE_MLP_NBUF
+};
+typedef struct pe_mlp_layout {
+    size_t total_bytes;
+    size_t offset[PE_MLP_NBUF];
+    size_t bytes[PE_MLP_NBUF];
+    int64_t nparams;
+} pe_mlp_layout;
+typedef struct pe_mlp pe_mlp;
+/* dims[0..nlayers]: widths (input, hidden..., output); max_batch: largest batch. */
+PE_API int pe_mlp_layout_for(int32_t nlayers, const int32_t* dims, int32_t max_batch, pe_mlp_layout* out);
+PE_API int pe_mlp_create(int32_t nlayers, const int32_t* dims, int32_t max_batch, void* arena, size_t arena_bytes,
+                         void* stream, pe_mlp** out);
+PE_API void pe_mlp_destroy(pe_mlp* net);
+/* Weights W = (2u - 1) a from the splitmix64 sequence of seed (u = (s_i >> 40) 2^-24, i the
+ * flat parameter index), a = sqrt(6 / d_in) (hidden) or sqrt(3 / d_in) (last layer);
+ * biases, Adam moments and the step counter 0; identity normalisation. Synchronises. */
+PE_API int pe_mlp_init(pe_mlp* net, uint64_t seed);
+/* z-score statistics of the training set X [npairs][d_0], Y [npairs][d_L] (FP32, device):
+ * population mean and deviation per component, deviations floored at 1e-6 of their
+ * largest; with period P > 0 the statistics are pooled over each block of P consecutive
+ * components (for data that is augmented by circular shifts within such blocks). */
+PE_API int pe_mlp_fit_norm(pe_mlp* net, const float* X, const float* Y, int64_t npairs, int32_t period);
+/* Inference: y = net(x) for B rows (1 <= B <= max_batch): x raw [B][d_0] (FP32, or FP64 if
+ * x_is_f64), normalised inside; y de-normalised [B][d_L] (FP32 or FP64). Device pointers. */
+PE_API int pe_mlp_forward(pe_mlp* net, const void* x, int32_t x_is_f64, int32_t B, void* y, int32_t y_is_f64);
+/* Gradients of the MSE loss over the batch rows[0..B) of (X, Y) (rows NULL: rows 0..B-1)
+ * into PE_MLP_GRADS; loss (device f32, may be NULL) gets the loss. No update. */
+PE_API int pe_mlp_grad(pe_mlp* net, const float* X, const float* Y, int64_t npairs, const int32_t* rows, int32_t B,
+                       float* loss);
+/* One Adam update from PE_MLP_GRADS (step counter on the device, advanced by one). */
+PE_API int pe_mlp_adam(pe_mlp* net, double lr, double beta1, double beta2, double eps);
+/* nsteps training steps: each draws B rows of (X, Y) and, with shift_period P > 0, one
+ * circular shift per row inside every block of P components (the same for input and
+ * target), from the splitmix64 sequence of (seed, step); gradients; Adam (0.9, 0.999, 1e-8).
+ * The step is captured once as a CUDA graph and replayed (eagerly on the legacy default
+ * stream). loss (device f32, may be NULL) gets the last step's loss. */
+PE_API int pe_mlp_train(pe_mlp* net, const float* X, const float* Y, int64_t npairs, int32_t B, int32_t shift_period,
+                        uint64_t seed, int32_t nsteps, float lr, float* loss);
+/* Loads the FP32 parameter vector params[nparams] (device; layout of PE_MLP_PARAMS) and
+ * rewrites the BF16 mirror. */
+PE_API int pe_mlp_set_params(pe_mlp* net, const float* params);
+/* Parameter count and device addresses of the step counter, parameters and gradients. */
+PE_API int pe_mlp_info(const pe_mlp* net, int64_t* nparams, int64_t* steps_device_ptr, void** params, void** grads);
+
+/* Gated surrogate macro step (the a-posteriori check of the learned slope). From the coarse
+ * state c at the start of the step: s_mlp = net(c); lift (unless fresh); a probe burst of
+ * K_probe fine steps with co-moving samples 0..K_probe; probe slope s_p and its standard
+ * error sigma_i (from the residuals of the line fit; K_probe >= 2). The prediction is
+ * accepted when ||s_mlp - s_p|| <= max(tol ||s_p||, noise_sigmas ||sigma||): then
+ * c <- c_{K_probe} + (Delta t - K_probe delta t) s_mlp. Otherwise the burst continues to K
+ * steps and the step ends as pe_step does (the probe is the burst's first K_probe steps, so
+ * nothing is recomputed). The network must map 2 n_coarse inputs to 2 n_coarse outputs;
+ * it runs on the context's stream. Synchronises once (the decision). */
+typedef struct pe_gate_cfg {
+    int32_t K_probe;     /* probe burst length, 2 <= K_probe < K */
+    double tol;          /* relative tolerance, e.g. 1e-2 */
+    double noise_sigmas; /* multiple of the probe slope's standard error, e.g. 3 */
+} pe_gate_cfg;
+typedef struct pe_gate_stats {
+    int32_t accepted;   /* 1 if the surrogate slope was used */
+    int32_t fine_steps; /* fine steps run in this macro step */
+    double err;         /* ||s_mlp - s_p|| */
+    double floor;       /* max(tol ||s_p||, noise_sigmas ||sigma||) */
+    double norm;        /* ||s_p|| */
+    double sigma;       /* ||sigma|| */
+} pe_gate_stats;
+PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* net, const pe_gate_cfg* gate, pe_gate_stats* out);
+/* The gate of pe_step_surrogate on its own: probe samples[(K_probe+1)][ncoef] at t_p = p dt,
+ * slope s_p_i = sum_p (t_p - tbar)(c_p,i - cbar_i) / sum_p (t_p - tbar)^2, standard error
+ * sigma_i^2 = sum_p r_p,i^2 / (K_probe - 1) / sum_p (t_p - tbar)^2 (r the fit residuals);
+ * decision as above; on acceptance coarse <- c_{K_probe} + (dT - K_probe dt) s_mlp and
+ * slope <- s_mlp (both [ncoef], untouched otherwise). result: one pe_gate_result in device
+ * memory. One block, fixed summation order. */
+typedef struct pe_gate_result {
+    double err, floor, norm, sigma;
+    int32_t accepted, pad;
+} pe_gate_result;
+PE_API int pe_gate(const double* samples, int32_t K_probe, int32_t ncoef, double dt, double dT, const double* s_mlp,
+                   double tol, double noise_sigmas, double* coarse, double* slope, pe_gate_result* result,
+                   void* stream);
+/* FP32 copy of the coarse state (what = 0) or of the last slope (what = 1) into out[2 n_coarse]
+ * (device), e.g. one row of a surrogate training set. */
+PE_API int pe_export_f32(pe_ctx* ctx, int32_t what, float* out);
 
 /* Number of kernels this library has launched in the process so far. */
 PE_API int64_t pe_launch_count(void);

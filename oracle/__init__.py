@@ -75,6 +75,8 @@ def _load():
                                              i32, i32, i32, dbl, i32, i32, P, P]),
                 "orc_pic_steps": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32,
                                                  i32, i32, dbl, i32, i32, P]),
+                "orc_moments": (None, [i64, P, P, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, i32, P, P]),
+                "orc_rel_l2": (dbl, [i64, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -318,3 +320,34 @@ def lift(coarse, cfg: dict, seed):
     mf = refine(coarse[1], ncell, wav)
     nf, uf = lift_profile(nf, mf)
     return quiet_start(cfg["N"], ncell, nf, uf, cfg["v_th"], seed)
+
+
+MOMENT_KEYS = ("charge", "momentum", "kinetic", "field_energy", "electron_energy", "total_energy",
+               "max_speed", "cfl")
+
+
+def moments(st: State, E, phi, ncell, dx, dt, qm, kick, s_w, mode=0):
+    """Conserved quantities and CFL number of a state (orc_moments); dict incl. charge_fx."""
+    E, phi = _f64(E), _f64(phi)
+    q = np.zeros(1, np.int64)
+    out = np.zeros(8)
+    _load().orc_moments(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), _p(E), _p(phi), ncell, dx, dt, qm,
+                        kick, s_w, mode, _p(q), _p(out))
+    d = dict(zip(MOMENT_KEYS, out.tolist()))
+    d["charge_fx"] = int(q[0])
+    return d
+
+
+def rel_l2(a, b):
+    """Section 4.1.1 error measure sqrt(sum (a-b)^2 / sum (a^2 + b^2))."""
+    a, b = _f64(a).ravel(), _f64(b).ravel()
+    assert a.shape == b.shape
+    return float(_load().orc_rel_l2(a.size, _p(a), _p(b)))
+
+
+def field_of(st: State, ncell, dx, s_w, phi, mode=0, tol=1e-12, maxit=50):
+    """Deposit + Newton + E of a state (the field step of a PIC step); phi updated in place."""
+    rho = deposit_fx(st.cell, st.theta, st.w, ncell, s_w)
+    dens = rho.astype(np.float64) * 2.0 ** -(s_w + 24)
+    phi[:] = newton_pb(dens, dx, phi0=phi, mode=mode, tol=tol, maxit=maxit)[0]
+    return efield(phi, dx)

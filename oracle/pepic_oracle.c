@@ -444,3 +444,55 @@ int orc_pic_steps(int64_t n, int32_t* cell, double* theta, double* v, const doub
     free(E);
     return fails;
 }
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Conserved quantities of the ion-particle / Boltzmann-electron system. Velocities are
+ * taken at integer time, Vbar = v + (kick - 1/2) qm dt E(X) (kick 1/2: v already at integer
+ * time). Each particle carries charge w dx (n_j = sum_p w_p S_j(X_p) with unit mean).
+ * The electron free energy follows from -phi'' + exp(phi) = n: with ion continuity the sum
+ * int n u^2/2 + int [E^2/2 + phi e^phi - e^phi + 1] dx is constant in time (for the
+ * linearised response 1 + phi the last bracket becomes E^2/2 + phi^2/2). */
+void orc_moments(int64_t n, const int32_t* cell, const double* theta, const double* v, const double* w,
+                 const double* E, const double* phi, int32_t ncell, double dx, double dt, double qm,
+                 double kick, int32_t s_w, int32_t mode, int64_t* charge_fx, double* out)
+{
+    double mom = 0.0, kin = 0.0, vmax = 0.0, wsum = 0.0;
+    int64_t q = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double vb = v[i] + (kick - 0.5) * qm * dt * orc_gather(E, ncell, cell[i], theta[i]);
+        mom += w[i] * vb;
+        kin += 0.5 * w[i] * vb * vb;
+        wsum += w[i];
+        if (fabs(vb) > vmax) vmax = fabs(vb);
+        q += (int64_t)llrint(ldexp(w[i], s_w)) * ((int64_t)1 << 24);
+    }
+    double fe = 0.0, ee = 0.0;
+    for (int32_t j = 0; j < ncell; ++j) {
+        fe += 0.5 * E[j] * E[j];
+        if (mode == 0)
+            ee += phi[j] * exp(phi[j]) - exp(phi[j]) + 1.0;
+        else
+            ee += 0.5 * phi[j] * phi[j];
+    }
+    *charge_fx = q;
+    out[0] = wsum * dx;          /* charge */
+    out[1] = mom * dx;           /* momentum */
+    out[2] = kin * dx;           /* ion kinetic energy */
+    out[3] = fe * dx;            /* field energy */
+    out[4] = ee * dx;            /* electron free energy */
+    out[5] = out[2] + out[3] + out[4];
+    out[6] = vmax;               /* max |Vbar| */
+    out[7] = vmax * dt / dx;     /* particle CFL number */
+}
+
+/* Relative L2 distance of Section 4.1.1: sqrt( sum (a-b)^2 / sum (a^2 + b^2) ). */
+double orc_rel_l2(int64_t n, const double* a, const double* b)
+{
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        num += (a[i] - b[i]) * (a[i] - b[i]);
+        den += a[i] * a[i] + b[i] * b[i];
+    }
+    return den > 0.0 ? sqrt(num / den) : 0.0;
+}

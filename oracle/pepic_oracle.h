@@ -134,6 +134,19 @@ int orc_pic_steps(int64_t n, int32_t* cell, double* theta, double* v, const doub
                   int32_t mode, int32_t s_w, double tol, int32_t maxit,
                   int32_t vel_at_integer, double* phi);
 
+/* Diagnostics (Section 4: conservation checks; particle CFL number). Integer-time
+ * velocities Vbar = v + (kick - 1/2) qm dt E(X). charge_fx = sum_p rn(w 2^s_w) 2^24 (the
+ * sum of the fixed-point deposit). out[8] = {charge sum w dx, momentum sum w Vbar dx,
+ * kinetic sum w Vbar^2 dx / 2, field sum E^2 dx / 2, electron free energy
+ * sum (phi e^phi - e^phi + 1) dx (mode 0) or sum phi^2 dx / 2 (mode 1), total,
+ * max |Vbar|, max |Vbar| dt / dx}. */
+void orc_moments(int64_t n, const int32_t* cell, const double* theta, const double* v, const double* w,
+                 const double* E, const double* phi, int32_t ncell, double dx, double dt, double qm,
+                 double kick, int32_t s_w, int32_t mode, int64_t* charge_fx, double* out);
+
+/* Section 4.1.1 error measure: sqrt(sum (a-b)^2 / sum (a^2 + b^2)); 0 if both vanish. */
+double orc_rel_l2(int64_t n, const double* a, const double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,8 +5,9 @@ sm_103a; this package only marshals arguments to its C ABI (``include/pepic.h``)
 Calls raise if the library is missing: there is no CPU path.
 """
 from . import inputs
-from ._binding import (BUF, Batch, Config, Context, PepicError, coarsen, deposit, field, layout, load, ls_project,
-                       make_config, make_sample_args, push, quiet_start, refine, sample, sort)
+from ._binding import (BUF, MLP, Batch, Config, Context, PepicError, coarsen, compute_moments, deposit, field, layout, load,
+                       ls_project, make_config, make_sample_args, push, quiet_start, refine, rel_l2, sample, sort)
 
-__all__ = ["BUF", "Batch", "Config", "Context", "PepicError", "coarsen", "deposit", "field", "inputs", "layout", "load",
-           "ls_project", "make_config", "make_sample_args", "push", "quiet_start", "refine", "sample", "sort"]
+__all__ = ["BUF", "MLP", "Batch", "Config", "Context", "PepicError", "coarsen", "compute_moments", "deposit", "field", "inputs",
+           "layout", "load", "ls_project", "make_config", "make_sample_args", "push", "quiet_start", "refine", "rel_l2",
+           "sample", "sort"]

@@ -19,9 +19,12 @@ PE_OK, PE_EINVAL, PE_ECUDA, PE_ENOCONV, PE_EOVERFLOW, PE_ERANGE, PE_ESTATE = ran
 PE_WAVELET = {"haar": 0, "d4": 1}
 PE_POISSON = {"boltzmann": 0, "linearized": 1}
 PE_PROFILE_SINE = 0
-PE_NBUF = 14
+PE_NBUF = 16
 BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
-           coarse=9, slope=10, profile=11, sort=12, status=13)
+           coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15)
+PE_MLP_NBUF = 7
+MLP_BUF = dict(params=0, params_bf16=1, grads=2, adam_m=3, adam_v=4, norm=5, work=6)
+PE_MOMENTS_SCRATCH_BYTES = 49152
 
 _lock = threading.Lock()
 _lib = None
@@ -55,6 +58,32 @@ class Diag(ctypes.Structure):
     _fields_ = [("macro_steps", ctypes.c_int64), ("fine_steps", ctypes.c_int64), ("time", ctypes.c_double),
                 ("particle_bank", ctypes.c_int32), ("v_at_integer", ctypes.c_int32), ("s_w", ctypes.c_int32),
                 ("s_p", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_uint32)]
+
+
+class Moments(ctypes.Structure):
+    _fields_ = [("charge_fx", ctypes.c_int64), ("invalid", ctypes.c_int64)] + [
+        (k, ctypes.c_double) for k in ("charge_fixed_point", "charge", "momentum", "kinetic", "field_energy",
+                                       "electron_energy", "total_energy", "max_speed", "cfl")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MLPLayout(ctypes.Structure):
+    _fields_ = [("total_bytes", ctypes.c_size_t), ("offset", ctypes.c_size_t * PE_MLP_NBUF),
+                ("bytes", ctypes.c_size_t * PE_MLP_NBUF), ("nparams", ctypes.c_int64)]
+
+
+class GateCfg(ctypes.Structure):
+    _fields_ = [("K_probe", ctypes.c_int32), ("tol", ctypes.c_double), ("noise_sigmas", ctypes.c_double)]
+
+
+class GateStats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int32), ("fine_steps", ctypes.c_int32), ("err", ctypes.c_double),
+                ("floor", ctypes.c_double), ("norm", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # exported symbol -> (restype, argtypes); the test-suite checks this against include/pepic.h
@@ -91,6 +120,24 @@ SIGNATURES = {
     "pe_profile": (ctypes.c_int, [P, i32]),
     "pe_profile_read": (ctypes.c_int, [P, P, P, P, P]),
     "pe_launch_count": (i64, []),
+    "pe_compute_moments": (ctypes.c_int, [P, P, P, P, i64, P, P, P, i32, f64, f64, f32, f32, i32, i32, P, P, P, P]),
+    "pe_rel_l2": (ctypes.c_int, [P, P, i64, P, P]),
+    "pe_state_moments": (ctypes.c_int, [P, ctypes.POINTER(Moments), i32]),
+    "pe_get_slope": (ctypes.c_int, [P, P, i32]),
+    "pe_export_f32": (ctypes.c_int, [P, i32, P]),
+    "pe_step_surrogate": (ctypes.c_int, [P, P, ctypes.POINTER(GateCfg), ctypes.POINTER(GateStats)]),
+    "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
+    "pe_mlp_layout_for": (ctypes.c_int, [i32, P, i32, ctypes.POINTER(MLPLayout)]),
+    "pe_mlp_create": (ctypes.c_int, [i32, P, i32, P, sz, P, ctypes.POINTER(P)]),
+    "pe_mlp_destroy": (None, [P]),
+    "pe_mlp_init": (ctypes.c_int, [P, u64]),
+    "pe_mlp_fit_norm": (ctypes.c_int, [P, P, P, i64, i32]),
+    "pe_mlp_forward": (ctypes.c_int, [P, P, i32, i32, P, i32]),
+    "pe_mlp_grad": (ctypes.c_int, [P, P, P, i64, P, i32, P]),
+    "pe_mlp_adam": (ctypes.c_int, [P, f64, f64, f64, f64]),
+    "pe_mlp_train": (ctypes.c_int, [P, P, P, i64, i32, i32, u64, i32, f32, P]),
+    "pe_mlp_set_params": (ctypes.c_int, [P, P]),
+    "pe_mlp_info": (ctypes.c_int, [P, P, P, P, P]),
     "pe_batch_scratch_bytes": (ctypes.c_int, [P, i32, ctypes.POINTER(sz)]),
     "pe_batch_create": (ctypes.c_int, [P, i32, P, sz, P, ctypes.POINTER(P)]),
     "pe_batch_step": (ctypes.c_int, [P]),
@@ -251,6 +298,30 @@ def sort_noalloc(cell, theta, v, w, ncell, status=None, stream=None):
     return oc, ot, ov, ow
 
 
+def compute_moments(cell, theta, v, w, Ef, ncell, dx, dt, qm_dt, kick, s_w, phi=None, E=None, mode="boltzmann",
+                    status=None, stream=None) -> dict:
+    """Conserved quantities and Courant number of a particle state (pe_compute_moments)."""
+    dev = cell.device
+    scratch = torch.empty(PE_MOMENTS_SCRATCH_BYTES // 8, dtype=torch.float64, device=dev)
+    out = torch.empty(ctypes.sizeof(Moments) // 8, dtype=torch.float64, device=dev)
+    status = _status(status, dev)
+    check(load().pe_compute_moments(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), _ptr(phi),
+                                    _ptr(E), ncell, float(dx), float(dt), float(qm_dt), float(kick), int(s_w),
+                                    PE_POISSON[mode], _ptr(scratch), _ptr(out), _ptr(status), _stream(stream)),
+          "pe_compute_moments")
+    m = Moments.from_buffer_copy(out.cpu().numpy().tobytes())
+    return m.as_dict()
+
+
+def rel_l2(a, b, stream=None) -> float:
+    """Section 4.1.1 error measure of two device FP64 vectors (pe_rel_l2)."""
+    a, b = a.contiguous(), b.contiguous()
+    assert a.dtype == torch.float64 and b.dtype == torch.float64 and a.numel() == b.numel()
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    check(load().pe_rel_l2(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream(stream)), "pe_rel_l2")
+    return float(out.item())
+
+
 # ------------------------------------------------------------------ context
 
 
@@ -342,6 +413,29 @@ class Context:
     def sync_status(self):
         return load().pe_sync_status(self._h)
 
+    def get_slope(self):
+        out = torch.empty((2, self.cfg.n_coarse), dtype=torch.float64, device=self.device)
+        self._call("pe_get_slope", _ptr(out), 1)
+        return out
+
+    def export_f32(self, what, out):
+        """FP32 copy of the coarse state (what=0) or last slope (what=1) into out[2 n_coarse] (device)."""
+        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.cfg.n_coarse
+        self._call("pe_export_f32", int(what), _ptr(out))
+
+    def step_surrogate(self, net, K_probe=5, tol=1e-2, noise_sigmas=3.0) -> dict:
+        """Gated surrogate macro step (pe_step_surrogate); returns the gate statistics."""
+        g = GateCfg(int(K_probe), float(tol), float(noise_sigmas))
+        st = GateStats()
+        self._call("pe_step_surrogate", net._h, ctypes.byref(g), ctypes.byref(st))
+        return st.as_dict()
+
+    def moments(self) -> dict:
+        """Charge, momentum, energies and Courant number of the current particles (pe_state_moments)."""
+        m = Moments()
+        check(load().pe_state_moments(self._h, ctypes.byref(m), 0), "pe_state_moments")
+        return m.as_dict()
+
     def diagnostics(self) -> Diag:
         d = Diag()
         check(load().pe_diagnostics(self._h, ctypes.byref(d)), "pe_diagnostics")
@@ -409,3 +503,112 @@ class Batch:
         if h is not None and h.value and _lib is not None:
             _lib.pe_batch_destroy(h)
             self._h = None
+
+
+# ------------------------------------------------------------------ learned surrogate
+
+
+def gate(samples, dt, dT, s_mlp, coarse, slope, tol=1e-2, noise_sigmas=3.0, stream=None) -> dict:
+    """pe_gate on device tensors: samples [(Ks+1)][n], s_mlp [n]; coarse, slope [n] updated on
+    acceptance. Returns the decision and statistics."""
+    Ks, n = samples.shape[0] - 1, samples.shape[1]
+    res = torch.zeros(5, dtype=torch.float64, device=samples.device)
+    check(load().pe_gate(_ptr(samples), Ks, n, float(dt), float(dT), _ptr(s_mlp), float(tol), float(noise_sigmas),
+                         _ptr(coarse), _ptr(slope), _ptr(res), _stream(stream)), "pe_gate")
+    r = res.cpu().numpy()
+    return dict(err=float(r[0]), floor=float(r[1]), norm=float(r[2]), sigma=float(r[3]),
+                accepted=int(r[4:5].view("int32")[0]))
+
+
+class MLP:
+    """The surrogate network (pe_mlp) in a caller-owned device arena (torch)."""
+
+    def __init__(self, dims, max_batch=256, device="cuda", stream=None):
+        self.dims = [int(d) for d in dims]
+        self.L = len(self.dims) - 1
+        self.max_batch = int(max_batch)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._dims_c = (ctypes.c_int32 * (self.L + 1))(*self.dims)
+        self.lay = MLPLayout()
+        check(load().pe_mlp_layout_for(self.L, self._dims_c, self.max_batch, ctypes.byref(self.lay)),
+              "pe_mlp_layout_for")
+        self.nparams = int(self.lay.nparams)
+        self.arena = torch.empty(self.lay.total_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena.data_ptr()
+        self._pad = (-base) % 256
+        self._h = ctypes.c_void_p()
+        check(load().pe_mlp_create(self.L, self._dims_c, self.max_batch, ctypes.c_void_p(base + self._pad),
+                                   self.lay.total_bytes, _stream(self.stream), ctypes.byref(self._h)),
+              "pe_mlp_create")
+        self.loss_dev = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pe_mlp_destroy(h)
+            self._h = None
+
+    def _view(self, buf, dtype, count):
+        off = self._pad + self.lay.offset[MLP_BUF[buf]]
+        esz = torch.tensor([], dtype=dtype).element_size()
+        return self.arena[off:off + count * esz].view(dtype)
+
+    def params(self):
+        return self._view("params", torch.float32, self.nparams)
+
+    def params_bf16(self):
+        return self._view("params_bf16", torch.bfloat16, self.nparams)
+
+    def grads(self):
+        return self._view("grads", torch.float32, self.nparams)
+
+    def adam_state(self):
+        return self._view("adam_m", torch.float32, self.nparams), self._view("adam_v", torch.float32, self.nparams)
+
+    def norm(self):
+        """[4][dmax] FP32: mu_in, sd_in, mu_out, sd_out."""
+        dmax = max(self.dims)
+        return self._view("norm", torch.float32, 4 * dmax).view(4, dmax)
+
+    def init(self, seed):
+        torch.cuda.synchronize(self.device)
+        check(load().pe_mlp_init(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF), "pe_mlp_init")
+
+    def set_params(self, flat):
+        src = flat.to(self.device).contiguous()
+        assert src.dtype == torch.float32 and src.numel() == self.nparams
+        check(load().pe_mlp_set_params(self._h, _ptr(src)), "pe_mlp_set_params")
+        self.stream.synchronize()
+
+    def fit_norm(self, X, Y, period=0):
+        assert X.dtype == torch.float32 and Y.dtype == torch.float32 and X.shape[0] == Y.shape[0]
+        check(load().pe_mlp_fit_norm(self._h, _ptr(X), _ptr(Y), X.shape[0], int(period)), "pe_mlp_fit_norm")
+        self.stream.synchronize()
+
+    def forward(self, x):
+        """x [B][d0] FP32 or FP64 on the device -> y [B][dL] of the same dtype (de-normalised)."""
+        x = x.contiguous()
+        is64 = x.dtype == torch.float64
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=x.dtype, device=self.device)
+        check(load().pe_mlp_forward(self._h, _ptr(x), int(is64), x.shape[0], _ptr(y), int(is64)), "pe_mlp_forward")
+        self.stream.synchronize()
+        return y
+
+    def grad(self, X, Y, rows=None, B=None) -> float:
+        B = int(B if B is not None else (rows.numel() if rows is not None else X.shape[0]))
+        check(load().pe_mlp_grad(self._h, _ptr(X), _ptr(Y), X.shape[0], _ptr(rows), B, _ptr(self.loss_dev)),
+              "pe_mlp_grad")
+        self.stream.synchronize()
+        return float(self.loss_dev.item())
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(load().pe_mlp_adam(self._h, float(lr), float(beta1), float(beta2), float(eps)), "pe_mlp_adam")
+        self.stream.synchronize()
+
+    def train(self, X, Y, B, nsteps, lr, seed=0, shift_period=0) -> float:
+        check(load().pe_mlp_train(self._h, _ptr(X), _ptr(Y), X.shape[0], int(B), int(shift_period),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(nsteps), float(lr), _ptr(self.loss_dev)),
+              "pe_mlp_train")
+        self.stream.synchronize()
+        return float(self.loss_dev.item())

@@ -154,6 +154,8 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_PROFILE] = 4 * 2 * nc;
     out->bytes[PE_BUF_SORT] = 4 * (2 * nc + 64);
     out->bytes[PE_BUF_STATUS] = 64;
+    out->bytes[PE_BUF_DIAG] = PE_MOMENTS_SCRATCH_BYTES + 256;
+    out->bytes[PE_BUF_SURROGATE] = align256(8 * 2 * ncoef) + 256;
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -389,40 +391,52 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     return pe_measure(x, x->coarse, 1);
 }
 
-extern "C" PE_API int pe_burst(pe_ctx* ctx)
+// Fine steps p_begin .. p_end-1 of a burst, each a fused push + co-moving sample of row p
+// followed by a field solve; then, with final_sample, the sample-only row p_end. A burst
+// that starts (p_begin == 0) first solves the field of the current particles and keeps it
+// as the frame field E_n (Appendix B). A later range continues the same burst.
+int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
 {
-    if (!ctx) return PE_EINVAL;
-    pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
+    if (p_begin < 0 || p_end < p_begin || p_end > c.K) return PE_EINVAL;
     const int b = x->bank;
-    if (!x->rho_valid) PE_TRY(deposit_current(x));
-    PE_TRY(field_solve(x));
-    if (cudaMemcpyAsync(x->E0f, x->Ef, sizeof(float) * c.ncell, cudaMemcpyDeviceToDevice, x->stream) != cudaSuccess)
-        return PE_ECUDA;
+    if (p_begin == 0) {
+        if (!x->rho_valid) PE_TRY(deposit_current(x));
+        PE_TRY(field_solve(x));
+        if (cudaMemcpyAsync(x->E0f, x->Ef, sizeof(float) * c.ncell, cudaMemcpyDeviceToDevice, x->stream) != cudaSuccess)
+            return PE_ECUDA;
+    }
     float kick = x->v_at_integer ? 0.5f : 1.0f;
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
-    for (int p = 0; p <= c.K; ++p) {
+    for (int p = p_begin; p < p_end; ++p) {
         const double tau = c.comoving ? c.dT - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
-        if (p == c.K) {
-            PE_TRY(timed(x, 0, [&] {
-                return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick,
-                                 &a, x->status, x->stream);
-            }));
-            break;
-        }
         PE_TRY(timed(x, 0, [&] {
             return pe_push(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                            kick, x->s_w, x->rho, &a, x->status, x->stream);
         }));
         PE_TRY(field_solve(x));
         kick = 1.0f;
+        x->v_at_integer = 0;
+        x->rho_valid = 1;
+        x->fine_steps += 1;
     }
-    x->v_at_integer = 0;
-    x->rho_valid = 1;
+    if (final_sample) {
+        const double tau = c.comoving ? c.dT - p_end * c.dt : 0.0;
+        pe_sample_args a = sample_args(x, tau, sample_row(x, p_end));
+        PE_TRY(timed(x, 0, [&] {
+            return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick, &a,
+                             x->status, x->stream);
+        }));
+    }
     x->fresh = 0;
-    x->fine_steps += c.K;
     return PE_OK;
+}
+
+extern "C" PE_API int pe_burst(pe_ctx* ctx)
+{
+    if (!ctx) return PE_EINVAL;
+    return pe_ctx_burst_range(ctx, 0, ctx->cfg.K, 1);
 }
 
 extern "C" PE_API int pe_restrict(pe_ctx* ctx)
@@ -492,6 +506,17 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
     return PE_OK;
 }
 
+extern "C" PE_API int pe_get_slope(pe_ctx* ctx, double* out, int32_t out_on_device)
+{
+    if (!ctx || !out) return PE_EINVAL;
+    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    if (cudaMemcpyAsync(out, ctx->slope, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (!out_on_device && cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    return PE_OK;
+}
+
 extern "C" PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device)
 {
     if (!ctx || !out) return PE_EINVAL;
@@ -527,6 +552,26 @@ extern "C" PE_API int pe_sync_status(pe_ctx* ctx)
     if (st & PE_FLAG_RANGE) return PE_ERANGE;
     if (st & PE_FLAG_OVERFLOW) return PE_EOVERFLOW;
     if (st & PE_FLAG_NOCONV) return PE_ENOCONV;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out_on_device)
+{
+    if (!ctx || !out) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    if (!x->rho_valid) PE_TRY(deposit_current(x));
+    PE_TRY(field_solve(x));
+    char* scratch = x->arena + x->lay.offset[PE_BUF_DIAG];
+    pe_moments* res = (pe_moments*)(scratch + PE_MOMENTS_SCRATCH_BYTES);
+    const int b = x->bank;
+    const float kick = x->v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(pe_compute_moments(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, x->phi, x->E, c.ncell, x->dx,
+                      c.dt, (float)(c.qm * c.dt), kick, x->s_w, c.poisson, scratch, res, x->status, x->stream));
+    if (cudaMemcpyAsync(out, res, sizeof(pe_moments), out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (!out_on_device && cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
     return PE_OK;
 }
 

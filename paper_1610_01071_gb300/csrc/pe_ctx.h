@@ -57,3 +57,4 @@ struct pe_ctx {
 // Internal helpers of the context API used by the batch code (pe_capi.cu).
 int pe_ctx_field_solve(pe_ctx* x);
 uint64_t pe_ctx_lift_seed(const pe_ctx* x);
+int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample);

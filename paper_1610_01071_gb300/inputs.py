@@ -61,3 +61,26 @@ def random_field(ncell: int, seed: int, amp: float = 0.1):
 def random_density(ncell: int, seed: int, amp: float = 0.3):
     """Positive periodic nodal density around 1 (float64)."""
     return 1.0 + random_field(ncell, seed, amp)
+
+
+def random_mlp_params(dims, seed: int, scale: float = 1.0):
+    """Random FP32 parameter vector of a dense network with widths dims (flat W_1 [d1][d0],
+    b_1, W_2, ...): weights N(0, scale^2 / d_in), biases N(0, 0.1^2)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(len(dims) - 1):
+        parts.append(rng.standard_normal(dims[l + 1] * dims[l]) * (scale / np.sqrt(dims[l])))
+        parts.append(0.1 * rng.standard_normal(dims[l + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def regression_set(n: int, d_in: int, d_out: int, seed: int):
+    """Smooth synthetic regression pairs: X ~ N(0, 1) + offsets, Y = tanh(X A) B + 0.1 X C,
+    FP32, for checking that training reduces a loss."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d_in)) + rng.standard_normal(d_in)
+    A = rng.standard_normal((d_in, 64)) / np.sqrt(d_in)
+    B = rng.standard_normal((64, d_out)) / 8.0
+    C = rng.standard_normal((d_in, d_out)) / np.sqrt(d_in)
+    Y = np.tanh(X @ A) @ B + 0.1 * X @ C + 3.0
+    return X.astype(np.float32), Y.astype(np.float32)

@@ -459,3 +459,86 @@ def test_cold_ion_acoustic_dispersion(mode):
     assert W == pytest.approx(W_leap, rel=3e-3)
     # the continuum answer k/sqrt(1+k^2) differs by more than the tolerance used above
     assert abs(k / np.sqrt(1 + k * k) - W_leap) / W_leap > 3e-3
+
+
+# ----------------------------------------------------------------- diagnostics (Section 4)
+
+
+def test_moments_closed_forms():
+    ncell, L = 32, 16.0
+    dx = L / ncell
+    x = np.arange(ncell) * dx
+    A = 0.7
+    E = A * np.sin(2 * np.pi * x / L)
+    # one particle at rest in the middle of cell 5, weight 0.25, field sampled there
+    st = orc.State([5], [0.5], [0.0], [0.25])
+    s_w = 20
+    zero = np.zeros(ncell)
+    m = orc.moments(st, E, zero, ncell, dx, 0.1, 1.0, 0.5, s_w)
+    # discrete sum of sin^2 over a whole period is ncell / 2
+    assert m["field_energy"] == pytest.approx(A * A * L / 4, rel=1e-14)
+    assert m["electron_energy"] == 0.0
+    assert m["charge"] == pytest.approx(0.25 * dx, rel=1e-15)
+    assert m["charge_fx"] == round(0.25 * 2**s_w) * 2**24
+    assert m["momentum"] == 0.0 and m["kinetic"] == 0.0
+    # kick = 1: the half kick of a half-integer velocity, E(X) = mean of the two nodes
+    st2 = orc.State([5], [0.5], [0.3], [0.25])
+    Ex = 0.5 * (E[5] + E[6])
+    m = orc.moments(st2, E, zero, ncell, dx, 0.1, 2.0, 1.0, s_w)
+    vb = 0.3 + 0.5 * 2.0 * 0.1 * Ex
+    assert m["momentum"] == pytest.approx(0.25 * vb * dx, rel=1e-14)
+    assert m["kinetic"] == pytest.approx(0.5 * 0.25 * vb * vb * dx, rel=1e-14)
+    assert m["cfl"] == pytest.approx(abs(vb) * 0.1 / dx, rel=1e-14)
+    # constant potential c: Boltzmann free energy (c e^c - e^c + 1) L, linearised c^2 L / 2
+    c = 0.4
+    phi = np.full(ncell, c)
+    m0 = orc.moments(st, zero, phi, ncell, dx, 0.1, 1.0, 0.5, s_w, mode=0)
+    m1 = orc.moments(st, zero, phi, ncell, dx, 0.1, 1.0, 0.5, s_w, mode=1)
+    assert m0["electron_energy"] == pytest.approx((c * np.exp(c) - np.exp(c) + 1) * L, rel=1e-13)
+    assert m1["electron_energy"] == pytest.approx(0.5 * c * c * L, rel=1e-13)
+
+
+def test_moments_of_quiet_start_maxwellian():
+    ncell, L, ppc, u0, vth = 32, 16.0, 1024, 0.3, 0.8
+    st = orc.quiet_start(ncell * ppc, ncell, np.ones(ncell), np.full(ncell, u0), vth, 7)
+    m = orc.moments(st, np.zeros(ncell), np.zeros(ncell), ncell, L / ncell, 0.1, 1.0, 0.5, 16)
+    assert m["charge"] == pytest.approx(L, rel=1e-12)
+    assert m["momentum"] == pytest.approx(u0 * L, rel=2e-3)
+    assert m["kinetic"] == pytest.approx(0.5 * L * (u0 * u0 + vth * vth), rel=2e-3)
+    # the charge in fixed point is the sum of the deposit
+    rho = orc.deposit_fx(st.cell, st.theta, st.w, ncell, 16)
+    assert m["charge_fx"] == int(rho.sum())
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_moments_energy_conserved_by_resolved_pic(mode):
+    """Ion kinetic + field + electron free energy stays constant while field and kinetic
+    energy exchange a much larger amount (Boltzmann and linearised electrons)."""
+    ncell, L, ppc, dt = 64, 32.0, 128, 0.1
+    dx = L / ncell
+    n, u = orc.sine_profile(ncell, L, 0.3)
+    st = orc.quiet_start(ncell * ppc, ncell, n, u, 0.1, 3)
+    s_w = orc.fx_shift(8.0 / ppc)
+    phi = np.zeros(ncell)
+    E = orc.field_of(st, ncell, dx, s_w, phi, mode=mode)
+    hist = [orc.moments(st, E, phi, ncell, dx, dt, 1.0, 0.5, s_w, mode)]
+    vint = True
+    for _ in range(6):
+        phi = orc.pic_steps(st, ncell, dx, dt, 1.0, 20, s_w, phi, mode=mode, vel_at_integer=vint)[0]
+        vint = False
+        E = orc.field_of(st, ncell, dx, s_w, phi, mode=mode)
+        hist.append(orc.moments(st, E, phi, ncell, dx, dt, 1.0, 1.0, s_w, mode))
+    H = np.array([h["total_energy"] for h in hist])
+    pot = np.array([h["field_energy"] + h["electron_energy"] for h in hist])
+    kin = np.array([h["kinetic"] for h in hist])
+    assert np.ptp(pot) > 0.05 and np.ptp(kin) > 0.05
+    assert np.abs(H - H[0]).max() < 0.05 * np.ptp(pot)
+
+
+def test_rel_l2_closed_forms():
+    a = np.array([1.0, -2.0, 3.0])
+    assert orc.rel_l2(a, a) == 0.0
+    assert orc.rel_l2(a, np.zeros(3)) == pytest.approx(1.0, rel=1e-15)
+    assert orc.rel_l2(a, -a) == pytest.approx(np.sqrt(2.0), rel=1e-15)
+    assert orc.rel_l2([1.0, 0.0], [0.0, 1.0]) == pytest.approx(1.0, rel=1e-15)
+    assert orc.rel_l2([3.0], [1.0]) == pytest.approx(np.sqrt(4.0 / 10.0), rel=1e-15)
