@@ -270,7 +270,8 @@ def run_gpu(args):
         t_e2e = time.perf_counter() - t0
         barrier()
         # ---------------- time to solution and accuracy against a resolved plain-PIC run
-        acc = run_accuracy(dev, cfg, pb) if not args.no_accuracy else None
+        acc, want, checks = run_accuracy(dev, cfg, pb) if not args.no_accuracy else (None, None, None)
+        sur = run_surrogate(dev, cfg, pb, want, checks) if (acc is not None and not args.no_surrogate) else None
         # ---------------- ensemble of 64 realisations of log-uniform sizes (pe_batch)
         ens = run_ensemble(dev, max(args.steps // 2, 2), 3, rank) if not args.no_ensemble else None
     clocks = sampler.stop()
@@ -316,6 +317,8 @@ def run_gpu(args):
     }
     if acc is not None:
         line["time_to_solution"] = acc
+    if sur is not None:
+        line["surrogate"] = sur
     if ens is not None:
         t_ens = max_over_ranks(ens["seconds"])
         line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10",
@@ -446,9 +449,106 @@ def run_accuracy(dev, cfg, pb):
     for m in checks:
         a, b = got[m].cpu().numpy(), want[m].cpu().numpy()
         eps[str(round(m * cfg["dT"]))] = float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
-    return {"T_end": steps * cfg["dT"], "projective_s": t_proj, "plain_pic_s": t_plain,
-            "speedup": t_plain / t_proj, "eps_coarse_density_at_T": eps,
-            "status": [ef.sync_status(), ref.sync_status()]}
+    out = {"T_end": steps * cfg["dT"], "projective_s": t_proj, "plain_pic_s": t_plain,
+           "speedup": t_plain / t_proj, "eps_coarse_density_at_T": eps,
+           "status": [ef.sync_status(), ref.sync_status()]}
+    return out, want, checks
+
+
+def _eps(a, b):
+    import numpy as np
+
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
+
+
+def run_surrogate(dev, cfg, pb, want, checks):
+    """The learned coarse-derivative surrogate on the ion-wave workload: training pairs
+    (c at the start of a macro step, that step's least-squares slope) from projective runs
+    at amplitudes 0.05..0.6 (2^22 ions each, augmented by circular shifts of the coarse
+    coefficients), training on the GPU, then the gated surrogate run (probe burst of 5
+    steps) against the projective run with bursts of K and of 5 steps, each timed to the
+    end time and compared with the resolved plain-PIC states `want`."""
+    import numpy as np
+    import torch
+
+    ncell, nc, K = cfg["ncell"], cfg["n_coarse"], cfg["K"]
+    n = 2 * nc
+    amps = np.linspace(0.05, 0.6, 12)
+    steps = cfg["macro_steps"]
+    X, Y = [], []
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for ai, a in enumerate(amps):
+        c = pb.make_config(ncell, nc, K, ncell * 1024, cfg["L"], cfg["dt"], cfg["dT"], qm=cfg["qm"], v_th=cfg["v_th"],
+                           seed=500 + ai, newton_tol=1e-10)
+        ctx = pb.Context(c, device=dev)
+        ctx.load_initial(float(a))
+        for _ in range(steps):
+            x = torch.empty(n, dtype=torch.float32, device=dev)
+            ctx.export_f32(0, x)
+            ctx.step()
+            y = torch.empty(n, dtype=torch.float32, device=dev)
+            ctx.export_f32(1, y)
+            X.append(x)
+            Y.append(y)
+        del ctx
+    X, Y = torch.stack(X).contiguous(), torch.stack(Y).contiguous()
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    dims = [n, 512, 512, 512, n]
+    stream = torch.cuda.Stream(dev)
+    net = pb.MLP(dims, max_batch=256, device=dev, stream=stream)
+    net.init(1)
+    net.fit_norm(X, Y, nc)
+    B, nsteps = 256, 6000
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    loss = net.train(X, Y, B, 4000, 1e-3, seed=1, shift_period=nc)
+    loss = net.train(X, Y, B, nsteps - 4000, 2e-4, seed=2, shift_period=nc)
+    ev1.record(stream)
+    stream.synchronize()
+    t_train = ev0.elapsed_time(ev1) / 1e3
+    mm = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    flops = nsteps * 2.0 * B * (2 * mm + (mm - dims[0] * dims[1]))  # forward, weight and data gradients
+    tflops = flops / t_train / 1e12
+
+    def run(kind, Kb, tol=None):
+        c = pb.make_config(ncell, nc, K if kind == "surrogate" else Kb, cfg["N"], cfg["L"], cfg["dt"], cfg["dT"], qm=cfg["qm"], v_th=cfg["v_th"],
+                           seed=11, newton_tol=1e-10)
+        ctx = pb.Context(c, device=dev)
+        ctx.load_initial(cfg["amplitude"])
+        got, fine, acc = {}, 0, 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for m in range(1, steps + 1):
+            if kind == "surrogate":
+                st = ctx.step_surrogate(net, K_probe=Kb, tol=tol, noise_sigmas=3.0)
+                fine += st["fine_steps"]
+                acc += st["accepted"]
+            else:
+                ctx.step()
+                fine += Kb
+            if m in checks:
+                got[m] = ctx.get_coarse()[0].clone()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        eps = {str(round(m * cfg["dT"])): _eps(got[m].cpu().numpy(), want[m].cpu().numpy()) for m in checks}
+        out = {"seconds": t, "fine_steps": fine, "eps_coarse_density_at_T": eps, "status": ctx.sync_status()}
+        if kind == "surrogate":
+            out["accepted"] = acc
+            out["gate_tol"] = tol
+        return out
+
+    return {
+        "network": "MLP %s, GELU, BF16 weights, FP32 accumulation" % "-".join(map(str, dims)),
+        "training_pairs": int(X.shape[0]), "augmented_pairs": int(X.shape[0]) * nc, "data_seconds": t_data,
+        "train_steps": nsteps, "batch": B, "train_seconds": t_train, "final_loss": loss,
+        "train_roofline": {"bound": "tensor", "achieved": tflops, "peak": 1900.0, "unit": "TFLOP/s",
+                           "frac": tflops / 1900.0, "peak_kind": "fallback (bf16 burst)"},
+        "projective_K%d" % K: run("efpi", K),
+        "projective_K5": run("efpi", 5),
+        "surrogate_probe5": run("surrogate", 5, 3e-3),
+    }
 
 
 def run_ensemble(dev, steps, warmup, rank=0):
@@ -494,6 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--kernel", default=None, help="time one kernel alone (profiling mode)")
     args = ap.parse_args()
     if args.kernel:

@@ -460,23 +460,25 @@ PE_API int pe_mlp_info(const pe_mlp* net, int64_t* nparams, int64_t* steps_devic
 
 /* Gated surrogate macro step (the a-posteriori check of the learned slope). From the coarse
  * state c at the start of the step: s_mlp = net(c); lift (unless fresh); a probe burst of
- * K_probe fine steps with co-moving samples 0..K_probe; probe slope s_p and its standard
- * error sigma_i (from the residuals of the line fit; K_probe >= 2). The prediction is
- * accepted when ||s_mlp - s_p|| <= max(tol ||s_p||, noise_sigmas ||sigma||): then
- * c <- c_{K_probe} + (Delta t - K_probe delta t) s_mlp. Otherwise the burst continues to K
- * steps and the step ends as pe_step does (the probe is the burst's first K_probe steps, so
- * nothing is recomputed). The network must map 2 n_coarse inputs to 2 n_coarse outputs;
- * it runs on the context's stream. Synchronises once (the decision). */
+ * K_probe fine steps with co-moving samples c_0..c_Kp; probe slope s_p and its standard
+ * error sigma_i (from the residuals of the line fit; K_probe >= 2). The estimated error of
+ * the step is the relative change the slope difference makes to the projected state,
+ * e = leap ||s_mlp - s_p|| / ||c_Kp|| with leap = Delta t - K_probe delta t; the prediction
+ * is accepted when e <= max(tol, noise_sigmas leap ||sigma|| / ||c_Kp||): then
+ * c <- c_Kp + leap s_mlp. Otherwise the burst continues to K steps and the step ends as
+ * pe_step does (the probe is the burst's first K_probe steps, so nothing is recomputed).
+ * The network must map 2 n_coarse inputs to 2 n_coarse outputs; it runs on the context's
+ * stream. Synchronises once (the decision). */
 typedef struct pe_gate_cfg {
     int32_t K_probe;     /* probe burst length, 2 <= K_probe < K */
-    double tol;          /* relative tolerance, e.g. 1e-2 */
+    double tol;          /* tolerance on the estimated relative state error, e.g. 1e-3 */
     double noise_sigmas; /* multiple of the probe slope's standard error, e.g. 3 */
 } pe_gate_cfg;
 typedef struct pe_gate_stats {
     int32_t accepted;   /* 1 if the surrogate slope was used */
     int32_t fine_steps; /* fine steps run in this macro step */
-    double err;         /* ||s_mlp - s_p|| */
-    double floor;       /* max(tol ||s_p||, noise_sigmas ||sigma||) */
+    double err;         /* estimated relative state error e */
+    double floor;       /* max(tol, noise floor) */
     double norm;        /* ||s_p|| */
     double sigma;       /* ||sigma|| */
 } pe_gate_stats;
@@ -484,9 +486,9 @@ PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* net, const pe_gate_cfg* gate, 
 /* The gate of pe_step_surrogate on its own: probe samples[(K_probe+1)][ncoef] at t_p = p dt,
  * slope s_p_i = sum_p (t_p - tbar)(c_p,i - cbar_i) / sum_p (t_p - tbar)^2, standard error
  * sigma_i^2 = sum_p r_p,i^2 / (K_probe - 1) / sum_p (t_p - tbar)^2 (r the fit residuals);
- * decision as above; on acceptance coarse <- c_{K_probe} + (dT - K_probe dt) s_mlp and
- * slope <- s_mlp (both [ncoef], untouched otherwise). result: one pe_gate_result in device
- * memory. One block, fixed summation order. */
+ * decision as above (result: err = e, floor, norm = ||s_p||, sigma = ||sigma||); on acceptance
+ * coarse <- c_{K_probe} + (dT - K_probe dt) s_mlp and slope <- s_mlp (both [ncoef], untouched
+ * otherwise). result: one pe_gate_result in device memory. One block, fixed summation order. */
 typedef struct pe_gate_result {
     double err, floor, norm, sigma;
     int32_t accepted, pad;

@@ -77,6 +77,13 @@ def _load():
                                                  i32, i32, dbl, i32, i32, P]),
                 "orc_moments": (None, [i64, P, P, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, i32, P, P]),
                 "orc_rel_l2": (dbl, [i64, P, P]),
+                "orc_ps_sample_fx": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, dbl, i32, i32, P]),
+                "orc_cdf_reconstruct": (ctypes.c_int, [i32, P]),
+                "orc_ps_lift_tables": (ctypes.c_int, [i32, i32, P, P, P]),
+                "orc_cdf_inverse": (dbl, [i32, P, dbl, dbl, dbl]),
+                "orc_ps_quiet_start": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
+                "orc_ps_burst": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl, i32,
+                                                i32, i32, dbl, dbl, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -351,3 +358,60 @@ def field_of(st: State, ncell, dx, s_w, phi, mode=0, tol=1e-12, maxit=50):
     dens = rho.astype(np.float64) * 2.0 ** -(s_w + 24)
     phi[:] = newton_pb(dens, dx, phi0=phi, mode=mode, tol=tol, maxit=maxit)[0]
     return efield(phi, dx)
+
+
+# ------------------------------------------------------------------ phase-space coarse variable
+
+
+def ps_sample_fx(st: State, vbar, E0, ncell, dx, tau, qm, bin_shift, vmin, dv, nv, s_w):
+    """Co-moving phase-space sample in fixed point: int64 [(ncell >> b), nv]."""
+    vbar, E0 = _f64(vbar), _f64(E0)
+    F = np.zeros((ncell >> bin_shift, nv), np.int64)
+    _load().orc_ps_sample_fx(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell, float(dx),
+                             float(tau), float(qm), int(bin_shift), float(vmin), float(dv), int(nv), int(s_w), _p(F))
+    return F
+
+
+def cdf_reconstruct(F):
+    """Appendix C reconstruction of a CDF array (copy); returns (F, pathological flag)."""
+    F = _f64(F).copy()
+    bad = _load().orc_cdf_reconstruct(F.shape[0] - 1, _p(F))
+    return F, int(bad)
+
+
+def ps_lift_tables(H):
+    """H [nxc, nv] (FP64 masses) -> (mass [nxc], cdf [nxc, nv+1], pathological flag)."""
+    H = _f64(H)
+    nxc, nv = H.shape
+    mass = np.zeros(nxc)
+    cdf = np.zeros((nxc, nv + 1))
+    bad = _load().orc_ps_lift_tables(nxc, nv, _p(H), _p(mass), _p(cdf))
+    return mass, cdf, int(bad)
+
+
+def cdf_inverse(F, b, vmin, dv):
+    F = _f64(F)
+    return float(_load().orc_cdf_inverse(F.shape[0] - 1, _p(F), float(b), float(vmin), float(dv)))
+
+
+def ps_quiet_start(N, ncell, bin_shift, mass, cdf, vmin, dv, seed):
+    mass, cdf = _f64(mass), _f64(cdf)
+    nv = cdf.shape[1] - 1
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_ps_quiet_start(N, ncell, int(bin_shift), _p(mass), _p(cdf), nv, float(vmin), float(dv),
+                               seed & 0xFFFFFFFFFFFFFFFF, _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def ps_burst(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, bin_shift, vmin, dv, nv, mode=0, tol=1e-11,
+             maxit=50, vel_at_integer=True):
+    """K fine steps in place with phase-space co-moving samples; returns (samples int64
+    [(K+1), nxc, nv], phi, fails)."""
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, ncell >> bin_shift, nv), np.int64)
+    fails = _load().orc_ps_burst(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx), float(dt),
+                                 float(qm), int(K), float(dT), int(mode), int(s_w), float(tol), int(maxit),
+                                 int(vel_at_integer), int(bin_shift), float(vmin), float(dv), int(nv), _p(phi),
+                                 _p(samples))
+    return samples, phi, int(fails)

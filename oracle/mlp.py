@@ -179,11 +179,14 @@ def ls_slope_with_sigma(samples, dt):
     return slope, sigma
 
 
-def gate(s_mlp, s_probe, sigma_probe, tol, nsig):
-    """A-posteriori check of a predicted slope against a short probe burst: accept when
-    ||s_mlp - s_probe|| <= max(tol ||s_probe||, nsig ||sigma_probe||). Returns
-    (accept, err, floor, norm)."""
-    err = float(np.linalg.norm(np.asarray(s_mlp) - np.asarray(s_probe)))
-    norm = float(np.linalg.norm(s_probe))
-    floor = max(tol * norm, nsig * float(np.linalg.norm(sigma_probe)))
-    return err <= floor, err, floor, norm
+def gate(s_mlp, s_probe, sigma_probe, c_last, leap, tol, nsig):
+    """A-posteriori check of a predicted slope against a short probe burst. The estimated
+    error is the relative change the slope difference makes to the projected coarse state,
+    e = leap ||s_mlp - s_probe|| / ||c_last|| (c_last the probe's last sample, leap =
+    Delta t - K_probe delta t); the probe's own noise gives the floor
+    nsig leap ||sigma_probe|| / ||c_last||. Accept when e <= max(tol, floor).
+    Returns (accept, e, max(tol, floor), ||s_probe||)."""
+    cn = float(np.linalg.norm(c_last))
+    err = leap * float(np.linalg.norm(np.asarray(s_mlp) - np.asarray(s_probe))) / cn
+    floor = max(tol, nsig * leap * float(np.linalg.norm(sigma_probe)) / cn)
+    return err <= floor, err, floor, float(np.linalg.norm(s_probe))

@@ -496,3 +496,255 @@ double orc_rel_l2(int64_t n, const double* a, const double* b)
     }
     return den > 0.0 ? sqrt(num / den) : 0.0;
 }
+
+/* ---------------------------------------------------------------- phase-space coarse variable */
+
+void orc_ps_sample_fx(int64_t n, const int32_t* cell, const double* theta, const double* vbar, const double* w,
+                      const double* E0, int32_t ncell, double dx, double tau, double qm, int32_t bin_shift,
+                      double vmin, double dv, int32_t nv, int32_t s_w, int64_t* F)
+{
+    int32_t nxc = ncell >> bin_shift;
+    memset(F, 0, sizeof(int64_t) * (size_t)nxc * (size_t)nv);
+    for (int64_t p = 0; p < n; ++p) {
+        double E0p = orc_gather(E0, ncell, cell[p], theta[p]);
+        int32_t c = cell[p];
+        double th = theta[p];
+        drift(&c, &th, tau * vbar[p] / dx, ncell);   /* X~ = X + tau V         (Eq. explicitflow) */
+        double vt = vbar[p] + qm * tau * E0p;         /* V~ = V + qm tau E_n(X) */
+        double jf = floor((vt - vmin) / dv);          /* nearest-grid-point cell in v */
+        int32_t j = jf < 0.0 ? 0 : (jf >= (double)nv ? nv - 1 : (int32_t)jf);
+        int64_t wq = (int64_t)llrint(ldexp(w[p], s_w));
+        int64_t tq = (int64_t)llrint(th * THETA_ONE);
+        int64_t qr = wq * tq, ql = wq * ((int64_t)THETA_ONE - tq);
+        int32_t b0 = c >> bin_shift, b1 = wrap((int64_t)c + 1, ncell) >> bin_shift;
+        F[(size_t)b0 * nv + j] += ql;
+        F[(size_t)b1 * nv + j] += qr;
+    }
+}
+
+/* Edge reconstruction (Appendix C) of the entries below 0 of F[0..N]: with k0 the largest
+ * index where F < 0, a ramp F[k] = (k - k_-) dF on [k_-, k_+) (zero below k_-) whose slope
+ * keeps sum_{k < k_+} F[k] (the first moment of the histogram); the range grows (k_- down,
+ * then k_+ up with k_- reset to k0 - 1) until 0 <= (k_+ - k_- - 1) dF <= F[k_+]. Returns 1 if
+ * no admissible range exists (the caller then clamps). */
+static int cdf_edge_low(int32_t N, double* F)
+{
+    int32_t k0 = -1;
+    for (int32_t k = N; k >= 0; --k)
+        if (F[k] < 0.0) {
+            k0 = k;
+            break;
+        }
+    if (k0 < 0) return 0;
+    int32_t km = k0 - 1, kp = k0 + 1;
+    for (;;) {
+        if (kp > N || km < 0) return 1;
+        double S = 0.0;
+        for (int32_t k = 0; k < kp; ++k) S += F[k];
+        double L = (double)(kp - km);
+        double dF = 2.0 * S / (L * (L - 1.0));
+        double top = (L - 1.0) * dF;
+        if (top >= 0.0 && top <= F[kp]) {
+            for (int32_t k = 0; k < km; ++k) F[k] = 0.0;
+            for (int32_t k = km; k < kp; ++k) F[k] = (double)(k - km) * dF;
+            return 0;
+        }
+        if (km > 0) {
+            km -= 1;
+        } else {
+            kp += 1;
+            km = k0 - 1;
+        }
+    }
+}
+
+/* Interior reconstruction (Appendix C) from the low indices: at the first descent k0, k1 the
+ * first index after it with F[k1] >= F[k0], k_+ the (first) minimum on (k0, k1], k_- the last
+ * index before k0 with F <= F[k_+]; a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) whose slope keeps
+ * sum_{k_- <= k < k_+} F[k]; k_+ grows until dF >= 0 and the ramp ends at or below F[k_+]. The
+ * admissibility test reads the printed condition with the ramp's base F[k_-] added (the form
+ * that makes the result monotone; the two agree when F[k_-] = 0). If k_+ reaches N without an
+ * admissible ramp, k_- moves one index down and k_+ restarts (the paper leaves this case
+ * open). Repeated until monotone. Returns 1 if no admissible range exists at all (that
+ * descent is then filled by a running max, which keeps only the zeroth moment). */
+static int cdf_interior_fwd(int32_t N, double* F)
+{
+    int bad = 0;
+    int32_t start = 0;
+    for (;;) {
+        int32_t k0 = -1;
+        for (int32_t k = start; k < N; ++k)
+            if (F[k] > F[k + 1]) {
+                k0 = k;
+                break;
+            }
+        if (k0 < 0) return bad;
+        int32_t k1 = k0 + 1;
+        while (k1 < N && F[k1] < F[k0]) ++k1;
+        int32_t kp0 = k0 + 1;
+        for (int32_t k = k0 + 1; k <= k1; ++k)
+            if (F[k] < F[kp0]) kp0 = k;
+        int32_t km = 0;
+        for (int32_t k = k0 - 1; k >= 0; --k)
+            if (F[k] <= F[kp0]) {
+                km = k;
+                break;
+            }
+        int done = 0;
+        for (; km >= 0 && !done; --km) {
+            for (int32_t kp = kp0; kp <= N; ++kp) {
+                double S = 0.0;
+                for (int32_t k = km; k < kp; ++k) S += F[k];
+                double L = (double)(kp - km);
+                double dF = 2.0 / (L - 1.0) * (S / L - F[km]);
+                double end = F[km] + (L - 1.0) * dF;
+                if (dF >= 0.0 && end <= F[kp]) {
+                    for (int32_t k = km + 1; k < kp; ++k) F[k] = F[km] + (double)(k - km) * dF;
+                    done = 1;
+                    break;
+                }
+            }
+            if (done) break;
+        }
+        if (!done) {
+            bad = 1;
+            for (int32_t k = k0 + 1; k <= N; ++k)
+                if (F[k] < F[k - 1]) F[k] = F[k - 1];
+            km = 0;
+        }
+        start = km;
+    }
+}
+
+static void cdf_mirror(int32_t N, const double* F, double* G)
+{
+    for (int32_t k = 0; k <= N; ++k) G[k] = 1.0 - F[N - k];
+}
+
+int orc_cdf_reconstruct(int32_t N, double* F)
+{
+    double* G = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    double* P = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    int bad = 0;
+    F[0] = 0.0;
+    F[N] = 1.0;
+    /* entries below 0, then entries above 1 (the low-edge procedure on the mirrored array) */
+    bad |= cdf_edge_low(N, F);
+    cdf_mirror(N, F, G);
+    bad |= cdf_edge_low(N, G);
+    cdf_mirror(N, G, F);
+    if (bad)
+        for (int32_t k = 0; k <= N; ++k) F[k] = F[k] < 0.0 ? 0.0 : (F[k] > 1.0 ? 1.0 : F[k]);
+    /* F+ from the low indices, F- from the high indices, averaged */
+    memcpy(P, F, sizeof(double) * (size_t)(N + 1));
+    bad |= cdf_interior_fwd(N, P);
+    cdf_mirror(N, F, G);
+    bad |= cdf_interior_fwd(N, G);
+    cdf_mirror(N, G, F);
+    for (int32_t k = 0; k <= N; ++k) F[k] = 0.5 * (P[k] + F[k]);
+    free(G);
+    free(P);
+    return bad;
+}
+
+int orc_ps_lift_tables(int32_t nxc, int32_t nv, const double* H, double* mass, double* cdf)
+{
+    int bad = 0;
+    double tot = 0.0, pos = 0.0;
+    for (int32_t i = 0; i < nxc; ++i) {
+        double s = 0.0;
+        for (int32_t j = 0; j < nv; ++j) s += H[(size_t)i * nv + j];
+        mass[i] = s;
+        tot += s;
+        pos += s > 0.0 ? s : 0.0;
+    }
+    double scale = pos > 0.0 ? tot / pos : 0.0; /* negative masses clamped, total kept */
+    for (int32_t i = 0; i < nxc; ++i) {
+        double* F = cdf + (size_t)i * (nv + 1);
+        double m = mass[i];
+        if (m > 0.0) {
+            double s = 0.0;
+            F[0] = 0.0;
+            for (int32_t j = 0; j < nv; ++j) {
+                s += H[(size_t)i * nv + j];
+                F[j + 1] = s / m;
+            }
+            bad |= orc_cdf_reconstruct(nv, F);
+        } else {
+            for (int32_t j = 0; j <= nv; ++j) F[j] = (double)j / (double)nv;
+        }
+        mass[i] = m > 0.0 ? m * scale : 0.0;
+    }
+    return bad;
+}
+
+double orc_cdf_inverse(int32_t nv, const double* F, double b, double vmin, double dv)
+{
+    int32_t k = 0;
+    while (k < nv - 1 && !(F[k + 1] > b)) ++k;  /* first k with F[k+1] > b */
+    double den = F[k + 1] - F[k];
+    double frac = den > 0.0 ? (b - F[k]) / den : 0.5;
+    return vmin + dv * ((double)k + frac);
+}
+
+void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                        int32_t nv, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                        double* v, double* w)
+{
+    int64_t ppc = N / ncell;
+    uint32_t half = (uint32_t)(2147483648.0 / (double)N);
+    uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
+    int m = 0;
+    while (((int64_t)1 << m) < ppc) ++m;
+    int pow2 = ((int64_t)1 << m) == ppc;
+    double per_node = ldexp(1.0, -bin_shift); /* Haar synthesis: a bin's mass spread evenly over its nodes */
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t i = s;
+        if (pow2 && m > 0) {
+            uint32_t k = (uint32_t)(s & (ppc - 1));
+            uint32_t r = brev32(k) >> (32 - m);
+            i = (s & ~(ppc - 1)) | (int64_t)r;
+        }
+        int32_t c = (int32_t)(i / ppc);
+        double th = (2.0 * (double)(i % ppc) + 1.0) / (2.0 * (double)ppc);
+        int32_t c1 = wrap((int64_t)c + 1, ncell);
+        int32_t b0 = c >> bin_shift, b1 = c1 >> bin_shift;
+        double nX = (1.0 - th) * mass[b0] * per_node + th * mass[b1] * per_node;
+        uint32_t B = brev32((uint32_t)i) + half + shift;
+        double b = ((double)B + 0.5) * 2.3283064365386963e-10;
+        double v0 = orc_cdf_inverse(nv, cdf + (size_t)b0 * (nv + 1), b, vmin, dv);
+        double v1 = orc_cdf_inverse(nv, cdf + (size_t)b1 * (nv + 1), b, vmin, dv);
+        cell[s] = c;
+        theta[s] = th;
+        w[s] = nX / (double)ppc;
+        v[s] = (1.0 - th) * v0 + th * v1;
+    }
+}
+
+int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const double* w, int32_t ncell, double dx,
+                 double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                 int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi,
+                 int64_t* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)n);
+    size_t row = (size_t)(ncell >> bin_shift) * (size_t)nv;
+    int fails = field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell);
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = v[i] + (kick - 0.5) * qm * dt * orc_gather(E, ncell, cell[i], theta[i]);
+        orc_ps_sample_fx(n, cell, theta, vbar, w, E0, ncell, dx, dT - p * dt, qm, bin_shift, vmin, dv, nv, s_w,
+                         samples + (size_t)p * row);
+        if (p == K) break;
+        orc_push(n, cell, theta, v, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}

@@ -147,6 +147,49 @@ void orc_moments(int64_t n, const int32_t* cell, const double* theta, const doub
 /* Section 4.1.1 error measure: sqrt(sum (a-b)^2 / sum (a^2 + b^2)); 0 if both vanish. */
 double orc_rel_l2(int64_t n, const double* a, const double* b);
 
+/* ---- phase-space coarse variable (Section 3.3 "A wavelet-based equation-free scheme",
+ * Appendices B and C), Haar reading: the active variables are the masses H[i][j] of the
+ * phase-space cells (coarse x-bin i of 2^b nodes, velocity cell j of width dv from vmin).
+ * These are the Haar scaling coefficients of the histogram up to one constant factor. */
+
+/* Co-moving phase-space restriction sample in the fixed-point rule: particle at
+ * X~ = X + tau Vbar (CIC nodes c, c+1 with offset theta~), V~ = Vbar + qm tau E_n(X), velocity
+ * cell j = floor((V~ - vmin)/dv) clamped to [0, nv): q_L = w_q (2^24 - theta~_q) to
+ * (c >> b, j), q_R = w_q theta~_q to ((c+1) >> b, j). F[(ncell >> b)][nv] int64, overwritten. */
+void orc_ps_sample_fx(int64_t n, const int32_t* cell, const double* theta, const double* vbar, const double* w,
+                      const double* E0, int32_t ncell, double dx, double tau, double qm, int32_t bin_shift,
+                      double vmin, double dv, int32_t nv, int32_t s_w, int64_t* F);
+
+/* Appendix C, momentum-conserving reconstruction of a cumulative distribution F[0..N]
+ * (F[0] = 0 and F[N] = 1 are imposed): edge reconstruction of entries below 0 and above 1,
+ * then the interior reconstruction from the low indices and from the high indices,
+ * averaged. In place. Returns 1 if a pathological case needed a clamp or running max. */
+int orc_cdf_reconstruct(int32_t N, double* F);
+
+/* Lifting tables of the phase-space histogram H[nxc][nv]: bin masses (negative masses
+ * clamped to 0, the rest rescaled to keep the total) into mass[nxc], and per bin the
+ * reconstructed CDF over velocity cells into cdf[nxc][nv+1] (uniform where the raw mass is
+ * not positive). Returns 1 if any reconstruction was pathological. */
+int orc_ps_lift_tables(int32_t nxc, int32_t nv, const double* H, double* mass, double* cdf);
+
+/* Inverse of a monotone CDF table F[0..nv] at b in (0, 1): with k the first index where
+ * F[k+1] > b, V = vmin + dv (k + (b - F[k]) / (F[k+1] - F[k])). */
+double orc_cdf_inverse(int32_t nv, const double* F, double b, double vmin, double dv);
+
+/* Appendix C particle loading on the phase-space tables: the Hammersley points of
+ * orc_quiet_start (same positions, quantiles b and storage order); nodal density
+ * n_j = mass[j >> b] 2^-b, w = n(X)/ppc (linear between the two nodes of the cell), and
+ * V = (1 - theta) G_{bin(c)}(b) + theta G_{bin(c+1)}(b) with G the CDF inverse of a bin. */
+void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                        int32_t nv, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                        double* v, double* w);
+
+/* orc_burst with phase-space samples: samples[(K+1)][(ncell >> b)][nv] int64. */
+int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const double* w, int32_t ncell, double dx,
+                 double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                 int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi,
+                 int64_t* samples);
+
 #ifdef __cplusplus
 }
 #endif

@@ -872,18 +872,21 @@ using GateResult = pe_gate_result;
 
 // Probe slope s_p and standard error sigma_i of every coefficient (line fit of the samples
 // c_0..c_Ks at t_p = p dt), the gate decision, and on acceptance the leap
-// c <- c_Ks + (dT - Ks dt) s_mlp (slope <- s_mlp). One block, fixed summation order.
+// c <- c_Ks + (dT - Ks dt) s_mlp (slope <- s_mlp). The estimated error is the relative change
+// of the projected state, e = leap ||s_mlp - s_p|| / ||c_Ks||, accepted when
+// e <= max(tol, nsig leap ||sigma|| / ||c_Ks||). One block, fixed summation order.
 __global__ void __launch_bounds__(1024) k_gate(const double* __restrict__ cs, int Ks, int n, double dt, double dT,
                                               const double* __restrict__ s_mlp, double tol, double nsig,
                                               double* __restrict__ coarse, double* __restrict__ slope,
                                               GateResult* __restrict__ res)
 {
-    __shared__ double red[3][32];
+    __shared__ double red[4][32];
     __shared__ int acc;
     const double tbar = 0.5 * Ks * dt;
+    const double leap = dT - Ks * dt;
     double sxx = 0.0;
     for (int p = 0; p <= Ks; ++p) sxx += (p * dt - tbar) * (p * dt - tbar);
-    double e2 = 0.0, n2 = 0.0, v2 = 0.0;
+    double e2 = 0.0, n2 = 0.0, v2 = 0.0, c2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double ybar = 0.0;
         for (int p = 0; p <= Ks; ++p) ybar += cs[(size_t)p * n + i];
@@ -897,42 +900,45 @@ __global__ void __launch_bounds__(1024) k_gate(const double* __restrict__ cs, in
             r2 += r * r;
         }
         const double d = s_mlp[i] - sp;
+        const double cl = cs[(size_t)Ks * n + i];
         e2 += d * d;
         n2 += sp * sp;
         v2 += r2 / (double)(Ks - 1) / sxx;
+        c2 += cl * cl;
     }
     e2 = warp_sum(e2);
     n2 = warp_sum(n2);
     v2 = warp_sum(v2);
+    c2 = warp_sum(c2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][w] = e2;
         red[1][w] = n2;
         red[2][w] = v2;
+        red[3][w] = c2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
             a += red[0][k];
             b += red[1][k];
             c += red[2][k];
+            d += red[3][k];
         }
-        const double norm = sqrt(b), sig = sqrt(c);
-        const double fl = fmax(tol * norm, nsig * sig);
+        const double cn = sqrt(d);
         GateResult r;
-        r.err = sqrt(a);
-        r.floor = fl;
-        r.norm = norm;
-        r.sigma = sig;
-        r.accepted = (sqrt(a) <= fl) ? 1 : 0;
+        r.err = cn > 0.0 ? leap * sqrt(a) / cn : INFINITY;
+        r.floor = fmax(tol, cn > 0.0 ? nsig * leap * sqrt(c) / cn : 0.0);
+        r.norm = sqrt(b);
+        r.sigma = sqrt(c);
+        r.accepted = (r.err <= r.floor) ? 1 : 0;
         r.pad = 0;
         *res = r;
         acc = r.accepted;
     }
     __syncthreads();
     if (acc) {
-        const double leap = dT - Ks * dt;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             coarse[i] = fma(leap, s_mlp[i], cs[(size_t)Ks * n + i]);
             slope[i] = s_mlp[i];

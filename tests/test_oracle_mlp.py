@@ -132,19 +132,14 @@ def test_ls_slope_with_sigma():
 
 def test_gate_rule():
     s = np.array([1.0, 0.0])
-    assert mlp.gate(s, s, np.zeros(2), 1e-2, 3.0)[0]
-    assert not mlp.gate(s + [0.02, 0], s, np.zeros(2), 1e-2, 3.0)[0]
-    # a noisy probe widens the acceptance floor
-    assert mlp.gate(s + [0.02, 0], s, np.array([0.01, 0.0]), 1e-2, 3.0)[0]
-
-
-def test_zscore_stats_per_component_and_pooled():
-    X = np.array([[1.0, 2.0, 10.0, 0.0], [3.0, 6.0, 10.0, 4.0], [5.0, 1.0, 10.0, 8.0]])
-    mu, sd = mlp.zscore_stats(X)
-    assert np.allclose(mu, [3.0, 3.0, 10.0, 4.0])
-    assert np.allclose(sd[[0, 1, 3]], [math.sqrt(8 / 3), math.sqrt(14 / 3), math.sqrt(32 / 3)])
-    assert sd[2] == pytest.approx(1e-6 * math.sqrt(32 / 3))  # floored constant component
-    mu, sd = mlp.zscore_stats(X, period=2)
-    a, b = X[:, :2].ravel(), X[:, 2:].ravel()
-    assert np.allclose(mu, [a.mean()] * 2 + [b.mean()] * 2)
-    assert np.allclose(sd, [a.std()] * 2 + [b.std()] * 2)
+    c = np.array([3.0, 4.0])  # |c| = 5
+    assert mlp.gate(s, s, np.zeros(2), c, 10.0, 1e-2, 3.0)[0]
+    # e = 10 * 0.004 / 5 = 0.008 <= 1e-2; 0.006 -> 0.012 > 1e-2
+    acc, e, fl, nrm = mlp.gate(s + [0.004, 0], s, np.zeros(2), c, 10.0, 1e-2, 3.0)
+    assert acc and e == pytest.approx(0.008) and fl == 1e-2 and nrm == 1.0
+    assert not mlp.gate(s + [0.006, 0], s, np.zeros(2), c, 10.0, 1e-2, 3.0)[0]
+    # a noisy probe widens the acceptance floor: 3 * 10 * 0.001 / 5 = 0.006 -> still 1e-2;
+    # sigma 0.0025 -> 0.015 >= 0.012
+    assert not mlp.gate(s + [0.006, 0], s, np.array([0.001, 0.0]), c, 10.0, 1e-2, 3.0)[0]
+    acc, e, fl, _ = mlp.gate(s + [0.006, 0], s, np.array([0.0025, 0.0]), c, 10.0, 1e-2, 3.0)
+    assert acc and fl == pytest.approx(0.015)
