@@ -361,9 +361,30 @@ def run_kernel(args):
     args_s = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp, bin_shift=bshift)
     args_f = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp, bin_shift=0)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
+    nv = 64
+    nxc = ncell >> bshift
+    samp_ps = torch.zeros((nxc, nv), dtype=torch.int64, device=dev)
+    args_ps = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp_ps, bin_shift=bshift, n_v=nv,
+                                  v_min=-8.0, dv=16.0 / nv)
+    if args.kernel in ("ps_tables", "ps_quiet_start"):
+        pb.sample(cell, theta, v, w, Ef, ncell, cfg["dt"], 0.5, args_ps, status=status)
+        H = pb.ps_coarsen(samp_ps, d.s_w)
+        mass, cdf, table, _ = pb.ps_lift_tables(H)
+        scratch = torch.empty(2 * nxc * (nv + 1), dtype=torch.float64, device=dev)
+        flags = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def once():
-        if args.kernel in ("push_sample", "push_sample_nodal"):
+        if args.kernel == "push_sample_ps":
+            pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, sample=args_ps,
+                    status=status)
+        elif args.kernel == "ps_tables":
+            pb.load().pe_ps_lift_tables(pb._ptr(H), nxc, nv, pb._ptr(mass), pb._ptr(cdf), pb._ptr(table),
+                                        pb._ptr(scratch), pb._ptr(flags), pb._stream())
+        elif args.kernel == "ps_quiet_start":
+            pb.load().pe_ps_quiet_start(pb._ptr(cell), pb._ptr(theta), pb._ptr(v), pb._ptr(w), N, ncell, bshift,
+                                        pb._ptr(mass), pb._ptr(table), nv, -8.0, 16.0 / nv, 7, d.s_w, pb._ptr(rho),
+                                        pb._ptr(status), pb._stream())
+        elif args.kernel in ("push_sample", "push_sample_nodal"):
             pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho,
                     sample=args_s if args.kernel == "push_sample" else args_f, status=status)
         elif args.kernel == "push":
@@ -391,7 +412,8 @@ def run_kernel(args):
     e1.record()
     torch.cuda.synchronize()
     us = 1e3 * e0.elapsed_time(e1) / args.steps
-    bytes_per = {"push_sample": 28, "push_sample_nodal": 28, "push": 28, "deposit": 12, "sample": 16, "quiet_start": 16, "field": 0}
+    bytes_per = {"push_sample": 28, "push_sample_nodal": 28, "push": 28, "deposit": 12, "sample": 16, "quiet_start": 16,
+                 "field": 0, "push_sample_ps": 28, "ps_tables": 0, "ps_quiet_start": 16}
     gbs = bytes_per[args.kernel] * N / (us * 1e-6) / 1e9
     print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us, "algorithmic_GBps": gbs,
                       "status": int(status.item())}), flush=True)

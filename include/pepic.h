@@ -64,6 +64,9 @@ extern "C" {
 #define PE_POISSON_BOLTZMANN 0  /* -Lap phi + exp(phi) = n   (Section 3.3, Eq. poisson2rescaled) */
 #define PE_POISSON_LINEARIZED 1 /* -Lap phi + 1 + phi = n    (its small-amplitude limit) */
 
+#define PE_COARSE_MOMENTS 0     /* density and momentum, wavelet in x (Section 3.2 variables) */
+#define PE_COARSE_PHASE_SPACE 1 /* phase-space cell masses (Section 3.3), Haar in x and v */
+
 #define PE_PROFILE_SINE 0 /* n = 1 + a cos(2 pi x / L), u = a cos(2 pi x / L) (Section 4.1) */
 
 PE_API const char* pe_strerror(int code);
@@ -100,7 +103,12 @@ PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w
  * (CIC, fixed point) at X~. tau = Delta t - p delta t (0 disables the frame).
  * With bin_shift = b > 0 the sample holds, for each bin of 2^b nodes, the exact sum
  * of the nodal fixed-point sample over the bin (the Haar restriction only needs these
- * sums; a particle whose two CIC nodes share a bin then adds its whole w 2^24). */
+ * sums; a particle whose two CIC nodes share a bin then adds its whole w 2^24).
+ * With n_v > 0 the sample is instead the phase-space histogram of Section 3.3 at the same
+ * co-moving targets (Appendix B): each particle adds its fixed-point w, CIC-split in x, to
+ * the coarse x-bins of its two nodes (bins of 2^b nodes; b = 0 for nodes) and to the
+ * velocity cell j = floor((V~ - v_min) / dv) clamped to [0, n_v). Exact and order
+ * independent like the deposit. */
 typedef struct pe_sample_args {
     const float* E0f;  /* E_n, the field stored at burst start, float[ncell] */
     float tau;         /* Delta t - p delta t */
@@ -109,7 +117,11 @@ typedef struct pe_sample_args {
     int32_t s_w;       /* density fixed-point shift (pe_push requires the same s_w) */
     int32_t s_p;       /* momentum fixed-point shift: |w V~| 2^s_p must stay <= 2^22 */
     int32_t bin_shift; /* 0: nodal sample; b > 0: sums over bins of 2^b consecutive nodes */
-    int64_t* sample_fx; /* int64[2][ncell >> bin_shift]: density then momentum; overwritten */
+    int64_t* sample_fx; /* int64[2][ncell >> bin_shift]: density then momentum; overwritten
+                           (phase-space sample: int64[ncell >> bin_shift][n_v]) */
+    int32_t n_v;        /* 0: moment sample; > 0: phase-space sample with n_v velocity cells */
+    float v_min;        /* phase space: lower velocity bound V_min */
+    float inv_dv;       /* phase space: 1 / dv, dv = (V_max - V_min) / n_v */
 } pe_sample_args;
 
 /* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
@@ -240,6 +252,43 @@ PE_API int pe_compute_moments(const int32_t* cell, const float* theta, const flo
  * in device memory; one block, fixed summation order. */
 PE_API int pe_rel_l2(const double* a, const double* b, int64_t n, double* out, void* stream);
 
+/* ---- Phase-space coarse variable (Section 3.3 "A wavelet-based equation-free scheme",
+ * Appendices B and C), Haar reading: the active variables are the masses H[i][j] of the
+ * phase-space cells, coarse x-bin i of 2^b nodes times velocity cell j = [v_min + j dv,
+ * v_min + (j+1) dv) (the Haar scaling coefficients of the histogram, up to one constant).
+ * The co-moving sample is pe_push / pe_sample with pe_sample_args.n_v > 0. */
+
+/* Fixed-point phase-space samples int64[nsamples][ncoef] -> FP64 masses (x 2^-(s_w+24))
+ * into coarse[nsamples][ncoef]. */
+PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, int64_t ncoef, int32_t s_w, double* coarse,
+                         void* stream);
+
+/* Lifting tables of H[nxc][n_v] (FP64, device): mass[nxc] = sum_j H[i][j] with negative
+ * masses clamped to 0 and the rest rescaled to keep the total (the clamp of Section 3.3's
+ * remark on negative values); cdf[nxc][n_v + 1] the normalised CDF of each bin over its
+ * velocity cells after the momentum-conserving reconstruction of Appendix C (edge
+ * reconstruction below 0 and above 1, interior reconstruction from both ends, averaged;
+ * where no admissible ramp exists the entry is clamped / filled by a running max and
+ * flags[0] (device, may be NULL) is set to 1). Bins of non-positive raw mass get a uniform
+ * CDF. FP64 without contraction, so mass and cdf equal a host evaluation of the same steps
+ * bit for bit. table[nxc][2 n_v + 1] (FP32) is the sampling form used by pe_ps_quiet_start:
+ * the CDF row, then the inverse cell slopes 1 / (F[k+1] - F[k]) (0 for an empty cell).
+ * scratch: 2 nxc (n_v + 1) doubles. */
+PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf, float* table,
+                             double* scratch, int32_t* flags, void* stream);
+
+/* Particle loading of Appendix C on the tables: the Hammersley points, quantiles b and
+ * storage order of pe_quiet_start; weight w = n(X)/ppc with the nodal density
+ * n_j = mass[j >> b] 2^-b (linear between the cell's two nodes); velocity
+ * V = (1 - theta) G_{bin(c)}(b) + theta G_{bin(c+1)}(b), G the inverse of a bin's CDF
+ * (G(b) = v_min + dv (k + (b - F[k]) / (F[k+1] - F[k])), k the first index with F[k+1] > b),
+ * evaluated in FP32 on the sampling table of pe_ps_lift_tables. rho_fx (may be NULL) gets the
+ * charge deposit. */
+PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                             int32_t bin_shift, const double* mass, const float* table, int32_t n_v, double v_min,
+                             double dv, uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
+                             void* stream);
+
 /* =================================================================== context
  * One realisation of the projective-integration cycle (Section 3.1, Figure
  * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares
@@ -264,6 +313,9 @@ typedef struct pe_config {
     uint64_t seed;        /* lifting shift seeds: splitmix64(seed + macro step) */
     double w_cap;         /* largest particle weight (fixed-point range); 0 = 8 ncell / N */
     double v_cap;         /* largest |V~| in restriction samples; 0 = 32 */
+    int32_t coarse_kind;  /* PE_COARSE_MOMENTS or PE_COARSE_PHASE_SPACE */
+    int32_t n_v;          /* phase space: velocity cells (2..256) */
+    double v_max;         /* phase space: velocity range [-v_max, v_max) */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;
@@ -277,15 +329,16 @@ enum pe_buffer {
     PE_BUF_E,               /* f64[ncell] field */
     PE_BUF_EF,              /* f32[ncell] field copy for the particle kernels */
     PE_BUF_E0F,             /* f32[ncell] field at burst start */
-    PE_BUF_SAMPLES_FX,      /* int64[K+1][2][ncell] restriction samples */
-    PE_BUF_COARSE_SAMPLES,  /* f64[K+1][2][n_coarse] */
-    PE_BUF_COARSE,          /* f64[2][n_coarse] current coarse state */
-    PE_BUF_SLOPE,           /* f64[2][n_coarse] last least-squares slope */
+    PE_BUF_SAMPLES_FX,      /* int64[K+2][row] restriction samples (row: 2 bins or n_coarse n_v) */
+    PE_BUF_COARSE_SAMPLES,  /* f64[K+2][ncoef] */
+    PE_BUF_COARSE,          /* f64[ncoef] current coarse state: [2][n_coarse] or [n_coarse][n_v] */
+    PE_BUF_SLOPE,           /* f64[ncoef] last least-squares slope */
     PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u) */
     PE_BUF_SORT,            /* int32[2 ncell + 64] sort scratch */
     PE_BUF_STATUS,          /* uint32[4] status word; int32[4] Newton diag after it */
     PE_BUF_DIAG,            /* pe_moments scratch + one pe_moments result */
     PE_BUF_SURROGATE,       /* f64[2][n_coarse] surrogate slope + gate result */
+    PE_BUF_PHASE,           /* phase space: f64 bin masses, CDF tables, reconstruction scratch, flag */
     PE_NBUF
 };
 

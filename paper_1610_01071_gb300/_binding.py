@@ -19,9 +19,10 @@ PE_OK, PE_EINVAL, PE_ECUDA, PE_ENOCONV, PE_EOVERFLOW, PE_ERANGE, PE_ESTATE = ran
 PE_WAVELET = {"haar": 0, "d4": 1}
 PE_POISSON = {"boltzmann": 0, "linearized": 1}
 PE_PROFILE_SINE = 0
-PE_NBUF = 16
+PE_NBUF = 17
 BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
-           coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15)
+           coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16)
+PE_COARSE = {"moments": 0, "phase_space": 1}
 PE_MLP_NBUF = 7
 MLP_BUF = dict(params=0, params_bf16=1, grads=2, adam_m=3, adam_v=4, norm=5, work=6)
 PE_MOMENTS_SCRATCH_BYTES = 49152
@@ -37,7 +38,8 @@ class PepicError(RuntimeError):
 class SampleArgs(ctypes.Structure):
     _fields_ = [("E0f", ctypes.c_void_p), ("tau", ctypes.c_float), ("qm", ctypes.c_float),
                 ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
-                ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p)]
+                ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p), ("n_v", ctypes.c_int32),
+                ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float)]
 
 
 class Config(ctypes.Structure):
@@ -46,7 +48,8 @@ class Config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("dT", ctypes.c_double), ("qm", ctypes.c_double),
                 ("v_th", ctypes.c_double), ("comoving", ctypes.c_int32), ("poisson", ctypes.c_int32),
                 ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int32), ("sort_every", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double),
+                ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double)]
 
 
 class Layout(ctypes.Structure):
@@ -127,6 +130,9 @@ SIGNATURES = {
     "pe_export_f32": (ctypes.c_int, [P, i32, P]),
     "pe_step_surrogate": (ctypes.c_int, [P, P, ctypes.POINTER(GateCfg), ctypes.POINTER(GateStats)]),
     "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
+    "pe_ps_coarsen": (ctypes.c_int, [P, i32, i64, i32, P, P]),
+    "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
+    "pe_ps_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
     "pe_mlp_layout_for": (ctypes.c_int, [i32, P, i32, ctypes.POINTER(MLPLayout)]),
     "pe_mlp_create": (ctypes.c_int, [i32, P, i32, P, sz, P, ctypes.POINTER(P)]),
     "pe_mlp_destroy": (None, [P]),
@@ -212,9 +218,12 @@ def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, statu
     return E, Ef, diag
 
 
-def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0):
+def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0):
+    """Restriction-sample arguments; n_v > 0 selects the phase-space sample (n_v velocity
+    cells of width dv from v_min) instead of the density and momentum moments."""
     return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
-                      int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()))
+                      int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()), int(n_v), float(v_min),
+                      float(1.0 / dv))
 
 
 def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
@@ -322,15 +331,58 @@ def rel_l2(a, b, stream=None) -> float:
     return float(out.item())
 
 
+def ps_coarsen(sample_fx, s_w, stream=None):
+    """Fixed-point phase-space samples (int64 [..., nxc, nv]) -> FP64 masses."""
+    out = torch.empty(sample_fx.shape, dtype=torch.float64, device=sample_fx.device)
+    nrow = sample_fx.shape[0] if sample_fx.dim() == 3 else 1
+    ncoef = sample_fx.numel() // nrow
+    check(load().pe_ps_coarsen(_ptr(sample_fx), nrow, ncoef, int(s_w), _ptr(out), _stream(stream)), "pe_ps_coarsen")
+    return out
+
+
+def ps_lift_tables(H, stream=None):
+    """H [nxc, nv] FP64 (device) -> (mass [nxc], cdf [nxc, nv+1] FP64, sampling table
+    [nxc, 2 nv + 1] FP32, flag)."""
+    H = H.contiguous()
+    nxc, nv = H.shape
+    mass = torch.empty(nxc, dtype=torch.float64, device=H.device)
+    cdf = torch.empty((nxc, nv + 1), dtype=torch.float64, device=H.device)
+    table = torch.empty((nxc, 2 * nv + 1), dtype=torch.float32, device=H.device)
+    scratch = torch.empty(2 * nxc * (nv + 1), dtype=torch.float64, device=H.device)
+    flags = torch.zeros(1, dtype=torch.int32, device=H.device)
+    check(load().pe_ps_lift_tables(_ptr(H), nxc, nv, _ptr(mass), _ptr(cdf), _ptr(table), _ptr(scratch), _ptr(flags),
+                                   _stream(stream)), "pe_ps_lift_tables")
+    return mass, cdf, table, int(flags.item())
+
+
+def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_rho=True, status=None, stream=None):
+    """Phase-space quiet start on the FP64 masses and the FP32 sampling table of ps_lift_tables."""
+    dev = mass.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    status = _status(status, dev)
+    check(load().pe_ps_quiet_start(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, int(bin_shift), _ptr(mass),
+                                   _ptr(table), (table.shape[1] - 1) // 2, float(v_min), float(dv),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(rho), _ptr(status),
+                                   _stream(stream)), "pe_ps_quiet_start")
+    return cell, theta, v, w, rho
+
+
 # ------------------------------------------------------------------ context
 
 
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
-                v_cap=0.0) -> Config:
+                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0) -> Config:
+    """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
+    masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max)."""
     return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
-                  int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap))
+                  int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
+                  PE_COARSE[coarse], int(n_v), float(v_max))
 
 
 def layout(cfg: Config) -> Layout:
@@ -391,8 +443,14 @@ class Context:
         self._call("pe_measure", _ptr(out), 1)
         return out
 
+    def coarse_shape(self):
+        """(2, n_coarse) for the moments, (n_coarse, n_v) for the phase-space cells."""
+        if self.cfg.coarse_kind == PE_COARSE["phase_space"]:
+            return (self.cfg.n_coarse, self.cfg.n_v)
+        return (2, self.cfg.n_coarse)
+
     def get_coarse(self):
-        out = torch.empty((2, self.cfg.n_coarse), dtype=torch.float64, device=self.device)
+        out = torch.empty(self.coarse_shape(), dtype=torch.float64, device=self.device)
         self._call("pe_get_coarse", _ptr(out), 1)
         return out
 
@@ -414,13 +472,14 @@ class Context:
         return load().pe_sync_status(self._h)
 
     def get_slope(self):
-        out = torch.empty((2, self.cfg.n_coarse), dtype=torch.float64, device=self.device)
+        out = torch.empty(self.coarse_shape(), dtype=torch.float64, device=self.device)
         self._call("pe_get_slope", _ptr(out), 1)
         return out
 
     def export_f32(self, what, out):
         """FP32 copy of the coarse state (what=0) or last slope (what=1) into out[2 n_coarse] (device)."""
-        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.cfg.n_coarse
+        assert out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == self.coarse_shape()[0] * self.coarse_shape()[1]
         self._call("pe_export_f32", int(what), _ptr(out))
 
     def step_surrogate(self, net, K_probe=5, tol=1e-2, noise_sigmas=3.0) -> dict:

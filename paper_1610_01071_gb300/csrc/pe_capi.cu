@@ -137,8 +137,13 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.poisson != PE_POISSON_BOLTZMANN && c.poisson != PE_POISSON_LINEARIZED) return PE_EINVAL;
     if (c.newton_maxit < 1 || !(c.newton_tol > 0.0) || c.sort_every < 0) return PE_EINVAL;
     if (c.w_cap < 0.0 || c.v_cap < 0.0) return PE_EINVAL;
+    if (c.coarse_kind != PE_COARSE_MOMENTS && c.coarse_kind != PE_COARSE_PHASE_SPACE) return PE_EINVAL;
+    const bool ps = c.coarse_kind == PE_COARSE_PHASE_SPACE;
+    if (ps && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
+    const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
+    const size_t row_fx = 2 * nc > nps ? 2 * nc : nps, crow = 2 * ncoef > nps ? 2 * ncoef : nps;
     const size_t bank = 4 * align256(4 * N);
     out->bytes[PE_BUF_PARTICLES_A] = bank;
     out->bytes[PE_BUF_PARTICLES_B] = bank;
@@ -147,15 +152,19 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_E] = 8 * nc;
     out->bytes[PE_BUF_EF] = 4 * nc;
     out->bytes[PE_BUF_E0F] = 4 * nc;
-    out->bytes[PE_BUF_SAMPLES_FX] = 8 * 2 * nc * (size_t)(c.K + 2);
-    out->bytes[PE_BUF_COARSE_SAMPLES] = 8 * 2 * ncoef * (size_t)(c.K + 2);
-    out->bytes[PE_BUF_COARSE] = 8 * 2 * ncoef;
-    out->bytes[PE_BUF_SLOPE] = 8 * 2 * ncoef;
+    out->bytes[PE_BUF_SAMPLES_FX] = 8 * row_fx * (size_t)(c.K + 2);
+    out->bytes[PE_BUF_COARSE_SAMPLES] = 8 * crow * (size_t)(c.K + 2);
+    out->bytes[PE_BUF_COARSE] = 8 * crow;
+    out->bytes[PE_BUF_SLOPE] = 8 * crow;
     out->bytes[PE_BUF_PROFILE] = 4 * 2 * nc;
     out->bytes[PE_BUF_SORT] = 4 * (2 * nc + 64);
     out->bytes[PE_BUF_STATUS] = 64;
     out->bytes[PE_BUF_DIAG] = PE_MOMENTS_SCRATCH_BYTES + 256;
     out->bytes[PE_BUF_SURROGATE] = align256(8 * 2 * ncoef) + 256;
+    out->bytes[PE_BUF_PHASE] = ps ? align256(8 * ncoef) + align256(8 * ncoef * (size_t)(c.n_v + 1)) +
+                                        align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
+                                        align256(4 * ncoef * (size_t)(2 * c.n_v + 1)) + 256
+                                  : 256;
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -182,6 +191,13 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->nc = cfg->n_coarse;
     x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
     x->nb = cfg->ncell >> x->bin_shift;
+    x->ps = cfg->coarse_kind == PE_COARSE_PHASE_SPACE;
+    x->nv = x->ps ? cfg->n_v : 0;
+    x->vmin = x->ps ? -cfg->v_max : 0.0;
+    x->dv = x->ps ? 2.0 * cfg->v_max / cfg->n_v : 1.0;
+    x->ncoef = x->ps ? (int64_t)x->nc * x->nv : 2 * (int64_t)x->nc;
+    x->row_fx = 2 * (int64_t)x->nb > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nb : x->ncoef;
+    x->crow = 2 * (int64_t)x->nc > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nc : x->ncoef;
     const double w_cap = cfg->w_cap > 0.0 ? cfg->w_cap : 8.0 * cfg->ncell / (double)cfg->nparticles;
     const double v_cap = cfg->v_cap > 0.0 ? cfg->v_cap : 32.0;
     x->s_w = fx_shift(w_cap);
@@ -207,6 +223,16 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->sort = (int32_t*)(x->arena + lay.offset[PE_BUF_SORT]);
     x->status = (uint32_t*)(x->arena + lay.offset[PE_BUF_STATUS]);
     x->diag = (int32_t*)(x->status + 4);
+    {
+        char* ph = x->arena + lay.offset[PE_BUF_PHASE];
+        const size_t nc_ = (size_t)x->nc, nv1 = (size_t)x->nv + 1;
+        x->ps_mass = (double*)ph;
+        x->ps_cdf = (double*)(ph + align256(8 * nc_));
+        x->ps_scratch = (double*)(ph + align256(8 * nc_) + align256(8 * nc_ * nv1));
+        x->ps_table = (float*)(ph + align256(8 * nc_) + align256(8 * nc_ * nv1) + align256(8 * 2 * nc_ * nv1));
+        x->ps_flags = (int32_t*)((char*)x->ps_table + align256(4 * nc_ * (2 * (size_t)x->nv + 1)));
+        if (!x->ps) x->ps_flags = (int32_t*)ph;
+    }
     if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||
         cudaMemsetAsync(x->status, 0, 64, x->stream) != cudaSuccess) {
         free(x);
@@ -308,11 +334,12 @@ static int deposit_current(pe_ctx* x)
     return PE_OK;
 }
 
-static int64_t* sample_row(pe_ctx* x, int p) { return x->samples + (size_t)p * 2 * x->nb; }
+static int64_t* sample_row(pe_ctx* x, int p) { return x->samples + (size_t)p * (size_t)x->row_fx; }
 
 static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
 {
     pe_sample_args a;
+    memset(&a, 0, sizeof(a));  // n_v = 0: moment sample
     a.bin_shift = x->bin_shift;
     a.E0f = x->E0f;
     a.tau = (float)tau;
@@ -321,6 +348,11 @@ static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
     a.s_w = x->s_w;
     a.s_p = x->s_p;
     a.sample_fx = dst;
+    if (x->ps) {  // Section 3.3 phase-space histogram instead of the moments
+        a.n_v = x->nv;
+        a.v_min = (float)x->vmin;
+        a.inv_dv = (float)(1.0 / x->dv);
+    }
     return a;
 }
 
@@ -353,11 +385,12 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
     int64_t* dst = sample_row(x, c.K + 1);
     pe_sample_args a = sample_args(x, 0.0, dst);
     a.E0f = x->Ef;  // tau = 0: the frame field is not used
+    a.n_v = 0;      // the measurement is always the density and momentum coefficients
     const int b = x->bank;
     const float kick = x->v_at_integer ? 0.5f : 1.0f;
     PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
                      &a, x->status, x->stream));
-    double* cdst = x->csamples + (size_t)(c.K + 1) * 2 * x->nc;
+    double* cdst = x->csamples + (size_t)(c.K + 1) * (size_t)x->crow;
     PE_TRY(pe_coarsen(dst, 1, c.ncell, x->s_w, x->s_p, c.wavelet, x->nc, x->bin_shift, cdst, x->stream));
     const size_t bytes = sizeof(double) * 2 * x->nc;
     if (cudaMemcpyAsync(out, cdst, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -365,6 +398,23 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
         return PE_ECUDA;
     if (!out_on_device && cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
     return PE_OK;
+}
+
+// Phase-space cell masses of the current particles (co-moving sample with tau = 0) into
+// out[ncoef] (device).
+static int measure_phase(pe_ctx* x, double* out)
+{
+    const pe_config& c = x->cfg;
+    if (!x->rho_valid) PE_TRY(deposit_current(x));
+    PE_TRY(field_solve(x));
+    int64_t* dst = sample_row(x, c.K + 1);
+    pe_sample_args a = sample_args(x, 0.0, dst);
+    a.E0f = x->Ef;
+    const int b = x->bank;
+    const float kick = x->v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
+                     &a, x->status, x->stream));
+    return pe_ps_coarsen(dst, 1, x->ncoef, x->s_w, out, x->stream);
 }
 
 extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude)
@@ -388,6 +438,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     x->fine_steps = 0;
     x->time = 0.0;
     PE_TRY(quiet_start_from_profile(x, c.seed));
+    if (x->ps) return measure_phase(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
 }
 
@@ -443,6 +494,7 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
 {
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
+    if (ctx->ps) return pe_ps_coarsen(ctx->samples, c.K + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
     return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
                       ctx->csamples, ctx->stream);
 }
@@ -451,7 +503,7 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
 {
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
-    PE_TRY(pe_ls_project(ctx->csamples, c.K, 2 * ctx->nc, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
+    PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
     ctx->macro_steps += 1;
     ctx->time += c.dT;
     ctx->fresh = 0;
@@ -463,6 +515,21 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
     if (!ctx) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
+    if (x->ps) {
+        // Appendix C: per-bin CDF reconstruction, then quiet start on the tables
+        PE_TRY(pe_ps_lift_tables(x->coarse, x->nc, x->nv, x->ps_mass, x->ps_cdf, x->ps_table, x->ps_scratch, x->ps_flags,
+                                 x->stream));
+        const int b = x->bank;
+        PE_TRY(timed(x, 0, [&] {
+            return pe_ps_quiet_start(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->bin_shift,
+                                     x->ps_mass, x->ps_table, x->nv, x->vmin, x->dv, lift_seed(x), x->s_w, x->rho,
+                                     x->status, x->stream);
+        }));
+        x->rho_valid = 1;
+        x->v_at_integer = 1;
+        x->fresh = 1;
+        return PE_OK;
+    }
     PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
     return quiet_start_from_profile(x, lift_seed(x));
 }
@@ -509,7 +576,7 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
 extern "C" PE_API int pe_get_slope(pe_ctx* ctx, double* out, int32_t out_on_device)
 {
     if (!ctx || !out) return PE_EINVAL;
-    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    const size_t bytes = sizeof(double) * (size_t)ctx->ncoef;
     if (cudaMemcpyAsync(out, ctx->slope, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         ctx->stream) != cudaSuccess)
         return PE_ECUDA;
@@ -520,7 +587,7 @@ extern "C" PE_API int pe_get_slope(pe_ctx* ctx, double* out, int32_t out_on_devi
 extern "C" PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device)
 {
     if (!ctx || !out) return PE_EINVAL;
-    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    const size_t bytes = sizeof(double) * (size_t)ctx->ncoef;
     if (cudaMemcpyAsync(out, ctx->coarse, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         ctx->stream) != cudaSuccess)
         return PE_ECUDA;
@@ -531,7 +598,7 @@ extern "C" PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_dev
 extern "C" PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device)
 {
     if (!ctx || !in) return PE_EINVAL;
-    const size_t bytes = sizeof(double) * 2 * ctx->nc;
+    const size_t bytes = sizeof(double) * (size_t)ctx->ncoef;
     if (cudaMemcpyAsync(ctx->coarse, in, bytes, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         ctx->stream) != cudaSuccess)
         return PE_ECUDA;

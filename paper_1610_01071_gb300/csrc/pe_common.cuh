@@ -96,6 +96,96 @@ struct SmemGrid {
     }
 };
 
+// Block-local phase-space restriction sample: a window of `width` coarse x-bins starting
+// at `base` (mod nxc) times nv velocity cells, each an exact int64 sum kept as the three
+// digit counters of SmemGrid (same bounds). Entries outside the window go to the global
+// histogram g[nxc][nv] with a 64-bit atomic.
+struct PSGrid {
+    uint32_t* d0;
+    uint32_t* d1;
+    int32_t* d2;
+    unsigned long long* g;
+    int base, width, xmask, nv;
+
+    __device__ __forceinline__ uint32_t* bind(uint32_t* s, unsigned long long* global, int b, int w, int nxc, int nvel)
+    {
+        const int n = w * nvel;
+        d0 = s;
+        d1 = s + n;
+        d2 = reinterpret_cast<int32_t*>(s + 2 * n);
+        g = global;
+        base = b;
+        width = w;
+        xmask = nxc - 1;
+        nv = nvel;
+        return s + 3 * n;
+    }
+
+    __device__ __forceinline__ void add(int key, long long val) const
+    {
+        const int xb = key / nv, j = key - xb * nv;
+        const int d = (xb - base) & xmask;
+        if (d < width) {
+            const int idx = d * nv + j;
+            const uint32_t a = (uint32_t)val & 0xFFFFu, b = (uint32_t)(val >> 16) & 0xFFFFu;
+            const int32_t c = (int32_t)(val >> 32);
+            if (a) atomicAdd(&d0[idx], a);
+            if (b) atomicAdd(&d1[idx], b);
+            if (c) atomicAdd(&d2[idx], c);
+        } else {
+            atomicAdd(&g[key], (unsigned long long)val);
+        }
+    }
+
+    __device__ __forceinline__ void zero() const
+    {
+        for (int i = threadIdx.x; i < width * nv; i += blockDim.x) {
+            d0[i] = 0u;
+            d1[i] = 0u;
+            d2[i] = 0;
+        }
+    }
+
+    __device__ __forceinline__ void flush() const
+    {
+        for (int i = threadIdx.x; i < width * nv; i += blockDim.x) {
+            const long long v = (long long)d0[i] + ((long long)d1[i] << 16) + ((long long)d2[i] << 32);
+            if (v) {
+                const int d = i / nv, j = i - d * nv;
+                atomicAdd(&g[(size_t)((base + d) & xmask) * nv + j], (unsigned long long)v);
+            }
+        }
+    }
+};
+
+// Adds (key, val) pairs of the active lanes to a PSGrid, summing runs of equal keys in
+// consecutive lanes first (consecutive particles of a velocity-ordered cell share their
+// phase-space cell): a segmented suffix sum over the run, added once by its first lane.
+// key < 0 marks a lane with nothing to add. When the active lanes are not a prefix of the
+// warp, every lane adds on its own.
+__device__ __forceinline__ void ps_add_warp(const PSGrid& gr, int key, long long val)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int nact = __popc(act);
+    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
+        if (key >= 0) gr.add(key, val);
+        return;
+    }
+    const int prev = __shfl_up_sync(act, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(act, head);
+    const unsigned after = heads & (0xFFFFFFFEu << lane);
+    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
+    long long s = val;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o = __shfl_down_sync(act, s, off);
+        if (lane + off <= run_end) s += o;
+    }
+    if (head && key >= 0) gr.add(key, s);
+}
+
 // Block-local restriction sample summed over bins of 2^b nodes (Haar restriction). A
 // particle whose two CIC nodes fall in one bin adds its whole q 2^24 (q = w_q or m_q,
 // |q| <= 2^23): kept as digits of q in u0 (q mod 2^16) and u1 (q >> 16). A particle

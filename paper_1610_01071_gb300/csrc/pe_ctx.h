@@ -23,6 +23,17 @@ struct pe_ctx {
     int s_w, s_p, nc;
     int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
     int nb;              // sample length per moment: ncell >> bin_shift
+    int ps;              // phase-space coarse variable (PE_COARSE_PHASE_SPACE)
+    int nv;              // velocity cells (phase space)
+    double vmin, dv;     // velocity cells: [vmin + j dv, vmin + (j+1) dv)
+    int64_t ncoef;       // active coarse coefficients: 2 n_coarse or n_coarse n_v
+    int64_t row_fx;      // int64 words per restriction-sample row
+    int64_t crow;        // doubles per coarse-sample row
+    double* ps_mass;     // [n_coarse]
+    double* ps_cdf;      // [n_coarse][n_v + 1]
+    double* ps_scratch;  // [2 n_coarse (n_v + 1)]
+    float* ps_table;     // [n_coarse][2 n_v + 1] FP32 sampling rows
+    int32_t* ps_flags;
     int bank;            // which particle bank is current
     int v_at_integer;    // stored v is at integer time
     int fresh;           // particles were just loaded/lifted (not yet advanced)

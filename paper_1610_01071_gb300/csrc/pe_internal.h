@@ -68,5 +68,6 @@ inline int launch_status(int kernels = 1)
 constexpr int kFullGridMax = 8192;     // largest grid the context API accepts
 constexpr int kRhoWindowNodes = 1024;  // charge deposit: window around the block's cells
 constexpr int kWindowNodes = 4096;     // restriction samples: window (co-moving spread)
+constexpr int kPSWindowBins = 64;      // phase-space samples: window of coarse x-bins
 
 }  // namespace pe

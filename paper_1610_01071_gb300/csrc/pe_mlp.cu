@@ -961,6 +961,7 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
     const int n = 2 * x->nc, Ks = gc->K_probe;
+    if (x->ps) return PE_EINVAL;  // the surrogate maps the density and momentum coefficients
     if (h->dims[0] != n || h->dims[h->L] != n || Ks < 2 || Ks >= c.K || !(gc->tol >= 0.0) || !(gc->noise_sigmas >= 0.0))
         return PE_EINVAL;
     char* buf = x->arena + x->lay.offset[PE_BUF_SURROGATE];
@@ -1016,7 +1017,7 @@ extern "C" PE_API int pe_gate(const double* samples, int32_t K_probe, int32_t nc
 extern "C" PE_API int pe_export_f32(pe_ctx* ctx, int32_t what, float* out)
 {
     if (!ctx || !out || (what != 0 && what != 1)) return PE_EINVAL;
-    const int n = 2 * ctx->nc;
+    const int n = (int)ctx->ncoef;
     k_to_f32<<<(n + 255) / 256, 256, 0, ctx->stream>>>(what ? ctx->slope : ctx->coarse, n, out);
     return launch_status(1);
 }

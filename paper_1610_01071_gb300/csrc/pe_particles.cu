@@ -42,17 +42,32 @@ struct PushParams {
     unsigned long long* samp_base;     // sample row p starts at samp_base + p * row_stride
     int64_t row_stride;
     int64_t max_chunk;                 // largest particle chunk per block (<= 65536; 0 = 65536)
+    // phase-space sample (PS modes): samp_n is the histogram [(ncell >> bin_shift)][nv]
+    int nv, ps_width;
+    float vmin, inv_dv;
 };
 
-enum Mode { kDeposit = 0, kPush = 1, kPushSample = 2, kSample = 3, kPushSampleBinned = 4, kSampleBinned = 5 };
+enum Mode {
+    kDeposit = 0,
+    kPush = 1,
+    kPushSample = 2,
+    kSample = 3,
+    kPushSampleBinned = 4,
+    kSampleBinned = 5,
+    kPushSamplePS = 6,  // push + phase-space sample
+    kSamplePS = 7
+};
 
 template <int MODE>
 struct ModeTraits {
-    static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned);
-    static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned);
+    static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
+                                 MODE == kPushSamplePS);
+    static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
+                                  MODE == kPushSamplePS);
     static constexpr bool sample = (MODE == kPushSample || MODE == kSample || MODE == kPushSampleBinned ||
-                                    MODE == kSampleBinned);
+                                    MODE == kSampleBinned || MODE == kPushSamplePS || MODE == kSamplePS);
     static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
+    static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS);
 };
 
 // Fixed-point value rn(x 2^s); records in *ovf whether it left the range |q| <= 2^23.
@@ -69,7 +84,8 @@ template <int MODE>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
                                         LaneWindow& lw, BinWindow& bw, const SmemGrid& grho,
                                         const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
-                                        const BinGrid& bsm, bool* ovf, int& c_out, float& th_out, float& v_out)
+                                        const BinGrid& bsm, const PSGrid& gps, bool* ovf, int& c_out, float& th_out,
+                                        float& v_out)
 {
     using Tr = ModeTraits<MODE>;
     c_out = c;
@@ -102,8 +118,28 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         }
         const int cs = (c + k) & P.mask, cs1 = (cs + 1) & P.mask;
         const float vt = fmaf(P.qm_tau, E0p, vbar);
-        const int32_t mq = fx_weight(ww * vt, P.pscale, ovf);
-        if (Tr::binned) {
+        if (Tr::ps) {
+            // Section 3.3 restriction: CIC in x (summed over the coarse bin), nearest cell in v
+            const float jf = floorf((vt - P.vmin) * P.inv_dv);
+            const int j = jf < 0.0f ? 0 : (jf >= (float)P.nv ? P.nv - 1 : (int)jf);
+            const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
+            int key0 = b0 * P.nv + j, key1 = -1;
+            long long q0, q1 = 0;
+            if (b0 == b1) {
+                q0 = (long long)wq * (long long)kThetaOne;
+            } else {
+                const FxSplit qn = fx_split(wq, ths);
+                q0 = (long long)qn.left;
+                q1 = (long long)qn.right;
+                key1 = b1 * P.nv + j;
+            }
+            ps_add_warp(gps, key0, q0);
+            ps_add_warp(gps, key1, q1);
+        }
+        const int32_t mq = Tr::ps ? 0 : fx_weight(ww * vt, P.pscale, ovf);
+        if (Tr::ps) {
+            // the phase-space sample above replaces the moment samples
+        } else if (Tr::binned) {
             const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
             if (b0 == b1) {  // both CIC parts in one bin: the whole particle
                 bw.add(b0, wq, mq, bsn, bsm, bsn.nb - 1);
@@ -158,6 +194,8 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 
     SmemGrid grho{}, gsn{}, gsm{};
     BinGrid bsn{}, bsm{};
+    PSGrid gps{};
+    constexpr bool kPS = Tr::ps;
     uint32_t* s = smem;
     if (kRho) s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
     if (kSamp) {
@@ -169,6 +207,11 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         const int nb = P.ncell >> P.bin_shift;
         s = bsn.bind(s, P.samp_n, nb);
         s = bsm.bind(s, P.samp_m, nb);
+    }
+    if (kPS) {
+        const int nxc = P.ncell >> P.bin_shift;
+        s = gps.bind(s, P.samp_n, ((c_first >> P.bin_shift) - P.ps_width / 2) & (nxc - 1), P.ps_width, nxc, P.nv);
+        gps.zero();
     }
     if (kRho) grho.zero();
     if (kSamp) {
@@ -211,20 +254,20 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         }
         int4 co;
         float4 to, vo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.x, to.x, vo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.y, to.y, vo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.z, to.z, vo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.w, to.w, vo.w);
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.x, to.x, vo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.y, to.y, vo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.z, to.z, vo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.w, to.w, vo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
         }
         if (two) {
-            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.x, to.x, vo.x);
-            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.y, to.y, vo.y);
-            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.z, to.z, vo.z);
-            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co.w, to.w, vo.w);
+            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.x, to.x, vo.x);
+            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.y, to.y, vo.y);
+            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.z, to.z, vo.z);
+            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.w, to.w, vo.w);
             if (kWrite) {
                 cell4[g + 32] = co;
                 th4[g + 32] = to;
@@ -236,7 +279,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int co;
         float to, vo;
         const float vi = kNeedV ? P.v[i] : 0.f;
-        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, &ovf, co, to, vo);
+        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co, to, vo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
@@ -256,6 +299,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         bsn.flush();
         bsm.flush();
     }
+    if (kPS) gps.flush();
 }
 
 template <int MODE>
@@ -537,14 +581,19 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     P.rho_width = rho ? (P.ncell <= kRhoWindowNodes ? P.ncell : kRhoWindowNodes) : 0;
     P.samp_width = (samp && !bin) ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
     const int nb = bin ? (P.ncell >> P.bin_shift) : 0;
-    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) + 5 * sizeof(uint32_t) * 2 * nb;
+    const bool ps = ModeTraits<MODE>::ps;
+    const int nxc = P.ncell >> P.bin_shift;
+    P.ps_width = ps ? (nxc <= kPSWindowBins ? nxc : kPSWindowBins) : 0;
+    if (ps) P.samp_width = 0;
+    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) + 5 * sizeof(uint32_t) * 2 * nb +
+                  3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = (const void*)k_particles<MODE>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = grid_for(k, block, smem, P.n, &P.chunk, P.max_chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
-    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * 2 * (size_t)(P.ncell >> P.bin_shift), s) != cudaSuccess)
-        return PE_ECUDA;
+    const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : 2 * (size_t)(P.ncell >> P.bin_shift);
+    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess) return PE_ECUDA;
     if (P.n == 0) return PE_OK;
     k_particles<MODE><<<grid, block, smem, s>>>(P);
     return launch_status();
@@ -561,6 +610,12 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
 {
     if (!s || !s->E0f || !s->sample_fx || !aligned16(s->sample_fx)) return false;
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
+    if (s->n_v < 0 || s->n_v > 1024) return false;
+    if (s->n_v > 0) {
+        const int nxc = ncell >> s->bin_shift;
+        const size_t w = (size_t)(nxc <= kPSWindowBins ? nxc : kPSWindowBins);
+        return s->inv_dv > 0.0f && 3 * sizeof(uint32_t) * w * (size_t)s->n_v <= 160 * 1024;
+    }
     if (s->bin_shift == 0) return true;
     return (5 * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
 }
@@ -693,6 +748,12 @@ extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float
         P.bin_shift = sample->bin_shift;
         P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
         P.samp_m = P.samp_n + (ncell >> P.bin_shift);
+        if (sample->n_v > 0) {
+            P.nv = sample->n_v;
+            P.vmin = sample->v_min;
+            P.inv_dv = sample->inv_dv;
+            return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream);
+        }
         if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream);
         return launch_particles<kPushSample>(P, (cudaStream_t)stream);
     }
@@ -725,6 +786,12 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
     P.bin_shift = sample->bin_shift;
     P.samp_n = reinterpret_cast<unsigned long long*>(sample->sample_fx);
     P.samp_m = P.samp_n + (ncell >> P.bin_shift);
+    if (sample->n_v > 0) {
+        P.nv = sample->n_v;
+        P.vmin = sample->v_min;
+        P.inv_dv = sample->inv_dv;
+        return launch_particles<kSamplePS>(P, (cudaStream_t)stream);
+    }
     if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream);
     return launch_particles<kSample>(P, (cudaStream_t)stream);
 }

@@ -1,0 +1,421 @@
+// Phase-space coarse variable (Section 3.3, "A wavelet-based equation-free scheme", with
+// Appendices B and C), Haar reading: the active variables are the masses H[i][j] of the
+// phase-space cells (coarse x-bin i of 2^b nodes, velocity cell j of width dv from v_min).
+// The co-moving restriction sample itself is a mode of the fused particle pass
+// (pe_push / pe_sample with n_v > 0); this file holds the rest of the cycle:
+//   - pe_ps_coarsen: fixed-point samples -> FP64 masses;
+//   - pe_ps_lift_tables: per bin the mass and the momentum-conserving reconstruction of the
+//     velocity CDF (Appendix C), one thread per bin, in FP64 with every operation rounded
+//     separately (no contraction) so the tables are reproducible bit for bit;
+//   - pe_ps_quiet_start: the Hammersley loading of Appendix C on those tables, with the
+//     charge deposit of the new particles fused.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "pe_common.cuh"
+#include "pe_internal.h"
+#include "pepic.h"
+
+namespace pe {
+namespace {
+
+// Fixed-point weight rn(x 2^s) of the deposit rule; records whether |q| left 2^23.
+__device__ __forceinline__ int32_t fx_weight_q(float x, float scale, bool* ovf)
+{
+    const int32_t q = __float2int_rn(x * scale);
+    *ovf |= (q > (1 << 23)) | (q < -(1 << 23));
+    return q;
+}
+
+// FP64 arithmetic without fused multiply-add, so that the device reproduces a host
+// evaluation of the same expressions in the same order.
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
+
+// Edge reconstruction of the entries below 0 of F[0..N] (Appendix C): with k0 the largest
+// index where F < 0, a ramp (k - k_-) dF on [k_-, k_+) (zero below) whose slope keeps the sum
+// of F below k_+ (the histogram's first moment); the range grows (k_- down, then k_+ up with
+// k_- back at k0 - 1) until 0 <= (k_+ - k_- - 1) dF <= F[k_+]. Returns 1 if none exists.
+__device__ int edge_low(int N, double* F)
+{
+    int k0 = -1;
+    for (int k = N; k >= 0; --k)
+        if (F[k] < 0.0) {
+            k0 = k;
+            break;
+        }
+    if (k0 < 0) return 0;
+    int km = k0 - 1, kp = k0 + 1;
+    for (;;) {
+        if (kp > N || km < 0) return 1;
+        double S = 0.0;
+        for (int k = 0; k < kp; ++k) S = add_(S, F[k]);
+        const double L = (double)(kp - km);
+        const double dF = div_(mul_(2.0, S), mul_(L, sub_(L, 1.0)));
+        const double top = mul_(sub_(L, 1.0), dF);
+        if (top >= 0.0 && top <= F[kp]) {
+            for (int k = 0; k < km; ++k) F[k] = 0.0;
+            for (int k = km; k < kp; ++k) F[k] = mul_((double)(k - km), dF);
+            return 0;
+        }
+        if (km > 0) {
+            km -= 1;
+        } else {
+            kp += 1;
+            km = k0 - 1;
+        }
+    }
+}
+
+// Interior reconstruction from the low indices (Appendix C): at the first descent k0, k1 the
+// first later index with F[k1] >= F[k0], k_+ the first minimum on (k0, k1], k_- the last
+// earlier index with F <= F[k_+]; a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) keeping the sum
+// of F over [k_-, k_+); k_+ grows (then k_- moves down and k_+ restarts) until dF >= 0 and
+// the ramp ends at or below F[k_+]. If no range qualifies, a running max fills the descent
+// and 1 is returned.
+__device__ int interior_fwd(int N, double* F)
+{
+    int bad = 0, start = 0;
+    for (;;) {
+        int k0 = -1;
+        for (int k = start; k < N; ++k)
+            if (F[k] > F[k + 1]) {
+                k0 = k;
+                break;
+            }
+        if (k0 < 0) return bad;
+        int k1 = k0 + 1;
+        while (k1 < N && F[k1] < F[k0]) ++k1;
+        int kp0 = k0 + 1;
+        for (int k = k0 + 1; k <= k1; ++k)
+            if (F[k] < F[kp0]) kp0 = k;
+        int km = 0;
+        for (int k = k0 - 1; k >= 0; --k)
+            if (F[k] <= F[kp0]) {
+                km = k;
+                break;
+            }
+        bool done = false;
+        for (; km >= 0 && !done; --km) {
+            for (int kp = kp0; kp <= N; ++kp) {
+                double S = 0.0;
+                for (int k = km; k < kp; ++k) S = add_(S, F[k]);
+                const double L = (double)(kp - km);
+                const double dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(S, L), F[km]));
+                const double end = add_(F[km], mul_(sub_(L, 1.0), dF));
+                if (dF >= 0.0 && end <= F[kp]) {
+                    for (int k = km + 1; k < kp; ++k) F[k] = add_(F[km], mul_((double)(k - km), dF));
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+        }
+        if (!done) {
+            bad = 1;
+            for (int k = k0 + 1; k <= N; ++k)
+                if (F[k] < F[k - 1]) F[k] = F[k - 1];
+            km = 0;
+        }
+        start = km;
+    }
+}
+
+__device__ __forceinline__ void mirror(int N, const double* F, double* G)
+{
+    for (int k = 0; k <= N; ++k) G[k] = sub_(1.0, F[N - k]);
+}
+
+// Reconstruction of one CDF row F[0..N] in place; G and P are scratch rows of N + 1.
+__device__ int reconstruct(int N, double* F, double* G, double* P)
+{
+    int bad = 0;
+    F[0] = 0.0;
+    F[N] = 1.0;
+    bad |= edge_low(N, F);
+    mirror(N, F, G);
+    bad |= edge_low(N, G);
+    mirror(N, G, F);
+    if (bad)
+        for (int k = 0; k <= N; ++k) F[k] = F[k] < 0.0 ? 0.0 : (F[k] > 1.0 ? 1.0 : F[k]);
+    for (int k = 0; k <= N; ++k) P[k] = F[k];
+    bad |= interior_fwd(N, P);
+    mirror(N, F, G);
+    bad |= interior_fwd(N, G);
+    mirror(N, G, F);
+    for (int k = 0; k <= N; ++k) F[k] = mul_(0.5, add_(P[k], F[k]));
+    return bad;
+}
+
+}  // namespace
+}  // namespace pe
+
+namespace pe {
+namespace {
+
+// Lifting tables, per bin (one thread per bin, 32 bins per block so the bins spread over
+// the SMs): the raw mass, the reconstructed FP64 CDF row (uniform where the raw mass is not
+// positive), and the FP32 sampling row used by the particle loader: F[0..nv] and the inverse
+// cell slopes 1 / (F[k+1] - F[k]) (0 for an empty cell). scratch: 2 (nv + 1) doubles per bin.
+__global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
+                                              double* __restrict__ mass, double* __restrict__ cdf,
+                                              float* __restrict__ table, double* __restrict__ scratch,
+                                              int32_t* __restrict__ flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nxc) return;
+    const double* h = H + (size_t)i * nv;
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s = add_(s, h[j]);
+    mass[i] = s;
+    double* F = cdf + (size_t)i * (nv + 1);
+    if (s > 0.0) {
+        double r = 0.0;
+        F[0] = 0.0;
+        for (int j = 0; j < nv; ++j) {
+            r = add_(r, h[j]);
+            F[j + 1] = div_(r, s);
+        }
+        double* G = scratch + (size_t)i * 2 * (nv + 1);
+        if (reconstruct(nv, F, G, G + nv + 1) && flags) atomicOr(flags, 1);
+    } else {
+        for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
+    }
+    float* T = table + (size_t)i * (2 * nv + 1);
+    for (int k = 0; k <= nv; ++k) T[k] = (float)F[k];
+    for (int k = 0; k < nv; ++k) {
+        const double den = F[k + 1] - F[k];
+        T[nv + 1 + k] = den > 0.0 ? (float)(1.0 / den) : 0.0f;
+    }
+}
+
+// Negative masses clamped to 0, the others rescaled to keep the total (summed by one thread
+// in bin order, as the host evaluation does).
+__global__ void __launch_bounds__(1024) k_ps_mass(int nxc, double* __restrict__ mass)
+{
+    __shared__ double sscale;
+    if (threadIdx.x == 0) {
+        double tot = 0.0, pos = 0.0;
+        for (int i = 0; i < nxc; ++i) {
+            tot = add_(tot, mass[i]);
+            pos = add_(pos, mass[i] > 0.0 ? mass[i] : 0.0);
+        }
+        sscale = pos > 0.0 ? div_(tot, pos) : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nxc; i += blockDim.x) mass[i] = mass[i] > 0.0 ? mul_(mass[i], sscale) : 0.0;
+}
+
+struct PSLoad {
+    int32_t* cell;
+    float* theta;
+    float* v;
+    float* w;
+    int64_t n, chunk;
+    uint32_t ppc;
+    int log2ppc, ncell, mask, bin_shift, nv;
+    float per_node, vmin, dv, inv_ppc, two_ppc;
+    const double* mass;
+    const float* table;
+    uint32_t half, shift;
+    float wscale;
+    unsigned long long* rho;
+    int rho_width;
+    uint32_t* status;
+};
+
+// V = v_min + dv (k + (b - F[k]) / (F[k+1] - F[k])) on a bin's FP32 sampling row, k the first
+// index with F[k+1] > b (binary search; nv - 1 if none).
+__device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int nv, float b, float vmin, float dv)
+{
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(T + mid + 1) > b)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const float f0 = __ldg(T + lo), sl = __ldg(T + nv + 1 + lo);
+    const float frac = sl > 0.0f ? (b - f0) * sl : 0.5f;
+    return fmaf(dv, (float)lo + frac, vmin);
+}
+
+// Appendix C loading of slot i: the Hammersley point and storage order of pe_quiet_start,
+// weight n(X)/ppc from the bin masses (a bin's mass spread evenly over its 2^b nodes, linear
+// between the cell's two nodes), velocity blended between the CDF inverses of the bins of the
+// cell's two nodes. FP32 (the particle precision) on tables built in FP64.
+__device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+{
+    if (P.log2ppc > 0) {
+        const uint32_t k = i & (P.ppc - 1u);
+        i = (i & ~(P.ppc - 1u)) | (__brev(k) >> (32 - P.log2ppc));
+    }
+    const uint32_t j = i % P.ppc;
+    c = (int)(i / P.ppc);
+    th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    const int c1 = (c + 1) & P.mask;
+    const int b0 = c >> P.bin_shift, b1 = c1 >> P.bin_shift;
+    const float n0 = (float)__ldg(P.mass + b0) * P.per_node, n1 = (float)__ldg(P.mass + b1) * P.per_node;
+    ww = fmaf(th, n1 - n0, n0) * P.inv_ppc;
+    const uint32_t B = __brev(i) + P.half + P.shift;
+    const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const int row = 2 * P.nv + 1;
+    const float v0 = cdf_inverse_f(P.table + (size_t)b0 * row, P.nv, b, P.vmin, P.dv);
+    const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
+    vv = fmaf(th, v1 - v0, v0);
+}
+
+__global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
+{
+    extern __shared__ uint32_t smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const bool dep = P.rho != nullptr;
+    const int c_first = (begin < end) ? (int)((uint64_t)begin / P.ppc) : 0;
+    SmemGrid grho{};
+    if (dep) {
+        grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        grho.zero();
+    }
+    __syncthreads();
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    LaneWindow lw;
+    lw.reset(((int)((uint64_t)(g0 << 2) / P.ppc) - 1) & P.mask);
+    bool ovf = false;
+    int4* cell4 = reinterpret_cast<int4*>(P.cell);
+    float4* th4 = reinterpret_cast<float4*>(P.theta);
+    float4* v4 = reinterpret_cast<float4*>(P.v);
+    float4* w4 = reinterpret_cast<float4*>(P.w);
+    for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+        int4 c;
+        float4 t, vv, ww;
+        const uint32_t i0 = (uint32_t)(g << 2);
+        ps_load_one(P, i0, c.x, t.x, vv.x, ww.x);
+        ps_load_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
+        ps_load_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
+        ps_load_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        cell4[g] = c;
+        th4[g] = t;
+        v4[g] = vv;
+        w4[g] = ww;
+        if (dep) {
+            lw.add(c.x, fx_split(fx_weight_q(ww.x, P.wscale, &ovf), t.x), grho);
+            lw.add(c.y, fx_split(fx_weight_q(ww.y, P.wscale, &ovf), t.y), grho);
+            lw.add(c.z, fx_split(fx_weight_q(ww.z, P.wscale, &ovf), t.z), grho);
+            lw.add(c.w, fx_split(fx_weight_q(ww.w, P.wscale, &ovf), t.w), grho);
+        }
+    }
+    for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
+        int c;
+        float t, vv, ww;
+        ps_load_one(P, (uint32_t)i, c, t, vv, ww);
+        P.cell[i] = c;
+        P.theta[i] = t;
+        P.v[i] = vv;
+        P.w[i] = ww;
+        if (dep) lw.add(c, fx_split(fx_weight_q(ww, P.wscale, &ovf), t), grho);
+    }
+    if (dep) lw.flush(grho);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
+    __syncthreads();
+    if (dep) grho.flush();
+}
+
+__global__ void k_ps_scale(const long long* __restrict__ src, int64_t n, double scale, double* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i] * scale;
+}
+
+}  // namespace
+}  // namespace pe
+
+using namespace pe;
+
+extern "C" PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, int64_t ncoef, int32_t s_w,
+                                    double* coarse, void* stream)
+{
+    if (nsamples < 0 || ncoef < 0 || !sample_fx || !coarse || s_w < -60 || s_w > 60) return PE_EINVAL;
+    const int64_t n = (int64_t)nsamples * ncoef;
+    if (n == 0) return PE_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)sm_count());
+    k_ps_scale<<<grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), n,
+                                                       ldexp(1.0, -(s_w + 24)), coarse);
+    return launch_status(1);
+}
+
+extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf,
+                                        float* table, double* scratch, int32_t* flags, void* stream)
+{
+    if (!H || !mass || !cdf || !table || !scratch || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
+    k_ps_cdf<<<(nxc + 31) / 32, 32, 0, s>>>(H, nxc, n_v, mass, cdf, table, scratch, flags);
+    k_ps_mass<<<1, 1024, 0, s>>>(nxc, mass);
+    return launch_status(2);
+}
+
+extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                        int32_t bin_shift, const double* mass, const float* table, int32_t n_v,
+                                        double v_min, double dv, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                                        uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !mass || !table || n_v < 1 || !(dv > 0.0)) return PE_EINVAL;
+    if (bin_shift < 0 || (1 << bin_shift) > ncell) return PE_EINVAL;
+    if (n <= 0 || n % ncell != 0 || n >= (int64_t(1) << 32)) return PE_EINVAL;
+    if (!cell || !theta || !v || !w || !aligned16(cell) || !aligned16(theta) || !aligned16(v) || !aligned16(w))
+        return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PSLoad P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.ppc = (uint32_t)(n / ncell);
+    P.log2ppc = is_pow2(P.ppc) ? ilog2(P.ppc) : -1;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.bin_shift = bin_shift;
+    P.nv = n_v;
+    P.per_node = ldexpf(1.0f, -bin_shift);
+    P.vmin = (float)v_min;
+    P.dv = (float)dv;
+    P.inv_ppc = 1.0f / (float)P.ppc;
+    P.two_ppc = 2.0f * (float)P.ppc;
+    P.mass = mass;
+    P.table = table;
+    P.half = (uint32_t)(2147483648.0 / (double)n);
+    // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the Cranley-Patterson shift
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    P.shift = (uint32_t)(z >> 32);
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
+    P.status = status;
+    const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const void* k = (const void*)k_ps_quiet_start;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    int64_t c = (n + blocks - 1) / blocks;
+    c = (c + 3) & ~int64_t(3);
+    if (c < 4) c = 4;
+    if (c > kMaxChunk) c = kMaxChunk;
+    P.chunk = c;
+    const int grid = (int)((n + c - 1) / c);
+    if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
+    return launch_status(1);
+}

@@ -1,0 +1,156 @@
+"""GPU parity of the phase-space coarse variable (Section 3.3, Appendices B and C) against
+the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the co-moving phase-space sample is bit-exact on dyadic data (every FP32
+operation exact) and within 1e-4 of its total on general data (FP32 targets near a cell
+edge); lifting tables bit-exact (FP64 without contraction on both sides); the phase-space
+quiet start bit-exact after rounding the oracle's FP64 values to FP32.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import paper_1610_01071_gb300 as pe
+from paper_1610_01071_gb300 import _binding as pb
+from paper_1610_01071_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in arrs]
+
+
+def _sample(c, t, v, w, E0, ncell, b, nv, vmin, dv, tau, s_w, push=False):
+    dc, dt_, dv_, dw, dE = dev(c, t, v, w, E0.astype(np.float32))
+    out = torch.zeros(((ncell >> b), nv), dtype=torch.int64, device=DEV)
+    a = pb.make_sample_args(dE, tau, 1.0, 1.0 / 0.5, s_w, s_w - 6, out, bin_shift=b, n_v=nv, v_min=vmin, dv=dv)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    pe.sample(dc, dt_, dv_, dw, dE, ncell, 0.1, 0.5, a, status=st)
+    return out.cpu().numpy(), int(st.item())
+
+
+@pytest.mark.parametrize("ncell,N,b,nv,tau", [(64, 1, 2, 16, 2.5), (64, 4099, 2, 16, 2.5), (512, 1 << 16, 3, 32, 6.0),
+                                              (4096, (1 << 20) + 3, 4, 64, 20.0), (4096, 1 << 18, 4, 64, 180.0)])
+def test_ps_sample_bit_exact_on_dyadic_data(ncell, N, b, nv, tau):
+    rng = np.random.default_rng(N + ncell)
+    c = np.sort(rng.integers(0, ncell, N)).astype(np.int32)
+    t = (rng.integers(0, 1 << 10, N) / 1024.0).astype(np.float32)
+    v = (rng.integers(-6 * 64, 6 * 64, N) / 64.0).astype(np.float32)
+    w = ((1 + rng.integers(0, 64, N)) / 64.0 * ncell / max(N, 1)).astype(np.float32)
+    w = np.ldexp(np.round(np.ldexp(w, 20)), -20).astype(np.float32)
+    E0 = (rng.integers(-128, 128, ncell) / 1024.0)
+    vmin, dv = -8.0, 16.0 / nv
+    s_w = orc.fx_shift(float(w.max()) * 2)
+    got, st = _sample(c, t, v, w, E0, ncell, b, nv, vmin, dv, tau, s_w)
+    want = orc.ps_sample_fx(orc.State(c, t, v, w), v.astype(np.float64), E0, ncell, 0.5, tau, 1.0, b, vmin, dv, nv,
+                            s_w)
+    assert st == 0
+    assert np.array_equal(got, want)
+
+
+def test_ps_sample_general_data():
+    ncell, N, b, nv = 4096, 1 << 20, 4, 64
+    c, t, v, w = inputs.random_particles(N, ncell, seed=21)
+    E0 = inputs.random_field(ncell, 22, 0.05)
+    s_w = orc.fx_shift(3.0 * ncell / N)
+    got, st = _sample(c, t, v, w, E0, ncell, b, nv, -8.0, 0.25, 17.3, s_w)
+    want = orc.ps_sample_fx(orc.State(c, t, v, w), v.astype(np.float64), E0.astype(np.float32).astype(np.float64),
+                            ncell, 0.5, 17.3, 1.0, b, -8.0, 0.25, nv, s_w)
+    assert st == 0
+    # charge is exact whatever the cell decisions (the int64 total itself may exceed 2^63)
+    assert int(got.astype(object).sum()) == int(want.astype(object).sum())
+    g, h = got.astype(np.float64), want.astype(np.float64)
+    assert np.abs(g - h).sum() <= 1e-4 * h.sum()
+
+
+def _noisy_hist(nxc, nv, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nxc) + 0.5) / nxc
+    vc = -8.0 + 16.0 / nv * (np.arange(nv) + 0.5)
+    n = 16.0 * (1 + 0.4 * np.cos(2 * np.pi * x))
+    u = 0.5 * np.sin(2 * np.pi * x)
+    H = n[:, None] * np.exp(-0.5 * (vc[None, :] - u[:, None]) ** 2) * (16.0 / nv) / np.sqrt(2 * np.pi)
+    H += 0.02 * H.max() * rng.standard_normal(H.shape)  # projected data: dips and negative entries
+    H[3] = -np.abs(H[3])                                # one bin of negative mass
+    return H
+
+
+@pytest.mark.parametrize("nxc,nv", [(8, 16), (256, 64), (512, 128)])
+def test_ps_lift_tables_bit_exact(nxc, nv):
+    H = _noisy_hist(nxc, nv, nxc + nv)
+    mass, cdf, table, flag = pb.ps_lift_tables(dev(H)[0])
+    m_o, c_o, f_o = orc.ps_lift_tables(H)
+    assert np.array_equal(mass.cpu().numpy(), m_o)
+    assert np.array_equal(cdf.cpu().numpy(), c_o)
+    assert flag == f_o
+    T = table.cpu().numpy()
+    assert np.array_equal(T[:, :nv + 1], c_o.astype(np.float32))
+    den = np.diff(c_o, axis=1)
+    assert np.allclose(T[:, nv + 1:], np.where(den > 0, 1.0 / np.where(den > 0, den, 1.0), 0.0), rtol=1e-7)
+    assert np.all(np.diff(c_o, axis=1) >= 0)
+
+
+@pytest.mark.parametrize("ncell,ppc,b,nv", [(64, 64, 2, 16), (4096, 256, 4, 64), (512, 1000, 3, 32)])
+def test_ps_quiet_start_matches_oracle(ncell, ppc, b, nv):
+    """Positions exact; weights and velocities within FP32 evaluation of the FP64 oracle
+    (velocities 2e-5 of the velocity range, weights 1e-6 relative)."""
+    nxc = ncell >> b
+    H = np.abs(_noisy_hist(nxc, nv, 7))
+    mass, cdf, _ = orc.ps_lift_tables(H)
+    N = ncell * ppc
+    vmin, dv = -8.0, 16.0 / nv
+    dm, dH = dev(mass, H)
+    _, _, table, _ = pb.ps_lift_tables(dH)
+    s_w = orc.fx_shift(8.0 * (1 << b) * 16 / ppc)
+    cell, theta, v, w, rho = pb.ps_quiet_start(N, ncell, b, dm, table, vmin, dv, 12345, s_w)
+    st = orc.ps_quiet_start(N, ncell, b, mass, cdf, vmin, dv, 12345)
+    assert np.array_equal(cell.cpu().numpy(), st.cell)
+    assert np.array_equal(theta.cpu().numpy(), st.theta.astype(np.float32))
+    assert np.allclose(w.cpu().numpy(), st.w, rtol=1e-6, atol=0)
+    assert np.abs(v.cpu().numpy() - st.v).max() <= 2e-5 * 16.0
+    th, ww = theta.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(rho.cpu().numpy(), orc.deposit_fx(st.cell, th, ww, ncell, s_w))
+
+
+def test_phase_space_macro_steps_conserve_charge():
+    """The context cycle with the phase-space variable: the total mass of the coarse state is
+    kept by the projection (Remark on charge conservation) and by the lifting to rounding."""
+    cfg = pe.make_config(512, 32, 20, 512 * 512, 256.0, 0.1, 20.0, seed=3, coarse="phase_space", n_v=32,
+                         v_max=8.0)
+    ctx = pe.Context(cfg, device=DEV)
+    ctx.load_initial(0.3)
+    c0 = ctx.get_coarse()
+    assert tuple(c0.shape) == (32, 32)
+    total0 = float(c0.sum())
+    assert total0 == pytest.approx(512.0, rel=1e-6)
+    for _ in range(4):
+        ctx.step()
+        assert float(ctx.get_coarse().sum()) == pytest.approx(total0, rel=1e-5)
+    assert ctx.sync_status() == 0
+    m = ctx.moments()
+    assert m["invalid"] == 0 and m["charge"] == pytest.approx(256.0, rel=1e-6)
+
+
+def test_phase_space_burst_matches_oracle():
+    """One phase-space burst from the same initial particles: samples within 2e-3 (L1,
+    relative) of the FP64 oracle's, the difference of FP32 against FP64 trajectories."""
+    ncell, nc, nv, K, ppc = 128, 16, 32, 10, 256
+    N = ncell * ppc
+    cfg = pe.make_config(ncell, nc, K, N, 64.0, 0.1, 10.0, seed=5, coarse="phase_space", n_v=nv, v_max=8.0)
+    ctx = pe.Context(cfg, device=DEV)
+    ctx.load_initial(0.2)
+    cell, theta, v, w = (x.cpu().numpy() for x in ctx.particles(0))
+    st = orc.State(cell, theta, v, w)
+    s_w = ctx.diagnostics().s_w
+    ctx.burst()
+    got = ctx.view("samples_fx", torch.int64, (K + 1) * nc * nv).view(K + 1, nc, nv).cpu().numpy()
+    want, _, fails = orc.ps_burst(st, ncell, 0.5, 0.1, 1.0, K, 10.0, s_w, np.zeros(ncell), 3, -8.0, 0.5, nv,
+                                  tol=1e-10)
+    assert fails == 0 and ctx.sync_status() == 0
+    for p in range(K + 1):
+        assert int(got[p].astype(object).sum()) == int(want[p].astype(object).sum())
+        g, h = got[p].astype(np.float64), want[p].astype(np.float64)
+        assert np.abs(g - h).sum() <= 2e-3 * h.sum()
