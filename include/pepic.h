@@ -271,18 +271,24 @@ PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, int64_t nco
  * where no admissible ramp exists the entry is clamped / filled by a running max and
  * flags[0] (device, may be NULL) is set to 1). Bins of non-positive raw mass get a uniform
  * CDF. FP64 without contraction, so mass and cdf equal a host evaluation of the same steps
- * bit for bit. table[nxc][2 n_v + 1] (FP32) is the sampling form used by pe_ps_quiet_start:
- * the CDF row, then the inverse cell slopes 1 / (F[k+1] - F[k]) (0 for an empty cell).
+ * bit for bit. table[nxc][3 n_v + 1] (FP32) is the sampling form used by pe_ps_quiet_start:
+ * the CDF row, the inverse cell masses 1 / p_k (p_k = F[k+1] - F[k]; 0 for an empty cell),
+ * and the cells' relative density slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to
+ * [-1, 1].
  * scratch: 2 nxc (n_v + 1) doubles. */
 PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf, float* table,
                              double* scratch, int32_t* flags, void* stream);
 
 /* Particle loading of Appendix C on the tables: the Hammersley points, quantiles b and
- * storage order of pe_quiet_start; weight w = n(X)/ppc with the nodal density
- * n_j = mass[j >> b] 2^-b (linear between the cell's two nodes); velocity
- * V = (1 - theta) G_{bin(c)}(b) + theta G_{bin(c+1)}(b), G the inverse of a bin's CDF
- * (G(b) = v_min + dv (k + (b - F[k]) / (F[k+1] - F[k])), k the first index with F[k+1] > b),
- * evaluated in FP32 on the sampling table of pe_ps_lift_tables. rho_fx (may be NULL) gets the
+ * storage order of pe_quiet_start. The lifted f(x, v) is linear in x between neighbouring
+ * bin centres (Section 3.3's linear interpolation): with phi the particle's distance from the
+ * centre of the bin b0 at or left of it, in bin widths, b1 = b0 + 1 (periodic),
+ * w = ((1 - phi) mass[b0] + phi mass[b1]) 2^-b / ppc and V = (1 - phi) G_b0(b) + phi G_b1(b),
+ * G the inverse of a bin's CDF: G(b) = v_min + dv (k + t), k the first index with
+ * F[k+1] > b and t in [0, 1] where t + sigma_k (t^2 - t) = (b - F[k]) / p_k, i.e. the density
+ * inside a velocity cell is linear, 1 + sigma_k (2t - 1), following its neighbours (uniform
+ * cells would add dv^2/12 to the temperature at every lift). FP32 on the sampling table of
+ * pe_ps_lift_tables. rho_fx (may be NULL) gets the
  * charge deposit. */
 PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
                              int32_t bin_shift, const double* mass, const float* table, int32_t n_v, double v_min,

@@ -80,7 +80,8 @@ def _load():
                 "orc_ps_sample_fx": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, dbl, i32, i32, P]),
                 "orc_cdf_reconstruct": (ctypes.c_int, [i32, P]),
                 "orc_ps_lift_tables": (ctypes.c_int, [i32, i32, P, P, P]),
-                "orc_cdf_inverse": (dbl, [i32, P, dbl, dbl, dbl]),
+                "orc_cdf_inverse": (dbl, [i32, P, P, dbl, dbl, dbl]),
+                "orc_cdf_cell_slopes": (None, [i32, P, P]),
                 "orc_ps_quiet_start": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
                 "orc_ps_burst": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl, i32,
                                                 i32, i32, dbl, dbl, i32, P, P]),
@@ -389,9 +390,19 @@ def ps_lift_tables(H):
     return mass, cdf, int(bad)
 
 
-def cdf_inverse(F, b, vmin, dv):
+def cdf_cell_slopes(F):
     F = _f64(F)
-    return float(_load().orc_cdf_inverse(F.shape[0] - 1, _p(F), float(b), float(vmin), float(dv)))
+    sig = np.zeros(F.shape[0] - 1)
+    _load().orc_cdf_cell_slopes(F.shape[0] - 1, _p(F), _p(sig))
+    return sig
+
+
+def cdf_inverse(F, b, vmin, dv, sigma=None):
+    """Inverse CDF; sigma (per-cell density slopes) None: uniform inside each cell."""
+    F = _f64(F)
+    sg = _f64(sigma) if sigma is not None else None
+    return float(_load().orc_cdf_inverse(F.shape[0] - 1, _p(F), _p(sg) if sg is not None else None, float(b),
+                                         float(vmin), float(dv)))
 
 
 def ps_quiet_start(N, ncell, bin_shift, mass, cdf, vmin, dv, seed):

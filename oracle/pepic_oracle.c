@@ -563,10 +563,10 @@ static int cdf_edge_low(int32_t N, double* F)
  * index before k0 with F <= F[k_+]; a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) whose slope keeps
  * sum_{k_- <= k < k_+} F[k]; k_+ grows until dF >= 0 and the ramp ends at or below F[k_+]. The
  * admissibility test reads the printed condition with the ramp's base F[k_-] added (the form
- * that makes the result monotone; the two agree when F[k_-] = 0). If k_+ reaches N without an
- * admissible ramp, k_- moves one index down and k_+ restarts (the paper leaves this case
- * open). Repeated until monotone. Returns 1 if no admissible range exists at all (that
- * descent is then filled by a running max, which keeps only the zeroth moment). */
+ * that makes the result monotone; the two agree when F[k_-] = 0). Repeated until monotone.
+ * A descent with no admissible range (near F = 1 the ramp cannot keep the sum without ending
+ * above 1) is filled by a running max instead, which moves only the few values of the
+ * descent; 1 is returned then. */
 static int cdf_interior_fwd(int32_t N, double* F)
 {
     int bad = 0;
@@ -581,36 +581,32 @@ static int cdf_interior_fwd(int32_t N, double* F)
         if (k0 < 0) return bad;
         int32_t k1 = k0 + 1;
         while (k1 < N && F[k1] < F[k0]) ++k1;
-        int32_t kp0 = k0 + 1;
+        int32_t kp = k0 + 1;
         for (int32_t k = k0 + 1; k <= k1; ++k)
-            if (F[k] < F[kp0]) kp0 = k;
+            if (F[k] < F[kp]) kp = k;
         int32_t km = 0;
         for (int32_t k = k0 - 1; k >= 0; --k)
-            if (F[k] <= F[kp0]) {
+            if (F[k] <= F[kp]) {
                 km = k;
                 break;
             }
         int done = 0;
-        for (; km >= 0 && !done; --km) {
-            for (int32_t kp = kp0; kp <= N; ++kp) {
-                double S = 0.0;
-                for (int32_t k = km; k < kp; ++k) S += F[k];
-                double L = (double)(kp - km);
-                double dF = 2.0 / (L - 1.0) * (S / L - F[km]);
-                double end = F[km] + (L - 1.0) * dF;
-                if (dF >= 0.0 && end <= F[kp]) {
-                    for (int32_t k = km + 1; k < kp; ++k) F[k] = F[km] + (double)(k - km) * dF;
-                    done = 1;
-                    break;
-                }
+        for (; kp <= N; ++kp) {
+            double S = 0.0;
+            for (int32_t k = km; k < kp; ++k) S += F[k];
+            double L = (double)(kp - km);
+            double dF = 2.0 / (L - 1.0) * (S / L - F[km]);
+            double end = F[km] + (L - 1.0) * dF;
+            if (dF >= 0.0 && end <= F[kp]) {
+                for (int32_t k = km + 1; k < kp; ++k) F[k] = F[km] + (double)(k - km) * dF;
+                done = 1;
+                break;
             }
-            if (done) break;
         }
         if (!done) {
             bad = 1;
             for (int32_t k = k0 + 1; k <= N; ++k)
                 if (F[k] < F[k - 1]) F[k] = F[k - 1];
-            km = 0;
         }
         start = km;
     }
@@ -678,13 +674,30 @@ int orc_ps_lift_tables(int32_t nxc, int32_t nv, const double* H, double* mass, d
     return bad;
 }
 
-double orc_cdf_inverse(int32_t nv, const double* F, double b, double vmin, double dv)
+void orc_cdf_cell_slopes(int32_t nv, const double* F, double* sigma)
+{
+    for (int32_t k = 0; k < nv; ++k) {
+        double p = F[k + 1] - F[k];
+        double pl = k > 0 ? F[k] - F[k - 1] : 0.0;
+        double pr = k + 1 < nv ? F[k + 2] - F[k + 1] : 0.0;
+        double s = p > 0.0 ? (pr - pl) / (4.0 * p) : 0.0;
+        sigma[k] = s > 1.0 ? 1.0 : (s < -1.0 ? -1.0 : s);
+    }
+}
+
+double orc_cdf_inverse(int32_t nv, const double* F, const double* sigma, double b, double vmin, double dv)
 {
     int32_t k = 0;
     while (k < nv - 1 && !(F[k + 1] > b)) ++k;  /* first k with F[k+1] > b */
     double den = F[k + 1] - F[k];
-    double frac = den > 0.0 ? (b - F[k]) / den : 0.5;
-    return vmin + dv * ((double)k + frac);
+    double r = den > 0.0 ? (b - F[k]) / den : 0.5;
+    if (r < 0.0) r = 0.0;
+    if (r > 1.0) r = 1.0;
+    /* inside the cell the density is 1 + sigma (2t - 1) (t in [0, 1]): the cell's CDF fraction is
+     * t + sigma (t^2 - t), inverted in the form that stays exact as sigma -> 0 */
+    double sg = sigma ? sigma[k] : 0.0;
+    double t = 2.0 * r / ((1.0 - sg) + sqrt((1.0 - sg) * (1.0 - sg) + 4.0 * sg * r));
+    return vmin + dv * ((double)k + t);
 }
 
 void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
@@ -698,6 +711,9 @@ void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const doubl
     while (((int64_t)1 << m) < ppc) ++m;
     int pow2 = ((int64_t)1 << m) == ppc;
     double per_node = ldexp(1.0, -bin_shift); /* Haar synthesis: a bin's mass spread evenly over its nodes */
+    int32_t nbins = ncell >> bin_shift;
+    double* sig = (double*)malloc(sizeof(double) * (size_t)nbins * (size_t)nv);
+    for (int32_t i = 0; i < nbins; ++i) orc_cdf_cell_slopes(nv, cdf + (size_t)i * (nv + 1), sig + (size_t)i * nv);
     for (int64_t s = 0; s < N; ++s) {
         int64_t i = s;
         if (pow2 && m > 0) {
@@ -707,18 +723,41 @@ void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const doubl
         }
         int32_t c = (int32_t)(i / ppc);
         double th = (2.0 * (double)(i % ppc) + 1.0) / (2.0 * (double)ppc);
-        int32_t c1 = wrap((int64_t)c + 1, ncell);
-        int32_t b0 = c >> bin_shift, b1 = c1 >> bin_shift;
-        double nX = (1.0 - th) * mass[b0] * per_node + th * mass[b1] * per_node;
+        /* position measured from the centre of the particle's bin, in bin widths: the lifted
+         * f(x, v) is linear in x between neighbouring bin centres (Section 3.3's linear
+         * interpolation), mass and velocity quantiles alike. A bin sums the CIC charge of its
+         * 2^b nodes, i.e. covers x/dx in [i 2^b - 1/2, (i+1) 2^b - 1/2). */
+        int32_t nxc = ncell >> bin_shift;
+        double t = th + 0.5;
+        int32_t cc = c;
+        if (t >= 1.0) {
+            t -= 1.0;
+            cc = wrap((int64_t)c + 1, ncell);
+        }
+        int32_t bin = cc >> bin_shift;
+        double pos = ((double)(cc & ((1 << bin_shift) - 1)) + t) * per_node; /* in [0, 1) */
+        int32_t b0, b1;
+        double phi;
+        if (pos >= 0.5) {
+            b0 = bin;
+            b1 = (bin + 1) % nxc;
+            phi = pos - 0.5;
+        } else {
+            b0 = (bin + nxc - 1) % nxc;
+            b1 = bin;
+            phi = pos + 0.5;
+        }
+        double nX = ((1.0 - phi) * mass[b0] + phi * mass[b1]) * per_node;
         uint32_t B = brev32((uint32_t)i) + half + shift;
         double b = ((double)B + 0.5) * 2.3283064365386963e-10;
-        double v0 = orc_cdf_inverse(nv, cdf + (size_t)b0 * (nv + 1), b, vmin, dv);
-        double v1 = orc_cdf_inverse(nv, cdf + (size_t)b1 * (nv + 1), b, vmin, dv);
+        double v0 = orc_cdf_inverse(nv, cdf + (size_t)b0 * (nv + 1), sig + (size_t)b0 * nv, b, vmin, dv);
+        double v1 = orc_cdf_inverse(nv, cdf + (size_t)b1 * (nv + 1), sig + (size_t)b1 * nv, b, vmin, dv);
         cell[s] = c;
         theta[s] = th;
         w[s] = nX / (double)ppc;
-        v[s] = (1.0 - th) * v0 + th * v1;
+        v[s] = (1.0 - phi) * v0 + phi * v1;
     }
+    free(sig);
 }
 
 int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const double* w, int32_t ncell, double dx,

@@ -172,14 +172,25 @@ int orc_cdf_reconstruct(int32_t N, double* F);
  * not positive). Returns 1 if any reconstruction was pathological. */
 int orc_ps_lift_tables(int32_t nxc, int32_t nv, const double* H, double* mass, double* cdf);
 
+/* Relative density slope of each velocity cell of a CDF table F[0..nv]:
+ * sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1], p_k = F[k+1] - F[k] (p = 0 outside),
+ * so that the cell's density 1 + sigma (2t - 1), t in [0, 1], follows its neighbours and stays
+ * non-negative. */
+void orc_cdf_cell_slopes(int32_t nv, const double* F, double* sigma);
+
 /* Inverse of a monotone CDF table F[0..nv] at b in (0, 1): with k the first index where
- * F[k+1] > b, V = vmin + dv (k + (b - F[k]) / (F[k+1] - F[k])). */
-double orc_cdf_inverse(int32_t nv, const double* F, double b, double vmin, double dv);
+ * F[k+1] > b and r = (b - F[k]) / (F[k+1] - F[k]), V = vmin + dv (k + t) where t solves
+ * t + sigma_k (t^2 - t) = r (linear density inside the cell; sigma NULL: uniform, t = r). */
+double orc_cdf_inverse(int32_t nv, const double* F, const double* sigma, double b, double vmin, double dv);
 
 /* Appendix C particle loading on the phase-space tables: the Hammersley points of
- * orc_quiet_start (same positions, quantiles b and storage order); nodal density
- * n_j = mass[j >> b] 2^-b, w = n(X)/ppc (linear between the two nodes of the cell), and
- * V = (1 - theta) G_{bin(c)}(b) + theta G_{bin(c+1)}(b) with G the CDF inverse of a bin. */
+ * orc_quiet_start (same positions, quantiles b and storage order). The lifted f(x, v) is
+ * linear in x between neighbouring bin centres: with phi the particle's distance from the
+ * centre of the bin b0 at or left of it, in bin widths, and b1 = b0 + 1 (periodic),
+ * w = ((1 - phi) mass[b0] + phi mass[b1]) 2^-b / ppc and V = (1 - phi) G_b0(b) + phi G_b1(b),
+ * G the CDF inverse of a bin (quantile interpolation) with linear density inside each velocity
+ * cell (orc_cdf_cell_slopes): uniform cells would add dv^2/12 to the temperature at every
+ * lift. */
 void orc_ps_quiet_start(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
                         int32_t nv, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
                         double* v, double* w);

@@ -342,12 +342,12 @@ def ps_coarsen(sample_fx, s_w, stream=None):
 
 def ps_lift_tables(H, stream=None):
     """H [nxc, nv] FP64 (device) -> (mass [nxc], cdf [nxc, nv+1] FP64, sampling table
-    [nxc, 2 nv + 1] FP32, flag)."""
+    [nxc, 3 nv + 1] FP32, flag)."""
     H = H.contiguous()
     nxc, nv = H.shape
     mass = torch.empty(nxc, dtype=torch.float64, device=H.device)
     cdf = torch.empty((nxc, nv + 1), dtype=torch.float64, device=H.device)
-    table = torch.empty((nxc, 2 * nv + 1), dtype=torch.float32, device=H.device)
+    table = torch.empty((nxc, 3 * nv + 1), dtype=torch.float32, device=H.device)
     scratch = torch.empty(2 * nxc * (nv + 1), dtype=torch.float64, device=H.device)
     flags = torch.zeros(1, dtype=torch.int32, device=H.device)
     check(load().pe_ps_lift_tables(_ptr(H), nxc, nv, _ptr(mass), _ptr(cdf), _ptr(table), _ptr(scratch), _ptr(flags),
@@ -365,7 +365,7 @@ def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_
     rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
     status = _status(status, dev)
     check(load().pe_ps_quiet_start(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, int(bin_shift), _ptr(mass),
-                                   _ptr(table), (table.shape[1] - 1) // 2, float(v_min), float(dv),
+                                   _ptr(table), (table.shape[1] - 1) // 3, float(v_min), float(dv),
                                    int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(rho), _ptr(status),
                                    _stream(stream)), "pe_ps_quiet_start")
     return cell, theta, v, w, rho

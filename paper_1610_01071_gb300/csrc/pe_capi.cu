@@ -163,7 +163,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_SURROGATE] = align256(8 * 2 * ncoef) + 256;
     out->bytes[PE_BUF_PHASE] = ps ? align256(8 * ncoef) + align256(8 * ncoef * (size_t)(c.n_v + 1)) +
                                         align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
-                                        align256(4 * ncoef * (size_t)(2 * c.n_v + 1)) + 256
+                                        align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
                                   : 256;
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
@@ -230,7 +230,7 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
         x->ps_cdf = (double*)(ph + align256(8 * nc_));
         x->ps_scratch = (double*)(ph + align256(8 * nc_) + align256(8 * nc_ * nv1));
         x->ps_table = (float*)(ph + align256(8 * nc_) + align256(8 * nc_ * nv1) + align256(8 * 2 * nc_ * nv1));
-        x->ps_flags = (int32_t*)((char*)x->ps_table + align256(4 * nc_ * (2 * (size_t)x->nv + 1)));
+        x->ps_flags = (int32_t*)((char*)x->ps_table + align256(4 * nc_ * (3 * (size_t)x->nv + 1)));
         if (!x->ps) x->ps_flags = (int32_t*)ph;
     }
     if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||

@@ -32,7 +32,7 @@ struct pe_ctx {
     double* ps_mass;     // [n_coarse]
     double* ps_cdf;      // [n_coarse][n_v + 1]
     double* ps_scratch;  // [2 n_coarse (n_v + 1)]
-    float* ps_table;     // [n_coarse][2 n_v + 1] FP32 sampling rows
+    float* ps_table;     // [n_coarse][3 n_v + 1] FP32 sampling rows
     int32_t* ps_flags;
     int bank;            // which particle bank is current
     int v_at_integer;    // stored v is at integer time

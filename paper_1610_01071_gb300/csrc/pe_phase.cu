@@ -76,9 +76,8 @@ __device__ int edge_low(int N, double* F)
 // Interior reconstruction from the low indices (Appendix C): at the first descent k0, k1 the
 // first later index with F[k1] >= F[k0], k_+ the first minimum on (k0, k1], k_- the last
 // earlier index with F <= F[k_+]; a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) keeping the sum
-// of F over [k_-, k_+); k_+ grows (then k_- moves down and k_+ restarts) until dF >= 0 and
-// the ramp ends at or below F[k_+]. If no range qualifies, a running max fills the descent
-// and 1 is returned.
+// of F over [k_-, k_+); k_+ grows until dF >= 0 and the ramp ends at or below F[k_+]. A
+// descent with no admissible range is filled by a running max and 1 is returned.
 __device__ int interior_fwd(int N, double* F)
 {
     int bad = 0, start = 0;
@@ -92,36 +91,32 @@ __device__ int interior_fwd(int N, double* F)
         if (k0 < 0) return bad;
         int k1 = k0 + 1;
         while (k1 < N && F[k1] < F[k0]) ++k1;
-        int kp0 = k0 + 1;
+        int kp = k0 + 1;
         for (int k = k0 + 1; k <= k1; ++k)
-            if (F[k] < F[kp0]) kp0 = k;
+            if (F[k] < F[kp]) kp = k;
         int km = 0;
         for (int k = k0 - 1; k >= 0; --k)
-            if (F[k] <= F[kp0]) {
+            if (F[k] <= F[kp]) {
                 km = k;
                 break;
             }
         bool done = false;
-        for (; km >= 0 && !done; --km) {
-            for (int kp = kp0; kp <= N; ++kp) {
-                double S = 0.0;
-                for (int k = km; k < kp; ++k) S = add_(S, F[k]);
-                const double L = (double)(kp - km);
-                const double dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(S, L), F[km]));
-                const double end = add_(F[km], mul_(sub_(L, 1.0), dF));
-                if (dF >= 0.0 && end <= F[kp]) {
-                    for (int k = km + 1; k < kp; ++k) F[k] = add_(F[km], mul_((double)(k - km), dF));
-                    done = true;
-                    break;
-                }
+        for (; kp <= N; ++kp) {
+            double S = 0.0;
+            for (int k = km; k < kp; ++k) S = add_(S, F[k]);
+            const double L = (double)(kp - km);
+            const double dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(S, L), F[km]));
+            const double end = add_(F[km], mul_(sub_(L, 1.0), dF));
+            if (dF >= 0.0 && end <= F[kp]) {
+                for (int k = km + 1; k < kp; ++k) F[k] = add_(F[km], mul_((double)(k - km), dF));
+                done = true;
+                break;
             }
-            if (done) break;
         }
         if (!done) {
             bad = 1;
             for (int k = k0 + 1; k <= N; ++k)
                 if (F[k] < F[k - 1]) F[k] = F[k - 1];
-            km = 0;
         }
         start = km;
     }
@@ -161,8 +156,10 @@ namespace {
 
 // Lifting tables, per bin (one thread per bin, 32 bins per block so the bins spread over
 // the SMs): the raw mass, the reconstructed FP64 CDF row (uniform where the raw mass is not
-// positive), and the FP32 sampling row used by the particle loader: F[0..nv] and the inverse
-// cell slopes 1 / (F[k+1] - F[k]) (0 for an empty cell). scratch: 2 (nv + 1) doubles per bin.
+// positive), and the FP32 sampling row used by the particle loader: F[0..nv], the inverse
+// cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells' relative density
+// slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1]. scratch: 2 (nv + 1)
+// doubles per bin.
 __global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
                                               double* __restrict__ mass, double* __restrict__ cdf,
                                               float* __restrict__ table, double* __restrict__ scratch,
@@ -187,11 +184,14 @@ __global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int
     } else {
         for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
     }
-    float* T = table + (size_t)i * (2 * nv + 1);
+    float* T = table + (size_t)i * (3 * nv + 1);
     for (int k = 0; k <= nv; ++k) T[k] = (float)F[k];
     for (int k = 0; k < nv; ++k) {
-        const double den = F[k + 1] - F[k];
-        T[nv + 1 + k] = den > 0.0 ? (float)(1.0 / den) : 0.0f;
+        const double p = F[k + 1] - F[k];
+        const double pl = k > 0 ? F[k] - F[k - 1] : 0.0, pr = k + 1 < nv ? F[k + 2] - F[k + 1] : 0.0;
+        const double sg = p > 0.0 ? (pr - pl) / (4.0 * p) : 0.0;
+        T[nv + 1 + k] = p > 0.0 ? (float)(1.0 / p) : 0.0f;
+        T[2 * nv + 1 + k] = (float)(sg > 1.0 ? 1.0 : (sg < -1.0 ? -1.0 : sg));
     }
 }
 
@@ -230,8 +230,9 @@ struct PSLoad {
     uint32_t* status;
 };
 
-// V = v_min + dv (k + (b - F[k]) / (F[k+1] - F[k])) on a bin's FP32 sampling row, k the first
-// index with F[k+1] > b (binary search; nv - 1 if none).
+// V = v_min + dv (k + t) on a bin's FP32 sampling row: k the first index with F[k+1] > b
+// (binary search; nv - 1 if none), t the position inside the cell where the cell's linear
+// density reaches the fraction r = (b - F[k]) / (F[k+1] - F[k]) of its mass.
 __device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int nv, float b, float vmin, float dv)
 {
     int lo = 0, hi = nv - 1;
@@ -242,15 +243,20 @@ __device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int 
         else
             lo = mid + 1;
     }
-    const float f0 = __ldg(T + lo), sl = __ldg(T + nv + 1 + lo);
-    const float frac = sl > 0.0f ? (b - f0) * sl : 0.5f;
-    return fmaf(dv, (float)lo + frac, vmin);
+    const float f0 = __ldg(T + lo), sl = __ldg(T + nv + 1 + lo), sg = __ldg(T + 2 * nv + 1 + lo);
+    const float r = sl > 0.0f ? fminf(fmaxf((b - f0) * sl, 0.0f), 1.0f) : 0.5f;
+    // linear density 1 + sigma (2t - 1) inside the cell: t solves t + sigma (t^2 - t) = r
+    const float om = 1.0f - sg;
+    const float t = 2.0f * r / (om + sqrtf(fmaf(om, om, 4.0f * sg * r)));
+    return fmaf(dv, (float)lo + t, vmin);
 }
 
-// Appendix C loading of slot i: the Hammersley point and storage order of pe_quiet_start,
-// weight n(X)/ppc from the bin masses (a bin's mass spread evenly over its 2^b nodes, linear
-// between the cell's two nodes), velocity blended between the CDF inverses of the bins of the
-// cell's two nodes. FP32 (the particle precision) on tables built in FP64.
+// Appendix C loading of slot i: the Hammersley point and storage order of pe_quiet_start;
+// the lifted f(x, v) is linear in x between neighbouring bin centres (Section 3.3's linear
+// interpolation): weight n(X)/ppc and velocity quantile blended between the two bins around
+// the particle. A piecewise-constant (Haar) lift would give the density steps at bin edges,
+// and the field spikes there, multiplied by the co-moving time tau ~ Delta t, spread the next
+// restriction sample in velocity. FP32 (the particle precision) on tables built in FP64.
 __device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww)
 {
     if (P.log2ppc > 0) {
@@ -260,16 +266,37 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c,
     const uint32_t j = i % P.ppc;
     c = (int)(i / P.ppc);
     th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
-    const int c1 = (c + 1) & P.mask;
-    const int b0 = c >> P.bin_shift, b1 = c1 >> P.bin_shift;
-    const float n0 = (float)__ldg(P.mass + b0) * P.per_node, n1 = (float)__ldg(P.mass + b1) * P.per_node;
-    ww = fmaf(th, n1 - n0, n0) * P.inv_ppc;
+    // linear in x between neighbouring bin centres: phi is the distance from the centre of
+    // bin b0 (at or left of the particle) in bin widths
+    // (a bin sums the CIC charge of its 2^b nodes: it covers x/dx in [i 2^b - 1/2, (i+1) 2^b - 1/2))
+    const int nxc_mask = ((P.mask + 1) >> P.bin_shift) - 1;
+    float t = th + 0.5f;
+    int cc = c;
+    if (t >= 1.0f) {
+        t -= 1.0f;
+        cc = (c + 1) & P.mask;
+    }
+    const int bin = cc >> P.bin_shift;
+    const float pos = ((float)(cc & ((1 << P.bin_shift) - 1)) + t) * P.per_node;
+    int b0, b1;
+    float phi;
+    if (pos >= 0.5f) {
+        b0 = bin;
+        b1 = (bin + 1) & nxc_mask;
+        phi = pos - 0.5f;
+    } else {
+        b0 = (bin - 1) & nxc_mask;
+        b1 = bin;
+        phi = pos + 0.5f;
+    }
+    const float n0 = (float)__ldg(P.mass + b0), n1 = (float)__ldg(P.mass + b1);
+    ww = fmaf(phi, n1 - n0, n0) * P.per_node * P.inv_ppc;
     const uint32_t B = __brev(i) + P.half + P.shift;
     const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const int row = 2 * P.nv + 1;
+    const int row = 3 * P.nv + 1;
     const float v0 = cdf_inverse_f(P.table + (size_t)b0 * row, P.nv, b, P.vmin, P.dv);
     const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
-    vv = fmaf(th, v1 - v0, v0);
+    vv = fmaf(phi, v1 - v0, v0);
 }
 
 __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)

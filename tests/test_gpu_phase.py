@@ -89,7 +89,9 @@ def test_ps_lift_tables_bit_exact(nxc, nv):
     T = table.cpu().numpy()
     assert np.array_equal(T[:, :nv + 1], c_o.astype(np.float32))
     den = np.diff(c_o, axis=1)
-    assert np.allclose(T[:, nv + 1:], np.where(den > 0, 1.0 / np.where(den > 0, den, 1.0), 0.0), rtol=1e-7)
+    assert np.allclose(T[:, nv + 1:2 * nv + 1], np.where(den > 0, 1.0 / np.where(den > 0, den, 1.0), 0.0), rtol=1e-7)
+    sig = np.array([orc.cdf_cell_slopes(row) for row in c_o])
+    assert np.allclose(T[:, 2 * nv + 1:], sig, rtol=1e-7, atol=1e-7)
     assert np.all(np.diff(c_o, axis=1) >= 0)
 
 
