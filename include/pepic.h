@@ -263,6 +263,17 @@ PE_API int pe_rel_l2(const double* a, const double* b, int64_t n, double* out, v
 PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, int64_t ncoef, int32_t s_w, double* coarse,
                          void* stream);
 
+/* Projective step of the phase-space masses (Section 3.3, Eqs. extrapolation2 and
+ * leastsquares) with the least-squares slope filtered before the leap: with filter bit 0 the
+ * slope of every x-bin is smoothed along v by (1/4, 1/2, 1/4) (zero beyond the velocity range),
+ * with bit 1 every velocity cell along x (periodic). The filter keeps the slope's sum (charge)
+ * and, along v, its first moment (momentum); it damps the grid-scale structure of the slope,
+ * which the leap multiplies by (dT - K dt) / (K dt / 2). samples[(K+1)][nxc][n_v]; work, out and
+ * slope [nxc][n_v] (work: the unfiltered slope; slope: the filtered one; none may alias
+ * samples or each other). filter = 0 gives pe_ls_project's result. */
+PE_API int pe_ps_project(const double* samples, int32_t K, int32_t nxc, int32_t n_v, double dt, double dT,
+                         int32_t filter, double* work, double* out, double* slope, void* stream);
+
 /* Lifting tables of H[nxc][n_v] (FP64, device): mass[nxc] = sum_j H[i][j] with negative
  * masses clamped to 0 and the rest rescaled to keep the total (the clamp of Section 3.3's
  * remark on negative values); cdf[nxc][n_v + 1] the normalised CDF of each bin over its
@@ -322,6 +333,7 @@ typedef struct pe_config {
     int32_t coarse_kind;  /* PE_COARSE_MOMENTS or PE_COARSE_PHASE_SPACE */
     int32_t n_v;          /* phase space: velocity cells (2..256) */
     double v_max;         /* phase space: velocity range [-v_max, v_max) */
+    int32_t ps_filter;    /* phase space: 1-2-1 filter of the projected slope; bit 0 in v, bit 1 in x */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;

@@ -696,7 +696,8 @@ double orc_cdf_inverse(int32_t nv, const double* F, const double* sigma, double 
     /* inside the cell the density is 1 + sigma (2t - 1) (t in [0, 1]): the cell's CDF fraction is
      * t + sigma (t^2 - t), inverted in the form that stays exact as sigma -> 0 */
     double sg = sigma ? sigma[k] : 0.0;
-    double t = 2.0 * r / ((1.0 - sg) + sqrt((1.0 - sg) * (1.0 - sg) + 4.0 * sg * r));
+    double den2 = (1.0 - sg) + sqrt((1.0 - sg) * (1.0 - sg) + 4.0 * sg * r);
+    double t = den2 > 0.0 ? 2.0 * r / den2 : 0.0; /* den2 = 0 only for sigma = 1, r = 0 */
     return vmin + dv * ((double)k + t);
 }
 

@@ -49,7 +49,8 @@ class Config(ctypes.Structure):
                 ("v_th", ctypes.c_double), ("comoving", ctypes.c_int32), ("poisson", ctypes.c_int32),
                 ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int32), ("sort_every", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double),
-                ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double)]
+                ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double),
+                ("ps_filter", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -131,6 +132,7 @@ SIGNATURES = {
     "pe_step_surrogate": (ctypes.c_int, [P, P, ctypes.POINTER(GateCfg), ctypes.POINTER(GateStats)]),
     "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
     "pe_ps_coarsen": (ctypes.c_int, [P, i32, i64, i32, P, P]),
+    "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
     "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
     "pe_ps_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
     "pe_mlp_layout_for": (ctypes.c_int, [i32, P, i32, ctypes.POINTER(MLPLayout)]),
@@ -376,13 +378,14 @@ def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_
 
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
-                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0) -> Config:
+                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0) -> Config:
     """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
-    masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max)."""
+    masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
+    filter of the projected phase-space slope (bit 0 along v, bit 1 along x)."""
     return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
                   int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
-                  PE_COARSE[coarse], int(n_v), float(v_max))
+                  PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter))
 
 
 def layout(cfg: Config) -> Layout:

@@ -140,6 +140,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.coarse_kind != PE_COARSE_MOMENTS && c.coarse_kind != PE_COARSE_PHASE_SPACE) return PE_EINVAL;
     const bool ps = c.coarse_kind == PE_COARSE_PHASE_SPACE;
     if (ps && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
+    if (c.ps_filter < 0 || c.ps_filter > 3) return PE_EINVAL;
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
@@ -503,7 +504,13 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
 {
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
-    PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
+    if (ctx->ps && c.ps_filter) {
+        double* work = ctx->csamples + (size_t)(c.K + 1) * (size_t)ctx->crow;  // measurement row as scratch
+        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, c.dT, c.ps_filter, work, ctx->coarse,
+                             ctx->slope, ctx->stream));
+    } else {
+        PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
+    }
     ctx->macro_steps += 1;
     ctx->time += c.dT;
     ctx->fresh = 0;

@@ -158,6 +158,31 @@ struct PSGrid {
     }
 };
 
+// Per-lane run of equal phase-space keys over consecutive particles of a lane (a lane's
+// four particles of a 16-byte group are neighbours in a velocity-ordered cell, so they
+// usually share their phase-space cell): adds accumulate while the key repeats; a new key
+// sends the finished run to the grid directly.
+struct PSAcc {
+    int key;
+    long long val;
+
+    __device__ __forceinline__ void reset()
+    {
+        key = -1;
+        val = 0;
+    }
+    __device__ __forceinline__ void add(int k, long long q, const PSGrid& gr)
+    {
+        if (k == key) {
+            val += q;
+        } else {
+            if (key >= 0) gr.add(key, val);
+            key = k;
+            val = q;
+        }
+    }
+};
+
 // Adds (key, val) pairs of the active lanes to a PSGrid, summing runs of equal keys in
 // consecutive lanes first (consecutive particles of a velocity-ordered cell share their
 // phase-space cell): a segmented suffix sum over the run, added once by its first lane.

@@ -84,8 +84,8 @@ template <int MODE>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
                                         LaneWindow& lw, BinWindow& bw, const SmemGrid& grho,
                                         const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
-                                        const BinGrid& bsm, const PSGrid& gps, bool* ovf, int& c_out, float& th_out,
-                                        float& v_out)
+                                        const BinGrid& bsm, const PSGrid& gps, PSAcc& acc, bool* ovf, int& c_out,
+                                        float& th_out, float& v_out)
 {
     using Tr = ModeTraits<MODE>;
     c_out = c;
@@ -123,18 +123,13 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
             const float jf = floorf((vt - P.vmin) * P.inv_dv);
             const int j = jf < 0.0f ? 0 : (jf >= (float)P.nv ? P.nv - 1 : (int)jf);
             const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
-            int key0 = b0 * P.nv + j, key1 = -1;
-            long long q0, q1 = 0;
             if (b0 == b1) {
-                q0 = (long long)wq * (long long)kThetaOne;
-            } else {
+                acc.add(b0 * P.nv + j, (long long)wq * (long long)kThetaOne, gps);
+            } else {  // split across a bin edge (rare): the right part goes straight to the grid
                 const FxSplit qn = fx_split(wq, ths);
-                q0 = (long long)qn.left;
-                q1 = (long long)qn.right;
-                key1 = b1 * P.nv + j;
+                acc.add(b0 * P.nv + j, (long long)qn.left, gps);
+                gps.add(b1 * P.nv + j, (long long)qn.right);
             }
-            ps_add_warp(gps, key0, q0);
-            ps_add_warp(gps, key1, q1);
         }
         const int32_t mq = Tr::ps ? 0 : fx_weight(ww * vt, P.pscale, ovf);
         if (Tr::ps) {
@@ -232,6 +227,8 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     lw.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);
     BinWindow bw;
     bw.reset(0);
+    PSAcc acc;
+    acc.reset();
     bool ovf = false;
 
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
@@ -254,24 +251,32 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         }
         int4 co;
         float4 to, vo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.x, to.x, vo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.y, to.y, vo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.z, to.z, vo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.w, to.w, vo.w);
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
         }
+        if (kPS) {  // one warp-aggregated add per group of four particles per lane
+            ps_add_warp(gps, acc.key, acc.val);
+            acc.reset();
+        }
         if (two) {
-            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.x, to.x, vo.x);
-            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.y, to.y, vo.y);
-            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.z, to.z, vo.z);
-            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co.w, to.w, vo.w);
+            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
+            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
+            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
+            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
             if (kWrite) {
                 cell4[g + 32] = co;
                 th4[g + 32] = to;
                 v4[g + 32] = vo;
+            }
+            if (kPS) {
+                ps_add_warp(gps, acc.key, acc.val);
+                acc.reset();
             }
         }
     }
@@ -279,11 +284,15 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int co;
         float to, vo;
         const float vi = kNeedV ? P.v[i] : 0.f;
-        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, gps, &ovf, co, to, vo);
+        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
             P.v[i] = vo;
+        }
+        if (kPS) {
+            ps_add_warp(gps, acc.key, acc.val);
+            acc.reset();
         }
     }
     if (kRho) lw.flush(grho);

@@ -247,7 +247,8 @@ __device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int 
     const float r = sl > 0.0f ? fminf(fmaxf((b - f0) * sl, 0.0f), 1.0f) : 0.5f;
     // linear density 1 + sigma (2t - 1) inside the cell: t solves t + sigma (t^2 - t) = r
     const float om = 1.0f - sg;
-    const float t = 2.0f * r / (om + sqrtf(fmaf(om, om, 4.0f * sg * r)));
+    const float den = om + sqrtf(fmaxf(fmaf(om, om, 4.0f * sg * r), 0.0f));
+    const float t = den > 0.0f ? fminf(2.0f * r / den, 1.0f) : 0.0f;  // den = 0 only for sigma = 1, r = 0
     return fmaf(dv, (float)lo + t, vmin);
 }
 
@@ -357,6 +358,37 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     if (dep) grho.flush();
 }
 
+// Least-squares slope of every phase-space cell (Eq. leastsquares), into raw[nxc][nv].
+__global__ void k_ps_slope(const double* __restrict__ c, int K, int n, double dt, double* __restrict__ raw)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double den = (double)K * (K + 1) * (K + 2) * dt;
+    double s = 0.0;
+    for (int p = 0; 2 * p <= K; ++p) s += 6.0 * (K - 2 * p) / den * (c[(size_t)(K - p) * n + i] - c[(size_t)p * n + i]);
+    raw[i] = s;
+}
+
+// Filtered slope (1/4, 1/2, 1/4 along v and/or x) and the leap c_K + (dT - K dt) slope.
+__global__ void k_ps_leap(const double* __restrict__ c, const double* __restrict__ raw, int K, int nxc, int nv,
+                          double leap, int filter, double* __restrict__ out, double* __restrict__ slope)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nxc * nv) return;
+    const int i = idx / nv, j = idx - i * nv;
+    auto at = [&](int ii, int jj) -> double {
+        if (jj < 0 || jj >= nv) return 0.0;
+        ii = (ii + nxc) % nxc;
+        return raw[(size_t)ii * nv + jj];
+    };
+    auto vfilt = [&](int ii) -> double {
+        return (filter & 1) ? 0.25 * at(ii, j - 1) + 0.5 * at(ii, j) + 0.25 * at(ii, j + 1) : at(ii, j);
+    };
+    const double s = (filter & 2) ? 0.25 * vfilt(i - 1) + 0.5 * vfilt(i) + 0.25 * vfilt(i + 1) : vfilt(i);
+    slope[idx] = s;
+    out[idx] = c[(size_t)K * nxc * nv + idx] + leap * s;
+}
+
 __global__ void k_ps_scale(const long long* __restrict__ src, int64_t n, double scale, double* __restrict__ dst)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -378,6 +410,18 @@ extern "C" PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, 
     k_ps_scale<<<grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), n,
                                                        ldexp(1.0, -(s_w + 24)), coarse);
     return launch_status(1);
+}
+
+extern "C" PE_API int pe_ps_project(const double* samples, int32_t K, int32_t nxc, int32_t n_v, double dt, double dT,
+                                    int32_t filter, double* work, double* out, double* slope, void* stream)
+{
+    if (!samples || !work || !out || !slope || K < 1 || nxc < 1 || n_v < 1 || !(dt > 0.0) || filter < 0 || filter > 3)
+        return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = nxc * n_v;
+    k_ps_slope<<<(n + 255) / 256, 256, 0, s>>>(samples, K, n, dt, work);
+    k_ps_leap<<<(n + 255) / 256, 256, 0, s>>>(samples, work, K, nxc, n_v, dT - K * dt, filter, out, slope);
+    return launch_status(2);
 }
 
 extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf,
