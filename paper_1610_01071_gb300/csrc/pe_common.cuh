@@ -312,47 +312,70 @@ struct LaneWindow {
     }
 };
 
-// Per-lane accumulator of whole-particle bin contributions (BinGrid::add_whole) of the
-// density and momentum samples for two consecutive bins base, base+1, in int32. It is
-// flushed when a particle's bin leaves the pair or after 255 additions (so |sum| < 2^31).
-struct BinWindow {
-    int base, count;
-    int32_t n0, n1, m0, m1;
+// Per-lane run of whole-particle bin contributions (BinGrid::add_whole) of the density and
+// momentum samples over the lane's four neighbouring particles; a new bin sends the finished
+// run to the grid. The run of a group is then summed across lanes (bin_add_warp).
+struct BinAcc {
+    int key;
+    int32_t n, m;
 
-    __device__ __forceinline__ void reset(int b)
+    __device__ __forceinline__ void reset()
     {
-        base = b;
-        count = 0;
-        n0 = n1 = m0 = m1 = 0;
+        key = -1;
+        n = m = 0;
     }
-
-    __device__ __forceinline__ void flush(const BinGrid& gn, const BinGrid& gm, int bmask) const
+    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, const BinGrid& gn, const BinGrid& gm)
     {
-        if (n0 | m0) {
-            gn.add_whole(base, n0);
-            gm.add_whole(base, m0);
+        if (b == key) {
+            n += wq;
+            m += mq;
+        } else {
+            if (key >= 0) {
+                gn.add_whole(key, n);
+                gm.add_whole(key, m);
+            }
+            key = b;
+            n = wq;
+            m = mq;
         }
-        if (n1 | m1) {
-            gn.add_whole((base + 1) & bmask, n1);
-            gm.add_whole((base + 1) & bmask, m1);
-        }
-    }
-
-    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, const BinGrid& gn, const BinGrid& gm, int bmask)
-    {
-        int d = (b - base) & bmask;
-        if (d > 1 || count == 255) {
-            flush(gn, gm, bmask);
-            reset(b);
-            d = 0;
-        }
-        ++count;
-        n0 += (d == 0) ? wq : 0;
-        m0 += (d == 0) ? mq : 0;
-        n1 += (d == 1) ? wq : 0;
-        m1 += (d == 1) ? mq : 0;
     }
 };
+
+// Adds the active lanes' bin runs to the density and momentum BinGrids, summing runs of
+// equal bins in consecutive lanes first (consecutive lanes hold neighbouring particles of a
+// velocity-ordered cell, whose co-moving bins mostly agree): |sum| <= 32 * 4 * 2^23 = 2^30.
+// Lanes with key < 0 add nothing; if the active lanes are not a prefix of the warp, every
+// lane adds on its own.
+__device__ __forceinline__ void bin_add_warp(const BinGrid& gn, const BinGrid& gm, int key, int32_t n, int32_t m)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int nact = __popc(act);
+    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
+        if (key >= 0) {
+            gn.add_whole(key, n);
+            gm.add_whole(key, m);
+        }
+        return;
+    }
+    const int prev = __shfl_up_sync(act, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(act, head);
+    const unsigned after = heads & (0xFFFFFFFEu << lane);
+    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t on = __shfl_down_sync(act, n, off), om = __shfl_down_sync(act, m, off);
+        if (lane + off <= run_end) {
+            n += on;
+            m += om;
+        }
+    }
+    if (head && key >= 0) {
+        gn.add_whole(key, n);
+        gm.add_whole(key, m);
+    }
+}
 
 // Contiguous particle range [begin, end) of block b when n particles are split into
 // chunks whose starts are multiples of 4 (so float4 loads stay aligned).

@@ -82,7 +82,7 @@ constexpr int kThreads = 256;
 
 template <int MODE>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
-                                        LaneWindow& lw, BinWindow& bw, const SmemGrid& grho,
+                                        LaneWindow& lw, BinAcc& bacc, const SmemGrid& grho,
                                         const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
                                         const BinGrid& bsm, const PSGrid& gps, PSAcc& acc, bool* ovf, int& c_out,
                                         float& th_out, float& v_out)
@@ -137,7 +137,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         } else if (Tr::binned) {
             const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
             if (b0 == b1) {  // both CIC parts in one bin: the whole particle
-                bw.add(b0, wq, mq, bsn, bsm, bsn.nb - 1);
+                bacc.add(b0, wq, mq, bsn, bsm);
             } else {
                 const FxSplit qn = fx_split(wq, ths), qp = fx_split(mq, ths);
                 bsn.add_part(b0, qn.left);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
 }
 
 // One block owns a contiguous chunk of <= 65536 particles; each warp a contiguous slice
-// of it, read with 16-byte loads (4 particles per lane, two groups in flight).
+// of it, read with 16-byte loads (4 particles per lane).
 template <int MODE>
 __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begin, int64_t end, uint32_t* smem)
 {
@@ -225,8 +225,8 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     const int lane = threadIdx.x & 31;
     LaneWindow lw;
     lw.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);
-    BinWindow bw;
-    bw.reset(0);
+    BinAcc bacc;
+    bacc.reset();
     PSAcc acc;
     acc.reset();
     bool ovf = false;
@@ -235,26 +235,19 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     float4* th4 = reinterpret_cast<float4*>(P.theta);
     float4* v4 = reinterpret_cast<float4*>(P.v);
     const float4* w4 = reinterpret_cast<const float4*>(P.w);
-    for (int64_t g = g0 + lane; g < g1; g += 64) {
-        const bool two = g + 32 < g1;
-        int4 ca = cell4[g];
-        float4 ta = th4[g];
-        float4 va = kNeedV ? v4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 wa = __ldg(w4 + g);
-        int4 cb = make_int4(0, 0, 0, 0);
-        float4 tb = make_float4(0.f, 0.f, 0.f, 0.f), vb = tb, wb = tb;
-        if (two) {
-            cb = cell4[g + 32];
-            tb = th4[g + 32];
-            if (kNeedV) vb = v4[g + 32];
-            wb = __ldg(w4 + g + 32);
-        }
+    // one 16-byte group (four particles) per lane per iteration: a single inlined copy of the
+    // particle step keeps the kernel small enough for the instruction cache
+    for (int64_t g = g0 + lane; g < g1; g += 32) {
+        const int4 ca = cell4[g];
+        const float4 ta = th4[g];
+        const float4 va = kNeedV ? v4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 wa = __ldg(w4 + g);
         int4 co;
         float4 to, vo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
@@ -264,27 +257,16 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
             ps_add_warp(gps, acc.key, acc.val);
             acc.reset();
         }
-        if (two) {
-            process<MODE>(P, cb.x, tb.x, vb.x, wb.x, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
-            process<MODE>(P, cb.y, tb.y, vb.y, wb.y, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
-            process<MODE>(P, cb.z, tb.z, vb.z, wb.z, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
-            process<MODE>(P, cb.w, tb.w, vb.w, wb.w, lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
-            if (kWrite) {
-                cell4[g + 32] = co;
-                th4[g + 32] = to;
-                v4[g + 32] = vo;
-            }
-            if (kPS) {
-                ps_add_warp(gps, acc.key, acc.val);
-                acc.reset();
-            }
+        if (kBin) {
+            bin_add_warp(bsn, bsm, bacc.key, bacc.n, bacc.m);
+            bacc.reset();
         }
     }
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {  // ragged tail (< 4 particles)
         int co;
         float to, vo;
         const float vi = kNeedV ? P.v[i] : 0.f;
-        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bw, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo);
+        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
@@ -294,9 +276,12 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
             ps_add_warp(gps, acc.key, acc.val);
             acc.reset();
         }
+        if (kBin) {
+            bin_add_warp(bsn, bsm, bacc.key, bacc.n, bacc.m);
+            bacc.reset();
+        }
     }
     if (kRho) lw.flush(grho);
-    if (kBin) bw.flush(bsn, bsm, bsn.nb - 1);
     if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
     __syncthreads();
     if (kRho) grho.flush();
@@ -312,7 +297,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 3) k_particles(PushParams P)
+__global__ void __launch_bounds__(kThreads, ModeTraits<MODE>::ps ? 3 : 4) k_particles(PushParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
@@ -330,7 +315,7 @@ struct WorkItem {
 // the next item from a global counter until none are left. Step p and the kick are the
 // same for every realisation; tau and the sample row follow from each descriptor.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 3) k_particles_batch(const PushParams* descs, const WorkItem* items,
+__global__ void __launch_bounds__(kThreads, 4) k_particles_batch(const PushParams* descs, const WorkItem* items,
                                                                  int nitems, int p, float kick, unsigned* counter)
 {
     extern __shared__ uint32_t smem[];
