@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the fused kernel from the ncu capture summarised
 # in profiles/k_particles_push_sample_iaw_large.md, valid while the kernel source hashes to
 # the value it was taken with.
-NCU_TRAFFIC = {"source_hash": "bd51059d80d12247", "bytes": 270.222080e6 + 145.538304e6}
+NCU_TRAFFIC = {"source_hash": "79f942924c6c7697", "bytes": 270.772992e6 + 145.276416e6}
 
 
 def kernel_source_hash():
