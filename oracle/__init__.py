@@ -85,6 +85,15 @@ def _load():
                 "orc_ps_quiet_start": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
                 "orc_ps_burst": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl, i32,
                                                 i32, i32, dbl, dbl, i32, P, P]),
+                "orc_newton_pb_walls": (ctypes.c_int, [i32, dbl, i32, P, P, dbl, i32, P]),
+                "orc_efield_walls": (None, [i32, dbl, P, P]),
+                "orc_push_walls": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, dbl]),
+                "orc_restrict_sample_walls": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, P, P]),
+                "orc_quiet_start_equal": (None, [i64, i32, P, P, dbl, u64, P, P, P, P]),
+                "orc_burst_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl,
+                                                   i32, i32, i32, dbl, i32, i32, P, P]),
+                "orc_pic_steps_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32,
+                                                       i32, i32, dbl, i32, i32, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -426,3 +435,115 @@ def ps_burst(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, bin_shift, vmin, dv,
                                  int(vel_at_integer), int(bin_shift), float(vmin), float(dv), int(nv), _p(phi),
                                  _p(samples))
     return samples, phi, int(fails)
+
+
+# ------------------------------------------------------------------ bounded domain (Section 4.2)
+# Walls at node 0 and node ncell-1, absorbing for the ions, phi' = 0 for the potential.
+
+
+def newton_pb_walls(dep, dx, phi0=None, mode=0, tol=1e-11, maxit=50):
+    """Newton for Poisson-Boltzmann with mirror ghosts; dep is the nodal deposit (the wall
+    nodes count twice in the density)."""
+    dep = _f64(dep)
+    if phi0 is not None:
+        phi = _f64(phi0).copy()
+    else:
+        dens = dep.copy()
+        dens[[0, -1]] *= 2.0
+        phi = np.log(np.maximum(dens, 1e-8))
+    iters = np.zeros(1, np.int32)
+    fail = _load().orc_newton_pb_walls(dep.shape[0], float(dx), int(mode), _p(dep), _p(phi), float(tol), int(maxit),
+                                       _p(iters))
+    return phi, int(iters[0]), int(fail)
+
+
+def efield_walls(phi, dx):
+    phi = _f64(phi)
+    E = np.zeros_like(phi)
+    _load().orc_efield_walls(phi.shape[0], float(dx), _p(phi), _p(E))
+    return E
+
+
+def push_walls(st: State, E, ncell, dx, dt, qm, kick=1.0):
+    E = _f64(E)
+    _load().orc_push_walls(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), _p(E), ncell, float(dx), float(dt),
+                           float(qm), float(kick))
+
+
+def restrict_sample_walls(st: State, vbar, E0, ncell, dx, tau, qm):
+    vbar, E0 = _f64(vbar), _f64(E0)
+    dens, mom = np.zeros(ncell), np.zeros(ncell)
+    _load().orc_restrict_sample_walls(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell,
+                                      float(dx), float(tau), float(qm), _p(dens), _p(mom))
+    return dens, mom
+
+
+def quiet_start_equal(N, ncell, nprof, uprof, v_th, seed):
+    nprof, uprof = _f64(nprof), _f64(uprof)
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_quiet_start_equal(N, ncell, _p(nprof), _p(uprof), float(v_th), seed & 0xFFFFFFFFFFFFFFFF,
+                                  _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def burst_walls(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, comoving=True, mode=0, tol=1e-11, maxit=50,
+                vel_at_integer=True):
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, 2, ncell))
+    fails = _load().orc_burst_walls(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                    float(dt), float(qm), int(K), float(dT), int(comoving), int(mode), int(s_w),
+                                    float(tol), int(maxit), int(vel_at_integer), _p(phi), _p(samples))
+    return samples, phi, int(fails)
+
+
+def pic_steps_walls(st: State, ncell, dx, dt, qm, nsteps, s_w, phi, mode=0, tol=1e-11, maxit=50,
+                    vel_at_integer=True):
+    phi = _f64(phi).copy()
+    fails = _load().orc_pic_steps_walls(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                        float(dt), float(qm), int(nsteps), int(mode), int(s_w), float(tol),
+                                        int(maxit), int(vel_at_integer), _p(phi))
+    return phi, int(fails)
+
+
+def slab_profile(ncell):
+    """Section 4.2 slab in vacuum, uniform variant: n = 1 on the nodes of the central eighth,
+    7 ncell/16 <= j <= 9 ncell/16, and 0 elsewhere; u = 0."""
+    n = np.zeros(ncell)
+    n[7 * ncell // 16: 9 * ncell // 16 + 1] = 1.0
+    return n, np.zeros(ncell)
+
+
+def field_of_walls(st: State, ncell, dx, s_w, phi, mode=0, tol=1e-12, maxit=50):
+    rho = deposit_fx(st.cell, st.theta, st.w, ncell, s_w)
+    dens = rho.astype(np.float64) * 2.0 ** -(s_w + 24)
+    phi[:] = newton_pb_walls(dens, dx, phi0=phi, mode=mode, tol=tol, maxit=maxit)[0]
+    return efield_walls(phi, dx)
+
+
+def efpi_macro_step_walls(st: State, cfg: dict, phi, vel_at_integer=True):
+    """efpi_macro_step in the bounded domain."""
+    ncell, nc, K = cfg["ncell"], cfg["n_coarse"], cfg["K"]
+    dx = cfg["L"] / ncell
+    samples, phi, fails = burst_walls(st, ncell, dx, cfg["dt"], cfg["qm"], K, cfg["dT"], cfg["s_w"], phi,
+                                      comoving=cfg.get("comoving", True), mode=cfg.get("mode", 0),
+                                      vel_at_integer=vel_at_integer)
+    wav = cfg.get("wavelet", "haar")
+    cs = np.zeros((K + 1, 2, nc))
+    for p in range(K + 1):
+        for m in range(2):
+            cs[p, m] = coarsen(samples[p, m], nc, wav)
+    coarse, _ = ls_project(cs.reshape(K + 1, 2 * nc), cfg["dt"], cfg["dT"])
+    return coarse.reshape(2, nc), cs, phi
+
+
+def lift_walls(coarse, cfg: dict, seed):
+    """Lifting in the bounded domain: refine, clamp, the wall nodes' deposits doubled to
+    densities, equal-weight loading."""
+    ncell = cfg["ncell"]
+    wav = cfg.get("wavelet", "haar")
+    nf = refine(coarse[0], ncell, wav)
+    mf = refine(coarse[1], ncell, wav)
+    nf, uf = lift_profile(nf, mf)
+    nf[[0, -1]] *= 2.0
+    return quiet_start_equal(cfg["N"], ncell, nf, uf, cfg["v_th"], seed)

@@ -788,3 +788,239 @@ int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const doubl
     free(vbar);
     return fails;
 }
+
+/* ---------------------------------------------------------------- bounded domain
+ * Walls at node 0 (x = 0) and node ncell-1 (x = (ncell-1) dx); the particles live in the
+ * ncell-1 cells between them. Section 4.2 runs the slab expansion with an absorbing
+ * boundary; the potential satisfies phi' = 0 at both walls (mirror ghosts phi_{-1} = phi_1,
+ * phi_{ncell} = phi_{ncell-2}). A wall node's CIC control volume is the half cell inside the
+ * domain, so its density is twice its deposit. */
+
+/* Tridiagonal solve a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j (Thomas; a_0 and c_{n-1} unused). */
+static void thomas_var(int32_t n, const double* a, const double* b, const double* c, const double* d, double* x)
+{
+    double* cp = (double*)malloc(sizeof(double) * (size_t)n);
+    double* dp = (double*)malloc(sizeof(double) * (size_t)n);
+    cp[0] = c[0] / b[0];
+    dp[0] = d[0] / b[0];
+    for (int32_t i = 1; i < n; ++i) {
+        double m = b[i] - a[i] * cp[i - 1];
+        cp[i] = c[i] / m;
+        dp[i] = (d[i] - a[i] * dp[i - 1]) / m;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int32_t i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    free(cp);
+    free(dp);
+}
+
+int orc_newton_pb_walls(int32_t ncell, double dx, int32_t mode, const double* dep, double* phi, double tol,
+                        int32_t maxit, int32_t* iters)
+{
+    const double inv_dx2 = 1.0 / (dx * dx);
+    double* a = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* b = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* c = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* delta = (double*)malloc(sizeof(double) * (size_t)ncell);
+    int status = 1;
+    int32_t it = 0;
+    for (it = 0; it < maxit; ++it) {
+        for (int32_t j = 0; j < ncell; ++j) {
+            /* mirror ghosts at the walls */
+            double pl = (j == 0) ? phi[1] : phi[j - 1];
+            double pr = (j == ncell - 1) ? phi[ncell - 2] : phi[j + 1];
+            double nj = (j == 0 || j == ncell - 1) ? 2.0 * dep[j] : dep[j];
+            double lap = (pl - 2.0 * phi[j] + pr) * inv_dx2;
+            double g = (mode == 0) ? exp(phi[j]) : 1.0 + phi[j];
+            double gp = (mode == 0) ? exp(phi[j]) : 1.0;
+            rhs[j] = -(-lap + g - nj);
+            b[j] = 2.0 * inv_dx2 + gp;
+            a[j] = (j == ncell - 1) ? -2.0 * inv_dx2 : -inv_dx2; /* d lap / d phi_{j-1} */
+            c[j] = (j == 0) ? -2.0 * inv_dx2 : -inv_dx2;         /* d lap / d phi_{j+1} */
+        }
+        thomas_var(ncell, a, b, c, rhs, delta);
+        double m = 0.0;
+        for (int32_t j = 0; j < ncell; ++j) m = fmax(m, fabs(delta[j]));
+        double scale = (m > 2.0) ? 2.0 / m : 1.0;
+        for (int32_t j = 0; j < ncell; ++j) phi[j] += scale * delta[j];
+        if (m < tol) {
+            status = 0;
+            ++it;
+            break;
+        }
+    }
+    if (iters) *iters = it;
+    free(a);
+    free(b);
+    free(c);
+    free(rhs);
+    free(delta);
+    return status;
+}
+
+void orc_efield_walls(int32_t ncell, double dx, const double* phi, double* E)
+{
+    E[0] = 0.0; /* -(phi_1 - phi_{-1}) / (2 dx) with the mirror ghost */
+    E[ncell - 1] = 0.0;
+    for (int32_t j = 1; j < ncell - 1; ++j) E[j] = -(phi[j + 1] - phi[j - 1]) / (2.0 * dx);
+}
+
+/* Leapfrog kick-drift in the bounded domain: a particle whose drift ends outside
+ * [0, (ncell-1) dx) is absorbed: w = 0, v = 0, parked on the wall node it crossed
+ * (cell 0 or ncell-1, theta 0). Particles with w = 0 are not moved. */
+void orc_push_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, const double* E,
+                    int32_t ncell, double dx, double dt, double qm, double kick)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        if (w[p] == 0.0) continue;
+        double Ep = (1.0 - theta[p]) * E[cell[p]] + theta[p] * E[cell[p] + 1];
+        v[p] += kick * qm * dt * Ep;
+        double s = theta[p] + v[p] * dt / dx;
+        double k = floor(s);
+        double cn = (double)cell[p] + k;
+        if (!(cn >= 0.0 && cn < (double)(ncell - 1))) {
+            cell[p] = (cn < 0.0) ? 0 : ncell - 1;
+            theta[p] = 0.0;
+            v[p] = 0.0;
+            w[p] = 0.0;
+            continue;
+        }
+        cell[p] = (int32_t)cn;
+        theta[p] = s - k;
+    }
+}
+
+/* Appendix B restriction sample in the bounded domain: as orc_restrict_sample; a
+ * particle whose co-moving position X~ lies outside [0, (ncell-1) dx) has left the
+ * domain by t_{n+1} and is not counted. Particles with w = 0 contribute nothing. */
+void orc_restrict_sample_walls(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                               const double* w, const double* E0, int32_t ncell, double dx, double tau,
+                               double qm, double* dens, double* mom)
+{
+    memset(dens, 0, sizeof(double) * (size_t)ncell);
+    memset(mom, 0, sizeof(double) * (size_t)ncell);
+    for (int64_t p = 0; p < n; ++p) {
+        if (w[p] == 0.0) continue;
+        double E0p = (1.0 - theta[p]) * E0[cell[p]] + theta[p] * E0[cell[p] + 1];
+        double s = theta[p] + tau * vbar[p] / dx;
+        double k = floor(s);
+        double cn = (double)cell[p] + k;
+        if (!(cn >= 0.0 && cn < (double)(ncell - 1))) continue;
+        int32_t c = (int32_t)cn;
+        double th = s - k;
+        double vt = vbar[p] + qm * tau * E0p;
+        dens[c] += w[p] * (1.0 - th);
+        dens[c + 1] += w[p] * th;
+        mom[c] += w[p] * vt * (1.0 - th);
+        mom[c + 1] += w[p] * vt * th;
+    }
+}
+
+/* Appendix C loading with equal weights in the bounded domain: the nodal density profile
+ * n_j (wall nodes included as densities) is linear inside each of the ncell-1 cells, with
+ * cell mass m_c = (n_c + n_{c+1}) / 2 and cumulative mass C_c = m_0 + ... + m_{c-1}, total M.
+ * Particle i sits at the quantile s_i = (i + 1/2) M / N of the cumulative mass: in the cell c
+ * with C_c <= s_i < C_{c+1} and m_c > 0, at the offset t that solves
+ * t + sigma (t^2 - t) = r, r = (s_i - C_c) / m_c, sigma = (n_{c+1} - n_c) / (n_{c+1} + n_c)
+ * (the mass of the linear density up to t). Every particle has w = M / N, so the number of
+ * particles per cell follows the mass (empty cells get none). V = u(X) + v_th Phi^{-1}(b_i)
+ * with the Hammersley second coordinate b_i of orc_quiet_start (slot s holds point i = s). */
+void orc_quiet_start_equal(int64_t N, int32_t ncell, const double* nprof, const double* uprof, double v_th,
+                           uint64_t seed, int32_t* cell, double* theta, double* v, double* w)
+{
+    const int32_t ncl = ncell - 1;
+    double* C = (double*)malloc(sizeof(double) * (size_t)(ncl + 1));
+    C[0] = 0.0;
+    for (int32_t c = 0; c < ncl; ++c) C[c + 1] = C[c] + 0.5 * (nprof[c] + nprof[c + 1]);
+    const double M = C[ncl];
+    uint32_t half = (uint32_t)(2147483648.0 / (double)N);
+    uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
+    int32_t c = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        double s = ((double)i + 0.5) * M / (double)N;
+        while (c < ncl - 1 && !(s < C[c + 1] && C[c + 1] > C[c])) ++c;
+        double mc = C[c + 1] - C[c];
+        double r = (mc > 0.0) ? (s - C[c]) / mc : 0.5;
+        if (r < 0.0) r = 0.0;
+        if (r > 1.0) r = 1.0;
+        double n0 = nprof[c], n1 = nprof[c + 1];
+        double sig = (n0 + n1 > 0.0) ? (n1 - n0) / (n1 + n0) : 0.0;
+        double den = (1.0 - sig) + sqrt((1.0 - sig) * (1.0 - sig) + 4.0 * sig * r);
+        double t = (den > 0.0) ? 2.0 * r / den : 0.0;
+        int32_t cc = c;
+        if (t >= 1.0) {
+            t = 0.0;
+            cc = c + 1;
+        }
+        double uX = (1.0 - t) * uprof[cc] + t * uprof[cc + 1 < ncell ? cc + 1 : cc];
+        uint32_t B = brev32((uint32_t)i) + half + shift;
+        double b = ((double)B + 0.5) * 2.3283064365386963e-10;
+        cell[i] = cc;
+        theta[i] = t;
+        w[i] = M / (double)N;
+        v[i] = uX + v_th * orc_ndtri(b);
+    }
+    free(C);
+}
+
+static int field_walls(int64_t n, const int32_t* cell, const double* theta, const double* w, int32_t ncell,
+                       double dx, int32_t mode, int32_t s_w, double tol, int32_t maxit, double* phi, double* E)
+{
+    int64_t* rho = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    double* dens = (double*)malloc(sizeof(double) * (size_t)ncell);
+    orc_deposit_fx(n, cell, theta, w, ncell, s_w, rho);
+    double scale = ldexp(1.0, -(s_w + 24));
+    for (int32_t j = 0; j < ncell; ++j) dens[j] = (double)rho[j] * scale;
+    int32_t iters = 0;
+    int fail = orc_newton_pb_walls(ncell, dx, mode, dens, phi, tol, maxit, &iters);
+    orc_efield_walls(ncell, dx, phi, E);
+    free(rho);
+    free(dens);
+    return fail;
+}
+
+int orc_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                    double dt, double qm, int32_t K, double dT, int32_t comoving, int32_t mode, int32_t s_w,
+                    double tol, int32_t maxit, int32_t vel_at_integer, double* phi, double* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int fails = field_walls(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell);
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = (w[i] == 0.0) ? v[i]
+                                    : v[i] + (kick - 0.5) * qm * dt *
+                                                 ((1.0 - theta[i]) * E[cell[i]] + theta[i] * E[cell[i] + 1]);
+        double tau = comoving ? dT - p * dt : 0.0;
+        double* dens = samples + (size_t)p * 2 * ncell;
+        orc_restrict_sample_walls(n, cell, theta, vbar, w, E0, ncell, dx, tau, qm, dens, dens + ncell);
+        if (p == K) break;
+        orc_push_walls(n, cell, theta, v, w, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_walls(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}
+
+int orc_pic_steps_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                        double dt, double qm, int32_t nsteps, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                        int32_t vel_at_integer, double* phi)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    int fails = 0;
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t s = 0; s < nsteps; ++s) {
+        fails += field_walls(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+        orc_push_walls(n, cell, theta, v, w, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+    }
+    free(E);
+    return fails;
+}
