@@ -68,6 +68,18 @@ extern "C" {
 #define PE_COARSE_PHASE_SPACE 1 /* phase-space cell masses (Section 3.3), Haar in x and v */
 
 #define PE_PROFILE_SINE 0 /* n = 1 + a cos(2 pi x / L), u = a cos(2 pi x / L) (Section 4.1) */
+#define PE_PROFILE_SLAB 1 /* n = 1 on the nodes 7 ncell/16 .. 9 ncell/16, 0 elsewhere; u = 0
+                             (Section 4.2's slab in vacuum, uniform variant; bounded grids) */
+
+/* Boundary of the grid. Periodic: nodes j = 0..ncell-1 wrap. Absorbing (Section 4.2, the
+ * slab expansion): walls at node 0 (x = 0) and node ncell-1 (x = (ncell-1) dx); the ions
+ * live in the ncell-1 cells between them, phi' = 0 at both walls (mirror ghosts, so E = 0
+ * there), a wall node's density is twice its deposit (half control volume), and an ion whose
+ * drift ends outside [0, (ncell-1) dx) is absorbed: its weight becomes 0, v = 0, and it is
+ * parked on the wall node it crossed (cell 0 or cell ncell-1, theta 0). Particles of weight
+ * 0 are not moved and add nothing to deposits, samples or diagnostics. */
+#define PE_BOUNDARY_PERIODIC 0
+#define PE_BOUNDARY_ABSORBING 1
 
 PE_API const char* pe_strerror(int code);
 PE_API const char* pe_version(void);
@@ -97,6 +109,14 @@ PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w
                     double tol, int32_t maxit, double* phi, double* E, float* Ef, int32_t* diag,
                     uint32_t* status, void* stream);
 
+/* pe_field with a boundary (PE_BOUNDARY_*). With PE_BOUNDARY_ABSORBING the equations at the
+ * wall nodes use the mirror ghosts and twice the deposit, E is 0 on the walls, and the
+ * Jacobian solve runs in FP64 (vacuum regions make it ill-conditioned for FP32).
+ * pe_field is pe_field_ex with PE_BOUNDARY_PERIODIC. */
+PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
+                       int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
+                       int32_t* diag, uint32_t* status, void* stream);
+
 /* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
  * follows it): each particle, at its integer-time velocity Vbar, is carried to
  * X~ = X + tau Vbar, V~ = Vbar + qm tau E_n(X), and w and w V~ are deposited
@@ -122,6 +142,8 @@ typedef struct pe_sample_args {
     int32_t n_v;        /* 0: moment sample; > 0: phase-space sample with n_v velocity cells */
     float v_min;        /* phase space: lower velocity bound V_min */
     float inv_dv;       /* phase space: 1 / dv, dv = (V_max - V_min) / n_v */
+    int32_t boundary;   /* PE_BOUNDARY_*: with walls, a particle whose target X~ lies outside
+                           [0, (ncell-1) dx) is not counted (it has left the domain by t_{n+1}) */
 } pe_sample_args;
 
 /* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
@@ -136,6 +158,15 @@ PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_
                    const float* Ef, int32_t ncell, float dt_over_dx, float qm_dt, float kick,
                    int32_t s_w, int64_t* rho_fx, const pe_sample_args* sample,
                    uint32_t* status, void* stream);
+
+/* pe_push with a boundary (PE_BOUNDARY_*). With PE_BOUNDARY_ABSORBING, w is written: an ion
+ * absorbed during this step gets w = 0 (see PE_BOUNDARY_ABSORBING); a live particle found on
+ * cell ncell-1 sets PE_FLAG_RANGE and is left unchanged. sample->boundary must equal boundary.
+ * pe_push is pe_push_ex with PE_BOUNDARY_PERIODIC (w only read). */
+PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef,
+                      int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w,
+                      int32_t boundary, int64_t* rho_fx, const pe_sample_args* sample,
+                      uint32_t* status, void* stream);
 
 /* Restriction sample only (no push), e.g. the last sample p = N_e of a burst:
  * the same sample as pe_push, with Vbar = v + (kick - 1/2) qm_dt E(X). */
@@ -185,6 +216,25 @@ PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64
                           int32_t ncell, const float* prof_n, const float* prof_u, float v_th,
                           uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
                           void* stream);
+
+/* Quiet-start loading with equal weights on a bounded grid (Appendix C's loading, with the
+ * particle count of each cell in proportion to its mass, as for Section 4.2's slab whose
+ * vacuum cells hold no ions). The nodal density profile (prof_n, its wall nodes multiplied by
+ * wall_factor: 1 when prof_n holds densities, 2 when it holds deposits) is linear inside each
+ * of the ncell-1 cells between the walls: cell mass m_c = (n_c + n_{c+1}) / 2, cumulative mass
+ * C_c = m_0 + ... + m_{c-1}, total M. Particle i (storage slot i) sits at the quantile
+ * (i + 1/2) M / n of the cumulative mass: in the cell c with C_c <= (i + 1/2) M / n < C_{c+1},
+ * at the offset t solving t + sigma (t^2 - t) = r, r the fraction of m_c below it and
+ * sigma = (n_{c+1} - n_c) / (n_{c+1} + n_c). w = M / n for every particle;
+ * V = u(X) + v_th Phi^-1(b_i) with b_i of pe_quiet_start. Output is sorted by cell.
+ * scratch: PE_EQ_SCRATCH_BYTES(ncell) bytes of device memory, 16-byte aligned. A profile of
+ * zero (or non-finite) mass sets PE_FLAG_RANGE and gives weight-0 particles in cell 0.
+ * If rho_fx != NULL it is overwritten with the charge deposit of the new particles. */
+#define PE_EQ_SCRATCH_BYTES(ncell) (16 * (size_t)(ncell) + 16)
+PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                                int32_t ncell, const float* prof_n, const float* prof_u,
+                                float wall_factor, float v_th, uint64_t seed, int32_t s_w,
+                                void* scratch, int64_t* rho_fx, uint32_t* status, void* stream);
 
 /* Sort by cell (counting sort), used by the plain PIC path to keep the deposit's
  * per-block grids local. Reads (cell, theta, v, w), writes the permuted particles to
@@ -334,6 +384,8 @@ typedef struct pe_config {
     int32_t n_v;          /* phase space: velocity cells (2..256) */
     double v_max;         /* phase space: velocity range [-v_max, v_max) */
     int32_t ps_filter;    /* phase space: 1-2-1 filter of the projected slope; bit 0 in v, bit 1 in x */
+    int32_t boundary;     /* PE_BOUNDARY_*; absorbing grids lift with pe_quiet_start_equal and
+                             take the moment coarse variables only */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;
@@ -356,7 +408,8 @@ enum pe_buffer {
     PE_BUF_STATUS,          /* uint32[4] status word; int32[4] Newton diag after it */
     PE_BUF_DIAG,            /* pe_moments scratch + one pe_moments result */
     PE_BUF_SURROGATE,       /* f64[2][n_coarse] surrogate slope + gate result */
-    PE_BUF_PHASE,           /* phase space: f64 bin masses, CDF tables, reconstruction scratch, flag */
+    PE_BUF_PHASE,           /* phase space: f64 bin masses, CDF tables, reconstruction scratch, flag;
+                               absorbing grids: the equal-weight loading scratch */
     PE_NBUF
 };
 
@@ -388,7 +441,9 @@ PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_bytes, void
 PE_API void pe_destroy(pe_ctx* ctx);
 
 /* Initial state at t = 0 from an analytic nodal profile (PE_PROFILE_SINE with the
- * given amplitude) by the quiet start; also computes the initial coarse state. */
+ * given amplitude, or PE_PROFILE_SLAB, amplitude unused) by the quiet start (periodic grids:
+ * pe_quiet_start; absorbing grids: pe_quiet_start_equal); also computes the initial coarse
+ * state. */
 PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude);
 
 /* Micro-scale evolution (Section 3.1): K fine steps from the current particles with

@@ -6,8 +6,9 @@ Calls raise if the library is missing: there is no CPU path.
 """
 from . import inputs
 from ._binding import (BUF, MLP, Batch, Config, Context, PepicError, coarsen, compute_moments, deposit, field, layout, load,
-                       ls_project, make_config, make_sample_args, push, quiet_start, refine, rel_l2, sample, sort)
+                       ls_project, make_config, make_sample_args, push, quiet_start, quiet_start_equal, refine, rel_l2,
+                       sample, sort)
 
 __all__ = ["BUF", "MLP", "Batch", "Config", "Context", "PepicError", "coarsen", "compute_moments", "deposit", "field", "inputs",
-           "layout", "load", "ls_project", "make_config", "make_sample_args", "push", "quiet_start", "refine", "rel_l2",
-           "sample", "sort"]
+           "layout", "load", "ls_project", "make_config", "make_sample_args", "push", "quiet_start",
+           "quiet_start_equal", "refine", "rel_l2", "sample", "sort"]

@@ -19,6 +19,8 @@ PE_OK, PE_EINVAL, PE_ECUDA, PE_ENOCONV, PE_EOVERFLOW, PE_ERANGE, PE_ESTATE = ran
 PE_WAVELET = {"haar": 0, "d4": 1}
 PE_POISSON = {"boltzmann": 0, "linearized": 1}
 PE_PROFILE_SINE = 0
+PE_PROFILE_SLAB = 1
+PE_BOUNDARY = {"periodic": 0, "absorbing": 1}
 PE_NBUF = 17
 BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
            coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16)
@@ -39,7 +41,7 @@ class SampleArgs(ctypes.Structure):
     _fields_ = [("E0f", ctypes.c_void_p), ("tau", ctypes.c_float), ("qm", ctypes.c_float),
                 ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
                 ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p), ("n_v", ctypes.c_int32),
-                ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float)]
+                ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float), ("boundary", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):
@@ -50,7 +52,7 @@ class Config(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int32), ("sort_every", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double),
                 ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double),
-                ("ps_filter", ctypes.c_int32)]
+                ("ps_filter", ctypes.c_int32), ("boundary", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -98,12 +100,16 @@ SIGNATURES = {
     "pe_version": (ctypes.c_char_p, []),
     "pe_deposit": (ctypes.c_int, [P, P, P, i64, i32, i32, P, P, P]),
     "pe_field": (ctypes.c_int, [P, i32, f64, i32, i32, f64, i32, P, P, P, P, P, P]),
+    "pe_field_ex": (ctypes.c_int, [P, i32, f64, i32, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
+    "pe_push_ex": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, i32, P, ctypes.POINTER(SampleArgs),
+                                  P, P]),
     "pe_sample": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, ctypes.POINTER(SampleArgs), P, P]),
     "pe_coarsen": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, i32, P, P]),
     "pe_ls_project": (ctypes.c_int, [P, i32, i32, f64, f64, P, P, P]),
     "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
     "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
+    "pe_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, f32, u64, i32, P, P, P, P]),
     "pe_sort": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P, P]),
     "pe_sort_noalloc": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P]),
     "pe_layout_for": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Layout)]),
@@ -209,34 +215,48 @@ def deposit(cell, theta, w, ncell, s_w, rho=None, status=None, stream=None):
     return rho
 
 
-def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, status=None, stream=None):
+def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, status=None, stream=None,
+          boundary="periodic"):
     dev = rho.device
     E = torch.empty(ncell, dtype=torch.float64, device=dev)
     Ef = torch.empty(ncell, dtype=torch.float32, device=dev)
     diag = torch.zeros(4, dtype=torch.int32, device=dev)
     status = _status(status, dev)
-    check(load().pe_field(_ptr(rho), ncell, float(dx), s_w, PE_POISSON[mode], float(tol), int(maxit), _ptr(phi),
-                          _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status), _stream(stream)), "pe_field")
+    if boundary == "periodic":
+        check(load().pe_field(_ptr(rho), ncell, float(dx), s_w, PE_POISSON[mode], float(tol), int(maxit), _ptr(phi),
+                              _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status), _stream(stream)), "pe_field")
+    else:
+        check(load().pe_field_ex(_ptr(rho), ncell, float(dx), s_w, PE_POISSON[mode], PE_BOUNDARY[boundary],
+                                 float(tol), int(maxit), _ptr(phi), _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status),
+                                 _stream(stream)), "pe_field_ex")
     return E, Ef, diag
 
 
-def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0):
+def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0,
+                     boundary="periodic"):
     """Restriction-sample arguments; n_v > 0 selects the phase-space sample (n_v velocity
     cells of width dv from v_min) instead of the density and momentum moments."""
     return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
                       int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()), int(n_v), float(v_min),
-                      float(1.0 / dv))
+                      float(1.0 / dv), PE_BOUNDARY[boundary])
 
 
 def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
-         stream=None):
+         stream=None, boundary="periodic"):
+    """Leapfrog push fused with the deposit (and the sample); boundary="absorbing" writes w of
+    the absorbed particles."""
     dev = cell.device
     rho = rho if rho is not None else torch.empty(ncell, dtype=torch.int64, device=dev)
     status = _status(status, dev)
     sp = ctypes.byref(sample) if sample is not None else None
-    check(load().pe_push(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), ncell,
-                         float(dt_over_dx), float(qm_dt), float(kick), s_w, _ptr(rho), sp, _ptr(status),
-                         _stream(stream)), "pe_push")
+    if boundary == "periodic":
+        check(load().pe_push(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), ncell,
+                             float(dt_over_dx), float(qm_dt), float(kick), s_w, _ptr(rho), sp, _ptr(status),
+                             _stream(stream)), "pe_push")
+    else:
+        check(load().pe_push_ex(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), _ptr(Ef), ncell,
+                                float(dt_over_dx), float(qm_dt), float(kick), s_w, PE_BOUNDARY[boundary], _ptr(rho),
+                                sp, _ptr(status), _stream(stream)), "pe_push_ex")
     return rho
 
 
@@ -285,6 +305,24 @@ def quiet_start(n, ncell, prof_n, prof_u, v_th, seed, s_w, with_rho=True, status
     check(load().pe_quiet_start(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, _ptr(prof_n), _ptr(prof_u),
                                 float(v_th), int(seed) & 0xFFFFFFFFFFFFFFFF, s_w, _ptr(rho), _ptr(status),
                                 _stream(stream)), "pe_quiet_start")
+    return cell, theta, v, w, rho
+
+
+def quiet_start_equal(n, ncell, prof_n, prof_u, v_th, seed, s_w, wall_factor=1.0, with_rho=True, status=None,
+                      stream=None):
+    """Equal-weight loading of a bounded grid (pe_quiet_start_equal)."""
+    dev = prof_n.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    scratch = torch.empty((16 * ncell + 16 + 15) // 8, dtype=torch.float64, device=dev)
+    status = _status(status, dev)
+    check(load().pe_quiet_start_equal(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, _ptr(prof_n),
+                                      _ptr(prof_u), float(wall_factor), float(v_th), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                      s_w, _ptr(scratch), _ptr(rho), _ptr(status), _stream(stream)),
+          "pe_quiet_start_equal")
     return cell, theta, v, w, rho
 
 
@@ -378,14 +416,15 @@ def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_
 
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
-                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0) -> Config:
+                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic") -> Config:
     """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
     masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
-    filter of the projected phase-space slope (bit 0 along v, bit 1 along x)."""
+    filter of the projected phase-space slope (bit 0 along v, bit 1 along x); boundary:
+    "periodic" or "absorbing" (walls at nodes 0 and ncell-1, Section 4.2)."""
     return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
                   int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
-                  PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter))
+                  PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter), PE_BOUNDARY[boundary])
 
 
 def layout(cfg: Config) -> Layout:
@@ -419,8 +458,9 @@ class Context:
         check(getattr(load(), name)(self._h, *args), name)
 
     # -- cycle
-    def load_initial(self, amplitude):
-        self._call("pe_load_initial", PE_PROFILE_SINE, float(amplitude))
+    def load_initial(self, amplitude=0.0, profile="sine"):
+        """profile "sine" (amplitude of the Section 4.1 wave) or "slab" (Section 4.2, bounded grids)."""
+        self._call("pe_load_initial", PE_PROFILE_SLAB if profile == "slab" else PE_PROFILE_SINE, float(amplitude))
 
     def burst(self):
         self._call("pe_burst")

@@ -37,7 +37,8 @@ int layout_for(pe_ctx* const* ctxs, int n, Layout* L)
     int64_t rho = 0, row = 0, items = 0;
     for (int r = 0; r < n; ++r) {
         const pe_ctx* x = ctxs[r];
-        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps) return PE_EINVAL;
+        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps || x->walls)
+            return PE_EINVAL;
         rho += x->cfg.ncell;
         row += 2 * (int64_t)x->nb;
         items += (x->cfg.nparticles + kMinChunk - 1) / kMinChunk;
@@ -131,7 +132,7 @@ static int build_descs(pe_batch* b)
                        x->s_w, x->s_p, x->csamples, x->coarse, x->slope);
         const bool cl = newton_cluster_size(c.ncell) == b->G && b->G > 1;
         char* dst = cl ? fc.data() + field_desc_size() * nc++ : fs.data() + field_desc_size() * ns++;
-        make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, c.newton_tol,
+        make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, 0, c.newton_tol,
                         c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status);
     }
     if (cudaMemcpy(at(b, b->L.push), push.data(), push.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -147,10 +148,10 @@ static int field_all(pe_batch* b)
 {
     const char* base = at(b, b->L.field);
     if (!b->cluster_ids.empty())
-        PE_TRY(launch_newton_batch(base, (int)b->cluster_ids.size(), b->G, b->max_ncell_cluster, b->stream));
+        PE_TRY(launch_newton_batch(base, (int)b->cluster_ids.size(), b->G, b->max_ncell_cluster, false, b->stream));
     if (!b->single_ids.empty())
         PE_TRY(launch_newton_batch(base + field_desc_size() * b->cluster_ids.size(), (int)b->single_ids.size(), 1,
-                                   b->max_ncell_single, b->stream));
+                                   b->max_ncell_single, false, b->stream));
     return PE_OK;
 }
 

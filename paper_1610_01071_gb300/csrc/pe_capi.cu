@@ -141,6 +141,9 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     const bool ps = c.coarse_kind == PE_COARSE_PHASE_SPACE;
     if (ps && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
     if (c.ps_filter < 0 || c.ps_filter > 3) return PE_EINVAL;
+    if (c.boundary != PE_BOUNDARY_PERIODIC && c.boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
+    const bool walls = c.boundary == PE_BOUNDARY_ABSORBING;
+    if (walls && ps) return PE_EINVAL;  // the phase-space variable is built for periodic grids
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
@@ -165,7 +168,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_PHASE] = ps ? align256(8 * ncoef) + align256(8 * ncoef * (size_t)(c.n_v + 1)) +
                                         align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
                                         align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
-                                  : 256;
+                                  : (walls ? align256(PE_EQ_SCRATCH_BYTES(nc)) : 256);
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -233,6 +236,8 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
         x->ps_table = (float*)(ph + align256(8 * nc_) + align256(8 * nc_ * nv1) + align256(8 * 2 * nc_ * nv1));
         x->ps_flags = (int32_t*)((char*)x->ps_table + align256(4 * nc_ * (3 * (size_t)x->nv + 1)));
         if (!x->ps) x->ps_flags = (int32_t*)ph;
+        x->walls = cfg->boundary == PE_BOUNDARY_ABSORBING;
+        x->eq_scratch = x->walls ? (void*)ph : nullptr;
     }
     if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||
         cudaMemsetAsync(x->status, 0, 64, x->stream) != cudaSuccess) {
@@ -321,8 +326,8 @@ static int field_solve(pe_ctx* x)
 {
     const pe_config& c = x->cfg;
     return timed(x, 1, [&] {
-        return pe_field(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.newton_tol, c.newton_maxit, x->phi, x->E,
-                        x->Ef, x->diag, x->status, x->stream);
+        return pe_field_ex(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.boundary, c.newton_tol, c.newton_maxit,
+                           x->phi, x->E, x->Ef, x->diag, x->status, x->stream);
     });
 }
 
@@ -349,6 +354,7 @@ static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
     a.s_w = x->s_w;
     a.s_p = x->s_p;
     a.sample_fx = dst;
+    a.boundary = x->cfg.boundary;
     if (x->ps) {  // Section 3.3 phase-space histogram instead of the moments
         a.n_v = x->nv;
         a.v_min = (float)x->vmin;
@@ -357,11 +363,18 @@ static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
     return a;
 }
 
-static int quiet_start_from_profile(pe_ctx* x, uint64_t seed)
+// Quiet start on the profiles in PE_BUF_PROFILE. Bounded grids load equal weights in
+// proportion to the mass; wall_factor 2 when the profile's wall nodes hold deposits (a
+// lifted restriction), 1 when they hold densities (an analytic initial profile).
+static int quiet_start_from_profile(pe_ctx* x, uint64_t seed, float wall_factor)
 {
     const pe_config& c = x->cfg;
     const int b = x->bank;
     PE_TRY(timed(x, 0, [&] {
+        if (x->walls)
+            return pe_quiet_start_equal(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->prof,
+                                        x->prof + c.ncell, wall_factor, (float)c.v_th, seed, x->s_w, x->eq_scratch,
+                                        x->rho, x->status, x->stream);
         return pe_quiet_start(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->prof,
                               x->prof + c.ncell, (float)c.v_th, seed, x->s_w, x->rho, x->status, x->stream);
     }));
@@ -420,11 +433,17 @@ static int measure_phase(pe_ctx* x, double* out)
 
 extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude)
 {
-    if (!ctx || profile != PE_PROFILE_SINE) return PE_EINVAL;
+    if (!ctx || (profile != PE_PROFILE_SINE && profile != PE_PROFILE_SLAB)) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
+    if (profile == PE_PROFILE_SLAB && !x->walls) return PE_EINVAL;
     std::vector<float> h(2 * (size_t)c.ncell);
     for (int j = 0; j < c.ncell; ++j) {
+        if (profile == PE_PROFILE_SLAB) {  // uniform slab on the central eighth, vacuum elsewhere
+            h[j] = (j >= 7 * c.ncell / 16 && j <= 9 * c.ncell / 16) ? 1.0f : 0.0f;
+            h[c.ncell + j] = 0.0f;
+            continue;
+        }
         const double xj = j * x->dx;
         const double pert = amplitude * cos(2.0 * M_PI * xj / c.L);
         h[j] = (float)(1.0 + pert);
@@ -438,7 +457,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     x->macro_steps = 0;
     x->fine_steps = 0;
     x->time = 0.0;
-    PE_TRY(quiet_start_from_profile(x, c.seed));
+    PE_TRY(quiet_start_from_profile(x, c.seed, 1.0f));
     if (x->ps) return measure_phase(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
 }
@@ -464,8 +483,8 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
         const double tau = c.comoving ? c.dT - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
         PE_TRY(timed(x, 0, [&] {
-            return pe_push(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
-                           kick, x->s_w, x->rho, &a, x->status, x->stream);
+            return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
+                              kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream);
         }));
         PE_TRY(field_solve(x));
         kick = 1.0f;
@@ -538,7 +557,7 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         return PE_OK;
     }
     PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
-    return quiet_start_from_profile(x, lift_seed(x));
+    return quiet_start_from_profile(x, lift_seed(x), 2.0f);  // refined restriction: wall nodes hold deposits
 }
 
 extern "C" PE_API int pe_step(pe_ctx* ctx)
@@ -568,8 +587,8 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
         const int b = x->bank;
         const float kick = x->v_at_integer ? 0.5f : 1.0f;
         PE_TRY(timed(x, 0, [&] {
-            return pe_push(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt, kick,
-                           x->s_w, x->rho, nullptr, x->status, x->stream);
+            return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
+                              kick, x->s_w, c.boundary, x->rho, nullptr, x->status, x->stream);
         }));
         x->v_at_integer = 0;
         x->rho_valid = 1;

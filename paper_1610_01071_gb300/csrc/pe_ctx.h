@@ -34,6 +34,8 @@ struct pe_ctx {
     double* ps_scratch;  // [2 n_coarse (n_v + 1)]
     float* ps_table;     // [n_coarse][3 n_v + 1] FP32 sampling rows
     int32_t* ps_flags;
+    int walls;           // bounded grid (PE_BOUNDARY_ABSORBING)
+    void* eq_scratch;    // equal-weight loading scratch (bounded grids)
     int bank;            // which particle bank is current
     int v_at_integer;    // stored v is at integer time
     int fresh;           // particles were just loaded/lifted (not yet advanced)

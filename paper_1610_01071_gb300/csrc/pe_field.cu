@@ -1,7 +1,11 @@
 // Field solve: the nonlinear Poisson-Boltzmann equation of Section 3.3 (Eq.
-// poisson2rescaled with lambda = n_0 = 1) on the periodic nodes,
+// poisson2rescaled with lambda = n_0 = 1) on the nodes,
 //   -(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 + g(phi_j) = n_j,   g = exp or 1 + phi,
 // by Newton's method, followed by the centred field E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx).
+// Periodic grids wrap; bounded grids (Section 4.2's slab expansion) have walls at nodes 0
+// and ncell-1 with phi' = 0 there (mirror ghosts phi_{-1} = phi_1, phi_{ncell} = phi_{ncell-2},
+// hence E = 0 on the walls), and a wall node's density is twice its deposit (its CIC
+// control volume is the half cell inside the domain).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,10 +26,12 @@ constexpr int kClusterMinCells = 512;  // grids at least this large use the mult
 // [g B, (g+1) B), one node per thread.
 //
 // Precision: phi, exp(phi), the Newton residual and the update are FP64; the Jacobian
-// correction J d = -F is solved in FP32. This is Newton's method with an inexact
-// linear solve (mixed-precision iterative refinement): the FP64 residual drives the
+// correction J d = -F is solved in FP32 on periodic grids. This is Newton's method with an
+// inexact linear solve (mixed-precision iterative refinement): the FP64 residual drives the
 // iteration, so it converges to the FP64 solution of the discrete equation, while the
 // FP32 solve only bounds the final contraction rate (~ cond(J) 2^-24 per iteration).
+// Bounded grids with vacuum regions have exp(phi) ~ 1e-6 there, so cond(J) reaches ~1e7 and
+// FP32 would no longer contract: their linear solve runs in FP64 (template parameter T).
 // On this GPU a dependent FP64 instruction costs ~100 cycles and the FP64 pipe retires
 // ~2 lanes per cycle per SM, so FP64 is used only for per-node work, spread over many
 // warps and SMs, and kept off the serial chains of the tridiagonal elimination.
@@ -54,29 +60,43 @@ __device__ __forceinline__ double exp_small(double x)
     return fma(p, x, 1.0);
 }
 
+template <typename T>
 struct M2 {
-    float a, b, c, d;  // [[a, b], [c, d]]
+    T a, b, c, d;  // [[a, b], [c, d]]
 };
-__device__ __forceinline__ M2 mmul(M2 x, M2 y)
+template <typename T>
+__device__ __forceinline__ M2<T> mmul(M2<T> x, M2<T> y)
 {
     return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
 }
-__device__ __forceinline__ M2 msub(M2 x, M2 y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
-__device__ __forceinline__ M2 minv(M2 x)
+template <typename T>
+__device__ __forceinline__ M2<T> msub(M2<T> x, M2<T> y)
 {
-    const float r = 1.0f / (x.a * x.d - x.b * x.c);
+    return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d};
+}
+template <typename T>
+__device__ __forceinline__ M2<T> minv(M2<T> x)
+{
+    const T r = T(1) / (x.a * x.d - x.b * x.c);
     return {x.d * r, -x.b * r, -x.c * r, x.a * r};
 }
-__device__ __forceinline__ float2 mvec(M2 x, float2 v) { return {x.a * v.x + x.b * v.y, x.c * v.x + x.d * v.y}; }
+template <typename T>
+__device__ __forceinline__ void mvec(M2<T> x, T v0, T v1, T* o0, T* o1)
+{
+    *o0 = x.a * v0 + x.b * v1;
+    *o1 = x.c * v0 + x.d * v1;
+}
 
 // Block cyclic reduction of the G block rows (thread k < G owns row k) stored as full
 // 2x2 matrices: L3[k] = {Mk(4), Dk(4), Pk(4), rk(2)}, row k: Mk z_{k-1} + Dk z_k + Pk z_{k+1} = rk.
-// After the steps with stride G/2 every row couples only to itself. zsol gets z.
-__device__ void block_pcr(float* L3, float* L3n, float* zsol, int G)
+// After the steps with stride G/2 every row couples only to itself. zsol gets z. (On a
+// bounded grid the corner blocks M_0 and P_{G-1} are zero, so the wrap adds nothing.)
+template <typename T>
+__device__ void block_pcr(T* L3, T* L3n, T* zsol, int G)
 {
     const int k = threadIdx.x;
-    auto ld = [](const float* p) { return M2{p[0], p[1], p[2], p[3]}; };
-    auto st = [](float* p, M2 m) {
+    auto ld = [](const T* p) { return M2<T>{p[0], p[1], p[2], p[3]}; };
+    auto st = [](T* p, M2<T> m) {
         p[0] = m.a;
         p[1] = m.b;
         p[2] = m.c;
@@ -84,21 +104,22 @@ __device__ void block_pcr(float* L3, float* L3n, float* zsol, int G)
     };
     for (int s = 1; s <= G / 2; s <<= 1) {
         if (k < G) {
-            const float* c = L3 + 14 * k;
-            const float* lm = L3 + 14 * ((k - s + G) % G);
-            const float* lp = L3 + 14 * ((k + s) % G);
-            const M2 al = mmul(ld(c), minv(ld(lm + 4)));      // Mk D_{k-s}^-1
-            const M2 ga = mmul(ld(c + 8), minv(ld(lp + 4)));  // Pk D_{k+s}^-1
-            float* o = L3n + 14 * k;
-            const M2 nM = mmul(al, ld(lm));
-            const M2 nP = mmul(ga, ld(lp + 8));
-            st(o, M2{-nM.a, -nM.b, -nM.c, -nM.d});
-            st(o + 8, M2{-nP.a, -nP.b, -nP.c, -nP.d});
+            const T* c = L3 + 14 * k;
+            const T* lm = L3 + 14 * ((k - s + G) % G);
+            const T* lp = L3 + 14 * ((k + s) % G);
+            const M2<T> al = mmul(ld(c), minv(ld(lm + 4)));      // Mk D_{k-s}^-1
+            const M2<T> ga = mmul(ld(c + 8), minv(ld(lp + 4)));  // Pk D_{k+s}^-1
+            T* o = L3n + 14 * k;
+            const M2<T> nM = mmul(al, ld(lm));
+            const M2<T> nP = mmul(ga, ld(lp + 8));
+            st(o, M2<T>{-nM.a, -nM.b, -nM.c, -nM.d});
+            st(o + 8, M2<T>{-nP.a, -nP.b, -nP.c, -nP.d});
             st(o + 4, msub(msub(ld(c + 4), mmul(al, ld(lm + 8))), mmul(ga, ld(lp))));
-            const float2 ra = mvec(al, make_float2(lm[12], lm[13]));
-            const float2 rg = mvec(ga, make_float2(lp[12], lp[13]));
-            o[12] = c[12] - ra.x - rg.x;
-            o[13] = c[13] - ra.y - rg.y;
+            T ra0, ra1, rg0, rg1;
+            mvec(al, lm[12], lm[13], &ra0, &ra1);
+            mvec(ga, lp[12], lp[13], &rg0, &rg1);
+            o[12] = c[12] - ra0 - rg0;
+            o[13] = c[13] - ra1 - rg1;
         }
         __syncthreads();
         if (k < G)
@@ -106,13 +127,14 @@ __device__ void block_pcr(float* L3, float* L3n, float* zsol, int G)
         __syncthreads();
     }
     if (k < G) {
-        const float* c = L3 + 14 * k;
-        M2 Dt = ld(c + 4);
-        const M2 Mm = ld(c), Pm = ld(c + 8);
-        Dt = M2{Dt.a + Mm.a + Pm.a, Dt.b + Mm.b + Pm.b, Dt.c + Mm.c + Pm.c, Dt.d + Mm.d + Pm.d};
-        const float2 z = mvec(minv(Dt), make_float2(c[12], c[13]));
-        zsol[2 * k] = z.x;
-        zsol[2 * k + 1] = z.y;
+        const T* c = L3 + 14 * k;
+        M2<T> Dt = ld(c + 4);
+        const M2<T> Mm = ld(c), Pm = ld(c + 8);
+        Dt = M2<T>{Dt.a + Mm.a + Pm.a, Dt.b + Mm.b + Pm.b, Dt.c + Mm.c + Pm.c, Dt.d + Mm.d + Pm.d};
+        T z0, z1;
+        mvec(minv(Dt), c[12], c[13], &z0, &z1);
+        zsol[2 * k] = z0;
+        zsol[2 * k + 1] = z1;
     }
     __syncthreads();
 }
@@ -126,12 +148,13 @@ struct FieldDesc {
     int* diag;
     uint32_t* status;
     double dx, nscale, tol;
-    int ncell, mode, maxit, pad;
+    int ncell, mode, maxit, walls;  // walls: 1 for a bounded grid
 };
 
 // Solver body for the realisation of this cluster: B = ncell / G nodes per block, one per
 // thread; threads at or beyond B (a batched launch sized for a larger grid) only take
-// part in the barriers.
+// part in the barriers. T is the precision of the linear solve.
+template <typename T>
 __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_group& cluster)
 {
     extern __shared__ double sh[];
@@ -145,33 +168,35 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     double* phi = d.phi;
     const double dx = d.dx, nscale = d.nscale, tol = d.tol;
     const int mode = d.mode, maxit = d.maxit;
-    double* ph = sh;                                 // [B + 2]
-    double* mymax = ph + B + 2;                      // [1]
-    float* A = reinterpret_cast<float*>(mymax + 1);  // [B] x 6
-    float* Bd = A + B;
-    float* C = Bd + B;
-    float* D = C + B;
-    float* Gs = D + B;
-    float* Hs = Gs + B;
-    float* red = Hs + B;      // [32]
-    float* mine = red + 32;   // [6]
-    float* L3 = mine + 8;     // [G][14]
-    float* L3n = L3 + 14 * G;
-    float* zsol = L3n + 14 * G;  // [2G]
+    double* ph = sh;                             // [B + 2]
+    double* mymax = ph + B + 2;                  // [1]
+    T* A = reinterpret_cast<T*>(mymax + 1);      // [B] x 6
+    T* Bd = A + B;
+    T* C = Bd + B;
+    T* D = C + B;
+    T* Gs = D + B;
+    T* Hs = Gs + B;
+    T* red = Hs + B;     // [32]
+    T* mine = red + 32;  // [6]
+    T* L3 = mine + 8;    // [G][14]
+    T* L3n = L3 + 14 * G;
+    T* zsol = L3n + 14 * G;  // [2G]
 
     const int mask = ncell - 1;
     const int j = g * B + (act ? i : 0);
+    const bool walls = d.walls != 0;
+    const bool wl = walls && j == 0, wr = walls && j == ncell - 1;  // this thread's node is a wall
     const double inv_dx2 = 1.0 / (dx * dx);
-    const float o = (float)(-inv_dx2);
+    const T o = (T)(-inv_dx2);
     const bool boltz = (mode == PE_POISSON_BOLTZMANN);
-    const double nj = act ? (double)__ldg(rho + j) * nscale : 0.0;
+    const double nj = act ? (double)__ldg(rho + j) * nscale * ((wl || wr) ? 2.0 : 1.0) : 0.0;
     double pj = act ? phi[j] : 0.0;
     double gj = boltz ? exp(pj) : 1.0 + pj;
 
     int it = 0;
     bool converged = false;
     for (it = 0; it < maxit; ++it) {
-        // ---- FP64 residual with the halo from the neighbouring blocks
+        // ---- FP64 residual with the halo from the neighbouring blocks (mirror ghosts at walls)
         if (act) {
             ph[i + 1] = pj;
             if (i == 0) ph[0] = phi[(g * B - 1) & mask];
@@ -179,23 +204,24 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         }
         __syncthreads();
         if (act) {
-            const double lap = (ph[i] - 2.0 * pj + ph[i + 2]) * inv_dx2;
-            A[i] = (i == 0) ? 0.f : o;
-            C[i] = (i == B - 1) ? 0.f : o;
-            Bd[i] = (float)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
-            D[i] = (float)(lap - gj + nj);  // -F_j
-            Gs[i] = (i == 0) ? o : 0.f;
-            Hs[i] = (i == B - 1) ? o : 0.f;
+            const double pl = wl ? ph[i + 2] : ph[i], pr = wr ? ph[i] : ph[i + 2];
+            const double lap = (pl - 2.0 * pj + pr) * inv_dx2;
+            A[i] = (i == 0) ? T(0) : (wr ? T(2) * o : o);
+            C[i] = (i == B - 1) ? T(0) : (wl ? T(2) * o : o);
+            Bd[i] = (T)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
+            D[i] = (T)(lap - gj + nj);  // -F_j
+            Gs[i] = (i == 0 && !wl) ? o : T(0);
+            Hs[i] = (i == B - 1 && !wr) ? o : T(0);
         }
         __syncthreads();
-        // ---- FP32 parallel cyclic reduction of the block rows, three right-hand sides
+        // ---- parallel cyclic reduction of the block rows, three right-hand sides
         for (int s = 1; s < B; s <<= 1) {
             const int im = act ? i - s : -1, ip = act ? i + s : B;
-            const float al = (im >= 0) ? A[i] / Bd[im] : 0.f;
-            const float ga = (ip < B) ? C[i] / Bd[ip] : 0.f;
-            const float nA = (im >= 0) ? -al * A[im] : 0.f;
-            const float nC = (ip < B) ? -ga * C[ip] : 0.f;
-            float nB = act ? Bd[i] : 0.f, nD = act ? D[i] : 0.f, nG = act ? Gs[i] : 0.f, nH = act ? Hs[i] : 0.f;
+            const T al = (im >= 0) ? A[i] / Bd[im] : T(0);
+            const T ga = (ip < B) ? C[i] / Bd[ip] : T(0);
+            const T nA = (im >= 0) ? -al * A[im] : T(0);
+            const T nC = (ip < B) ? -ga * C[ip] : T(0);
+            T nB = act ? Bd[i] : T(0), nD = act ? D[i] : T(0), nG = act ? Gs[i] : T(0), nH = act ? Hs[i] : T(0);
             if (im >= 0) {
                 nB -= al * C[im];
                 nD -= al * D[im];
@@ -219,9 +245,9 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
             }
             __syncthreads();
         }
-        const float rb = act ? 1.0f / Bd[i] : 0.f;
-        const float y = act ? D[i] * rb : 0.f, gsp = act ? Gs[i] * rb : 0.f,
-                    hsp = act ? Hs[i] * rb : 0.f;  // x = y - g X_left - h X_right
+        const T rb = act ? T(1) / Bd[i] : T(0);
+        const T y = act ? D[i] * rb : T(0), gsp = act ? Gs[i] * rb : T(0),
+                hsp = act ? Hs[i] * rb : T(0);  // x = y - g X_left - h X_right
         if (i == 0) {
             mine[0] = y;
             mine[1] = gsp;
@@ -235,27 +261,33 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         cluster.sync();  // #1: every block's boundary rows are visible
         // ---- cyclic block-tridiagonal system of the blocks' (first, last) unknowns
         if (i < G) {
-            const float* rem = cluster.map_shared_rank(mine, i);
-            float* r = L3 + 14 * i;
+            const T* rem = cluster.map_shared_rank(mine, i);
+            T* r = L3 + 14 * i;
             // F_k + g0 L_{k-1} + h0 F_{k+1} = y0 ;  L_k + gB L_{k-1} + hB F_{k+1} = yB
-            r[0] = 0.f; r[1] = rem[1]; r[2] = 0.f; r[3] = rem[4];      // M: picks L_{k-1}
-            r[4] = 1.f; r[5] = 0.f;    r[6] = 0.f; r[7] = 1.f;         // D = I
-            r[8] = rem[2]; r[9] = 0.f; r[10] = rem[5]; r[11] = 0.f;    // P: picks F_{k+1}
+            r[0] = T(0); r[1] = rem[1]; r[2] = T(0); r[3] = rem[4];     // M: picks L_{k-1}
+            r[4] = T(1); r[5] = T(0);   r[6] = T(0); r[7] = T(1);       // D = I
+            r[8] = rem[2]; r[9] = T(0); r[10] = rem[5]; r[11] = T(0);   // P: picks F_{k+1}
             r[12] = rem[0]; r[13] = rem[3];
         }
         __syncthreads();
-        block_pcr(L3, L3n, zsol, G);
-        const float Xl = zsol[2 * ((g - 1 + G) % G) + 1];  // previous block's last unknown
-        const float Xr = zsol[2 * ((g + 1) % G)];          // next block's first unknown
-        const float dlt = y - gsp * Xl - hsp * Xr;
+        block_pcr<T>(L3, L3n, zsol, G);
+        const T Xl = zsol[2 * ((g - 1 + G) % G) + 1];  // previous block's last unknown
+        const T Xr = zsol[2 * ((g + 1) % G)];          // next block's first unknown
+        const T dlt = y - gsp * Xl - hsp * Xr;
         // ---- global max |update| (damping and convergence)
-        float mloc = fabsf(dlt);
-        for (int off = 16; off > 0; off >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, off));
+        T mloc = act ? (dlt < T(0) ? -dlt : dlt) : T(0);
+        for (int off = 16; off > 0; off >>= 1) {
+            const T oth = __shfl_xor_sync(0xffffffffu, mloc, off);
+            mloc = oth > mloc ? oth : mloc;
+        }
         if ((i & 31) == 0) red[i >> 5] = mloc;
         __syncthreads();
         if (i < 32) {
-            float v = (i < ((blockDim.x + 31) >> 5)) ? red[i] : 0.f;
-            for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+            T v = (i < ((blockDim.x + 31) >> 5)) ? red[i] : T(0);
+            for (int off = 16; off > 0; off >>= 1) {
+                const T oth = __shfl_xor_sync(0xffffffffu, v, off);
+                v = oth > v ? oth : v;
+            }
             if (i == 0) *mymax = (double)v;
         }
         cluster.sync();  // #2: block maxima visible; level-3 rows no longer read
@@ -284,7 +316,7 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     }
     __syncthreads();
     if (act) {
-        const double e = -(ph[i + 2] - ph[i]) * (0.5 / dx);
+        const double e = (wl || wr) ? 0.0 : -(ph[i + 2] - ph[i]) * (0.5 / dx);
         d.E[j] = e;
         d.Ef[j] = (float)e;
     }
@@ -299,18 +331,20 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(1024) k_newton_cluster(FieldDesc d)
 {
     cg::cluster_group cluster = cg::this_cluster();
-    newton_body(d, cluster);
+    newton_body<T>(d, cluster);
 }
 
 // One cluster per realisation: cluster c solves descs[c].
+template <typename T>
 __global__ void __launch_bounds__(1024) k_newton_batch(const FieldDesc* descs)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const FieldDesc d = descs[blockIdx.x / cluster.num_blocks()];
-    newton_body(d, cluster);
+    newton_body<T>(d, cluster);
 }
 
 static int cluster_size_for(int ncell)
@@ -320,7 +354,8 @@ static int cluster_size_for(int ncell)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (!cached[dev]) {
-        cudaFuncSetAttribute((const void*)k_newton_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute((const void*)k_newton_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute((const void*)k_newton_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -333,7 +368,8 @@ static int cluster_size_for(int ncell)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int size = 0;
-        if (cudaOccupancyMaxPotentialClusterSize(&size, (const void*)k_newton_cluster, &cfg) != cudaSuccess) size = 8;
+        if (cudaOccupancyMaxPotentialClusterSize(&size, (const void*)k_newton_cluster<float>, &cfg) != cudaSuccess)
+            size = 8;
         cudaGetLastError();
         int p = 1;
         while (p * 2 <= size && p * 2 <= kClusterMax) p *= 2;
@@ -346,9 +382,10 @@ static int cluster_size_for(int ncell)
     return G <= kClusterMax ? G : 0;
 }
 
-size_t newton_smem_bytes(int B, int G)
+size_t newton_smem_bytes(int B, int G, bool fp64)
 {
-    return sizeof(double) * ((size_t)B + 3) + sizeof(float) * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    const size_t t = fp64 ? sizeof(double) : sizeof(float);
+    return sizeof(double) * ((size_t)B + 3) + t * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
 }
 
 static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int nclusters, int block, size_t smem,
@@ -369,52 +406,59 @@ static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int n
 }
 
 static int launch_newton_cluster(int G, const long long* rho, int ncell, double dx, double nscale, int mode,
-                                 double tol, int maxit, double* phi, double* E, float* Ef, int* diag, uint32_t* status,
-                                 cudaStream_t s)
+                                 int walls, double tol, int maxit, double* phi, double* E, float* Ef, int* diag,
+                                 uint32_t* status, cudaStream_t s)
 {
     const int B = ncell / G;  // one node per thread
     if (B > 1024 || B < 2) return PE_EINVAL;
-    const size_t smem = newton_smem_bytes(B, G);
-    if (ensure_smem((const void*)k_newton_cluster, smem) != PE_OK) return PE_ECUDA;
-    FieldDesc d{rho, phi, E, Ef, diag, status, dx, nscale, tol, ncell, mode, maxit, 0};
+    const bool fp64 = walls != 0;
+    const size_t smem = newton_smem_bytes(B, G, fp64);
+    const void* k = fp64 ? (const void*)k_newton_cluster<double> : (const void*)k_newton_cluster<float>;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    FieldDesc d{rho, phi, E, Ef, diag, status, dx, nscale, tol, ncell, mode, maxit, walls ? 1 : 0};
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(attr, G, 1, B, smem, s);
-    if (cudaLaunchKernelEx(&cfg, k_newton_cluster, d) != cudaSuccess) return PE_ECUDA;
+    const cudaError_t e = fp64 ? cudaLaunchKernelEx(&cfg, k_newton_cluster<double>, d)
+                               : cudaLaunchKernelEx(&cfg, k_newton_cluster<float>, d);
+    if (e != cudaSuccess) return PE_ECUDA;
     return launch_status();
 }
 
 int newton_cluster_size(int ncell) { return cluster_size_for(ncell); }
 
-// Batched field solves: descs[R] on the device, every grid with the same cluster size G.
-int launch_newton_batch(const void* descs, int R, int G, int max_ncell, cudaStream_t s)
+// Batched field solves: descs[R] on the device, every grid with the same cluster size G;
+// fp64: the linear solves run in FP64 (needed when any grid is bounded).
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, cudaStream_t s)
 {
     const int B = max_ncell / G;
     if (B > 1024 || B < 2 || R < 1) return PE_EINVAL;
-    const size_t smem = newton_smem_bytes(B, G);
-    if (ensure_smem((const void*)k_newton_batch, smem) != PE_OK) return PE_ECUDA;
-    static bool nonportable[64] = {false};
+    const size_t smem = newton_smem_bytes(B, G, fp64);
+    const void* k = fp64 ? (const void*)k_newton_batch<double> : (const void*)k_newton_batch<float>;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    static bool nonportable[2][64] = {{false}};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PE_ECUDA;
-    if (G > 8 && !nonportable[dev]) {
-        if (cudaFuncSetAttribute((const void*)k_newton_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess)
+    if (G > 8 && !nonportable[fp64][dev]) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
             return PE_ECUDA;
-        nonportable[dev] = true;
+        nonportable[fp64][dev] = true;
     }
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(attr, G, R, B, smem, s);
-    if (cudaLaunchKernelEx(&cfg, k_newton_batch, static_cast<const FieldDesc*>(descs)) != cudaSuccess)
-        return PE_ECUDA;
+    const FieldDesc* dd = static_cast<const FieldDesc*>(descs);
+    const cudaError_t e = fp64 ? cudaLaunchKernelEx(&cfg, k_newton_batch<double>, dd)
+                               : cudaLaunchKernelEx(&cfg, k_newton_batch<float>, dd);
+    if (e != cudaSuccess) return PE_ECUDA;
     return launch_status();
 }
 
 size_t field_desc_size() { return sizeof(FieldDesc); }
 
-void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, double tol, int maxit,
-                     double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status)
+void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, int walls, double tol,
+                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status)
 {
     FieldDesc d{reinterpret_cast<const long long*>(rho), phi, E, Ef, diag, status, dx, ldexp(1.0, -(s_w + 24)), tol,
-                ncell, mode, maxit, 0};
+                ncell, mode, maxit, walls ? 1 : 0};
     memcpy(out, &d, sizeof(d));
 }
 
@@ -422,18 +466,28 @@ void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_
 
 using namespace pe;
 
-extern "C" PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode, double tol,
-                               int32_t maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
-                               void* stream)
+extern "C" PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
+                                  int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
+                                  int32_t* diag, uint32_t* status, void* stream)
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !phi || !E || !Ef || !(dx > 0.0) || maxit < 0) return PE_EINVAL;
     if (mode != PE_POISSON_BOLTZMANN && mode != PE_POISSON_LINEARIZED) return PE_EINVAL;
+    if (boundary != PE_BOUNDARY_PERIODIC && boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
     const double nscale = ldexp(1.0, -(s_w + 24));
     if (ncell >= 8 && ncell <= kFullGridMax) {
         const int G = cluster_size_for(ncell);
         if (G >= 1)
-            return launch_newton_cluster(G, reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode, tol,
-                                         maxit, phi, E, Ef, diag, status, (cudaStream_t)stream);
+            return launch_newton_cluster(G, reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode,
+                                         boundary == PE_BOUNDARY_ABSORBING, tol, maxit, phi, E, Ef, diag, status,
+                                         (cudaStream_t)stream);
     }
     return PE_EINVAL;
+}
+
+extern "C" PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode, double tol,
+                               int32_t maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
+                               void* stream)
+{
+    return pe_field_ex(rho_fx, ncell, dx, s_w, mode, PE_BOUNDARY_PERIODIC, tol, maxit, phi, E, Ef, diag, status,
+                       stream);
 }

@@ -31,10 +31,10 @@ int blocks_per_sm(const void* kernel, int block, size_t smem);
 // Batched field solves (pe_field.cu): descriptor size, descriptor builder, cluster size
 // used for a grid of ncell nodes, and the launch over R realisations of one cluster size.
 size_t field_desc_size();
-void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, double tol, int maxit,
-                     double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status);
+void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, int walls, double tol,
+                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status);
 int newton_cluster_size(int ncell);
-int launch_newton_batch(const void* descs, int R, int G, int max_ncell, cudaStream_t s);
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, cudaStream_t s);
 
 // Batched particle passes (pe_particles.cu).
 size_t push_desc_size();

@@ -45,6 +45,11 @@ struct PushParams {
     // phase-space sample (PS modes): samp_n is the histogram [(ncell >> bin_shift)][nv]
     int nv, ps_width;
     float vmin, inv_dv;
+    // bounded grid (walls at nodes 0 and ncell-1, Section 4.2): a particle whose drift ends
+    // outside [0, (ncell-1) dx) is absorbed (weight 0 written to w_out, parked on the wall node
+    // with v = 0); particles of weight 0 are not moved; co-moving targets outside are dropped
+    int walls;
+    float* w_out;
 };
 
 enum Mode {
@@ -80,20 +85,35 @@ __device__ __forceinline__ int32_t fx_weight(float x, float scale, bool* ovf)
 
 constexpr int kThreads = 256;
 
+// True when cell c + k (k = fl, an integer-valued float) lies between the walls,
+// [0, ncell - 1); NaN counts as outside.
+__device__ __forceinline__ bool inside_walls(const PushParams& P, int c, float fl)
+{
+    return fl >= -(float)c && fl < (float)(P.ncell - 1 - c);
+}
+
 template <int MODE>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
                                         LaneWindow& lw, BinAcc& bacc, const SmemGrid& grho,
                                         const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
                                         const BinGrid& bsm, const PSGrid& gps, PSAcc& acc, bool* ovf, int& c_out,
-                                        float& th_out, float& v_out)
+                                        float& th_out, float& v_out, float& w_out)
 {
     using Tr = ModeTraits<MODE>;
     c_out = c;
     th_out = th;
     v_out = vv;
+    w_out = ww;
     if ((unsigned)c >= (unsigned)P.ncell) {
         raise_flag(P.status, PE_FLAG_RANGE);
         return;
+    }
+    if (P.walls) {
+        if (ww == 0.0f) return;  // absorbed: frozen, carries nothing
+        if (c >= P.ncell - 1) {  // a live particle must lie between the walls
+            raise_flag(P.status, PE_FLAG_RANGE);
+            return;
+        }
     }
     const int32_t wq = fx_weight(ww, P.wscale, ovf);
     if (MODE == kDeposit) {
@@ -109,16 +129,18 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         const float E0c = __ldg(P.E0f + c), E0c1 = __ldg(P.E0f + c1);
         const float E0p = fmaf(th, E0c1 - E0c, E0c);
         const float xs = fmaf(P.tau_dx, vbar, th);
-        const float fl = floorf(xs);
+        float fl = floorf(xs);
         float ths = xs - fl;
-        int k = (int)fl;
         if (ths >= 1.0f) {
             ths = 0.0f;
-            k += 1;
+            fl += 1.0f;
         }
+        const int k = (int)fl;
         const int cs = (c + k) & P.mask, cs1 = (cs + 1) & P.mask;
         const float vt = fmaf(P.qm_tau, E0p, vbar);
-        if (Tr::ps) {
+        // bounded grid: a target beyond a wall has left the domain by t_{n+1}
+        const bool counted = !P.walls || inside_walls(P, c, fl);
+        if (Tr::ps && counted) {
             // Section 3.3 restriction: CIC in x (summed over the coarse bin), nearest cell in v
             const float jf = floorf((vt - P.vmin) * P.inv_dv);
             const int j = jf < 0.0f ? 0 : (jf >= (float)P.nv ? P.nv - 1 : (int)jf);
@@ -131,41 +153,47 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
                 gps.add(b1 * P.nv + j, (long long)qn.right);
             }
         }
-        const int32_t mq = Tr::ps ? 0 : fx_weight(ww * vt, P.pscale, ovf);
-        if (Tr::ps) {
-            // the phase-space sample above replaces the moment samples
-        } else if (Tr::binned) {
-            const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
-            if (b0 == b1) {  // both CIC parts in one bin: the whole particle
-                bacc.add(b0, wq, mq, bsn, bsm);
+        if (!Tr::ps && counted) {
+            const int32_t mq = fx_weight(ww * vt, P.pscale, ovf);
+            if (Tr::binned) {
+                const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
+                if (b0 == b1) {  // both CIC parts in one bin: the whole particle
+                    bacc.add(b0, wq, mq, bsn, bsm);
+                } else {
+                    const FxSplit qn = fx_split(wq, ths), qp = fx_split(mq, ths);
+                    bsn.add_part(b0, qn.left);
+                    bsn.add_part(b1, qn.right);
+                    bsm.add_part(b0, qp.left);
+                    bsm.add_part(b1, qp.right);
+                }
             } else {
-                const FxSplit qn = fx_split(wq, ths), qp = fx_split(mq, ths);
-                bsn.add_part(b0, qn.left);
-                bsn.add_part(b1, qn.right);
-                bsm.add_part(b0, qp.left);
-                bsm.add_part(b1, qp.right);
+                const FxSplit qn = fx_split(wq, ths);
+                const FxSplit qp = fx_split(mq, ths);
+                gsn.add(cs, qn.left);
+                gsn.add(cs1, qn.right);
+                gsm.add(cs, qp.left);
+                gsm.add(cs1, qp.right);
             }
-        } else {
-            const FxSplit qn = fx_split(wq, ths);
-            const FxSplit qp = fx_split(mq, ths);
-            gsn.add(cs, qn.left);
-            gsn.add(cs1, qn.right);
-            gsm.add(cs, qp.left);
-            gsm.add(cs1, qp.right);
         }
     }
     if (Tr::push) {
         // Section 2.2 leapfrog: kick with the gathered field, then drift
         const float vn = fmaf(P.kick * P.qm_dt, Ep, vv);
         const float s = fmaf(vn, P.dt_dx, th);
-        const float fl = floorf(s);
+        float fl = floorf(s);
         float thn = s - fl;
-        int k = (int)fl;
         if (thn >= 1.0f) {
             thn = 0.0f;
-            k += 1;
+            fl += 1.0f;
         }
-        const int cn = (c + k) & P.mask;
+        if (P.walls && !inside_walls(P, c, fl)) {  // absorbed at the wall it crossed
+            c_out = (fl < 0.0f) ? 0 : P.ncell - 1;
+            th_out = 0.0f;
+            v_out = 0.0f;
+            w_out = 0.0f;
+            return;
+        }
+        const int cn = (c + (int)fl) & P.mask;
         c_out = cn;
         th_out = thn;
         v_out = vn;
@@ -243,15 +271,21 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         const float4 va = kNeedV ? v4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 wa = __ldg(w4 + g);
         int4 co;
-        float4 to, vo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w);
+        float4 to, vo, wo;
+        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x,
+                      wo.x);
+        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y,
+                      wo.y);
+        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z,
+                      wo.z);
+        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w,
+                      wo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
+            if (P.walls && (wo.x != wa.x || wo.y != wa.y || wo.z != wa.z || wo.w != wa.w))
+                reinterpret_cast<float4*>(P.w_out)[g] = wo;  // an absorption in this group
         }
         if (kPS) {  // one warp-aggregated add per group of four particles per lane
             ps_add_warp(gps, acc.key, acc.val);
@@ -264,13 +298,16 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     }
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {  // ragged tail (< 4 particles)
         int co;
-        float to, vo;
+        float to, vo, wo;
         const float vi = kNeedV ? P.v[i] : 0.f;
-        process<MODE>(P, P.cell[i], P.theta[i], vi, P.w[i], lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo);
+        const float wi = P.w[i];
+        process<MODE>(P, P.cell[i], P.theta[i], vi, wi, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo,
+                      wo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
             P.v[i] = vo;
+            if (P.walls && wo != wi) P.w_out[i] = wo;
         }
         if (kPS) {
             ps_add_warp(gps, acc.key, acc.val);
@@ -449,6 +486,201 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     if (dep) grho.flush();
 }
 
+// ------------------------------------------------------------------ equal-weight loading
+
+// Scratch of the equal-weight loading: cumulative cell masses and first particle of each
+// cell. Layout in the caller's scratch: double C[ncl + 1], int64 first[ncl + 1], double MoN.
+struct EqTable {
+    const double* C;
+    const long long* first;
+    const double* MoN;
+};
+
+constexpr int kEqThreads = 1024;
+
+// One block: cell masses m_c = (n_c f_c + n_{c+1} f_{c+1}) / 2 of the linear profile over
+// the ncl = ncell - 1 cells between the walls (f = wall_factor on the wall nodes, 1 inside),
+// their cumulative sums C (each thread sums a contiguous run of cells, then an exclusive scan
+// of the run totals in a fixed order), M = C[ncl], MoN = M / n and
+// first[c] = ceil(C_c n / M - 1/2), the first particle i with (i + 1/2) M / n >= C_c.
+__global__ void __launch_bounds__(kEqThreads) k_eq_table(const float* __restrict__ prof_n, int ncell,
+                                                        float wall_factor, int64_t n, double* C, long long* first,
+                                                        double* MoN, uint32_t* status)
+{
+    __shared__ double part[kEqThreads];
+    const int ncl = ncell - 1;
+    const int per = (ncl + kEqThreads - 1) / kEqThreads;
+    const int t = threadIdx.x;
+    const int c0 = t * per, c1 = (c0 + per < ncl) ? c0 + per : ncl;
+    auto dens = [&](int j) {
+        const double v = (double)prof_n[j];
+        return (j == 0 || j == ncell - 1) ? v * (double)wall_factor : v;
+    };
+    double run = 0.0;
+    for (int c = c0; c < c1; ++c) run += 0.5 * (dens(c) + dens(c + 1));
+    part[t] = run;
+    __syncthreads();
+    if (t == 0) {  // exclusive scan of the 1024 run totals (serial: fixed order, ~1k adds)
+        double acc = 0.0;
+        for (int k = 0; k < kEqThreads; ++k) {
+            const double v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    double acc = part[t];
+    for (int c = c0; c < c1; ++c) {
+        C[c] = acc;
+        acc += 0.5 * (dens(c) + dens(c + 1));
+    }
+    if (c1 == ncl && c0 < c1) C[ncl] = acc;
+    __syncthreads();
+    const double M = C[ncl];
+    const bool ok = M > 0.0 && isfinite(M);
+    if (t == 0) {
+        *MoN = ok ? M / (double)n : 0.0;
+        if (!ok) raise_flag(status, PE_FLAG_RANGE);
+    }
+    for (int c = t; c <= ncl; c += kEqThreads) {
+        long long f;
+        if (!ok) {
+            f = (c == 0) ? 0 : n;  // no mass: every particle in cell 0 with weight 0
+        } else {
+            const double q = ceil(C[c] * ((double)n / M) - 0.5);
+            f = q < 0.0 ? 0 : (q > (double)n ? n : (long long)q);
+        }
+        first[c] = (c == ncl) ? n : f;
+    }
+}
+
+struct EqParams {
+    int32_t* cell;
+    float* theta;
+    float* v;
+    float* w;
+    int64_t n;
+    int64_t chunk;
+    int ncell, mask;
+    float wall_factor;
+    const float* prof_n;
+    const float* prof_u;
+    EqTable tab;
+    float v_th, wscale;
+    uint32_t half, shift;
+    unsigned long long* rho;
+    int rho_width;
+    uint32_t* status;
+};
+
+// Cell of particle i: the largest c in [0, ncl) with first[c] <= i (binary search; always
+// in range whatever the table holds).
+__device__ __forceinline__ int eq_cell_of(const EqParams& P, long long i)
+{
+    int lo = 0, hi = P.ncell - 1;  // first[lo] <= i < first[hi] on a valid table
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(P.tab.first + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+{
+    // advance from the previous particle's cell (consecutive i rarely change cell)
+    while (c < P.ncell - 2 && __ldg(P.tab.first + c + 1) <= (long long)i) ++c;
+    const double C0 = __ldg(P.tab.C + c), C1 = __ldg(P.tab.C + c + 1);
+    const double MoN = __ldg(P.tab.MoN);
+    const double mc = C1 - C0;
+    double r = mc > 0.0 ? (((double)i + 0.5) * MoN - C0) / mc : 0.5;
+    r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+    float n0 = __ldg(P.prof_n + c), n1 = __ldg(P.prof_n + c + 1);
+    if (c == 0) n0 *= P.wall_factor;
+    if (c + 1 == P.ncell - 1) n1 *= P.wall_factor;
+    const float sum = n0 + n1;
+    const float sig = sum > 0.0f ? (n1 - n0) / sum : 0.0f;
+    // mass of the linear density 1 + sig (2t - 1) up to t is t + sig (t^2 - t) = r
+    const float rf = (float)r;
+    const float om = 1.0f - sig;
+    const float den = om + sqrtf(fmaxf(om * om + 4.0f * sig * rf, 0.0f));
+    float t = den > 0.0f ? 2.0f * rf / den : 0.0f;
+    t = fminf(fmaxf(t, 0.0f), 0.99999994f);  // stay inside the cell (largest float below 1)
+    th = t;
+    const float u0 = __ldg(P.prof_u + c), u1 = __ldg(P.prof_u + c + 1);
+    const float uX = fmaf(t, u1 - u0, u0);
+    ww = (float)MoN;
+    const uint32_t Bi = __brev(i) + P.half + P.shift;
+    const bool upper = (Bi & 0x80000000u) != 0u;
+    const uint32_t bs = upper ? ~Bi : Bi;
+    const float b = fmaf(__uint2float_rn(bs), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float z = normcdfinvf(b);
+    vv = fmaf(P.v_th, upper ? -z : z, uX);
+}
+
+__global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
+{
+    extern __shared__ uint32_t smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const bool dep = P.rho != nullptr;
+    const int c_first = (begin < end) ? eq_cell_of(P, begin) : 0;
+    SmemGrid grho{};
+    if (dep) {
+        grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        grho.zero();
+    }
+    __syncthreads();
+
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    LaneWindow lw;
+    lw.reset((c_first - 1) & P.mask);
+    bool ovf = false;
+    int4* cell4 = reinterpret_cast<int4*>(P.cell);
+    float4* th4 = reinterpret_cast<float4*>(P.theta);
+    float4* v4 = reinterpret_cast<float4*>(P.v);
+    float4* w4 = reinterpret_cast<float4*>(P.w);
+    for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+        int4 c;
+        float4 t, vv, ww;
+        const uint32_t i0 = (uint32_t)(g << 2);
+        c.x = eq_cell_of(P, i0);
+        eq_one(P, i0, c.x, t.x, vv.x, ww.x);
+        c.y = c.x;
+        eq_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
+        c.z = c.y;
+        eq_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
+        c.w = c.z;
+        eq_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        cell4[g] = c;
+        th4[g] = t;
+        v4[g] = vv;
+        w4[g] = ww;
+        if (dep) {
+            lw.add(c.x, fx_split(fx_weight(ww.x, P.wscale, &ovf), t.x), grho);
+            lw.add(c.y, fx_split(fx_weight(ww.y, P.wscale, &ovf), t.y), grho);
+            lw.add(c.z, fx_split(fx_weight(ww.z, P.wscale, &ovf), t.z), grho);
+            lw.add(c.w, fx_split(fx_weight(ww.w, P.wscale, &ovf), t.w), grho);
+        }
+    }
+    for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
+        int c = eq_cell_of(P, i);
+        float t, vv, ww;
+        eq_one(P, (uint32_t)i, c, t, vv, ww);
+        P.cell[i] = c;
+        P.theta[i] = t;
+        P.v[i] = vv;
+        P.w[i] = ww;
+        if (dep) lw.add(c, fx_split(fx_weight(ww, P.wscale, &ovf), t), grho);
+    }
+    if (dep) lw.flush(grho);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
+    __syncthreads();
+    if (dep) grho.flush();
+}
+
 // ------------------------------------------------------------------ counting sort
 
 __device__ __forceinline__ void warp_count(unsigned* hist, int c)
@@ -603,6 +835,7 @@ static bool particles_ok(const void* a, const void* b, const void* c, const void
 static bool sample_ok(const pe_sample_args* s, int ncell)
 {
     if (!s || !s->E0f || !s->sample_fx || !aligned16(s->sample_fx)) return false;
+    if (s->boundary != PE_BOUNDARY_PERIODIC && s->boundary != PE_BOUNDARY_ABSORBING) return false;
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
     if (s->n_v < 0 || s->n_v > 1024) return false;
     if (s->n_v > 0) {
@@ -713,12 +946,14 @@ extern "C" PE_API int pe_deposit(const int32_t* cell, const float* theta, const 
     return launch_particles<kDeposit>(P, (cudaStream_t)stream);
 }
 
-extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
-                              int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w, int64_t* rho_fx,
-                              const pe_sample_args* sample, uint32_t* status, void* stream)
+extern "C" PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef,
+                                 int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w,
+                                 int32_t boundary, int64_t* rho_fx, const pe_sample_args* sample, uint32_t* status,
+                                 void* stream)
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !Ef || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
-    if (sample && (!sample_ok(sample, ncell) || sample->s_w != s_w)) return PE_EINVAL;
+    if (boundary != PE_BOUNDARY_PERIODIC && boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
+    if (sample && (!sample_ok(sample, ncell) || sample->s_w != s_w || sample->boundary != boundary)) return PE_EINVAL;
     PushParams P{};
     P.cell = cell;
     P.theta = theta;
@@ -734,6 +969,8 @@ extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float
     P.wscale = ldexpf(1.0f, s_w);
     P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
     P.status = status;
+    P.walls = boundary == PE_BOUNDARY_ABSORBING;
+    P.w_out = w;
     if (sample) {
         P.E0f = sample->E0f;
         P.tau_dx = sample->tau * sample->inv_dx;
@@ -754,6 +991,16 @@ extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float
     return launch_particles<kPush>(P, (cudaStream_t)stream);
 }
 
+extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
+                              int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w, int64_t* rho_fx,
+                              const pe_sample_args* sample, uint32_t* status, void* stream)
+{
+    if (sample && sample->boundary != PE_BOUNDARY_PERIODIC) return PE_EINVAL;
+    // periodic: the weights are only read
+    return pe_push_ex(cell, theta, v, const_cast<float*>(w), n, Ef, ncell, dt_over_dx, qm_dt, kick, s_w,
+                      PE_BOUNDARY_PERIODIC, rho_fx, sample, status, stream);
+}
+
 extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
                                 const float* Ef, int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample,
                                 uint32_t* status, void* stream)
@@ -761,6 +1008,7 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
     if (!is_pow2(ncell) || ncell < 8 || !Ef || !particles_ok(cell, theta, v, w, n) || !sample_ok(sample, ncell))
         return PE_EINVAL;
     PushParams P{};
+    P.walls = sample->boundary == PE_BOUNDARY_ABSORBING;
     P.cell = const_cast<int32_t*>(cell);
     P.theta = const_cast<float*>(theta);
     P.v = const_cast<float*>(v);
@@ -831,6 +1079,54 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start<<<grid, block, smem, s>>>(P);
     return launch_status();
+}
+
+extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                           const float* prof_n, const float* prof_u, float wall_factor, float v_th,
+                                           uint64_t seed, int32_t s_w, void* scratch, int64_t* rho_fx,
+                                           uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !prof_n || !prof_u || !scratch || !particles_ok(cell, theta, v, w, n))
+        return PE_EINVAL;
+    if (n == 0 || n >= (int64_t(1) << 32) || ((uintptr_t)scratch & 15u) || !(wall_factor >= 0.0f))
+        return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ncl = ncell - 1;
+    double* C = static_cast<double*>(scratch);
+    long long* first = reinterpret_cast<long long*>(C + ncl + 1);
+    double* MoN = reinterpret_cast<double*>(first + ncl + 1);
+    k_eq_table<<<1, kEqThreads, 0, s>>>(prof_n, ncell, wall_factor, n, C, first, MoN, status);
+    EqParams P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.wall_factor = wall_factor;
+    P.prof_n = prof_n;
+    P.prof_u = prof_u;
+    P.tab = EqTable{C, first, MoN};
+    P.v_th = v_th;
+    P.wscale = ldexpf(1.0f, s_w);
+    P.half = (uint32_t)(2147483648.0 / (double)n);
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL;  // splitmix64 of the seed: the shift is its upper half
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    P.shift = (uint32_t)(z >> 32);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.rho_width = rho_fx ? (ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes) : 0;
+    P.status = status;
+    const int block = 256;
+    const size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
+    const void* k = (const void*)k_quiet_start_equal;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    const int grid = grid_for(k, block, smem, n, &P.chunk);
+    if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    k_quiet_start_equal<<<grid, block, smem, s>>>(P);
+    return launch_status(2);
 }
 
 // Device address of g_sort_static on the current device, looked up once per device.

@@ -12,6 +12,11 @@ Section 4; normalised units lambda_D = omega_pi = c_s = 1, ion q/m = 1):
 * ``iaw_large``  — ion-wave steepening at scale: periodic 4096 cells (dx=0.5,
   L=2048), 2^24 ions, amplitude 0.5 on the longest mode, v_th=1, K=20, M=10,
   50 macro-steps, 256 coarse coefficients per moment.
+* ``slab``       — slab expansion into vacuum (Section 4.2's test, uniform-slab
+  variant): bounded grid of 8192 cells (dx=0.5, absorbing walls), n = 1 on the
+  central eighth and vacuum elsewhere, 2^25 equal-weight ions (none in the vacuum
+  cells), v_th=1, dt=0.1, K=30, M=8, 40 macro-steps, 512 coarse coefficients per
+  moment.
 """
 from __future__ import annotations
 
@@ -22,6 +27,8 @@ WORKLOADS = {
                       n_coarse=16, macro_steps=5, wavelet="haar"),
     "iaw_large": dict(ncell=4096, L=2048.0, N=1 << 24, amplitude=0.5, v_th=1.0, dt=0.1, K=20, M=10,
                       n_coarse=256, macro_steps=50, wavelet="haar"),
+    "slab": dict(ncell=8192, L=4096.0, N=1 << 25, amplitude=0.0, v_th=1.0, dt=0.1, K=30, M=8,
+                 n_coarse=512, macro_steps=40, wavelet="haar", boundary="absorbing"),
 }
 
 

@@ -302,3 +302,24 @@ def test_pic_walls_charge_accounting_is_exact():
     q1 = int(orc.deposit_fx(st.cell, st.theta, st.w, ncell, s_w).sum())
     assert q1 + (int(wq[gone].sum()) << 24) == q0
     assert np.all((st.cell[~gone] >= 0) & (st.cell[~gone] < ncell - 1))
+
+
+def test_restrict_of_lift_walls_reproduces_coarse_state():
+    # lifting (refine, clamp, wall deposits doubled to densities, equal-weight loading) followed
+    # by the tau = 0 restriction returns the coarse state up to the loading's quadrature error;
+    # the coarse state is non-zero at the walls, so the wall doubling is exercised
+    ncell, nc, N = 256, 32, 256 * 512
+    dx = 0.5
+    j = np.arange(ncell)
+    dens = 1.0 + 0.4 * np.cos(np.pi * 3 * j / (ncell - 1))
+    dep = dens.copy()
+    dep[[0, -1]] *= 0.5
+    mom = 0.1 * dep
+    c = np.stack([orc.coarsen(dep, nc), orc.coarsen(mom, nc)])
+    cfg = dict(ncell=ncell, N=N, v_th=0.0, wavelet="haar")
+    st = orc.lift_walls(c, cfg, seed=3)
+    d, m = orc.restrict_sample_walls(st, st.v, np.zeros(ncell), ncell, dx, 0.0, 1.0)
+    back = np.stack([orc.coarsen(d, nc), orc.coarsen(m, nc)])
+    assert np.max(np.abs(back - c)) < 2e-3 * np.max(np.abs(c))
+    # total charge is exact: sum of the weights = sum of the refined deposits
+    assert st.w.sum() == pytest.approx(orc.refine(c[0], ncell).sum(), rel=1e-12)
