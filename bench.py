@@ -272,6 +272,7 @@ def run_gpu(args):
         # ---------------- time to solution and accuracy against a resolved plain-PIC run
         acc, want, checks = run_accuracy(dev, cfg, pb) if not args.no_accuracy else (None, None, None)
         sur = run_surrogate(dev, cfg, pb, want, checks) if (acc is not None and not args.no_surrogate) else None
+        slab = run_slab(dev, pb) if not args.no_slab else None
         # ---------------- ensemble of 64 realisations of log-uniform sizes (pe_batch)
         ens = run_ensemble(dev, max(args.steps // 2, 2), 3, rank) if not args.no_ensemble else None
     clocks = sampler.stop()
@@ -319,6 +320,8 @@ def run_gpu(args):
         line["time_to_solution"] = acc
     if sur is not None:
         line["surrogate"] = sur
+    if slab is not None:
+        line["slab"] = slab
     if ens is not None:
         t_ens = max_over_ranks(ens["seconds"])
         line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10",
@@ -527,6 +530,55 @@ def _eps(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
 
 
+def run_slab(dev, pb):
+    """Slab expansion into vacuum (bounded grid, absorbing walls): projective steps with the
+    moment coarse variables vs plain GPU PIC to the same end time, time to solution and the
+    coarse-density error (Section 4.1.1's measure) at three times."""
+    import numpy as np
+    import torch
+
+    from paper_1610_01071_gb300 import inputs
+
+    w = inputs.workload("slab")
+    c = pb.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"],
+                       v_th=w["v_th"], wavelet=w["wavelet"], seed=21, sort_every=20, newton_tol=1e-10,
+                       newton_maxit=80, boundary="absorbing")
+    steps = w["macro_steps"]
+    per = int(round(w["dT"] / w["dt"]))
+    checks = sorted({max(1, steps // 5), steps // 2, steps})
+    ef, ref = pb.Context(c, device=dev), pb.Context(c, device=dev)
+    ef.load_initial(profile="slab")
+    ref.load_initial(profile="slab")
+    q0 = ef.moments()["charge"]
+    got = {}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for m in range(1, steps + 1):
+        ef.step()
+        if m in checks:
+            got[m] = ef.get_coarse()[0].clone()
+    torch.cuda.synchronize(dev)
+    t_proj = time.perf_counter() - t0
+    want = {}
+    t0 = time.perf_counter()
+    done = 0
+    for m in checks:
+        ref.pic_steps((m - done) * per)
+        done = m
+        want[m] = ref.measure()[0].clone()
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    eps = {str(round(m * w["dT"])): _eps(got[m].cpu().numpy(), want[m].cpu().numpy()) for m in checks}
+    q_ref = ref.moments()["charge"]
+    return {"workload": "slab expansion: bounded 8192 cells, absorbing walls, uniform slab on the central "
+                        "eighth, 2^25 equal-weight ions, v_th=1, K=30, M=8, 40 macro steps, 512 coarse per moment",
+            "T_end": steps * w["dT"], "projective_s": t_proj, "plain_pic_s": t_plain, "speedup": t_plain / t_proj,
+            "particle_steps_per_s": {"projective": float(w["N"]) * w["K"] * steps / t_proj,
+                                     "plain_pic": float(w["N"]) * steps * per / t_plain},
+            "eps_coarse_density_at_T": eps, "charge_left_plain_pic": q_ref / q0,
+            "status": [ef.sync_status(), ref.sync_status()]}
+
+
 def run_surrogate(dev, cfg, pb, want, checks):
     """The learned coarse-derivative surrogate on the ion-wave workload: training pairs
     (c at the start of a macro step, that step's least-squares slope) from projective runs
@@ -661,6 +713,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-slab", action="store_true")
     ap.add_argument("--kernel", default=None, help="time one kernel alone (profiling mode)")
     args = ap.parse_args()
     if args.kernel:
