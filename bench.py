@@ -324,7 +324,8 @@ def run_gpu(args):
         line["slab"] = slab
     if ens is not None:
         t_ens = max_over_ranks(ens["seconds"])
-        line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10",
+        line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10, "
+                                        "odd: periodic sinusoid, even: bounded slab",
                             "value": sum_over_ranks(ens["particle_steps"]) / t_ens, "unit": UNIT,
                             "ms_per_step": 1e3 * t_ens / ens["steps"], "particles": ens["particles"],
                             "tuned_chunk": ens["tuned_chunk"], "steps": ens["steps"]}
@@ -425,7 +426,8 @@ def run_kernel(args):
 
 def ensemble_sizes(count=64, seed=4):
     """Ensemble workload: grids of 2^U cells, U uniform in 9..13, and 2^V ions, V uniform
-    in 18..22 (log-uniform sizes), sinusoidal densities with amplitude U(0.05, 0.6)."""
+    in 18..22 (log-uniform sizes); odd realisations a periodic sinusoid of amplitude
+    U(0.05, 0.6), even ones the bounded slab (absorbing walls, uniform central eighth)."""
     import numpy as np
 
     rng = np.random.default_rng(seed)
@@ -433,7 +435,7 @@ def ensemble_sizes(count=64, seed=4):
     for i in range(count):
         ncell = 1 << int(rng.integers(9, 14))
         n = 1 << int(rng.integers(18, 23))
-        out.append((ncell, max(n, ncell), float(rng.uniform(0.05, 0.6))))
+        out.append((ncell, max(n, ncell), float(rng.uniform(0.05, 0.6)), i % 2 == 0))
     return out
 
 
@@ -677,11 +679,14 @@ def run_ensemble(dev, steps, warmup, rank=0):
 
     K, M, dt = 20, 10, 0.1
     ctxs = []
-    for i, (ncell, n, amp) in enumerate(ensemble_sizes()):
+    for i, (ncell, n, amp, slab) in enumerate(ensemble_sizes()):
         c = pb.make_config(ncell, min(256, ncell // 16), K, n, 0.5 * ncell, dt, M * K * dt, seed=7000 + 97 * i + rank,
-                           newton_tol=1e-10)
+                           newton_tol=1e-10, newton_maxit=80, boundary="absorbing" if slab else "periodic")
         ctx = pb.Context(c, device=dev)
-        ctx.load_initial(amp)
+        if slab:
+            ctx.load_initial(profile="slab")
+        else:
+            ctx.load_initial(amp)
         ctxs.append(ctx)
     batch = pb.Batch(ctxs)
     chunk = batch.tune()

@@ -37,8 +37,7 @@ int layout_for(pe_ctx* const* ctxs, int n, Layout* L)
     int64_t rho = 0, row = 0, items = 0;
     for (int r = 0; r < n; ++r) {
         const pe_ctx* x = ctxs[r];
-        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps || x->walls)
-            return PE_EINVAL;
+        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps) return PE_EINVAL;
         rho += x->cfg.ncell;
         row += 2 * (int64_t)x->nb;
         items += (x->cfg.nparticles + kMinChunk - 1) / kMinChunk;
@@ -77,9 +76,13 @@ struct pe_batch {
     int K;
     int64_t chunk;
     int nitems;
-    int max_ncell_cluster, max_ncell_single, max_nb;
-    std::vector<int> cluster_ids, single_ids;  // realisations by field-solve cluster size
-    int G;                                     // cluster size of the multi-block group
+    int max_ncell, max_nb;
+    // Field-solve groups, one launch each: (multi-block clusters of size G | single blocks) x
+    // (FP32 | FP64 Jacobian solve: bounded grids). Every realisation is solved exactly as its
+    // context alone would solve it.
+    std::vector<int> field_ids[4];
+    int field_maxn[4];
+    int G;  // cluster size of the multi-block groups
     std::vector<int64_t> rho_off, e0_off, samp_off;
     std::vector<int> banks;  // particle bank of each context when the descriptors were built
     cudaGraphExec_t graph;
@@ -113,8 +116,13 @@ static int build_descs(pe_batch* b)
 {
     const int R = (int)b->ctx.size();
     std::vector<char> push(push_desc_size() * R), proj(proj_desc_size() * R);
-    std::vector<char> fc(field_desc_size() * R), fs(field_desc_size() * R);
-    int nc = 0, ns = 0;
+    std::vector<char> fd(field_desc_size() * R);
+    std::vector<int> slot(R, 0);  // position of each realisation's field descriptor
+    {
+        int o = 0;
+        for (int g = 0; g < 4; ++g)
+            for (int r : b->field_ids[g]) slot[r] = o++;
+    }
     int64_t* rho_all = reinterpret_cast<int64_t*>(at(b, b->L.rho));
     float* e0_all = reinterpret_cast<float*>(at(b, b->L.e0));
     int64_t* samp_all = reinterpret_cast<int64_t*>(at(b, b->L.samp));
@@ -127,19 +135,16 @@ static int build_descs(pe_batch* b)
         make_push_desc(push.data() + push_desc_size() * r, x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles,
                        x->Ef, c.ncell, (float)(c.dt / x->dx), (float)(c.qm * c.dt), x->s_w, rho_all + b->rho_off[r],
                        e0_all + b->e0_off[r], c.dT, c.dt, (float)(1.0 / x->dx), (float)c.qm, c.comoving,
-                       x->s_p, x->bin_shift, samp_all + b->samp_off[r], b->L.samp_row, x->status);
+                       x->s_p, x->bin_shift, samp_all + b->samp_off[r], b->L.samp_row, x->walls, x->status);
         make_proj_desc(proj.data() + proj_desc_size() * r, samp_all + b->samp_off[r], b->L.samp_row, c.ncell, x->nc,
                        x->s_w, x->s_p, x->csamples, x->coarse, x->slope);
-        const bool cl = newton_cluster_size(c.ncell) == b->G && b->G > 1;
-        char* dst = cl ? fc.data() + field_desc_size() * nc++ : fs.data() + field_desc_size() * ns++;
-        make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, 0, c.newton_tol,
+        char* dst = fd.data() + field_desc_size() * slot[r];
+        make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, x->walls, c.newton_tol,
                         c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status);
     }
     if (cudaMemcpy(at(b, b->L.push), push.data(), push.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(at(b, b->L.proj), proj.data(), proj.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(at(b, b->L.field), fc.data(), field_desc_size() * nc, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(at(b, b->L.field) + field_desc_size() * nc, fs.data(), field_desc_size() * ns,
-                   cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(at(b, b->L.field), fd.data(), fd.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return PE_ECUDA;
     return PE_OK;
 }
@@ -147,11 +152,13 @@ static int build_descs(pe_batch* b)
 static int field_all(pe_batch* b)
 {
     const char* base = at(b, b->L.field);
-    if (!b->cluster_ids.empty())
-        PE_TRY(launch_newton_batch(base, (int)b->cluster_ids.size(), b->G, b->max_ncell_cluster, false, b->stream));
-    if (!b->single_ids.empty())
-        PE_TRY(launch_newton_batch(base + field_desc_size() * b->cluster_ids.size(), (int)b->single_ids.size(), 1,
-                                   b->max_ncell_single, false, b->stream));
+    size_t o = 0;
+    for (int g = 0; g < 4; ++g) {
+        const int n = (int)b->field_ids[g].size();
+        if (n) PE_TRY(launch_newton_batch(base + field_desc_size() * o, n, g < 2 ? b->G : 1, b->field_maxn[g], g & 1,
+                                          b->stream));
+        o += (size_t)n;
+    }
     return PE_OK;
 }
 
@@ -174,17 +181,12 @@ static int burst_restrict_project(pe_batch* b)
         if (cudaMemsetAsync(samp_all + (size_t)p * b->L.samp_row, 0, row_bytes, s) != cudaSuccess) return PE_ECUDA;
         if (p == b->K) {
             PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, p, 1.0f, counter,
-                                          b->max_ncell_cluster > b->max_ncell_single ? b->max_ncell_cluster
-                                                                                     : b->max_ncell_single,
-                                          b->max_nb, s));
+                                          b->max_ncell, b->max_nb, s));
             break;
         }
         if (cudaMemsetAsync(rho_all, 0, 8 * (size_t)b->L.rho_total, s) != cudaSuccess) return PE_ECUDA;
         PE_TRY(launch_particles_batch(0, at(b, b->L.push), at(b, b->L.items), b->nitems, p, p == 0 ? 0.5f : 1.0f,
-                                      counter,
-                                      b->max_ncell_cluster > b->max_ncell_single ? b->max_ncell_cluster
-                                                                                 : b->max_ncell_single,
-                                      b->max_nb, s));
+                                      counter, b->max_ncell, b->max_nb, s));
         PE_TRY(field_all(b));
     }
     const pe_config& c0 = b->ctx[0]->cfg;
@@ -227,7 +229,8 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
     }
     b->G = 1;
     for (int r = 0; r < n; ++r) b->G = newton_cluster_size(ctxs[r]->cfg.ncell) > b->G ? newton_cluster_size(ctxs[r]->cfg.ncell) : b->G;
-    b->max_ncell_cluster = b->max_ncell_single = 0;
+    b->max_ncell = 0;
+    for (int g = 0; g < 4; ++g) b->field_maxn[g] = 0;
     b->max_nb = 0;
     int64_t ro = 0, so = 0;
     for (int r = 0; r < n; ++r) {
@@ -238,13 +241,11 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
         ro += x->cfg.ncell;
         so += 2 * (int64_t)x->nb;
         if (x->nb > b->max_nb) b->max_nb = x->nb;
-        if (b->G > 1 && newton_cluster_size(x->cfg.ncell) == b->G) {
-            b->cluster_ids.push_back(r);
-            if (x->cfg.ncell > b->max_ncell_cluster) b->max_ncell_cluster = x->cfg.ncell;
-        } else {
-            b->single_ids.push_back(r);
-            if (x->cfg.ncell > b->max_ncell_single) b->max_ncell_single = x->cfg.ncell;
-        }
+        if (x->cfg.ncell > b->max_ncell) b->max_ncell = x->cfg.ncell;
+        const bool cl = b->G > 1 && newton_cluster_size(x->cfg.ncell) == b->G;
+        const int g = (cl ? 0 : 2) + (x->walls ? 1 : 0);
+        b->field_ids[g].push_back(r);
+        if (x->cfg.ncell > b->field_maxn[g]) b->field_maxn[g] = x->cfg.ncell;
     }
     int rc = build_descs(b);
     if (rc == PE_OK) rc = build_items(b);
@@ -276,7 +277,7 @@ extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
 {
     if (!b) return PE_EINVAL;
     unsigned* counter = reinterpret_cast<unsigned*>(at(b, b->L.counter));
-    const int maxn = b->max_ncell_cluster > b->max_ncell_single ? b->max_ncell_cluster : b->max_ncell_single;
+    const int maxn = b->max_ncell;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PE_ECUDA;
     float best = 1e30f;
@@ -334,9 +335,14 @@ extern "C" PE_API int pe_batch_step(pe_batch* b)
         const int k = x->bank;
         if (!fresh) {
             PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, b->stream));
-            PE_TRY(pe_quiet_start(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell, x->prof,
-                                  x->prof + c.ncell, (float)c.v_th, pe_ctx_lift_seed(x), x->s_w,
-                                  rho_all + b->rho_off[r], x->status, b->stream));
+            if (x->walls)  // bounded grid: equal weights, wall deposits doubled to densities
+                PE_TRY(pe_quiet_start_equal(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell,
+                                            x->prof, x->prof + c.ncell, 2.0f, (float)c.v_th, pe_ctx_lift_seed(x),
+                                            x->s_w, x->eq_scratch, rho_all + b->rho_off[r], x->status, b->stream));
+            else
+                PE_TRY(pe_quiet_start(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell, x->prof,
+                                      x->prof + c.ncell, (float)c.v_th, pe_ctx_lift_seed(x), x->s_w,
+                                      rho_all + b->rho_off[r], x->status, b->stream));
         } else {
             PE_TRY(pe_deposit(x->cell[k], x->theta[k], x->w[k], c.nparticles, c.ncell, x->s_w,
                               rho_all + b->rho_off[r], x->status, b->stream));

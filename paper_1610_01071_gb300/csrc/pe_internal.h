@@ -42,7 +42,7 @@ size_t work_item_size();
 void make_push_desc(void* out, int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
                     int ncell, float dt_dx, float qm_dt, int s_w, int64_t* rho, const float* E0f, double dT, double dt,
                     float inv_dx, float qm, int comoving, int s_p, int bin_shift, int64_t* samp_base,
-                    int64_t row_stride, uint32_t* status);
+                    int64_t row_stride, int walls, uint32_t* status);
 void make_work_item(void* out, int r, int64_t begin, int64_t end);
 int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
                            unsigned* counter, int max_ncell, int max_nb, cudaStream_t s);

@@ -855,13 +855,15 @@ size_t work_item_size() { return sizeof(WorkItem); }
 void make_push_desc(void* out, int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
                     int ncell, float dt_dx, float qm_dt, int s_w, int64_t* rho, const float* E0f, double dT, double dt,
                     float inv_dx, float qm, int comoving, int s_p, int bin_shift, int64_t* samp_base,
-                    int64_t row_stride, uint32_t* status)
+                    int64_t row_stride, int walls, uint32_t* status)
 {
     PushParams P{};
     P.cell = cell;
     P.theta = theta;
     P.v = v;
     P.w = w;
+    P.walls = walls ? 1 : 0;
+    P.w_out = const_cast<float*>(w);  // written only for absorbed ions of a bounded grid
     P.n = n;
     P.Ef = Ef;
     P.ncell = ncell;
