@@ -226,7 +226,11 @@ PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64
  * (i + 1/2) M / n of the cumulative mass: in the cell c with C_c <= (i + 1/2) M / n < C_{c+1},
  * at the offset t solving t + sigma (t^2 - t) = r, r the fraction of m_c below it and
  * sigma = (n_{c+1} - n_c) / (n_{c+1} + n_c). w = M / n for every particle;
- * V = u(X) + v_th Phi^-1(b_i) with b_i of pe_quiet_start. Output is sorted by cell.
+ * V = u(X) + v_th Phi^-1(b_i) with b_i of pe_quiet_start. Storage: inside every full
+ * aligned block of 4096 slots, slot s holds point i = s with its low 12 bits reversed (the
+ * block's points, within 4096 mass quantiles of each other, in ascending velocity quantile:
+ * co-moving targets then vary smoothly along the array); the ragged tail holds i = s. Cells
+ * are non-decreasing from block to block.
  * scratch: PE_EQ_SCRATCH_BYTES(ncell) bytes of device memory, 16-byte aligned. A profile of
  * zero (or non-finite) mass sets PE_FLAG_RANGE and gives weight-0 particles in cell 0.
  * If rho_fx != NULL it is overwritten with the charge deposit of the new particles. */

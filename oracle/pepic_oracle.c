@@ -925,7 +925,10 @@ void orc_restrict_sample_walls(int64_t n, const int32_t* cell, const double* the
  * t + sigma (t^2 - t) = r, r = (s_i - C_c) / m_c, sigma = (n_{c+1} - n_c) / (n_{c+1} + n_c)
  * (the mass of the linear density up to t). Every particle has w = M / N, so the number of
  * particles per cell follows the mass (empty cells get none). V = u(X) + v_th Phi^{-1}(b_i)
- * with the Hammersley second coordinate b_i of orc_quiet_start (slot s holds point i = s). */
+ * with the Hammersley second coordinate b_i of orc_quiet_start. Storage: within each aligned
+ * block of 4096 slots (all but a ragged tail), slot s holds point i = s with its low 12 bits
+ * reversed, i.e. the block's points in ascending velocity quantile (their positions are
+ * within 4096 mass quantiles of each other); tail slots hold i = s. */
 void orc_quiet_start_equal(int64_t N, int32_t ncell, const double* nprof, const double* uprof, double v_th,
                            uint64_t seed, int32_t* cell, double* theta, double* v, double* w)
 {
@@ -948,18 +951,17 @@ void orc_quiet_start_equal(int64_t N, int32_t ncell, const double* nprof, const 
         double sig = (n0 + n1 > 0.0) ? (n1 - n0) / (n1 + n0) : 0.0;
         double den = (1.0 - sig) + sqrt((1.0 - sig) * (1.0 - sig) + 4.0 * sig * r);
         double t = (den > 0.0) ? 2.0 * r / den : 0.0;
-        int32_t cc = c;
-        if (t >= 1.0) {
-            t = 0.0;
-            cc = c + 1;
-        }
-        double uX = (1.0 - t) * uprof[cc] + t * uprof[cc + 1 < ncell ? cc + 1 : cc];
+        if (t >= 1.0) t = nextafter(1.0, 0.0); /* stay inside the cell */
+        const int32_t cc = c;
+        double uX = (1.0 - t) * uprof[cc] + t * uprof[cc + 1];
         uint32_t B = brev32((uint32_t)i) + half + shift;
         double b = ((double)B + 0.5) * 2.3283064365386963e-10;
-        cell[i] = cc;
-        theta[i] = t;
-        w[i] = M / (double)N;
-        v[i] = uX + v_th * orc_ndtri(b);
+        int64_t slot = i; /* bit reversal inside full blocks of 4096 is its own inverse */
+        if ((i | 4095) < N) slot = (i & ~(int64_t)4095) | (int64_t)(brev32((uint32_t)(i & 4095)) >> 20);
+        cell[slot] = cc;
+        theta[slot] = t;
+        w[slot] = M / (double)N;
+        v[slot] = uX + v_th * orc_ndtri(b);
     }
     free(C);
 }

@@ -30,8 +30,9 @@ constexpr int kClusterMinCells = 512;  // grids at least this large use the mult
 // inexact linear solve (mixed-precision iterative refinement): the FP64 residual drives the
 // iteration, so it converges to the FP64 solution of the discrete equation, while the
 // FP32 solve only bounds the final contraction rate (~ cond(J) 2^-24 per iteration).
-// Bounded grids with vacuum regions have exp(phi) ~ 1e-6 there, so cond(J) reaches ~1e7 and
-// FP32 would no longer contract: their linear solve runs in FP64 (template parameter T).
+// Bounded grids with vacuum regions have exp(phi) ~ 1e-6 there and cond(J) ~ 1e7: the FP32
+// solve still contracts, but slowly (7 Newton iterations instead of 3 on an 8192-node slab from
+// a warm start), so their linear solve runs in FP64 (template parameter T).
 // On this GPU a dependent FP64 instruction costs ~100 cycles and the FP64 pipe retires
 // ~2 lanes per cycle per SM, so FP64 is used only for per-node work, spread over many
 // warps and SMs, and kept off the serial chains of the tridiagonal elimination.
@@ -58,6 +59,17 @@ __device__ __forceinline__ double exp_small(double x)
     p = fma(p, x, 0.5);
     p = fma(p, x, 1.0);
     return fma(p, x, 1.0);
+}
+
+// Reciprocal for the elimination: FP32 division, or in FP64 two Newton-Raphson steps
+// r <- r (2 - x r) from the FP32 reciprocal (each step squares the relative error, 2^-24 ->
+// 2^-48 -> 2^-96), which avoids the long FP64 division sequence on the PCR's serial chain.
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+__device__ __forceinline__ double recip(double x)
+{
+    double r = (double)(1.0f / (float)x);
+    r = r * fma(-x, r, 2.0);
+    return r * fma(-x, r, 2.0);
 }
 
 template <typename T>
@@ -170,13 +182,14 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     const int mode = d.mode, maxit = d.maxit;
     double* ph = sh;                             // [B + 2]
     double* mymax = ph + B + 2;                  // [1]
-    T* A = reinterpret_cast<T*>(mymax + 1);      // [B] x 6
+    T* A = reinterpret_cast<T*>(mymax + 1);      // [B] x 7
     T* Bd = A + B;
     T* C = Bd + B;
     T* D = C + B;
     T* Gs = D + B;
     T* Hs = Gs + B;
-    T* red = Hs + B;     // [32]
+    T* Rb = Hs + B;      // [B] reciprocals of the diagonal
+    T* red = Rb + B;     // [32]
     T* mine = red + 32;  // [6]
     T* L3 = mine + 8;    // [G][14]
     T* L3n = L3 + 14 * G;
@@ -209,6 +222,7 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
             A[i] = (i == 0) ? T(0) : (wr ? T(2) * o : o);
             C[i] = (i == B - 1) ? T(0) : (wl ? T(2) * o : o);
             Bd[i] = (T)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
+            Rb[i] = recip(Bd[i]);
             D[i] = (T)(lap - gj + nj);  // -F_j
             Gs[i] = (i == 0 && !wl) ? o : T(0);
             Hs[i] = (i == B - 1 && !wr) ? o : T(0);
@@ -217,8 +231,8 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         // ---- parallel cyclic reduction of the block rows, three right-hand sides
         for (int s = 1; s < B; s <<= 1) {
             const int im = act ? i - s : -1, ip = act ? i + s : B;
-            const T al = (im >= 0) ? A[i] / Bd[im] : T(0);
-            const T ga = (ip < B) ? C[i] / Bd[ip] : T(0);
+            const T al = (im >= 0) ? A[i] * Rb[im] : T(0);
+            const T ga = (ip < B) ? C[i] * Rb[ip] : T(0);
             const T nA = (im >= 0) ? -al * A[im] : T(0);
             const T nC = (ip < B) ? -ga * C[ip] : T(0);
             T nB = act ? Bd[i] : T(0), nD = act ? D[i] : T(0), nG = act ? Gs[i] : T(0), nH = act ? Hs[i] : T(0);
@@ -239,13 +253,14 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
                 A[i] = nA;
                 C[i] = nC;
                 Bd[i] = nB;
+                Rb[i] = recip(nB);
                 D[i] = nD;
                 Gs[i] = nG;
                 Hs[i] = nH;
             }
             __syncthreads();
         }
-        const T rb = act ? T(1) / Bd[i] : T(0);
+        const T rb = act ? Rb[i] : T(0);
         const T y = act ? D[i] * rb : T(0), gsp = act ? Gs[i] * rb : T(0),
                 hsp = act ? Hs[i] * rb : T(0);  // x = y - g X_left - h X_right
         if (i == 0) {
@@ -385,7 +400,7 @@ static int cluster_size_for(int ncell)
 size_t newton_smem_bytes(int B, int G, bool fp64)
 {
     const size_t t = fp64 ? sizeof(double) : sizeof(float);
-    return sizeof(double) * ((size_t)B + 3) + t * (6 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    return sizeof(double) * ((size_t)B + 3) + t * (7 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
 }
 
 static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int nclusters, int block, size_t smem,

@@ -588,7 +588,7 @@ __device__ __forceinline__ int eq_cell_of(const EqParams& P, long long i)
 
 __device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
 {
-    // advance from the previous particle's cell (consecutive i rarely change cell)
+    // walk forward from a cell at or before the point's
     while (c < P.ncell - 2 && __ldg(P.tab.first + c + 1) <= (long long)i) ++c;
     const double C0 = __ldg(P.tab.C + c), C1 = __ldg(P.tab.C + c + 1);
     const double MoN = __ldg(P.tab.MoN);
@@ -618,13 +618,28 @@ __device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, fl
     vv = fmaf(P.v_th, upper ? -z : z, uX);
 }
 
+// Storage order of the equal-weight loading: inside every full aligned block of 2^kEqBlockBits
+// slots, slot s holds point i = s with its low kEqBlockBits bits reversed, so that the block's
+// points (all within 2^kEqBlockBits mass quantiles of each other) are stored in ascending
+// velocity quantile, as a power-of-two cell of pe_quiet_start stores its points: the 128
+// slots a warp visits at once then span 1/32 of the velocity range and their co-moving
+// targets stay together. The ragged tail keeps i = s. The reversal is its own inverse.
+constexpr int kEqBlockBits = 12;
+constexpr uint32_t kEqBlockMask = (1u << kEqBlockBits) - 1u;
+
+__device__ __forceinline__ uint32_t eq_point_of_slot(uint32_t s, int64_t n)
+{
+    return ((int64_t)(s | kEqBlockMask) < n) ? ((s & ~kEqBlockMask) | (__brev(s & kEqBlockMask) >> (32 - kEqBlockBits)))
+                                              : s;
+}
+
 __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
     block_chunk(P.n, P.chunk, &begin, &end);
     const bool dep = P.rho != nullptr;
-    const int c_first = (begin < end) ? eq_cell_of(P, begin) : 0;
+    const int c_first = (begin < end) ? eq_cell_of(P, eq_point_of_slot((uint32_t)begin, P.n)) : 0;
     SmemGrid grho{};
     if (dep) {
         grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
@@ -645,15 +660,17 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
     for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
         int4 c;
         float4 t, vv, ww;
-        const uint32_t i0 = (uint32_t)(g << 2);
-        c.x = eq_cell_of(P, i0);
-        eq_one(P, i0, c.x, t.x, vv.x, ww.x);
-        c.y = c.x;
-        eq_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
-        c.z = c.y;
-        eq_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
-        c.w = c.z;
-        eq_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        const uint32_t s0 = (uint32_t)(g << 2);
+        const uint32_t p0 = eq_point_of_slot(s0, P.n), p1 = eq_point_of_slot(s0 + 1, P.n),
+                       p2 = eq_point_of_slot(s0 + 2, P.n), p3 = eq_point_of_slot(s0 + 3, P.n);
+        // the four points lie within one block; search from the smallest
+        const uint32_t pmin = min(min(p0, p1), min(p2, p3));
+        const int cb = eq_cell_of(P, pmin);
+        c.x = c.y = c.z = c.w = cb;
+        eq_one(P, p0, c.x, t.x, vv.x, ww.x);
+        eq_one(P, p1, c.y, t.y, vv.y, ww.y);
+        eq_one(P, p2, c.z, t.z, vv.z, ww.z);
+        eq_one(P, p3, c.w, t.w, vv.w, ww.w);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -666,9 +683,10 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
         }
     }
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
-        int c = eq_cell_of(P, i);
+        const uint32_t pi = eq_point_of_slot((uint32_t)i, P.n);
+        int c = eq_cell_of(P, pi);
         float t, vv, ww;
-        eq_one(P, (uint32_t)i, c, t, vv, ww);
+        eq_one(P, pi, c, t, vv, ww);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;

@@ -158,13 +158,33 @@ def test_restrict_sample_walls_is_deposit_of_moved_particles_inside():
     assert (~keep & (w > 0)).sum() > 100  # the walls removed a part of the sample
 
 
+def _point_order(N, bits=12):
+    """Point index held by each storage slot: the low 12 bits reversed inside full blocks of 4096."""
+    s = np.arange(N)
+    rev = np.zeros(N, np.int64)
+    for b in range(bits):
+        rev |= ((s >> b) & 1) << (bits - 1 - b)
+    full = (s | ((1 << bits) - 1)) < N
+    return np.where(full, (s & ~((1 << bits) - 1)) | rev, s)
+
+
+def _by_point(arr, N):
+    out = np.empty_like(arr)
+    out[_point_order(N)] = arr
+    return out
+
+
 def test_quiet_start_equal_uniform_profile_is_uniform_lattice():
-    ncell, N = 33, 3200
+    ncell, N = 33, 3 * 4096 + 17  # a ragged last block
     dx = 0.5
     st = orc.quiet_start_equal(N, ncell, np.ones(ncell), np.zeros(ncell), 1.0, 5)
-    X = (st.cell + st.theta) * dx
+    X = _by_point((st.cell + st.theta) * dx, N)
     assert np.allclose(X, (np.arange(N) + 0.5) / N * (ncell - 1) * dx, atol=1e-12)
     assert np.all(st.w == (ncell - 1) / N)
+    # storage: every full block of 4096 slots holds its points in ascending velocity quantile,
+    # cyclically (the Cranley-Patterson shift wraps the quantiles once)
+    v = st.v[: (N // 4096) * 4096].reshape(-1, 4096)
+    assert np.all(np.sum(np.diff(v, axis=1) < 0, axis=1) <= 1)
 
 
 def test_quiet_start_equal_counts_follow_mass_and_ramp_is_sqrt():
@@ -176,20 +196,21 @@ def test_quiet_start_equal_counts_follow_mass_and_ramp_is_sqrt():
     M = C[-1]
     assert st.w.sum() == pytest.approx(M, rel=1e-13)
     counts = np.bincount(st.cell, minlength=ncell)
+    cell_p, theta_p = _by_point(st.cell, N), _by_point(st.theta, N)
     # particle i sits in cell c iff C_c <= (i + 1/2) M / N < C_{c+1}
     want = np.ceil(C[1:] * N / M - 0.5) - np.ceil(C[:-1] * N / M - 0.5)
     assert np.array_equal(counts[:-1], want.astype(int)) and counts[-1] == 0
     assert counts[: 7 * ncell // 16 - 1].sum() == 0 and counts[9 * ncell // 16 + 1:].sum() == 0
     # rising ramp cell (density 0 -> 1): mass up to t is t^2 / 2, so t = sqrt(r)
     c0 = 7 * ncell // 16 - 1
-    idx = np.nonzero(st.cell == c0)[0]
+    idx = np.nonzero(cell_p == c0)[0]
     r = ((idx + 0.5) * M / N - C[c0]) / m[c0]
-    assert np.allclose(st.theta[idx], np.sqrt(r), atol=1e-13)
+    assert np.allclose(theta_p[idx], np.sqrt(r), atol=1e-13)
     # falling ramp (1 -> 0): t = 1 - sqrt(1 - r)
     c1 = 9 * ncell // 16
-    idx = np.nonzero(st.cell == c1)[0]
+    idx = np.nonzero(cell_p == c1)[0]
     r = ((idx + 0.5) * M / N - C[c1]) / m[c1]
-    assert np.allclose(st.theta[idx], 1 - np.sqrt(1 - r), atol=1e-12)
+    assert np.allclose(theta_p[idx], 1 - np.sqrt(1 - r), atol=1e-12)
 
 
 def test_quiet_start_equal_deposit_reproduces_profile():
