@@ -92,7 +92,7 @@ __device__ __forceinline__ bool inside_walls(const PushParams& P, int c, float f
     return fl >= -(float)c && fl < (float)(P.ncell - 1 - c);
 }
 
-template <int MODE>
+template <int MODE, bool WALLS>
 __device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
                                         LaneWindow& lw, BinAcc& bacc, const SmemGrid& grho,
                                         const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
@@ -108,7 +108,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         raise_flag(P.status, PE_FLAG_RANGE);
         return;
     }
-    if (P.walls) {
+    if (WALLS) {
         if (ww == 0.0f) return;  // absorbed: frozen, carries nothing
         if (c >= P.ncell - 1) {  // a live particle must lie between the walls
             raise_flag(P.status, PE_FLAG_RANGE);
@@ -139,7 +139,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         const int cs = (c + k) & P.mask, cs1 = (cs + 1) & P.mask;
         const float vt = fmaf(P.qm_tau, E0p, vbar);
         // bounded grid: a target beyond a wall has left the domain by t_{n+1}
-        const bool counted = !P.walls || inside_walls(P, c, fl);
+        const bool counted = !WALLS || inside_walls(P, c, fl);
         if (Tr::ps && counted) {
             // Section 3.3 restriction: CIC in x (summed over the coarse bin), nearest cell in v
             const float jf = floorf((vt - P.vmin) * P.inv_dv);
@@ -186,7 +186,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
             thn = 0.0f;
             fl += 1.0f;
         }
-        if (P.walls && !inside_walls(P, c, fl)) {  // absorbed at the wall it crossed
+        if (WALLS && !inside_walls(P, c, fl)) {  // absorbed at the wall it crossed
             c_out = (fl < 0.0f) ? 0 : P.ncell - 1;
             th_out = 0.0f;
             v_out = 0.0f;
@@ -203,7 +203,7 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
 
 // One block owns a contiguous chunk of <= 65536 particles; each warp a contiguous slice
 // of it, read with 16-byte loads (4 particles per lane).
-template <int MODE>
+template <int MODE, bool WALLS>
 __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begin, int64_t end, uint32_t* smem)
 {
     using Tr = ModeTraits<MODE>;
@@ -272,19 +272,19 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         const float4 wa = __ldg(w4 + g);
         int4 co;
         float4 to, vo, wo;
-        process<MODE>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.x, to.x, vo.x,
-                      wo.x);
-        process<MODE>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.y, to.y, vo.y,
-                      wo.y);
-        process<MODE>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.z, to.z, vo.z,
-                      wo.z);
-        process<MODE>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co.w, to.w, vo.w,
-                      wo.w);
+        process<MODE, WALLS>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
+                             &ovf, co.x, to.x, vo.x, wo.x);
+        process<MODE, WALLS>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
+                             &ovf, co.y, to.y, vo.y, wo.y);
+        process<MODE, WALLS>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
+                             &ovf, co.z, to.z, vo.z, wo.z);
+        process<MODE, WALLS>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
+                             &ovf, co.w, to.w, vo.w, wo.w);
         if (kWrite) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
-            if (P.walls && (wo.x != wa.x || wo.y != wa.y || wo.z != wa.z || wo.w != wa.w))
+            if (WALLS && (wo.x != wa.x || wo.y != wa.y || wo.z != wa.z || wo.w != wa.w))
                 reinterpret_cast<float4*>(P.w_out)[g] = wo;  // an absorption in this group
         }
         if (kPS) {  // one warp-aggregated add per group of four particles per lane
@@ -301,13 +301,13 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         float to, vo, wo;
         const float vi = kNeedV ? P.v[i] : 0.f;
         const float wi = P.w[i];
-        process<MODE>(P, P.cell[i], P.theta[i], vi, wi, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co, to, vo,
-                      wo);
+        process<MODE, WALLS>(P, P.cell[i], P.theta[i], vi, wi, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co,
+                             to, vo, wo);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
             P.v[i] = vo;
-            if (P.walls && wo != wi) P.w_out[i] = wo;
+            if (WALLS && wo != wi) P.w_out[i] = wo;
         }
         if (kPS) {
             ps_add_warp(gps, acc.key, acc.val);
@@ -333,13 +333,14 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     if (kPS) gps.flush();
 }
 
-template <int MODE>
+// WALLS: bounded grid (a separate instantiation, so that periodic launches carry no wall code)
+template <int MODE, bool WALLS>
 __global__ void __launch_bounds__(kThreads, ModeTraits<MODE>::ps ? 3 : 4) k_particles(PushParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
     block_chunk(P.n, P.chunk, &begin, &end);
-    particle_chunk<MODE>(P, begin, end, smem);
+    particle_chunk<MODE, WALLS>(P, begin, end, smem);
 }
 
 // Work item of a batched launch: particles [begin, end) of realisation r.
@@ -373,7 +374,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_particles_batch(const PushParam
             P.samp_n = P.samp_base + (int64_t)p * P.row_stride;
             P.samp_m = P.samp_n + (P.ncell >> P.bin_shift);
         }
-        particle_chunk<MODE>(P, wi.begin, wi.end, smem);
+        if (P.walls)  // per realisation: uniform in the block
+            particle_chunk<MODE, true>(P, wi.begin, wi.end, smem);
+        else
+            particle_chunk<MODE, false>(P, wi.begin, wi.end, smem);
         __syncthreads();
     }
 }
@@ -832,14 +836,17 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) + 5 * sizeof(uint32_t) * 2 * nb +
                   3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    const void* k = (const void*)k_particles<MODE>;
+    const void* k = P.walls ? (const void*)k_particles<MODE, true> : (const void*)k_particles<MODE, false>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = grid_for(k, block, smem, P.n, &P.chunk, P.max_chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
     const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : 2 * (size_t)(P.ncell >> P.bin_shift);
     if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess) return PE_ECUDA;
     if (P.n == 0) return PE_OK;
-    k_particles<MODE><<<grid, block, smem, s>>>(P);
+    if (P.walls)
+        k_particles<MODE, true><<<grid, block, smem, s>>>(P);
+    else
+        k_particles<MODE, false><<<grid, block, smem, s>>>(P);
     return launch_status();
 }
 
