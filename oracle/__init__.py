@@ -118,13 +118,46 @@ def _i32(a):
 
 # ------------------------------------------------------------------ filters
 # Orthonormal scaling filters (sum h = sqrt 2). Haar; Daubechies' 4-tap filter
-# from its closed form (two vanishing moments of the wavelet).
+# from its closed form (two vanishing moments of the wavelet); the coiflet of order 4
+# (Appendix A: four vanishing moments of the wavelet, and of the scaling function the
+# moments 1..3) from its defining equations.
 _S3 = np.sqrt(3.0)
+
+
+def coif4_equations(h):
+    """Residuals of the order-4 coiflet conditions for 12 taps h_k, k = -4..7: sum h = sqrt 2;
+    sum k^p h_k = 0 (p = 1, 2, 3: scaling-function moments about 0); sum (-1)^k k^p h_k = 0
+    (p = 0..3: wavelet moments, the wavelet filter being (-1)^k h_{1-k}); sum_k h_k h_{k+2m} =
+    delta_m (m = 0..5: orthonormal translates)."""
+    k = np.arange(-4, 8, dtype=np.float64)
+    r = [np.sum(h) - np.sqrt(2.0)]
+    r += [np.sum(k**p * h) for p in (1, 2, 3)]
+    r += [np.sum((-1.0) ** k * k**p * h) for p in (0, 1, 2, 3)]
+    r += [np.dot(h[: 12 - 2 * m], h[2 * m:]) - (1.0 if m == 0 else 0.0) for m in range(6)]
+    return np.array(r)
+
+
+def _coif4():
+    """Solves the 14 coiflet equations for 12 taps by nonlinear least squares from the
+    linear B-spline filter (1/2, 1, 1/2)/sqrt 2 centred on k = 0. The real solutions of the
+    system are few (four); this start reaches the one whose taps concentrate at k = 0 (the
+    largest central tap), Daubechies' choice. Taps returned in the order k = -4..7."""
+    from scipy.optimize import least_squares
+
+    x0 = np.zeros(12)
+    x0[3:6] = np.array([0.5, 1.0, 0.5]) / np.sqrt(2.0)
+    sol = least_squares(coif4_equations, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=5000)
+    if np.max(np.abs(coif4_equations(sol.x))) > 1e-13:
+        raise RuntimeError("coiflet equations not solved")
+    return sol.x
+
+
 FILTERS = {
     "haar": np.array([1.0, 1.0]) / np.sqrt(2.0),
     "d4": np.array([1 + _S3, 3 + _S3, 3 - _S3, 1 - _S3]) / (4 * np.sqrt(2.0)),
+    "coif4": _coif4(),
 }
-WAVELET_IDS = {0: "haar", 1: "d4"}
+WAVELET_IDS = {0: "haar", 1: "d4", 2: "coif4"}
 
 
 def splitmix64(x: int) -> int:

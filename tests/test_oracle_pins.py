@@ -230,7 +230,7 @@ def test_restrict_sample_follows_characteristics():
 # ----------------------------------------------------------------- wavelets (App. A)
 
 
-@pytest.mark.parametrize("wav", ["haar", "d4"])
+@pytest.mark.parametrize("wav", ["haar", "d4", "coif4"])
 def test_filter_is_orthonormal(wav):
     h = orc.FILTERS[wav]
     L = len(h)
@@ -238,17 +238,64 @@ def test_filter_is_orthonormal(wav):
     for s in range(0, L, 2):
         assert np.dot(h[: L - s], h[s:]) == pytest.approx(1.0 if s == 0 else 0.0, abs=1e-15)
     g = np.array([(-1) ** m * h[L - 1 - m] for m in range(L)])
-    moments = L // 2
+    moments = {"haar": 1, "d4": 2, "coif4": 4}[wav]  # Daubechies: L/2; the coiflet trades two for phi's
     for q in range(moments):  # vanishing moments of the wavelet
         assert np.dot(np.arange(L) ** q, g) == pytest.approx(0.0, abs=1e-13)
 
 
-@pytest.mark.parametrize("wav", ["haar", "d4"])
+@pytest.mark.parametrize("wav", ["haar", "d4", "coif4"])
 def test_dwt_round_trip_and_parseval(wav):
     x = np.random.default_rng(1).standard_normal(64)
     a, d = orc.dwt_level(x, wav)
     assert np.sum(a**2) + np.sum(d**2) == pytest.approx(np.sum(x**2), rel=1e-14)
     assert np.max(np.abs(orc.idwt_level(a, d, wav) - x)) < 1e-14
+
+
+def test_coif4_moments_through_the_transform():
+    # four vanishing wavelet moments: the interior detail coefficients of a cubic vanish
+    # (Daubechies-4, with two, does not annihilate it)
+    n = 128
+    x = np.arange(n, dtype=np.float64)
+    cubic = 0.3 + 0.02 * x - 1e-3 * x**2 + 2e-5 * x**3
+    _, d = orc.dwt_level(cubic, "coif4")
+    inner = slice(0, n // 2 - 6)  # away from the periodic wrap of the 12-tap filter
+    assert np.max(np.abs(d[inner])) < 1e-12 * np.max(np.abs(cubic))
+    _, d4 = orc.dwt_level(cubic, "d4")
+    assert np.max(np.abs(d4[inner])) > 1e-6
+
+
+@pytest.mark.parametrize("wav,order", [("coif4", 4), ("haar", 1)])
+def test_coarse_scaling_coefficients_sample_the_function(wav, order):
+    # coiflet property (vanishing scaling-function moments 1..3): after L analysis levels the
+    # scaling coefficient k is 2^{L/2} f(2^L k + s_L) up to O(h^4), with s_L = 4 (2^L - 1) for
+    # taps stored from k = -4; Haar's block mean is only first order about its block centre.
+    L = 2
+    errs = []
+    for n in (64, 128, 256):
+        t = np.arange(n) / n
+        f = np.sin(2 * np.pi * 3 * t) + 0.5 * np.cos(2 * np.pi * 5 * t)
+        c = orc.coarsen(f, n >> L, wav) * 2.0 ** (np.log2(n) / 2)  # undo the 2^{-J_f/2} of the fine level
+        shift = 4 * (2**L - 1) if wav == "coif4" else 0
+        tk = ((2**L * np.arange(n >> L) + shift) % n) / n
+        want = 2 ** (L / 2) * (np.sin(2 * np.pi * 3 * tk) + 0.5 * np.cos(2 * np.pi * 5 * tk))
+        errs.append(np.max(np.abs(c - want)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > order - 0.3), rates
+
+
+def test_coif4_is_the_concentrated_solution():
+    # the coiflet equations have four real solutions; the one used has the largest central
+    # tap (its scaling function peaks at 0), and its taps solve the equations to rounding
+    h = orc.FILTERS["coif4"]
+    assert np.max(np.abs(orc.coif4_equations(h))) < 1e-14
+    assert np.argmax(np.abs(h)) == 4 and h[4] > 0.8
+    from scipy.optimize import least_squares
+
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        r = least_squares(orc.coif4_equations, rng.standard_normal(12) * 0.5, xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        if np.max(np.abs(orc.coif4_equations(r.x))) < 1e-12:
+            assert r.x[4] <= h[4] + 1e-12
 
 
 def test_haar_coarsen_is_scaled_block_mean():
@@ -261,7 +308,7 @@ def test_haar_coarsen_is_scaled_block_mean():
     assert np.allclose(back, np.repeat(f.reshape(nc, -1).mean(axis=1), nf // nc), atol=1e-13)
 
 
-@pytest.mark.parametrize("wav", ["haar", "d4"])
+@pytest.mark.parametrize("wav", ["haar", "d4", "coif4"])
 def test_coarsen_constant_and_refine_coarsen_identity(wav):
     nf, nc = 128, 16
     c = orc.coarsen(np.full(nf, 3.0), nc, wav)
