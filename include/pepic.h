@@ -60,6 +60,9 @@ extern "C" {
 
 #define PE_WAVELET_HAAR 0 /* orthonormal Haar filter */
 #define PE_WAVELET_D4 1   /* Daubechies 4-tap orthonormal filter */
+#define PE_WAVELET_COIF4 2 /* order-4 coiflet of Appendix A (12 taps, k = -4..7): four vanishing
+                              wavelet moments, scaling-function moments 1..3 vanish; its taps are
+                              solved from those equations by the library at first use */
 
 #define PE_POISSON_BOLTZMANN 0  /* -Lap phi + exp(phi) = n   (Section 3.3, Eq. poisson2rescaled) */
 #define PE_POISSON_LINEARIZED 1 /* -Lap phi + 1 + phi = n    (its small-amplitude limit) */

@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpepic.so")
 
 PE_OK, PE_EINVAL, PE_ECUDA, PE_ENOCONV, PE_EOVERFLOW, PE_ERANGE, PE_ESTATE = range(7)
-PE_WAVELET = {"haar": 0, "d4": 1}
+PE_WAVELET = {"haar": 0, "d4": 1, "coif4": 2}
 PE_POISSON = {"boltzmann": 0, "linearized": 1}
 PE_PROFILE_SINE = 0
 PE_PROFILE_SLAB = 1

@@ -133,7 +133,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.K < 1 || c.K > 4096) return PE_EINVAL;
     if (c.nparticles < c.ncell || c.nparticles % c.ncell != 0 || c.nparticles >= (int64_t(1) << 32)) return PE_EINVAL;
     if (!(c.L > 0.0) || !(c.dt > 0.0) || !(c.dT >= c.K * c.dt * (1.0 - 1e-12)) || !(c.v_th >= 0.0)) return PE_EINVAL;
-    if (c.wavelet != PE_WAVELET_HAAR && c.wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    if (c.wavelet != PE_WAVELET_HAAR && c.wavelet != PE_WAVELET_D4 && c.wavelet != PE_WAVELET_COIF4) return PE_EINVAL;
     if (c.poisson != PE_POISSON_BOLTZMANN && c.poisson != PE_POISSON_LINEARIZED) return PE_EINVAL;
     if (c.newton_maxit < 1 || !(c.newton_tol > 0.0) || c.sort_every < 0) return PE_EINVAL;
     if (c.w_cap < 0.0 || c.v_cap < 0.0) return PE_EINVAL;

@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "pe_common.cuh"
 #include "pe_internal.h"
 
@@ -13,14 +15,142 @@ namespace pe {
 // Orthonormal scaling filter (sum h = sqrt 2); the wavelet filter is
 // g_m = (-1)^m h_{len-1-m} and is not needed: details are discarded.
 struct Filter {
-    double h[4];
+    double h[12];
     int len;
 };
+
+// Order-4 coiflet (Appendix A: the wavelet has four vanishing moments and the scaling
+// function vanishing moments 1..3), taps h_k for k = -4..7 stored from k = -4. Its taps are
+// the solution of 14 equations in 12 unknowns:
+//   sum h_k = sqrt 2;  sum k^p h_k = 0 (p = 1..3);  sum (-1)^k k^p h_k = 0 (p = 0..3);
+//   sum_k h_k h_{k+2m} = delta_m (m = 0..5),
+// solved here on the host by Gauss-Newton on the normal equations (analytic Jacobian), from
+// the linear B-spline filter (1/2, 1, 1/2)/sqrt 2 centred on k = 0: of the few real solutions
+// that start reaches the one concentrated at k = 0 (largest central tap), Daubechies' coiflet.
+static void coif4_residual(const double* h, double* r, double J[14][12])
+{
+    int e = 0;
+    double s = 0.0;
+    for (int i = 0; i < 12; ++i) s += h[i];
+    r[e] = s - sqrt(2.0);
+    for (int i = 0; i < 12; ++i) J[e][i] = 1.0;
+    ++e;
+    for (int p = 1; p <= 3; ++p, ++e) {
+        r[e] = 0.0;
+        for (int i = 0; i < 12; ++i) {
+            const double k = i - 4, kp = pow(k, p);
+            r[e] += kp * h[i];
+            J[e][i] = kp;
+        }
+    }
+    for (int p = 0; p <= 3; ++p, ++e) {
+        r[e] = 0.0;
+        for (int i = 0; i < 12; ++i) {
+            const double k = i - 4, sg = ((i - 4) & 1) ? -1.0 : 1.0, kp = sg * (p ? pow(k, p) : 1.0);
+            r[e] += kp * h[i];
+            J[e][i] = kp;
+        }
+    }
+    for (int m = 0; m < 6; ++m, ++e) {
+        r[e] = (m == 0) ? -1.0 : 0.0;
+        for (int i = 0; i < 12; ++i) J[e][i] = 0.0;
+        for (int i = 0; i + 2 * m < 12; ++i) {
+            r[e] += h[i] * h[i + 2 * m];
+            J[e][i] += h[i + 2 * m];
+            J[e][i + 2 * m] += h[i];
+        }
+    }
+}
+
+static bool coif4_solve(double* h)
+{
+    for (int i = 0; i < 12; ++i) h[i] = 0.0;
+    h[3] = 0.5 / sqrt(2.0);
+    h[4] = 1.0 / sqrt(2.0);
+    h[5] = 0.5 / sqrt(2.0);
+    double r[14], J[14][12];
+    for (int it = 0; it < 200; ++it) {
+        coif4_residual(h, r, J);
+        double nr = 0.0;
+        for (int e = 0; e < 14; ++e) nr = fmax(nr, fabs(r[e]));
+        if (nr < 1e-15) return true;
+        // normal equations (J^T J) d = -J^T r, Gaussian elimination with partial pivoting
+        double A[12][13];
+        for (int i = 0; i < 12; ++i) {
+            for (int j = 0; j < 12; ++j) {
+                double a = 0.0;
+                for (int e = 0; e < 14; ++e) a += J[e][i] * J[e][j];
+                A[i][j] = a;
+            }
+            double b = 0.0;
+            for (int e = 0; e < 14; ++e) b -= J[e][i] * r[e];
+            A[i][12] = b;
+        }
+        for (int c = 0; c < 12; ++c) {
+            int piv = c;
+            for (int i = c + 1; i < 12; ++i)
+                if (fabs(A[i][c]) > fabs(A[piv][c])) piv = i;
+            if (fabs(A[piv][c]) < 1e-300) return false;
+            for (int j = 0; j <= 12; ++j) {
+                const double t = A[c][j];
+                A[c][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+            for (int i = c + 1; i < 12; ++i) {
+                const double f = A[i][c] / A[c][c];
+                for (int j = c; j <= 12; ++j) A[i][j] -= f * A[c][j];
+            }
+        }
+        double d[12];
+        for (int i = 11; i >= 0; --i) {
+            double v = A[i][12];
+            for (int j = i + 1; j < 12; ++j) v -= A[i][j] * d[j];
+            d[i] = v / A[i][i];
+        }
+        // step halving until the residual decreases
+        double t = 1.0, hn[12], rn[14], Jn[14][12];
+        for (;;) {
+            for (int i = 0; i < 12; ++i) hn[i] = h[i] + t * d[i];
+            coif4_residual(hn, rn, Jn);
+            double nn = 0.0, n0 = 0.0;
+            for (int e = 0; e < 14; ++e) {
+                nn += rn[e] * rn[e];
+                n0 += r[e] * r[e];
+            }
+            if (nn < n0 || t < 1e-6) break;
+            t *= 0.5;
+        }
+        for (int i = 0; i < 12; ++i) h[i] = hn[i];
+    }
+    coif4_residual(h, r, J);
+    double nr = 0.0;
+    for (int e = 0; e < 14; ++e) nr = fmax(nr, fabs(r[e]));
+    return nr < 1e-14;
+}
+
+static const double* coif4_taps()
+{
+    static double taps[12];
+    static int state = 0;  // 0: not solved, 1: solved, -1: failed
+    static std::once_flag once;
+    std::call_once(once, [] { state = coif4_solve(taps) ? 1 : -1; });
+    return state == 1 ? taps : nullptr;
+}
+
+static bool wavelet_ok(int wavelet)
+{
+    if (wavelet == PE_WAVELET_HAAR || wavelet == PE_WAVELET_D4) return true;
+    return wavelet == PE_WAVELET_COIF4 && coif4_taps() != nullptr;
+}
 
 static Filter make_filter(int wavelet)
 {
     Filter f{};
-    if (wavelet == PE_WAVELET_D4) {
+    if (wavelet == PE_WAVELET_COIF4) {
+        const double* t = coif4_taps();
+        for (int i = 0; i < 12; ++i) f.h[i] = t ? t[i] : 0.0;
+        f.len = 12;
+    } else if (wavelet == PE_WAVELET_D4) {
         // Daubechies' four-tap filter in closed form: (1+r3, 3+r3, 3-r3, 1-r3) / (4 sqrt 2)
         const double r3 = sqrt(3.0), den = 4.0 * sqrt(2.0);
         f.h[0] = (1.0 + r3) / den;
@@ -228,7 +358,7 @@ extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int
 {
     if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || nsamples < 1 || !sample_fx || !coarse)
         return PE_EINVAL;
-    if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    if (!wavelet_ok(wavelet)) return PE_EINVAL;
     if (bin_shift < 0 || (bin_shift > 0 && wavelet != PE_WAVELET_HAAR) || (ncell >> bin_shift) < n_coarse)
         return PE_EINVAL;
     const int nb = ncell >> bin_shift;  // input length per row
@@ -257,7 +387,7 @@ extern "C" PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t 
                                 float* prof_u, void* stream)
 {
     if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || !coarse || !prof_n || !prof_u) return PE_EINVAL;
-    if (wavelet != PE_WAVELET_HAAR && wavelet != PE_WAVELET_D4) return PE_EINVAL;
+    if (!wavelet_ok(wavelet)) return PE_EINVAL;
     const size_t smem = 3 * sizeof(double) * (size_t)ncell;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     if (ensure_smem((const void*)k_refine, smem) != PE_OK) return PE_ECUDA;

@@ -87,9 +87,10 @@ def test_macro_step_matches_oracle():
     assert np.max(np.abs(got - want)) < 1e-4 * np.max(np.abs(want))
 
 
-def test_two_macro_steps_with_lift_match_oracle():
+@pytest.mark.parametrize("wavelet", ["haar", "coif4"])
+def test_two_macro_steps_with_lift_match_oracle(wavelet):
     cfg = dict(SMALL, K=6, M=3)
-    ctx = make_ctx(cfg, seed=17)
+    ctx = make_ctx(cfg, seed=17, wavelet=wavelet)
     ctx.load_initial(cfg["amp"])
     ctx.step()
     ctx.step()  # lifts from the projected coarse state
@@ -97,9 +98,9 @@ def test_two_macro_steps_with_lift_match_oracle():
     assert ctx.sync_status() == 0
     d = ctx.diagnostics()
     assert d.macro_steps == 2
-    ocfg = oracle_cfg(cfg, d.s_w)
+    ocfg = oracle_cfg(cfg, d.s_w, wavelet=wavelet)
     c1, _, phi = orc.efpi_macro_step(oracle_state(cfg, 17), ocfg, np.zeros(cfg["ncell"]))
-    # lifting seed: splitmix64 shift of seed + golden * (macro step + 1), as documented in the design doc
+    # lifting seed of macro step m: seed + 0x632BE59BD9B4E019 (m + 1), its splitmix64 shift
     seed2 = (17 + 0x632BE59BD9B4E019 * 2) % 2**64
     st = orc.lift(c1, dict(ocfg, N=cfg["N"]), seed2)
     c2, _, _ = orc.efpi_macro_step(st, ocfg, phi)

@@ -221,7 +221,8 @@ def test_sample_matches_oracle(tau):
 # ----------------------------------------------------------------- coarse variables
 
 
-@pytest.mark.parametrize("wav,ncell,nc", [("haar", 128, 16), ("haar", 4096, 256), ("d4", 512, 32), ("haar", 64, 64)])
+@pytest.mark.parametrize("wav,ncell,nc", [("haar", 128, 16), ("haar", 4096, 256), ("d4", 512, 32), ("haar", 64, 64),
+                                          ("coif4", 512, 32), ("coif4", 4096, 256), ("coif4", 64, 8)])
 def test_coarsen_matches_oracle(wav, ncell, nc):
     rng = np.random.default_rng(ncell)
     nsamp, s_w, s_p = 5, 30, 25
@@ -256,7 +257,8 @@ def test_ls_project_matches_oracle(K):
     assert np.allclose(out.cpu().numpy(), want, rtol=1e-11, atol=1e-10)
 
 
-@pytest.mark.parametrize("wav,ncell,nc", [("haar", 128, 16), ("haar", 4096, 256), ("d4", 256, 32)])
+@pytest.mark.parametrize("wav,ncell,nc", [("haar", 128, 16), ("haar", 4096, 256), ("d4", 256, 32),
+                                          ("coif4", 256, 32), ("coif4", 4096, 256)])
 def test_refine_matches_oracle(wav, ncell, nc):
     rng = np.random.default_rng(nc)
     coarse = np.stack([1.0 + 0.6 * rng.standard_normal(nc), 0.3 * rng.standard_normal(nc)]) * 2.0 ** (
