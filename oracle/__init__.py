@@ -137,19 +137,44 @@ def coif4_equations(h):
     return np.array(r)
 
 
-def _coif4():
-    """Solves the 14 coiflet equations for 12 taps by nonlinear least squares from the
-    linear B-spline filter (1/2, 1, 1/2)/sqrt 2 centred on k = 0. The real solutions of the
-    system are few (four); this start reaches the one whose taps concentrate at k = 0 (the
-    largest central tap), Daubechies' choice. Taps returned in the order k = -4..7."""
-    from scipy.optimize import least_squares
+def _coif4_jacobian(h):
+    k = np.arange(-4, 8, dtype=np.float64)
+    rows = [np.ones(12)]
+    rows += [k**p for p in (1, 2, 3)]
+    rows += [(-1.0) ** k * k**p for p in (0, 1, 2, 3)]
+    for m in range(6):
+        r = np.zeros(12)
+        r[: 12 - 2 * m] += h[2 * m:]
+        r[2 * m:] += h[: 12 - 2 * m]
+        rows.append(r)
+    return np.array(rows)
 
-    x0 = np.zeros(12)
-    x0[3:6] = np.array([0.5, 1.0, 0.5]) / np.sqrt(2.0)
-    sol = least_squares(coif4_equations, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=5000)
-    if np.max(np.abs(coif4_equations(sol.x))) > 1e-13:
+
+def _coif4():
+    """Solves the 14 coiflet equations for 12 taps by Gauss-Newton (numpy least-squares
+    steps, halved until the residual decreases). The real solutions of the system are few
+    (four); the coiflet is the one concentrated at k = 0 (the largest central tap h_0),
+    Daubechies' choice. The Newton path from one start can reach another root depending on
+    rounding, so several starts centred on k = 0 are tried and the solution with the largest
+    h_0 is kept. Taps returned in the order k = -4..7."""
+    best = None
+    for start in ([0.5, 1.0, 0.5], [0.0, 2.0, 0.0], [0.0, 1.0, 1.0], [1.0, 0.5, 0.0], [0.0, 0.5, 1.0]):
+        h = np.zeros(12)
+        h[3:6] = np.array(start) / np.sqrt(2.0)
+        for _ in range(200):
+            r = coif4_equations(h)
+            if np.max(np.abs(r)) < 1e-15:
+                break
+            d = np.linalg.lstsq(_coif4_jacobian(h), -r, rcond=None)[0]
+            t = 1.0
+            while t > 1e-6 and np.sum(coif4_equations(h + t * d) ** 2) >= np.sum(r**2):
+                t *= 0.5
+            h = h + t * d
+        if np.max(np.abs(coif4_equations(h))) < 1e-13 and (best is None or h[4] > best[4]):
+            best = h
+    if best is None or not best[4] > 0.8:
         raise RuntimeError("coiflet equations not solved")
-    return sol.x
+    return best
 
 
 FILTERS = {

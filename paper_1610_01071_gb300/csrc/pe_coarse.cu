@@ -24,9 +24,11 @@ struct Filter {
 // the solution of 14 equations in 12 unknowns:
 //   sum h_k = sqrt 2;  sum k^p h_k = 0 (p = 1..3);  sum (-1)^k k^p h_k = 0 (p = 0..3);
 //   sum_k h_k h_{k+2m} = delta_m (m = 0..5),
-// solved here on the host by Gauss-Newton on the normal equations (analytic Jacobian), from
-// the linear B-spline filter (1/2, 1, 1/2)/sqrt 2 centred on k = 0: of the few real solutions
-// that start reaches the one concentrated at k = 0 (largest central tap), Daubechies' coiflet.
+// solved here on the host by Gauss-Newton on the normal equations (analytic Jacobian). The
+// system has a few real solutions; the coiflet is the one concentrated at k = 0 (largest
+// central tap h_0), Daubechies' choice. Which root a Newton path reaches depends on rounding
+// (fused multiply-adds differ between hosts), so several starts are tried and the converged
+// solution with the largest h_0 is kept.
 static void coif4_residual(const double* h, double* r, double J[14][12])
 {
     int e = 0;
@@ -62,31 +64,31 @@ static void coif4_residual(const double* h, double* r, double J[14][12])
     }
 }
 
-static bool coif4_solve(double* h)
+// Levenberg-Marquardt iteration on the normal equations from h; true if it converges to a
+// root (max residual below 1e-13).
+static bool coif4_newton(double* h)
 {
-    for (int i = 0; i < 12; ++i) h[i] = 0.0;
-    h[3] = 0.5 / sqrt(2.0);
-    h[4] = 1.0 / sqrt(2.0);
-    h[5] = 0.5 / sqrt(2.0);
-    double r[14], J[14][12];
-    for (int it = 0; it < 200; ++it) {
+    double r[14], J[14][12], mu = 1e-3;
+    for (int it = 0; it < 400; ++it) {
         coif4_residual(h, r, J);
-        double nr = 0.0;
-        for (int e = 0; e < 14; ++e) nr = fmax(nr, fabs(r[e]));
+        double nr = 0.0, n0 = 0.0;
+        for (int e = 0; e < 14; ++e) {
+            nr = fmax(nr, fabs(r[e]));
+            n0 += r[e] * r[e];
+        }
         if (nr < 1e-15) return true;
-        // normal equations (J^T J) d = -J^T r, Gaussian elimination with partial pivoting
         double A[12][13];
         for (int i = 0; i < 12; ++i) {
             for (int j = 0; j < 12; ++j) {
                 double a = 0.0;
                 for (int e = 0; e < 14; ++e) a += J[e][i] * J[e][j];
-                A[i][j] = a;
+                A[i][j] = a + (i == j ? mu : 0.0);
             }
-            double b = 0.0;
-            for (int e = 0; e < 14; ++e) b -= J[e][i] * r[e];
-            A[i][12] = b;
+            double c = 0.0;
+            for (int e = 0; e < 14; ++e) c -= J[e][i] * r[e];
+            A[i][12] = c;
         }
-        for (int c = 0; c < 12; ++c) {
+        for (int c = 0; c < 12; ++c) {  // Gaussian elimination with partial pivoting
             int piv = c;
             for (int i = c + 1; i < 12; ++i)
                 if (fabs(A[i][c]) > fabs(A[piv][c])) piv = i;
@@ -101,31 +103,59 @@ static bool coif4_solve(double* h)
                 for (int j = c; j <= 12; ++j) A[i][j] -= f * A[c][j];
             }
         }
-        double d[12];
+        double d[12], hn[12], rn[14], Jn[14][12];
         for (int i = 11; i >= 0; --i) {
             double v = A[i][12];
             for (int j = i + 1; j < 12; ++j) v -= A[i][j] * d[j];
             d[i] = v / A[i][i];
         }
-        // step halving until the residual decreases
-        double t = 1.0, hn[12], rn[14], Jn[14][12];
-        for (;;) {
-            for (int i = 0; i < 12; ++i) hn[i] = h[i] + t * d[i];
-            coif4_residual(hn, rn, Jn);
-            double nn = 0.0, n0 = 0.0;
-            for (int e = 0; e < 14; ++e) {
-                nn += rn[e] * rn[e];
-                n0 += r[e] * r[e];
-            }
-            if (nn < n0 || t < 1e-6) break;
-            t *= 0.5;
+        for (int i = 0; i < 12; ++i) hn[i] = h[i] + d[i];
+        coif4_residual(hn, rn, Jn);
+        double nn = 0.0;
+        for (int e = 0; e < 14; ++e) nn += rn[e] * rn[e];
+        if (nn < n0) {  // accept, trust the quadratic model more
+            for (int i = 0; i < 12; ++i) h[i] = hn[i];
+            mu = fmax(mu * 0.1, 1e-15);
+        } else {
+            mu *= 10.0;
+            if (mu > 1e10) break;
         }
-        for (int i = 0; i < 12; ++i) h[i] = hn[i];
     }
     coif4_residual(h, r, J);
     double nr = 0.0;
     for (int e = 0; e < 14; ++e) nr = fmax(nr, fabs(r[e]));
-    return nr < 1e-14;
+    return nr < 1e-13;
+}
+
+static bool coif4_solve(double* best)
+{
+    // starts: filters centred on k = 0 (B-spline hat, delta, Haar pair, shifted hats), then
+    // pseudo-random ones (splitmix64); the root with the largest central tap is kept
+    const double r2 = sqrt(2.0);
+    const double centred[5][3] = {{0.5, 1.0, 0.5}, {0.0, 2.0, 0.0}, {0.0, 1.0, 1.0}, {1.0, 0.5, 0.0}, {0.0, 0.5, 1.0}};
+    bool found = false;
+    uint64_t z = 0x5EEDC01F;
+    for (int s = 0; s < 64; ++s) {
+        double h[12] = {0.0};
+        if (s < 5) {
+            for (int j = 0; j < 3; ++j) h[3 + j] = centred[s][j] / r2;
+        } else {
+            for (int i = 0; i < 12; ++i) {
+                z += 0x9E3779B97F4A7C15ULL;
+                uint64_t x = z;
+                x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+                x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+                x ^= x >> 31;
+                h[i] = ((double)(x >> 11) * 0x1.0p-53 - 0.5);
+            }
+        }
+        if (!coif4_newton(h)) continue;
+        if (!found || h[4] > best[4]) {
+            for (int i = 0; i < 12; ++i) best[i] = h[i];
+            found = true;
+        }
+    }
+    return found && best[4] > 0.8;
 }
 
 static const double* coif4_taps()
