@@ -94,6 +94,11 @@ def _load():
                                                    i32, i32, i32, dbl, i32, i32, P, P]),
                 "orc_pic_steps_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32,
                                                        i32, i32, dbl, i32, i32, P]),
+                "orc_ps_sample_fx_walls": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, dbl, i32, i32,
+                                                  P]),
+                "orc_ps_quiet_start_equal": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
+                "orc_ps_burst_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl,
+                                                      i32, i32, i32, dbl, dbl, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -605,3 +610,63 @@ def lift_walls(coarse, cfg: dict, seed):
     nf, uf = lift_profile(nf, mf)
     nf[[0, -1]] *= 2.0
     return quiet_start_equal(cfg["N"], ncell, nf, uf, cfg["v_th"], seed)
+
+
+# ------------------------------------------------------------------ phase space on the bounded grid
+
+
+def ps_sample_fx_walls(st: State, vbar, E0, ncell, dx, tau, qm, bin_shift, vmin, dv, nv, s_w):
+    vbar, E0 = _f64(vbar), _f64(E0)
+    F = np.zeros((ncell >> bin_shift, nv), np.int64)
+    _load().orc_ps_sample_fx_walls(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell, float(dx),
+                                   float(tau), float(qm), int(bin_shift), float(vmin), float(dv), int(nv), int(s_w),
+                                   _p(F))
+    return F
+
+
+def ps_quiet_start_equal(N, ncell, bin_shift, mass, cdf, vmin, dv, seed):
+    mass, cdf = _f64(mass), _f64(cdf)
+    nv = cdf.shape[1] - 1
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_ps_quiet_start_equal(N, ncell, int(bin_shift), _p(mass), _p(cdf), nv, float(vmin), float(dv),
+                                     seed & 0xFFFFFFFFFFFFFFFF, _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def ps_burst_walls(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, bin_shift, vmin, dv, nv, mode=0, tol=1e-11,
+                   maxit=50, vel_at_integer=True):
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, ncell >> bin_shift, nv), np.int64)
+    fails = _load().orc_ps_burst_walls(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                       float(dt), float(qm), int(K), float(dT), int(mode), int(s_w), float(tol),
+                                       int(maxit), int(vel_at_integer), int(bin_shift), float(vmin), float(dv),
+                                       int(nv), _p(phi), _p(samples))
+    return samples, phi, int(fails)
+
+
+def ps_project(samples, dt, dT, filt=0):
+    """Projective step of the phase-space masses samples [(K+1), nxc, nv] (Section 3.3, Eqs.
+    extrapolation2 and leastsquares) with the least-squares slope filtered before the leap:
+    filt bit 0 smooths every x-bin's slope along v by (1/4, 1/2, 1/4) with zero beyond the
+    velocity range; bit 1 smooths every velocity cell's slope along x, periodically, or with
+    bit 2 reflecting at the walls (the edge value repeated, which keeps the sum). Returns
+    (out, filtered slope), both [nxc, nv]."""
+    y = _f64(samples)
+    K1, nxc, nv = y.shape
+    _, raw = ls_project(y.reshape(K1, nxc * nv), dt, dT)
+    raw = raw.reshape(nxc, nv)
+    s = raw
+    if filt & 1:
+        pad = np.zeros((nxc, nv + 2))
+        pad[:, 1:-1] = s
+        s = 0.25 * pad[:, :-2] + 0.5 * pad[:, 1:-1] + 0.25 * pad[:, 2:]
+    if filt & 2:
+        if filt & 4:
+            left = np.concatenate([s[:1], s[:-1]])
+            right = np.concatenate([s[1:], s[-1:]])
+        else:
+            left, right = np.roll(s, 1, axis=0), np.roll(s, -1, axis=0)
+        s = 0.25 * left + 0.5 * s + 0.25 * right
+    out = y[-1] + (dT - (K1 - 1) * dt) * s
+    return out, s

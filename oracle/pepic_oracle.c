@@ -1026,3 +1026,150 @@ int orc_pic_steps_walls(int64_t n, int32_t* cell, double* theta, double* v, doub
     free(E);
     return fails;
 }
+
+/* ---------------------------------------------------------------- phase space, bounded grid */
+
+/* orc_ps_sample_fx on the bounded grid: ions of weight 0 carry nothing, and an ion whose
+ * co-moving target X~ lies outside [0, (ncell-1) dx) has left the domain by t_{n+1} and is
+ * not counted (as orc_restrict_sample_walls). */
+void orc_ps_sample_fx_walls(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                            const double* w, const double* E0, int32_t ncell, double dx, double tau, double qm,
+                            int32_t bin_shift, double vmin, double dv, int32_t nv, int32_t s_w, int64_t* F)
+{
+    int32_t nxc = ncell >> bin_shift;
+    memset(F, 0, sizeof(int64_t) * (size_t)nxc * (size_t)nv);
+    for (int64_t p = 0; p < n; ++p) {
+        if (w[p] == 0.0) continue;
+        double E0p = (1.0 - theta[p]) * E0[cell[p]] + theta[p] * E0[cell[p] + 1];
+        double s = theta[p] + tau * vbar[p] / dx;
+        double k = floor(s);
+        double cn = (double)cell[p] + k;
+        if (!(cn >= 0.0 && cn < (double)(ncell - 1))) continue;
+        int32_t c = (int32_t)cn;
+        double th = s - k;
+        double vt = vbar[p] + qm * tau * E0p;
+        double jf = floor((vt - vmin) / dv);
+        int32_t j = jf < 0.0 ? 0 : (jf >= (double)nv ? nv - 1 : (int32_t)jf);
+        int64_t wq = (int64_t)llrint(ldexp(w[p], s_w));
+        int64_t tq = (int64_t)llrint(th * THETA_ONE);
+        int64_t qr = wq * tq, ql = wq * ((int64_t)THETA_ONE - tq);
+        F[(size_t)(c >> bin_shift) * nv + j] += ql;
+        F[(size_t)((c + 1) >> bin_shift) * nv + j] += qr;
+    }
+}
+
+/* Appendix C loading of the phase-space tables on the bounded grid, with equal weights.
+ * Bin i sums the CIC charge of its 2^b nodes, i.e. spans x/dx in [i 2^b - 1/2, (i+1) 2^b - 1/2)
+ * cut to the domain [0, ncell-1]: the first and last bins span 2^b - 1/2 node widths. The lifted
+ * density in x is linear between the bins' span midpoints, with value mass_i / width_i there,
+ * and constant beyond the first and last midpoints (no wrap): its values at the nodes, n_j, are
+ * the profile that orc_quiet_start_equal loads (positions by mass quantile, storage order in
+ * velocity-ordered blocks); every ion then gets w = (sum of the bin masses) / N, so lifting keeps
+ * the charge, and V = (1 - phi) G_b0(b_i) + phi G_b1(b_i) blended between the inverse CDFs of the
+ * two bins whose midpoints bracket its position (phi the fraction of the way from b0's), b_i its
+ * Hammersley quantile. */
+static double ps_mid(int32_t i, int32_t nxc, double width, int32_t ncell)
+{
+    if (i == 0) return 0.5 * (width - 0.5);
+    if (i == nxc - 1) return 0.5 * ((nxc - 1) * width - 0.5 + (double)(ncell - 1));
+    return (i + 0.5) * width - 0.5;
+}
+
+/* The bins b0 <= b1 whose midpoints bracket x (nodes), and the fraction phi of the way. */
+static void ps_bins_at(double x, int32_t nxc, double width, int32_t ncell, int32_t* b0, int32_t* b1, double* phi)
+{
+    if (nxc < 2 || x <= ps_mid(0, nxc, width, ncell)) {
+        *b0 = *b1 = 0;
+        *phi = 0.0;
+        return;
+    }
+    if (x >= ps_mid(nxc - 1, nxc, width, ncell)) {
+        *b0 = *b1 = nxc - 1;
+        *phi = 0.0;
+        return;
+    }
+    int32_t i = (int32_t)floor((x + 0.5) / width - 0.5);
+    if (i < 0) i = 0;
+    if (i > nxc - 2) i = nxc - 2;
+    while (i > 0 && x < ps_mid(i, nxc, width, ncell)) --i;
+    while (i < nxc - 2 && x >= ps_mid(i + 1, nxc, width, ncell)) ++i;
+    const double m0 = ps_mid(i, nxc, width, ncell), m1 = ps_mid(i + 1, nxc, width, ncell);
+    *b0 = i;
+    *b1 = i + 1;
+    *phi = (x - m0) / (m1 - m0);
+}
+
+void orc_ps_quiet_start_equal(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                              int32_t nv, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                              double* v, double* w)
+{
+    const int32_t nxc = ncell >> bin_shift;
+    const double width = ldexp(1.0, bin_shift);
+    double* prof = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* zero = (double*)calloc((size_t)ncell, sizeof(double));
+    double* dens = (double*)malloc(sizeof(double) * (size_t)nxc);
+    double* sig = (double*)malloc(sizeof(double) * (size_t)nxc * (size_t)nv);
+    for (int32_t i = 0; i < nxc; ++i) orc_cdf_cell_slopes(nv, cdf + (size_t)i * (nv + 1), sig + (size_t)i * nv);
+    double total = 0.0;
+    for (int32_t i = 0; i < nxc; ++i) {
+        total += mass[i];
+        const double wi = (i == 0 || i == nxc - 1) ? width - 0.5 : width;
+        dens[i] = mass[i] / wi;
+    }
+    for (int32_t j = 0; j < ncell; ++j) {
+        int32_t b0, b1;
+        double phi;
+        ps_bins_at((double)j, nxc, width, ncell, &b0, &b1, &phi);
+        prof[j] = (1.0 - phi) * dens[b0] + phi * dens[b1];
+    }
+    orc_quiet_start_equal(N, ncell, prof, zero, 0.0, seed, cell, theta, v, w);
+    uint32_t half = (uint32_t)(2147483648.0 / (double)N);
+    uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t i = s; /* point held by slot s (the loader's block order) */
+        if ((s | 4095) < N) i = (s & ~(int64_t)4095) | (int64_t)(brev32((uint32_t)(s & 4095)) >> 20);
+        int32_t b0, b1;
+        double phi;
+        ps_bins_at((double)cell[s] + theta[s], nxc, width, ncell, &b0, &b1, &phi);
+        uint32_t B = brev32((uint32_t)i) + half + shift;
+        double b = ((double)B + 0.5) * 2.3283064365386963e-10;
+        double v0 = orc_cdf_inverse(nv, cdf + (size_t)b0 * (nv + 1), sig + (size_t)b0 * nv, b, vmin, dv);
+        double v1 = orc_cdf_inverse(nv, cdf + (size_t)b1 * (nv + 1), sig + (size_t)b1 * nv, b, vmin, dv);
+        v[s] = (1.0 - phi) * v0 + phi * v1;
+        w[s] = total / (double)N;
+    }
+    free(prof);
+    free(zero);
+    free(dens);
+    free(sig);
+}
+
+int orc_ps_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                       double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol,
+                       int32_t maxit, int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv,
+                       double* phi, int64_t* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    size_t row = (size_t)(ncell >> bin_shift) * (size_t)nv;
+    int fails = field_walls(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell);
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = (w[i] == 0.0) ? v[i]
+                                    : v[i] + (kick - 0.5) * qm * dt *
+                                                 ((1.0 - theta[i]) * E[cell[i]] + theta[i] * E[cell[i] + 1]);
+        orc_ps_sample_fx_walls(n, cell, theta, vbar, w, E0, ncell, dx, dT - p * dt, qm, bin_shift, vmin, dv, nv,
+                               s_w, samples + (size_t)p * row);
+        if (p == K) break;
+        orc_push_walls(n, cell, theta, v, w, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_walls(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}

@@ -201,6 +201,35 @@ int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const doubl
                  int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi,
                  int64_t* samples);
 
+/* ---- bounded grid (Section 4.2): walls at node 0 and node ncell-1, absorbing for the ions,
+ * phi' = 0 for the potential (mirror ghosts), wall nodes at half control volume. */
+int orc_newton_pb_walls(int32_t ncell, double dx, int32_t mode, const double* dep, double* phi, double tol,
+                        int32_t maxit, int32_t* iters);
+void orc_efield_walls(int32_t ncell, double dx, const double* phi, double* E);
+void orc_push_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, const double* E,
+                    int32_t ncell, double dx, double dt, double qm, double kick);
+void orc_restrict_sample_walls(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                               const double* w, const double* E0, int32_t ncell, double dx, double tau,
+                               double qm, double* dens, double* mom);
+void orc_quiet_start_equal(int64_t N, int32_t ncell, const double* nprof, const double* uprof, double v_th,
+                           uint64_t seed, int32_t* cell, double* theta, double* v, double* w);
+int orc_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                    double dt, double qm, int32_t K, double dT, int32_t comoving, int32_t mode, int32_t s_w,
+                    double tol, int32_t maxit, int32_t vel_at_integer, double* phi, double* samples);
+int orc_pic_steps_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                        double dt, double qm, int32_t nsteps, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                        int32_t vel_at_integer, double* phi);
+void orc_ps_sample_fx_walls(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                            const double* w, const double* E0, int32_t ncell, double dx, double tau, double qm,
+                            int32_t bin_shift, double vmin, double dv, int32_t nv, int32_t s_w, int64_t* F);
+void orc_ps_quiet_start_equal(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                              int32_t nv, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                              double* v, double* w);
+int orc_ps_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, double* w, int32_t ncell, double dx,
+                       double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol,
+                       int32_t maxit, int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv,
+                       double* phi, int64_t* samples);
+
 #ifdef __cplusplus
 }
 #endif

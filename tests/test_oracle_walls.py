@@ -344,3 +344,108 @@ def test_restrict_of_lift_walls_reproduces_coarse_state():
     assert np.max(np.abs(back - c)) < 2e-3 * np.max(np.abs(c))
     # total charge is exact: sum of the weights = sum of the refined deposits
     assert st.w.sum() == pytest.approx(orc.refine(c[0], ncell).sum(), rel=1e-12)
+
+
+# ----------------------------------------------------------------- phase space on the bounded grid
+
+
+def test_ps_quiet_start_equal_uniform_tables_closed_form():
+    # equal bin masses and identical uniform velocity histograms: positions on the uniform
+    # lattice and V = v_min + (n_v dv) b_i exactly (the inverse CDF of a uniform histogram)
+    ncell, b, nv, N, seed = 64, 3, 16, 3 * 4096 + 5, 7
+    H = np.ones((ncell >> b, nv))
+    mass, cdf, bad = orc.ps_lift_tables(H)
+    assert bad == 0
+    vmin, dv = -4.0, 0.5
+    st = orc.ps_quiet_start_equal(N, ncell, b, mass, cdf, vmin, dv, seed)
+    X = _by_point(st.cell + st.theta, N)
+    # every bin's density is its mass over its width inside the domain (the wall bins are half
+    # a node narrower): the ends of the profile are denser, and the lattice follows the mass
+    width = 1 << b
+    wid = np.full(ncell >> b, float(width))
+    wid[[0, -1]] -= 0.5
+    assert np.all(np.diff(X) > 0) and X[0] > 0 and X[-1] < ncell - 1
+    i = np.arange(N, dtype=np.uint64)
+    rev = np.zeros(N, np.uint64)
+    for k in range(32):
+        rev |= ((i >> np.uint64(k)) & np.uint64(1)) << np.uint64(31 - k)
+    B = (rev + np.uint64(2**31 // N) + np.uint64(orc.splitmix64(seed) >> 32)) % np.uint64(2**32)
+    bq = (B.astype(np.float64) + 0.5) * 2.0**-32
+    interior = (bq > 1.0 / nv) & (bq < 1.0 - 1.0 / nv)  # edge cells carry a density slope
+    assert np.allclose(_by_point(st.v, N)[interior], (vmin + nv * dv * bq)[interior], atol=1e-12)
+    assert st.w.sum() == pytest.approx(mass.sum(), rel=1e-13) and np.all(st.w == st.w[0])
+
+
+def test_ps_lift_walls_restrict_reproduces_the_masses():
+    # smooth phase-space density, non-zero at the walls: the tau = 0 sample of the loaded ions
+    # returns each bin's mass to the interpolation and quadrature error, and the total exactly
+    ncell, b, nv, N = 128, 3, 32, 128 * 512
+    nxc = ncell >> b
+    vmin, dv = -6.0, 12.0 / nv
+    x = (np.arange(nxc) + 0.5) / nxc
+    vc = vmin + dv * (np.arange(nv) + 0.5)
+    n = 8.0 * (1.2 + 0.5 * np.cos(np.pi * x))
+    H = n[:, None] * np.exp(-0.5 * (vc[None, :] - 0.3) ** 2) * dv / np.sqrt(2 * np.pi)
+    mass, cdf, _ = orc.ps_lift_tables(H)
+    st = orc.ps_quiet_start_equal(N, ncell, b, mass, cdf, vmin, dv, 3)
+    s_w = orc.fx_shift(4 * st.w.max())
+    F = orc.ps_sample_fx_walls(st, st.v, np.zeros(ncell), ncell, 0.5, 0.0, 1.0, b, vmin, dv, nv, s_w)
+    got = F * 2.0 ** -(s_w + 24)
+    assert got.sum() == pytest.approx(mass.sum(), rel=1e-6)
+    # the profile linear between bin midpoints is not conservative bin by bin: its error is the
+    # reconstruction's (curvature x width^2, ~1 % for this profile), the total is exact
+    assert np.max(np.abs(got.sum(axis=1) - mass) / mass) < 0.02
+    vel_marg = got.sum(axis=0) / got.sum()
+    want_marg = H.sum(axis=0) / H.sum()
+    assert np.max(np.abs(vel_marg - want_marg)) < 0.01 * want_marg.max()
+
+
+def test_ps_sample_walls_reduces_to_the_periodic_sample_inside():
+    ncell, b, nv, N = 64, 2, 16, 3000
+    rng = np.random.default_rng(5)
+    X = 10 + rng.random(N) * 40  # far from the walls; tau v below 4 cells
+    cell = np.floor(X).astype(np.int32)
+    st = orc.State(cell, X - cell, rng.standard_normal(N) * 0.5, 0.5 + rng.random(N))
+    E0 = 0.05 * np.sin(np.arange(ncell) * 0.2)
+    a = orc.ps_sample_fx_walls(st, st.v, E0, ncell, 0.5, 3.0, 1.0, b, -4.0, 0.5, nv, 20)
+    p = orc.ps_sample_fx(st, st.v, E0, ncell, 0.5, 3.0, 1.0, b, -4.0, 0.5, nv, 20)
+    assert np.array_equal(a, p)
+
+
+@pytest.mark.parametrize("filt", [0, 1, 2, 3, 6, 7])
+def test_ps_project_filters(filt):
+    rng = np.random.default_rng(filt)
+    K, nxc, nv, dt, dT = 6, 12, 16, 0.1, 4.0
+    y = rng.standard_normal((K + 1, nxc, nv))
+    y[:, :, :2] = y[:, :, -2:] = 0.0  # empty velocity edges: the v filter then keeps both moments
+    out, s = orc.ps_project(y, dt, dT, filt)
+    c0, raw = orc.ls_project(y.reshape(K + 1, -1), dt, dT)
+    raw = raw.reshape(nxc, nv)
+    if filt == 0:
+        assert np.allclose(out, c0.reshape(nxc, nv), atol=1e-13)
+    # the slope's total is kept (charge), and with the v filter its first v moment (momentum)
+    assert s.sum() == pytest.approx(raw.sum(), abs=1e-12)
+    j = np.arange(nv)
+    assert np.allclose((s * j).sum(axis=1).sum(), (raw * j).sum(axis=1).sum(), atol=1e-11)
+    if filt & 2 and not filt & 4:  # periodic x: each velocity cell's x-sum is kept too
+        assert np.allclose(s.sum(axis=0), (orc.ps_project(y, dt, dT, filt & 1)[1]).sum(axis=0), atol=1e-12)
+    # a smooth (linear) slope in v passes the v filter unchanged away from the edges
+    assert np.allclose(out, y[-1] + (dT - K * dt) * s, atol=1e-13)
+
+
+def test_ps_burst_walls_mirror_symmetry():
+    ncell, b, nv, dx, dt, K = 128, 3, 16, 0.5, 0.1, 12
+    n, u = orc.slab_profile(ncell)
+    half = orc.quiet_start_equal(4096, ncell, n, u, 1.0, 3)
+    half.v *= 10.0
+    mir = _mirror(half, ncell)
+    st = orc.State(np.concatenate([half.cell, mir.cell]), np.concatenate([half.theta, mir.theta]),
+                   np.concatenate([half.v, mir.v]), np.concatenate([half.w, mir.w]))
+    s_w = orc.fx_shift(4 * st.w.max())
+    K = 30
+    samples, phi, fails = orc.ps_burst_walls(st, ncell, dx, dt, 1.0, K, 4.0, s_w, np.zeros(ncell), b, -32.0, 4.0,
+                                             nv, tol=1e-13)
+    assert fails == 0
+    # mirror: x-bin i <-> nxc-1-i, velocity cell j <-> nv-1-j (symmetric velocity range)
+    assert np.array_equal(samples, samples[:, ::-1, ::-1])
+    assert (st.w == 0).sum() > 0
