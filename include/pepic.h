@@ -323,7 +323,8 @@ PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, int64_t nco
 /* Projective step of the phase-space masses (Section 3.3, Eqs. extrapolation2 and
  * leastsquares) with the least-squares slope filtered before the leap: with filter bit 0 the
  * slope of every x-bin is smoothed along v by (1/4, 1/2, 1/4) (zero beyond the velocity range),
- * with bit 1 every velocity cell along x (periodic). The filter keeps the slope's sum (charge)
+ * with bit 1 every velocity cell along x (periodic; with bit 2 as well, reflecting at the walls
+ * of a bounded grid: the edge bin's slope stands in beyond it). The filter keeps the slope's sum (charge)
  * and, along v, its first moment (momentum); it damps the grid-scale structure of the slope,
  * which the leap multiplies by (dT - K dt) / (K dt / 2). samples[(K+1)][nxc][n_v]; work, out and
  * slope [nxc][n_v] (work: the unfiltered slope; slope: the filtered one; none may alias
@@ -363,6 +364,23 @@ PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, in
                              double dv, uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
                              void* stream);
 
+/* The phase-space loading on a bounded grid (walls at nodes 0 and ncell-1), with equal
+ * weights placed by mass. Bin i sums the CIC charge of its 2^b nodes, x/dx in
+ * [i 2^b - 1/2, (i+1) 2^b - 1/2) cut to the domain [0, ncell-1] (the first and last bins are
+ * half a node narrower); the lifted density in x is linear between the bins' span midpoints,
+ * with value mass_i / width_i there, and constant beyond the first and last midpoints. Its
+ * nodal values are loaded by pe_quiet_start_equal's rule (positions by mass quantile, storage in
+ * velocity-ordered blocks of 4096); every ion gets w = (sum of the bin masses) / n, so lifting
+ * keeps the charge; V = (1 - phi) G_b0(b) + phi G_b1(b) blends the inverse CDFs of the two
+ * bins whose midpoints bracket the ion (phi the fraction of the way from b0's), with b the
+ * ion's Hammersley quantile and G as in pe_ps_quiet_start. scratch: PE_PS_EQ_SCRATCH_BYTES(ncell)
+ * bytes of device memory, 16-byte aligned. */
+#define PE_PS_EQ_SCRATCH_BYTES(ncell) (24 * (size_t)(ncell) + 32)
+PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                   int32_t bin_shift, const double* mass, const float* table, int32_t n_v,
+                                   double v_min, double dv, uint64_t seed, int32_t s_w, void* scratch,
+                                   int64_t* rho_fx, uint32_t* status, void* stream);
+
 /* =================================================================== context
  * One realisation of the projective-integration cycle (Section 3.1, Figure
  * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares
@@ -391,8 +409,8 @@ typedef struct pe_config {
     int32_t n_v;          /* phase space: velocity cells (2..256) */
     double v_max;         /* phase space: velocity range [-v_max, v_max) */
     int32_t ps_filter;    /* phase space: 1-2-1 filter of the projected slope; bit 0 in v, bit 1 in x */
-    int32_t boundary;     /* PE_BOUNDARY_*; absorbing grids lift with pe_quiet_start_equal and
-                             take the moment coarse variables only */
+    int32_t boundary;     /* PE_BOUNDARY_*; absorbing grids lift with pe_quiet_start_equal
+                             (moments) or pe_ps_quiet_start_equal (phase space) */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;

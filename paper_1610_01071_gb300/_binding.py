@@ -141,6 +141,8 @@ SIGNATURES = {
     "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
     "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
     "pe_ps_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
+    "pe_ps_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P,
+                                               P]),
     "pe_mlp_layout_for": (ctypes.c_int, [i32, P, i32, ctypes.POINTER(MLPLayout)]),
     "pe_mlp_create": (ctypes.c_int, [i32, P, i32, P, sz, P, ctypes.POINTER(P)]),
     "pe_mlp_destroy": (None, [P]),
@@ -408,6 +410,35 @@ def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_
                                    _ptr(table), (table.shape[1] - 1) // 3, float(v_min), float(dv),
                                    int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(rho), _ptr(status),
                                    _stream(stream)), "pe_ps_quiet_start")
+    return cell, theta, v, w, rho
+
+
+def ps_project(samples, dt, dT, filt=0, stream=None):
+    """Filtered phase-space projective step (pe_ps_project) of samples [(K+1), nxc, n_v] (FP64,
+    device); returns (out, filtered slope), each [nxc, n_v]."""
+    K, nxc, nv = samples.shape[0] - 1, samples.shape[1], samples.shape[2]
+    out = torch.empty((nxc, nv), dtype=torch.float64, device=samples.device)
+    slope, work = torch.empty_like(out), torch.empty_like(out)
+    check(load().pe_ps_project(_ptr(samples), K, nxc, nv, float(dt), float(dT), int(filt), _ptr(work), _ptr(out),
+                               _ptr(slope), _stream(stream)), "pe_ps_project")
+    return out, slope
+
+
+def ps_quiet_start_equal(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_rho=True, status=None,
+                         stream=None):
+    """Phase-space loading of a bounded grid with equal weights (pe_ps_quiet_start_equal)."""
+    dev = mass.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    scratch = torch.empty((24 * ncell + 32 + 7) // 8, dtype=torch.float64, device=dev)
+    status = _status(status, dev)
+    check(load().pe_ps_quiet_start_equal(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, int(bin_shift),
+                                         _ptr(mass), _ptr(table), (table.shape[1] - 1) // 3, float(v_min), float(dv),
+                                         int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(scratch), _ptr(rho),
+                                         _ptr(status), _stream(stream)), "pe_ps_quiet_start_equal")
     return cell, theta, v, w, rho
 
 

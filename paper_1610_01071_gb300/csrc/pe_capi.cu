@@ -143,7 +143,6 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.ps_filter < 0 || c.ps_filter > 3) return PE_EINVAL;
     if (c.boundary != PE_BOUNDARY_PERIODIC && c.boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
     const bool walls = c.boundary == PE_BOUNDARY_ABSORBING;
-    if (walls && ps) return PE_EINVAL;  // the phase-space variable is built for periodic grids
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
@@ -165,10 +164,11 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_STATUS] = 64;
     out->bytes[PE_BUF_DIAG] = PE_MOMENTS_SCRATCH_BYTES + 256;
     out->bytes[PE_BUF_SURROGATE] = align256(8 * 2 * ncoef) + 256;
-    out->bytes[PE_BUF_PHASE] = ps ? align256(8 * ncoef) + align256(8 * ncoef * (size_t)(c.n_v + 1)) +
-                                        align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
-                                        align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
-                                  : (walls ? align256(PE_EQ_SCRATCH_BYTES(nc)) : 256);
+    out->bytes[PE_BUF_PHASE] = (ps ? align256(8 * ncoef) + align256(8 * ncoef * (size_t)(c.n_v + 1)) +
+                                         align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
+                                         align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
+                                   : 256) +
+                                (walls ? align256(PE_PS_EQ_SCRATCH_BYTES(nc)) : 0);
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -237,7 +237,11 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
         x->ps_flags = (int32_t*)((char*)x->ps_table + align256(4 * nc_ * (3 * (size_t)x->nv + 1)));
         if (!x->ps) x->ps_flags = (int32_t*)ph;
         x->walls = cfg->boundary == PE_BOUNDARY_ABSORBING;
-        x->eq_scratch = x->walls ? (void*)ph : nullptr;
+        // equal-weight loading scratch after the phase-space tables (bounded grids)
+        const size_t ps_bytes = x->ps ? align256(8 * nc_) + align256(8 * nc_ * nv1) + align256(8 * 2 * nc_ * nv1) +
+                                             align256(4 * nc_ * (3 * (size_t)x->nv + 1)) + 256
+                                       : 256;
+        x->eq_scratch = x->walls ? (void*)(ph + ps_bytes) : nullptr;
     }
     if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||
         cudaMemsetAsync(x->status, 0, 64, x->stream) != cudaSuccess) {
@@ -525,8 +529,9 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
     const pe_config& c = ctx->cfg;
     if (ctx->ps && c.ps_filter) {
         double* work = ctx->csamples + (size_t)(c.K + 1) * (size_t)ctx->crow;  // measurement row as scratch
-        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, c.dT, c.ps_filter, work, ctx->coarse,
-                             ctx->slope, ctx->stream));
+        const int filt = c.ps_filter | ((ctx->walls && (c.ps_filter & 2)) ? 4 : 0);  // reflecting x at walls
+        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, c.dT, filt, work, ctx->coarse, ctx->slope,
+                             ctx->stream));
     } else {
         PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
     }
@@ -547,6 +552,10 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
                                  x->stream));
         const int b = x->bank;
         PE_TRY(timed(x, 0, [&] {
+            if (x->walls)
+                return pe_ps_quiet_start_equal(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell,
+                                               x->bin_shift, x->ps_mass, x->ps_table, x->nv, x->vmin, x->dv,
+                                               lift_seed(x), x->s_w, x->eq_scratch, x->rho, x->status, x->stream);
             return pe_ps_quiet_start(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->bin_shift,
                                      x->ps_mass, x->ps_table, x->nv, x->vmin, x->dv, lift_seed(x), x->s_w, x->rho,
                                      x->status, x->stream);

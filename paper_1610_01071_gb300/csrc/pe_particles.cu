@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "pe_common.cuh"
+#include "pe_eq.cuh"
 #include "pe_internal.h"
 
 namespace pe {
@@ -491,72 +492,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
 }
 
 // ------------------------------------------------------------------ equal-weight loading
-
-// Scratch of the equal-weight loading: cumulative cell masses and first particle of each
-// cell. Layout in the caller's scratch: double C[ncl + 1], int64 first[ncl + 1], double MoN.
-struct EqTable {
-    const double* C;
-    const long long* first;
-    const double* MoN;
-};
-
-constexpr int kEqThreads = 1024;
-
-// One block: cell masses m_c = (n_c f_c + n_{c+1} f_{c+1}) / 2 of the linear profile over
-// the ncl = ncell - 1 cells between the walls (f = wall_factor on the wall nodes, 1 inside),
-// their cumulative sums C (each thread sums a contiguous run of cells, then an exclusive scan
-// of the run totals in a fixed order), M = C[ncl], MoN = M / n and
-// first[c] = ceil(C_c n / M - 1/2), the first particle i with (i + 1/2) M / n >= C_c.
-__global__ void __launch_bounds__(kEqThreads) k_eq_table(const float* __restrict__ prof_n, int ncell,
-                                                        float wall_factor, int64_t n, double* C, long long* first,
-                                                        double* MoN, uint32_t* status)
-{
-    __shared__ double part[kEqThreads];
-    const int ncl = ncell - 1;
-    const int per = (ncl + kEqThreads - 1) / kEqThreads;
-    const int t = threadIdx.x;
-    const int c0 = t * per, c1 = (c0 + per < ncl) ? c0 + per : ncl;
-    auto dens = [&](int j) {
-        const double v = (double)prof_n[j];
-        return (j == 0 || j == ncell - 1) ? v * (double)wall_factor : v;
-    };
-    double run = 0.0;
-    for (int c = c0; c < c1; ++c) run += 0.5 * (dens(c) + dens(c + 1));
-    part[t] = run;
-    __syncthreads();
-    if (t == 0) {  // exclusive scan of the 1024 run totals (serial: fixed order, ~1k adds)
-        double acc = 0.0;
-        for (int k = 0; k < kEqThreads; ++k) {
-            const double v = part[k];
-            part[k] = acc;
-            acc += v;
-        }
-    }
-    __syncthreads();
-    double acc = part[t];
-    for (int c = c0; c < c1; ++c) {
-        C[c] = acc;
-        acc += 0.5 * (dens(c) + dens(c + 1));
-    }
-    if (c1 == ncl && c0 < c1) C[ncl] = acc;
-    __syncthreads();
-    const double M = C[ncl];
-    const bool ok = M > 0.0 && isfinite(M);
-    if (t == 0) {
-        *MoN = ok ? M / (double)n : 0.0;
-        if (!ok) raise_flag(status, PE_FLAG_RANGE);
-    }
-    for (int c = t; c <= ncl; c += kEqThreads) {
-        long long f;
-        if (!ok) {
-            f = (c == 0) ? 0 : n;  // no mass: every particle in cell 0 with weight 0
-        } else {
-            const double q = ceil(C[c] * ((double)n / M) - 0.5);
-            f = q < 0.0 ? 0 : (q > (double)n ? n : (long long)q);
-        }
-        first[c] = (c == ncl) ? n : f;
-    }
-}
+// (cumulative-mass table, positions and storage order: pe_eq.cuh)
 
 struct EqParams {
     int32_t* cell;
@@ -577,43 +513,13 @@ struct EqParams {
     uint32_t* status;
 };
 
-// Cell of particle i: the largest c in [0, ncl) with first[c] <= i (binary search; always
-// in range whatever the table holds).
-__device__ __forceinline__ int eq_cell_of(const EqParams& P, long long i)
-{
-    int lo = 0, hi = P.ncell - 1;  // first[lo] <= i < first[hi] on a valid table
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(P.tab.first + mid) <= i) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
 {
-    // walk forward from a cell at or before the point's
-    while (c < P.ncell - 2 && __ldg(P.tab.first + c + 1) <= (long long)i) ++c;
-    const double C0 = __ldg(P.tab.C + c), C1 = __ldg(P.tab.C + c + 1);
-    const double MoN = __ldg(P.tab.MoN);
-    const double mc = C1 - C0;
-    double r = mc > 0.0 ? (((double)i + 0.5) * MoN - C0) / mc : 0.5;
-    r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
-    float n0 = __ldg(P.prof_n + c), n1 = __ldg(P.prof_n + c + 1);
-    if (c == 0) n0 *= P.wall_factor;
-    if (c + 1 == P.ncell - 1) n1 *= P.wall_factor;
-    const float sum = n0 + n1;
-    const float sig = sum > 0.0f ? (n1 - n0) / sum : 0.0f;
-    // mass of the linear density 1 + sig (2t - 1) up to t is t + sig (t^2 - t) = r
-    const float rf = (float)r;
-    const float om = 1.0f - sig;
-    const float den = om + sqrtf(fmaxf(om * om + 4.0f * sig * rf, 0.0f));
-    float t = den > 0.0f ? 2.0f * rf / den : 0.0f;
-    t = fminf(fmaxf(t, 0.0f), 0.99999994f);  // stay inside the cell (largest float below 1)
+    const float t = eq_position(P.tab, P.prof_n, P.wall_factor, P.ncell, i, c);
     th = t;
     const float u0 = __ldg(P.prof_u + c), u1 = __ldg(P.prof_u + c + 1);
     const float uX = fmaf(t, u1 - u0, u0);
-    ww = (float)MoN;
+    ww = (float)__ldg(P.tab.MoN);
     const uint32_t Bi = __brev(i) + P.half + P.shift;
     const bool upper = (Bi & 0x80000000u) != 0u;
     const uint32_t bs = upper ? ~Bi : Bi;
@@ -622,28 +528,13 @@ __device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, fl
     vv = fmaf(P.v_th, upper ? -z : z, uX);
 }
 
-// Storage order of the equal-weight loading: inside every full aligned block of 2^kEqBlockBits
-// slots, slot s holds point i = s with its low kEqBlockBits bits reversed, so that the block's
-// points (all within 2^kEqBlockBits mass quantiles of each other) are stored in ascending
-// velocity quantile, as a power-of-two cell of pe_quiet_start stores its points: the 128
-// slots a warp visits at once then span 1/32 of the velocity range and their co-moving
-// targets stay together. The ragged tail keeps i = s. The reversal is its own inverse.
-constexpr int kEqBlockBits = 12;
-constexpr uint32_t kEqBlockMask = (1u << kEqBlockBits) - 1u;
-
-__device__ __forceinline__ uint32_t eq_point_of_slot(uint32_t s, int64_t n)
-{
-    return ((int64_t)(s | kEqBlockMask) < n) ? ((s & ~kEqBlockMask) | (__brev(s & kEqBlockMask) >> (32 - kEqBlockBits)))
-                                              : s;
-}
-
 __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
     block_chunk(P.n, P.chunk, &begin, &end);
     const bool dep = P.rho != nullptr;
-    const int c_first = (begin < end) ? eq_cell_of(P, eq_point_of_slot((uint32_t)begin, P.n)) : 0;
+    const int c_first = (begin < end) ? eq_cell_of(P.tab, P.ncell, eq_point_of_slot((uint32_t)begin, P.n)) : 0;
     SmemGrid grho{};
     if (dep) {
         grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
@@ -669,7 +560,7 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
                        p2 = eq_point_of_slot(s0 + 2, P.n), p3 = eq_point_of_slot(s0 + 3, P.n);
         // the four points lie within one block; search from the smallest
         const uint32_t pmin = min(min(p0, p1), min(p2, p3));
-        const int cb = eq_cell_of(P, pmin);
+        const int cb = eq_cell_of(P.tab, P.ncell, pmin);
         c.x = c.y = c.z = c.w = cb;
         eq_one(P, p0, c.x, t.x, vv.x, ww.x);
         eq_one(P, p1, c.y, t.y, vv.y, ww.y);
@@ -688,7 +579,7 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
     }
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         const uint32_t pi = eq_point_of_slot((uint32_t)i, P.n);
-        int c = eq_cell_of(P, pi);
+        int c = eq_cell_of(P.tab, P.ncell, pi);
         float t, vv, ww;
         eq_one(P, pi, c, t, vv, ww);
         P.cell[i] = c;
@@ -1122,7 +1013,7 @@ extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v
     double* C = static_cast<double*>(scratch);
     long long* first = reinterpret_cast<long long*>(C + ncl + 1);
     double* MoN = reinterpret_cast<double*>(first + ncl + 1);
-    k_eq_table<<<1, kEqThreads, 0, s>>>(prof_n, ncell, wall_factor, n, C, first, MoN, status);
+    k_eq_table<float><<<1, kEqThreads, 0, s>>>(prof_n, ncell, wall_factor, n, C, first, MoN, status);
     EqParams P{};
     P.cell = cell;
     P.theta = theta;

@@ -8,7 +8,9 @@
 //     velocity CDF (Appendix C), one thread per bin, in FP64 with every operation rounded
 //     separately (no contraction) so the tables are reproducible bit for bit;
 //   - pe_ps_quiet_start: the Hammersley loading of Appendix C on those tables, with the
-//     charge deposit of the new particles fused.
+//     charge deposit of the new particles fused;
+//   - pe_ps_quiet_start_equal: the same on a bounded grid, with equal weights placed by the
+//     mass of the bins (the equal-weight loader of pe_eq.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -17,6 +19,7 @@
 #include <algorithm>
 
 #include "pe_common.cuh"
+#include "pe_eq.cuh"
 #include "pe_internal.h"
 #include "pepic.h"
 
@@ -378,7 +381,10 @@ __global__ void k_ps_leap(const double* __restrict__ c, const double* __restrict
     const int i = idx / nv, j = idx - i * nv;
     auto at = [&](int ii, int jj) -> double {
         if (jj < 0 || jj >= nv) return 0.0;
-        ii = (ii + nxc) % nxc;
+        if (filter & 4)  // bounded grid: reflecting at the walls (keeps the sum)
+            ii = ii < 0 ? 0 : (ii >= nxc ? nxc - 1 : ii);
+        else
+            ii = (ii + nxc) % nxc;
         return raw[(size_t)ii * nv + jj];
     };
     auto vfilt = [&](int ii) -> double {
@@ -393,6 +399,167 @@ __global__ void k_ps_scale(const long long* __restrict__ src, int64_t n, double 
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (double)src[i] * scale;
+}
+
+// ---- bounded grid: equal-weight loading of the phase-space tables
+// Bin i sums the CIC charge of its 2^b nodes, x/dx in [i 2^b - 1/2, (i+1) 2^b - 1/2), cut to
+// the domain [0, ncell - 1]: the first and last bins are half a node narrower. The lifted
+// density in x is linear between the bins' span midpoints, mass_i / width_i there, constant
+// beyond the first and last midpoints.
+__device__ __forceinline__ double ps_mid(int i, int nxc, double width, int ncell)
+{
+    if (i == 0) return 0.5 * (width - 0.5);
+    if (i == nxc - 1) return 0.5 * ((nxc - 1) * width - 0.5 + (double)(ncell - 1));
+    return (i + 0.5) * width - 0.5;
+}
+
+// Bins b0 <= b1 whose midpoints bracket x (in nodes) and the fraction phi of the way.
+__device__ __forceinline__ void ps_bracket(double x, int nxc, double width, int ncell, int& b0, int& b1, double& phi)
+{
+    if (nxc < 2 || x <= ps_mid(0, nxc, width, ncell)) {
+        b0 = b1 = 0;
+        phi = 0.0;
+        return;
+    }
+    if (x >= ps_mid(nxc - 1, nxc, width, ncell)) {
+        b0 = b1 = nxc - 1;
+        phi = 0.0;
+        return;
+    }
+    int i = (int)floor((x + 0.5) / width - 0.5);
+    i = i < 0 ? 0 : (i > nxc - 2 ? nxc - 2 : i);
+    while (i > 0 && x < ps_mid(i, nxc, width, ncell)) --i;
+    while (i < nxc - 2 && x >= ps_mid(i + 1, nxc, width, ncell)) ++i;
+    const double m0 = ps_mid(i, nxc, width, ncell), m1 = ps_mid(i + 1, nxc, width, ncell);
+    b0 = i;
+    b1 = i + 1;
+    phi = (x - m0) / (m1 - m0);
+}
+
+// One block: the nodal profile prof[ncell] (FP64) of the bin densities and total = sum of the
+// bin masses (fixed-order tree).
+__global__ void __launch_bounds__(1024) k_ps_profile(const double* __restrict__ mass, int nxc, int bin_shift,
+                                                     int ncell, double* __restrict__ prof, double* total)
+{
+    __shared__ double red[32];
+    const double width = ldexp(1.0, bin_shift);
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        int b0, b1;
+        double phi;
+        ps_bracket((double)j, nxc, width, ncell, b0, b1, phi);
+        const double w0 = (b0 == 0 || b0 == nxc - 1) ? width - 0.5 : width;
+        const double w1 = (b1 == 0 || b1 == nxc - 1) ? width - 0.5 : width;
+        prof[j] = (1.0 - phi) * (mass[b0] / w0) + phi * (mass[b1] / w1);
+    }
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nxc; i += blockDim.x) acc += mass[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) *total = v;
+    }
+}
+
+struct PSEqLoad {
+    int32_t* cell;
+    float* theta;
+    float* v;
+    float* w;
+    int64_t n, chunk;
+    int ncell, mask, bin_shift, nv, nxc;
+    float vmin, dv;
+    const double* prof;
+    const double* total;
+    EqTable tab;
+    const float* table;
+    uint32_t half, shift;
+    float wscale;
+    unsigned long long* rho;
+    int rho_width;
+    uint32_t* status;
+};
+
+__device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+{
+    const float t = eq_position(P.tab, P.prof, 1.0f, P.ncell, i, c);
+    th = t;
+    int b0, b1;
+    double phi;
+    ps_bracket((double)c + (double)t, P.nxc, ldexp(1.0, P.bin_shift), P.ncell, b0, b1, phi);
+    const uint32_t B = __brev(i) + P.half + P.shift;
+    const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const int row = 3 * P.nv + 1;
+    const float v0 = cdf_inverse_f(P.table + (size_t)b0 * row, P.nv, b, P.vmin, P.dv);
+    const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
+    const float ph = (float)phi;
+    vv = fmaf(ph, v1 - v0, v0);
+    ww = (float)(__ldg(P.total) / (double)P.n);
+}
+
+__global__ void __launch_bounds__(256) k_ps_quiet_start_equal(PSEqLoad P)
+{
+    extern __shared__ uint32_t smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const bool dep = P.rho != nullptr;
+    const int c_first = (begin < end) ? eq_cell_of(P.tab, P.ncell, eq_point_of_slot((uint32_t)begin, P.n)) : 0;
+    SmemGrid grho{};
+    if (dep) {
+        grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        grho.zero();
+    }
+    __syncthreads();
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    LaneWindow lw;
+    lw.reset((c_first - 1) & P.mask);
+    bool ovf = false;
+    int4* cell4 = reinterpret_cast<int4*>(P.cell);
+    float4* th4 = reinterpret_cast<float4*>(P.theta);
+    float4* v4 = reinterpret_cast<float4*>(P.v);
+    float4* w4 = reinterpret_cast<float4*>(P.w);
+    for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+        int4 c;
+        float4 t, vv, ww;
+        const uint32_t s0 = (uint32_t)(g << 2);
+        const uint32_t p0 = eq_point_of_slot(s0, P.n), p1 = eq_point_of_slot(s0 + 1, P.n),
+                       p2 = eq_point_of_slot(s0 + 2, P.n), p3 = eq_point_of_slot(s0 + 3, P.n);
+        const int cb = eq_cell_of(P.tab, P.ncell, min(min(p0, p1), min(p2, p3)));
+        c.x = c.y = c.z = c.w = cb;
+        ps_eq_one(P, p0, c.x, t.x, vv.x, ww.x);
+        ps_eq_one(P, p1, c.y, t.y, vv.y, ww.y);
+        ps_eq_one(P, p2, c.z, t.z, vv.z, ww.z);
+        ps_eq_one(P, p3, c.w, t.w, vv.w, ww.w);
+        cell4[g] = c;
+        th4[g] = t;
+        v4[g] = vv;
+        w4[g] = ww;
+        if (dep) {
+            lw.add(c.x, fx_split(fx_weight_q(ww.x, P.wscale, &ovf), t.x), grho);
+            lw.add(c.y, fx_split(fx_weight_q(ww.y, P.wscale, &ovf), t.y), grho);
+            lw.add(c.z, fx_split(fx_weight_q(ww.z, P.wscale, &ovf), t.z), grho);
+            lw.add(c.w, fx_split(fx_weight_q(ww.w, P.wscale, &ovf), t.w), grho);
+        }
+    }
+    for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
+        const uint32_t pi = eq_point_of_slot((uint32_t)i, P.n);
+        int c = eq_cell_of(P.tab, P.ncell, pi);
+        float t, vv, ww;
+        ps_eq_one(P, pi, c, t, vv, ww);
+        P.cell[i] = c;
+        P.theta[i] = t;
+        P.v[i] = vv;
+        P.w[i] = ww;
+        if (dep) lw.add(c, fx_split(fx_weight_q(ww, P.wscale, &ovf), t), grho);
+    }
+    if (dep) lw.flush(grho);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
+    __syncthreads();
+    if (dep) grho.flush();
 }
 
 }  // namespace
@@ -415,7 +582,7 @@ extern "C" PE_API int pe_ps_coarsen(const int64_t* sample_fx, int32_t nsamples, 
 extern "C" PE_API int pe_ps_project(const double* samples, int32_t K, int32_t nxc, int32_t n_v, double dt, double dT,
                                     int32_t filter, double* work, double* out, double* slope, void* stream)
 {
-    if (!samples || !work || !out || !slope || K < 1 || nxc < 1 || n_v < 1 || !(dt > 0.0) || filter < 0 || filter > 3)
+    if (!samples || !work || !out || !slope || K < 1 || nxc < 1 || n_v < 1 || !(dt > 0.0) || filter < 0 || filter > 7)
         return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = nxc * n_v;
@@ -489,4 +656,65 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
     return launch_status(1);
+}
+
+extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                                              int32_t ncell, int32_t bin_shift, const double* mass, const float* table,
+                                              int32_t n_v, double v_min, double dv, uint64_t seed, int32_t s_w,
+                                              void* scratch, int64_t* rho_fx, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !mass || !table || !scratch || n_v < 1 || !(dv > 0.0)) return PE_EINVAL;
+    if (bin_shift < 0 || (1 << bin_shift) > ncell) return PE_EINVAL;
+    if (n <= 0 || n >= (int64_t(1) << 32) || ((uintptr_t)scratch & 15u)) return PE_EINVAL;
+    if (!cell || !theta || !v || !w || !aligned16(cell) || !aligned16(theta) || !aligned16(v) || !aligned16(w))
+        return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nxc = ncell >> bin_shift, ncl = ncell - 1;
+    double* prof = static_cast<double*>(scratch);                       // [ncell]
+    double* C = prof + ncell;                                            // [ncl + 1]
+    long long* first = reinterpret_cast<long long*>(C + ncl + 1);        // [ncl + 1]
+    double* MoN = reinterpret_cast<double*>(first + ncl + 1);           // [1]
+    double* total = MoN + 1;                                             // [1]
+    k_ps_profile<<<1, 1024, 0, s>>>(mass, nxc, bin_shift, ncell, prof, total);
+    k_eq_table<double><<<1, kEqThreads, 0, s>>>(prof, ncell, 1.0f, n, C, first, MoN, status);
+    PSEqLoad P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.bin_shift = bin_shift;
+    P.nv = n_v;
+    P.nxc = nxc;
+    P.vmin = (float)v_min;
+    P.dv = (float)dv;
+    P.prof = prof;
+    P.total = total;
+    P.tab = EqTable{C, first, MoN};
+    P.table = table;
+    P.half = (uint32_t)(2147483648.0 / (double)n);
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL;  // splitmix64 of the seed: the shift is its upper half
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    P.shift = (uint32_t)(z >> 32);
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
+    P.status = status;
+    const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const void* k = (const void*)k_ps_quiet_start_equal;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    int64_t c = (n + blocks - 1) / blocks;
+    c = (c + 3) & ~int64_t(3);
+    if (c < 4) c = 4;
+    if (c > kMaxChunk) c = kMaxChunk;
+    P.chunk = c;
+    const int grid = (int)((n + c - 1) / c);
+    if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    k_ps_quiet_start_equal<<<grid, 256, smem, s>>>(P);
+    return launch_status(3);
 }

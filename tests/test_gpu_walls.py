@@ -18,6 +18,7 @@ import torch
 
 import oracle as orc
 import paper_1610_01071_gb300 as pe
+from paper_1610_01071_gb300 import _binding as pb
 from paper_1610_01071_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -288,3 +289,102 @@ def test_context_slab_projective_steps_follow_plain_pic():
     assert q_ref < q0 and q_ef < q0
     assert abs(q_ef - q_ref) < 0.3 * q0
     assert eps < 0.3
+
+
+# ----------------------------------------------------------------- phase space on the bounded grid
+
+
+@pytest.mark.parametrize("filt", [0, 1, 2, 3, 6, 7])
+def test_ps_project_filters_match_oracle(filt):
+    rng = np.random.default_rng(10 + filt)
+    K, nxc, nv = 10, 32, 24
+    y = rng.standard_normal((K + 1, nxc, nv))
+    out, sl = pb.ps_project(*to_dev(y), 0.1, 4.0, filt)
+    want, wsl = orc.ps_project(y, 0.1, 4.0, filt)
+    assert np.allclose(sl.cpu().numpy(), wsl, rtol=1e-12, atol=1e-12)
+    assert np.allclose(out.cpu().numpy(), want, rtol=1e-12, atol=1e-11)
+
+
+def _ps_tables(nxc, nv, vmin, dv, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nxc) + 0.5) / nxc
+    vc = vmin + dv * (np.arange(nv) + 0.5)
+    n = 8.0 * (1.0 + 0.6 * np.cos(np.pi * x)) * (x > 0.2)  # vacuum on the left
+    H = n[:, None] * np.exp(-0.5 * ((vc[None, :] - 0.5 * np.sin(np.pi * x)[:, None]) / 0.8) ** 2) * dv
+    H *= 1.0 + 0.05 * rng.standard_normal(H.shape)
+    return H
+
+
+@pytest.mark.parametrize("ncell,b,nv,N", [(64, 2, 16, 3 * 4096 + 6), (512, 4, 32, 1 << 16), (8192, 4, 64, 1 << 21)])
+def test_ps_quiet_start_equal_matches_oracle(ncell, b, nv, N):
+    nxc = ncell >> b
+    vmin, dv = -6.0, 12.0 / nv
+    H = _ps_tables(nxc, nv, vmin, dv, ncell)
+    mass, cdf, table, _ = pb.ps_lift_tables(*to_dev(H))
+    s_w = orc.fx_shift(4.0 * float(mass.sum()) / N)
+    st = status_word()
+    cell, theta, v, w, rho = pb.ps_quiet_start_equal(N, ncell, b, mass, table, vmin, dv, 99, s_w, status=st)
+    so = orc.ps_quiet_start_equal(N, ncell, b, mass.cpu().numpy(), cdf.cpu().numpy(), vmin, dv, 99)
+    gc, gt, gv, gw = (x.cpu().numpy() for x in (cell, theta, v, w))
+    assert int(st.item()) == 0
+    assert np.max(np.abs((gc + gt.astype(np.float64)) - (so.cell + so.theta))) < 2e-6 * max(1.0, ncell / 1024)
+    assert np.all((gc >= 0) & (gc < ncell - 1)) and np.all((gt >= 0) & (gt < 1))
+    assert np.allclose(gw, so.w, rtol=1e-7)
+    assert np.max(np.abs(gv - so.v)) < 5e-5 * (abs(vmin) + 1)
+    assert torch.equal(rho, pe.deposit(cell, theta, w, ncell, s_w))
+    # equal weights, placed by mass: the vacuum bins receive no ions
+    assert np.all(gc[gw > 0] >= int(0.2 * ncell) - (1 << b))
+
+
+def _small_ps_slab_cfg(**kw):
+    c = dict(ncell=256, n_coarse=32, K=10, nparticles=256 * 128, L=128.0, dt=0.1, dT=4.0, v_th=1.0, seed=5,
+             boundary="absorbing", newton_tol=1e-12, newton_maxit=80, coarse="phase_space", n_v=32, v_max=8.0,
+             ps_filter=3)
+    c.update(kw)
+    return pe.make_config(c.pop("ncell"), c.pop("n_coarse"), c.pop("K"), c.pop("nparticles"), c.pop("L"),
+                          c.pop("dt"), c.pop("dT"), **c)
+
+
+def test_context_ps_slab_burst_matches_oracle():
+    cfg = _small_ps_slab_cfg()
+    ctx = pe.Context(cfg, device=DEV)
+    ctx.load_initial(profile="slab")
+    c, t, v, w = _ctx_state(ctx)
+    s_w = ctx.diagnostics().s_w
+    st = orc.State(c, t, v, w)
+    samples, phi, fails = orc.ps_burst_walls(st, 256, 0.5, 0.1, 1.0, 10, 4.0, s_w, np.zeros(256), 3, -8.0, 0.5, 32,
+                                             tol=1e-12)
+    assert fails == 0
+    ctx.burst()
+    assert ctx.sync_status() == 0
+    got = ctx.view("samples_fx", torch.int64, 11 * 32 * 32).cpu().numpy().reshape(11, 32, 32)
+    for p in (0, 5, 10):
+        g, h = got[p].astype(np.float64), samples[p].astype(np.float64)
+        assert int(got[p].astype(object).sum()) == pytest.approx(int(samples[p].astype(object).sum()), rel=1e-4)
+        assert np.abs(g - h).sum() <= 2e-3 * h.sum(), p
+
+
+def test_context_ps_slab_projective_steps_follow_plain_pic():
+    # the phase-space variable on the bounded grid, against the resolved run at T = 20 (the
+    # moment variables lose 26 % of the charge by then against 9 % resolved)
+    cfg = _small_ps_slab_cfg()
+    ef = pe.Context(cfg, device=DEV)
+    ref = pe.Context(_small_slab_cfg(), device=DEV)
+    ef.load_initial(profile="slab")
+    ref.load_initial(profile="slab")
+    q0 = ref.moments()["charge"]
+    for _ in range(5):
+        ef.step()
+    ref.pic_steps(5 * 40)
+    assert ef.sync_status() == 0 and ref.sync_status() == 0
+    H = ef.get_coarse().cpu().numpy()  # [nxc, n_v] masses
+    nb = 256 // 32
+    dens = H.sum(axis=1) * 2.0 ** (-(np.log2(256) + 3) / 2)  # Haar density coefficient of each bin
+    want = ref.measure().cpu().numpy()[0]
+    eps = float(np.sqrt(np.sum((dens - want) ** 2) / np.sum(dens**2 + want**2)))
+    ef.lift()
+    q_ef, q_ref = ef.moments()["charge"], ref.moments()["charge"]
+    print(f"slab phase space T=20: eps {eps:.4f}, charge left projective {q_ef / q0:.4f}, resolved {q_ref / q0:.4f}")
+    assert np.all(np.isfinite(H)) and nb == 8
+    assert abs(q_ef - q_ref) < 0.05 * q0
+    assert eps < 0.05
