@@ -371,9 +371,11 @@ PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, in
  * with value mass_i / width_i there, and constant beyond the first and last midpoints. Its
  * nodal values are loaded by pe_quiet_start_equal's rule (positions by mass quantile, storage in
  * velocity-ordered blocks of 4096); every ion gets w = (sum of the bin masses) / n, so lifting
- * keeps the charge; V = (1 - phi) G_b0(b) + phi G_b1(b) blends the inverse CDFs of the two
- * bins whose midpoints bracket the ion (phi the fraction of the way from b0's), with b the
- * ion's Hammersley quantile and G as in pe_ps_quiet_start. scratch: PE_PS_EQ_SCRATCH_BYTES(ncell)
+ * keeps the charge; V = (1 - f) G_b0(b) + f G_b1(b) blends the inverse CDFs of the two bins
+ * whose midpoints bracket the ion, with b the ion's Hammersley quantile, G as in
+ * pe_ps_quiet_start, and f = phi d1 / ((1 - phi) d0 + phi d1) bin b1's share of the density at
+ * the ion (phi the fraction of the way from b0's midpoint, d the bin densities): a bin without
+ * ions, next to the expansion front, then lends no velocities. scratch: PE_PS_EQ_SCRATCH_BYTES(ncell)
  * bytes of device memory, 16-byte aligned. */
 #define PE_PS_EQ_SCRATCH_BYTES(ncell) (24 * (size_t)(ncell) + 32)
 PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,

@@ -1065,9 +1065,12 @@ void orc_ps_sample_fx_walls(int64_t n, const int32_t* cell, const double* theta,
  * and constant beyond the first and last midpoints (no wrap): its values at the nodes, n_j, are
  * the profile that orc_quiet_start_equal loads (positions by mass quantile, storage order in
  * velocity-ordered blocks); every ion then gets w = (sum of the bin masses) / N, so lifting keeps
- * the charge, and V = (1 - phi) G_b0(b_i) + phi G_b1(b_i) blended between the inverse CDFs of the
- * two bins whose midpoints bracket its position (phi the fraction of the way from b0's), b_i its
- * Hammersley quantile. */
+ * the charge, and V = (1 - f) G_b0(b_i) + f G_b1(b_i) blended between the inverse CDFs of the two
+ * bins whose midpoints bracket its position, b_i its Hammersley quantile, with f b1's share of
+ * the density there, phi d_b1 / ((1 - phi) d_b0 + phi d_b1) (phi the fraction of the way from
+ * b0's midpoint): a bin without ions lends no velocities. (Blending by phi alone, as the
+ * periodic loader does, gave the ions just outside the expansion front velocities drawn halfway
+ * from an empty bin's placeholder table.) */
 static double ps_mid(int32_t i, int32_t nxc, double width, int32_t ncell)
 {
     if (i == 0) return 0.5 * (width - 0.5);
@@ -1131,11 +1134,21 @@ void orc_ps_quiet_start_equal(int64_t N, int32_t ncell, int32_t bin_shift, const
         int32_t b0, b1;
         double phi;
         ps_bins_at((double)cell[s] + theta[s], nxc, width, ncell, &b0, &b1, &phi);
+        if ((1.0 - phi) * dens[b0] + phi * dens[b1] <= 0.0) {
+            /* the cell's linear profile reaches past the midpoint interpolation's zero (next to
+             * an empty bin): take the velocities at the cell's denser node */
+            const int32_t c = cell[s];
+            ps_bins_at(prof[c + 1] > prof[c] ? (double)(c + 1) : (double)c, nxc, width, ncell, &b0, &b1, &phi);
+        }
         uint32_t B = brev32((uint32_t)i) + half + shift;
         double b = ((double)B + 0.5) * 2.3283064365386963e-10;
         double v0 = orc_cdf_inverse(nv, cdf + (size_t)b0 * (nv + 1), sig + (size_t)b0 * nv, b, vmin, dv);
         double v1 = orc_cdf_inverse(nv, cdf + (size_t)b1 * (nv + 1), sig + (size_t)b1 * nv, b, vmin, dv);
-        v[s] = (1.0 - phi) * v0 + phi * v1;
+        /* quantiles blended by each bin's share of the density at x: a bin without ions (whose
+         * table is a placeholder) contributes nothing */
+        double r0 = (1.0 - phi) * dens[b0], r1 = phi * dens[b1];
+        double f = (r0 + r1 > 0.0) ? r1 / (r0 + r1) : phi;
+        v[s] = (1.0 - f) * v0 + f * v1;
         w[s] = total / (double)N;
     }
     free(prof);

@@ -473,6 +473,7 @@ struct PSEqLoad {
     float vmin, dv;
     const double* prof;
     const double* total;
+    const double* mass;
     EqTable tab;
     const float* table;
     uint32_t half, shift;
@@ -488,14 +489,30 @@ __device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c,
     th = t;
     int b0, b1;
     double phi;
-    ps_bracket((double)c + (double)t, P.nxc, ldexp(1.0, P.bin_shift), P.ncell, b0, b1, phi);
+    const double width = ldexp(1.0, P.bin_shift);
+    ps_bracket((double)c + (double)t, P.nxc, width, P.ncell, b0, b1, phi);
+    double w0 = (b0 == 0 || b0 == P.nxc - 1) ? width - 0.5 : width;
+    double w1 = (b1 == 0 || b1 == P.nxc - 1) ? width - 0.5 : width;
+    double r0 = (1.0 - phi) * (__ldg(P.mass + b0) / w0), r1 = phi * (__ldg(P.mass + b1) / w1);
+    if (!(r0 + r1 > 0.0)) {
+        // the cell's linear profile reaches past the midpoint interpolation's zero (next to an
+        // empty bin): take the velocities at the cell's denser node
+        const double x = (__ldg(P.prof + c + 1) > __ldg(P.prof + c)) ? (double)(c + 1) : (double)c;
+        ps_bracket(x, P.nxc, width, P.ncell, b0, b1, phi);
+        w0 = (b0 == 0 || b0 == P.nxc - 1) ? width - 0.5 : width;
+        w1 = (b1 == 0 || b1 == P.nxc - 1) ? width - 0.5 : width;
+        r0 = (1.0 - phi) * (__ldg(P.mass + b0) / w0);
+        r1 = phi * (__ldg(P.mass + b1) / w1);
+    }
     const uint32_t B = __brev(i) + P.half + P.shift;
     const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const int row = 3 * P.nv + 1;
     const float v0 = cdf_inverse_f(P.table + (size_t)b0 * row, P.nv, b, P.vmin, P.dv);
     const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
-    const float ph = (float)phi;
-    vv = fmaf(ph, v1 - v0, v0);
+    // quantiles blended by each bin's share of the density at x: a bin without ions (whose
+    // table is a placeholder) contributes nothing
+    const float f = (float)((r0 + r1 > 0.0) ? r1 / (r0 + r1) : phi);
+    vv = fmaf(f, v1 - v0, v0);
     ww = (float)(__ldg(P.total) / (double)P.n);
 }
 
@@ -692,6 +709,7 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     P.dv = (float)dv;
     P.prof = prof;
     P.total = total;
+    P.mass = mass;
     P.tab = EqTable{C, first, MoN};
     P.table = table;
     P.half = (uint32_t)(2147483648.0 / (double)n);

@@ -449,3 +449,19 @@ def test_ps_burst_walls_mirror_symmetry():
     # mirror: x-bin i <-> nxc-1-i, velocity cell j <-> nv-1-j (symmetric velocity range)
     assert np.array_equal(samples, samples[:, ::-1, ::-1])
     assert (st.w == 0).sum() > 0
+
+
+def test_ps_quiet_start_equal_empty_bins_lend_no_velocities():
+    # ions next to the expansion front take their velocities from the occupied bins only: bins
+    # without ions have a placeholder (uniform) table that must not leak into the blend
+    ncell, b, nv, N = 128, 3, 32, 1 << 15
+    nxc = ncell >> b
+    vmin, dv = -8.0, 0.5
+    vc = vmin + dv * (np.arange(nv) + 0.5)
+    H = np.zeros((nxc, nv))
+    H[4:10] = np.exp(-0.5 * ((vc - 2.0) / 0.3) ** 2)[None, :]  # a cold beam at v = 2 in bins 4..9
+    mass, cdf, _ = orc.ps_lift_tables(H)
+    st = orc.ps_quiet_start_equal(N, ncell, b, mass, cdf, vmin, dv, 4)
+    occupied = vc[H[4] > 1e-12 * H[4].max()]
+    assert st.v.min() >= occupied.min() - dv and st.v.max() <= occupied.max() + dv
+    assert np.all((st.cell >= 4 * 8 - 5) & (st.cell < 10 * 8 + 4))
