@@ -334,7 +334,7 @@ def test_ps_quiet_start_equal_matches_oracle(ncell, b, nv, N):
     # a few velocities by a fraction of a cell; typical differences are at the FP32 level
     dv_ = np.abs(gv - so.v)
     assert dv_.max() <= 0.2 * dv and dv_.mean() <= 2e-6 * 12.0
-    assert np.mean(dv_ > 5e-5) < 1e-4
+    assert np.sum(dv_ > 5e-5) <= max(3, 1e-4 * N)
     assert torch.equal(rho, pe.deposit(cell, theta, w, ncell, s_w))
     # equal weights, placed by mass: the vacuum bins receive no ions
     assert np.all(gc[gw > 0] >= int(0.2 * ncell) - (1 << b))
@@ -373,8 +373,8 @@ def test_context_ps_slab_projective_steps_follow_plain_pic():
     # co-moving restriction (Appendix B) carries each ion over tau = Delta t - p delta t <= 4
     # with the burst-start field at its position; at the expansion front that field is a spike,
     # so the projected velocities overshoot and the front reaches the walls early: with these
-    # steps the oracle keeps 77 % of the charge against 91 % resolved (and 92 % without a leap,
-    # Delta t = K delta t). The bounds fence that known error of the method at this Delta t.
+    # steps the oracle and the GPU keep 77 % of the charge against 91 % resolved (92 % without
+    # a leap, Delta t = K delta t). The bounds fence that known error of the method here.
     cfg = _small_ps_slab_cfg()
     ef = pe.Context(cfg, device=DEV)
     ref = pe.Context(_small_slab_cfg(), device=DEV)
