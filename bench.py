@@ -532,53 +532,70 @@ def _eps(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
 
 
-def run_slab(dev, pb):
+def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 15))):
     """Slab expansion into vacuum (bounded grid, absorbing walls): projective steps with the
-    moment coarse variables vs plain GPU PIC to the same end time, time to solution and the
-    coarse-density error (Section 4.1.1's measure) at three times."""
+    moment coarse variables (the workload's K = 30, M = 8), then with the phase-space variable
+    at the given (Delta t, K), against plain GPU PIC to the same end time: time to solution and
+    the coarse-density error (Section 4.1.1's measure) at three times."""
     import numpy as np
     import torch
 
     from paper_1610_01071_gb300 import inputs
 
     w = inputs.workload("slab")
-    c = pb.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"],
-                       v_th=w["v_th"], wavelet=w["wavelet"], seed=21, sort_every=20, newton_tol=1e-10,
-                       newton_maxit=80, boundary="absorbing")
     steps = w["macro_steps"]
-    per = int(round(w["dT"] / w["dt"]))
-    checks = sorted({max(1, steps // 5), steps // 2, steps})
-    ef, ref = pb.Context(c, device=dev), pb.Context(c, device=dev)
-    ef.load_initial(profile="slab")
+    T_end = steps * w["dT"]
+
+    def make(coarse="moments", dT=None, K=None):
+        return pb.make_config(w["ncell"], w["n_coarse"], K or w["K"], w["N"], w["L"], w["dt"], dT or w["dT"],
+                              qm=w["qm"], v_th=w["v_th"], wavelet=w["wavelet"], seed=21, sort_every=20,
+                              newton_tol=1e-10, newton_maxit=80, boundary="absorbing", coarse=coarse, n_v=64,
+                              v_max=8.0, ps_filter=3)
+
+    checks_t = [T_end / 5, T_end / 2, T_end]
+    ref = pb.Context(make(), device=dev)
     ref.load_initial(profile="slab")
-    q0 = ef.moments()["charge"]
-    got = {}
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for m in range(1, steps + 1):
-        ef.step()
-        if m in checks:
-            got[m] = ef.get_coarse()[0].clone()
-    torch.cuda.synchronize(dev)
-    t_proj = time.perf_counter() - t0
-    want = {}
-    t0 = time.perf_counter()
-    done = 0
-    for m in checks:
-        ref.pic_steps((m - done) * per)
-        done = m
-        want[m] = ref.measure()[0].clone()
+    q0 = ref.moments()["charge"]
+    want, t0, done = {}, time.perf_counter(), 0
+    for T in checks_t:
+        n = int(round(T / w["dt"]))
+        ref.pic_steps(n - done)
+        done = n
+        want[T] = ref.measure()[0].clone()
     torch.cuda.synchronize(dev)
     t_plain = time.perf_counter() - t0
-    eps = {str(round(m * w["dT"])): _eps(got[m].cpu().numpy(), want[m].cpu().numpy()) for m in checks}
     q_ref = ref.moments()["charge"]
+
+    def run(coarse, dT, K):
+        ctx = pb.Context(make(coarse, dT, K), device=dev)
+        ctx.load_initial(profile="slab")
+        b = int(np.log2(w["ncell"] // w["n_coarse"]))
+        scale = 2.0 ** (-(np.log2(w["ncell"]) + b) / 2)  # bin mass -> Haar density coefficient
+        got, t, wall = {}, 0.0, 0.0
+        for T in checks_t:
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            while t < T - 1e-9:
+                ctx.step()
+                t += dT
+            torch.cuda.synchronize(dev)
+            wall += time.perf_counter() - t1
+            c = ctx.get_coarse()
+            got[T] = (c.sum(1) * scale if coarse == "phase_space" else c[0]).cpu().numpy()
+        eps = {str(round(T)): _eps(got[T], want[T].cpu().numpy()) for T in checks_t}
+        ctx.lift()
+        return {"coarse": coarse, "dT": dT, "K": K, "M": dT / (K * w["dt"]), "seconds": wall,
+                "speedup_vs_plain_pic": t_plain / wall,
+                "particle_steps_per_s": float(w["N"]) * K * round(T_end / dT) / wall,
+                "eps_coarse_density_at_T": eps, "charge_left": ctx.moments()["charge"] / q0,
+                "status": ctx.sync_status()}
+
+    runs = [run("moments", w["dT"], w["K"])] + [run(*v) for v in variants]
     return {"workload": "slab expansion: bounded 8192 cells, absorbing walls, uniform slab on the central "
                         "eighth, 2^25 equal-weight ions, v_th=1, K=30, M=8, 40 macro steps, 512 coarse per moment",
-            "T_end": steps * w["dT"], "projective_s": t_proj, "plain_pic_s": t_plain, "speedup": t_plain / t_proj,
-            "particle_steps_per_s": {"projective": float(w["N"]) * w["K"] * steps / t_proj,
-                                     "plain_pic": float(w["N"]) * steps * per / t_plain},
-            "eps_coarse_density_at_T": eps, "charge_left_plain_pic": q_ref / q0,
-            "status": [ef.sync_status(), ref.sync_status()]}
+            "T_end": T_end, "plain_pic_s": t_plain,
+            "plain_pic_particle_steps_per_s": float(w["N"]) * round(T_end / w["dt"]) / t_plain,
+            "charge_left_plain_pic": q_ref / q0, "status_plain_pic": ref.sync_status(), "projective": runs}
 
 
 def run_surrogate(dev, cfg, pb, want, checks):
