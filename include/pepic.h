@@ -377,7 +377,7 @@ PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, in
  * the ion (phi the fraction of the way from b0's midpoint, d the bin densities): a bin without
  * ions, next to the expansion front, then lends no velocities. scratch: PE_PS_EQ_SCRATCH_BYTES(ncell)
  * bytes of device memory, 16-byte aligned. */
-#define PE_PS_EQ_SCRATCH_BYTES(ncell) (24 * (size_t)(ncell) + 32)
+#define PE_PS_EQ_SCRATCH_BYTES(ncell) (28 * (size_t)(ncell) + 64)
 PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
                                    int32_t bin_shift, const double* mass, const float* table, int32_t n_v,
                                    double v_min, double dv, uint64_t seed, int32_t s_w, void* scratch,

@@ -433,7 +433,7 @@ def ps_quiet_start_equal(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w,
     v = torch.empty_like(theta)
     w = torch.empty_like(theta)
     rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
-    scratch = torch.empty((24 * ncell + 32 + 7) // 8, dtype=torch.float64, device=dev)
+    scratch = torch.empty((28 * ncell + 64 + 7) // 8, dtype=torch.float64, device=dev)
     status = _status(status, dev)
     check(load().pe_ps_quiet_start_equal(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, int(bin_shift),
                                          _ptr(mass), _ptr(table), (table.shape[1] - 1) // 3, float(v_min), float(dv),

@@ -436,10 +436,40 @@ __device__ __forceinline__ void ps_bracket(double x, int nxc, double width, int 
     phi = (x - m0) / (m1 - m0);
 }
 
-// One block: the nodal profile prof[ncell] (FP64) of the bin densities and total = sum of the
-// bin masses (fixed-order tree).
+// FP32 form of ps_bracket for the per-ion blend (the interior midpoints are a power-of-two
+// width apart; the end midpoints are passed in).
+__device__ __forceinline__ void ps_bracket_f(float x, int nxc, float width, float inv_width, float mid_first,
+                                             float mid_last, int& b0, int& b1, float& phi)
+{
+    if (nxc < 2 || x <= mid_first) {
+        b0 = b1 = 0;
+        phi = 0.0f;
+        return;
+    }
+    if (x >= mid_last) {
+        b0 = b1 = nxc - 1;
+        phi = 0.0f;
+        return;
+    }
+    auto mid = [&](int i) {
+        return i == 0 ? mid_first : (i == nxc - 1 ? mid_last : fmaf((float)i + 0.5f, width, -0.5f));
+    };
+    int i = (int)floorf(fmaf(x + 0.5f, inv_width, -0.5f));
+    i = i < 0 ? 0 : (i > nxc - 2 ? nxc - 2 : i);
+    if (i > 0 && x < mid(i)) --i;
+    if (i < nxc - 2 && x >= mid(i + 1)) ++i;
+    const float m0 = mid(i), m1 = mid(i + 1);
+    b0 = i;
+    b1 = i + 1;
+    phi = fminf(fmaxf((x - m0) / (m1 - m0), 0.0f), 1.0f);
+}
+
+// One block: the nodal profile prof[ncell] (FP64) of the bin densities, total = sum of the bin
+// masses (fixed-order tree), and for the per-ion blend the FP32 bin densities densf[nxc] and the
+// ion weight total / n.
 __global__ void __launch_bounds__(1024) k_ps_profile(const double* __restrict__ mass, int nxc, int bin_shift,
-                                                     int ncell, double* __restrict__ prof, double* total)
+                                                     int ncell, int64_t n, double* __restrict__ prof, double* total,
+                                                     float* __restrict__ densf, float* wn)
 {
     __shared__ double red[32];
     const double width = ldexp(1.0, bin_shift);
@@ -451,6 +481,8 @@ __global__ void __launch_bounds__(1024) k_ps_profile(const double* __restrict__ 
         const double w1 = (b1 == 0 || b1 == nxc - 1) ? width - 0.5 : width;
         prof[j] = (1.0 - phi) * (mass[b0] / w0) + phi * (mass[b1] / w1);
     }
+    for (int i = threadIdx.x; i < nxc; i += blockDim.x)
+        densf[i] = (float)(mass[i] / ((i == 0 || i == nxc - 1) ? width - 0.5 : width));
     double acc = 0.0;
     for (int i = threadIdx.x; i < nxc; i += blockDim.x) acc += mass[i];
     acc = warp_sum(acc);
@@ -459,7 +491,10 @@ __global__ void __launch_bounds__(1024) k_ps_profile(const double* __restrict__ 
     if (threadIdx.x < 32) {
         double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
         v = warp_sum(v);
-        if (threadIdx.x == 0) *total = v;
+        if (threadIdx.x == 0) {
+            *total = v;
+            *wn = (float)(v / (double)n);
+        }
     }
 }
 
@@ -472,8 +507,9 @@ struct PSEqLoad {
     int ncell, mask, bin_shift, nv, nxc;
     float vmin, dv;
     const double* prof;
-    const double* total;
-    const double* mass;
+    const float* densf;
+    const float* wn;
+    float width, inv_width, mid_first, mid_last;
     EqTable tab;
     const float* table;
     uint32_t half, shift;
@@ -488,21 +524,16 @@ __device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c,
     const float t = eq_position(P.tab, P.prof, 1.0f, P.ncell, i, c);
     th = t;
     int b0, b1;
-    double phi;
-    const double width = ldexp(1.0, P.bin_shift);
-    ps_bracket((double)c + (double)t, P.nxc, width, P.ncell, b0, b1, phi);
-    double w0 = (b0 == 0 || b0 == P.nxc - 1) ? width - 0.5 : width;
-    double w1 = (b1 == 0 || b1 == P.nxc - 1) ? width - 0.5 : width;
-    double r0 = (1.0 - phi) * (__ldg(P.mass + b0) / w0), r1 = phi * (__ldg(P.mass + b1) / w1);
-    if (!(r0 + r1 > 0.0)) {
+    float phi;
+    ps_bracket_f((float)c + t, P.nxc, P.width, P.inv_width, P.mid_first, P.mid_last, b0, b1, phi);
+    float r0 = (1.0f - phi) * __ldg(P.densf + b0), r1 = phi * __ldg(P.densf + b1);
+    if (!(r0 + r1 > 0.0f)) {
         // the cell's linear profile reaches past the midpoint interpolation's zero (next to an
         // empty bin): take the velocities at the cell's denser node
-        const double x = (__ldg(P.prof + c + 1) > __ldg(P.prof + c)) ? (double)(c + 1) : (double)c;
-        ps_bracket(x, P.nxc, width, P.ncell, b0, b1, phi);
-        w0 = (b0 == 0 || b0 == P.nxc - 1) ? width - 0.5 : width;
-        w1 = (b1 == 0 || b1 == P.nxc - 1) ? width - 0.5 : width;
-        r0 = (1.0 - phi) * (__ldg(P.mass + b0) / w0);
-        r1 = phi * (__ldg(P.mass + b1) / w1);
+        const float x = (__ldg(P.prof + c + 1) > __ldg(P.prof + c)) ? (float)(c + 1) : (float)c;
+        ps_bracket_f(x, P.nxc, P.width, P.inv_width, P.mid_first, P.mid_last, b0, b1, phi);
+        r0 = (1.0f - phi) * __ldg(P.densf + b0);
+        r1 = phi * __ldg(P.densf + b1);
     }
     const uint32_t B = __brev(i) + P.half + P.shift;
     const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
@@ -511,9 +542,9 @@ __device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c,
     const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
     // quantiles blended by each bin's share of the density at x: a bin without ions (whose
     // table is a placeholder) contributes nothing
-    const float f = (float)((r0 + r1 > 0.0) ? r1 / (r0 + r1) : phi);
+    const float f = (r0 + r1 > 0.0f) ? r1 / (r0 + r1) : phi;
     vv = fmaf(f, v1 - v0, v0);
-    ww = (float)(__ldg(P.total) / (double)P.n);
+    ww = __ldg(P.wn);
 }
 
 __global__ void __launch_bounds__(256) k_ps_quiet_start_equal(PSEqLoad P)
@@ -692,7 +723,9 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     long long* first = reinterpret_cast<long long*>(C + ncl + 1);        // [ncl + 1]
     double* MoN = reinterpret_cast<double*>(first + ncl + 1);           // [1]
     double* total = MoN + 1;                                             // [1]
-    k_ps_profile<<<1, 1024, 0, s>>>(mass, nxc, bin_shift, ncell, prof, total);
+    float* densf = reinterpret_cast<float*>(total + 1);                  // [nxc]
+    float* wn = densf + nxc;                                             // [1]
+    k_ps_profile<<<1, 1024, 0, s>>>(mass, nxc, bin_shift, ncell, n, prof, total, densf, wn);
     k_eq_table<double><<<1, kEqThreads, 0, s>>>(prof, ncell, 1.0f, n, C, first, MoN, status);
     PSEqLoad P{};
     P.cell = cell;
@@ -708,8 +741,12 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     P.vmin = (float)v_min;
     P.dv = (float)dv;
     P.prof = prof;
-    P.total = total;
-    P.mass = mass;
+    P.densf = densf;
+    P.wn = wn;
+    P.width = ldexpf(1.0f, bin_shift);
+    P.inv_width = ldexpf(1.0f, -bin_shift);
+    P.mid_first = 0.5f * (P.width - 0.5f);
+    P.mid_last = (float)(0.5 * ((nxc - 1) * (double)P.width - 0.5 + (double)(ncell - 1)));
     P.tab = EqTable{C, first, MoN};
     P.table = table;
     P.half = (uint32_t)(2147483648.0 / (double)n);
