@@ -140,7 +140,7 @@ static int build_descs(pe_batch* b)
                        x->s_w, x->s_p, x->csamples, x->coarse, x->slope);
         char* dst = fd.data() + field_desc_size() * slot[r];
         make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, x->walls, c.newton_tol,
-                        c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status);
+                        c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, x->phi + c.ncell);
     }
     if (cudaMemcpy(at(b, b->L.push), push.data(), push.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(at(b, b->L.proj), proj.data(), proj.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -149,14 +149,17 @@ static int build_descs(pe_batch* b)
     return PE_OK;
 }
 
-static int field_all(pe_batch* b)
+// extrap: the Newton starts extrapolate the last two solutions (the solves after a push), as
+// the context path's burst does.
+static int field_all(pe_batch* b, bool extrap)
 {
     const char* base = at(b, b->L.field);
     size_t o = 0;
     for (int g = 0; g < 4; ++g) {
         const int n = (int)b->field_ids[g].size();
-        if (n) PE_TRY(launch_newton_batch(base + field_desc_size() * o, n, g < 2 ? b->G : 1, b->field_maxn[g], g & 1,
-                                          b->stream));
+        if (n)
+            PE_TRY(launch_newton_batch(base + field_desc_size() * o, n, g < 2 ? b->G : 1, b->field_maxn[g], g & 1,
+                                       extrap, b->stream));
         o += (size_t)n;
     }
     return PE_OK;
@@ -171,7 +174,7 @@ static int burst_restrict_project(pe_batch* b)
     int64_t* samp_all = reinterpret_cast<int64_t*>(at(b, b->L.samp));
     float* e0_all = reinterpret_cast<float*>(at(b, b->L.e0));
     unsigned* counter = reinterpret_cast<unsigned*>(at(b, b->L.counter));
-    PE_TRY(field_all(b));  // field at burst start (charge deposited by the lifting)
+    PE_TRY(field_all(b, false));  // field at burst start (charge deposited by the lifting)
     for (int r = 0; r < R; ++r)
         if (cudaMemcpyAsync(e0_all + b->e0_off[r], b->ctx[r]->Ef, 4 * (size_t)b->ctx[r]->cfg.ncell,
                             cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -187,7 +190,7 @@ static int burst_restrict_project(pe_batch* b)
         if (cudaMemsetAsync(rho_all, 0, 8 * (size_t)b->L.rho_total, s) != cudaSuccess) return PE_ECUDA;
         PE_TRY(launch_particles_batch(0, at(b, b->L.push), at(b, b->L.items), b->nitems, p, p == 0 ? 0.5f : 1.0f,
                                       counter, b->max_ncell, b->max_nb, s));
-        PE_TRY(field_all(b));
+        PE_TRY(field_all(b, true));
     }
     const pe_config& c0 = b->ctx[0]->cfg;
     return launch_restrict_project_batch(at(b, b->L.proj), R, b->K, c0.dt, c0.dT, s);

@@ -151,7 +151,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_PARTICLES_A] = bank;
     out->bytes[PE_BUF_PARTICLES_B] = bank;
     out->bytes[PE_BUF_RHO] = 8 * nc;
-    out->bytes[PE_BUF_PHI] = 8 * nc;
+    out->bytes[PE_BUF_PHI] = 8 * 2 * nc;  // phi and the previous solution (Newton start)
     out->bytes[PE_BUF_E] = 8 * nc;
     out->bytes[PE_BUF_EF] = 4 * nc;
     out->bytes[PE_BUF_E0F] = 4 * nc;
@@ -326,13 +326,21 @@ extern "C" PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* pus
     return PE_OK;
 }
 
-static int field_solve(pe_ctx* x)
+// Field solve of the current charge. mode 0: a solve outside the time stepping (measurement,
+// diagnostics): the solution history is left alone. mode 1: the solve that starts a burst or a
+// plain-PIC step: records the history; its Newton start extrapolates the last two solutions
+// when they belong to the same trajectory one fine step apart (phi_hist).
+static int field_solve(pe_ctx* x, int step = 0)
 {
     const pe_config& c = x->cfg;
-    return timed(x, 1, [&] {
-        return pe_field_ex(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.boundary, c.newton_tol, c.newton_maxit,
-                           x->phi, x->E, x->Ef, x->diag, x->status, x->stream);
-    });
+    const int extrap = step && x->phi_hist;
+    double* prev = step ? x->phi + c.ncell : nullptr;
+    PE_TRY(timed(x, 1, [&] {
+        return field_solve_history(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.boundary, c.newton_tol,
+                                   c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, prev, extrap, x->stream);
+    }));
+    if (step) x->phi_hist = 1;
+    return PE_OK;
 }
 
 static int deposit_current(pe_ctx* x)
@@ -385,6 +393,7 @@ static int quiet_start_from_profile(pe_ctx* x, uint64_t seed, float wall_factor)
     x->rho_valid = 1;
     x->v_at_integer = 1;
     x->fresh = 1;
+    x->phi_hist = 0;
     return PE_OK;
 }
 
@@ -477,7 +486,8 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     const int b = x->bank;
     if (p_begin == 0) {
         if (!x->rho_valid) PE_TRY(deposit_current(x));
-        PE_TRY(field_solve(x));
+        x->phi_hist = 0;  // a burst starts a new stretch of trajectory (after a lift or a load)
+        PE_TRY(field_solve(x, 1));
         if (cudaMemcpyAsync(x->E0f, x->Ef, sizeof(float) * c.ncell, cudaMemcpyDeviceToDevice, x->stream) != cudaSuccess)
             return PE_ECUDA;
     }
@@ -490,7 +500,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                               kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream);
         }));
-        PE_TRY(field_solve(x));
+        PE_TRY(field_solve(x, 1));
         kick = 1.0f;
         x->v_at_integer = 0;
         x->rho_valid = 1;
@@ -563,6 +573,7 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         x->rho_valid = 1;
         x->v_at_integer = 1;
         x->fresh = 1;
+        x->phi_hist = 0;
         return PE_OK;
     }
     PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
@@ -592,7 +603,7 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
             x->bank = o;
         }
         if (!x->rho_valid) PE_TRY(deposit_current(x));
-        PE_TRY(field_solve(x));
+        PE_TRY(field_solve(x, 1));
         const int b = x->bank;
         const float kick = x->v_at_integer ? 0.5f : 1.0f;
         PE_TRY(timed(x, 0, [&] {

@@ -35,6 +35,7 @@ struct pe_ctx {
     float* ps_table;     // [n_coarse][3 n_v + 1] FP32 sampling rows
     int32_t* ps_flags;
     int walls;           // bounded grid (PE_BOUNDARY_ABSORBING)
+    int phi_hist;        // phi and phi + ncell hold two solutions one fine step apart
     void* eq_scratch;    // equal-weight loading scratch (bounded grids)
     int bank;            // which particle bank is current
     int v_at_integer;    // stored v is at integer time

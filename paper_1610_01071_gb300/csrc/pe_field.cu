@@ -161,6 +161,10 @@ struct FieldDesc {
     uint32_t* status;
     double dx, nscale, tol;
     int ncell, mode, maxit, walls;  // walls: 1 for a bounded grid
+    // Newton start: phi_prev (may be null) keeps the solution before the current one; with
+    // extrap the start is the linear extrapolation 2 phi - phi_prev (solves one fine step apart)
+    double* phi_prev;
+    int extrap, pad2;
 };
 
 // Solver body for the realisation of this cluster: B = ncell / G nodes per block, one per
@@ -204,6 +208,18 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     const bool boltz = (mode == PE_POISSON_BOLTZMANN);
     const double nj = act ? (double)__ldg(rho + j) * nscale * ((wl || wr) ? 2.0 : 1.0) : 0.0;
     double pj = act ? phi[j] : 0.0;
+    if (d.phi_prev && act) {
+        const double pp = d.phi_prev[j];
+        d.phi_prev[j] = pj;
+        if (d.extrap) {
+            pj = 2.0 * pj - pp;
+            phi[j] = pj;
+        }
+    }
+    if (d.phi_prev && d.extrap) {  // extrapolated starts visible to the neighbouring blocks' halos
+        __threadfence();
+        cluster.sync();
+    }
     double gj = boltz ? exp(pj) : 1.0 + pj;
 
     int it = 0;
@@ -353,12 +369,13 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(FieldDesc d)
     newton_body<T>(d, cluster);
 }
 
-// One cluster per realisation: cluster c solves descs[c].
+// One cluster per realisation: cluster c solves descs[c]; extrap applies to every realisation.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_newton_batch(const FieldDesc* descs)
+__global__ void __launch_bounds__(1024) k_newton_batch(const FieldDesc* descs, int extrap)
 {
     cg::cluster_group cluster = cg::this_cluster();
-    const FieldDesc d = descs[blockIdx.x / cluster.num_blocks()];
+    FieldDesc d = descs[blockIdx.x / cluster.num_blocks()];
+    d.extrap = extrap;
     newton_body<T>(d, cluster);
 }
 
@@ -422,7 +439,7 @@ static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int n
 
 static int launch_newton_cluster(int G, const long long* rho, int ncell, double dx, double nscale, int mode,
                                  int walls, double tol, int maxit, double* phi, double* E, float* Ef, int* diag,
-                                 uint32_t* status, cudaStream_t s)
+                                 uint32_t* status, double* phi_prev, int extrap, cudaStream_t s)
 {
     const int B = ncell / G;  // one node per thread
     if (B > 1024 || B < 2) return PE_EINVAL;
@@ -430,7 +447,8 @@ static int launch_newton_cluster(int G, const long long* rho, int ncell, double 
     const size_t smem = newton_smem_bytes(B, G, fp64);
     const void* k = fp64 ? (const void*)k_newton_cluster<double> : (const void*)k_newton_cluster<float>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    FieldDesc d{rho, phi, E, Ef, diag, status, dx, nscale, tol, ncell, mode, maxit, walls ? 1 : 0};
+    FieldDesc d{rho, phi, E, Ef, diag, status, dx, nscale, tol, ncell, mode, maxit, walls ? 1 : 0, phi_prev,
+                extrap ? 1 : 0, 0};
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(attr, G, 1, B, smem, s);
     const cudaError_t e = fp64 ? cudaLaunchKernelEx(&cfg, k_newton_cluster<double>, d)
@@ -443,7 +461,7 @@ int newton_cluster_size(int ncell) { return cluster_size_for(ncell); }
 
 // Batched field solves: descs[R] on the device, every grid with the same cluster size G;
 // fp64: the linear solves run in FP64 (needed when any grid is bounded).
-int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, cudaStream_t s)
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s)
 {
     const int B = max_ncell / G;
     if (B > 1024 || B < 2 || R < 1) return PE_EINVAL;
@@ -461,8 +479,9 @@ int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp6
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(attr, G, R, B, smem, s);
     const FieldDesc* dd = static_cast<const FieldDesc*>(descs);
-    const cudaError_t e = fp64 ? cudaLaunchKernelEx(&cfg, k_newton_batch<double>, dd)
-                               : cudaLaunchKernelEx(&cfg, k_newton_batch<float>, dd);
+    const int ex = extrap ? 1 : 0;
+    const cudaError_t e = fp64 ? cudaLaunchKernelEx(&cfg, k_newton_batch<double>, dd, ex)
+                               : cudaLaunchKernelEx(&cfg, k_newton_batch<float>, dd, ex);
     if (e != cudaSuccess) return PE_ECUDA;
     return launch_status();
 }
@@ -470,10 +489,10 @@ int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp6
 size_t field_desc_size() { return sizeof(FieldDesc); }
 
 void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, int walls, double tol,
-                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status)
+                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status, double* phi_prev)
 {
     FieldDesc d{reinterpret_cast<const long long*>(rho), phi, E, Ef, diag, status, dx, ldexp(1.0, -(s_w + 24)), tol,
-                ncell, mode, maxit, walls ? 1 : 0};
+                ncell, mode, maxit, walls ? 1 : 0, phi_prev, 0, 0};
     memcpy(out, &d, sizeof(d));
 }
 
@@ -481,22 +500,32 @@ void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_
 
 using namespace pe;
 
-extern "C" PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
-                                  int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
-                                  int32_t* diag, uint32_t* status, void* stream)
+namespace pe {
+// Field solve with a Newton start from the solution history (context path): phi_prev keeps the
+// solution before the current one, extrap selects the extrapolated start.
+int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, int mode, int boundary, double tol,
+                        int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
+                        double* phi_prev, int extrap, cudaStream_t s)
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !phi || !E || !Ef || !(dx > 0.0) || maxit < 0) return PE_EINVAL;
     if (mode != PE_POISSON_BOLTZMANN && mode != PE_POISSON_LINEARIZED) return PE_EINVAL;
     if (boundary != PE_BOUNDARY_PERIODIC && boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
     const double nscale = ldexp(1.0, -(s_w + 24));
-    if (ncell >= 8 && ncell <= kFullGridMax) {
-        const int G = cluster_size_for(ncell);
-        if (G >= 1)
-            return launch_newton_cluster(G, reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode,
-                                         boundary == PE_BOUNDARY_ABSORBING, tol, maxit, phi, E, Ef, diag, status,
-                                         (cudaStream_t)stream);
-    }
-    return PE_EINVAL;
+    if (ncell > kFullGridMax) return PE_EINVAL;
+    const int G = cluster_size_for(ncell);
+    if (G < 1) return PE_EINVAL;
+    return launch_newton_cluster(G, reinterpret_cast<const long long*>(rho_fx), ncell, dx, nscale, mode,
+                                 boundary == PE_BOUNDARY_ABSORBING, tol, maxit, phi, E, Ef, diag, status, phi_prev,
+                                 extrap, s);
+}
+}  // namespace pe
+
+extern "C" PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
+                                  int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
+                                  int32_t* diag, uint32_t* status, void* stream)
+{
+    return field_solve_history(rho_fx, ncell, dx, s_w, mode, boundary, tol, maxit, phi, E, Ef, diag, status, nullptr,
+                               0, (cudaStream_t)stream);
 }
 
 extern "C" PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode, double tol,

@@ -32,9 +32,14 @@ int blocks_per_sm(const void* kernel, int block, size_t smem);
 // used for a grid of ncell nodes, and the launch over R realisations of one cluster size.
 size_t field_desc_size();
 void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_w, int mode, int walls, double tol,
-                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status);
+                     int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
+                     double* phi_prev);
 int newton_cluster_size(int ncell);
-int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, cudaStream_t s);
+int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s);
+// Single field solve whose Newton start may extrapolate the solution history (context path).
+int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, int mode, int boundary, double tol,
+                        int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
+                        double* phi_prev, int extrap, cudaStream_t s);
 
 // Batched particle passes (pe_particles.cu).
 size_t push_desc_size();
