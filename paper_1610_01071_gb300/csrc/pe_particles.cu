@@ -697,14 +697,20 @@ static __device__ __align__(256) unsigned g_sort_static[2 * PE_SORT_STATIC_MAX_C
 
 // ------------------------------------------------------------------ host side
 
+// Grid of a particle pass: one chunk of particles per block, as many blocks as are resident
+// at once (one wave). When the chunk cap (which keeps the shared-memory digit counters exact)
+// forces more blocks than that, the chunk is shrunk so that the blocks fill whole waves: a
+// last wave holding a few full-size blocks would leave most SMs idle while it runs.
 static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk = 0)
 {
-    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(kernel, block, smem);
+    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(kernel, block, smem);
+    const int64_t cap = (max_chunk > 0 && max_chunk < kMaxChunk) ? (max_chunk & ~int64_t(3)) : kMaxChunk;
+    const int64_t waves = (n + slots * cap - 1) / (slots * cap);
+    const int64_t blocks = slots * (waves < 1 ? 1 : waves);
     int64_t c = (n + blocks - 1) / blocks;
     c = (c + 3) & ~int64_t(3);
     if (c < 4) c = 4;
-    const int64_t cap = (max_chunk > 0 && max_chunk < kMaxChunk) ? (max_chunk & ~int64_t(3)) : kMaxChunk;
-    if (c > cap) c = cap;  // the cap keeps the shared-memory digit counters exact
+    if (c > cap) c = cap;
     *chunk = c;
     int64_t g = (n + c - 1) / c;
     return (int)(g < 1 ? 1 : g);

@@ -694,7 +694,10 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    // whole waves of resident blocks, chunks within the digit counters' bound (as grid_for)
+    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    const int64_t waves = (n + slots * kMaxChunk - 1) / (slots * kMaxChunk);
+    const int64_t blocks = slots * (waves < 1 ? 1 : waves);
     int64_t c = (n + blocks - 1) / blocks;
     c = (c + 3) & ~int64_t(3);
     if (c < 4) c = 4;
@@ -762,7 +765,10 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start_equal;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    int64_t blocks = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    // whole waves of resident blocks, chunks within the digit counters' bound (as grid_for)
+    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
+    const int64_t waves = (n + slots * kMaxChunk - 1) / (slots * kMaxChunk);
+    const int64_t blocks = slots * (waves < 1 ? 1 : waves);
     int64_t c = (n + blocks - 1) / blocks;
     c = (c + 3) & ~int64_t(3);
     if (c < 4) c = 4;
