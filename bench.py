@@ -545,7 +545,7 @@ def _eps(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a * a + b * b)))
 
 
-def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 15))):
+def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 20), ("phase_space", 6.0, 15))):
     """Slab expansion into vacuum (bounded grid, absorbing walls): projective steps with the
     moment coarse variables (the workload's K = 30, M = 8), then with the phase-space variable
     at the given (Delta t, K), against plain GPU PIC to the same end time: time to solution and
