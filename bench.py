@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the fused kernel from the ncu capture summarised
 # in profiles/k_particles_push_sample_iaw_large.md, valid while the kernel source hashes to
 # the value it was taken with.
-NCU_TRAFFIC = {"source_hash": "f13479941cc58083", "bytes": 270.737664e6 + 145.399296e6}
+NCU_TRAFFIC = {"source_hash": "47e15c62144f7b6f", "bytes": 270.744064e6 + 145.735168e6}
 
 
 def kernel_source_hash():
