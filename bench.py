@@ -350,10 +350,64 @@ def run_gpu(args):
     return 0
 
 
+def run_kernel_slab(args):
+    """The fused push + phase-space sample on the bounded slab (2^25 ions, 8192 cells), on the
+    state after two phase-space macro steps (Delta t = 6, bursts of 30), timed alone."""
+    import torch
+
+    from paper_1610_01071_gb300 import _binding as pb
+    from paper_1610_01071_gb300 import _build, inputs
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    w = inputs.workload("slab")
+    N, ncell, nv = w["N"], w["ncell"], 64
+    c = pb.make_config(ncell, w["n_coarse"], 30, N, w["L"], w["dt"], 6.0, qm=w["qm"], v_th=w["v_th"], seed=21,
+                       newton_tol=1e-10, newton_maxit=80, boundary="absorbing", coarse="phase_space", n_v=nv,
+                       v_max=8.0, ps_filter=3)
+    ctx = pb.Context(c, device=dev)
+    ctx.load_initial(profile="slab")
+    for _ in range(2):
+        ctx.step()
+    d = ctx.diagnostics()
+    cell, theta, v, wt = ctx.particles(d.particle_bank)
+    rho = ctx.view("rho", torch.int64, ncell)
+    Ef = ctx.view("Ef", torch.float32, ncell)
+    E0f = ctx.view("E0f", torch.float32, ncell)
+    bshift = (ncell // w["n_coarse"]).bit_length() - 1
+    samp = torch.zeros(((ncell >> bshift), nv), dtype=torch.int64, device=dev)
+    dx = w["L"] / ncell
+    sa = pb.make_sample_args(E0f, 6.0, w["qm"], 1.0 / dx, d.s_w, d.s_p, samp, bin_shift=bshift, n_v=nv, v_min=-8.0,
+                             dv=16.0 / nv, boundary="absorbing")
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def once():
+        pb.push(cell, theta, v, wt, Ef, ncell, w["dt"] / dx, w["dt"], 1.0, d.s_w, rho=rho, sample=sa, status=status,
+                boundary="absorbing")
+
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us,
+                      "algorithmic_GBps": 28 * N / (us * 1e-6) / 1e9, "status": int(status.item())}), flush=True)
+    return 0
+
+
 def run_kernel(args):
     """Times one hot-path kernel alone on the workload's particle state (for profiling):
-    ``--kernel push_sample|push|deposit|sample|field|quiet_start``."""
+    ``--kernel push_sample|push|deposit|sample|field|quiet_start|push_sample_ps|ps_tables|
+    ps_quiet_start|push_sample_ps_slab``."""
     import torch
+
+    if args.kernel == "push_sample_ps_slab":
+        return run_kernel_slab(args)
 
     from paper_1610_01071_gb300 import _binding as pb
     from paper_1610_01071_gb300 import _build
