@@ -188,6 +188,29 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ ranks (replicas)
+
+
+def reduce_over_ranks(x, op, world, device):
+    """Max or sum of one float over the ranks of the process group (identity with one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_totals(t_local, work_local, world, device):
+    """Whole-job throughput of weakly scaled replicas: the work of all ranks over the slowest
+    rank's time. Returns (throughput, max time, total work)."""
+    t = reduce_over_ranks(t_local, "max", world, device)
+    w = reduce_over_ranks(work_local, "sum", world, device)
+    return w / t, t, w
+
+
 # ------------------------------------------------------------------ GPU leg
 
 
@@ -220,18 +243,10 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", world, dev)
 
     def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(x, "sum", world, dev)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -290,12 +305,10 @@ def run_gpu(args):
         ens = run_ensemble(dev, max(args.steps // 2, 2), 3, rank) if not args.no_ensemble else None
     clocks = sampler.stop()
 
-    t_proj_max = max_over_ranks(t_proj)
+    value, t_proj_max, ps_proj = replica_totals(t_proj, float(N) * K * args.steps, world, dev)
     t_plain_max = max_over_ranks(t_plain)
     t_e2e_max = max_over_ranks(t_e2e)
-    ps_proj = sum_over_ranks(float(N) * K * args.steps)
     ps_plain = sum_over_ranks(float(N) * n_plain)
-    value = ps_proj / t_proj_max
     sim_proj = cfg["dT"] * args.steps / t_proj_max
     sim_plain = cfg["dt"] * n_plain / t_plain_max
     peak, peak_kind = peak_hbm()
