@@ -23,9 +23,10 @@
  *   launch error). Faults found on the device (particle cell out of range,
  *   fixed-point overflow, Newton non-convergence) are OR-ed into a caller-owned
  *   device status word (uint32) as PE_FLAG_* bits and never trap; the caller reads
- *   it after synchronising (the context API does this in pe_sync_status). Device-side
- *   waits are bounded (about one second); a wait that runs out sets PE_FLAG_TIMEOUT and
- *   the kernel returns instead of hanging.
+ *   it after synchronising (the context API does this in pe_sync_status). No kernel
+ *   spins on a flag or a counter: the only device-side waits are block and cluster
+ *   barriers that every thread reaches. PE_FLAG_TIMEOUT / PE_ETIMEOUT are reserved for a
+ *   bounded wait that runs out; no current kernel has one.
  */
 #ifndef PEPIC_H
 #define PEPIC_H
@@ -51,7 +52,7 @@ extern "C" {
 #define PE_EOVERFLOW 4 /* a weight or momentum exceeded its fixed-point range */
 #define PE_ERANGE 5    /* a particle cell index was outside [0, ncell) */
 #define PE_ESTATE 6    /* call out of order for the context state */
-#define PE_ETIMEOUT 7  /* a bounded device-side wait (asynchronous copy) timed out */
+#define PE_ETIMEOUT 7  /* a bounded device-side wait timed out (reserved: no current kernel waits) */
 
 #define PE_FLAG_NOCONV 1u
 #define PE_FLAG_OVERFLOW 2u
