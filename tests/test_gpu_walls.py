@@ -397,3 +397,35 @@ def test_context_ps_slab_projective_steps_follow_plain_pic():
     assert q_ref < q0 and q_ef < q0
     assert abs(q_ef - q_ref) < 0.25 * q0
     assert eps < 0.3
+
+
+def test_slab_full_size_properties():
+    # the slab workload at its full size and in the benchmark's launch configuration (2^25 ions,
+    # 8192 cells): properties that hold at any size, checked exactly
+    w = inputs.workload("slab")
+    cfg = pe.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], v_th=w["v_th"], seed=21,
+                         sort_every=20, newton_tol=1e-10, newton_maxit=80, boundary="absorbing")
+    ctx = pe.Context(cfg, device=DEV)
+    ctx.load_initial(profile="slab")
+    ncell, N = w["ncell"], w["N"]
+    cell, theta, v, wt = ctx.particles()
+    # per-cell counts: particle i sits in cell c iff C_c <= (i + 1/2) M / N < C_{c+1} (FP64 profile)
+    n, _ = orc.slab_profile(ncell)
+    n = n.astype(np.float32).astype(np.float64)
+    C = np.concatenate([[0.0], np.cumsum(0.5 * (n[:-1] + n[1:]))])
+    M = C[-1]
+    want = (np.ceil(C[1:] * N / M - 0.5) - np.ceil(C[:-1] * N / M - 0.5)).astype(np.int64)
+    counts = torch.bincount(cell.long(), minlength=ncell).cpu().numpy()
+    assert np.abs(counts[:-1] - want).max() <= 1 and counts.sum() == N and counts[-1] == 0
+    ww = wt.cpu().numpy()
+    assert np.all(ww == ww[0]) and ww[0] == np.float32(M / N)
+    vv = v.cpu().numpy().astype(np.float64)
+    assert abs(vv.mean()) < 1e-4 and vv.var() == pytest.approx(1.0, rel=1e-3)
+    # plain steps with absorption: the live ions' fixed-point charge is the deposit, exactly
+    m0 = ctx.moments()
+    ctx.pic_steps(400)
+    assert ctx.sync_status() == 0
+    m1 = ctx.moments()
+    wq = np.rint(ctx.particles()[3].cpu().numpy().astype(np.float64) * 2.0 ** ctx.diagnostics().s_w)
+    assert m1["charge_fx"] == int(wq.astype(np.int64).sum()) << 24
+    assert m1["charge_fx"] <= m0["charge_fx"] and m1["invalid"] == 0
