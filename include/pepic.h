@@ -286,9 +286,10 @@ PE_API int pe_sort_noalloc(const int32_t* cell, const float* theta, const float*
  * PE_FLAG_RANGE. scratch: PE_MOMENTS_SCRATCH_BYTES of device memory (16-byte aligned);
  * out: one pe_moments in device memory, written on the stream. Floating-point sums use a
  * fixed partition for a given n, so repeated calls return identical bits. */
-#define PE_MOMENTS_SCRATCH_BYTES 49152
+#define PE_MOMENTS_SCRATCH_BYTES 65536
 typedef struct pe_moments {
-    int64_t charge_fx;          /* sum_p rn(w 2^s_w) 2^24: equals the sum of the deposit */
+    int64_t charge_fx;          /* sum_p rn(w 2^s_w) 2^24: equals the sum of the deposit (modulo 2^64:
+                                   the total wraps beyond 2^63, e.g. 2^25 ions near the weight cap) */
     int64_t invalid;            /* particles left out (see above) */
     double charge_fixed_point;  /* charge_fx 2^-(s_w+24) dx */
     double charge;              /* sum w dx */
@@ -299,6 +300,8 @@ typedef struct pe_moments {
     double total_energy;        /* kinetic + field + electron */
     double max_speed;           /* max |Vbar| */
     double cfl;                 /* max_speed dt / dx */
+    int64_t charge_wq;          /* sum_p rn(w 2^s_w): the exact charge in weight units (no wrap up
+                                   to 2^40 ions) */
 } pe_moments;
 PE_API int pe_compute_moments(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
                       const float* Ef, const double* phi, const double* E, int32_t ncell, double dx, double dt,

@@ -27,7 +27,7 @@ BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples
 PE_COARSE = {"moments": 0, "phase_space": 1}
 PE_MLP_NBUF = 7
 MLP_BUF = dict(params=0, params_bf16=1, grads=2, adam_m=3, adam_v=4, norm=5, work=6)
-PE_MOMENTS_SCRATCH_BYTES = 49152
+PE_MOMENTS_SCRATCH_BYTES = 65536
 
 _lock = threading.Lock()
 _lib = None
@@ -69,7 +69,8 @@ class Diag(ctypes.Structure):
 class Moments(ctypes.Structure):
     _fields_ = [("charge_fx", ctypes.c_int64), ("invalid", ctypes.c_int64)] + [
         (k, ctypes.c_double) for k in ("charge_fixed_point", "charge", "momentum", "kinetic", "field_energy",
-                                       "electron_energy", "total_energy", "max_speed", "cfl")]
+                                       "electron_energy", "total_energy", "max_speed", "cfl")] + [
+        ("charge_wq", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

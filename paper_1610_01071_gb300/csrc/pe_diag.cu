@@ -23,6 +23,7 @@ constexpr int kFinalThreads = 1024;
 
 struct DiagScratch {
     long long charge[kDiagMaxBlocks];
+    long long wq[kDiagMaxBlocks];
     long long invalid[kDiagMaxBlocks];
     double mom[kDiagMaxBlocks];
     double kin[kDiagMaxBlocks];
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_moments_particles(
     const float* __restrict__ w, int64_t n, const float* __restrict__ Ef, int ncell, float hk, float wscale,
     DiagScratch* __restrict__ out, uint32_t* status)
 {
-    long long q = 0, bad = 0;
+    long long q = 0, bad = 0, qw = 0;
     double mom = 0.0, kin = 0.0, ws = 0.0;
     float vmax = 0.0f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -65,19 +66,22 @@ __global__ void __launch_bounds__(kDiagThreads) k_moments_particles(
         const int c1 = (c + 1 == ncell) ? 0 : c + 1;
         const float Ec = __ldg(Ef + c), Ec1 = __ldg(Ef + c1);
         const float vb = fmaf(hk, fmaf(th, Ec1 - Ec, Ec), vv);
-        q += (long long)__float2int_rn(ww * wscale) * (long long)kThetaOne;
+        const long long wqi = (long long)__float2int_rn(ww * wscale);
+        q += wqi * (long long)kThetaOne;
+        qw += wqi;
         const double wd = (double)ww, vd = (double)vb;
         mom += wd * vd;
         kin += 0.5 * wd * vd * vd;
         ws += wd;
         vmax = fmaxf(vmax, fabsf(vb));
     }
-    __shared__ long long sq[kDiagThreads / 32], sb[kDiagThreads / 32];
+    __shared__ long long sq[kDiagThreads / 32], sb[kDiagThreads / 32], sqw[kDiagThreads / 32];
     __shared__ double sm[kDiagThreads / 32], sk[kDiagThreads / 32], sw[kDiagThreads / 32];
     __shared__ float sv[kDiagThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     q = warp_sum_i64(q);
     bad = warp_sum_i64(bad);
+    qw = warp_sum_i64(qw);
     mom = warp_sum(mom);
     kin = warp_sum(kin);
     ws = warp_sum(ws);
@@ -85,6 +89,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_moments_particles(
     if (lane == 0) {
         sq[wid] = q;
         sb[wid] = bad;
+        sqw[wid] = qw;
         sm[wid] = mom;
         sk[wid] = kin;
         sw[wid] = ws;
@@ -95,6 +100,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_moments_particles(
         for (int k = 1; k < kDiagThreads / 32; ++k) {
             q += sq[k];
             bad += sb[k];
+            qw += sqw[k];
             mom += sm[k];
             kin += sk[k];
             ws += sw[k];
@@ -102,6 +108,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_moments_particles(
         }
         out->charge[blockIdx.x] = q;
         out->invalid[blockIdx.x] = bad;
+        out->wq[blockIdx.x] = qw;
         out->mom[blockIdx.x] = mom;
         out->kin[blockIdx.x] = kin;
         out->wsum[blockIdx.x] = ws;
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_moments_final(
     __shared__ float rf[32];
     const int t = threadIdx.x;
     const bool have = t < nblocks;
-    long long q = have ? part->charge[t] : 0, bad = have ? part->invalid[t] : 0;
+    long long q = have ? part->charge[t] : 0, bad = have ? part->invalid[t] : 0, qw = have ? part->wq[t] : 0;
     double mom = have ? part->mom[t] : 0.0, kin = have ? part->kin[t] : 0.0, ws = have ? part->wsum[t] : 0.0;
     float vmax = have ? part->vmax[t] : 0.0f;
     double fe = 0.0, ee = 0.0;
@@ -153,6 +160,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_moments_final(
     q = block_reduce(q, ri, add_i);
     const long long qs = q;
     bad = block_reduce(bad, ri, add_i);
+    const long long bads = bad;
+    qw = block_reduce(qw, ri, add_i);
     mom = block_reduce(mom, rd, add_d);
     const double moms = mom;
     kin = block_reduce(kin, rd, add_d);
@@ -166,7 +175,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_moments_final(
     if (t == 0) {
         pe_moments m;
         m.charge_fx = qs;
-        m.invalid = bad;
+        m.invalid = bads;
+        m.charge_wq = qw;
         m.charge_fixed_point = (double)qs * charge_scale * dx;
         m.charge = wss * dx;
         m.momentum = moms * dx;
