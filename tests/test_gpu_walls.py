@@ -430,4 +430,5 @@ def test_slab_full_size_properties():
     # in weight units (the deposit units' total, sum w_q 2^24, exceeds 2^63 at this size)
     assert m1["charge_wq"] == int(wq.astype(np.int64).sum())
     assert m1["charge_wq"] < m0["charge_wq"] and m1["invalid"] == 0
-    assert m0["charge_fx"] == (m0["charge_wq"] << 24) - (1 << 64) * ((m0["charge_wq"] << 24) >= (1 << 63))
+    wrapped = (((m0["charge_wq"] << 24) + (1 << 63)) % (1 << 64)) - (1 << 63)  # int64 two's complement
+    assert m0["charge_fx"] == wrapped
