@@ -41,6 +41,10 @@ int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, in
                         int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
                         double* phi_prev, int extrap, cudaStream_t s);
 
+// Grid of a particle pass (pe_particles.cu): one chunk of particles (a multiple of 4, at most
+// max_chunk or 65536) per block, filling whole waves of resident blocks; returns the block count.
+int particle_grid(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk = 0);
+
 // Batched particle passes (pe_particles.cu).
 size_t push_desc_size();
 size_t work_item_size();

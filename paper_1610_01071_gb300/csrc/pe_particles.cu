@@ -701,7 +701,7 @@ static __device__ __align__(256) unsigned g_sort_static[2 * PE_SORT_STATIC_MAX_C
 // at once (one wave). When the chunk cap (which keeps the shared-memory digit counters exact)
 // forces more blocks than that, the chunk is shrunk so that the blocks fill whole waves: a
 // last wave holding a few full-size blocks would leave most SMs idle while it runs.
-static int grid_for(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk = 0)
+int particle_grid(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk)
 {
     const int64_t slots = (int64_t)sm_count() * blocks_per_sm(kernel, block, smem);
     const int64_t cap = (max_chunk > 0 && max_chunk < kMaxChunk) ? (max_chunk & ~int64_t(3)) : kMaxChunk;
@@ -735,7 +735,7 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = P.walls ? (const void*)k_particles<MODE, true> : (const void*)k_particles<MODE, false>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    int grid = grid_for(k, block, smem, P.n, &P.chunk, P.max_chunk);
+    int grid = particle_grid(k, block, smem, P.n, &P.chunk, P.max_chunk);
     if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
     const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : 2 * (size_t)(P.ncell >> P.bin_shift);
     if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess) return PE_ECUDA;
@@ -999,7 +999,7 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
     const void* k = (const void*)k_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    int grid = grid_for(k, block, smem, n, &P.chunk);
+    int grid = particle_grid(k, block, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start<<<grid, block, smem, s>>>(P);
     return launch_status();
@@ -1047,7 +1047,7 @@ extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v
     const size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
     const void* k = (const void*)k_quiet_start_equal;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    const int grid = grid_for(k, block, smem, n, &P.chunk);
+    const int grid = particle_grid(k, block, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start_equal<<<grid, block, smem, s>>>(P);
     return launch_status(2);
@@ -1100,7 +1100,7 @@ extern "C" PE_API int pe_sort(const int32_t* cell, const float* theta, const flo
     if (ensure_smem((const void*)k_sort_count, smem1) != PE_OK ||
         ensure_smem((const void*)k_sort_scatter, smem2) != PE_OK)
         return PE_ECUDA;
-    int grid = grid_for((const void*)k_sort_scatter, block, smem2, n, &chunk);
+    int grid = particle_grid((const void*)k_sort_scatter, block, smem2, n, &chunk);
     k_sort_count<<<grid, block, smem1, s>>>(cell, n, chunk, ncell, counts, status);
     k_sort_scan<<<1, 1024, 0, s>>>(counts, cursor, ncell);
     k_sort_scatter<<<grid, block, smem2, s>>>(cell, theta, v, w, n, chunk, ncell, cursor, out_cell, out_theta, out_v,

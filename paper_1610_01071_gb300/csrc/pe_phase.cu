@@ -694,16 +694,7 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    // whole waves of resident blocks, chunks within the digit counters' bound (as grid_for)
-    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
-    const int64_t waves = (n + slots * kMaxChunk - 1) / (slots * kMaxChunk);
-    const int64_t blocks = slots * (waves < 1 ? 1 : waves);
-    int64_t c = (n + blocks - 1) / blocks;
-    c = (c + 3) & ~int64_t(3);
-    if (c < 4) c = 4;
-    if (c > kMaxChunk) c = kMaxChunk;
-    P.chunk = c;
-    const int grid = (int)((n + c - 1) / c);
+    const int grid = particle_grid(k, 256, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
     return launch_status(1);
@@ -765,16 +756,7 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start_equal;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-    // whole waves of resident blocks, chunks within the digit counters' bound (as grid_for)
-    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, 256, smem);
-    const int64_t waves = (n + slots * kMaxChunk - 1) / (slots * kMaxChunk);
-    const int64_t blocks = slots * (waves < 1 ? 1 : waves);
-    int64_t c = (n + blocks - 1) / blocks;
-    c = (c + 3) & ~int64_t(3);
-    if (c < 4) c = 4;
-    if (c > kMaxChunk) c = kMaxChunk;
-    P.chunk = c;
-    const int grid = (int)((n + c - 1) / c);
+    const int grid = particle_grid(k, 256, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_ps_quiet_start_equal<<<grid, 256, smem, s>>>(P);
     return launch_status(3);
