@@ -305,10 +305,17 @@ struct LaneWindow {
             reset((c - 1) & grid.mask);
             d = 1;
         }
-        s0 += (d == 0) ? q.left : 0ull;
-        s1 += (d == 0) ? q.right : ((d == 1) ? q.left : 0ull);
-        s2 += (d == 1) ? q.right : ((d == 2) ? q.left : 0ull);
-        s3 += (d == 2) ? q.right : 0ull;
+        // one pair of 64-bit adds under a predicate (no selects of 64-bit values)
+        if (d == 1) {
+            s1 += q.left;
+            s2 += q.right;
+        } else if (d == 0) {
+            s0 += q.left;
+            s1 += q.right;
+        } else {
+            s2 += q.left;
+            s3 += q.right;
+        }
     }
 };
 
