@@ -351,12 +351,23 @@ struct BinAcc {
 // Adds the active lanes' bin runs to the density and momentum BinGrids, summing runs of
 // equal bins in consecutive lanes first (consecutive lanes hold neighbouring particles of a
 // velocity-ordered cell, whose co-moving bins mostly agree): |sum| <= 32 * 4 * 2^23 = 2^30.
+// One warp sum when every active lane holds the same bin, else a segmented sum per run.
 // Lanes with key < 0 add nothing; if the active lanes are not a prefix of the warp, every
 // lane adds on its own.
 __device__ __forceinline__ void bin_add_warp(const BinGrid& gn, const BinGrid& gm, int key, int32_t n, int32_t m)
 {
     const unsigned act = __activemask();
     const int lane = threadIdx.x & 31;
+    const int first = __ffs(act) - 1;
+    const int k0 = __shfl_sync(act, key, first);
+    if (__all_sync(act, key == k0)) {  // one bin for every active lane (the common case)
+        const int32_t sn = __reduce_add_sync(act, n), sm = __reduce_add_sync(act, m);
+        if (k0 >= 0 && lane == first) {
+            gn.add_whole(k0, sn);
+            gm.add_whole(k0, sm);
+        }
+        return;
+    }
     const int nact = __popc(act);
     if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
         if (key >= 0) {
