@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the fused kernel from the ncu capture summarised
 # in profiles/k_particles_push_sample_iaw_large.md, valid while the kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
-NCU_TRAFFIC = {"source_hash": "8f6d1e8b0363d19f", "bytes": 270.744064e6 + 145.735168e6}
+NCU_TRAFFIC = {"source_hash": "35e21ff27381b258", "bytes": 270.735360e6 + 145.710336e6}
 
 
 def kernel_source_hash():

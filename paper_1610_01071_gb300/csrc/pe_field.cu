@@ -221,16 +221,18 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         cluster.sync();
     }
     double gj = boltz ? exp(pj) : 1.0 + pj;
+    // Halo ph[0], ph[B + 1]: the neighbouring blocks' boundary nodes, read once and then
+    // advanced here with the same damped updates their owners apply (the boundary unknowns of
+    // the reduced system, known to every block), so they stay bit-identical to the owners'
+    // values. Only threads 0 and B - 1 read and write them.
+    if (act && i == 0) ph[0] = phi[(g * B - 1) & mask];
+    if (act && i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
 
     int it = 0;
     bool converged = false;
     for (it = 0; it < maxit; ++it) {
         // ---- FP64 residual with the halo from the neighbouring blocks (mirror ghosts at walls)
-        if (act) {
-            ph[i + 1] = pj;
-            if (i == 0) ph[0] = phi[(g * B - 1) & mask];
-            if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
-        }
+        if (act) ph[i + 1] = pj;
         __syncthreads();
         if (act) {
             const double pl = wl ? ph[i + 2] : ph[i], pr = wr ? ph[i] : ph[i + 2];
@@ -304,7 +306,9 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         block_pcr<T>(L3, L3n, zsol, G);
         const T Xl = zsol[2 * ((g - 1 + G) % G) + 1];  // previous block's last unknown
         const T Xr = zsol[2 * ((g + 1) % G)];          // next block's first unknown
-        const T dlt = y - gsp * Xl - hsp * Xr;
+        // the block's own first and last unknowns are those of the reduced system (equal to
+        // y - g X_left - h X_right up to rounding), so that the neighbours' halos follow them
+        const T dlt = (i == 0) ? zsol[2 * g] : ((i == B - 1) ? zsol[2 * g + 1] : y - gsp * Xl - hsp * Xr);
         // ---- global max |update| (damping and convergence)
         T mloc = act ? (dlt < T(0) ? -dlt : dlt) : T(0);
         for (int off = 16; off > 0; off >>= 1) {
@@ -321,30 +325,28 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
             }
             if (i == 0) *mymax = (double)v;
         }
-        cluster.sync();  // #2: block maxima visible; level-3 rows no longer read
+        // #2: block maxima visible; level-3 rows no longer read. The next iteration rewrites
+        // mine and mymax only after its barrier #1, which every block reaches after reading them.
+        cluster.sync();
         double m = 0.0;
         for (int k = 0; k < G; ++k) m = fmax(m, *cluster.map_shared_rank(mymax, k));
         const double scale = (m > 2.0) ? 2.0 / m : 1.0;
         const double x = act ? scale * (double)dlt : 0.0;
         pj += x;
         if (act) phi[j] = pj;
+        if (act && i == 0) ph[0] += scale * (double)Xl;
+        if (act && i == B - 1) ph[B + 1] += scale * (double)Xr;
         if (boltz)
             gj = (fabs(x) <= 0.03125) ? gj * exp_small(x) : exp(pj);
         else
             gj = 1.0 + pj;
-        __threadfence();
-        cluster.sync();  // #3: updated phi visible to the neighbouring blocks
         if (m < tol) {
             converged = true;
             ++it;
             break;
         }
     }
-    if (act) {
-        ph[i + 1] = pj;
-        if (i == 0) ph[0] = phi[(g * B - 1) & mask];
-        if (i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
-    }
+    if (act) ph[i + 1] = pj;
     __syncthreads();
     if (act) {
         const double e = (wl || wr) ? 0.0 : -(ph[i + 2] - ph[i]) * (0.5 / dx);
@@ -360,6 +362,7 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         }
         if (!converged) raise_flag(d.status, PE_FLAG_NOCONV);
     }
+    cluster.sync();  // no block leaves while another may still read its mymax
 }
 
 template <typename T>
