@@ -61,13 +61,16 @@ __device__ __forceinline__ double exp_small(double x)
     return fma(p, x, 1.0);
 }
 
-// Reciprocal for the elimination: FP32 division, or in FP64 two Newton-Raphson steps
-// r <- r (2 - x r) from the FP32 reciprocal (each step squares the relative error, 2^-24 ->
-// 2^-48 -> 2^-96), which avoids the long FP64 division sequence on the PCR's serial chain.
-__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+// Reciprocal for the elimination (and the 2x2 inverses of the boundary system): the fast FP32
+// reciprocal (__fdividef, within 2 ulp for the diagonal magnitudes that occur here), or in
+// FP64 two Newton-Raphson steps r <- r (2 - x r) from it (each step squares the relative
+// error, 2^-22 -> 2^-44 -> 2^-88), which avoids the long division sequences on the
+// reductions' serial chains. The FP32 solve is the inexact linear solve of a Newton
+// iteration whose residual is FP64, so a 2-ulp reciprocal only changes its contraction rate.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x)
 {
-    double r = (double)(1.0f / (float)x);
+    double r = (double)__fdividef(1.0f, (float)x);
     r = r * fma(-x, r, 2.0);
     return r * fma(-x, r, 2.0);
 }
@@ -89,7 +92,7 @@ __device__ __forceinline__ M2<T> msub(M2<T> x, M2<T> y)
 template <typename T>
 __device__ __forceinline__ M2<T> minv(M2<T> x)
 {
-    const T r = T(1) / (x.a * x.d - x.b * x.c);
+    const T r = recip(x.a * x.d - x.b * x.c);
     return {x.d * r, -x.b * r, -x.c * r, x.a * r};
 }
 template <typename T>
@@ -103,6 +106,7 @@ __device__ __forceinline__ void mvec(M2<T> x, T v0, T v1, T* o0, T* o1)
 // 2x2 matrices: L3[k] = {Mk(4), Dk(4), Pk(4), rk(2)}, row k: Mk z_{k-1} + Dk z_k + Pk z_{k+1} = rk.
 // After the steps with stride G/2 every row couples only to itself. zsol gets z. (On a
 // bounded grid the corner blocks M_0 and P_{G-1} are zero, so the wrap adds nothing.)
+// The steps alternate between L3 and L3n, one barrier per step.
 template <typename T>
 __device__ void block_pcr(T* L3, T* L3n, T* zsol, int G)
 {
@@ -133,10 +137,10 @@ __device__ void block_pcr(T* L3, T* L3n, T* zsol, int G)
             o[12] = c[12] - ra0 - rg0;
             o[13] = c[13] - ra1 - rg1;
         }
-        __syncthreads();
-        if (k < G)
-            for (int q = 0; q < 14; ++q) L3[14 * k + q] = L3n[14 * k + q];
-        __syncthreads();
+        __syncthreads();  // the next step reads L3n and overwrites L3, whose reads are done
+        T* t = L3;
+        L3 = L3n;
+        L3n = t;
     }
     if (k < G) {
         const T* c = L3 + 14 * k;
@@ -186,14 +190,11 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     const int mode = d.mode, maxit = d.maxit;
     double* ph = sh;                             // [B + 2]
     double* mymax = ph + B + 2;                  // [1]
-    T* A = reinterpret_cast<T*>(mymax + 1);      // [B] x 7
-    T* Bd = A + B;
-    T* C = Bd + B;
-    T* D = C + B;
-    T* Gs = D + B;
-    T* Hs = Gs + B;
-    T* Rb = Hs + B;      // [B] reciprocals of the diagonal
-    T* red = Rb + B;     // [32]
+    // two sets of the seven row arrays (A, Bd, C, D, Gs, Hs, Rb: sub-, main and super-diagonal,
+    // right-hand side, the two coupling columns, reciprocal of the diagonal); the reduction
+    // steps alternate between them
+    T* rows = reinterpret_cast<T*>(mymax + 1);   // [2][7][B]
+    T* red = rows + 14 * B;  // [32]
     T* mine = red + 32;  // [6]
     T* L3 = mine + 8;    // [G][14]
     T* L3n = L3 + 14 * G;
@@ -234,6 +235,13 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         // ---- FP64 residual with the halo from the neighbouring blocks (mirror ghosts at walls)
         if (act) ph[i + 1] = pj;
         __syncthreads();
+        T* A = rows;
+        T* Bd = A + B;
+        T* C = Bd + B;
+        T* D = C + B;
+        T* Gs = D + B;
+        T* Hs = Gs + B;
+        T* Rb = Hs + B;
         if (act) {
             const double pl = wl ? ph[i + 2] : ph[i], pr = wr ? ph[i] : ph[i + 2];
             const double lap = (pl - 2.0 * pj + pr) * inv_dx2;
@@ -246,8 +254,10 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
             Hs[i] = (i == B - 1 && !wr) ? o : T(0);
         }
         __syncthreads();
-        // ---- parallel cyclic reduction of the block rows, three right-hand sides
+        // ---- parallel cyclic reduction of the block rows, three right-hand sides; step s reads
+        // one row set and writes the other, so one barrier per step separates the steps
         for (int s = 1; s < B; s <<= 1) {
+            T* nx = (A == rows) ? rows + 7 * B : rows;  // the other row set
             const int im = act ? i - s : -1, ip = act ? i + s : B;
             const T al = (im >= 0) ? A[i] * Rb[im] : T(0);
             const T ga = (ip < B) ? C[i] * Rb[ip] : T(0);
@@ -266,7 +276,13 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
                 nG -= ga * Gs[ip];
                 nH -= ga * Hs[ip];
             }
-            __syncthreads();
+            A = nx;
+            Bd = nx + B;
+            C = nx + 2 * B;
+            D = nx + 3 * B;
+            Gs = nx + 4 * B;
+            Hs = nx + 5 * B;
+            Rb = nx + 6 * B;
             if (act) {
                 A[i] = nA;
                 C[i] = nC;
@@ -420,7 +436,7 @@ static int cluster_size_for(int ncell)
 size_t newton_smem_bytes(int B, int G, bool fp64)
 {
     const size_t t = fp64 ? sizeof(double) : sizeof(float);
-    return sizeof(double) * ((size_t)B + 3) + t * (7 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    return sizeof(double) * ((size_t)B + 3) + t * (14 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
 }
 
 static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int nclusters, int block, size_t smem,
