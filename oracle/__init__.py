@@ -99,6 +99,13 @@ def _load():
                 "orc_ps_quiet_start_equal": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
                 "orc_ps_burst_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl,
                                                       i32, i32, i32, dbl, dbl, i32, P, P]),
+                "orc_poisson_periodic": (None, [i32, dbl, P, P, P]),
+                "orc_field_kinetic": (None, [i64, P, P, P, i64, P, P, P, i32, dbl, i32, P, P]),
+                "orc_pic_steps_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32,
+                                                 i32, i32, P]),
+                "orc_burst_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, dbl,
+                                             i32, i32, i32, dbl, dbl, i32, P, P, P]),
+                "orc_boltzmann_electrons": (None, [i64, i32, P, dbl, u64, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -670,3 +677,63 @@ def ps_project(samples, dt, dT, filt=0):
         s = 0.25 * left + 0.5 * s + 0.25 * right
     out = y[-1] + (dT - (K1 - 1) * dt) * s
     return out, s
+
+
+# ------------------------------------------------------------------ kinetic electrons (Section 4.1)
+# Both species as particles in the bursts; ions q/m = qm_i, electrons q/m = qm_e (-1800 in the
+# paper's runs). The field is the periodic Poisson equation for the net charge n_i - n_e.
+
+
+def poisson_periodic(r, dx):
+    """-(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 = r_j - <r>, <phi> = 0; returns (phi, E)."""
+    r = _f64(r)
+    phi, E = np.zeros_like(r), np.zeros_like(r)
+    _load().orc_poisson_periodic(r.shape[0], float(dx), _p(r), _p(phi), _p(E))
+    return phi, E
+
+
+def field_kinetic(ions: State, electrons: State, ncell, dx, s_w):
+    """Fixed-point deposits of both species, net density, periodic Poisson: (phi, E)."""
+    phi, E = np.zeros(ncell), np.zeros(ncell)
+    _load().orc_field_kinetic(ions.n, _p(ions.cell), _p(ions.theta), _p(ions.w), electrons.n, _p(electrons.cell),
+                              _p(electrons.theta), _p(electrons.w), ncell, float(dx), int(s_w), _p(phi), _p(E))
+    return phi, E
+
+
+def pic_steps_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, nsteps, s_w, vel_at_integer=True):
+    """nsteps two-species leapfrog steps in place; returns the last step's phi."""
+    phi = np.zeros(ncell)
+    _load().orc_pic_steps_kinetic(ions.n, _p(ions.cell), _p(ions.theta), _p(ions.v), _p(ions.w), electrons.n,
+                                  _p(electrons.cell), _p(electrons.theta), _p(electrons.v), _p(electrons.w), ncell,
+                                  float(dx), float(dt), float(qm_i), float(qm_e), int(nsteps), int(s_w),
+                                  int(vel_at_integer), _p(phi))
+    return phi
+
+
+def burst_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, K, dT, s_w, vel_at_integer=True,
+                  nv=0, bin_shift=0, vmin=0.0, dv=1.0):
+    """K two-species steps in place with the ions' co-moving restriction; returns (samples, phi):
+    moments [(K+1), 2, ncell] (double) for nv = 0, else phase-space int64 [(K+1), nxc, nv]."""
+    phi = np.zeros(ncell)
+    if nv > 0:
+        sfx = np.zeros((K + 1, ncell >> bin_shift, nv), np.int64)
+        sd = np.zeros(1)
+    else:
+        sd = np.zeros((K + 1, 2, ncell))
+        sfx = np.zeros(1, np.int64)
+    _load().orc_burst_kinetic(ions.n, _p(ions.cell), _p(ions.theta), _p(ions.v), _p(ions.w), electrons.n,
+                              _p(electrons.cell), _p(electrons.theta), _p(electrons.v), _p(electrons.w), ncell,
+                              float(dx), float(dt), float(qm_i), float(qm_e), int(K), float(dT), int(s_w),
+                              int(vel_at_integer), int(bin_shift), float(vmin), float(dv), int(nv), _p(phi), _p(sd),
+                              _p(sfx))
+    return (sfx if nv > 0 else sd), phi
+
+
+def boltzmann_electrons(N, ncell, phi, v_th_e, seed):
+    """Electrons of the lifting: quiet start on n_e = exp(phi), zero mean velocity."""
+    phi = _f64(phi)
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_boltzmann_electrons(N, ncell, _p(phi), float(v_th_e), seed & 0xFFFFFFFFFFFFFFFF, _p(cell),
+                                    _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)

@@ -789,6 +789,137 @@ int orc_ps_burst(int64_t n, int32_t* cell, double* theta, double* v, const doubl
     return fails;
 }
 
+/* ---------------------------------------------------------------- kinetic electrons
+ * Section 4.1: in the paper's ion-acoustic runs both species are particles in the PIC
+ * bursts (q_e/m_e = -1800 against q_i/m_i = 1, a time step that resolves the electron
+ * plasma period); the Boltzmann relation only serves the lifting. The field is then the
+ * plain Poisson equation for the net charge n_i - n_e: an electron of weight w carries
+ * charge -w dx, an ion +w dx. */
+
+/* Periodic Poisson equation -(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 = r_j - <r> with
+ * <phi> = 0, and the centred field E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx). Solved through
+ * the face fields F_{j+1/2} = -(phi_{j+1} - phi_j) / dx: consecutive faces differ by
+ * dx (r_j - <r>) (the discrete Gauss law) and the faces sum to zero (phi is periodic);
+ * E_j = (F_{j+1/2} + F_{j-1/2}) / 2. */
+void orc_poisson_periodic(int32_t ncell, double dx, const double* r, double* phi, double* E)
+{
+    double* F = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double mean = 0.0;
+    for (int32_t j = 0; j < ncell; ++j) mean += r[j];
+    mean /= ncell;
+    double acc = 0.0, fsum = 0.0;
+    for (int32_t j = 0; j < ncell; ++j) { /* F_{j+1/2} - F_{-1/2} */
+        acc += dx * (r[j] - mean);
+        F[j] = acc;
+        fsum += acc;
+    }
+    for (int32_t j = 0; j < ncell; ++j) F[j] -= fsum / ncell;
+    double p = 0.0, psum = 0.0;
+    for (int32_t j = 0; j < ncell; ++j) { /* phi_0 = 0, phi_{j+1} = phi_j - dx F_{j+1/2} */
+        phi[j] = p;
+        psum += p;
+        p -= dx * F[j];
+    }
+    for (int32_t j = 0; j < ncell; ++j) phi[j] -= psum / ncell;
+    for (int32_t j = 0; j < ncell; ++j) E[j] = 0.5 * (F[j] + F[wrap((int64_t)j - 1, ncell)]);
+    free(F);
+}
+
+/* Field of a two-species state: fixed-point deposits of ions and electrons (the same rule
+ * and shift s_w), net density (rho_i - rho_e) 2^-(s_w+24), periodic Poisson, centred E. */
+static void field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const double* wi, int64_t ne,
+                          const int32_t* ce, const double* te, const double* we, int32_t ncell, double dx,
+                          int32_t s_w, double* phi, double* E)
+{
+    int64_t* rho_i = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t* rho_e = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    double* r = (double*)malloc(sizeof(double) * (size_t)ncell);
+    orc_deposit_fx(ni, ci, ti, wi, ncell, s_w, rho_i);
+    orc_deposit_fx(ne, ce, te, we, ncell, s_w, rho_e);
+    const double scale = ldexp(1.0, -(s_w + 24));
+    for (int32_t j = 0; j < ncell; ++j) r[j] = (double)(rho_i[j] - rho_e[j]) * scale;
+    orc_poisson_periodic(ncell, dx, r, phi, E);
+    free(rho_i);
+    free(rho_e);
+    free(r);
+}
+
+void orc_field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const double* wi, int64_t ne,
+                       const int32_t* ce, const double* te, const double* we, int32_t ncell, double dx, int32_t s_w,
+                       double* phi, double* E)
+{
+    field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
+}
+
+/* Plain two-species PIC steps (Section 2.2 leapfrog for each species in the field of both). */
+void orc_pic_steps_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
+                           int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
+                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer, double* phi)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t s = 0; s < nsteps; ++s) {
+        field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
+        orc_push(ni, ci, ti, vi, E, ncell, dx, dt, qm_i, kick);
+        orc_push(ne, ce, te, ve, E, ncell, dx, dt, qm_e, kick);
+        kick = 1.0;
+    }
+    free(E);
+}
+
+/* Burst of K two-species steps with the co-moving restriction of the ions (Appendix B), as
+ * orc_burst / orc_ps_burst: nv = 0 records the ion density and momentum samples (double,
+ * [K+1][2][ncell]) in samples; nv > 0 the fixed-point phase-space samples ([K+1][nxc][nv])
+ * in samples_fx. */
+void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
+                       int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
+                       double qm_i, double qm_e, int32_t K, double dT, int32_t s_w, int32_t vel_at_integer,
+                       int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi, double* samples,
+                       int64_t* samples_fx)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)ni);
+    const size_t row = nv > 0 ? (size_t)(ncell >> bin_shift) * (size_t)nv : 2 * (size_t)ncell;
+    field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell); /* E_n, stored at burst start */
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < ni; ++i)
+            vbar[i] = vi[i] + (kick - 0.5) * qm_i * dt * orc_gather(E, ncell, ci[i], ti[i]);
+        const double tau = dT - p * dt;
+        if (nv > 0) {
+            orc_ps_sample_fx(ni, ci, ti, vbar, wi, E0, ncell, dx, tau, qm_i, bin_shift, vmin, dv, nv, s_w,
+                             samples_fx + (size_t)p * row);
+        } else {
+            double* dens = samples + (size_t)p * row;
+            orc_restrict_sample(ni, ci, ti, vbar, wi, E0, ncell, dx, tau, qm_i, dens, dens + ncell);
+        }
+        if (p == K) break;
+        orc_push(ni, ci, ti, vi, E, ncell, dx, dt, qm_i, kick);
+        orc_push(ne, ce, te, ve, E, ncell, dx, dt, qm_e, kick);
+        kick = 1.0;
+        field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+}
+
+/* Electrons of the lifting (Section 3.3, Eq. electronpassive): Boltzmann density
+ * n_e = exp(phi) of the Poisson-Boltzmann potential of the ion density, no mean velocity,
+ * Maxwellian of thermal speed v_th_e, quiet start on that profile. */
+void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, double v_th_e, uint64_t seed,
+                             int32_t* cell, double* theta, double* v, double* w)
+{
+    double* n = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* u = (double*)calloc((size_t)ncell, sizeof(double));
+    for (int32_t j = 0; j < ncell; ++j) n[j] = exp(phi[j]);
+    orc_quiet_start(N, ncell, n, u, v_th_e, seed, cell, theta, v, w);
+    free(n);
+    free(u);
+}
+
 /* ---------------------------------------------------------------- bounded domain
  * Walls at node 0 (x = 0) and node ncell-1 (x = (ncell-1) dx); the particles live in the
  * ncell-1 cells between them. Section 4.2 runs the slab expansion with an absorbing

@@ -230,6 +230,22 @@ int orc_ps_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, doubl
                        int32_t maxit, int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv,
                        double* phi, int64_t* samples);
 
+/* Kinetic electrons (Section 4.1's two-species bursts). */
+void orc_poisson_periodic(int32_t ncell, double dx, const double* r, double* phi, double* E);
+void orc_field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const double* wi, int64_t ne,
+                       const int32_t* ce, const double* te, const double* we, int32_t ncell, double dx, int32_t s_w,
+                       double* phi, double* E);
+void orc_pic_steps_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
+                           int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
+                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer, double* phi);
+void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
+                       int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
+                       double qm_i, double qm_e, int32_t K, double dT, int32_t s_w, int32_t vel_at_integer,
+                       int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi, double* samples,
+                       int64_t* samples_fx);
+void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, double v_th_e, uint64_t seed,
+                             int32_t* cell, double* theta, double* v, double* w);
+
 #ifdef __cplusplus
 }
 #endif
