@@ -85,6 +85,18 @@ extern "C" {
 #define PE_BOUNDARY_PERIODIC 0
 #define PE_BOUNDARY_ABSORBING 1
 
+/* Electrons. Boltzmann: a fluid in equilibrium with the potential (Eq. electronpassive), so the
+ * field is the Poisson-Boltzmann equation (pe_field). Kinetic (Section 4.1: the paper's PIC
+ * bursts move both species): nparticles electron particles beside the ions, charge-to-mass
+ * ratio qm_e, pushed with the same kernels; the field is the Poisson equation for the net
+ * charge (pe_field_kinetic). Every load and every lift places the electrons in Boltzmann
+ * equilibrium with the ions: the Poisson-Boltzmann potential of the ion density, then a quiet
+ * start on exp(phi) with thermal speed v_th_e and no drift (pe_boltzmann_profile). Kinetic
+ * electrons need a periodic grid and a time step that resolves the electron plasma period
+ * (|qm_e|^(-1/2) in these units). */
+#define PE_ELECTRONS_BOLTZMANN 0
+#define PE_ELECTRONS_KINETIC 1
+
 PE_API const char* pe_strerror(int code);
 PE_API const char* pe_version(void);
 
@@ -120,6 +132,28 @@ PE_API int pe_field(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w
 PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
                        int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
                        int32_t* diag, uint32_t* status, void* stream);
+
+/* Field of a two-species (kinetic-electron) state, Section 4.1: the paper's ion-acoustic
+ * bursts move the electrons as particles (q_e/m_e = -1800), so the field is the plain
+ * Poisson equation for the net charge on the periodic grid,
+ *   -(phi_{j+1} - 2 phi_j + phi_{j-1}) / dx^2 = r_j - <r>,  r_j = (rho_i_j - rho_e_j) 2^-(s_w+24),
+ * with <phi> = 0 (the mean of r, a fixed-point rounding remainder of a neutral system, is
+ * a uniform background), and E_j = -(phi_{j+1} - phi_{j-1}) / (2 dx).
+ * rho_i[ncell], rho_e[ncell]: fixed-point deposits (pe_deposit / pe_push rule, same s_w) of
+ * the ions and of the electrons (both with positive weights). Writes phi[ncell], E[ncell]
+ * (FP64) and Ef[ncell] (FP32). One block: a prefix sum of the net charge (the per-node int64
+ * difference is exact, the sums FP64 in a fixed order) gives the face fields
+ * F_{j+1/2} = -(phi_{j+1} - phi_j)/dx (discrete Gauss law), their mean is removed (phi
+ * periodic), then E_j = (F_{j+1/2} + F_{j-1/2}) / 2 and phi by a second sum. Periodic grids
+ * only; ncell a power of two, 8..8192. */
+PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_e, int32_t ncell, double dx, int32_t s_w,
+                            double* phi, double* E, float* Ef, void* stream);
+
+/* Boltzmann electron profile of the lifting, Eq. (electronpassive): n_prof[j] = exp(phi[j])
+ * (FP32) and u_prof[j] = 0, the two profile arrays pe_quiet_start loads the electrons from
+ * (with their thermal speed). phi[ncell]: the Poisson-Boltzmann potential of the ion density
+ * (pe_field). */
+PE_API int pe_boltzmann_profile(const double* phi, int32_t ncell, float* n_prof, float* u_prof, void* stream);
 
 /* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
  * follows it): each particle, at its integer-time velocity Vbar, is carried to
@@ -417,6 +451,11 @@ typedef struct pe_config {
     int32_t ps_filter;    /* phase space: 1-2-1 filter of the projected slope; bit 0 in v, bit 1 in x */
     int32_t boundary;     /* PE_BOUNDARY_*; absorbing grids lift with pe_quiet_start_equal
                              (moments) or pe_ps_quiet_start_equal (phase space) */
+    int32_t electrons;    /* PE_ELECTRONS_*: Boltzmann fluid (0) or kinetic particles (1) */
+    int32_t reset_every;  /* kinetic electrons, plain PIC: reload the electrons in Boltzmann
+                             equilibrium with the ions every this many steps (0 = never) */
+    double qm_e;          /* kinetic electrons: charge-to-mass ratio (0 = -1800, the paper's value) */
+    double v_th_e;        /* kinetic electrons: thermal speed (0 = sqrt(-qm_e), i.e. T_e = 1) */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;
@@ -441,6 +480,9 @@ enum pe_buffer {
     PE_BUF_SURROGATE,       /* f64[2][n_coarse] surrogate slope + gate result */
     PE_BUF_PHASE,           /* phase space: f64 bin masses, CDF tables, reconstruction scratch, flag;
                                absorbing grids: the equal-weight loading scratch */
+    PE_BUF_ELECTRONS_A,     /* kinetic electrons: cell | theta | v | w, as the ion banks (else empty) */
+    PE_BUF_ELECTRONS_B,     /* kinetic electrons: second bank (sort target) */
+    PE_BUF_RHO_E,           /* kinetic electrons: int64[ncell] electron deposit */
     PE_NBUF
 };
 
@@ -459,6 +501,8 @@ typedef struct pe_diag {
     int32_t s_w, s_p;       /* fixed-point shifts in use */
     int32_t newton_iters;   /* iterations of the last field solve (after sync) */
     uint32_t status;        /* device status word (after sync) */
+    int32_t electron_bank;  /* kinetic electrons: which PE_BUF_ELECTRONS_* holds them */
+    int32_t e_v_at_integer; /* kinetic electrons: 1 if their stored v is at integer time */
 } pe_diag;
 
 /* Validates cfg and fills the arena layout. PE_EINVAL on a bad configuration. */
@@ -474,23 +518,28 @@ PE_API void pe_destroy(pe_ctx* ctx);
 /* Initial state at t = 0 from an analytic nodal profile (PE_PROFILE_SINE with the
  * given amplitude, or PE_PROFILE_SLAB, amplitude unused) by the quiet start (periodic grids:
  * pe_quiet_start; absorbing grids: pe_quiet_start_equal); also computes the initial coarse
- * state. */
+ * state. Kinetic electrons start in Boltzmann equilibrium with these ions. */
 PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude);
 
 /* Micro-scale evolution (Section 3.1): K fine steps from the current particles with
- * the co-moving restriction sample of each of the K+1 instants (Appendix B). */
+ * the co-moving restriction sample of each of the K+1 instants (Appendix B). With kinetic
+ * electrons every fine step pushes both species in the field of the net charge; the
+ * samples are the ions'. */
 PE_API int pe_burst(pe_ctx* ctx);
 /* Coarsening of the K+1 samples (pe_coarsen into PE_BUF_COARSE_SAMPLES). */
 PE_API int pe_restrict(pe_ctx* ctx);
 /* Least-squares slope and forward-Euler leap to t + Delta t (pe_ls_project). */
 PE_API int pe_project(pe_ctx* ctx);
-/* Lifting (Section 3.3 + Appendix C): coarse state -> profiles -> quiet start. */
+/* Lifting (Section 3.3 + Appendix C): coarse state -> profiles -> quiet start; kinetic
+ * electrons are then placed in Boltzmann equilibrium with the lifted ions. */
 PE_API int pe_lift(pe_ctx* ctx);
 /* One projective macro step: lift (unless the particles are fresh), burst,
  * restrict, project. Advances time by Delta t. */
 PE_API int pe_step(pe_ctx* ctx);
-/* Plain (resolved) PIC: nsteps leapfrog steps with deposit + Newton each step,
- * sorting every sort_every steps. Advances time by nsteps dt. */
+/* Plain (resolved) PIC: nsteps leapfrog steps with deposit + Newton each step (kinetic
+ * electrons: both species, Poisson field), sorting every sort_every steps; with kinetic
+ * electrons and reset_every > 0 the electrons are reloaded in Boltzmann equilibrium with the
+ * ions every reset_every steps (Section 4.1's reset runs). Advances time by nsteps dt. */
 PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps);
 /* Coarse state of the current particles (restriction at integer time, no frame
  * shift) into host or device memory out[2][n_coarse]. */
@@ -526,7 +575,8 @@ PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches,
 
 /* =================================================================== batch
  * Ensemble of independent realisations advanced together (the same burst length, fine
- * and macro steps; any grid of at least 64 cells, any particle count, Haar wavelet).
+ * and macro steps; any grid of at least 64 cells, any particle count, Haar wavelet, moment
+ * coarse variables and Boltzmann electrons: other contexts make it PE_EINVAL).
  * Each fine step of the whole ensemble is one persistent particle launch over a shared
  * work list of particle chunks plus one launch of field-solve clusters (one per
  * realisation); from the second pe_batch_step on, the burst, restriction and

@@ -102,7 +102,7 @@ def _load():
                 "orc_poisson_periodic": (None, [i32, dbl, P, P, P]),
                 "orc_field_kinetic": (None, [i64, P, P, P, i64, P, P, P, i32, dbl, i32, P, P]),
                 "orc_pic_steps_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32,
-                                                 i32, i32, P]),
+                                                 i32, i32, i32, P]),
                 "orc_burst_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, dbl,
                                              i32, i32, i32, dbl, dbl, i32, P, P, P]),
                 "orc_boltzmann_electrons": (None, [i64, i32, P, dbl, u64, P, P, P, P]),
@@ -700,13 +700,16 @@ def field_kinetic(ions: State, electrons: State, ncell, dx, s_w):
     return phi, E
 
 
-def pic_steps_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, nsteps, s_w, vel_at_integer=True):
-    """nsteps two-species leapfrog steps in place; returns the last step's phi."""
+def pic_steps_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, nsteps, s_w, vel_at_integer=True,
+                      e_vel_at_integer=None):
+    """nsteps two-species leapfrog steps in place; returns the last step's phi. The electrons'
+    first kick is a half kick if e_vel_at_integer (default: vel_at_integer)."""
     phi = np.zeros(ncell)
+    ev = vel_at_integer if e_vel_at_integer is None else e_vel_at_integer
     _load().orc_pic_steps_kinetic(ions.n, _p(ions.cell), _p(ions.theta), _p(ions.v), _p(ions.w), electrons.n,
                                   _p(electrons.cell), _p(electrons.theta), _p(electrons.v), _p(electrons.w), ncell,
                                   float(dx), float(dt), float(qm_i), float(qm_e), int(nsteps), int(s_w),
-                                  int(vel_at_integer), _p(phi))
+                                  int(vel_at_integer), int(ev), _p(phi))
     return phi
 
 

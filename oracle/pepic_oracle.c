@@ -851,18 +851,21 @@ void orc_field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const do
     field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
 }
 
-/* Plain two-species PIC steps (Section 2.2 leapfrog for each species in the field of both). */
+/* Plain two-species PIC steps (Section 2.2 leapfrog for each species in the field of both).
+ * vel_at_integer / e_vel_at_integer: the ions' / electrons' stored velocities are at integer
+ * time (just loaded), so their first kick is a half kick. */
 void orc_pic_steps_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
                            int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
-                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer, double* phi)
+                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer,
+                           int32_t e_vel_at_integer, double* phi)
 {
     double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
-    double kick = vel_at_integer ? 0.5 : 1.0;
+    double kick_i = vel_at_integer ? 0.5 : 1.0, kick_e = e_vel_at_integer ? 0.5 : 1.0;
     for (int32_t s = 0; s < nsteps; ++s) {
         field_kinetic(ni, ci, ti, wi, ne, ce, te, we, ncell, dx, s_w, phi, E);
-        orc_push(ni, ci, ti, vi, E, ncell, dx, dt, qm_i, kick);
-        orc_push(ne, ce, te, ve, E, ncell, dx, dt, qm_e, kick);
-        kick = 1.0;
+        orc_push(ni, ci, ti, vi, E, ncell, dx, dt, qm_i, kick_i);
+        orc_push(ne, ce, te, ve, E, ncell, dx, dt, qm_e, kick_e);
+        kick_i = kick_e = 1.0;
     }
     free(E);
 }

@@ -237,7 +237,8 @@ void orc_field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const do
                        double* phi, double* E);
 void orc_pic_steps_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
                            int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
-                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer, double* phi);
+                           double qm_i, double qm_e, int32_t nsteps, int32_t s_w, int32_t vel_at_integer,
+                           int32_t e_vel_at_integer, double* phi);
 void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const double* wi, int64_t ne,
                        int32_t* ce, double* te, double* ve, const double* we, int32_t ncell, double dx, double dt,
                        double qm_i, double qm_e, int32_t K, double dT, int32_t s_w, int32_t vel_at_integer,

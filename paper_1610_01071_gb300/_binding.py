@@ -21,9 +21,11 @@ PE_POISSON = {"boltzmann": 0, "linearized": 1}
 PE_PROFILE_SINE = 0
 PE_PROFILE_SLAB = 1
 PE_BOUNDARY = {"periodic": 0, "absorbing": 1}
-PE_NBUF = 17
+PE_NBUF = 20
 BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
-           coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16)
+           coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16, electrons_a=17,
+           electrons_b=18, rho_e=19)
+PE_ELECTRONS = {"boltzmann": 0, "kinetic": 1}
 PE_COARSE = {"moments": 0, "phase_space": 1}
 PE_MLP_NBUF = 7
 MLP_BUF = dict(params=0, params_bf16=1, grads=2, adam_m=3, adam_v=4, norm=5, work=6)
@@ -52,7 +54,8 @@ class Config(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int32), ("sort_every", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double),
                 ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double),
-                ("ps_filter", ctypes.c_int32), ("boundary", ctypes.c_int32)]
+                ("ps_filter", ctypes.c_int32), ("boundary", ctypes.c_int32), ("electrons", ctypes.c_int32),
+                ("reset_every", ctypes.c_int32), ("qm_e", ctypes.c_double), ("v_th_e", ctypes.c_double)]
 
 
 class Layout(ctypes.Structure):
@@ -63,7 +66,8 @@ class Layout(ctypes.Structure):
 class Diag(ctypes.Structure):
     _fields_ = [("macro_steps", ctypes.c_int64), ("fine_steps", ctypes.c_int64), ("time", ctypes.c_double),
                 ("particle_bank", ctypes.c_int32), ("v_at_integer", ctypes.c_int32), ("s_w", ctypes.c_int32),
-                ("s_p", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_uint32)]
+                ("s_p", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_uint32),
+                ("electron_bank", ctypes.c_int32), ("e_v_at_integer", ctypes.c_int32)]
 
 
 class Moments(ctypes.Structure):
@@ -102,6 +106,8 @@ SIGNATURES = {
     "pe_deposit": (ctypes.c_int, [P, P, P, i64, i32, i32, P, P, P]),
     "pe_field": (ctypes.c_int, [P, i32, f64, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_field_ex": (ctypes.c_int, [P, i32, f64, i32, i32, i32, f64, i32, P, P, P, P, P, P]),
+    "pe_field_kinetic": (ctypes.c_int, [P, P, i32, f64, i32, P, P, P, P]),
+    "pe_boltzmann_profile": (ctypes.c_int, [P, i32, P, P, P]),
     "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
     "pe_push_ex": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, i32, P, ctypes.POINTER(SampleArgs),
                                   P, P]),
@@ -233,6 +239,26 @@ def field(rho, ncell, dx, s_w, phi, mode="boltzmann", tol=1e-11, maxit=50, statu
                                  float(tol), int(maxit), _ptr(phi), _ptr(E), _ptr(Ef), _ptr(diag), _ptr(status),
                                  _stream(stream)), "pe_field_ex")
     return E, Ef, diag
+
+
+def field_kinetic(rho_i, rho_e, ncell, dx, s_w, phi=None, stream=None):
+    """Periodic Poisson field of the net charge of ions and electrons (both fixed-point
+    deposits with positive weights); returns (phi, E, Ef)."""
+    dev = rho_i.device
+    phi = phi if phi is not None else torch.empty(ncell, dtype=torch.float64, device=dev)
+    E = torch.empty(ncell, dtype=torch.float64, device=dev)
+    Ef = torch.empty(ncell, dtype=torch.float32, device=dev)
+    check(load().pe_field_kinetic(_ptr(rho_i), _ptr(rho_e), ncell, float(dx), int(s_w), _ptr(phi), _ptr(E), _ptr(Ef),
+                                  _stream(stream)), "pe_field_kinetic")
+    return phi, E, Ef
+
+
+def boltzmann_profile(phi, ncell, stream=None):
+    """Boltzmann electron profile exp(phi) (and zero mean velocity) as float32 [2, ncell]."""
+    prof = torch.empty(2 * ncell, dtype=torch.float32, device=phi.device)
+    check(load().pe_boltzmann_profile(_ptr(phi), ncell, _ptr(prof), _ptr(prof[ncell:]), _stream(stream)),
+          "pe_boltzmann_profile")
+    return prof.view(2, ncell)
 
 
 def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0,
@@ -448,15 +474,20 @@ def ps_quiet_start_equal(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w,
 
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
-                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic") -> Config:
+                v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic",
+                electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0) -> Config:
     """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
     masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
     filter of the projected phase-space slope (bit 0 along v, bit 1 along x); boundary:
-    "periodic" or "absorbing" (walls at nodes 0 and ncell-1, Section 4.2)."""
+    "periodic" or "absorbing" (walls at nodes 0 and ncell-1, Section 4.2); electrons:
+    "boltzmann" (fluid) or "kinetic" (particles of charge-to-mass ratio qm_e, default -1800,
+    thermal speed v_th_e, default sqrt(-qm_e); plain PIC reloads them in Boltzmann equilibrium
+    every reset_every steps if > 0)."""
     return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
                   int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
-                  PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter), PE_BOUNDARY[boundary])
+                  PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter), PE_BOUNDARY[boundary],
+                  PE_ELECTRONS[electrons], int(reset_every), float(qm_e), float(v_th_e))
 
 
 def layout(cfg: Config) -> Layout:
@@ -593,13 +624,21 @@ class Context:
         t = self.arena[off:off + nbytes].view(dtype)
         return t if count is None else t[:count]
 
-    def particles(self, bank=None):
-        """(cell, theta, v, w) views of the current (or given) particle bank."""
-        if bank is None:
-            bank = self.diagnostics().particle_bank
+    def particles(self, bank=None, species="ions"):
+        """(cell, theta, v, w) views of the current (or given) particle bank of the ions, or
+        of the kinetic electrons (species="electrons")."""
+        d = self.diagnostics() if bank is None else None
+        if species == "electrons":
+            if bank is None:
+                bank = d.electron_bank
+            first = BUF["electrons_a"]
+        else:
+            if bank is None:
+                bank = d.particle_bank
+            first = BUF["particles_a"]
         N = self.cfg.nparticles
         stride = ((4 * N + 255) // 256) * 256
-        off = self._pad + self.lay.offset[BUF["particles_a"] + bank]
+        off = self._pad + self.lay.offset[first + bank]
         seg = [self.arena[off + k * stride: off + k * stride + 4 * N] for k in range(4)]
         return (seg[0].view(torch.int32), seg[1].view(torch.float32), seg[2].view(torch.float32),
                 seg[3].view(torch.float32))

@@ -143,6 +143,13 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.ps_filter < 0 || c.ps_filter > 3) return PE_EINVAL;
     if (c.boundary != PE_BOUNDARY_PERIODIC && c.boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
     const bool walls = c.boundary == PE_BOUNDARY_ABSORBING;
+    if (c.electrons != PE_ELECTRONS_BOLTZMANN && c.electrons != PE_ELECTRONS_KINETIC) return PE_EINVAL;
+    const bool kin = c.electrons == PE_ELECTRONS_KINETIC;
+    // kinetic electrons: periodic grids, the exponential Boltzmann relation for the lifting,
+    // a negative charge-to-mass ratio (0 selects the default)
+    if (kin && (walls || c.poisson != PE_POISSON_BOLTZMANN || !(c.qm_e <= 0.0) || !(c.v_th_e >= 0.0) ||
+                c.reset_every < 0))
+        return PE_EINVAL;
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
@@ -169,6 +176,9 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
                                          align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
                                    : 256) +
                                 (walls ? align256(PE_PS_EQ_SCRATCH_BYTES(nc)) : 0);
+    out->bytes[PE_BUF_ELECTRONS_A] = kin ? bank : 0;
+    out->bytes[PE_BUF_ELECTRONS_B] = kin ? bank : 0;
+    out->bytes[PE_BUF_RHO_E] = kin ? 8 * nc : 0;
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -215,6 +225,19 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
         x->w[b] = (float*)(base + 3 * align256(4 * N));
     }
     x->rho = (int64_t*)(x->arena + lay.offset[PE_BUF_RHO]);
+    x->kinetic = cfg->electrons == PE_ELECTRONS_KINETIC;
+    x->qm_e = cfg->qm_e != 0.0 ? cfg->qm_e : -1800.0;
+    x->v_th_e = cfg->v_th_e > 0.0 ? cfg->v_th_e : sqrt(-x->qm_e);
+    if (x->kinetic) {
+        for (int b = 0; b < 2; ++b) {
+            char* base = x->arena + lay.offset[PE_BUF_ELECTRONS_A + b];
+            x->ecell[b] = (int32_t*)base;
+            x->etheta[b] = (float*)(base + align256(4 * N));
+            x->ev[b] = (float*)(base + 2 * align256(4 * N));
+            x->ew[b] = (float*)(base + 3 * align256(4 * N));
+        }
+        x->rho_e = (int64_t*)(x->arena + lay.offset[PE_BUF_RHO_E]);
+    }
     x->phi = (double*)(x->arena + lay.offset[PE_BUF_PHI]);
     x->E = (double*)(x->arena + lay.offset[PE_BUF_E]);
     x->Ef = (float*)(x->arena + lay.offset[PE_BUF_EF]);
@@ -333,6 +356,10 @@ extern "C" PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* pus
 static int field_solve(pe_ctx* x, int step = 0)
 {
     const pe_config& c = x->cfg;
+    if (x->kinetic)  // Section 4.1's two-species bursts: Poisson for the net charge
+        return timed(x, 1, [&] {
+            return pe_field_kinetic(x->rho, x->rho_e, c.ncell, x->dx, x->s_w, x->phi, x->E, x->Ef, x->stream);
+        });
     const int extrap = step && x->phi_hist;
     double* prev = step ? x->phi + c.ncell : nullptr;
     PE_TRY(timed(x, 1, [&] {
@@ -348,7 +375,49 @@ static int deposit_current(pe_ctx* x)
     const int b = x->bank;
     PE_TRY(pe_deposit(x->cell[b], x->theta[b], x->w[b], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho, x->status,
                       x->stream));
+    if (x->kinetic) {
+        const int e = x->ebank;
+        PE_TRY(pe_deposit(x->ecell[e], x->etheta[e], x->ew[e], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho_e,
+                          x->status, x->stream));
+    }
     x->rho_valid = 1;
+    return PE_OK;
+}
+
+// Electrons in Boltzmann equilibrium with the current ion deposit (Eq. electronpassive), as the
+// lifting of Section 3.3 places them and as Section 4.1's reset runs reload them: the
+// Poisson-Boltzmann potential of the ion density, then a quiet start on exp(phi) with the
+// electrons' thermal speed and no drift. Leaves their deposit in rho_e.
+static uint64_t electron_seed(uint64_t s) { return s ^ 0xD1B54A32D192ED03ULL; }
+
+static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed)
+{
+    const pe_config& c = x->cfg;
+    PE_TRY(field_solve_history(x->rho, c.ncell, x->dx, x->s_w, PE_POISSON_BOLTZMANN, PE_BOUNDARY_PERIODIC,
+                               c.newton_tol, c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, nullptr, 0,
+                               x->stream));
+    PE_TRY(pe_boltzmann_profile(x->phi, c.ncell, x->prof, x->prof + c.ncell, x->stream));
+    const int e = x->ebank;
+    PE_TRY(timed(x, 0, [&] {
+        return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof,
+                              x->prof + c.ncell, (float)x->v_th_e, seed, x->s_w, x->rho_e, x->status, x->stream);
+    }));
+    x->e_v_at_integer = 1;
+    return PE_OK;
+}
+
+// Electron push of a fine step (kinetic electrons), in the field Ef of the ions' push.
+static int push_electrons(pe_ctx* x)
+{
+    const pe_config& c = x->cfg;
+    const int e = x->ebank;
+    const float kick = x->e_v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(timed(x, 0, [&] {
+        return pe_push_ex(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, c.ncell,
+                          (float)(c.dt / x->dx), (float)(x->qm_e * c.dt), kick, x->s_w, c.boundary, x->rho_e, nullptr,
+                          x->status, x->stream);
+    }));
+    x->e_v_at_integer = 0;
     return PE_OK;
 }
 
@@ -471,6 +540,10 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     x->fine_steps = 0;
     x->time = 0.0;
     PE_TRY(quiet_start_from_profile(x, c.seed, 1.0f));
+    if (x->kinetic) {
+        x->ebank = 0;
+        PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed)));
+    }
     if (x->ps) return measure_phase(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
 }
@@ -500,6 +573,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                               kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream);
         }));
+        if (x->kinetic) PE_TRY(push_electrons(x));
         PE_TRY(field_solve(x, 1));
         kick = 1.0f;
         x->v_at_integer = 0;
@@ -574,10 +648,12 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         x->v_at_integer = 1;
         x->fresh = 1;
         x->phi_hist = 0;
-        return PE_OK;
+    } else {
+        PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
+        PE_TRY(quiet_start_from_profile(x, lift_seed(x), 2.0f));  // refined restriction: wall nodes hold deposits
     }
-    PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
-    return quiet_start_from_profile(x, lift_seed(x), 2.0f);  // refined restriction: wall nodes hold deposits
+    if (x->kinetic) PE_TRY(load_boltzmann_electrons(x, electron_seed(lift_seed(x))));
+    return PE_OK;
 }
 
 extern "C" PE_API int pe_step(pe_ctx* ctx)
@@ -601,8 +677,16 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
             PE_TRY(pe_sort(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->cell[o], x->theta[o],
                            x->v[o], x->w[o], x->sort, x->status, x->stream));
             x->bank = o;
+            if (x->kinetic) {
+                const int e = x->ebank, eo = 1 - e;
+                PE_TRY(pe_sort(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->ecell[eo],
+                               x->etheta[eo], x->ev[eo], x->ew[eo], x->sort, x->status, x->stream));
+                x->ebank = eo;
+            }
         }
         if (!x->rho_valid) PE_TRY(deposit_current(x));
+        if (x->kinetic && c.reset_every > 0 && (x->fine_steps % c.reset_every) == 0 && !x->fresh)
+            PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed + 0x9E3779B97F4A7C15ULL * (uint64_t)x->fine_steps)));
         PE_TRY(field_solve(x, 1));
         const int b = x->bank;
         const float kick = x->v_at_integer ? 0.5f : 1.0f;
@@ -610,6 +694,7 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                               kick, x->s_w, c.boundary, x->rho, nullptr, x->status, x->stream);
         }));
+        if (x->kinetic) PE_TRY(push_electrons(x));
         x->v_at_integer = 0;
         x->rho_valid = 1;
         x->fresh = 0;
@@ -699,6 +784,8 @@ extern "C" PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out)
     out->v_at_integer = ctx->v_at_integer;
     out->s_w = ctx->s_w;
     out->s_p = ctx->s_p;
+    out->electron_bank = ctx->ebank;
+    out->e_v_at_integer = ctx->e_v_at_integer;
     int32_t d[2] = {0, 0};
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
     if (cudaMemcpy(d, ctx->diag, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;

@@ -48,6 +48,16 @@ struct pe_ctx {
     float* v[2];
     float* w[2];
     int64_t* rho;
+    // kinetic electrons (PE_ELECTRONS_KINETIC)
+    int kinetic;
+    double qm_e, v_th_e;
+    int ebank;           // which electron bank is current
+    int e_v_at_integer;  // stored electron v is at integer time
+    int32_t* ecell[2];
+    float* etheta[2];
+    float* ev[2];
+    float* ew[2];
+    int64_t* rho_e;
     double* phi;
     double* E;
     float* Ef;

@@ -539,6 +539,152 @@ int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, in
 }
 }  // namespace pe
 
+// ---------------------------------------------------------------------------------
+// Kinetic electrons (Section 4.1's two-species bursts): periodic Poisson equation for the
+// net charge, one block. Thread t owns the m = ncell / 1024 (at least 1) consecutive nodes
+// j0 = t m ...; the sums run lane by lane, then warp by warp, in a fixed order.
+
+constexpr int kPoissonThreads = 1024;
+constexpr int kPoissonMaxPer = kFullGridMax / kPoissonThreads;
+
+// Exclusive prefix sum over the block of one value per thread, and the block total.
+// wsum: 32 shared slots. Every thread of the block calls it.
+template <typename V>
+__device__ __forceinline__ V block_exclusive_scan(V x, V* total, V* wsum)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    V incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        V s = lane < nw ? wsum[lane] : V(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const V y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const V base = w > 0 ? wsum[w - 1] : V(0);
+    *total = wsum[nw - 1];
+    __syncthreads();  // wsum is reused by the next call
+    return base + incl - x;
+}
+
+__global__ void __launch_bounds__(kPoissonThreads) k_poisson_periodic(const long long* rho_i, const long long* rho_e,
+                                                                      int n, double dx, double nscale, double* phi,
+                                                                      double* E, float* Ef)
+{
+    __shared__ double wd[32];
+    __shared__ double last_face[kPoissonThreads];
+    const int t = threadIdx.x;
+    const int m = n >= (int)blockDim.x ? n / (int)blockDim.x : 1;
+    const int nt = n / m;  // threads that own nodes
+    const int j0 = t * m;
+    const bool act = t < nt;
+    // net charge per node: the int64 difference of the deposits is exact; the sums are FP64
+    // (a fixed-point prefix sum of a strongly non-neutral state would leave the int64 range)
+    double S[kPoissonMaxPer];
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPoissonMaxPer; ++k) {
+        if (k < m) {
+            const double q = act ? (double)(__ldg(rho_i + j0 + k) - __ldg(rho_e + j0 + k)) : 0.0;
+            s += q;
+            S[k] = s;
+        }
+    }
+    double tot;
+    const double off = block_exclusive_scan(s, &tot, wd);
+    // face fields before the gauge: F_{j+1/2} - F_{-1/2} = dx nscale (S_j - (j + 1) <S>)
+    const double mean = tot / n;
+    const double c = dx * nscale;
+    double F[kPoissonMaxPer];
+    double fs = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPoissonMaxPer; ++k) {
+        if (k < m) {
+            F[k] = act ? c * ((off + S[k]) - (double)(j0 + k + 1) * mean) : 0.0;
+            fs += F[k];
+        }
+    }
+    double ftot;
+    (void)block_exclusive_scan(fs, &ftot, wd);
+    const double gauge = ftot / n;  // the faces of a periodic phi sum to zero
+    double ps = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPoissonMaxPer; ++k) {
+        if (k < m) {
+            F[k] = act ? F[k] - gauge : 0.0;
+            ps += F[k];
+        }
+    }
+    // phi_0 = 0, phi_{j+1} = phi_j - dx F_{j+1/2}
+    double ptot;
+    const double poff = block_exclusive_scan(ps, &ptot, wd);
+    double P[kPoissonMaxPer];
+    double acc = -dx * poff, psum = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPoissonMaxPer; ++k) {
+        if (k < m) {
+            P[k] = acc;
+            psum += act ? acc : 0.0;
+            acc -= dx * F[k];
+        }
+    }
+    double pt;
+    (void)block_exclusive_scan(psum, &pt, wd);
+    const double pmean = pt / n;
+    if (act) last_face[t] = F[m - 1];
+    __syncthreads();
+    const double Fprev = act ? last_face[(t - 1 + nt) % nt] : 0.0;  // F_{j0-1/2}
+#pragma unroll
+    for (int k = 0; k < kPoissonMaxPer; ++k) {
+        if (k < m && act) {
+            const int j = j0 + k;
+            const double e = 0.5 * (F[k] + (k ? F[k - 1] : Fprev));
+            E[j] = e;
+            Ef[j] = (float)e;
+            phi[j] = P[k] - pmean;
+        }
+    }
+}
+
+__global__ void k_boltzmann_profile(const double* phi, int n, float* nprof, float* uprof)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        nprof[j] = (float)exp(phi[j]);
+        uprof[j] = 0.0f;
+    }
+}
+
+extern "C" PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_e, int32_t ncell, double dx,
+                                       int32_t s_w, double* phi, double* E, float* Ef, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || ncell > kFullGridMax || !rho_i || !rho_e || !phi || !E || !Ef ||
+        !(dx > 0.0))
+        return PE_EINVAL;
+    k_poisson_periodic<<<1, kPoissonThreads, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const long long*>(rho_i), reinterpret_cast<const long long*>(rho_e), ncell, dx,
+        ldexp(1.0, -(s_w + 24)), phi, E, Ef);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_boltzmann_profile(const double* phi, int32_t ncell, float* n_prof, float* u_prof,
+                                           void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || ncell > kFullGridMax || !phi || !n_prof || !u_prof) return PE_EINVAL;
+    k_boltzmann_profile<<<(ncell + 255) / 256, 256, 0, (cudaStream_t)stream>>>(phi, ncell, n_prof, u_prof);
+    return launch_status();
+}
+
 extern "C" PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t s_w, int32_t mode,
                                   int32_t boundary, double tol, int32_t maxit, double* phi, double* E, float* Ef,
                                   int32_t* diag, uint32_t* status, void* stream)

@@ -64,3 +64,21 @@ def test_layout_is_host_only_and_validates(lib):
     with pytest.raises(b.PepicError):
         b.layout(bad)
     assert lib.pe_strerror is not None
+
+
+def test_kinetic_electron_layout_and_checks(lib):
+    from paper_1610_01071_gb300 import _binding as b
+
+    base = (64, 16, 4, 64 * 16, 32.0, 0.005, 0.1)
+    for bad in (dict(boundary="absorbing"),   # kinetic electrons: periodic grids only
+                dict(poisson="linearized"),   # the lifting's Boltzmann relation is exponential
+                dict(qm_e=5.0), dict(v_th_e=-1.0), dict(reset_every=-1)):
+        with pytest.raises(b.PepicError):
+            b.layout(b.make_config(*base, electrons="kinetic", **bad))
+    lay = b.layout(b.make_config(*base, electrons="kinetic"))
+    bank = 4 * ((4 * 64 * 16 + 255) // 256) * 256
+    assert lay.bytes[b.BUF["electrons_a"]] == bank and lay.bytes[b.BUF["electrons_b"]] == bank
+    assert lay.bytes[b.BUF["rho_e"]] == 8 * 64
+    lay0 = b.layout(b.make_config(*base))
+    assert lay0.bytes[b.BUF["electrons_a"]] == 0 and lay0.bytes[b.BUF["rho_e"]] == 0
+    assert lay.total_bytes >= lay0.total_bytes + 2 * bank

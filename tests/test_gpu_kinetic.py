@@ -1,0 +1,197 @@
+"""GPU parity of the kinetic-electron path (Section 4.1: both species are particles in the
+PIC bursts, q_e/m_e = -1800; the field is the periodic Poisson equation for the net charge)
+against the oracle: the Poisson kernel, the Boltzmann electrons of a load, plain two-species
+PIC with and without the periodic electron reset, and a projective macro step.
+
+Tolerances: the Poisson solve agrees to FP64 summation-order rounding (1e-10 of max |E|);
+particle states after a few FP32 steps to 1e-4 of a cell and of the thermal speed; coarse
+states to 1e-4 of their largest entry (the fixed-point samples against the FP64 oracle)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import paper_1610_01071_gb300 as pe
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+QM_E = -1800.0
+V_TH_E = float(np.float32(np.sqrt(-QM_E)))
+MASK64 = 0xFFFFFFFFFFFFFFFF
+
+KIN = dict(ncell=64, L=18.0, N=64 * 64, dt=0.25 / np.sqrt(-QM_E), K=6, M=5, n_coarse=16, v_th=0.22, amp=0.2)
+
+
+def electron_seed(s):
+    return (s & MASK64) ^ 0xD1B54A32D192ED03
+
+
+@pytest.mark.parametrize("ncell", [8, 64, 1024, 8192])
+@pytest.mark.parametrize("neutral", [True, False])
+def test_field_kinetic_matches_oracle(ncell, neutral):
+    rng = np.random.default_rng(ncell + neutral)
+    s_w = 30
+    base = (1.0 + 0.3 * np.cos(2 * np.pi * np.arange(ncell) / ncell)) * 2.0 ** (s_w + 24 - 6)
+    rho_i = np.round(base * (1 + 0.05 * rng.normal(size=ncell))).astype(np.int64)
+    rho_e = np.round(base * (1 + 0.05 * rng.normal(size=ncell))).astype(np.int64) if neutral else np.zeros(
+        ncell, np.int64)
+    dx = 0.37
+    phi, E, Ef = pe.field_kinetic(torch.from_numpy(rho_i).to(DEV), torch.from_numpy(rho_e).to(DEV), ncell, dx, s_w)
+    torch.cuda.synchronize()
+    r = (rho_i - rho_e).astype(np.float64) * 2.0 ** -(s_w + 24)
+    phi_o, E_o = orc.poisson_periodic(r, dx)
+    E, phi = E.cpu().numpy(), phi.cpu().numpy()
+    assert np.abs(E - E_o).max() <= 1e-10 * np.abs(E_o).max()
+    assert np.abs(phi - phi_o).max() <= 1e-10 * np.abs(phi_o).max()
+    assert np.array_equal(Ef.cpu().numpy(), E.astype(np.float32))
+
+
+def test_field_kinetic_rejects_bad_sizes():
+    z = torch.zeros(12, dtype=torch.int64, device=DEV)
+    with pytest.raises(pe.PepicError):
+        pe.field_kinetic(z, z, 12, 0.5, 30)
+    z = torch.zeros(16384, dtype=torch.int64, device=DEV)
+    with pytest.raises(pe.PepicError):
+        pe.field_kinetic(z, z, 16384, 0.5, 30)
+
+
+def test_boltzmann_profile_is_exp_phi():
+    phi = torch.linspace(-3.0, 2.0, 512, dtype=torch.float64, device=DEV)
+    prof = pe.boltzmann_profile(phi, 512).cpu().numpy()
+    want = np.exp(phi.cpu().numpy())
+    assert np.allclose(prof[0], want, rtol=2e-7, atol=0)
+    assert not prof[1].any()
+
+
+def make_kinetic(cfg, seed, **kw):
+    dT = cfg["M"] * cfg["K"] * cfg["dt"]
+    c = pe.make_config(cfg["ncell"], cfg["n_coarse"], cfg["K"], cfg["N"], cfg["L"], cfg["dt"], dT, qm=1.0,
+                       v_th=cfg["v_th"], seed=seed, newton_tol=1e-11, electrons="kinetic", **kw)
+    return pe.Context(c, device=DEV)
+
+
+def oracle_ions(cfg, seed):
+    nprof, uprof = orc.sine_profile(cfg["ncell"], cfg["L"], cfg["amp"])
+    return orc.quiet_start(cfg["N"], cfg["ncell"], nprof.astype(np.float32), uprof.astype(np.float32),
+                           float(np.float32(cfg["v_th"])), seed)
+
+
+def oracle_electrons(cfg, ions, s_w, seed, phi0=None):
+    # the loading of the library: Poisson-Boltzmann potential of the ion deposit, then the
+    # quiet start on the FP32 profile exp(phi)
+    ncell = cfg["ncell"]
+    dx = cfg["L"] / ncell
+    dens = orc.deposit_fx(ions.cell, ions.theta, ions.w, ncell, s_w) * 2.0 ** -(s_w + 24)
+    phi = orc.newton_pb(dens, dx, phi0=np.zeros(ncell) if phi0 is None else phi0, tol=1e-11)[0]
+    prof = np.exp(phi).astype(np.float32)
+    return orc.quiet_start(cfg["N"], ncell, prof, np.zeros(ncell, np.float32), V_TH_E, seed)
+
+
+def state_of(ctx, species):
+    c, t, v, w = (a.cpu().numpy() for a in ctx.particles(species=species))
+    return orc.State(c, t, v, w)
+
+
+def assert_states_close(got, want, ncell, v_scale, what):
+    d = (got.cell + got.theta.astype(np.float64)) - (want.cell + want.theta)
+    d = (d + ncell / 2) % ncell - ncell / 2  # periodic distance in cells
+    assert np.abs(d).max() < 1e-4, f"{what}: position {np.abs(d).max()} cells"
+    assert np.abs(got.v - want.v).max() < 1e-4 * v_scale, f"{what}: velocity {np.abs(got.v - want.v).max()}"
+    assert np.allclose(got.w, want.w, rtol=1e-6, atol=0), what
+
+
+def test_load_places_boltzmann_electrons_like_the_oracle():
+    cfg = KIN
+    ctx = make_kinetic(cfg, seed=3)
+    ctx.load_initial(cfg["amp"])
+    assert ctx.sync_status() == 0
+    d = ctx.diagnostics()
+    ions = oracle_ions(cfg, 3)
+    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(3))
+    gi, ge = state_of(ctx, "ions"), state_of(ctx, "electrons")
+    assert np.array_equal(gi.cell, ions.cell) and np.array_equal(ge.cell, elec.cell)
+    assert np.array_equal(ge.theta, elec.theta.astype(np.float32))
+    assert_states_close(ge, elec, cfg["ncell"], V_TH_E, "electrons")
+    assert d.e_v_at_integer == 1
+    # the loaded electrons balance the ions' charge (fixed point: to the rounding of each weight)
+    rho_i = ctx.view("rho", torch.int64, cfg["ncell"]).cpu().numpy()
+    rho_e = ctx.view("rho_e", torch.int64, cfg["ncell"]).cpu().numpy()
+    total = float(rho_i.sum(dtype=object))
+    assert abs(float(rho_e.sum(dtype=object)) - total) <= 1e-6 * total
+
+
+@pytest.mark.parametrize("reset_every", [0, 4])
+def test_plain_two_species_pic_matches_oracle(reset_every):
+    cfg = KIN
+    nsteps = 9
+    seed = 5
+    ctx = make_kinetic(cfg, seed=seed, reset_every=reset_every)
+    ctx.load_initial(cfg["amp"])
+    ctx.pic_steps(nsteps)
+    assert ctx.sync_status() == 0
+    d = ctx.diagnostics()
+    s_w = d.s_w
+    ncell, dx = cfg["ncell"], cfg["L"] / cfg["ncell"]
+    ions = oracle_ions(cfg, seed)
+    elec = oracle_electrons(cfg, ions, s_w, electron_seed(seed))
+    done, v_int, e_int = 0, True, True
+    while done < nsteps:
+        if reset_every and done > 0 and done % reset_every == 0:
+            # Section 4.1's reset: electrons reloaded in equilibrium with the current ions
+            elec = oracle_electrons(cfg, ions, s_w, electron_seed(seed + 0x9E3779B97F4A7C15 * done))
+            e_int = True
+        n = min(nsteps - done, reset_every - done % reset_every if reset_every else nsteps)
+        orc.pic_steps_kinetic(ions, elec, ncell, dx, cfg["dt"], 1.0, QM_E, n, s_w, vel_at_integer=v_int,
+                              e_vel_at_integer=e_int)
+        done += n
+        v_int = e_int = False
+    assert_states_close(state_of(ctx, "ions"), ions, ncell, cfg["v_th"], "ions")
+    assert_states_close(state_of(ctx, "electrons"), elec, ncell, V_TH_E, "electrons")
+
+
+def test_kinetic_macro_step_matches_oracle():
+    cfg = KIN
+    seed = 7
+    ctx = make_kinetic(cfg, seed=seed)
+    ctx.load_initial(cfg["amp"])
+    ctx.step()
+    assert ctx.sync_status() == 0
+    got = ctx.get_coarse().cpu().numpy()
+    d = ctx.diagnostics()
+    ncell, nc, K = cfg["ncell"], cfg["n_coarse"], cfg["K"]
+    dx = cfg["L"] / ncell
+    dT = cfg["M"] * K * cfg["dt"]
+    ions = oracle_ions(cfg, seed)
+    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(seed))
+    samples, _ = orc.burst_kinetic(ions, elec, ncell, dx, cfg["dt"], 1.0, QM_E, K, dT, d.s_w)
+    cs = np.stack([np.concatenate([orc.coarsen(samples[p, 0], nc), orc.coarsen(samples[p, 1], nc)])
+                   for p in range(K + 1)])
+    coarse, _ = orc.ls_project(cs, cfg["dt"], dT)
+    want = coarse.reshape(2, nc)
+    assert np.max(np.abs(got - want)) < 1e-4 * np.max(np.abs(want))
+    # after the burst both species moved K steps: compare the particle states too
+    assert_states_close(state_of(ctx, "ions"), ions, ncell, cfg["v_th"], "ions")
+    assert_states_close(state_of(ctx, "electrons"), elec, ncell, V_TH_E, "electrons")
+
+
+def test_kinetic_lift_reloads_boltzmann_electrons():
+    cfg = KIN
+    ctx = make_kinetic(cfg, seed=11)
+    ctx.load_initial(cfg["amp"])
+    ctx.step()
+    ctx.lift()
+    assert ctx.sync_status() == 0
+    d = ctx.diagnostics()
+    assert d.e_v_at_integer == 1 and d.v_at_integer == 1
+    gi = state_of(ctx, "ions")
+    # electrons in equilibrium with the lifted ions (the GPU's own lifted ions as input)
+    lift_seed = (11 + 0x632BE59BD9B4E019 * (d.macro_steps + 1)) & MASK64
+    elec = oracle_electrons(cfg, gi, d.s_w, electron_seed(lift_seed))
+    assert_states_close(state_of(ctx, "electrons"), elec, cfg["ncell"], V_TH_E, "electrons")
+
+
+def test_kinetic_contexts_are_not_batched():
+    c = pe.make_config(64, 16, 4, 64 * 16, 32.0, 0.005, 0.1, electrons="kinetic")
+    ctx = pe.Context(c, device=DEV)
+    with pytest.raises(pe.PepicError):  # the batched ensemble runs Boltzmann electrons only
+        pe.Batch([ctx])
