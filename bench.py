@@ -308,6 +308,7 @@ def run_gpu(args):
         acc, want, checks = run_accuracy(dev, cfg, pb) if not args.no_accuracy else (None, None, None)
         sur = run_surrogate(dev, cfg, pb, want, checks) if (acc is not None and not args.no_surrogate) else None
         slab = run_slab(dev, pb) if not args.no_slab else None
+        kin = run_kinetic(dev, pb) if not args.no_kinetic else None
         # ---------------- ensemble of 64 realisations of log-uniform sizes (pe_batch)
         ens = run_ensemble(dev, max(args.steps // 2, 2), 3, rank) if not args.no_ensemble else None
     clocks = sampler.stop()
@@ -355,6 +356,8 @@ def run_gpu(args):
         line["surrogate"] = sur
     if slab is not None:
         line["slab"] = slab
+    if kin is not None:
+        line["kinetic_electrons"] = kin
     if ens is not None:
         t_ens = max_over_ranks(ens["seconds"])
         line["ensemble"] = {"workload": "64 realisations, 2^9..2^13 cells, 2^18..2^22 ions (log-uniform), K=20, M=10, "
@@ -420,14 +423,60 @@ def run_kernel_slab(args):
     return 0
 
 
+def run_kernel_kinetic(args):
+    """Kinetic-electron workload (iaw_kinetic) for profiling: `warmup` then `steps` phase-space
+    projective macro steps, then 150 plain two-species PIC steps, each timed with CUDA events;
+    the push and field-solve launch times come from the context's own event pairs."""
+    import torch
+
+    from paper_1610_01071_gb300 import _binding as pb
+    from paper_1610_01071_gb300 import _build, inputs
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    w = inputs.workload("iaw_kinetic")
+    c = pb.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"], v_th=w["v_th"],
+                       seed=11, sort_every=20, newton_tol=1e-10, coarse="phase_space", n_v=w["n_v"],
+                       v_max=w["v_max"], ps_filter=3, electrons="kinetic", qm_e=w["qm_e"])
+    ctx = pb.Context(c, device=dev)
+    ctx.load_initial(w["amplitude"])
+    for _ in range(args.warmup):
+        ctx.step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    ctx.profile(True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms_macro = e0.elapsed_time(e1) / args.steps
+    e0.record()
+    ctx.pic_steps(150)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "kinetic", "ions": w["N"], "electrons": w["N"], "ncell": w["ncell"],
+                      "ms_per_macro_step": ms_macro, "plain_pic_us_per_step": 1e3 * e0.elapsed_time(e1) / 150,
+                      "particle_pass_us": 1e3 * prof["push_ms"] / max(prof["push_launches"], 1),
+                      "particle_passes": prof["push_launches"],
+                      "field_us": 1e3 * prof["field_ms"] / max(prof["field_launches"], 1),
+                      "status": ctx.sync_status()}), flush=True)
+    return 0
+
+
 def run_kernel(args):
     """Times one hot-path kernel alone on the workload's particle state (for profiling):
     ``--kernel push_sample|push|deposit|sample|field|quiet_start|push_sample_ps|ps_tables|
-    ps_quiet_start|push_sample_ps_slab``."""
+    ps_quiet_start|push_sample_ps_slab|kinetic``."""
     import torch
 
     if args.kernel == "push_sample_ps_slab":
         return run_kernel_slab(args)
+    if args.kernel == "kinetic":
+        return run_kernel_kinetic(args)
 
     from paper_1610_01071_gb300 import _binding as pb
     from paper_1610_01071_gb300 import _build
@@ -685,6 +734,77 @@ def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 2
             "charge_left_plain_pic": q_ref / q0, "status_plain_pic": ref.sync_status(), "projective": runs}
 
 
+def run_kinetic(dev, pb, per_reset=150):
+    """Kinetic electrons (Section 4.1: both species as particles, q_e/m_e = -1800, dt resolving
+    the electron plasma period): phase-space projective integration against plain two-species
+    GPU PIC to the same end time, and against plain PIC whose electrons are reloaded in
+    Boltzmann equilibrium with the ions every 150 steps (the paper's reset runs): time to
+    solution and the coarse-density error (Section 4.1.1) at a third, two thirds and the end."""
+    import numpy as np
+    import torch
+
+    from paper_1610_01071_gb300 import inputs
+
+    w = inputs.workload("iaw_kinetic")
+    steps, per = w["macro_steps"], int(round(w["dT"] / w["dt"]))
+    T_end = steps * w["dT"]
+    checks = [steps // 3, 2 * steps // 3, steps]
+
+    def make(coarse="phase_space", reset=0):
+        return pb.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"],
+                              v_th=w["v_th"], seed=11, sort_every=20, newton_tol=1e-10, coarse=coarse, n_v=w["n_v"],
+                              v_max=w["v_max"], ps_filter=3, electrons="kinetic", qm_e=w["qm_e"],
+                              reset_every=reset)
+
+    wants, plain = {}, {}
+    for reset in (0, per_reset):
+        ref = pb.Context(make("moments", reset), device=dev)
+        ref.load_initial(w["amplitude"])
+        want, done = {}, 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for m in checks:
+            ref.pic_steps((m - done) * per)
+            done = m
+            want[m] = ref.measure()[0].clone()
+        torch.cuda.synchronize(dev)
+        plain[reset] = {"seconds": time.perf_counter() - t0, "status": ref.sync_status()}
+        wants[reset] = want
+    t_plain = plain[0]["seconds"]
+    ctx = pb.Context(make(), device=dev)
+    ctx.load_initial(w["amplitude"])
+    b = int(np.log2(w["ncell"] // w["n_coarse"]))
+    scale = 2.0 ** (-(np.log2(w["ncell"]) + b) / 2)  # bin mass -> Haar density coefficient
+    got, wall, done = {}, 0.0, 0
+    for m in checks:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(m - done):
+            ctx.step()
+        done = m
+        torch.cuda.synchronize(dev)
+        wall += time.perf_counter() - t0
+        got[m] = (ctx.get_coarse().sum(1) * scale).cpu().numpy()
+    key = {m: str(round(m * w["dT"])) for m in checks}
+    eps_plain = {key[m]: _eps(got[m], wants[0][m].cpu().numpy()) for m in checks}
+    eps_reset = {key[m]: _eps(got[m], wants[per_reset][m].cpu().numpy()) for m in checks}
+    eps_pic = {key[m]: _eps(wants[per_reset][m].cpu().numpy(), wants[0][m].cpu().numpy()) for m in checks}
+    particles = 2.0 * w["N"]
+    return {"workload": "iaw_kinetic: periodic 1024 cells (L=288), 2^23 ions + 2^23 electrons (q/m -1800), "
+                        "amplitude 0.2, dt=0.25/omega_pe, K=30 per macro step of 150 dt, 325 macro steps, "
+                        "256 x-bins x 64 velocity cells",
+            "T_end": T_end, "fine_steps_plain": steps * per, "plain_pic_s": t_plain,
+            "plain_pic_particle_steps_per_s": particles * steps * per / t_plain,
+            "plain_pic_reset_s": plain[per_reset]["seconds"], "reset_every": per_reset,
+            "projective": {"coarse": "phase_space", "dT": w["dT"], "K": w["K"], "seconds": wall,
+                           "speedup_vs_plain_pic": t_plain / wall,
+                           "particle_steps_per_s": particles * w["K"] * steps / wall,
+                           "eps_vs_plain_pic": eps_plain, "eps_vs_reset_pic": eps_reset,
+                           "status": ctx.sync_status()},
+            "eps_reset_pic_vs_plain_pic": eps_pic,
+            "status_plain_pic": [plain[0]["status"], plain[per_reset]["status"]]}
+
+
 def run_surrogate(dev, cfg, pb, want, checks):
     """The learned coarse-derivative surrogate on the ion-wave workload: training pairs
     (c at the start of a macro step, that step's least-squares slope) from projective runs
@@ -824,6 +944,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-slab", action="store_true")
+    ap.add_argument("--no-kinetic", action="store_true")
     ap.add_argument("--kernel", default=None, help="time one kernel alone (profiling mode)")
     args = ap.parse_args()
     if args.kernel:

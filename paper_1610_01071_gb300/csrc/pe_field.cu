@@ -541,11 +541,13 @@ int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, in
 
 // ---------------------------------------------------------------------------------
 // Kinetic electrons (Section 4.1's two-species bursts): periodic Poisson equation for the
-// net charge, one block. Thread t owns the m = ncell / 1024 (at least 1) consecutive nodes
-// j0 = t m ...; the sums run lane by lane, then warp by warp, in a fixed order.
+// net charge, one block of 256 threads; thread t owns the m = ncell / 256 (at least 1)
+// consecutive nodes j0 = t m ... The net charge and then the face fields and potentials live
+// in shared memory; every sum runs node by node within a thread, then lane by lane and warp
+// by warp, in a fixed order. FP64 throughput of one SM bounds this kernel, so each node costs
+// a handful of FP64 operations and the block-wide sums run over 256 partial sums.
 
-constexpr int kPoissonThreads = 1024;
-constexpr int kPoissonMaxPer = kFullGridMax / kPoissonThreads;
+constexpr int kPoissonThreads = 256;
 
 // Exclusive prefix sum over the block of one value per thread, and the block total.
 // wsum: 32 shared slots. Every thread of the block calls it.
@@ -581,79 +583,70 @@ __global__ void __launch_bounds__(kPoissonThreads) k_poisson_periodic(const long
                                                                       int n, double dx, double nscale, double* phi,
                                                                       double* E, float* Ef)
 {
+    extern __shared__ double psh[];
+    double* F = psh;      // [n]: net charge, then the face fields F_{j+1/2}
+    double* P = psh + n;  // [n]: potential before its mean is removed
     __shared__ double wd[32];
-    __shared__ double last_face[kPoissonThreads];
     const int t = threadIdx.x;
     const int m = n >= (int)blockDim.x ? n / (int)blockDim.x : 1;
     const int nt = n / m;  // threads that own nodes
     const int j0 = t * m;
     const bool act = t < nt;
-    // net charge per node: the int64 difference of the deposits is exact; the sums are FP64
-    // (a fixed-point prefix sum of a strongly non-neutral state would leave the int64 range)
-    double S[kPoissonMaxPer];
+    // net charge per node (the int64 difference of the deposits is exact), and its sum
     double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < kPoissonMaxPer; ++k) {
-        if (k < m) {
-            const double q = act ? (double)(__ldg(rho_i + j0 + k) - __ldg(rho_e + j0 + k)) : 0.0;
+    if (act)
+        for (int k = 0; k < m; ++k) {
+            const double q = (double)(__ldg(rho_i + j0 + k) - __ldg(rho_e + j0 + k));
+            F[j0 + k] = q;
             s += q;
-            S[k] = s;
         }
-    }
     double tot;
     const double off = block_exclusive_scan(s, &tot, wd);
     // face fields before the gauge: F_{j+1/2} - F_{-1/2} = dx nscale (S_j - (j + 1) <S>)
-    const double mean = tot / n;
-    const double c = dx * nscale;
-    double F[kPoissonMaxPer];
+    const double mean = tot / n, c = dx * nscale;
     double fs = 0.0;
-#pragma unroll
-    for (int k = 0; k < kPoissonMaxPer; ++k) {
-        if (k < m) {
-            F[k] = act ? c * ((off + S[k]) - (double)(j0 + k + 1) * mean) : 0.0;
-            fs += F[k];
+    if (act) {
+        double acc = off;
+        for (int k = 0; k < m; ++k) {
+            acc += F[j0 + k];
+            const double f = c * (acc - (double)(j0 + k + 1) * mean);
+            F[j0 + k] = f;
+            fs += f;
         }
     }
     double ftot;
     (void)block_exclusive_scan(fs, &ftot, wd);
     const double gauge = ftot / n;  // the faces of a periodic phi sum to zero
     double ps = 0.0;
-#pragma unroll
-    for (int k = 0; k < kPoissonMaxPer; ++k) {
-        if (k < m) {
-            F[k] = act ? F[k] - gauge : 0.0;
-            ps += F[k];
+    if (act)
+        for (int k = 0; k < m; ++k) {
+            const double f = F[j0 + k] - gauge;
+            F[j0 + k] = f;
+            ps += f;
         }
-    }
     // phi_0 = 0, phi_{j+1} = phi_j - dx F_{j+1/2}
     double ptot;
     const double poff = block_exclusive_scan(ps, &ptot, wd);
-    double P[kPoissonMaxPer];
-    double acc = -dx * poff, psum = 0.0;
-#pragma unroll
-    for (int k = 0; k < kPoissonMaxPer; ++k) {
-        if (k < m) {
-            P[k] = acc;
-            psum += act ? acc : 0.0;
-            acc -= dx * F[k];
+    double psum = 0.0;
+    if (act) {
+        double p = -dx * poff;
+        for (int k = 0; k < m; ++k) {
+            P[j0 + k] = p;
+            psum += p;
+            p -= dx * F[j0 + k];
         }
     }
     double pt;
-    (void)block_exclusive_scan(psum, &pt, wd);
+    (void)block_exclusive_scan(psum, &pt, wd);  // its barriers also publish F to the neighbours
     const double pmean = pt / n;
-    if (act) last_face[t] = F[m - 1];
-    __syncthreads();
-    const double Fprev = act ? last_face[(t - 1 + nt) % nt] : 0.0;  // F_{j0-1/2}
-#pragma unroll
-    for (int k = 0; k < kPoissonMaxPer; ++k) {
-        if (k < m && act) {
+    if (act)
+        for (int k = 0; k < m; ++k) {
             const int j = j0 + k;
-            const double e = 0.5 * (F[k] + (k ? F[k - 1] : Fprev));
+            const double e = 0.5 * (F[j] + F[j > 0 ? j - 1 : n - 1]);  // E_j = (F_{j+1/2} + F_{j-1/2}) / 2
             E[j] = e;
             Ef[j] = (float)e;
-            phi[j] = P[k] - pmean;
+            phi[j] = P[j] - pmean;
         }
-    }
 }
 
 __global__ void k_boltzmann_profile(const double* phi, int n, float* nprof, float* uprof)
@@ -671,7 +664,9 @@ extern "C" PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_
     if (!is_pow2(ncell) || ncell < 8 || ncell > kFullGridMax || !rho_i || !rho_e || !phi || !E || !Ef ||
         !(dx > 0.0))
         return PE_EINVAL;
-    k_poisson_periodic<<<1, kPoissonThreads, 0, (cudaStream_t)stream>>>(
+    const size_t smem = 2 * sizeof(double) * (size_t)ncell;
+    if (ensure_smem((const void*)k_poisson_periodic, smem) != PE_OK) return PE_ECUDA;
+    k_poisson_periodic<<<1, kPoissonThreads, smem, (cudaStream_t)stream>>>(
         reinterpret_cast<const long long*>(rho_i), reinterpret_cast<const long long*>(rho_e), ncell, dx,
         ldexp(1.0, -(s_w + 24)), phi, E, Ef);
     return launch_status();

@@ -17,6 +17,13 @@ Section 4; normalised units lambda_D = omega_pi = c_s = 1, ion q/m = 1):
   central eighth and vacuum elsewhere, 2^25 equal-weight ions (none in the vacuum
   cells), v_th=1, dt=0.1, K=30, M=8, 40 macro-steps, 512 coarse coefficients per
   moment.
+* ``iaw_kinetic`` — the paper's two-species ion-acoustic setting (Section 4.1, Runs 5-8
+  shape): periodic 1024 cells at dx = 0.28125 (L = 288, about the paper's L = 8 at
+  h = 0.28 Debye lengths), 2^23 ions and 2^23 electrons (8192 per cell and species),
+  amplitude 0.2, ion v_th = 0.22, electrons q/m = -1800 with v_th = sqrt(1800), dt =
+  0.25 / omega_pe, bursts of K = 30 fine steps per macro step of 150 dt (the paper's
+  Delta t / delta t), 325 macro steps (T = 287, the paper's t = 8 in ion plasma periods
+  of its units), 256 coarse x-bins by 64 velocity cells over [-2.5, 2.5).
 """
 from __future__ import annotations
 
@@ -29,6 +36,9 @@ WORKLOADS = {
                       n_coarse=256, macro_steps=50, wavelet="haar"),
     "slab": dict(ncell=8192, L=4096.0, N=1 << 25, amplitude=0.0, v_th=1.0, dt=0.1, K=30, M=8,
                  n_coarse=512, macro_steps=40, wavelet="haar", boundary="absorbing"),
+    "iaw_kinetic": dict(ncell=1024, L=288.0, N=1 << 23, amplitude=0.2, v_th=0.22, dt=0.25 / np.sqrt(1800.0),
+                        K=30, M=5, n_coarse=256, macro_steps=325, wavelet="haar", electrons="kinetic",
+                        qm_e=-1800.0, n_v=64, v_max=2.5),
 }
 
 
