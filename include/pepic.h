@@ -382,7 +382,7 @@ PE_API int pe_ps_project(const double* samples, int32_t K, int32_t nxc, int32_t 
  * the CDF row, the inverse cell masses 1 / p_k (p_k = F[k+1] - F[k]; 0 for an empty cell),
  * and the cells' relative density slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to
  * [-1, 1].
- * scratch: 2 nxc (n_v + 1) doubles. */
+ * scratch: not used (may be NULL); the reconstruction works in shared memory. */
 PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf, float* table,
                              double* scratch, int32_t* flags, void* stream);
 

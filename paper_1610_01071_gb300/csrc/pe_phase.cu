@@ -55,10 +55,13 @@ __device__ int edge_low(int N, double* F)
         }
     if (k0 < 0) return 0;
     int km = k0 - 1, kp = k0 + 1;
+    // S = F[0] + ... + F[kp-1] summed left to right; it depends on kp only, so it is carried
+    // from one kp to the next (the same additions in the same order as summing afresh)
+    int s_kp = 0;
+    double S = 0.0;
     for (;;) {
         if (kp > N || km < 0) return 1;
-        double S = 0.0;
-        for (int k = 0; k < kp; ++k) S = add_(S, F[k]);
+        for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
         const double L = (double)(kp - km);
         const double dF = div_(mul_(2.0, S), mul_(L, sub_(L, 1.0)));
         const double top = mul_(sub_(L, 1.0), dF);
@@ -104,9 +107,10 @@ __device__ int interior_fwd(int N, double* F)
                 break;
             }
         bool done = false;
+        double S = 0.0;  // F[km] + ... + F[kp-1], left to right, extended as kp grows
+        int s_kp = km;
         for (; kp <= N; ++kp) {
-            double S = 0.0;
-            for (int k = km; k < kp; ++k) S = add_(S, F[k]);
+            for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
             const double L = (double)(kp - km);
             const double dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(S, L), F[km]));
             const double end = add_(F[km], mul_(sub_(L, 1.0), dF));
@@ -157,24 +161,26 @@ __device__ int reconstruct(int N, double* F, double* G, double* P)
 namespace pe {
 namespace {
 
-// Lifting tables, per bin (one thread per bin, 32 bins per block so the bins spread over
+// Lifting tables, per bin (one thread per bin, up to 32 bins per block so the bins spread over
 // the SMs): the raw mass, the reconstructed FP64 CDF row (uniform where the raw mass is not
 // positive), and the FP32 sampling row used by the particle loader: F[0..nv], the inverse
 // cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells' relative density
-// slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1]. scratch: 2 (nv + 1)
-// doubles per bin.
+// slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1]. The reconstruction, whose
+// loops reread the row many times, works on three rows per thread in shared memory.
 __global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
                                               double* __restrict__ mass, double* __restrict__ cdf,
-                                              float* __restrict__ table, double* __restrict__ scratch,
-                                              int32_t* __restrict__ flags)
+                                              float* __restrict__ table, int32_t* __restrict__ flags)
 {
+    extern __shared__ double rows[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nxc) return;
+    double* F = rows + (size_t)threadIdx.x * 3 * (nv + 1);
+    double* G = F + nv + 1;
+    double* Pr = G + nv + 1;
     const double* h = H + (size_t)i * nv;
     double s = 0.0;
     for (int j = 0; j < nv; ++j) s = add_(s, h[j]);
     mass[i] = s;
-    double* F = cdf + (size_t)i * (nv + 1);
     if (s > 0.0) {
         double r = 0.0;
         F[0] = 0.0;
@@ -182,11 +188,12 @@ __global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int
             r = add_(r, h[j]);
             F[j + 1] = div_(r, s);
         }
-        double* G = scratch + (size_t)i * 2 * (nv + 1);
-        if (reconstruct(nv, F, G, G + nv + 1) && flags) atomicOr(flags, 1);
+        if (reconstruct(nv, F, G, Pr) && flags) atomicOr(flags, 1);
     } else {
         for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
     }
+    double* out = cdf + (size_t)i * (nv + 1);
+    for (int k = 0; k <= nv; ++k) out[k] = F[k];
     float* T = table + (size_t)i * (3 * nv + 1);
     for (int k = 0; k <= nv; ++k) T[k] = (float)F[k];
     for (int k = 0; k < nv; ++k) {
@@ -642,10 +649,17 @@ extern "C" PE_API int pe_ps_project(const double* samples, int32_t K, int32_t nx
 extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_v, double* mass, double* cdf,
                                         float* table, double* scratch, int32_t* flags, void* stream)
 {
-    if (!H || !mass || !cdf || !table || !scratch || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
+    (void)scratch;  // the rows live in shared memory
+    if (!H || !mass || !cdf || !table || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
-    k_ps_cdf<<<(nxc + 31) / 32, 32, 0, s>>>(H, nxc, n_v, mass, cdf, table, scratch, flags);
+    // three FP64 rows of n_v + 1 per thread; up to 32 threads, fewer for wide rows (<= 192 KB)
+    const size_t row3 = 3 * sizeof(double) * ((size_t)n_v + 1);
+    int per_block = (int)std::min<size_t>(32, (size_t)(192 * 1024) / row3);
+    if (per_block < 1) return PE_EINVAL;
+    const size_t smem = row3 * (size_t)per_block;
+    if (ensure_smem((const void*)k_ps_cdf, smem) != PE_OK) return PE_ECUDA;
+    k_ps_cdf<<<(nxc + per_block - 1) / per_block, per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
     k_ps_mass<<<1, 1024, 0, s>>>(nxc, mass);
     return launch_status(2);
 }
