@@ -91,7 +91,8 @@ extern "C" {
  * ratio qm_e, pushed with the same kernels; the field is the Poisson equation for the net
  * charge (pe_field_kinetic). Every load and every lift places the electrons in Boltzmann
  * equilibrium with the ions: the Poisson-Boltzmann potential of the ion density, then a quiet
- * start on exp(phi) with thermal speed v_th_e and no drift (pe_boltzmann_profile). Kinetic
+ * start on exp(phi) with thermal speed v_th_e drifting with the ions' mean velocity
+ * (pe_boltzmann_profile). Kinetic
  * electrons need a periodic grid and a time step that resolves the electron plasma period
  * (|qm_e|^(-1/2) in these units). */
 #define PE_ELECTRONS_BOLTZMANN 0
@@ -149,11 +150,15 @@ PE_API int pe_field_ex(const int64_t* rho_fx, int32_t ncell, double dx, int32_t 
 PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_e, int32_t ncell, double dx, int32_t s_w,
                             double* phi, double* E, float* Ef, void* stream);
 
-/* Boltzmann electron profile of the lifting, Eq. (electronpassive): n_prof[j] = exp(phi[j])
- * (FP32) and u_prof[j] = 0, the two profile arrays pe_quiet_start loads the electrons from
- * (with their thermal speed). phi[ncell]: the Poisson-Boltzmann potential of the ion density
- * (pe_field). */
-PE_API int pe_boltzmann_profile(const double* phi, int32_t ncell, float* n_prof, float* u_prof, void* stream);
+/* Boltzmann electron profile of the lifting, Eq. (electronpassive): n_e = exp(phi) and
+ * V_e = V_i. n_prof[j] = exp(phi[j]) (FP32), the profile pe_quiet_start loads the electrons
+ * from (with their thermal speed); phi[ncell] is the Poisson-Boltzmann potential of the ion
+ * density (pe_field). u_prof[j] = the ions' mean velocity at node j, m_j 2^-s_p / (n_j 2^-s_w),
+ * from their nodal moment sample ion_moments (int64[2][ncell], density then momentum: pe_sample
+ * with tau = 0 and bin_shift = 0, shifts s_w and s_p); 0 where n_j <= 0, and everywhere when
+ * ion_moments is NULL. */
+PE_API int pe_boltzmann_profile(const double* phi, const int64_t* ion_moments, int32_t s_w, int32_t s_p,
+                                int32_t ncell, float* n_prof, float* u_prof, void* stream);
 
 /* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
  * follows it): each particle, at its integer-time velocity Vbar, is carried to
@@ -482,7 +487,8 @@ enum pe_buffer {
                                absorbing grids: the equal-weight loading scratch */
     PE_BUF_ELECTRONS_A,     /* kinetic electrons: cell | theta | v | w, as the ion banks (else empty) */
     PE_BUF_ELECTRONS_B,     /* kinetic electrons: second bank (sort target) */
-    PE_BUF_RHO_E,           /* kinetic electrons: int64[ncell] electron deposit */
+    PE_BUF_RHO_E,           /* kinetic electrons: int64[ncell] electron deposit, then int64[2][ncell]
+                               ion moments for the electrons' drift */
     PE_NBUF
 };
 

@@ -105,7 +105,7 @@ def _load():
                                                  i32, i32, i32, P]),
                 "orc_burst_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, dbl,
                                              i32, i32, i32, dbl, dbl, i32, P, P, P]),
-                "orc_boltzmann_electrons": (None, [i64, i32, P, dbl, u64, P, P, P, P]),
+                "orc_boltzmann_electrons": (None, [i64, i32, P, i64, P, P, P, P, dbl, u64, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -732,11 +732,16 @@ def burst_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, K, d
     return (sfx if nv > 0 else sd), phi
 
 
-def boltzmann_electrons(N, ncell, phi, v_th_e, seed):
-    """Electrons of the lifting: quiet start on n_e = exp(phi), zero mean velocity."""
+def boltzmann_electrons(N, ncell, phi, v_th_e, seed, ions: State = None):
+    """Electrons of the lifting: quiet start on n_e = exp(phi), drifting with the ions' nodal
+    mean velocity (V_e = V_i; no drift without ions)."""
     phi = _f64(phi)
     cell = np.zeros(N, np.int32)
     theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
-    _load().orc_boltzmann_electrons(N, ncell, _p(phi), float(v_th_e), seed & 0xFFFFFFFFFFFFFFFF, _p(cell),
+    if ions is not None:
+        ia = (ions.n, _p(ions.cell), _p(ions.theta), _p(ions.v), _p(ions.w))
+    else:
+        ia = (0, None, None, None, None)
+    _load().orc_boltzmann_electrons(N, ncell, _p(phi), *ia, float(v_th_e), seed & 0xFFFFFFFFFFFFFFFF, _p(cell),
                                     _p(theta), _p(v), _p(w))
     return State(cell, theta, v, w)

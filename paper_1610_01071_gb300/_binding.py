@@ -107,7 +107,7 @@ SIGNATURES = {
     "pe_field": (ctypes.c_int, [P, i32, f64, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_field_ex": (ctypes.c_int, [P, i32, f64, i32, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_field_kinetic": (ctypes.c_int, [P, P, i32, f64, i32, P, P, P, P]),
-    "pe_boltzmann_profile": (ctypes.c_int, [P, i32, P, P, P]),
+    "pe_boltzmann_profile": (ctypes.c_int, [P, P, i32, i32, i32, P, P, P]),
     "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
     "pe_push_ex": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, i32, P, ctypes.POINTER(SampleArgs),
                                   P, P]),
@@ -253,11 +253,13 @@ def field_kinetic(rho_i, rho_e, ncell, dx, s_w, phi=None, stream=None):
     return phi, E, Ef
 
 
-def boltzmann_profile(phi, ncell, stream=None):
-    """Boltzmann electron profile exp(phi) (and zero mean velocity) as float32 [2, ncell]."""
+def boltzmann_profile(phi, ncell, ion_moments=None, s_w=0, s_p=0, stream=None):
+    """Boltzmann electron profile: exp(phi) and the ions' mean velocity from their nodal moment
+    sample ion_moments (int64 [2, ncell]; zero drift without it), float32 [2, ncell]."""
     prof = torch.empty(2 * ncell, dtype=torch.float32, device=phi.device)
-    check(load().pe_boltzmann_profile(_ptr(phi), ncell, _ptr(prof), _ptr(prof[ncell:]), _stream(stream)),
-          "pe_boltzmann_profile")
+    mom = _ptr(ion_moments) if ion_moments is not None else None
+    check(load().pe_boltzmann_profile(_ptr(phi), mom, int(s_w), int(s_p), ncell, _ptr(prof), _ptr(prof[ncell:]),
+                                      _stream(stream)), "pe_boltzmann_profile")
     return prof.view(2, ncell)
 
 

@@ -178,7 +178,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
                                 (walls ? align256(PE_PS_EQ_SCRATCH_BYTES(nc)) : 0);
     out->bytes[PE_BUF_ELECTRONS_A] = kin ? bank : 0;
     out->bytes[PE_BUF_ELECTRONS_B] = kin ? bank : 0;
-    out->bytes[PE_BUF_RHO_E] = kin ? 8 * nc : 0;
+    out->bytes[PE_BUF_RHO_E] = kin ? 8 * 3 * nc : 0;  // electron deposit + ion moments [2][ncell]
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -384,19 +384,35 @@ static int deposit_current(pe_ctx* x)
     return PE_OK;
 }
 
-// Electrons in Boltzmann equilibrium with the current ion deposit (Eq. electronpassive), as the
-// lifting of Section 3.3 places them and as Section 4.1's reset runs reload them: the
-// Poisson-Boltzmann potential of the ion density, then a quiet start on exp(phi) with the
-// electrons' thermal speed and no drift. Leaves their deposit in rho_e.
+// Electrons in Boltzmann equilibrium with the current ions (Eq. electronpassive: n_e = exp(phi),
+// V_e = V_i, T_e = T_e0), as the lifting of Section 3.3 places them and as Section 4.1's reset
+// runs reload them: the Poisson-Boltzmann potential of the ion density, then a quiet start on
+// exp(phi) with the electrons' thermal speed, drifting with the ions' mean velocity. Leaves
+// their deposit in rho_e.
 static uint64_t electron_seed(uint64_t s) { return s ^ 0xD1B54A32D192ED03ULL; }
 
 static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed)
 {
     const pe_config& c = x->cfg;
+    // the ions' nodal density and momentum at their stored velocities (kick 1/2: Vbar = v; at
+    // integer time after a load or lift, half a step earlier in a plain-PIC reset), for V_e = V_i
+    int64_t* mom = x->rho_e + c.ncell;
+    pe_sample_args a;
+    memset(&a, 0, sizeof(a));
+    a.E0f = x->Ef;  // tau = 0: the frame field is not used
+    a.qm = (float)c.qm;
+    a.inv_dx = (float)(1.0 / x->dx);
+    a.s_w = x->s_w;
+    a.s_p = x->s_p;
+    a.sample_fx = mom;
+    a.boundary = c.boundary;
+    const int b = x->bank;
+    PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), 0.5f,
+                     &a, x->status, x->stream));
     PE_TRY(field_solve_history(x->rho, c.ncell, x->dx, x->s_w, PE_POISSON_BOLTZMANN, PE_BOUNDARY_PERIODIC,
                                c.newton_tol, c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, nullptr, 0,
                                x->stream));
-    PE_TRY(pe_boltzmann_profile(x->phi, c.ncell, x->prof, x->prof + c.ncell, x->stream));
+    PE_TRY(pe_boltzmann_profile(x->phi, mom, x->s_w, x->s_p, c.ncell, x->prof, x->prof + c.ncell, x->stream));
     const int e = x->ebank;
     PE_TRY(timed(x, 0, [&] {
         return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof,

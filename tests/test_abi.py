@@ -78,7 +78,7 @@ def test_kinetic_electron_layout_and_checks(lib):
     lay = b.layout(b.make_config(*base, electrons="kinetic"))
     bank = 4 * ((4 * 64 * 16 + 255) // 256) * 256
     assert lay.bytes[b.BUF["electrons_a"]] == bank and lay.bytes[b.BUF["electrons_b"]] == bank
-    assert lay.bytes[b.BUF["rho_e"]] == 8 * 64
+    assert lay.bytes[b.BUF["rho_e"]] == 8 * 3 * 64  # electron deposit + the ions' moments [2][ncell]
     lay0 = b.layout(b.make_config(*base))
     assert lay0.bytes[b.BUF["electrons_a"]] == 0 and lay0.bytes[b.BUF["rho_e"]] == 0
     assert lay.total_bytes >= lay0.total_bytes + 2 * bank

@@ -55,12 +55,24 @@ def test_field_kinetic_rejects_bad_sizes():
         pe.field_kinetic(z, z, 16384, 0.5, 30)
 
 
-def test_boltzmann_profile_is_exp_phi():
+def test_boltzmann_profile_is_exp_phi_with_the_ions_drift():
     phi = torch.linspace(-3.0, 2.0, 512, dtype=torch.float64, device=DEV)
     prof = pe.boltzmann_profile(phi, 512).cpu().numpy()
     want = np.exp(phi.cpu().numpy())
     assert np.allclose(prof[0], want, rtol=2e-7, atol=0)
-    assert not prof[1].any()
+    assert not prof[1].any()  # no ion moments: no drift
+    # V_e = V_i = m 2^-s_p / (n 2^-s_w) where the ion density is positive, 0 elsewhere
+    rng = np.random.default_rng(2)
+    s_w, s_p = 30, 27
+    n = rng.integers(0, 2**40, 512)
+    n[::7] = 0
+    u = rng.normal(size=512) * 0.3
+    m = np.round(u * n * 2.0 ** (s_p - s_w)).astype(np.int64)
+    mom = torch.from_numpy(np.concatenate([n, m]).astype(np.int64)).to(DEV)
+    prof = pe.boltzmann_profile(phi, 512, mom, s_w, s_p).cpu().numpy()
+    want_u = np.where(n > 0, m / np.where(n > 0, n, 1) * 2.0 ** (s_w - s_p), 0.0)
+    assert np.allclose(prof[1], want_u.astype(np.float32), rtol=1e-6, atol=0)
+    assert not prof[1][::7].any()
 
 
 def make_kinetic(cfg, seed, **kw):
@@ -78,13 +90,15 @@ def oracle_ions(cfg, seed):
 
 def oracle_electrons(cfg, ions, s_w, seed, phi0=None):
     # the loading of the library: Poisson-Boltzmann potential of the ion deposit, then the
-    # quiet start on the FP32 profile exp(phi)
+    # quiet start on the FP32 profiles exp(phi) and the ions' nodal mean velocity (V_e = V_i)
     ncell = cfg["ncell"]
     dx = cfg["L"] / ncell
     dens = orc.deposit_fx(ions.cell, ions.theta, ions.w, ncell, s_w) * 2.0 ** -(s_w + 24)
     phi = orc.newton_pb(dens, dx, phi0=np.zeros(ncell) if phi0 is None else phi0, tol=1e-11)[0]
     prof = np.exp(phi).astype(np.float32)
-    return orc.quiet_start(cfg["N"], ncell, prof, np.zeros(ncell, np.float32), V_TH_E, seed)
+    d, m = orc.deposit_f64(ions.cell, ions.theta, ions.w, ncell, vel=ions.v)
+    u = np.where(d > 0, m / np.where(d > 0, d, 1.0), 0.0).astype(np.float32)
+    return orc.quiet_start(cfg["N"], ncell, prof, u, V_TH_E, seed)
 
 
 def state_of(ctx, species):

@@ -161,3 +161,22 @@ def test_kinetic_burst_runs_the_same_steps_as_plain_pic():
     vbar = ions.v  # loaded at integer time
     dens, mom = orc.restrict_sample(ions, vbar, E, ncell, dx, dT, 1.0)
     assert np.array_equal(samples[0, 0], dens) and np.array_equal(samples[0, 1], mom)
+
+
+def test_boltzmann_electrons_drift_with_the_ions():
+    # Eq. electronpassive: V_e = V_i. A uniform ion drift gives the electrons exactly that drift
+    # on top of their symmetric quiet-start Maxwellian; a sinusoidal one is reproduced node by node
+    ncell, ppc, dx = 64, 64, 0.5
+    N = ncell * ppc
+    ions = orc.quiet_start(N, ncell, np.ones(ncell), np.full(ncell, 0.3), 0.0, 3)  # cold: V_i = 0.3
+    phi = np.zeros(ncell)
+    e = orc.boltzmann_electrons(N, ncell, phi, np.sqrt(-QM_E), 5, ions=ions)
+    e0 = orc.boltzmann_electrons(N, ncell, phi, np.sqrt(-QM_E), 5)
+    assert np.allclose(e.v - e0.v, 0.3, rtol=0, atol=1e-12)  # the same draws, shifted by the drift
+    n, u = orc.sine_profile(ncell, ncell * dx, 0.2)
+    ions = orc.quiet_start(N, ncell, n, u, 0.0, 3)  # cold ions: V_i(x) = u(x)
+    e = orc.boltzmann_electrons(N, ncell, phi, 1e-9, 6, ions=ions)
+    d, m = orc.deposit_f64(e.cell, e.theta, e.w, ncell, vel=e.v)
+    # up to the O((k dx)^2) smoothing of the CIC deposits and the linear profile interpolation
+    kdx = 2 * np.pi / ncell
+    assert np.abs(m / d - u).max() < 0.2 * kdx**2 / 2
