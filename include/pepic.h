@@ -563,8 +563,11 @@ PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
 PE_API int pe_sync_status(pe_ctx* ctx);
 /* Conserved quantities of the current particles at the current time (pe_compute_moments
  * with the field of the current positions; deposits and solves it first, which also
- * refreshes the Newton warm start, as pe_measure does). out: host (synchronises) or
- * device memory. */
+ * refreshes the Newton warm start, as pe_measure does). With kinetic electrons the charge
+ * entries are the ions', electron_energy is the electrons' kinetic energy (mass w / |q_e/m_e|
+ * per unit weight), momentum and the speed and CFL maxima cover both species, and
+ * total_energy = ion kinetic + field + electron kinetic energy, what the two-species system
+ * conserves. out: host (synchronises) or device memory. */
 PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out_on_device);
 /* Host-side counters (no synchronisation except for newton_iters/status, which are
  * read after a stream synchronise). */

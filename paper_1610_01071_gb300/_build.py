@@ -67,7 +67,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         for _, err in results:
             print(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
+    # every symbol must resolve at link time (a missing definition fails the build, not the load)
+    cmd = [cc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

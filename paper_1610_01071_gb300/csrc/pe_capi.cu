@@ -780,8 +780,20 @@ extern "C" PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out
     pe_moments* res = (pe_moments*)(scratch + PE_MOMENTS_SCRATCH_BYTES);
     const int b = x->bank;
     const float kick = x->v_at_integer ? 0.5f : 1.0f;
-    PE_TRY(pe_compute_moments(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, x->phi, x->E, c.ncell, x->dx,
-                      c.dt, (float)(c.qm * c.dt), kick, x->s_w, c.poisson, scratch, res, x->status, x->stream));
+    // kinetic electrons: no Boltzmann free energy (phi not passed); the electron particles'
+    // moments are folded in below
+    PE_TRY(pe_compute_moments(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef,
+                              x->kinetic ? nullptr : x->phi, x->E, c.ncell, x->dx, c.dt, (float)(c.qm * c.dt), kick,
+                              x->s_w, c.poisson, scratch, res, x->status, x->stream));
+    if (x->kinetic) {
+        pe_moments* eres = (pe_moments*)(scratch + PE_MOMENTS_SCRATCH_BYTES + 128);
+        const int e = x->ebank;
+        const float ekick = x->e_v_at_integer ? 0.5f : 1.0f;
+        PE_TRY(pe_compute_moments(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, nullptr, nullptr,
+                                  c.ncell, x->dx, c.dt, (float)(x->qm_e * c.dt), ekick, x->s_w, c.poisson, scratch,
+                                  eres, x->status, x->stream));
+        PE_TRY(combine_kinetic_moments(res, eres, x->qm_e, x->stream));
+    }
     if (cudaMemcpyAsync(out, res, sizeof(pe_moments), out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         x->stream) != cudaSuccess)
         return PE_ECUDA;

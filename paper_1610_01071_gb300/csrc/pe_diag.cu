@@ -242,6 +242,32 @@ extern "C" PE_API int pe_compute_moments(const int32_t* cell, const float* theta
     return launch_status(2);
 }
 
+namespace pe {
+
+// Kinetic electrons: the ions' moments (out) absorb the electrons' (e, velocities of the
+// electron pass, mass w / |q_e/m_e| per particle): electron_energy = the electrons' kinetic
+// energy, momentum of both species, the larger speed and CFL number, total = kinetic of the
+// ions + field + electrons.
+__global__ void k_moments_kinetic(pe_moments* out, const pe_moments* e, double inv_mass_ratio)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    out->electron_energy = e->kinetic * inv_mass_ratio;
+    out->momentum += e->momentum * inv_mass_ratio;
+    out->total_energy = out->kinetic + out->field_energy + out->electron_energy;
+    out->max_speed = fmax(out->max_speed, e->max_speed);
+    out->cfl = fmax(out->cfl, e->cfl);
+    out->invalid += e->invalid;
+}
+
+int combine_kinetic_moments(pe_moments* out, const pe_moments* electrons, double qm_e, cudaStream_t s)
+{
+    if (!(qm_e < 0.0)) return PE_EINVAL;
+    k_moments_kinetic<<<1, 32, 0, s>>>(out, electrons, 1.0 / -qm_e);
+    return launch_status(1);
+}
+
+}  // namespace pe
+
 extern "C" PE_API int pe_rel_l2(const double* a, const double* b, int64_t n, double* out, void* stream)
 {
     if (n < 0 || !out || (n > 0 && (!a || !b))) return PE_EINVAL;

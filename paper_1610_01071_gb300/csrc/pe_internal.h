@@ -62,6 +62,9 @@ void make_proj_desc(void* out, const int64_t* samp, int64_t row_stride, int ncel
                     double* csamples, double* coarse, double* slope);
 int launch_restrict_project_batch(const void* descs, int R, int K, double dt, double dT, cudaStream_t s);
 
+// Kinetic electrons: folds the electrons' moments into the ions' (pe_diag.cu).
+int combine_kinetic_moments(pe_moments* out, const pe_moments* electrons, double qm_e, cudaStream_t s);
+
 // Counts kernel launches (exported through pe_launch_count).
 void note_launches(int n);
 

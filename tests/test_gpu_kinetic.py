@@ -209,3 +209,24 @@ def test_kinetic_contexts_are_not_batched():
     ctx = pe.Context(c, device=DEV)
     with pytest.raises(pe.PepicError):  # the batched ensemble runs Boltzmann electrons only
         pe.Batch([ctx])
+
+
+def test_kinetic_diagnostics_cover_both_species_and_conserve_energy():
+    cfg = KIN
+    ctx = make_kinetic(cfg, seed=13)
+    ctx.load_initial(cfg["amp"])
+    m0 = ctx.moments()
+    dx = cfg["L"] / cfg["ncell"]
+    ge = state_of(ctx, "electrons")  # velocities at integer time after the load
+    ke = 0.5 * np.sum(ge.w * ge.v**2) * dx / -QM_E
+    assert m0["electron_energy"] == pytest.approx(ke, rel=1e-5)
+    assert m0["total_energy"] == pytest.approx(m0["kinetic"] + m0["field_energy"] + m0["electron_energy"], rel=1e-12)
+    assert m0["cfl"] >= np.abs(ge.v).max() * cfg["dt"] / dx * (1 - 1e-6)  # the electrons set it
+    assert m0["invalid"] == 0
+    ctx.pic_steps(40)
+    m1 = ctx.moments()
+    assert ctx.sync_status() == 0
+    # the two-species system conserves energy up to the slow heating of explicit PIC, and its
+    # momentum (ions plus electrons of mass w / |q_e/m_e|) up to the fixed-point deposit
+    assert abs(m1["total_energy"] - m0["total_energy"]) < 1e-3 * m0["total_energy"]
+    assert abs(m1["momentum"] - m0["momentum"]) < 1e-4 * cfg["L"] * cfg["amp"]
