@@ -712,6 +712,48 @@ typedef struct pe_gate_result {
 PE_API int pe_gate(const double* samples, int32_t K_probe, int32_t ncoef, double dt, double dT, const double* s_mlp,
                    double tol, double noise_sigmas, double* coarse, double* slope, pe_gate_result* result,
                    void* stream);
+/* =================================================================== adaptive macro step
+ * The paper keeps Delta t fixed and names error estimators that adapt the projective time
+ * step as the goal (Section 3.1's remark); this is one such estimator and controller.
+ *
+ * pe_leap_curvature: per coarse component i the quadratic least-squares coefficient q_i of
+ * a burst's samples[(K+1)][ncoef] at t_p = p dt (c ~ a + b t + q t^2) and its sampling
+ * variance var_i (the fit's residual variance, K - 2 degrees of freedom, over the sum of the
+ * squared quadratic basis); out[0] = sqrt(max(0, ||q||^2 - sum var_i)), the curvature with the
+ * particle noise's bias removed, out[1] = ||c_K||_2, out[2] = sqrt(sum var_i) (device,
+ * double[3]). On a quadratic trajectory the least-squares slope is the derivative at the
+ * burst's midpoint, so the forward-Euler leap of length L from c_K errs by exactly
+ * q L (L + K dt): e(L) = out[0] L (L + K dt) / out[1] estimates the relative error of a leap.
+ * K >= 2 (K = 2 leaves no residual: no noise correction). One block, fixed summation order. */
+PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* out, void* stream);
+
+/* pe_step_adaptive: one macro step whose Delta t is a whole number M of bursts, M K dt, chosen
+ * from the estimate e of the previous step: lift (unless fresh), burst and restriction with
+ * the current Delta t (the co-moving frame depends on it, so it is fixed before the burst),
+ * then e(L) with L = Delta t - K dt. If e > tol and M > M_min the burst is rejected: the
+ * coarse state is lifted again (same seed) and the step rerun with the M of the tolerance
+ * (at most M - 1). Otherwise the step is projected, and the next step takes
+ * M = floor((K dt + safety L_tol) / (K dt)) bursts, L_tol the leap with e(L_tol) = tol,
+ * clamped to [M_min, min(M_max, floor(grow M))]. Synchronises once per burst (the decision). */
+typedef struct pe_adapt_cfg {
+    double tol;      /* bound on the estimated relative error of one leap, e.g. 1e-4 */
+    int32_t M_min;   /* smallest macro step in bursts (>= 1; 1 means no leap) */
+    int32_t M_max;   /* largest macro step in bursts */
+    double safety;   /* fraction of L_tol taken for the next step, in (0, 1] */
+    double grow;     /* the next M is at most grow times the current one (>= 1) */
+} pe_adapt_cfg;
+typedef struct pe_adapt_stats {
+    double dT;        /* the macro step taken */
+    double err;       /* its estimated relative leap error */
+    double dT_next;   /* the next macro step */
+    int32_t rejected; /* bursts rejected and rerun in this step */
+    int32_t fine_steps; /* fine steps run in this step */
+} pe_adapt_stats;
+PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* cfg, pe_adapt_stats* out);
+/* Delta t of the next macro steps (>= K dt); the configured dT until set. Bursts, projections,
+ * pe_step and pe_step_surrogate use it; a batch refuses contexts whose Delta t was changed. */
+PE_API int pe_set_macro_step(pe_ctx* ctx, double dT);
+
 /* FP32 copy of the coarse state (what = 0) or of the last slope (what = 1) into out[2 n_coarse]
  * (device), e.g. one row of a surrogate training set. */
 PE_API int pe_export_f32(pe_ctx* ctx, int32_t what, float* out);

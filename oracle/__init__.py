@@ -745,3 +745,36 @@ def boltzmann_electrons(N, ncell, phi, v_th_e, seed, ions: State = None):
     _load().orc_boltzmann_electrons(N, ncell, _p(phi), *ia, float(v_th_e), seed & 0xFFFFFFFFFFFFFFFF, _p(cell),
                                     _p(theta), _p(v), _p(w))
     return State(cell, theta, v, w)
+
+
+# ------------------------------------------------------------------ adaptive macro step
+
+
+def leap_curvature(samples, dt):
+    """(qn, ||c_K||, noise) for coarse samples [(K+1), ncoef] at t_p = p dt: q the quadratic
+    coefficient of the least-squares fit c ~ a + b t + q t^2 of each component (numpy.polyfit),
+    var_q = (residual sum of squares / (K - 2)) / sum_p g_p^2 with g_p the quadratic basis
+    orthogonal to {1, t} on the samples (the variance of the leading coefficient), and
+    qn = sqrt(max(0, sum q^2 - sum var_q)), noise = sqrt(sum var_q)."""
+    samples = _f64(samples)
+    K = samples.shape[0] - 1
+    t = np.arange(K + 1) * float(dt)
+    coef, res, _, _, _ = np.polyfit(t, samples, 2, full=True)
+    q = coef[0]
+    tau = t - t.mean()
+    g = tau * tau - np.mean(tau * tau)
+    if K > 2:
+        fit = np.polyval(coef, t[:, None]) if samples.ndim == 2 else np.polyval(coef, t)
+        rss = np.sum((samples - fit) ** 2, axis=0)
+        var = rss / (K - 2) / np.sum(g * g)
+    else:
+        var = np.zeros_like(q)
+    qn = float(np.sqrt(max(0.0, np.sum(q * q) - np.sum(var))))
+    return qn, float(np.sqrt(np.sum(samples[-1] ** 2))), float(np.sqrt(np.sum(var)))
+
+
+def leap_for_tol(qn, cn, Kdt, tol):
+    """Leap L >= 0 with qn L (L + K dt) = tol cn (infinite without curvature)."""
+    if not qn > 0:
+        return float("inf")
+    return 0.5 * (-Kdt + np.sqrt(Kdt * Kdt + 4.0 * tol * cn / qn))

@@ -97,6 +97,19 @@ class GateStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AdaptCfg(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("M_min", ctypes.c_int32), ("M_max", ctypes.c_int32),
+                ("safety", ctypes.c_double), ("grow", ctypes.c_double)]
+
+
+class AdaptStats(ctypes.Structure):
+    _fields_ = [("dT", ctypes.c_double), ("err", ctypes.c_double), ("dT_next", ctypes.c_double),
+                ("rejected", ctypes.c_int32), ("fine_steps", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # exported symbol -> (restype, argtypes); the test-suite checks this against include/pepic.h
 P, i32, i64, u64, f32, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
                                   ctypes.c_float, ctypes.c_double, ctypes.c_size_t)
@@ -143,6 +156,9 @@ SIGNATURES = {
     "pe_get_slope": (ctypes.c_int, [P, P, i32]),
     "pe_export_f32": (ctypes.c_int, [P, i32, P]),
     "pe_step_surrogate": (ctypes.c_int, [P, P, ctypes.POINTER(GateCfg), ctypes.POINTER(GateStats)]),
+    "pe_leap_curvature": (ctypes.c_int, [P, i32, i32, f64, P, P]),
+    "pe_step_adaptive": (ctypes.c_int, [P, ctypes.POINTER(AdaptCfg), ctypes.POINTER(AdaptStats)]),
+    "pe_set_macro_step": (ctypes.c_int, [P, f64]),
     "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
     "pe_ps_coarsen": (ctypes.c_int, [P, i32, i64, i32, P, P]),
     "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
@@ -251,6 +267,16 @@ def field_kinetic(rho_i, rho_e, ncell, dx, s_w, phi=None, stream=None):
     check(load().pe_field_kinetic(_ptr(rho_i), _ptr(rho_e), ncell, float(dx), int(s_w), _ptr(phi), _ptr(E), _ptr(Ef),
                                   _stream(stream)), "pe_field_kinetic")
     return phi, E, Ef
+
+
+def leap_curvature(samples, dt, stream=None):
+    """(noise-corrected ||q||, ||c_K||, noise of q) of coarse samples [(K+1), ncoef]
+    (pe_leap_curvature), as a device tensor."""
+    K1, n = samples.shape
+    out = torch.empty(3, dtype=torch.float64, device=samples.device)
+    check(load().pe_leap_curvature(_ptr(samples), K1 - 1, n, float(dt), _ptr(out), _stream(stream)),
+          "pe_leap_curvature")
+    return out
 
 
 def boltzmann_profile(phi, ncell, ion_moments=None, s_w=0, s_p=0, stream=None):
@@ -596,6 +622,17 @@ class Context:
         st = GateStats()
         self._call("pe_step_surrogate", net._h, ctypes.byref(g), ctypes.byref(st))
         return st.as_dict()
+
+    def step_adaptive(self, tol=1e-4, M_min=1, M_max=16, safety=0.8, grow=2.0) -> dict:
+        """Macro step with the curvature-controlled Delta t (pe_step_adaptive); returns its statistics."""
+        a = AdaptCfg(float(tol), int(M_min), int(M_max), float(safety), float(grow))
+        st = AdaptStats()
+        self._call("pe_step_adaptive", ctypes.byref(a), ctypes.byref(st))
+        return st.as_dict()
+
+    def set_macro_step(self, dT):
+        """Delta t of the next macro steps (>= K dt)."""
+        self._call("pe_set_macro_step", float(dT))
 
     def moments(self) -> dict:
         """Charge, momentum, energies and Courant number of the current particles (pe_state_moments)."""

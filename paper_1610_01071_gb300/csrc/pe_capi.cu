@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -202,6 +203,7 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->arena = (char*)arena;
     x->stream = (cudaStream_t)stream;
     x->dx = cfg->L / cfg->ncell;
+    x->dT_cur = cfg->dT;
     x->nc = cfg->n_coarse;
     x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
     x->nb = cfg->ncell >> x->bin_shift;
@@ -583,7 +585,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     float kick = x->v_at_integer ? 0.5f : 1.0f;
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
     for (int p = p_begin; p < p_end; ++p) {
-        const double tau = c.comoving ? c.dT - p * c.dt : 0.0;
+        const double tau = c.comoving ? x->dT_cur - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
         PE_TRY(timed(x, 0, [&] {
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
@@ -597,7 +599,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
         x->fine_steps += 1;
     }
     if (final_sample) {
-        const double tau = c.comoving ? c.dT - p_end * c.dt : 0.0;
+        const double tau = c.comoving ? x->dT_cur - p_end * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p_end));
         PE_TRY(timed(x, 0, [&] {
             return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick, &a,
@@ -630,13 +632,14 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
     if (ctx->ps && c.ps_filter) {
         double* work = ctx->csamples + (size_t)(c.K + 1) * (size_t)ctx->crow;  // measurement row as scratch
         const int filt = c.ps_filter | ((ctx->walls && (c.ps_filter & 2)) ? 4 : 0);  // reflecting x at walls
-        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, c.dT, filt, work, ctx->coarse, ctx->slope,
+        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, ctx->dT_cur, filt, work, ctx->coarse, ctx->slope,
                              ctx->stream));
     } else {
-        PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, c.dT, ctx->coarse, ctx->slope, ctx->stream));
+        PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, ctx->dT_cur, ctx->coarse, ctx->slope,
+                             ctx->stream));
     }
     ctx->macro_steps += 1;
-    ctx->time += c.dT;
+    ctx->time += ctx->dT_cur;
     ctx->fresh = 0;
     return PE_OK;
 }
@@ -679,6 +682,73 @@ extern "C" PE_API int pe_step(pe_ctx* ctx)
     PE_TRY(pe_burst(ctx));
     PE_TRY(pe_restrict(ctx));
     return pe_project(ctx);
+}
+
+extern "C" PE_API int pe_set_macro_step(pe_ctx* ctx, double dT)
+{
+    if (!ctx || !(dT >= ctx->cfg.K * ctx->cfg.dt * (1.0 - 1e-12)) || !(dT < 1e300)) return PE_EINVAL;
+    ctx->dT_cur = dT;
+    return PE_OK;
+}
+
+// Leap length L >= 0 with ||q|| L (L + K dt) = tol ||c_K||; infinite when the trajectory has
+// no curvature.
+static double leap_for_tol(double qn, double cn, double Kdt, double tol)
+{
+    if (!(qn > 0.0)) return INFINITY;
+    const double r = tol * cn / qn;
+    return 0.5 * (-Kdt + sqrt(Kdt * Kdt + 4.0 * r));
+}
+
+extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_adapt_stats* out)
+{
+    if (!ctx || !a || !(a->tol > 0.0) || a->M_min < 1 || a->M_max < a->M_min || !(a->safety > 0.0) ||
+        !(a->safety <= 1.0) || !(a->grow >= 1.0))
+        return PE_EINVAL;
+    pe_ctx* x = ctx;
+    const pe_config& c = x->cfg;
+    if (c.K < 2) return PE_EINVAL;
+    const double Kdt = c.K * c.dt;
+    auto bursts = [&](double dT) { return std::max(1, (int)floor(dT / Kdt + 1e-9)); };
+    int M = std::min(a->M_max, std::max(a->M_min, bursts(x->dT_cur)));
+    double* qc = (double*)(x->arena + x->lay.offset[PE_BUF_DIAG]);  // moments scratch, free here
+    const int64_t f0 = x->fine_steps;
+    int rejected = 0;
+    double err = 0.0, L_tol = 0.0;
+    for (;;) {
+        x->dT_cur = M * Kdt;
+        if (!x->fresh) PE_TRY(pe_lift(x));
+        PE_TRY(pe_burst(x));
+        PE_TRY(pe_restrict(x));
+        PE_TRY(pe_leap_curvature(x->csamples, c.K, (int32_t)x->ncoef, c.dt, qc, x->stream));
+        double h[3];
+        if (cudaMemcpyAsync(h, qc, sizeof(h), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess) return PE_ECUDA;
+        if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
+        const double L = x->dT_cur - Kdt;
+        err = h[1] > 0.0 ? h[0] * L * (L + Kdt) / h[1] : 0.0;
+        L_tol = leap_for_tol(h[0], h[1], Kdt, a->tol);
+        if (err > a->tol && M > a->M_min) {  // rejected: rerun from the same coarse state
+            const int Mt = bursts(Kdt + a->safety * L_tol);
+            M = std::max(a->M_min, std::min(M - 1, Mt));
+            rejected += 1;
+            continue;  // the burst consumed the lifted particles: pe_lift runs again
+        }
+        break;
+    }
+    const double taken = x->dT_cur;
+    PE_TRY(pe_project(x));
+    const double Mn = isinf(L_tol) ? (double)a->M_max : floor((Kdt + a->safety * L_tol) / Kdt + 1e-9);
+    const double cap = std::min((double)a->M_max, floor(a->grow * M + 1e-9));
+    const int M_next = (int)std::max((double)a->M_min, std::min(cap, Mn));
+    x->dT_cur = M_next * Kdt;
+    if (out) {
+        out->dT = taken;
+        out->err = err;
+        out->dT_next = x->dT_cur;
+        out->rejected = rejected;
+        out->fine_steps = (int32_t)(x->fine_steps - f0);
+    }
+    return PE_OK;
 }
 
 extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)

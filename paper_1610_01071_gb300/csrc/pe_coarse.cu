@@ -379,9 +379,68 @@ int launch_restrict_project_batch(const void* descs, int R, int K, double dt, do
     return launch_status();
 }
 
+// Curvature of a burst's coarse trajectory: per component the quadratic least-squares
+// coefficient q_i of the K+1 samples at tau_p = (p - K/2) dt on the basis {1, tau, g = tau^2 - m2}
+// (m2 the mean of tau^2; the three are orthogonal on the symmetric points):
+// q_i = sum_p g_p c_p,i / G with G = sum_p g_p^2, and its sampling variance
+// var_i = s_i^2 / G, s_i^2 the residual variance of the fit (K - 2 degrees of freedom).
+// out[0] = sqrt(max(0, sum q_i^2 - sum var_i)) (the curvature with the noise's bias removed),
+// out[1] = ||c_K||_2, out[2] = sqrt(sum var_i). One block; every sum in a fixed order.
+__global__ void __launch_bounds__(256) k_leap_curvature(const double* __restrict__ c, int K, int n, double dt,
+                                                        double* __restrict__ out)
+{
+    __shared__ double red[32];
+    const double m2 = dt * dt * (double)K * (double)(K + 2) / 12.0;
+    double G = 0.0, T2 = 0.0;
+    for (int p = 0; p <= K; ++p) {
+        const double tp = (p - 0.5 * K) * dt, g = tp * tp - m2;
+        G += g * g;
+        T2 += tp * tp;
+    }
+    double qq = 0.0, cc = 0.0, vv = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double a = 0.0, b = 0.0, q = 0.0;
+        for (int p = 0; p <= K; ++p) {
+            const double tp = (p - 0.5 * K) * dt, x = c[(size_t)p * n + i];
+            a += x;
+            b += tp * x;
+            q += (tp * tp - m2) * x;
+        }
+        a /= (K + 1);
+        b /= T2;
+        q /= G;
+        double rr = 0.0;
+        for (int p = 0; p <= K; ++p) {
+            const double tp = (p - 0.5 * K) * dt;
+            const double r = c[(size_t)p * n + i] - (a + b * tp + q * (tp * tp - m2));
+            rr += r * r;
+        }
+        const double cK = c[(size_t)K * n + i];
+        qq += q * q;
+        cc += cK * cK;
+        vv += K > 2 ? rr / (K - 2) / G : 0.0;
+    }
+    qq = block_sum_d(qq, red);
+    cc = block_sum_d(cc, red);
+    vv = block_sum_d(vv, red);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(fmax(0.0, qq - vv));
+        out[1] = sqrt(cc);
+        out[2] = sqrt(vv);
+    }
+}
+
 }  // namespace pe
 
 using namespace pe;
+
+extern "C" PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* out,
+                                        void* stream)
+{
+    if (!samples || !out || K < 2 || ncoef < 1 || !(dt > 0.0)) return PE_EINVAL;
+    k_leap_curvature<<<1, 256, 0, (cudaStream_t)stream>>>(samples, K, ncoef, dt, out);
+    return launch_status();
+}
 
 extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w, int32_t s_p,
                                  int32_t wavelet, int32_t n_coarse, int32_t bin_shift, double* coarse, void* stream)

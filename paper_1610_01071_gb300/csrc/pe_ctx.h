@@ -43,6 +43,7 @@ struct pe_ctx {
     int rho_valid;       // rho holds the deposit of the current particles
     int64_t macro_steps, fine_steps;
     double time;
+    double dT_cur;       // Delta t of the next macro step (the configured one unless set or adapted)
     int32_t* cell[2];
     float* theta[2];
     float* v[2];

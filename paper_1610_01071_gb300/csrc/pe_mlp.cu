@@ -977,7 +977,7 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     PE_TRY(pe_ctx_burst_range(x, 0, Ks, 1));
     PE_TRY(pe_coarsen(x->samples, Ks + 1, c.ncell, x->s_w, x->s_p, c.wavelet, x->nc, x->bin_shift, x->csamples,
                       x->stream));
-    PE_TRY(pe_gate(x->csamples, Ks, n, c.dt, c.dT, s_mlp, gc->tol, gc->noise_sigmas, x->coarse, x->slope, res,
+    PE_TRY(pe_gate(x->csamples, Ks, n, c.dt, x->dT_cur, s_mlp, gc->tol, gc->noise_sigmas, x->coarse, x->slope, res,
                    x->stream));
     GateResult r;
     if (cudaMemcpyAsync(&r, res, sizeof(r), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
@@ -992,7 +992,7 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     if (r.accepted) {
         out->fine_steps = Ks;
         x->macro_steps += 1;
-        x->time += c.dT;
+        x->time += x->dT_cur;
         x->fresh = 0;
         return PE_OK;
     }
