@@ -724,8 +724,10 @@ PE_API int pe_gate(const double* samples, int32_t K_probe, int32_t ncoef, double
  * double[3]). On a quadratic trajectory the least-squares slope is the derivative at the
  * burst's midpoint, so the forward-Euler leap of length L from c_K errs by exactly
  * q L (L + K dt): e(L) = out[0] L (L + K dt) / out[1] estimates the relative error of a leap.
- * K >= 2 (K = 2 leaves no residual: no noise correction). One block, fixed summation order. */
-PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* out, void* stream);
+ * K >= 2 (K = 2 leaves no residual: no noise correction). scratch: device, double[3 * 1024]
+ * (per-block partial sums). Every sum in a fixed order: repeated calls give identical bits. */
+PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* scratch,
+                             double* out, void* stream);
 
 /* pe_step_adaptive: one macro step whose Delta t is a whole number M of bursts, M K dt, chosen
  * from the estimate e of the previous step: lift (unless fresh), burst and restriction with

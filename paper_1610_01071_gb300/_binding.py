@@ -156,7 +156,7 @@ SIGNATURES = {
     "pe_get_slope": (ctypes.c_int, [P, P, i32]),
     "pe_export_f32": (ctypes.c_int, [P, i32, P]),
     "pe_step_surrogate": (ctypes.c_int, [P, P, ctypes.POINTER(GateCfg), ctypes.POINTER(GateStats)]),
-    "pe_leap_curvature": (ctypes.c_int, [P, i32, i32, f64, P, P]),
+    "pe_leap_curvature": (ctypes.c_int, [P, i32, i32, f64, P, P, P]),
     "pe_step_adaptive": (ctypes.c_int, [P, ctypes.POINTER(AdaptCfg), ctypes.POINTER(AdaptStats)]),
     "pe_set_macro_step": (ctypes.c_int, [P, f64]),
     "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
@@ -274,7 +274,8 @@ def leap_curvature(samples, dt, stream=None):
     (pe_leap_curvature), as a device tensor."""
     K1, n = samples.shape
     out = torch.empty(3, dtype=torch.float64, device=samples.device)
-    check(load().pe_leap_curvature(_ptr(samples), K1 - 1, n, float(dt), _ptr(out), _stream(stream)),
+    scratch = torch.empty(3 * 1024, dtype=torch.float64, device=samples.device)
+    check(load().pe_leap_curvature(_ptr(samples), K1 - 1, n, float(dt), _ptr(scratch), _ptr(out), _stream(stream)),
           "pe_leap_curvature")
     return out
 

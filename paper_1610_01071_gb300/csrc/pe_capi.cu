@@ -711,7 +711,9 @@ extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_ad
     const double Kdt = c.K * c.dt;
     auto bursts = [&](double dT) { return std::max(1, (int)floor(dT / Kdt + 1e-9)); };
     int M = std::min(a->M_max, std::max(a->M_min, bursts(x->dT_cur)));
-    double* qc = (double*)(x->arena + x->lay.offset[PE_BUF_DIAG]);  // moments scratch, free here
+    // the moments scratch (64 KB) is free here: partial sums, then the three results
+    double* part = (double*)(x->arena + x->lay.offset[PE_BUF_DIAG]);
+    double* qc = part + 3 * 1024;
     const int64_t f0 = x->fine_steps;
     int rejected = 0;
     double err = 0.0, L_tol = 0.0;
@@ -720,7 +722,7 @@ extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_ad
         if (!x->fresh) PE_TRY(pe_lift(x));
         PE_TRY(pe_burst(x));
         PE_TRY(pe_restrict(x));
-        PE_TRY(pe_leap_curvature(x->csamples, c.K, (int32_t)x->ncoef, c.dt, qc, x->stream));
+        PE_TRY(pe_leap_curvature(x->csamples, c.K, (int32_t)x->ncoef, c.dt, part, qc, x->stream));
         double h[3];
         if (cudaMemcpyAsync(h, qc, sizeof(h), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess) return PE_ECUDA;
         if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;

@@ -1,6 +1,8 @@
 // Coarse-variable kernels (FP64): restriction of the fine moment samples to wavelet
 // scaling coefficients, the least-squares projective leap, and the lifting profile.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -384,10 +386,15 @@ int launch_restrict_project_batch(const void* descs, int R, int K, double dt, do
 // (m2 the mean of tau^2; the three are orthogonal on the symmetric points):
 // q_i = sum_p g_p c_p,i / G with G = sum_p g_p^2, and its sampling variance
 // var_i = s_i^2 / G, s_i^2 the residual variance of the fit (K - 2 degrees of freedom).
+// Block b sums q_i^2, c_K,i^2 and var_i over its components (a fixed grid-stride partition)
+// into part[3 b ..]; the final block adds the partial sums in block order:
 // out[0] = sqrt(max(0, sum q_i^2 - sum var_i)) (the curvature with the noise's bias removed),
-// out[1] = ||c_K||_2, out[2] = sqrt(sum var_i). One block; every sum in a fixed order.
-__global__ void __launch_bounds__(256) k_leap_curvature(const double* __restrict__ c, int K, int n, double dt,
-                                                        double* __restrict__ out)
+// out[1] = ||c_K||_2, out[2] = sqrt(sum var_i). The FP64 work is spread over the SMs.
+constexpr int kCurvThreads = 256;
+constexpr int kCurvMaxBlocks = 1024;
+
+__global__ void __launch_bounds__(kCurvThreads) k_leap_curvature_part(const double* __restrict__ c, int K, int n,
+                                                                     double dt, double* __restrict__ part)
 {
     __shared__ double red[32];
     const double m2 = dt * dt * (double)K * (double)(K + 2) / 12.0;
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(256) k_leap_curvature(const double* __restrict
         T2 += tp * tp;
     }
     double qq = 0.0, cc = 0.0, vv = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double a = 0.0, b = 0.0, q = 0.0;
         for (int p = 0; p <= K; ++p) {
             const double tp = (p - 0.5 * K) * dt, x = c[(size_t)p * n + i];
@@ -424,22 +431,39 @@ __global__ void __launch_bounds__(256) k_leap_curvature(const double* __restrict
     cc = block_sum_d(cc, red);
     vv = block_sum_d(vv, red);
     if (threadIdx.x == 0) {
-        out[0] = sqrt(fmax(0.0, qq - vv));
-        out[1] = sqrt(cc);
-        out[2] = sqrt(vv);
+        part[3 * blockIdx.x] = qq;
+        part[3 * blockIdx.x + 1] = cc;
+        part[3 * blockIdx.x + 2] = vv;
     }
+}
+
+__global__ void k_leap_curvature_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double qq = 0.0, cc = 0.0, vv = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        qq += part[3 * b];
+        cc += part[3 * b + 1];
+        vv += part[3 * b + 2];
+    }
+    out[0] = sqrt(fmax(0.0, qq - vv));
+    out[1] = sqrt(cc);
+    out[2] = sqrt(vv);
 }
 
 }  // namespace pe
 
 using namespace pe;
 
-extern "C" PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* out,
-                                        void* stream)
+extern "C" PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* scratch,
+                                        double* out, void* stream)
 {
-    if (!samples || !out || K < 2 || ncoef < 1 || !(dt > 0.0)) return PE_EINVAL;
-    k_leap_curvature<<<1, 256, 0, (cudaStream_t)stream>>>(samples, K, ncoef, dt, out);
-    return launch_status();
+    if (!samples || !out || !scratch || K < 2 || ncoef < 1 || !(dt > 0.0)) return PE_EINVAL;
+    const int nb = std::min(kCurvMaxBlocks, (ncoef + kCurvThreads - 1) / kCurvThreads);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_leap_curvature_part<<<nb, kCurvThreads, 0, s>>>(samples, K, ncoef, dt, scratch);
+    k_leap_curvature_final<<<1, 32, 0, s>>>(scratch, nb, out);
+    return launch_status(2);
 }
 
 extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w, int32_t s_p,
