@@ -156,9 +156,18 @@ PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_e, int32_t 
  * density (pe_field). u_prof[j] = the ions' mean velocity at node j, m_j 2^-s_p / (n_j 2^-s_w),
  * from their nodal moment sample ion_moments (int64[2][ncell], density then momentum: pe_sample
  * with tau = 0 and bin_shift = 0, shifts s_w and s_p); 0 where n_j <= 0, and everywhere when
- * ion_moments is NULL. */
+ * ion_moments is NULL. u_prof may be NULL when ion_moments is: only n_prof is written (the
+ * caller's u_prof already holds the ions' velocity, e.g. the lifting profile). */
 PE_API int pe_boltzmann_profile(const double* phi, const int64_t* ion_moments, int32_t s_w, int32_t s_p,
                                 int32_t ncell, float* n_prof, float* u_prof, void* stream);
+
+/* Mean ion velocity of a phase-space coarse state at the nodes, for V_e = V_i when the ions are
+ * lifted from it (Section 3.3: the ion density and velocity follow by integrating the coarse
+ * distribution along v): per x-bin b the mean sum_k (v_min + (k + 1/2) dv) (F_b[k+1] - F_b[k])
+ * of its reconstructed CDF row (pe_ps_lift_tables' cdf[nxc][n_v + 1]), then linear between bin
+ * midpoints (periodic) into u_prof[ncell] (FP32); ncell = nxc 2^bin_shift. */
+PE_API int pe_ps_mean_velocity(const double* cdf, int32_t nxc, int32_t n_v, double v_min, double dv,
+                               int32_t bin_shift, int32_t ncell, float* u_prof, void* stream);
 
 /* Co-moving restriction sample, Appendix B (Eq. explicitflow and the deposit that
  * follows it): each particle, at its integer-time velocity Vbar, is carried to

@@ -105,7 +105,7 @@ def _load():
                                                  i32, i32, i32, P]),
                 "orc_burst_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, dbl,
                                              i32, i32, i32, dbl, dbl, i32, P, P, P]),
-                "orc_boltzmann_electrons": (None, [i64, i32, P, i64, P, P, P, P, dbl, u64, P, P, P, P]),
+                "orc_boltzmann_electrons": (None, [i64, i32, P, P, dbl, u64, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -732,19 +732,39 @@ def burst_kinetic(ions: State, electrons: State, ncell, dx, dt, qm_i, qm_e, K, d
     return (sfx if nv > 0 else sd), phi
 
 
-def boltzmann_electrons(N, ncell, phi, v_th_e, seed, ions: State = None):
-    """Electrons of the lifting: quiet start on n_e = exp(phi), drifting with the ions' nodal
-    mean velocity (V_e = V_i; no drift without ions)."""
+def ion_mean_velocity(ions: State, ncell):
+    """The ions' nodal mean velocity: CIC momentum over CIC density (0 where the density is 0)."""
+    d, m = deposit_f64(ions.cell, ions.theta, ions.w, ncell, vel=ions.v)
+    return np.where(d > 0, m / np.where(d > 0, d, 1.0), 0.0)
+
+
+def boltzmann_electrons(N, ncell, phi, v_th_e, seed, u=None, ions: State = None):
+    """Electrons of the lifting: quiet start on n_e = exp(phi) drifting with the ions' mean
+    velocity u (V_e = V_i), or with that of the particles `ions`; no drift without either."""
     phi = _f64(phi)
+    if u is None and ions is not None:
+        u = ion_mean_velocity(ions, ncell)
+    ua = _f64(u) if u is not None else None
     cell = np.zeros(N, np.int32)
     theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
-    if ions is not None:
-        ia = (ions.n, _p(ions.cell), _p(ions.theta), _p(ions.v), _p(ions.w))
-    else:
-        ia = (0, None, None, None, None)
-    _load().orc_boltzmann_electrons(N, ncell, _p(phi), *ia, float(v_th_e), seed & 0xFFFFFFFFFFFFFFFF, _p(cell),
-                                    _p(theta), _p(v), _p(w))
+    _load().orc_boltzmann_electrons(N, ncell, _p(phi), _p(ua) if ua is not None else None, float(v_th_e),
+                                    seed & 0xFFFFFFFFFFFFFFFF, _p(cell), _p(theta), _p(v), _p(w))
     return State(cell, theta, v, w)
+
+
+def ps_mean_velocity(cdf, vmin, dv, bin_shift, ncell):
+    """Nodal mean ion velocity of a phase-space state: per x-bin the mean of its reconstructed
+    CDF row over cell centres, then linear between bin midpoints (periodic)."""
+    cdf = _f64(cdf)
+    nxc, nv = cdf.shape[0], cdf.shape[1] - 1
+    vc = vmin + (np.arange(nv) + 0.5) * dv
+    ub = np.sum(vc * np.diff(cdf, axis=1), axis=1)
+    B = 2 ** bin_shift
+    t = (np.arange(ncell) - 0.5 * (B - 1)) / B
+    b0 = np.floor(t)
+    f = t - b0
+    b0 = b0.astype(np.int64) % nxc
+    return (1 - f) * ub[b0] + f * ub[(b0 + 1) % nxc]
 
 
 # ------------------------------------------------------------------ adaptive macro step

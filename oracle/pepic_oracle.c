@@ -911,27 +911,17 @@ void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const do
 
 /* Electrons of the lifting (Section 3.3, Eq. electronpassive: n_e = n_0 exp(phi), V_e = V_i,
  * T_e = T_e0): density exp(phi) of the Poisson-Boltzmann potential of the ion density, mean
- * velocity the ions' at each node (their CIC momentum over their CIC density, from velocities v_i;
- * zero where the ion density vanishes, and everywhere when ni = 0), Maxwellian of thermal speed
- * v_th_e, quiet start on that profile. */
-void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, int64_t ni, const int32_t* ci,
-                             const double* ti, const double* vi, const double* wi, double v_th_e, uint64_t seed,
-                             int32_t* cell, double* theta, double* v, double* w)
+ * velocity u[ncell] the ions' (NULL: none), Maxwellian of thermal speed v_th_e, quiet start on
+ * that profile. */
+void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, const double* u, double v_th_e,
+                             uint64_t seed, int32_t* cell, double* theta, double* v, double* w)
 {
     double* n = (double*)malloc(sizeof(double) * (size_t)ncell);
-    double* u = (double*)calloc((size_t)ncell, sizeof(double));
-    double* dens = (double*)malloc(sizeof(double) * (size_t)ncell);
-    double* mom = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* u0 = (double*)calloc((size_t)ncell, sizeof(double));
     for (int32_t j = 0; j < ncell; ++j) n[j] = exp(phi[j]);
-    if (ni > 0) {
-        orc_deposit_f64(ni, ci, ti, wi, vi, ncell, dens, mom);
-        for (int32_t j = 0; j < ncell; ++j) u[j] = dens[j] > 0.0 ? mom[j] / dens[j] : 0.0;
-    }
-    orc_quiet_start(N, ncell, n, u, v_th_e, seed, cell, theta, v, w);
+    orc_quiet_start(N, ncell, n, u ? u : u0, v_th_e, seed, cell, theta, v, w);
     free(n);
-    free(u);
-    free(dens);
-    free(mom);
+    free(u0);
 }
 
 /* ---------------------------------------------------------------- bounded domain

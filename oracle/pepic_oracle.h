@@ -244,9 +244,8 @@ void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const do
                        double qm_i, double qm_e, int32_t K, double dT, int32_t s_w, int32_t vel_at_integer,
                        int32_t bin_shift, double vmin, double dv, int32_t nv, double* phi, double* samples,
                        int64_t* samples_fx);
-void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, int64_t ni, const int32_t* ci,
-                             const double* ti, const double* vi, const double* wi, double v_th_e, uint64_t seed,
-                             int32_t* cell, double* theta, double* v, double* w);
+void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, const double* u, double v_th_e,
+                             uint64_t seed, int32_t* cell, double* theta, double* v, double* w);
 
 #ifdef __cplusplus
 }

@@ -121,6 +121,7 @@ SIGNATURES = {
     "pe_field_ex": (ctypes.c_int, [P, i32, f64, i32, i32, i32, f64, i32, P, P, P, P, P, P]),
     "pe_field_kinetic": (ctypes.c_int, [P, P, i32, f64, i32, P, P, P, P]),
     "pe_boltzmann_profile": (ctypes.c_int, [P, P, i32, i32, i32, P, P, P]),
+    "pe_ps_mean_velocity": (ctypes.c_int, [P, i32, i32, f64, f64, i32, i32, P, P]),
     "pe_push": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, P, ctypes.POINTER(SampleArgs), P, P]),
     "pe_push_ex": (ctypes.c_int, [P, P, P, P, i64, P, i32, f32, f32, f32, i32, i32, P, ctypes.POINTER(SampleArgs),
                                   P, P]),
@@ -267,6 +268,15 @@ def field_kinetic(rho_i, rho_e, ncell, dx, s_w, phi=None, stream=None):
     check(load().pe_field_kinetic(_ptr(rho_i), _ptr(rho_e), ncell, float(dx), int(s_w), _ptr(phi), _ptr(E), _ptr(Ef),
                                   _stream(stream)), "pe_field_kinetic")
     return phi, E, Ef
+
+
+def ps_mean_velocity(cdf, v_min, dv, bin_shift, ncell, stream=None):
+    """Nodal mean ion velocity (float32 [ncell]) of phase-space CDF rows cdf [nxc, n_v + 1]."""
+    nxc, nv1 = cdf.shape
+    u = torch.empty(ncell, dtype=torch.float32, device=cdf.device)
+    check(load().pe_ps_mean_velocity(_ptr(cdf), nxc, nv1 - 1, float(v_min), float(dv), int(bin_shift), ncell, _ptr(u),
+                                     _stream(stream)), "pe_ps_mean_velocity")
+    return u
 
 
 def leap_curvature(samples, dt, stream=None):

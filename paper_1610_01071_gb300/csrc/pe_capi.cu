@@ -393,32 +393,43 @@ static int deposit_current(pe_ctx* x)
 // their deposit in rho_e.
 static uint64_t electron_seed(uint64_t s) { return s ^ 0xD1B54A32D192ED03ULL; }
 
-static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed)
+// Where the ions' mean velocity for V_e = V_i comes from: the lifting profile already in
+// PE_BUF_PROFILE's u half (a load or a moment lift), the phase-space coarse state (a
+// phase-space lift), or a moment sample of the ion particles (a plain-PIC reset).
+enum ElectronDrift { kDriftProfile, kDriftPhaseSpace, kDriftParticles };
+
+static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed, ElectronDrift drift)
 {
     const pe_config& c = x->cfg;
-    // the ions' nodal density and momentum at their stored velocities (kick 1/2: Vbar = v; at
-    // integer time after a load or lift, half a step earlier in a plain-PIC reset), for V_e = V_i
-    int64_t* mom = x->rho_e + c.ncell;
-    pe_sample_args a;
-    memset(&a, 0, sizeof(a));
-    a.E0f = x->Ef;  // tau = 0: the frame field is not used
-    a.qm = (float)c.qm;
-    a.inv_dx = (float)(1.0 / x->dx);
-    a.s_w = x->s_w;
-    a.s_p = x->s_p;
-    a.sample_fx = mom;
-    a.boundary = c.boundary;
-    const int b = x->bank;
-    PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), 0.5f,
-                     &a, x->status, x->stream));
+    float* u = x->prof + c.ncell;
+    int64_t* mom = nullptr;
+    if (drift == kDriftParticles) {
+        // the ions' nodal density and momentum at their stored velocities (kick 1/2: Vbar = v,
+        // half a step before integer time in a plain-PIC reset)
+        mom = x->rho_e + c.ncell;
+        pe_sample_args a;
+        memset(&a, 0, sizeof(a));
+        a.E0f = x->Ef;  // tau = 0: the frame field is not used
+        a.qm = (float)c.qm;
+        a.inv_dx = (float)(1.0 / x->dx);
+        a.s_w = x->s_w;
+        a.s_p = x->s_p;
+        a.sample_fx = mom;
+        a.boundary = c.boundary;
+        const int b = x->bank;
+        PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell,
+                         (float)(c.qm * c.dt), 0.5f, &a, x->status, x->stream));
+    } else if (drift == kDriftPhaseSpace) {
+        PE_TRY(pe_ps_mean_velocity(x->ps_cdf, x->nc, x->nv, x->vmin, x->dv, x->bin_shift, c.ncell, u, x->stream));
+    }
     PE_TRY(field_solve_history(x->rho, c.ncell, x->dx, x->s_w, PE_POISSON_BOLTZMANN, PE_BOUNDARY_PERIODIC,
                                c.newton_tol, c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, nullptr, 0,
                                x->stream));
-    PE_TRY(pe_boltzmann_profile(x->phi, mom, x->s_w, x->s_p, c.ncell, x->prof, x->prof + c.ncell, x->stream));
+    PE_TRY(pe_boltzmann_profile(x->phi, mom, x->s_w, x->s_p, c.ncell, x->prof, mom ? u : nullptr, x->stream));
     const int e = x->ebank;
     PE_TRY(timed(x, 0, [&] {
-        return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof,
-                              x->prof + c.ncell, (float)x->v_th_e, seed, x->s_w, x->rho_e, x->status, x->stream);
+        return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof, u,
+                              (float)x->v_th_e, seed, x->s_w, x->rho_e, x->status, x->stream);
     }));
     x->e_v_at_integer = 1;
     return PE_OK;
@@ -560,7 +571,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     PE_TRY(quiet_start_from_profile(x, c.seed, 1.0f));
     if (x->kinetic) {
         x->ebank = 0;
-        PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed)));
+        PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed), kDriftProfile));
     }
     if (x->ps) return measure_phase(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
@@ -671,7 +682,8 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
         PE_TRY(quiet_start_from_profile(x, lift_seed(x), 2.0f));  // refined restriction: wall nodes hold deposits
     }
-    if (x->kinetic) PE_TRY(load_boltzmann_electrons(x, electron_seed(lift_seed(x))));
+    if (x->kinetic)
+        PE_TRY(load_boltzmann_electrons(x, electron_seed(lift_seed(x)), x->ps ? kDriftPhaseSpace : kDriftProfile));
     return PE_OK;
 }
 
@@ -774,7 +786,8 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
         }
         if (!x->rho_valid) PE_TRY(deposit_current(x));
         if (x->kinetic && c.reset_every > 0 && (x->fine_steps % c.reset_every) == 0 && !x->fresh)
-            PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed + 0x9E3779B97F4A7C15ULL * (uint64_t)x->fine_steps)));
+            PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed + 0x9E3779B97F4A7C15ULL * (uint64_t)x->fine_steps),
+                                            kDriftParticles));
         PE_TRY(field_solve(x, 1));
         const int b = x->bank;
         const float kick = x->v_at_integer ? 0.5f : 1.0f;

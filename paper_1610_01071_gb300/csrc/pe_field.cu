@@ -655,12 +655,14 @@ __global__ void k_boltzmann_profile(const double* phi, const long long* mom, int
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) {
         nprof[j] = (float)exp(phi[j]);
-        float u = 0.0f;
-        if (mom) {  // V_e = V_i: the ions' momentum over their density at the node
-            const long long d = mom[j], m = mom[n + j];
-            if (d > 0) u = (float)((double)m / (double)d * vscale);
+        if (uprof) {
+            float u = 0.0f;
+            if (mom) {  // V_e = V_i: the ions' momentum over their density at the node
+                const long long d = mom[j], m = mom[n + j];
+                if (d > 0) u = (float)((double)m / (double)d * vscale);
+            }
+            uprof[j] = u;
         }
-        uprof[j] = u;
     }
 }
 
@@ -681,7 +683,8 @@ extern "C" PE_API int pe_field_kinetic(const int64_t* rho_i, const int64_t* rho_
 extern "C" PE_API int pe_boltzmann_profile(const double* phi, const int64_t* ion_moments, int32_t s_w, int32_t s_p,
                                            int32_t ncell, float* n_prof, float* u_prof, void* stream)
 {
-    if (!is_pow2(ncell) || ncell < 8 || ncell > kFullGridMax || !phi || !n_prof || !u_prof) return PE_EINVAL;
+    if (!is_pow2(ncell) || ncell < 8 || ncell > kFullGridMax || !phi || !n_prof || (ion_moments && !u_prof))
+        return PE_EINVAL;
     k_boltzmann_profile<<<(ncell + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
         phi, reinterpret_cast<const long long*>(ion_moments), ncell, ldexp(1.0, s_w - s_p), n_prof, u_prof);
     return launch_status();

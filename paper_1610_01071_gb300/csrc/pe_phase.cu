@@ -664,6 +664,47 @@ extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_
     return launch_status(2);
 }
 
+namespace pe {
+namespace {
+
+// Mean velocity of the reconstructed distribution of bin b (cells of width dv from v_min,
+// cell k holding F[k+1] - F[k] of the bin's mass), then linear between bin midpoints (periodic)
+// at the nodes.
+__device__ double ps_bin_mean(const double* cdf, int b, int nv, double vmin, double dv)
+{
+    const double* F = cdf + (size_t)b * (nv + 1);
+    double m = 0.0;
+    for (int k = 0; k < nv; ++k) m += (vmin + (k + 0.5) * dv) * (F[k + 1] - F[k]);
+    return m;
+}
+
+__global__ void k_ps_mean_velocity(const double* __restrict__ cdf, int nxc, int nv, double vmin, double dv,
+                                   int bin_shift, int ncell, float* __restrict__ u)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncell) return;
+    const double B = (double)(1 << bin_shift);
+    const double t = ((double)j - 0.5 * (B - 1.0)) / B;  // bin-midpoint coordinate of node j
+    const double f0 = floor(t);
+    const double f = t - f0;
+    const int b0 = (((int)f0) % nxc + nxc) % nxc, b1 = (b0 + 1) % nxc;
+    u[j] = (float)((1.0 - f) * ps_bin_mean(cdf, b0, nv, vmin, dv) + f * ps_bin_mean(cdf, b1, nv, vmin, dv));
+}
+
+}  // namespace
+}  // namespace pe
+
+extern "C" PE_API int pe_ps_mean_velocity(const double* cdf, int32_t nxc, int32_t n_v, double v_min, double dv,
+                                          int32_t bin_shift, int32_t ncell, float* u_prof, void* stream)
+{
+    if (!cdf || !u_prof || nxc < 1 || n_v < 1 || !(dv > 0.0) || bin_shift < 0 || !is_pow2(ncell) ||
+        (int64_t)nxc << bin_shift != ncell)
+        return PE_EINVAL;
+    pe::k_ps_mean_velocity<<<(ncell + 255) / 256, 256, 0, (cudaStream_t)stream>>>(cdf, nxc, n_v, v_min, dv, bin_shift,
+                                                                                  ncell, u_prof);
+    return launch_status(1);
+}
+
 extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
                                         int32_t bin_shift, const double* mass, const float* table, int32_t n_v,
                                         double v_min, double dv, uint64_t seed, int32_t s_w, int64_t* rho_fx,

@@ -88,17 +88,22 @@ def oracle_ions(cfg, seed):
                            float(np.float32(cfg["v_th"])), seed)
 
 
-def oracle_electrons(cfg, ions, s_w, seed, phi0=None):
+def oracle_electrons(cfg, ions, s_w, seed, u=None):
     # the loading of the library: Poisson-Boltzmann potential of the ion deposit, then the
-    # quiet start on the FP32 profiles exp(phi) and the ions' nodal mean velocity (V_e = V_i)
+    # quiet start on the FP32 profiles exp(phi) and the ions' mean velocity (V_e = V_i): the
+    # given lifting profile u, else the ion particles' nodal mean velocity (a plain-PIC reset)
     ncell = cfg["ncell"]
     dx = cfg["L"] / ncell
     dens = orc.deposit_fx(ions.cell, ions.theta, ions.w, ncell, s_w) * 2.0 ** -(s_w + 24)
-    phi = orc.newton_pb(dens, dx, phi0=np.zeros(ncell) if phi0 is None else phi0, tol=1e-11)[0]
+    phi = orc.newton_pb(dens, dx, phi0=np.zeros(ncell), tol=1e-11)[0]
     prof = np.exp(phi).astype(np.float32)
-    d, m = orc.deposit_f64(ions.cell, ions.theta, ions.w, ncell, vel=ions.v)
-    u = np.where(d > 0, m / np.where(d > 0, d, 1.0), 0.0).astype(np.float32)
-    return orc.quiet_start(cfg["N"], ncell, prof, u, V_TH_E, seed)
+    if u is None:
+        u = orc.ion_mean_velocity(ions, ncell)
+    return orc.quiet_start(cfg["N"], ncell, prof, np.asarray(u).astype(np.float32), V_TH_E, seed)
+
+
+def sine_u(cfg):
+    return orc.sine_profile(cfg["ncell"], cfg["L"], cfg["amp"])[1]
 
 
 def state_of(ctx, species):
@@ -121,7 +126,7 @@ def test_load_places_boltzmann_electrons_like_the_oracle():
     assert ctx.sync_status() == 0
     d = ctx.diagnostics()
     ions = oracle_ions(cfg, 3)
-    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(3))
+    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(3), u=sine_u(cfg))
     gi, ge = state_of(ctx, "ions"), state_of(ctx, "electrons")
     assert np.array_equal(gi.cell, ions.cell) and np.array_equal(ge.cell, elec.cell)
     assert np.array_equal(ge.theta, elec.theta.astype(np.float32))
@@ -147,7 +152,7 @@ def test_plain_two_species_pic_matches_oracle(reset_every):
     s_w = d.s_w
     ncell, dx = cfg["ncell"], cfg["L"] / cfg["ncell"]
     ions = oracle_ions(cfg, seed)
-    elec = oracle_electrons(cfg, ions, s_w, electron_seed(seed))
+    elec = oracle_electrons(cfg, ions, s_w, electron_seed(seed), u=sine_u(cfg))
     done, v_int, e_int = 0, True, True
     while done < nsteps:
         if reset_every and done > 0 and done % reset_every == 0:
@@ -176,7 +181,7 @@ def test_kinetic_macro_step_matches_oracle():
     dx = cfg["L"] / ncell
     dT = cfg["M"] * K * cfg["dt"]
     ions = oracle_ions(cfg, seed)
-    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(seed))
+    elec = oracle_electrons(cfg, ions, d.s_w, electron_seed(seed), u=sine_u(cfg))
     samples, _ = orc.burst_kinetic(ions, elec, ncell, dx, cfg["dt"], 1.0, QM_E, K, dT, d.s_w)
     cs = np.stack([np.concatenate([orc.coarsen(samples[p, 0], nc), orc.coarsen(samples[p, 1], nc)])
                    for p in range(K + 1)])
@@ -193,15 +198,62 @@ def test_kinetic_lift_reloads_boltzmann_electrons():
     ctx = make_kinetic(cfg, seed=11)
     ctx.load_initial(cfg["amp"])
     ctx.step()
+    coarse = ctx.get_coarse().cpu().numpy()
     ctx.lift()
     assert ctx.sync_status() == 0
     d = ctx.diagnostics()
     assert d.e_v_at_integer == 1 and d.v_at_integer == 1
     gi = state_of(ctx, "ions")
-    # electrons in equilibrium with the lifted ions (the GPU's own lifted ions as input)
+    # electrons in equilibrium with the lifted ions (the GPU's own lifted ions as input), drifting
+    # with the lifting profile's velocity u = m / n of the refined coarse state
+    ncell = cfg["ncell"]
+    _, u = orc.lift_profile(orc.refine(coarse[0], ncell), orc.refine(coarse[1], ncell))
     lift_seed = (11 + 0x632BE59BD9B4E019 * (d.macro_steps + 1)) & MASK64
-    elec = oracle_electrons(cfg, gi, d.s_w, electron_seed(lift_seed))
-    assert_states_close(state_of(ctx, "electrons"), elec, cfg["ncell"], V_TH_E, "electrons")
+    elec = oracle_electrons(cfg, gi, d.s_w, electron_seed(lift_seed), u=u)
+    assert_states_close(state_of(ctx, "electrons"), elec, ncell, V_TH_E, "electrons")
+
+
+def test_ps_mean_velocity_matches_oracle():
+    rng = np.random.default_rng(4)
+    nxc, nv, b = 64, 32, 2
+    p = rng.uniform(0.0, 1.0, (nxc, nv))
+    cdf = np.concatenate([np.zeros((nxc, 1)), np.cumsum(p, axis=1) / p.sum(axis=1, keepdims=True)], axis=1)
+    got = pe._binding.ps_mean_velocity(torch.from_numpy(cdf).to(DEV), -3.0, 6.0 / nv, b, nxc << b).cpu().numpy()
+    want = orc.ps_mean_velocity(cdf, -3.0, 6.0 / nv, b, nxc << b)
+    assert np.allclose(got, want.astype(np.float32), rtol=2e-6, atol=1e-7)
+    # a symmetric distribution has no drift; all mass in one cell drifts at its centre
+    sym = np.linspace(0, 1, nv + 1)[None, :].repeat(nxc, 0)
+    assert np.abs(pe._binding.ps_mean_velocity(torch.from_numpy(sym).to(DEV), -3.0, 6.0 / nv, b,
+                                               nxc << b).cpu().numpy()).max() < 1e-6
+    one = np.zeros((nxc, nv + 1))
+    one[:, 10:] = 1.0
+    u1 = pe._binding.ps_mean_velocity(torch.from_numpy(one).to(DEV), -3.0, 6.0 / nv, b, nxc << b).cpu().numpy()
+    assert np.allclose(u1, -3.0 + 9.5 * 6.0 / nv, atol=1e-6)
+
+
+def test_phase_space_lift_gives_the_electrons_the_ions_drift():
+    cfg = KIN
+    dT = cfg["M"] * cfg["K"] * cfg["dt"]
+    c = pe.make_config(cfg["ncell"], cfg["n_coarse"], cfg["K"], cfg["N"], cfg["L"], cfg["dt"], dT, qm=1.0,
+                       v_th=cfg["v_th"], seed=12, newton_tol=1e-11, electrons="kinetic", coarse="phase_space",
+                       n_v=32, v_max=2.0, ps_filter=3)
+    ctx = pe.Context(c, device=DEV)
+    ctx.load_initial(cfg["amp"])
+    ctx.step()
+    ctx.lift()
+    assert ctx.sync_status() == 0
+    d = ctx.diagnostics()
+    gi = state_of(ctx, "ions")
+    ncell, nc, nv = cfg["ncell"], cfg["n_coarse"], 32
+    # V_e = V_i from the lifted phase-space tables: the library's reconstructed CDF rows (in the
+    # phase buffer after the bin masses) through the oracle's mean velocity
+    off = ((8 * nc + 255) // 256) * 256 // 8
+    cdf = ctx.view("phase", torch.float64)[off:off + nc * (nv + 1)].cpu().numpy().reshape(nc, nv + 1)
+    u = orc.ps_mean_velocity(cdf, -2.0, 4.0 / nv, 2, ncell)
+    lift_seed = (12 + 0x632BE59BD9B4E019 * (d.macro_steps + 1)) & MASK64
+    elec = oracle_electrons(cfg, gi, d.s_w, electron_seed(lift_seed), u=u)
+    assert_states_close(state_of(ctx, "electrons"), elec, ncell, V_TH_E, "electrons")
+    assert np.abs(u).max() > 0.05  # the ion wave's drift is there to be carried
 
 
 def test_kinetic_contexts_are_not_batched():
@@ -230,3 +282,40 @@ def test_kinetic_diagnostics_cover_both_species_and_conserve_energy():
     # momentum (ions plus electrons of mass w / |q_e/m_e|) up to the fixed-point deposit
     assert abs(m1["total_energy"] - m0["total_energy"]) < 1e-3 * m0["total_energy"]
     assert abs(m1["momentum"] - m0["momentum"]) < 1e-4 * cfg["L"] * cfg["amp"]
+
+
+def test_kinetic_full_size_properties():
+    # the bench's iaw_kinetic workload at full size (2^23 ions + 2^23 electrons, 1024 cells):
+    # both species' fixed-point charge is conserved exactly through pushes and sorts, the field
+    # of the actual deposits matches the oracle's Poisson solve, and macro steps run clean
+    from paper_1610_01071_gb300 import inputs
+
+    w = inputs.workload("iaw_kinetic")
+    c = pe.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"],
+                       v_th=w["v_th"], seed=11, sort_every=20, newton_tol=1e-10, coarse="phase_space", n_v=w["n_v"],
+                       v_max=w["v_max"], ps_filter=3, electrons="kinetic", qm_e=w["qm_e"])
+    ctx = pe.Context(c, device=DEV)
+    ctx.load_initial(w["amplitude"])
+    ncell = w["ncell"]
+
+    def charge(name):
+        return int(ctx.view(name, torch.int64, ncell).cpu().numpy().sum(dtype=object))
+
+    qi0, qe0 = charge("rho"), charge("rho_e")
+    assert abs(qe0 - qi0) <= 1e-6 * qi0  # the Boltzmann electrons balance the ions
+    m0 = ctx.moments()
+    ctx.pic_steps(45)  # crosses two sorts
+    assert ctx.sync_status() == 0
+    assert (charge("rho"), charge("rho_e")) == (qi0, qe0)
+    m1 = ctx.moments()
+    assert abs(m1["total_energy"] - m0["total_energy"]) < 1e-3 * m0["total_energy"]
+    s_w = ctx.diagnostics().s_w
+    rho_i = ctx.view("rho", torch.int64, ncell).cpu().numpy()
+    rho_e = ctx.view("rho_e", torch.int64, ncell).cpu().numpy()
+    _, E_o = orc.poisson_periodic((rho_i - rho_e).astype(np.float64) * 2.0 ** -(s_w + 24), w["L"] / ncell)
+    E = ctx.view("E", torch.float64, ncell).cpu().numpy()
+    assert np.abs(E - E_o).max() <= 1e-10 * np.abs(E_o).max()
+    ctx.step()
+    ctx.step()
+    assert ctx.sync_status() == 0
+    assert np.all(np.isfinite(ctx.get_coarse().cpu().numpy()))
