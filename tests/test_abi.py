@@ -82,3 +82,44 @@ def test_kinetic_electron_layout_and_checks(lib):
     lay0 = b.layout(b.make_config(*base))
     assert lay0.bytes[b.BUF["electrons_a"]] == 0 and lay0.bytes[b.BUF["rho_e"]] == 0
     assert lay.total_bytes >= lay0.total_bytes + 2 * bank
+
+
+def test_a_c_program_links_and_calls_the_host_entry_points(lib, tmp_path):
+    # the boundary is plain C: a C99 program includes the header, links libpepic and calls the
+    # host-only entry points (no GPU needed)
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "pepic.h"
+int main(void) {
+    pe_config c;
+    memset(&c, 0, sizeof c);
+    c.ncell = 4096; c.n_coarse = 256; c.wavelet = PE_WAVELET_HAAR; c.K = 20;
+    c.nparticles = (int64_t)1 << 24; c.L = 2048.0; c.dt = 0.1; c.dT = 20.0; c.qm = 1.0; c.v_th = 1.0;
+    c.comoving = 1; c.poisson = PE_POISSON_BOLTZMANN; c.newton_tol = 1e-10; c.newton_maxit = 50;
+    pe_layout lay;
+    int rc = pe_layout_for(&c, &lay);
+    c.ncell = 4000;
+    int bad = pe_layout_for(&c, &lay);
+    printf("%s|%d|%d|%s|%zu\n", pe_version(), rc, bad, pe_strerror(PE_EINVAL), lay.total_bytes > 0 ? (size_t)1 : (size_t)0);
+    return rc == PE_OK && bad == PE_EINVAL ? 0 : 1;
+}
+""")
+    libdir = os.path.join(ROOT, "paper_1610_01071_gb300")
+    exe = tmp_path / "abi"
+    cuda_lib = "/usr/local/cuda/lib64"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe), "-L", libdir, "-lpepic", "-Wl,-rpath," + libdir, "-Wl,-rpath," + cuda_lib],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, run.stdout + run.stderr
+    version, rc, bad, msg, _ = run.stdout.strip().split("|")
+    assert version.startswith("pepic") and rc == "0" and bad == "1" and msg
