@@ -134,8 +134,11 @@ __device__ __forceinline__ void mirror(int N, const double* F, double* G)
     for (int k = 0; k <= N; ++k) G[k] = sub_(1.0, F[N - k]);
 }
 
-// Reconstruction of one CDF row F[0..N] in place; G and P are scratch rows of N + 1.
-__device__ int reconstruct(int N, double* F, double* G, double* P)
+// Reconstruction of one CDF row F[0..N] (Appendix C), in three parts so that the two
+// interior passes, which are independent, can run on two lanes: reconstruct_edges fixes both
+// edges of F (clamped if an edge had no admissible range) and leaves P = F and G = mirror(F);
+// interior_fwd then runs on P and on G; reconstruct_join sets F = (P + mirror(G)) / 2.
+__device__ int reconstruct_edges(int N, double* F, double* G, double* P)
 {
     int bad = 0;
     F[0] = 0.0;
@@ -147,12 +150,14 @@ __device__ int reconstruct(int N, double* F, double* G, double* P)
     if (bad)
         for (int k = 0; k <= N; ++k) F[k] = F[k] < 0.0 ? 0.0 : (F[k] > 1.0 ? 1.0 : F[k]);
     for (int k = 0; k <= N; ++k) P[k] = F[k];
-    bad |= interior_fwd(N, P);
     mirror(N, F, G);
-    bad |= interior_fwd(N, G);
+    return bad;
+}
+
+__device__ void reconstruct_join(int N, double* F, const double* G, const double* P)
+{
     mirror(N, G, F);
     for (int k = 0; k <= N; ++k) F[k] = mul_(0.5, add_(P[k], F[k]));
-    return bad;
 }
 
 }  // namespace
@@ -167,30 +172,51 @@ namespace {
 // cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells' relative density
 // slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1]. The reconstruction, whose
 // loops reread the row many times, works on three rows per thread in shared memory.
-__global__ void __launch_bounds__(32) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
+__global__ void __launch_bounds__(64) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
                                               double* __restrict__ mass, double* __restrict__ cdf,
                                               float* __restrict__ table, int32_t* __restrict__ flags)
 {
     extern __shared__ double rows[];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nxc) return;
-    double* F = rows + (size_t)threadIdx.x * 3 * (nv + 1);
+    // two lanes per bin (neighbours in one warp): lane 0 does the serial parts, the two
+    // interior passes run one per lane
+    const int half = threadIdx.x & 1, local = threadIdx.x >> 1;
+    const int i = blockIdx.x * (blockDim.x >> 1) + local;
+    const bool valid = i < nxc;
+    double* F = rows + (size_t)local * 3 * (nv + 1);
     double* G = F + nv + 1;
     double* Pr = G + nv + 1;
-    const double* h = H + (size_t)i * nv;
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = add_(s, h[j]);
-    mass[i] = s;
-    if (s > 0.0) {
-        double r = 0.0;
-        F[0] = 0.0;
-        for (int j = 0; j < nv; ++j) {
-            r = add_(r, h[j]);
-            F[j + 1] = div_(r, s);
+    int bad = 0, positive = 0;
+    if (valid && half == 0) {
+        const double* h = H + (size_t)i * nv;
+        double s = 0.0;
+        for (int j = 0; j < nv; ++j) s = add_(s, h[j]);
+        mass[i] = s;
+        if (s > 0.0) {
+            positive = 1;
+            double r = 0.0;
+            F[0] = 0.0;
+            for (int j = 0; j < nv; ++j) {
+                r = add_(r, h[j]);
+                F[j + 1] = div_(r, s);
+            }
+            bad = reconstruct_edges(nv, F, G, Pr);
+        } else {
+            for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
         }
-        if (reconstruct(nv, F, G, Pr) && flags) atomicOr(flags, 1);
-    } else {
-        for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
+    }
+    // the lanes of this warp that exist (blocks smaller than a warp for wide rows; the block
+    // size is even, so both lanes of a pair exist)
+    const int wfirst = threadIdx.x & ~31, wlanes = min(32, (int)blockDim.x - wfirst);
+    const unsigned wmask = wlanes == 32 ? 0xffffffffu : ((1u << wlanes) - 1u);
+    __syncwarp(wmask);
+    positive = __shfl_sync(wmask, positive, (threadIdx.x & 31) & ~1);
+    if (valid && positive) bad |= interior_fwd(nv, half == 0 ? Pr : G);
+    __syncwarp(wmask);
+    bad |= __shfl_xor_sync(wmask, bad, 1);
+    if (!valid || half != 0) return;
+    if (positive) {
+        reconstruct_join(nv, F, G, Pr);
+        if (bad && flags) atomicOr(flags, 1);
     }
     double* out = cdf + (size_t)i * (nv + 1);
     for (int k = 0; k <= nv; ++k) out[k] = F[k];
@@ -653,13 +679,14 @@ extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_
     if (!H || !mass || !cdf || !table || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
-    // three FP64 rows of n_v + 1 per thread; up to 32 threads, fewer for wide rows (<= 192 KB)
+    // three FP64 rows of n_v + 1 per bin, two threads per bin; up to 32 bins per block, fewer
+    // for wide rows (<= 192 KB)
     const size_t row3 = 3 * sizeof(double) * ((size_t)n_v + 1);
     int per_block = (int)std::min<size_t>(32, (size_t)(192 * 1024) / row3);
     if (per_block < 1) return PE_EINVAL;
     const size_t smem = row3 * (size_t)per_block;
     if (ensure_smem((const void*)k_ps_cdf, smem) != PE_OK) return PE_ECUDA;
-    k_ps_cdf<<<(nxc + per_block - 1) / per_block, per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
+    k_ps_cdf<<<(nxc + per_block - 1) / per_block, 2 * per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
     k_ps_mass<<<1, 1024, 0, s>>>(nxc, mass);
     return launch_status(2);
 }

@@ -78,8 +78,8 @@ def _noisy_hist(nxc, nv, seed):
     return H
 
 
-@pytest.mark.parametrize("nxc,nv", [(8, 16), (256, 64), (512, 128)])
-def test_ps_lift_tables_bit_exact(nxc, nv):
+@pytest.mark.parametrize("nxc,nv", [(8, 16), (256, 64), (512, 128), (40, 600), (8, 1024)])
+def test_ps_lift_tables_bit_exact(nxc, nv):  # wide rows: blocks of fewer than 32 threads
     H = _noisy_hist(nxc, nv, nxc + nv)
     mass, cdf, table, flag = pb.ps_lift_tables(dev(H)[0])
     m_o, c_o, f_o = orc.ps_lift_tables(H)
