@@ -679,10 +679,11 @@ extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_
     if (!H || !mass || !cdf || !table || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
-    // three FP64 rows of n_v + 1 per bin, two threads per bin; up to 32 bins per block, fewer
-    // for wide rows (<= 192 KB)
+    // three FP64 rows of n_v + 1 per bin, two threads per bin. The FP64 pipe of an SM is the
+    // bound (the divisions of the CDF and of the sampling rows), so few bins per block spread
+    // the bins over many SMs: 4 per block (fewer for wide rows, <= 192 KB)
     const size_t row3 = 3 * sizeof(double) * ((size_t)n_v + 1);
-    int per_block = (int)std::min<size_t>(32, (size_t)(192 * 1024) / row3);
+    int per_block = (int)std::min<size_t>(4, (size_t)(192 * 1024) / row3);
     if (per_block < 1) return PE_EINVAL;
     const size_t smem = row3 * (size_t)per_block;
     if (ensure_smem((const void*)k_ps_cdf, smem) != PE_OK) return PE_ECUDA;
