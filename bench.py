@@ -186,10 +186,13 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "iaw_large_oracle_sample", "ncell": cfg["ncell"], "particles": n_sample,
-                       "K": cfg["K"], "M": cfg["M"], "n_coarse": cfg["n_coarse"]},
+            # the GPU arm's workload and config; each step a bounded sample of it (cpu_baseline.sample)
+            "config": {"workload": "iaw_large", "ncell": cfg["ncell"], "particles": cfg["N"], "K": cfg["K"],
+                       "M": cfg["M"], "n_coarse": cfg["n_coarse"], "wavelet": cfg["wavelet"], "dt": cfg["dt"],
+                       "dT": cfg["dT"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one macro step with {n_sample} of {cfg['N']} particles"},
+                             "sample": f"each step: one projective macro step of the iaw_large workload with "
+                                       f"{n_sample} of its {cfg['N']} particles (FP64 oracle, one thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
