@@ -567,6 +567,18 @@ PE_API int pe_get_slope(pe_ctx* ctx, double* out, int32_t out_on_device);
 PE_API int pe_get_coarse(pe_ctx* ctx, double* out, int32_t out_on_device);
 PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
 
+/* Checkpoint and resume between macro steps. Projective integration's state is the coarse
+ * state: with the clock (macro and fine step counts, time, the next Delta t), which seeds the
+ * next lifting, and the potential that starts its first Newton solve, it determines every later
+ * step, so a context restored from a checkpoint continues bit for bit as the original would.
+ * Valid after a projection (the next step lifts; a context whose particles are current, just
+ * loaded or advanced by plain PIC, returns PE_ESTATE). pe_checkpoint_bytes gives the size of
+ * the host buffer; the image holds a header (sizes checked on restore: PE_EINVAL on a
+ * mismatch), the coarse state, the last slope and phi with its Newton history. Synchronises. */
+PE_API int pe_checkpoint_bytes(const pe_ctx* ctx, size_t* bytes);
+PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t bytes);
+PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* Synchronises the context's stream and returns PE_OK or the first device fault
  * (PE_ETIMEOUT, PE_ERANGE, PE_EOVERFLOW, PE_ENOCONV); clears the status word. */
 PE_API int pe_sync_status(pe_ctx* ctx);

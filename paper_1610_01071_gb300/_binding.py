@@ -160,6 +160,9 @@ SIGNATURES = {
     "pe_leap_curvature": (ctypes.c_int, [P, i32, i32, f64, P, P, P]),
     "pe_step_adaptive": (ctypes.c_int, [P, ctypes.POINTER(AdaptCfg), ctypes.POINTER(AdaptStats)]),
     "pe_set_macro_step": (ctypes.c_int, [P, f64]),
+    "pe_checkpoint_bytes": (ctypes.c_int, [P, ctypes.POINTER(sz)]),
+    "pe_checkpoint_save": (ctypes.c_int, [P, P, sz]),
+    "pe_checkpoint_restore": (ctypes.c_int, [P, P, sz]),
     "pe_gate": (ctypes.c_int, [P, i32, i32, f64, f64, P, f64, f64, P, P, P, P]),
     "pe_ps_coarsen": (ctypes.c_int, [P, i32, i64, i32, P, P]),
     "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
@@ -640,6 +643,19 @@ class Context:
         st = AdaptStats()
         self._call("pe_step_adaptive", ctypes.byref(a), ctypes.byref(st))
         return st.as_dict()
+
+    def checkpoint(self) -> bytes:
+        """Checkpoint image (bytes) of the context between macro steps (pe_checkpoint_save)."""
+        n = ctypes.c_size_t()
+        self._call("pe_checkpoint_bytes", ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        self._call("pe_checkpoint_save", buf, n.value)
+        return buf.raw
+
+    def restore(self, image: bytes):
+        """Resume from a checkpoint image of a context of the same configuration."""
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        self._call("pe_checkpoint_restore", buf, len(image))
 
     def set_macro_step(self, dT):
         """Delta t of the next macro steps (>= K dt)."""

@@ -383,6 +383,7 @@ extern "C" PE_API int pe_batch_step(pe_batch* b)
     for (int r = 0; r < R; ++r) {
         pe_ctx* x = b->ctx[r];
         x->macro_steps += 1;
+        x->coarse_state = 1;
         x->fine_steps += b->K;
         x->time += x->cfg.dT;
         x->v_at_integer = 0;

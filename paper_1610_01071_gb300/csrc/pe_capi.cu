@@ -568,6 +568,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     x->macro_steps = 0;
     x->fine_steps = 0;
     x->time = 0.0;
+    x->coarse_state = 0;
     PE_TRY(quiet_start_from_profile(x, c.seed, 1.0f));
     if (x->kinetic) {
         x->ebank = 0;
@@ -650,6 +651,7 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
                              ctx->stream));
     }
     ctx->macro_steps += 1;
+    ctx->coarse_state = 1;
     ctx->time += ctx->dT_cur;
     ctx->fresh = 0;
     return PE_OK;
@@ -771,6 +773,7 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
+    if (nsteps > 0) x->coarse_state = 0;  // the particles move on alone
     for (int s = 0; s < nsteps; ++s) {
         if (c.sort_every > 0 && (x->fine_steps % c.sort_every) == 0 && !x->fresh) {
             const int b = x->bank, o = 1 - b;
@@ -836,6 +839,72 @@ extern "C" PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on
         return PE_ECUDA;
     if (!in_on_device && cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
     ctx->fresh = 0;  // the next step lifts from this state
+    ctx->coarse_state = 1;
+    return PE_OK;
+}
+
+// Checkpoint image: header, coarse[ncoef], slope[ncoef], phi[2 ncell] (phi and its history).
+struct CheckpointHeader {
+    uint32_t magic, version;
+    int32_t ncell, phi_hist;
+    int64_t ncoef, macro_steps, fine_steps;
+    double time, dT_cur;
+};
+constexpr uint32_t kCheckpointMagic = 0x50455043u;  // "PEPC"
+
+extern "C" PE_API int pe_checkpoint_bytes(const pe_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return PE_EINVAL;
+    *bytes = sizeof(CheckpointHeader) + sizeof(double) * (2 * (size_t)ctx->ncoef + 2 * (size_t)ctx->cfg.ncell);
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    PE_TRY(pe_checkpoint_bytes(ctx, &need));
+    if (!host_buf || bytes < need) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    if (!x->coarse_state || x->macro_steps < 1) return PE_ESTATE;  // the particles are the state
+    CheckpointHeader h{kCheckpointMagic, 1u, x->cfg.ncell, x->phi_hist, x->ncoef, x->macro_steps, x->fine_steps,
+                       x->time, x->dT_cur};
+    char* p = (char*)host_buf;
+    memcpy(p, &h, sizeof(h));
+    double* d = (double*)(p + sizeof(h));
+    const size_t nco = (size_t)x->ncoef, nphi = 2 * (size_t)x->cfg.ncell;
+    if (cudaMemcpyAsync(d, x->coarse, sizeof(double) * nco, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d + nco, x->slope, sizeof(double) * nco, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d + 2 * nco, x->phi, sizeof(double) * nphi, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    return cudaStreamSynchronize(x->stream) == cudaSuccess ? PE_OK : PE_ECUDA;
+}
+
+extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    PE_TRY(pe_checkpoint_bytes(ctx, &need));
+    if (!host_buf || bytes < need) return PE_EINVAL;
+    pe_ctx* x = ctx;
+    CheckpointHeader h;
+    memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kCheckpointMagic || h.version != 1u || h.ncell != x->cfg.ncell || h.ncoef != x->ncoef ||
+        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)))
+        return PE_EINVAL;
+    const double* d = (const double*)((const char*)host_buf + sizeof(h));
+    const size_t nco = (size_t)x->ncoef, nphi = 2 * (size_t)x->cfg.ncell;
+    if (cudaMemcpyAsync(x->coarse, d, sizeof(double) * nco, cudaMemcpyHostToDevice, x->stream) != cudaSuccess ||
+        cudaMemcpyAsync(x->slope, d + nco, sizeof(double) * nco, cudaMemcpyHostToDevice, x->stream) != cudaSuccess ||
+        cudaMemcpyAsync(x->phi, d + 2 * nco, sizeof(double) * nphi, cudaMemcpyHostToDevice, x->stream) != cudaSuccess)
+        return PE_ECUDA;
+    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
+    x->macro_steps = h.macro_steps;
+    x->fine_steps = h.fine_steps;
+    x->time = h.time;
+    x->dT_cur = h.dT_cur;
+    x->phi_hist = h.phi_hist;
+    x->fresh = 0;  // the next step lifts from the restored coarse state
+    x->coarse_state = 1;
+    x->rho_valid = 0;
     return PE_OK;
 }
 

@@ -44,6 +44,8 @@ struct pe_ctx {
     int64_t macro_steps, fine_steps;
     double time;
     double dT_cur;       // Delta t of the next macro step (the configured one unless set or adapted)
+    int coarse_state;    // the coarse state (not the particles) is the state: after a projection,
+                         // pe_set_coarse or a restore; 0 after a load or plain PIC
     int32_t* cell[2];
     float* theta[2];
     float* v[2];

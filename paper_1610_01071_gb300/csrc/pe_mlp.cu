@@ -992,6 +992,7 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     if (r.accepted) {
         out->fine_steps = Ks;
         x->macro_steps += 1;
+        x->coarse_state = 1;
         x->time += x->dT_cur;
         x->fresh = 0;
         return PE_OK;
