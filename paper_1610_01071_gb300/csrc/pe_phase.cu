@@ -706,17 +706,22 @@ __device__ double ps_bin_mean(const double* cdf, int b, int nv, double vmin, dou
     return m;
 }
 
-__global__ void k_ps_mean_velocity(const double* __restrict__ cdf, int nxc, int nv, double vmin, double dv,
-                                   int bin_shift, int ncell, float* __restrict__ u)
+// One block: the bin means into shared memory first (each bin once), then the nodes.
+__global__ void __launch_bounds__(1024) k_ps_mean_velocity(const double* __restrict__ cdf, int nxc, int nv,
+                                                           double vmin, double dv, int bin_shift, int ncell,
+                                                           float* __restrict__ u)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ncell) return;
+    extern __shared__ double ub[];
+    for (int b = threadIdx.x; b < nxc; b += blockDim.x) ub[b] = ps_bin_mean(cdf, b, nv, vmin, dv);
+    __syncthreads();
     const double B = (double)(1 << bin_shift);
-    const double t = ((double)j - 0.5 * (B - 1.0)) / B;  // bin-midpoint coordinate of node j
-    const double f0 = floor(t);
-    const double f = t - f0;
-    const int b0 = (((int)f0) % nxc + nxc) % nxc, b1 = (b0 + 1) % nxc;
-    u[j] = (float)((1.0 - f) * ps_bin_mean(cdf, b0, nv, vmin, dv) + f * ps_bin_mean(cdf, b1, nv, vmin, dv));
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        const double t = ((double)j - 0.5 * (B - 1.0)) / B;  // bin-midpoint coordinate of node j
+        const double f0 = floor(t);
+        const double f = t - f0;
+        const int b0 = (((int)f0) % nxc + nxc) % nxc, b1 = (b0 + 1) % nxc;
+        u[j] = (float)((1.0 - f) * ub[b0] + f * ub[b1]);
+    }
 }
 
 }  // namespace
@@ -728,8 +733,10 @@ extern "C" PE_API int pe_ps_mean_velocity(const double* cdf, int32_t nxc, int32_
     if (!cdf || !u_prof || nxc < 1 || n_v < 1 || !(dv > 0.0) || bin_shift < 0 || !is_pow2(ncell) ||
         (int64_t)nxc << bin_shift != ncell)
         return PE_EINVAL;
-    pe::k_ps_mean_velocity<<<(ncell + 255) / 256, 256, 0, (cudaStream_t)stream>>>(cdf, nxc, n_v, v_min, dv, bin_shift,
-                                                                                  ncell, u_prof);
+    const size_t smem = sizeof(double) * (size_t)nxc;
+    if (ensure_smem((const void*)pe::k_ps_mean_velocity, smem) != PE_OK) return PE_ECUDA;
+    pe::k_ps_mean_velocity<<<1, 1024, smem, (cudaStream_t)stream>>>(cdf, nxc, n_v, v_min, dv, bin_shift, ncell,
+                                                                    u_prof);
     return launch_status(1);
 }
 
