@@ -68,7 +68,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             print(err)
     tmp = LIB + f".{os.getpid()}.tmp"
     # every symbol must resolve at link time (a missing definition fails the build, not the load)
-    cmd = [cc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
+    cmd = [cc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + [o for o, _ in results] + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

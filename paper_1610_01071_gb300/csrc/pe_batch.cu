@@ -316,6 +316,7 @@ extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
 
 extern "C" PE_API int pe_batch_step(pe_batch* b)
 {
+    NvtxRange nvtx("pe_batch_step");
     if (!b) return PE_EINVAL;
     const int R = (int)b->ctx.size();
     const bool fresh = b->ctx[0]->fresh != 0;

@@ -502,6 +502,7 @@ uint64_t pe_ctx_lift_seed(const pe_ctx* x) { return lift_seed(x); }
 
 extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device)
 {
+    NvtxRange nvtx("pe_measure");
     if (!ctx || !out) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
@@ -544,6 +545,7 @@ static int measure_phase(pe_ctx* x, double* out)
 
 extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude)
 {
+    NvtxRange nvtx("pe_load_initial");
     if (!ctx || (profile != PE_PROFILE_SINE && profile != PE_PROFILE_SLAB)) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
@@ -624,12 +626,14 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
 
 extern "C" PE_API int pe_burst(pe_ctx* ctx)
 {
+    NvtxRange nvtx("pe_burst");
     if (!ctx) return PE_EINVAL;
     return pe_ctx_burst_range(ctx, 0, ctx->cfg.K, 1);
 }
 
 extern "C" PE_API int pe_restrict(pe_ctx* ctx)
 {
+    NvtxRange nvtx("pe_restrict");
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
     if (ctx->ps) return pe_ps_coarsen(ctx->samples, c.K + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
@@ -639,6 +643,7 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
 
 extern "C" PE_API int pe_project(pe_ctx* ctx)
 {
+    NvtxRange nvtx("pe_project");
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
     if (ctx->ps && c.ps_filter) {
@@ -659,6 +664,7 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
 
 extern "C" PE_API int pe_lift(pe_ctx* ctx)
 {
+    NvtxRange nvtx("pe_lift");
     if (!ctx) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
@@ -691,6 +697,7 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
 
 extern "C" PE_API int pe_step(pe_ctx* ctx)
 {
+    NvtxRange nvtx("pe_step");
     if (!ctx) return PE_EINVAL;
     if (!ctx->fresh) PE_TRY(pe_lift(ctx));
     PE_TRY(pe_burst(ctx));
@@ -716,6 +723,7 @@ static double leap_for_tol(double qn, double cn, double Kdt, double tol)
 
 extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_adapt_stats* out)
 {
+    NvtxRange nvtx("pe_step_adaptive");
     if (!ctx || !a || !(a->tol > 0.0) || a->M_min < 1 || a->M_max < a->M_min || !(a->safety > 0.0) ||
         !(a->safety <= 1.0) || !(a->grow >= 1.0))
         return PE_EINVAL;
@@ -769,6 +777,7 @@ extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_ad
 
 extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
 {
+    NvtxRange nvtx("pe_pic_steps");
     if (!ctx || nsteps < 0) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
@@ -861,6 +870,7 @@ extern "C" PE_API int pe_checkpoint_bytes(const pe_ctx* ctx, size_t* bytes)
 
 extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t bytes)
 {
+    NvtxRange nvtx("pe_checkpoint_save");
     size_t need = 0;
     PE_TRY(pe_checkpoint_bytes(ctx, &need));
     if (!host_buf || bytes < need) return PE_EINVAL;
@@ -881,6 +891,7 @@ extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t byt
 
 extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, size_t bytes)
 {
+    NvtxRange nvtx("pe_checkpoint_restore");
     size_t need = 0;
     PE_TRY(pe_checkpoint_bytes(ctx, &need));
     if (!host_buf || bytes < need) return PE_EINVAL;
@@ -925,6 +936,7 @@ extern "C" PE_API int pe_sync_status(pe_ctx* ctx)
 
 extern "C" PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out_on_device)
 {
+    NvtxRange nvtx("pe_state_moments");
     if (!ctx || !out) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;

@@ -957,6 +957,7 @@ __global__ void k_to_f32(const double* __restrict__ src, int n, float* __restric
 
 extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cfg* gc, pe_gate_stats* out)
 {
+    NvtxRange nvtx("pe_step_surrogate");
     if (!ctx || !h || !gc || !out) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
