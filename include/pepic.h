@@ -573,8 +573,9 @@ PE_API int pe_set_coarse(pe_ctx* ctx, const double* in, int32_t in_on_device);
  * step, so a context restored from a checkpoint continues bit for bit as the original would.
  * Valid after a projection (the next step lifts; a context whose particles are current, just
  * loaded or advanced by plain PIC, returns PE_ESTATE). pe_checkpoint_bytes gives the size of
- * the host buffer; the image holds a header (sizes checked on restore: PE_EINVAL on a
- * mismatch), the coarse state, the last slope and phi with its Newton history. Synchronises. */
+ * the host buffer; the image holds a header (with the context's pe_config: a restore into a
+ * context of another configuration, seed included, returns PE_EINVAL), the coarse state, the
+ * last slope and phi with its Newton history. Synchronises. */
 PE_API int pe_checkpoint_bytes(const pe_ctx* ctx, size_t* bytes);
 PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t bytes);
 PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, size_t bytes);

@@ -858,6 +858,7 @@ struct CheckpointHeader {
     int32_t ncell, phi_hist;
     int64_t ncoef, macro_steps, fine_steps;
     double time, dT_cur;
+    pe_config cfg;  // a restore needs the same configuration, byte for byte
 };
 constexpr uint32_t kCheckpointMagic = 0x50455043u;  // "PEPC"
 
@@ -876,8 +877,18 @@ extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t byt
     if (!host_buf || bytes < need) return PE_EINVAL;
     pe_ctx* x = ctx;
     if (!x->coarse_state || x->macro_steps < 1) return PE_ESTATE;  // the particles are the state
-    CheckpointHeader h{kCheckpointMagic, 1u, x->cfg.ncell, x->phi_hist, x->ncoef, x->macro_steps, x->fine_steps,
-                       x->time, x->dT_cur};
+    CheckpointHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kCheckpointMagic;
+    h.version = 1u;
+    h.ncell = x->cfg.ncell;
+    h.phi_hist = x->phi_hist;
+    h.ncoef = x->ncoef;
+    h.macro_steps = x->macro_steps;
+    h.fine_steps = x->fine_steps;
+    h.time = x->time;
+    h.dT_cur = x->dT_cur;
+    h.cfg = x->cfg;
     char* p = (char*)host_buf;
     memcpy(p, &h, sizeof(h));
     double* d = (double*)(p + sizeof(h));
@@ -899,7 +910,8 @@ extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, s
     CheckpointHeader h;
     memcpy(&h, host_buf, sizeof(h));
     if (h.magic != kCheckpointMagic || h.version != 1u || h.ncell != x->cfg.ncell || h.ncoef != x->ncoef ||
-        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)))
+        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)) ||
+        memcmp(&h.cfg, &x->cfg, sizeof(pe_config)) != 0)
         return PE_EINVAL;
     const double* d = (const double*)((const char*)host_buf + sizeof(h));
     const size_t nco = (size_t)x->ncoef, nphi = 2 * (size_t)x->cfg.ncell;

@@ -50,6 +50,8 @@ def test_checkpoints_are_refused_where_they_cannot_resume():
     other = make(ncell=256)
     with pytest.raises(pe.PepicError):  # another grid
         other.restore(image)
+    with pytest.raises(pe.PepicError):  # the same grid but another seed: another trajectory
+        make(seed=10).restore(image)
     bad = bytearray(image)
     bad[0] ^= 0xFF
     with pytest.raises(pe.PepicError):  # not an image
