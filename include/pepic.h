@@ -165,7 +165,7 @@ PE_API int pe_boltzmann_profile(const double* phi, const int64_t* ion_moments, i
  * lifted from it (Section 3.3: the ion density and velocity follow by integrating the coarse
  * distribution along v): per x-bin b the mean sum_k (v_min + (k + 1/2) dv) (F_b[k+1] - F_b[k])
  * of its reconstructed CDF row (pe_ps_lift_tables' cdf[nxc][n_v + 1]), then linear between bin
- * midpoints (periodic) into u_prof[ncell] (FP32); ncell = nxc 2^bin_shift. */
+ * midpoints (periodic) into u_prof[ncell] (FP32); ncell = nxc 2^bin_shift <= 8192. */
 PE_API int pe_ps_mean_velocity(const double* cdf, int32_t nxc, int32_t n_v, double v_min, double dv,
                                int32_t bin_shift, int32_t ncell, float* u_prof, void* stream);
 

@@ -730,8 +730,8 @@ __global__ void __launch_bounds__(1024) k_ps_mean_velocity(const double* __restr
 extern "C" PE_API int pe_ps_mean_velocity(const double* cdf, int32_t nxc, int32_t n_v, double v_min, double dv,
                                           int32_t bin_shift, int32_t ncell, float* u_prof, void* stream)
 {
-    if (!cdf || !u_prof || nxc < 1 || n_v < 1 || !(dv > 0.0) || bin_shift < 0 || !is_pow2(ncell) ||
-        (int64_t)nxc << bin_shift != ncell)
+    if (!cdf || !u_prof || nxc < 1 || n_v < 1 || !(dv > 0.0) || bin_shift < 0 || bin_shift > 13 || !is_pow2(ncell) ||
+        ncell > kFullGridMax || ((int64_t)nxc << bin_shift) != ncell)
         return PE_EINVAL;
     const size_t smem = sizeof(double) * (size_t)nxc;
     if (ensure_smem((const void*)pe::k_ps_mean_velocity, smem) != PE_OK) return PE_ECUDA;
