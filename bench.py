@@ -32,12 +32,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s and simulated time per wall-second, projective vs plain PIC"
 UNIT = "particle-steps/s"
-FUSED_BYTES_PER_PARTICLE = 28  # read cell, theta, v, w (16 B) + write cell, theta, v (12 B)
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per launch of the fused kernel from the ncu capture summarised
-# in profiles/k_particles_push_sample_iaw_large.md, valid while the kernels' device code
+# Algorithmic bytes per particle of each particle kernel (reads and writes of the particle
+# arrays; the grids stay in shared memory and L2).
+KERNEL_BYTES = {
+    "push_sample": (28, "k_particles<push + binned moment sample> (gather, kick, drift, deposit, co-moving sample)"),
+    "push": (28, "k_particles<push> (gather, kick, drift, deposit; plain PIC)"),
+    "sample": (16, "k_particles<binned moment sample> (last co-moving sample of a burst, read only)"),
+    "deposit": (12, "k_particles<deposit> (charge deposit alone: cell, theta, w read)"),
+    "load": (16, "k_quiet_start (lifting: quiet-start loading with the deposit fused, write only)"),
+    "push_sample_ps": (28, "k_particles<push + phase-space sample> (64 x-bins x 64 velocity cells window)"),
+}
+# DRAM bytes (read + write) per launch on the 2^24-ion workload from the ncu captures
+# summarised in profiles/, each valid while the particle kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
-NCU_TRAFFIC = {"source_hash": "35e21ff27381b258", "bytes": 270.735360e6 + 145.710336e6}
+NCU_TRAFFIC = {
+    "push_sample": {"source_hash": "35e21ff27381b258", "bytes": 270.735360e6 + 145.710336e6},
+}
 
 
 def kernel_source_hash():
@@ -161,12 +172,69 @@ def oracle_macro_step(cfg, n_sample, seed):
     return n_sample * cfg["K"], time.perf_counter() - t0
 
 
-def cpu_baseline(cfg, n_sample=1 << 23):
-    ps, t = oracle_macro_step(cfg, n_sample, seed=1)
-    return {"value": ps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one projective macro step (lift, {cfg['K']}-step burst with co-moving restriction, "
-                       f"coarsening, projection) of the {cfg['ncell']}-cell workload with {n_sample} of its "
-                       f"{cfg['N']} particles, FP64, single thread; {t:.1f} s")}
+def host_cores():
+    """Host cores this process may run on (the all-core oracle leg uses one process per core)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(cfg, n_sample, seeds, barrier, out):
+    import oracle as orc
+
+    orc._load()  # compile/load before the common start
+    for k, seed in enumerate(seeds):
+        barrier.wait()
+        t0 = time.perf_counter()
+        ps, _ = oracle_macro_step(cfg, n_sample, seed)
+        out.put((k, ps, t0, time.perf_counter()))
+
+
+def oracle_all_cores(cfg, n_sample, seed0, cores, steps=1):
+    """The oracle as it stands, one independent macro step per host core and step (processes
+    started once with spawn; each step released together by a barrier). Returns per step the
+    whole-host particle-steps and the wall time from the common start to the last worker's end
+    (perf_counter is the system-wide monotonic clock, so the processes' readings compare)."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(cfg, n_sample, [seed0 + 1000 * k + j for k in range(steps)], barrier, out))
+             for j in range(cores)]
+    for p in procs:
+        p.start()
+    res = [out.get() for _ in range(cores * steps)]
+    for p in procs:
+        p.join()
+    per_step = []
+    for k in range(steps):
+        rk = [r for r in res if r[0] == k]
+        per_step.append((sum(r[1] for r in rk), max(r[3] for r in rk) - min(r[2] for r in rk)))
+    return per_step
+
+
+def cpu_baseline(cfg, n_single=1 << 23, n_each=1 << 22):
+    """The FP64 oracle on the host cores: one thread on a 2^23-particle sample, and all cores
+    (one process per core, each a 2^22-particle sample with its own seed)."""
+    ps1, t1 = oracle_macro_step(cfg, n_single, seed=1)
+    cores = host_cores()
+    psn, tn = oracle_all_cores(cfg, n_each, 50, cores)[0]
+    return {"value": psn / tn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"all {cores} host cores, one process each: one projective macro step (lift, {cfg['K']}-step "
+                       f"burst with co-moving restriction, coarsening, projection) of the {cfg['ncell']}-cell workload "
+                       f"with {n_each} of its {cfg['N']} particles per process (own seed), FP64; {tn:.1f} s wall"),
+            "single_core": {"value": ps1 / t1, "unit": UNIT, "cores": 1,
+                            "sample": f"one thread, one macro step with {n_single} particles; {t1:.1f} s"}}
+
+
+def bench_config(cfg, world):
+    """The workload entry of the JSON line (the same for the GPU arm and the reference arm)."""
+    return {"workload": "iaw_large", "ncell": cfg["ncell"], "particles": cfg["N"], "K": cfg["K"], "M": cfg["M"],
+            "n_coarse": cfg["n_coarse"], "wavelet": cfg["wavelet"], "dt": cfg["dt"], "dT": cfg["dT"],
+            "l2": "inputs larger than L2 (268 MB of particles per realisation), no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
@@ -174,25 +242,19 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = workload_cfg()
-    n_sample = 1 << 20
-    for _ in range(args.warmup):
-        oracle_macro_step(cfg, n_sample, seed=7)
-    tot_ps, tot_t = 0, 0.0
-    for k in range(args.steps):
-        ps, t = oracle_macro_step(cfg, n_sample, seed=100 + k)
-        tot_ps += ps
-        tot_t += t
+    cores = host_cores()
+    n_each = 1 << 20
+    runs = oracle_all_cores(cfg, n_each, 100, cores, steps=args.warmup + args.steps)[args.warmup:]
+    tot_ps, tot_t = sum(r[0] for r in runs), sum(r[1] for r in runs)
     value = tot_ps / tot_t
+    sample = (f"each step: one projective macro step of the iaw_large workload per host core ({cores} processes), "
+              f"each with {n_each} of its {cfg['N']} particles and its own seed (FP64 oracle)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             # the GPU arm's workload and config; each step a bounded sample of it (cpu_baseline.sample)
-            "config": {"workload": "iaw_large", "ncell": cfg["ncell"], "particles": cfg["N"], "K": cfg["K"],
-                       "M": cfg["M"], "n_coarse": cfg["n_coarse"], "wavelet": cfg["wavelet"], "dt": cfg["dt"],
-                       "dT": cfg["dT"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one projective macro step of the iaw_large workload with "
-                                       f"{n_sample} of its {cfg['N']} particles (FP64 oracle, one thread)"},
+            "config": bench_config(cfg, args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -279,7 +341,7 @@ def run_gpu(args):
         barrier()
         launches = pb.launch_count() - launches0
         ctx.profile(False)
-        prof = ctx.profile_read()
+        prof = ctx.profile_read_kinds()
         newton_iters = ctx.diagnostics().newton_iters
         t_proj = ev0.elapsed_time(ev1) / 1e3
         st = ctx.sync_status()
@@ -289,12 +351,18 @@ def run_gpu(args):
         ctx.load_initial(cfg["amplitude"])
         ctx.pic_steps(max(3, args.warmup) * K)
         n_plain = max(args.steps, 1) * K
+        ctx.profile_read_kinds()
+        ctx.profile(True)
         barrier()
         ev0.record(stream)
         ctx.pic_steps(n_plain)
         ev1.record(stream)
         barrier()
+        ctx.profile(False)
+        prof_plain = ctx.profile_read_kinds()
         t_plain = ev0.elapsed_time(ev1) / 1e3
+        # ---------------- the deposit alone and the phase-space pass, for their rooflines
+        kern = time_kernels(ctx, cfg, pb, stream)
         # ---------------- end to end through the C ABI with host buffers
         host = torch.empty((2, cfg["n_coarse"]), dtype=torch.float64).pin_memory()
         ctx.load_initial(cfg["amplitude"])
@@ -323,8 +391,11 @@ def run_gpu(args):
     sim_proj = cfg["dT"] * args.steps / t_proj_max
     sim_plain = cfg["dt"] * n_plain / t_plain_max
     peak, peak_kind = peak_hbm()
-    push_ms = prof["push_ms"] / max(prof["push_launches"], 1)
-    achieved = FUSED_BYTES_PER_PARTICLE * N / (push_ms / 1e3) / 1e9
+    src_hash = kernel_source_hash()
+    means = {k: (v["ms"] / v["launches"], v["launches"]) for k, v in prof.items() if v["launches"] and k != "field"}
+    means["push"] = (prof_plain["push"]["ms"] / max(prof_plain["push"]["launches"], 1), prof_plain["push"]["launches"])
+    means.update(kern)
+    roof = {k: roofline_entry(k, ms, n, N, peak, peak_kind, src_hash) for k, (ms, n) in means.items()}
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -332,22 +403,17 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_proj_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "iaw_large", "ncell": ncell, "particles": N, "K": K, "M": cfg["M"],
-                   "n_coarse": cfg["n_coarse"], "wavelet": cfg["wavelet"], "dt": cfg["dt"], "dT": cfg["dT"],
-                   "l2": "inputs larger than L2 (268 MB of particles per realisation), no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(cfg, world),
         "sim_time_per_wall_s": {"projective": sim_proj, "plain_pic": sim_plain,
                                 "ratio": sim_proj / sim_plain},
         "plain_pic": {"value": ps_plain / t_plain_max, "unit": UNIT, "steps": n_plain,
                       "ms_per_step": 1e3 * t_plain_max / n_plain, "sort_every": 20},
-        "field_solve_us": 1e3 * prof["field_ms"] / max(prof["field_launches"], 1),
+        "field_solve_us": 1e3 * prof["field"]["ms"] / max(prof["field"]["launches"], 1),
+        "field_solve_us_plain_pic": 1e3 * prof_plain["field"]["ms"] / max(prof_plain["field"]["launches"], 1),
         "newton_iters_last": newton_iters,
-        "roofline": {"kernel": "k_particles<push+sample> (gather, kick, drift, deposit, co-moving sample)",
-                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": NCU_TRAFFIC["bytes"] if kernel_source_hash() == NCU_TRAFFIC["source_hash"] else None,
-                     "bytes_per_particle": FUSED_BYTES_PER_PARTICLE, "launch_us": 1e3 * push_ms,
-                     "launches": prof["push_launches"]},
+        # the dominant kernel: the fused pass of the bursts, from its own launches only
+        "roofline": roof["push_sample"],
+        "roofline_kernels": [roof[k] for k in KERNEL_BYTES if k in roof and k != "push_sample"],
         "e2e": {"value": ps_proj / t_e2e_max, "unit": UNIT, "h2d_bytes_per_step": 8 * 2 * cfg["n_coarse"],
                 "d2h_bytes_per_step": 8 * 2 * cfg["n_coarse"]},
         "gpu_launches": launches,
@@ -374,6 +440,59 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def roofline_entry(kind, ms, launches, N, peak, peak_kind, src_hash):
+    """Roofline of one particle kernel: algorithmic bytes per launch (bytes per particle x N)
+    over its mean CUDA-event launch time, against the measured HBM copy bandwidth."""
+    bpp, name = KERNEL_BYTES[kind]
+    achieved = bpp * N / (ms / 1e3) / 1e9
+    t = NCU_TRAFFIC.get(kind)
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": t["bytes"] if t and t["source_hash"] == src_hash else None,
+            "bytes_per_particle": bpp, "algorithmic_bytes": bpp * N, "launch_us": 1e3 * ms, "launches": launches}
+
+
+def time_kernels(ctx, cfg, pb, stream, reps=10):
+    """Mean launch time (ms) of the charge deposit alone on the context's particles, and of the
+    fused push + phase-space sample in a phase-space context of the same workload (two macro
+    steps with the context's own event pairs), for the per-kernel rooflines."""
+    import torch
+
+    dev = stream.device
+    N, ncell = cfg["N"], cfg["ncell"]
+    d = ctx.diagnostics()
+    cell, theta, _, w = ctx.particles(d.particle_bank)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            pb.deposit(cell, theta, w, ncell, d.s_w, rho=rho, status=st, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pb.deposit(cell, theta, w, ncell, d.s_w, rho=rho, status=st, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        out["deposit"] = (e0.elapsed_time(e1) / reps, reps)
+        c = pb.make_config(ncell, cfg["n_coarse"], cfg["K"], N, cfg["L"], cfg["dt"], 8.0, qm=cfg["qm"],
+                           v_th=cfg["v_th"], seed=13, newton_tol=1e-10, coarse="phase_space", n_v=64, v_max=8.0,
+                           ps_filter=3)
+        ps = pb.Context(c, device=dev, stream=stream)
+        ps.load_initial(cfg["amplitude"])
+        ps.step()
+        ps.profile_read_kinds()
+        ps.profile(True)
+        for _ in range(2):
+            ps.step()
+        ps.profile(False)
+        k = ps.profile_read_kinds()["push_sample_ps"]
+        out["push_sample_ps"] = (k["ms"] / max(k["launches"], 1), k["launches"])
+        if int(st.item()) != 0 or ps.sync_status() != 0:
+            raise RuntimeError("device status set while timing the deposit / phase-space pass")
+    return out
 
 
 def run_kernel_slab(args):

@@ -310,8 +310,9 @@ PE_API int pe_sort(const int32_t* cell, const float* theta, const float* v, cons
  * the library keeps until the process exits. It calls no cudaMalloc, cudaFree or any
  * allocating routine.
  * - ncell must not exceed PE_SORT_STATIC_MAX_CELLS; larger grids return PE_EINVAL.
- * - The first call on a device (with that device current) looks up the array's device
- *   address; make that first call before any stream capture.
+ * - Each call looks up the array's device address in the current context (no allocation),
+ *   so it follows the device and context that are current when it is made; the first call
+ *   in a process may load the library's device code, so make it before any stream capture.
  * - All calls share the one array (the counters are cleared at the start of each call):
  *   calls that may overlap on the GPU (different streams, or different threads without
  *   ordering) race and give wrong results. Serialise them.
@@ -596,13 +597,34 @@ PE_API int pe_state_moments(pe_ctx* ctx, pe_moments* out, int32_t out_on_device)
 PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out);
 
 /* Kernel timing for measurement: while enabled, the context records a pair of CUDA
- * events on its stream around every particle-kernel launch (pe_push, pe_sample,
- * pe_quiet_start) and every field solve (pe_field) it issues. pe_profile_read
- * synchronises, returns the summed elapsed milliseconds and launch counts since the
- * last read, and resets them. Events are host resources created on first use. */
+ * events on its stream around every particle-kernel launch and every field solve it
+ * issues, pooled by launch kind:
+ *   PE_PROF_PUSH_SAMPLE     fused push + deposit + moment restriction sample (a burst step)
+ *   PE_PROF_PUSH            push + deposit without a sample (plain PIC, kinetic electrons)
+ *   PE_PROF_SAMPLE          restriction sample alone (the last sample of a burst)
+ *   PE_PROF_DEPOSIT         charge deposit alone
+ *   PE_PROF_LOAD            quiet-start loading and lifting (deposit fused)
+ *   PE_PROF_PUSH_SAMPLE_PS  fused push + deposit + phase-space restriction sample
+ *   PE_PROF_FIELD           field solve (Newton, or the kinetic-electron Poisson solve)
+ * pe_profile_read synchronises, returns the summed elapsed milliseconds and launch counts
+ * since the last read (push_* = every kind but PE_PROF_FIELD, field_* = PE_PROF_FIELD) and
+ * resets them. pe_profile_read_kinds returns the same per kind (ms[PE_PROF_NKINDS],
+ * launches[PE_PROF_NKINDS], host arrays) and resets them. Events are host resources created
+ * on first use. */
+enum {
+    PE_PROF_PUSH_SAMPLE = 0,
+    PE_PROF_PUSH = 1,
+    PE_PROF_SAMPLE = 2,
+    PE_PROF_DEPOSIT = 3,
+    PE_PROF_LOAD = 4,
+    PE_PROF_PUSH_SAMPLE_PS = 5,
+    PE_PROF_FIELD = 6,
+    PE_PROF_NKINDS = 7
+};
 PE_API int pe_profile(pe_ctx* ctx, int32_t enable);
 PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
                            int64_t* field_launches);
+PE_API int pe_profile_read_kinds(pe_ctx* ctx, double* ms, int64_t* launches);
 
 /* =================================================================== batch
  * Ensemble of independent realisations advanced together (the same burst length, fine

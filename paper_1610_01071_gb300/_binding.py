@@ -22,6 +22,8 @@ PE_PROFILE_SINE = 0
 PE_PROFILE_SLAB = 1
 PE_BOUNDARY = {"periodic": 0, "absorbing": 1}
 PE_NBUF = 20
+# launch kinds of the context's kernel timing, in the order of PE_PROF_* (include/pepic.h)
+PROFILE_KINDS = ("push_sample", "push", "sample", "deposit", "load", "push_sample_ps", "field")
 BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples_fx=7, coarse_samples=8,
            coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16, electrons_a=17,
            electrons_b=18, rho_e=19)
@@ -150,6 +152,7 @@ SIGNATURES = {
     "pe_diagnostics": (ctypes.c_int, [P, ctypes.POINTER(Diag)]),
     "pe_profile": (ctypes.c_int, [P, i32]),
     "pe_profile_read": (ctypes.c_int, [P, P, P, P, P]),
+    "pe_profile_read_kinds": (ctypes.c_int, [P, P, P]),
     "pe_launch_count": (i64, []),
     "pe_compute_moments": (ctypes.c_int, [P, P, P, P, i64, P, P, P, i32, f64, f64, f32, f32, i32, i32, P, P, P, P]),
     "pe_rel_l2": (ctypes.c_int, [P, P, i64, P, P]),
@@ -407,14 +410,21 @@ def sort(cell, theta, v, w, ncell, status=None, stream=None):
     return oc, ot, ov, ow
 
 
-def sort_noalloc(cell, theta, v, w, ncell, status=None, stream=None):
+def sort_noalloc(cell, theta, v, w, ncell, status=None, stream=None, out=None):
     """pe_sort without a scratch argument: its counters live in the library's static
-    device array (for callers that cannot allocate device memory when they sort)."""
+    device array (for callers that cannot allocate device memory when they sort). With
+    `out` = (cell, theta, v, w) and `status` given, this wrapper allocates nothing either.
+    The call runs with the particles' device current, on `stream` or that device's current
+    stream."""
     dev = cell.device
-    oc, ot, ov, ow = torch.empty_like(cell), torch.empty_like(theta), torch.empty_like(v), torch.empty_like(w)
-    status = _status(status, dev)
-    check(load().pe_sort_noalloc(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), ncell, _ptr(oc), _ptr(ot),
-                                 _ptr(ov), _ptr(ow), _ptr(status), _stream(stream)), "pe_sort_noalloc")
+    with torch.cuda.device(dev):
+        if out is None:
+            out = (torch.empty_like(cell), torch.empty_like(theta), torch.empty_like(v), torch.empty_like(w))
+        oc, ot, ov, ow = out
+        status = _status(status, dev)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        check(load().pe_sort_noalloc(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), cell.numel(), ncell, _ptr(oc),
+                                     _ptr(ot), _ptr(ov), _ptr(ow), _ptr(status), _stream(s)), "pe_sort_noalloc")
     return oc, ot, ov, ow
 
 
@@ -681,6 +691,13 @@ class Context:
         check(load().pe_profile_read(self._h, ctypes.byref(pm), ctypes.byref(pl), ctypes.byref(fm),
                                      ctypes.byref(fl)), "pe_profile_read")
         return dict(push_ms=pm.value, push_launches=pl.value, field_ms=fm.value, field_launches=fl.value)
+
+    def profile_read_kinds(self):
+        """Summed event time (ms) and launch count per launch kind (PROFILE_KINDS), then reset."""
+        ms = (ctypes.c_double * len(PROFILE_KINDS))()
+        n = (ctypes.c_int64 * len(PROFILE_KINDS))()
+        check(load().pe_profile_read_kinds(self._h, ms, n), "pe_profile_read_kinds")
+        return {k: dict(ms=ms[i], launches=n[i]) for i, k in enumerate(PROFILE_KINDS)}
 
     # -- typed views into the arena (for tests and inspection)
     def view(self, buf: str, dtype, count=None):

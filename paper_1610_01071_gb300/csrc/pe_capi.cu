@@ -287,8 +287,7 @@ static void destroy_events(std::vector<cudaEvent_t>* v)
 extern "C" PE_API void pe_destroy(pe_ctx* ctx)
 {
     if (!ctx) return;
-    destroy_events(ctx->ev_push);
-    destroy_events(ctx->ev_field);
+    for (int k = 0; k < PE_PROF_NKINDS; ++k) destroy_events(ctx->prof_ev[k]);
     free(ctx);
 }
 
@@ -307,16 +306,15 @@ static int record(pe_ctx* x, std::vector<cudaEvent_t>*& pool, size_t slot, int s
     return cudaEventRecord((*pool)[i], x->stream) == cudaSuccess ? PE_OK : PE_ECUDA;
 }
 
-// Wraps one launch in a start/stop event pair when profiling is on.
+// Wraps one launch in a start/stop event pair of the given kind (PE_PROF_*) when profiling is on.
 template <class F>
-static int timed(pe_ctx* x, int is_field, F&& launch)
+static int timed(pe_ctx* x, int kind, F&& launch)
 {
     if (!x->profiling) return launch();
-    std::vector<cudaEvent_t>*& pool = is_field ? x->ev_field : x->ev_push;
-    size_t& n = is_field ? x->n_field : x->n_push;
-    PE_TRY(record(x, pool, n, 0));
+    size_t& n = x->prof_n[kind];
+    PE_TRY(record(x, x->prof_ev[kind], n, 0));
     PE_TRY(launch());
-    PE_TRY(record(x, pool, n, 1));
+    PE_TRY(record(x, x->prof_ev[kind], n, 1));
     ++n;
     return PE_OK;
 }
@@ -338,16 +336,35 @@ static double sum_pairs(std::vector<cudaEvent_t>* pool, size_t n)
     return tot;
 }
 
+extern "C" PE_API int pe_profile_read_kinds(pe_ctx* ctx, double* ms, int64_t* launches)
+{
+    if (!ctx || !ms || !launches) return PE_EINVAL;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
+    for (int k = 0; k < PE_PROF_NKINDS; ++k) {
+        ms[k] = ctx->prof_n[k] ? sum_pairs(ctx->prof_ev[k], ctx->prof_n[k]) : 0.0;
+        launches[k] = (int64_t)ctx->prof_n[k];
+        ctx->prof_n[k] = 0;
+    }
+    return PE_OK;
+}
+
 extern "C" PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
                                       int64_t* field_launches)
 {
-    if (!ctx) return PE_EINVAL;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
-    if (push_ms) *push_ms = ctx->n_push ? sum_pairs(ctx->ev_push, ctx->n_push) : 0.0;
-    if (push_launches) *push_launches = (int64_t)ctx->n_push;
-    if (field_ms) *field_ms = ctx->n_field ? sum_pairs(ctx->ev_field, ctx->n_field) : 0.0;
-    if (field_launches) *field_launches = (int64_t)ctx->n_field;
-    ctx->n_push = ctx->n_field = 0;
+    double ms[PE_PROF_NKINDS];
+    int64_t n[PE_PROF_NKINDS];
+    PE_TRY(pe_profile_read_kinds(ctx, ms, n));
+    double pm = 0.0;
+    int64_t pn = 0;
+    for (int k = 0; k < PE_PROF_NKINDS; ++k)
+        if (k != PE_PROF_FIELD) {
+            pm += ms[k];
+            pn += n[k];
+        }
+    if (push_ms) *push_ms = pm;
+    if (push_launches) *push_launches = pn;
+    if (field_ms) *field_ms = ms[PE_PROF_FIELD];
+    if (field_launches) *field_launches = n[PE_PROF_FIELD];
     return PE_OK;
 }
 
@@ -359,12 +376,12 @@ static int field_solve(pe_ctx* x, int step = 0)
 {
     const pe_config& c = x->cfg;
     if (x->kinetic)  // Section 4.1's two-species bursts: Poisson for the net charge
-        return timed(x, 1, [&] {
+        return timed(x, PE_PROF_FIELD, [&] {
             return pe_field_kinetic(x->rho, x->rho_e, c.ncell, x->dx, x->s_w, x->phi, x->E, x->Ef, x->stream);
         });
     const int extrap = step && x->phi_hist;
     double* prev = step ? x->phi + c.ncell : nullptr;
-    PE_TRY(timed(x, 1, [&] {
+    PE_TRY(timed(x, PE_PROF_FIELD, [&] {
         return field_solve_history(x->rho, c.ncell, x->dx, x->s_w, c.poisson, c.boundary, c.newton_tol,
                                    c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, prev, extrap, x->stream);
     }));
@@ -375,8 +392,10 @@ static int field_solve(pe_ctx* x, int step = 0)
 static int deposit_current(pe_ctx* x)
 {
     const int b = x->bank;
-    PE_TRY(pe_deposit(x->cell[b], x->theta[b], x->w[b], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho, x->status,
-                      x->stream));
+    PE_TRY(timed(x, PE_PROF_DEPOSIT, [&] {
+        return pe_deposit(x->cell[b], x->theta[b], x->w[b], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho,
+                          x->status, x->stream);
+    }));
     if (x->kinetic) {
         const int e = x->ebank;
         PE_TRY(pe_deposit(x->ecell[e], x->etheta[e], x->ew[e], x->cfg.nparticles, x->cfg.ncell, x->s_w, x->rho_e,
@@ -427,7 +446,7 @@ static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed, ElectronDrift drif
                                x->stream));
     PE_TRY(pe_boltzmann_profile(x->phi, mom, x->s_w, x->s_p, c.ncell, x->prof, mom ? u : nullptr, x->stream));
     const int e = x->ebank;
-    PE_TRY(timed(x, 0, [&] {
+    PE_TRY(timed(x, PE_PROF_LOAD, [&] {
         return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof, u,
                               (float)x->v_th_e, seed, x->s_w, x->rho_e, x->status, x->stream);
     }));
@@ -441,7 +460,7 @@ static int push_electrons(pe_ctx* x)
     const pe_config& c = x->cfg;
     const int e = x->ebank;
     const float kick = x->e_v_at_integer ? 0.5f : 1.0f;
-    PE_TRY(timed(x, 0, [&] {
+    PE_TRY(timed(x, PE_PROF_PUSH, [&] {
         return pe_push_ex(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, c.ncell,
                           (float)(c.dt / x->dx), (float)(x->qm_e * c.dt), kick, x->s_w, c.boundary, x->rho_e, nullptr,
                           x->status, x->stream);
@@ -480,7 +499,7 @@ static int quiet_start_from_profile(pe_ctx* x, uint64_t seed, float wall_factor)
 {
     const pe_config& c = x->cfg;
     const int b = x->bank;
-    PE_TRY(timed(x, 0, [&] {
+    PE_TRY(timed(x, PE_PROF_LOAD, [&] {
         if (x->walls)
             return pe_quiet_start_equal(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->prof,
                                         x->prof + c.ncell, wall_factor, (float)c.v_th, seed, x->s_w, x->eq_scratch,
@@ -601,7 +620,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     for (int p = p_begin; p < p_end; ++p) {
         const double tau = c.comoving ? x->dT_cur - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
-        PE_TRY(timed(x, 0, [&] {
+        PE_TRY(timed(x, x->ps ? PE_PROF_PUSH_SAMPLE_PS : PE_PROF_PUSH_SAMPLE, [&] {
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                               kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream);
         }));
@@ -615,7 +634,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     if (final_sample) {
         const double tau = c.comoving ? x->dT_cur - p_end * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p_end));
-        PE_TRY(timed(x, 0, [&] {
+        PE_TRY(timed(x, PE_PROF_SAMPLE, [&] {
             return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick, &a,
                              x->status, x->stream);
         }));
@@ -673,7 +692,7 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         PE_TRY(pe_ps_lift_tables(x->coarse, x->nc, x->nv, x->ps_mass, x->ps_cdf, x->ps_table, x->ps_scratch, x->ps_flags,
                                  x->stream));
         const int b = x->bank;
-        PE_TRY(timed(x, 0, [&] {
+        PE_TRY(timed(x, PE_PROF_LOAD, [&] {
             if (x->walls)
                 return pe_ps_quiet_start_equal(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell,
                                                x->bin_shift, x->ps_mass, x->ps_table, x->nv, x->vmin, x->dv,
@@ -803,7 +822,7 @@ extern "C" PE_API int pe_pic_steps(pe_ctx* ctx, int32_t nsteps)
         PE_TRY(field_solve(x, 1));
         const int b = x->bank;
         const float kick = x->v_at_integer ? 0.5f : 1.0f;
-        PE_TRY(timed(x, 0, [&] {
+        PE_TRY(timed(x, PE_PROF_PUSH, [&] {
             return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
                               kick, x->s_w, c.boundary, x->rho, nullptr, x->status, x->stream);
         }));
@@ -910,8 +929,14 @@ extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, s
     CheckpointHeader h;
     memcpy(&h, host_buf, sizeof(h));
     if (h.magic != kCheckpointMagic || h.version != 1u || h.ncell != x->cfg.ncell || h.ncoef != x->ncoef ||
-        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)) ||
+        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)) || !(h.dT_cur < 1e300) ||
         memcmp(&h.cfg, &x->cfg, sizeof(pe_config)) != 0)
+        return PE_EINVAL;
+    // the clock and the Newton history drive the lifting seed, the sort and reset cadence and
+    // the first solve: a header that passes the checks above but carries an impossible clock
+    // (a negative step count, a non-finite or negative time, a history flag other than 0/1)
+    // is refused rather than loaded
+    if (h.fine_steps < 0 || !(h.time >= 0.0 && h.time < 1e300) || (h.phi_hist != 0 && h.phi_hist != 1))
         return PE_EINVAL;
     const double* d = (const double*)((const char*)host_buf + sizeof(h));
     const size_t nco = (size_t)x->ncoef, nphi = 2 * (size_t)x->cfg.ncell;

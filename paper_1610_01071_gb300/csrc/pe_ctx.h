@@ -73,11 +73,10 @@ struct pe_ctx {
     int32_t* sort;
     uint32_t* status;
     int32_t* diag;
-    // kernel timing (pe_profile)
+    // kernel timing (pe_profile): start/stop event pairs per launch kind (PE_PROF_*)
     int profiling;
-    std::vector<cudaEvent_t>* ev_push;   // start/stop pairs
-    std::vector<cudaEvent_t>* ev_field;
-    size_t n_push, n_field;               // pairs recorded since the last read
+    std::vector<cudaEvent_t>* prof_ev[PE_PROF_NKINDS];
+    size_t prof_n[PE_PROF_NKINDS];  // pairs recorded since the last read
 };
 
 

@@ -1053,21 +1053,18 @@ extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v
     return launch_status(2);
 }
 
-// Device address of g_sort_static on the current device, looked up once per device.
+// Device address of g_sort_static in the current context. Looked up on every call (the lookup
+// allocates nothing): a cached address could go stale when another context becomes current
+// or after cudaDeviceReset reloads the module, and a cache shared by threads would need
+// synchronisation.
 static unsigned* sort_static_ptr()
 {
-    static unsigned* cache[64] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!cache[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sort_static) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cache[dev] = static_cast<unsigned*>(p);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_static) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return cache[dev];
+    return static_cast<unsigned*>(p);
 }
 
 extern "C" PE_API int pe_sort_noalloc(const int32_t* cell, const float* theta, const float* v, const float* w,

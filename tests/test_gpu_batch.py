@@ -1,10 +1,12 @@
 """Batched ensemble (pe_batch_*): many realisations of different sizes advanced in
 shared launches and a replayed CUDA graph must give, bit for bit, the coarse states of
-each realisation advanced alone with pe_step."""
+each realisation advanced alone with pe_step, and each realisation's coarse state must
+match the oracle's projective macro step (Section 3.1 cycle) from the same particles."""
 import numpy as np
 import pytest
 import torch
 
+import oracle as orc
 import paper_1610_01071_gb300 as pe
 
 pytestmark = pytest.mark.gpu
@@ -62,6 +64,36 @@ def test_batch_of_sinusoids_and_slabs_matches_individual_contexts_bit_for_bit():
             assert np.array_equal(ga, gb), f"step {step}, realisation {k}: max diff {np.abs(ga - gb).max()}"
     for c in group:
         assert c.sync_status() == 0
+
+
+def test_batch_matches_oracle_per_realisation():
+    # a mixed ensemble (periodic sinusoids and bounded slabs of different sizes): one batched
+    # macro step from the loaded particles, then a second one that lifts from the projected
+    # coarse state, each realisation against the oracle's macro step (efpi_macro_step or its
+    # bounded-grid form) at the tolerances of the single-context cycle tests
+    sizes = [(256, 1 << 14, False), (512, 1 << 15, True), (128, 1 << 13, False), (256, 1 << 14, True)]
+    group = [make(i, n, N, slab) for i, (n, N, slab) in enumerate(sizes)]
+    states = [orc.State(*[x.cpu().numpy() for x in c.particles()]) for c in group]
+    batch = pe.Batch(group)
+    batch.step()
+    got1 = [c.get_coarse().cpu().numpy() for c in group]
+    batch.step()
+    got2 = [c.get_coarse().cpu().numpy() for c in group]
+    for i, ((ncell, N, slab), ctx, st) in enumerate(zip(sizes, group, states)):
+        assert ctx.sync_status() == 0
+        K, M, dt = 6, 3, 0.1
+        ocfg = dict(ncell=ncell, n_coarse=16, K=K, L=ncell * 0.5, dt=dt, qm=1.0, dT=M * K * dt, N=N, v_th=1.0,
+                    s_w=ctx.diagnostics().s_w)
+        macro = orc.efpi_macro_step_walls if slab else orc.efpi_macro_step
+        lift = orc.lift_walls if slab else orc.lift
+        c1, _, phi = macro(st, ocfg, np.zeros(ncell))
+        err1 = np.max(np.abs(got1[i] - c1)) / np.max(np.abs(c1))
+        assert err1 < 1e-4, f"realisation {i}, step 1: {err1:.3e}"
+        # lifting seed of macro step m: seed + 0x632BE59BD9B4E019 (m + 1)
+        seed2 = (100 + i + 0x632BE59BD9B4E019 * 2) % 2**64
+        c2, _, _ = macro(lift(c1, ocfg, seed2), ocfg, phi)
+        err2 = np.max(np.abs(got2[i] - c2)) / np.max(np.abs(c2))
+        assert err2 < 2e-4, f"realisation {i}, step 2: {err2:.3e}"
 
 
 def test_batch_rejects_mixed_states():

@@ -56,6 +56,16 @@ def test_checkpoints_are_refused_where_they_cannot_resume():
     bad[0] ^= 0xFF
     with pytest.raises(pe.PepicError):  # not an image
         make().restore(bytes(bad))
+    # a valid header with an impossible clock: header fields at byte offsets 12 (phi history
+    # flag, int32), 32 (fine steps, int64) and 40 (time, float64)
+    import struct
+
+    for off, fmt, val in ((12, "<i", 2), (32, "<q", -1), (40, "<d", float("nan")), (40, "<d", -1.0)):
+        bad = bytearray(image)
+        struct.pack_into(fmt, bad, off, val)
+        with pytest.raises(pe.PepicError):
+            make().restore(bytes(bad))
+    make().restore(image)  # the untouched image still loads
     a.pic_steps(3)
     with pytest.raises(pe.PepicError):  # advanced by plain PIC: the particles are the state again
         a.checkpoint()
