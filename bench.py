@@ -462,6 +462,7 @@ def time_kernels(ctx, cfg, pb, stream, reps=10):
 
     dev = stream.device
     N, ncell = cfg["N"], cfg["ncell"]
+    ctx.load_initial(cfg["amplitude"])  # a freshly loaded (velocity-ordered) state, as a lift leaves it
     d = ctx.diagnostics()
     cell, theta, _, w = ctx.particles(d.particle_bank)
     rho = torch.empty(ncell, dtype=torch.int64, device=dev)

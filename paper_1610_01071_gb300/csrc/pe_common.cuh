@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include "pepic.h"
 
 namespace pe {
@@ -43,55 +45,161 @@ __device__ __forceinline__ FxSplit fx_split(int32_t q, float theta)
 // window). The flush recombines them exactly: the same integer as a plain int64 sum.
 constexpr int kMaxChunk = 65536;
 
+// Shared-memory reductions on a 32-bit shared-window address (one register per array
+// instead of a 64-bit generic pointer; the digits of a node sit at fixed offsets from it).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int OFF>
+__device__ __forceinline__ void red_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(a), "r"(v), "n"(OFF) : "memory");
+}
+
+template <int OFF>
+__device__ __forceinline__ void red_s32(uint32_t a, int32_t v)
+{
+    asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(a), "r"(v), "n"(OFF) : "memory");
+}
+
+// The node's digits are interleaved, four words per node (d0, d1, d2, unused).
+constexpr int kSmemGridWords = 4;
+
 struct SmemGrid {
-    uint32_t* d0;
-    uint32_t* d1;
-    int32_t* d2;
+    uint32_t* p;  // generic pointer to node 0 (zero, flush)
+    uint32_t s;   // shared address of node 0
     unsigned long long* g;
     int base, width, mask;
 
-    // Carves three arrays of `width` counters from s; returns the next free word.
-    __device__ __forceinline__ uint32_t* bind(uint32_t* s, unsigned long long* global, int b, int w, int m)
+    // Carves `width` nodes from sm; returns the next free word.
+    __device__ __forceinline__ uint32_t* bind(uint32_t* sm, unsigned long long* global, int b, int w, int m)
     {
-        d0 = s;
-        d1 = s + w;
-        d2 = reinterpret_cast<int32_t*>(s + 2 * w);
+        p = sm;
+        s = smem_u32(sm);
         g = global;
         base = b;
         width = w;
         mask = m;
-        return s + 3 * w;
+        return sm + kSmemGridWords * w;
+    }
+
+    // Adds one value given as its three digits (a = v mod 2^16, b = (v >> 16) mod 2^16,
+    // c = v >> 32); digit sums of several values (each digit sum exact in 32 bits) add the
+    // sum of the values.
+    __device__ __forceinline__ void add_digits(int node, uint32_t a, uint32_t b, int32_t c) const
+    {
+        const int idx = (node - base) & mask;
+        if (idx < width) {
+            const uint32_t at = s + 16u * (uint32_t)idx;
+            if (a) red_u32<0>(at, a);
+            if (b) red_u32<4>(at, b);
+            if (c) red_s32<8>(at, c);
+        } else {
+            const long long v = (long long)a + ((long long)b << 16) + ((long long)c << 32);
+            if (v) atomicAdd(&g[node], (unsigned long long)v);
+        }
     }
 
     __device__ __forceinline__ void add(int node, unsigned long long val) const
     {
-        const int idx = (node - base) & mask;
-        if (idx < width) {
-            const uint32_t a = (uint32_t)val & 0xFFFFu, b = (uint32_t)(val >> 16) & 0xFFFFu;
-            const int32_t c = (int32_t)((long long)val >> 32);
-            if (a) atomicAdd(&d0[idx], a);
-            if (b) atomicAdd(&d1[idx], b);
-            if (c) atomicAdd(&d2[idx], c);
-        } else {
-            atomicAdd(&g[node], val);
-        }
+        add_digits(node, (uint32_t)val & 0xFFFFu, (uint32_t)(val >> 16) & 0xFFFFu, (int32_t)((long long)val >> 32));
     }
 
     __device__ __forceinline__ void zero() const
     {
-        for (int i = threadIdx.x; i < width; i += blockDim.x) {
-            d0[i] = 0u;
-            d1[i] = 0u;
-            d2[i] = 0;
-        }
+        for (int i = threadIdx.x; i < width; i += blockDim.x)
+            reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
     }
 
     // Adds the non-zero node sums to the global grid; call after __syncthreads().
     __device__ __forceinline__ void flush() const
     {
         for (int i = threadIdx.x; i < width; i += blockDim.x) {
-            const long long v = (long long)d0[i] + ((long long)d1[i] << 16) + ((long long)d2[i] << 32);
+            const uint4 d = reinterpret_cast<const uint4*>(p)[i];
+            const long long v = (long long)d.x + ((long long)d.y << 16) + ((long long)(int32_t)d.z << 32);
             if (v) atomicAdd(&g[(base + i) & mask], (unsigned long long)v);
+        }
+    }
+};
+
+// Charge-deposit window shared by the 32 lanes of a warp: four consecutive nodes base ..
+// base+3, each lane holding its own partial sums of them in registers. The base is the same in
+// every lane and moves only by warp-wide decisions, so the window's flushes are warp-uniform:
+// each flushed node is summed across the warp (16/16/32-bit digit sums with redux.sync, each
+// exact) and added to the block grid by one lane. Lanes that held a per-lane window of their own
+// moved it at different particles, so the warp ran the flush code at almost every particle
+// with a few lanes active, and those lanes hit the same shared-memory words.
+// Every member function must be called by all 32 lanes of the warp, converged.
+struct WarpWindow {
+    int base;
+    unsigned long long s0, s1, s2, s3;
+
+    __device__ __forceinline__ void reset(int b)
+    {
+        base = b;
+        s0 = s1 = s2 = s3 = 0ull;
+    }
+
+    // Adds the window's nodes 0 .. n-1 (n warp-uniform, <= 4) to the grid.
+    __device__ __forceinline__ void flush_first(const SmemGrid& grid, int n) const
+    {
+        const int lane = threadIdx.x & 31;
+        uint32_t A = 0u, B = 0u;
+        int32_t C = 0;
+        const unsigned long long s[4] = {s0, s1, s2, s3};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < n) {
+                const uint32_t a = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)s[k] & 0xFFFFu);
+                const uint32_t b = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(s[k] >> 16) & 0xFFFFu);
+                const int32_t c = __reduce_add_sync(0xFFFFFFFFu, (int32_t)((long long)s[k] >> 32));
+                if (lane == k) {
+                    A = a;
+                    B = b;
+                    C = c;
+                }
+            }
+        }
+        if (lane < n) grid.add_digits((base + lane) & grid.mask, A, B, C);
+    }
+
+    // Moves the base by sh nodes (warp-uniform); the nodes that leave the window are flushed.
+    __device__ __forceinline__ void move(const SmemGrid& grid, int sh)
+    {
+        if (sh >= 1 && sh <= 3) {
+            flush_first(grid, sh);
+            if (sh == 1) {
+                s0 = s1;
+                s1 = s2;
+                s2 = s3;
+            } else if (sh == 2) {
+                s0 = s2;
+                s1 = s3;
+                s2 = 0ull;
+            } else {
+                s0 = s3;
+                s1 = s2 = 0ull;
+            }
+            s3 = 0ull;
+        } else {
+            flush_first(grid, 4);
+            s0 = s1 = s2 = s3 = 0ull;
+        }
+        base = (base + sh) & grid.mask;
+    }
+
+    // Deposits q (left part at window node d, right part at d + 1), d in {0, 1, 2}: one pair
+    // of 64-bit adds under a predicate.
+    __device__ __forceinline__ void add(int d, const FxSplit& q)
+    {
+        if (d == 1) {
+            s1 += q.left;
+            s2 += q.right;
+        } else if (d == 0) {
+            s0 += q.left;
+            s1 += q.right;
+        } else {
+            s2 += q.left;
+            s3 += q.right;
         }
     }
 };
@@ -218,57 +326,70 @@ __device__ __forceinline__ void ps_add_warp(const PSGrid& gr, int key, long long
 // (v0, v1, v2, as in SmemGrid). The flush recombines
 //   sum = (u0 + u1 2^16) 2^24 + v0 + v1 2^16 + v2 2^32
 // exactly; the bounds of SmemGrid apply per bin (at most 65536 additions per block).
+// The bin's counters are interleaved, eight words per bin (u0, u1, v0, v1, v2, unused).
+constexpr int kBinGridWords = 8;
+
 struct BinGrid {
-    uint32_t* u0;
-    int32_t* u1;
-    uint32_t* v0;
-    uint32_t* v1;
-    int32_t* v2;
+    uint32_t* p;  // generic pointer to bin 0 (zero, flush)
+    uint32_t s;   // shared address of bin 0
     unsigned long long* g;
     int nb;
 
-    __device__ __forceinline__ uint32_t* bind(uint32_t* s, unsigned long long* global, int nbins)
+    __device__ __forceinline__ uint32_t* bind(uint32_t* sm, unsigned long long* global, int nbins)
     {
-        u0 = s;
-        u1 = reinterpret_cast<int32_t*>(s + nbins);
-        v0 = s + 2 * nbins;
-        v1 = s + 3 * nbins;
-        v2 = reinterpret_cast<int32_t*>(s + 4 * nbins);
+        p = sm;
+        s = smem_u32(sm);
         g = global;
         nb = nbins;
-        return s + 5 * nbins;
+        return sm + kBinGridWords * nbins;
     }
 
     __device__ __forceinline__ void add_whole(int b, int32_t q) const
     {
-        atomicAdd(&u0[b], (uint32_t)q & 0xFFFFu);
-        atomicAdd(&u1[b], q >> 16);
+        const uint32_t at = s + 32u * (uint32_t)b;
+        red_u32<0>(at, (uint32_t)q & 0xFFFFu);
+        red_s32<4>(at, q >> 16);
+    }
+
+    // Adds whole contributions given as digit sums: lo = sum (q mod 2^16), hi = sum (q >> 16).
+    __device__ __forceinline__ void add_whole_digits(int b, uint32_t lo, int32_t hi) const
+    {
+        const uint32_t at = s + 32u * (uint32_t)b;
+        if (lo) red_u32<0>(at, lo);
+        if (hi) red_s32<4>(at, hi);
     }
 
     __device__ __forceinline__ void add_part(int b, unsigned long long val) const
     {
-        atomicAdd(&v0[b], (uint32_t)val & 0xFFFFu);
-        atomicAdd(&v1[b], (uint32_t)(val >> 16) & 0xFFFFu);
-        atomicAdd(&v2[b], (int32_t)((long long)val >> 32));
+        const uint32_t at = s + 32u * (uint32_t)b;
+        red_u32<8>(at, (uint32_t)val & 0xFFFFu);
+        red_u32<12>(at, (uint32_t)(val >> 16) & 0xFFFFu);
+        red_s32<16>(at, (int32_t)((long long)val >> 32));
+    }
+
+    // Moves t from bin b to bin b + 1 (periodic): the right CIC parts of particles whose two
+    // nodes straddle the edge between the bins, counted whole in bin b.
+    __device__ __forceinline__ void add_transfer(int b, long long t) const
+    {
+        if (t == 0) return;
+        add_part(b, (unsigned long long)(-t));
+        add_part((b + 1) & (nb - 1), (unsigned long long)t);
     }
 
     __device__ __forceinline__ void zero() const
     {
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-            u0[i] = 0u;
-            u1[i] = 0;
-            v0[i] = 0u;
-            v1[i] = 0u;
-            v2[i] = 0;
-        }
+        for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x)
+            reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
     }
 
     __device__ __forceinline__ void flush() const
     {
         for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-            const long long whole = (long long)u0[i] + ((long long)u1[i] << 16);
-            const long long v = whole * (long long)kThetaOne + (long long)v0[i] + ((long long)v1[i] << 16) +
-                                ((long long)v2[i] << 32);
+            const uint4 a = reinterpret_cast<const uint4*>(p)[2 * i];
+            const uint32_t v2 = p[8 * i + 4];
+            const long long whole = (long long)a.x + ((long long)(int32_t)a.y << 16);
+            const long long v = whole * (long long)kThetaOne + (long long)a.z + ((long long)a.w << 16) +
+                                ((long long)(int32_t)v2 << 32);
             if (v) atomicAdd(&g[i], (unsigned long long)v);
         }
     }
@@ -319,80 +440,83 @@ struct LaneWindow {
     }
 };
 
-// Per-lane run of whole-particle bin contributions (BinGrid::add_whole) of the density and
-// momentum samples over the lane's four neighbouring particles; a new bin sends the finished
-// run to the grid. The run of a group is then summed across lanes (bin_add_warp).
-struct BinAcc {
-    int key;
-    int32_t n, m;
+// Sum over the lanes in `mask` of a 64-bit value, as three exact digit sums (each lane's
+// value split into 16 + 16 + 32 bits); every lane in `mask` gets the total.
+__device__ __forceinline__ long long warp_sum64(unsigned mask, long long v)
+{
+    const uint32_t a = __reduce_add_sync(mask, (uint32_t)v & 0xFFFFu);
+    const uint32_t b = __reduce_add_sync(mask, (uint32_t)((unsigned long long)v >> 16) & 0xFFFFu);
+    const int32_t c = __reduce_add_sync(mask, (int32_t)(v >> 32));
+    return (long long)a + ((long long)b << 16) + ((long long)c << 32);
+}
 
-    __device__ __forceinline__ void reset()
+// Haar-binned restriction sample of one warp group (four particles per lane): a window of two
+// bins K, K+1, with K the lowest bin the warp's particles sample (warp-uniform). Every particle
+// adds its whole w_q (m_q) to the bin of its left node; a particle on the last node of bin K
+// also adds its right part q theta_q to the transfers tn (tm), which move from bin K to K+1.
+// The bin totals are then exactly those of the split CIC deposit summed over the bins. Samples
+// outside the window (a spread over more than two bins) go straight to the grids. At the end of
+// the group the window is summed across the warp and added once.
+struct BinWindow {
+    int K;
+    int32_t n0, m0, n1, m1;
+    long long tn, tm;
+
+    __device__ __forceinline__ void begin(int k)
     {
-        key = -1;
-        n = m = 0;
+        K = k;
+        n0 = m0 = n1 = m1 = 0;
+        tn = tm = 0;
     }
-    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, const BinGrid& gn, const BinGrid& gm)
+
+    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, uint32_t tq, const BinGrid& gn,
+                                        const BinGrid& gm)
     {
-        if (b == key) {
-            n += wq;
-            m += mq;
+        const int d = (b - K) & (gn.nb - 1);
+        if (d == 0) {
+            n0 += wq;
+            m0 += mq;
+            tn += (long long)wq * (long long)tq;
+            tm += (long long)mq * (long long)tq;
+        } else if (d == 1 && tq == 0u) {
+            n1 += wq;
+            m1 += mq;
         } else {
-            if (key >= 0) {
-                gn.add_whole(key, n);
-                gm.add_whole(key, m);
+            gn.add_whole(b, wq);
+            gm.add_whole(b, mq);
+            if (tq) {
+                gn.add_transfer(b, (long long)wq * (long long)tq);
+                gm.add_transfer(b, (long long)mq * (long long)tq);
             }
-            key = b;
-            n = wq;
-            m = mq;
+        }
+    }
+
+    // Sums the window across the warp and adds it (all 32 lanes, converged);
+    // |sum of n| <= 32 * 4 * 2^23 = 2^30.
+    __device__ __forceinline__ void end(const BinGrid& gn, const BinGrid& gm) const
+    {
+        const int lane = threadIdx.x & 31;
+        const int32_t N0 = __reduce_add_sync(0xFFFFFFFFu, n0), M0 = __reduce_add_sync(0xFFFFFFFFu, m0);
+        const int32_t N1 = __reduce_add_sync(0xFFFFFFFFu, n1), M1 = __reduce_add_sync(0xFFFFFFFFu, m1);
+        // lanes 0..3 add bin K's and K+1's density and momentum, one each
+        const int32_t v = lane == 0 ? N0 : (lane == 1 ? N1 : (lane == 2 ? M0 : M1));
+        if (lane < 4 && v != 0) ((lane & 2) ? gm : gn).add_whole((K + (lane & 1)) & (gn.nb - 1), v);
+        if (__any_sync(0xFFFFFFFFu, (tn | tm) != 0)) {
+            const long long TN = warp_sum64(0xFFFFFFFFu, tn), TM = warp_sum64(0xFFFFFFFFu, tm);
+            if (lane < 2) (lane ? gm : gn).add_transfer(K, lane ? TM : TN);
         }
     }
 };
 
-// Adds the active lanes' bin runs to the density and momentum BinGrids, summing runs of
-// equal bins in consecutive lanes first (consecutive lanes hold neighbouring particles of a
-// velocity-ordered cell, whose co-moving bins mostly agree): |sum| <= 32 * 4 * 2^23 = 2^30.
-// One warp sum when every active lane holds the same bin, else a segmented sum per run.
-// Lanes with key < 0 add nothing; if the active lanes are not a prefix of the warp, every
-// lane adds on its own.
-__device__ __forceinline__ void bin_add_warp(const BinGrid& gn, const BinGrid& gm, int key, int32_t n, int32_t m)
+// Warp-uniform base bin of a group: the lowest of the lanes' bins b (where ok), compared
+// periodically around lane 0's bin; all 32 lanes, converged.
+__device__ __forceinline__ int warp_low_bin(int b, bool ok, int nb)
 {
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int first = __ffs(act) - 1;
-    const int k0 = __shfl_sync(act, key, first);
-    if (__all_sync(act, key == k0)) {  // one bin for every active lane (the common case)
-        const int32_t sn = __reduce_add_sync(act, n), sm = __reduce_add_sync(act, m);
-        if (k0 >= 0 && lane == first) {
-            gn.add_whole(k0, sn);
-            gm.add_whole(k0, sm);
-        }
-        return;
-    }
-    const int nact = __popc(act);
-    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
-        if (key >= 0) {
-            gn.add_whole(key, n);
-            gm.add_whole(key, m);
-        }
-        return;
-    }
-    const int prev = __shfl_up_sync(act, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const unsigned heads = __ballot_sync(act, head);
-    const unsigned after = heads & (0xFFFFFFFEu << lane);
-    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int32_t on = __shfl_down_sync(act, n, off), om = __shfl_down_sync(act, m, off);
-        if (lane + off <= run_end) {
-            n += on;
-            m += om;
-        }
-    }
-    if (head && key >= 0) {
-        gn.add_whole(key, n);
-        gm.add_whole(key, m);
-    }
+    const int ref = __shfl_sync(0xFFFFFFFFu, b, 0);
+    const int h = nb >> 1;
+    const int rel = ok ? ((b - ref + h) & (nb - 1)) - h : INT_MAX;
+    const int lo = __reduce_min_sync(0xFFFFFFFFu, rel);
+    return lo == INT_MAX ? (ref & (nb - 1)) : ((ref + lo) & (nb - 1));
 }
 
 // Contiguous particle range [begin, end) of block b when n particles are split into

@@ -11,6 +11,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <climits>
+
 #include "pe_common.cuh"
 #include "pe_eq.cuh"
 #include "pe_internal.h"
@@ -86,6 +88,33 @@ __device__ __forceinline__ int32_t fx_weight(float x, float scale, bool* ovf)
 
 constexpr int kThreads = 256;
 
+// Block-local table of the nodal fields the gathers read, for the nodes [base, base + width)
+// (mod ncell) around the block's first cell: entry i holds, for node c = base + i,
+// {E_c, E_{c+1} - E_c, E0_c, E0_{c+1} - E0_c} (E0 only when the pass samples). A CIC gather is
+// then one shared-memory load and one fma per field; the differences are the same FP32
+// subtractions the gather would do, so results are unchanged. Nodes outside the window (a
+// particle far from its block's cells) read the global fields.
+constexpr int kFieldTabNodes = 256;
+
+struct FieldTab {
+    uint32_t s;  // shared address of entry 0
+    int base, width;
+};
+
+__device__ __forceinline__ float4 lds_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float2 lds_f2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+
 // True when cell c + k (k = fl, an integer-valued float) lies between the walls,
 // [0, ncell - 1); NaN counts as outside.
 __device__ __forceinline__ bool inside_walls(const PushParams& P, int c, float fl)
@@ -93,42 +122,79 @@ __device__ __forceinline__ bool inside_walls(const PushParams& P, int c, float f
     return fl >= -(float)c && fl < (float)(P.ncell - 1 - c);
 }
 
+// One particle: gather, co-moving restriction sample, kick and drift (as the mode asks). Returns
+// true when the particle's charge is to be deposited at (c_out, th_out) with fixed-point weight
+// wq_out (the caller deposits a whole group at once, see deposit_group).
+// Binned restriction sample of one particle, left for the caller's warp-uniform bin window:
+// the bin of its left node, its fixed-point weight and momentum, and theta_q when its right
+// node lies in the next bin (0 otherwise); ok = false when it samples nothing.
+struct BinSample {
+    int b;
+    int32_t mq;
+    uint32_t tq;
+    bool ok;
+};
+
 template <int MODE, bool WALLS>
-__device__ __forceinline__ void process(const PushParams& P, int c, float th, float vv, float ww,
-                                        LaneWindow& lw, BinAcc& bacc, const SmemGrid& grho,
-                                        const SmemGrid& gsn, const SmemGrid& gsm, const BinGrid& bsn,
-                                        const BinGrid& bsm, const PSGrid& gps, PSAcc& acc, bool* ovf, int& c_out,
-                                        float& th_out, float& v_out, float& w_out)
+__device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft, bool act, int c, float th,
+                                        float vv, float ww, BinSample& bs, const SmemGrid& gsn, const SmemGrid& gsm,
+                                        const PSGrid& gps, PSAcc& acc, bool* ovf, int& c_out, float& th_out,
+                                        float& v_out, float& w_out, int32_t& wq_out)
 {
     using Tr = ModeTraits<MODE>;
     c_out = c;
     th_out = th;
     v_out = vv;
     w_out = ww;
+    wq_out = 0;
+    bs.b = 0;
+    bs.mq = 0;
+    bs.tq = 0u;
+    bs.ok = false;
+    if (!act) return false;  // a lane past the end of its warp's slice
     if ((unsigned)c >= (unsigned)P.ncell) {
         raise_flag(P.status, PE_FLAG_RANGE);
-        return;
+        return false;
     }
     if (WALLS) {
-        if (ww == 0.0f) return;  // absorbed: frozen, carries nothing
-        if (c >= P.ncell - 1) {  // a live particle must lie between the walls
+        if (ww == 0.0f) return false;  // absorbed: frozen, carries nothing
+        if (c >= P.ncell - 1) {        // a live particle must lie between the walls
             raise_flag(P.status, PE_FLAG_RANGE);
-            return;
+            return false;
         }
     }
     const int32_t wq = fx_weight(ww, P.wscale, ovf);
-    if (MODE == kDeposit) {
-        lw.add(c, fx_split(wq, th), grho);
-        return;
+    wq_out = wq;
+    if (MODE == kDeposit) return true;
+    // CIC gather of E (and of the frame field E0 when sampling) at the particle
+    float Ec, dE, E0c = 0.f, dE0 = 0.f;
+    const int fi = (c - ft.base) & P.mask;
+    if (fi < ft.width) {
+        if (Tr::sample) {
+            const float4 f = lds_f4(ft.s + 16u * (uint32_t)fi);
+            Ec = f.x;
+            dE = f.y;
+            E0c = f.z;
+            dE0 = f.w;
+        } else {
+            const float2 f = lds_f2(ft.s + 8u * (uint32_t)fi);
+            Ec = f.x;
+            dE = f.y;
+        }
+    } else {
+        const int c1 = (c + 1) & P.mask;
+        Ec = __ldg(P.Ef + c);
+        dE = __ldg(P.Ef + c1) - Ec;
+        if (Tr::sample) {
+            E0c = __ldg(P.E0f + c);
+            dE0 = __ldg(P.E0f + c1) - E0c;
+        }
     }
-    const int c1 = (c + 1) & P.mask;
-    const float Ec = __ldg(P.Ef + c), Ec1 = __ldg(P.Ef + c1);
-    const float Ep = fmaf(th, Ec1 - Ec, Ec);  // CIC gather
+    const float Ep = fmaf(th, dE, Ec);
     if (Tr::sample) {
         // Appendix B: carry the particle along the approximate characteristic to t_{n+1}
         const float vbar = fmaf((P.kick - 0.5f) * P.qm_dt, Ep, vv);  // integer-time velocity
-        const float E0c = __ldg(P.E0f + c), E0c1 = __ldg(P.E0f + c1);
-        const float E0p = fmaf(th, E0c1 - E0c, E0c);
+        const float E0p = fmaf(th, dE0, E0c);
         const float xs = fmaf(P.tau_dx, vbar, th);
         float fl = floorf(xs);
         float ths = xs - fl;
@@ -157,16 +223,13 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
         if (!Tr::ps && counted) {
             const int32_t mq = fx_weight(ww * vt, P.pscale, ovf);
             if (Tr::binned) {
-                const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
-                if (b0 == b1) {  // both CIC parts in one bin: the whole particle
-                    bacc.add(b0, wq, mq, bsn, bsm);
-                } else {
-                    const FxSplit qn = fx_split(wq, ths), qp = fx_split(mq, ths);
-                    bsn.add_part(b0, qn.left);
-                    bsn.add_part(b1, qn.right);
-                    bsm.add_part(b0, qp.left);
-                    bsm.add_part(b1, qp.right);
-                }
+                // whole particle in the bin of its left node; the right part of a particle on a
+                // bin's last node moves to the next bin (theta_q as in fx_split)
+                const int bm = (1 << P.bin_shift) - 1;
+                bs.b = cs >> P.bin_shift;
+                bs.mq = mq;
+                bs.tq = ((cs & bm) == bm) ? __float2uint_rn(ths * kThetaOneF) : 0u;
+                bs.ok = true;
             } else {
                 const FxSplit qn = fx_split(wq, ths);
                 const FxSplit qp = fx_split(mq, ths);
@@ -192,13 +255,65 @@ __device__ __forceinline__ void process(const PushParams& P, int c, float th, fl
             th_out = 0.0f;
             v_out = 0.0f;
             w_out = 0.0f;
-            return;
+            return false;
         }
-        const int cn = (c + (int)fl) & P.mask;
-        c_out = cn;
+        c_out = (c + (int)fl) & P.mask;
         th_out = thn;
         v_out = vn;
-        lw.add(cn, fx_split(wq, thn), grho);
+        return true;
+    }
+    return false;
+}
+
+// Charge deposit of one particle straight to the block grid (outside the warp window).
+__device__ __forceinline__ void deposit_direct(const SmemGrid& g, int c, float th, int32_t wq, int mask)
+{
+    const FxSplit q = fx_split(wq, th);
+    g.add(c, q.left);
+    g.add((c + 1) & mask, q.right);
+}
+
+// Deposits a group (four particles per lane, dep_k set where particle k deposits at cell c_k,
+// offset th_k, weight q_k) through the warp window: when the warp's cells leave the window's
+// three cells, the window moves (warp-uniformly) to the lowest cell; cells still beyond it
+// (a spread of more than three cells) go straight to the grid. Called by all 32 lanes.
+__device__ __forceinline__ void deposit_group(WarpWindow& win, const SmemGrid& g, int ncell, int mask, const int4& c,
+                                              const float4& th, int32_t q0, int32_t q1, int32_t q2, int32_t q3,
+                                              bool e0, bool e1, bool e2, bool e3)
+{
+    const int H = ncell >> 1;  // cells as signed offsets from the base (periodic)
+    int r0 = ((c.x - win.base + H) & mask) - H, r1 = ((c.y - win.base + H) & mask) - H;
+    int r2 = ((c.z - win.base + H) & mask) - H, r3 = ((c.w - win.base + H) & mask) - H;
+    int lo = INT_MAX, hi = INT_MIN;
+    if (e0) lo = min(lo, r0), hi = max(hi, r0);
+    if (e1) lo = min(lo, r1), hi = max(hi, r1);
+    if (e2) lo = min(lo, r2), hi = max(hi, r2);
+    if (e3) lo = min(lo, r3), hi = max(hi, r3);
+    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+    if (lo == INT_MAX) return;  // nothing to deposit in this group
+    if (lo < 0 || hi > 2) {
+        win.move(g, lo);
+        r0 -= lo;
+        r1 -= lo;
+        r2 -= lo;
+        r3 -= lo;
+    }
+    if (e0) {
+        if ((unsigned)r0 <= 2u) win.add(r0, fx_split(q0, th.x));
+        else deposit_direct(g, c.x, th.x, q0, mask);
+    }
+    if (e1) {
+        if ((unsigned)r1 <= 2u) win.add(r1, fx_split(q1, th.y));
+        else deposit_direct(g, c.y, th.y, q1, mask);
+    }
+    if (e2) {
+        if ((unsigned)r2 <= 2u) win.add(r2, fx_split(q2, th.z));
+        else deposit_direct(g, c.z, th.z, q2, mask);
+    }
+    if (e3) {
+        if ((unsigned)r3 <= 2u) win.add(r3, fx_split(q3, th.w));
+        else deposit_direct(g, c.w, th.w, q3, mask);
     }
 }
 
@@ -221,6 +336,23 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     PSGrid gps{};
     constexpr bool kPS = Tr::ps;
     uint32_t* s = smem;
+    FieldTab ft{0u, 0, 0};
+    if (kNeedV) {  // field table first (16-byte aligned); filled before the block barrier below
+        ft.width = P.ncell < kFieldTabNodes ? P.ncell : kFieldTabNodes;
+        ft.base = P.ncell <= kFieldTabNodes ? 0 : ((c_first - kFieldTabNodes / 4) & P.mask);
+        ft.s = smem_u32(s);
+        for (int i = threadIdx.x; i < ft.width; i += blockDim.x) {
+            const int n0 = (ft.base + i) & P.mask, n1 = (n0 + 1) & P.mask;
+            const float e0 = __ldg(P.Ef + n0), e1 = __ldg(P.Ef + n1);
+            if (Tr::sample) {
+                const float f0 = __ldg(P.E0f + n0), f1 = __ldg(P.E0f + n1);
+                reinterpret_cast<float4*>(s)[i] = make_float4(e0, e1 - e0, f0, f1 - f0);
+            } else {
+                reinterpret_cast<float2*>(s)[i] = make_float2(e0, e1 - e0);
+            }
+        }
+        s += (Tr::sample ? 4 : 2) * kFieldTabNodes;
+    }
     if (kRho) s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
     if (kSamp) {
         const int sb = P.samp_width < P.ncell ? ((c_first - P.samp_width / 2) & P.mask) : 0;
@@ -252,10 +384,11 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     int64_t g0, g1;
     warp_groups(gb0, gb1, &g0, &g1);
     const int lane = threadIdx.x & 31;
-    LaneWindow lw;
-    lw.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);
-    BinAcc bacc;
-    bacc.reset();
+    WarpWindow win;
+    win.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);  // the same address in every lane
+    BinWindow bw;
+    bw.begin(0);
+    BinSample bs;
     PSAcc acc;
     acc.reset();
     bool ovf = false;
@@ -265,23 +398,39 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     float4* v4 = reinterpret_cast<float4*>(P.v);
     const float4* w4 = reinterpret_cast<const float4*>(P.w);
     // one 16-byte group (four particles) per lane per iteration: a single inlined copy of the
-    // particle step keeps the kernel small enough for the instruction cache
-    for (int64_t g = g0 + lane; g < g1; g += 32) {
-        const int4 ca = cell4[g];
-        const float4 ta = th4[g];
-        const float4 va = kNeedV ? v4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 wa = __ldg(w4 + g);
+    // particle step keeps the kernel small enough for the instruction cache. The loop bound is
+    // the same for the whole warp (the deposit and sample windows are warp-uniform); lanes past
+    // the end of the slice process nothing.
+    for (int64_t gs = g0; gs < g1; gs += 32) {
+        const int64_t g = gs + lane;
+        const bool act = g < g1;
+        int4 ca = make_int4(0, 0, 0, 0);
+        float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), va = ta, wa = ta;
+        if (act) {
+            ca = cell4[g];
+            ta = th4[g];
+            if (kNeedV) va = v4[g];
+            wa = __ldg(w4 + g);
+        }
         int4 co;
         float4 to, vo, wo;
-        process<MODE, WALLS>(P, ca.x, ta.x, va.x, wa.x, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
-                             &ovf, co.x, to.x, vo.x, wo.x);
-        process<MODE, WALLS>(P, ca.y, ta.y, va.y, wa.y, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
-                             &ovf, co.y, to.y, vo.y, wo.y);
-        process<MODE, WALLS>(P, ca.z, ta.z, va.z, wa.z, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
-                             &ovf, co.z, to.z, vo.z, wo.z);
-        process<MODE, WALLS>(P, ca.w, ta.w, va.w, wa.w, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc,
-                             &ovf, co.w, to.w, vo.w, wo.w);
-        if (kWrite) {
+        int32_t q0, q1, q2, q3;
+        const bool e0 = process<MODE, WALLS>(P, ft, act, ca.x, ta.x, va.x, wa.x, bs, gsn, gsm, gps, acc, &ovf, co.x,
+                                             to.x, vo.x, wo.x, q0);
+        if (kBin) {  // the group's bin window starts at the lowest bin of the lanes' first particles
+            bw.begin(warp_low_bin(bs.b, bs.ok, P.ncell >> P.bin_shift));
+            if (bs.ok) bw.add(bs.b, q0, bs.mq, bs.tq, bsn, bsm);
+        }
+        const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gps, acc, &ovf, co.y,
+                                             to.y, vo.y, wo.y, q1);
+        if (kBin && bs.ok) bw.add(bs.b, q1, bs.mq, bs.tq, bsn, bsm);
+        const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gps, acc, &ovf, co.z,
+                                             to.z, vo.z, wo.z, q2);
+        if (kBin && bs.ok) bw.add(bs.b, q2, bs.mq, bs.tq, bsn, bsm);
+        const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gps, acc, &ovf, co.w,
+                                             to.w, vo.w, wo.w, q3);
+        if (kBin && bs.ok) bw.add(bs.b, q3, bs.mq, bs.tq, bsn, bsm);
+        if (kWrite && act) {
             cell4[g] = co;
             th4[g] = to;
             v4[g] = vo;
@@ -292,18 +441,18 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
             ps_add_warp(gps, acc.key, acc.val);
             acc.reset();
         }
-        if (kBin) {
-            bin_add_warp(bsn, bsm, bacc.key, bacc.n, bacc.m);
-            bacc.reset();
-        }
+        if (kBin) bw.end(bsn, bsm);
+        if (kRho) deposit_group(win, grho, P.ncell, P.mask, co, to, q0, q1, q2, q3, e0, e1, e2, e3);
     }
+    if (kRho) win.flush_first(grho, 4);
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {  // ragged tail (< 4 particles)
         int co;
         float to, vo, wo;
+        int32_t q;
         const float vi = kNeedV ? P.v[i] : 0.f;
         const float wi = P.w[i];
-        process<MODE, WALLS>(P, P.cell[i], P.theta[i], vi, wi, lw, bacc, grho, gsn, gsm, bsn, bsm, gps, acc, &ovf, co,
-                             to, vo, wo);
+        const bool e = process<MODE, WALLS>(P, ft, true, P.cell[i], P.theta[i], vi, wi, bs, gsn, gsm, gps, acc, &ovf, co,
+                                            to, vo, wo, q);
         if (kWrite) {
             P.cell[i] = co;
             P.theta[i] = to;
@@ -314,12 +463,16 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
             ps_add_warp(gps, acc.key, acc.val);
             acc.reset();
         }
-        if (kBin) {
-            bin_add_warp(bsn, bsm, bacc.key, bacc.n, bacc.m);
-            bacc.reset();
+        if (kBin && bs.ok) {  // straight to the grids
+            bsn.add_whole(bs.b, q);
+            bsm.add_whole(bs.b, bs.mq);
+            if (bs.tq) {
+                bsn.add_transfer(bs.b, (long long)q * (long long)bs.tq);
+                bsm.add_transfer(bs.b, (long long)bs.mq * (long long)bs.tq);
+            }
         }
+        if (kRho && e) deposit_direct(grho, co, to, q, P.mask);
     }
-    if (kRho) lw.flush(grho);
     if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
     __syncthreads();
     if (kRho) grho.flush();
@@ -335,8 +488,16 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 }
 
 // WALLS: bounded grid (a separate instantiation, so that periodic launches carry no wall code)
+// Resident blocks per SM the register budget is set for (the phase-space passes hold a larger
+// shared-memory window and more registers).
+template <int MODE>
+constexpr int min_blocks()
+{
+    return ModeTraits<MODE>::ps ? 3 : 4;
+}
+
 template <int MODE, bool WALLS>
-__global__ void __launch_bounds__(kThreads, ModeTraits<MODE>::ps ? 3 : 4) k_particles(PushParams P)
+__global__ void __launch_bounds__(kThreads, min_blocks<MODE>()) k_particles(PushParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
@@ -354,7 +515,7 @@ struct WorkItem {
 // the next item from a global counter until none are left. Step p and the kick are the
 // same for every realisation; tau and the sample row follow from each descriptor.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 4) k_particles_batch(const PushParams* descs, const WorkItem* items,
+__global__ void __launch_bounds__(kThreads, min_blocks<MODE>()) k_particles_batch(const PushParams* descs, const WorkItem* items,
                                                                  int nitems, int p, float kick, unsigned* counter)
 {
     extern __shared__ uint32_t smem[];
@@ -730,7 +891,9 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     const int nxc = P.ncell >> P.bin_shift;
     P.ps_width = ps ? (nxc <= kPSWindowBins ? nxc : kPSWindowBins) : 0;
     if (ps) P.samp_width = 0;
-    size_t smem = 3 * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) + 5 * sizeof(uint32_t) * 2 * nb +
+    const size_t tab = MODE == kDeposit ? 0 : (samp ? sizeof(float4) : sizeof(float2)) * (size_t)kFieldTabNodes;
+    size_t smem = tab + kSmemGridWords * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) +
+                  kBinGridWords * sizeof(uint32_t) * 2 * nb +
                   3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = P.walls ? (const void*)k_particles<MODE, true> : (const void*)k_particles<MODE, false>;
@@ -766,7 +929,7 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
         return s->inv_dv > 0.0f && 3 * sizeof(uint32_t) * w * (size_t)s->n_v <= 160 * 1024;
     }
     if (s->bin_shift == 0) return true;
-    return (5 * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
+    return (kBinGridWords * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
 }
 
 // ------------------------------------------------------------------ batched launches
@@ -821,7 +984,8 @@ int batch_grid(int mode, int max_ncell, int max_nb)
 {
     const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
     const void* k = (mode == 0) ? (const void*)k_particles_batch<kPushSampleBinned> : (const void*)k_particles_batch<kSampleBinned>;
-    const size_t smem = 3 * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) + 5 * sizeof(uint32_t) * 2 * max_nb;
+    const size_t smem = sizeof(float4) * (size_t)kFieldTabNodes + kSmemGridWords * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) +
+                        kBinGridWords * sizeof(uint32_t) * 2 * max_nb;
     return sm_count() * blocks_per_sm(k, kThreads, smem);
 }
 
@@ -830,7 +994,8 @@ int launch_particles_batch(int mode, const void* descs, const void* items, int n
                            unsigned* counter, int max_ncell, int max_nb, cudaStream_t s)
 {
     const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
-    const size_t smem = 3 * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) + 5 * sizeof(uint32_t) * 2 * max_nb;
+    const size_t smem = sizeof(float4) * (size_t)kFieldTabNodes + kSmemGridWords * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) +
+                        kBinGridWords * sizeof(uint32_t) * 2 * max_nb;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
     const auto* d = static_cast<const PushParams*>(descs);
@@ -996,7 +1161,7 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     P.rho_width = rho_fx ? (ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes) : 0;
     P.status = status;
     const int block = 256;
-    size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
+    size_t smem = kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width;
     const void* k = (const void*)k_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = particle_grid(k, block, smem, n, &P.chunk);
@@ -1044,7 +1209,7 @@ extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v
     P.rho_width = rho_fx ? (ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes) : 0;
     P.status = status;
     const int block = 256;
-    const size_t smem = 3 * sizeof(uint32_t) * (size_t)P.rho_width;
+    const size_t smem = kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width;
     const void* k = (const void*)k_quiet_start_equal;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     const int grid = particle_grid(k, block, smem, n, &P.chunk);

@@ -781,7 +781,7 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
     P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
     P.status = status;
-    const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const size_t smem = rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     const int grid = particle_grid(k, 256, smem, n, &P.chunk);
@@ -843,7 +843,7 @@ extern "C" PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float
     P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
     P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
     P.status = status;
-    const size_t smem = rho_fx ? 3 * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const size_t smem = rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0;
     const void* k = (const void*)k_ps_quiet_start_equal;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     const int grid = particle_grid(k, 256, smem, n, &P.chunk);
