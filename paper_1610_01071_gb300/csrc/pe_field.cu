@@ -37,28 +37,44 @@ constexpr int kClusterMinCells = 512;  // grids at least this large use the mult
 // ~2 lanes per cycle per SM, so FP64 is used only for per-node work, spread over many
 // warps and SMs, and kept off the serial chains of the tridiagonal elimination.
 //
-// Linear solve (SPIKE-style partition): each block solves its B rows, with the two
-// couplings to the neighbouring blocks moved to the right-hand side, by parallel
-// cyclic reduction with three right-hand sides, x = y - g X_left - h X_right. The
-// blocks' first and last unknowns then satisfy a cyclic block-tridiagonal system with
-// 2x2 blocks; every block gathers it through distributed shared memory and solves it
-// by block cyclic reduction. exp(phi) is evaluated once per solve and then carried
-// multiplicatively, exp(phi + s d) = exp(phi) exp(s d), with a Taylor polynomial.
+// Linear solve (nested separators, scalar tridiagonal systems only): the last row of every
+// warp is a separator, and the last row of every block is a separator of the cluster. Each
+// warp solves its other rows (its interior) by parallel cyclic reduction with register
+// shuffles, with the couplings to the two separators around it moved to two extra right-hand
+// sides (x = y - g S_left - h S_right). Substituting the interiors next to a separator into
+// its row leaves a scalar tridiagonal system over the separators: one warp of the block solves
+// the block's warp separators in terms of the two block separators around them, and one warp
+// of every block solves the cyclic system of the cluster's block separators, whose rows every
+// block pushes into every other block's shared memory before the cluster barrier. exp(phi) is
+// evaluated once per solve and then carried multiplicatively, exp(phi + s d) = exp(phi)
+// exp(s d), with a Taylor polynomial.
+//
+// Stopping: besides max |update| < tol, the iteration stops before a linear solve when the
+// residual already bounds the next update below tol. The Jacobian J = L + diag(g'(phi)) has
+// L symmetric with zero row sums and non-positive off-diagonals (periodic or mirror-wall
+// rows), so J is an M-matrix with row sums g'(phi_j) and ||J^-1||_inf <= 1 / min_j g'(phi_j):
+// the next Newton update is at most max|F| / min g' in every component.
 
 constexpr int kClusterMax = 16;
+constexpr int kNewtonMaxThreads = 512;  // nodes (threads) per block: 16 blocks cover the largest grid
 
-// exp(x) for |x| <= 2^-5 by its Taylor polynomial to degree 8 (relative error < 1e-18).
+// exp(x) for |x| <= 2^-5 by its Taylor polynomial to degree 8 (relative error < 1e-18),
+// evaluated by Estrin's scheme: a dependent FP64 operation costs ~100 cycles here, and the
+// scheme's dependency depth is 5 instead of the 9 of Horner's rule.
 __device__ __forceinline__ double exp_small(double x)
 {
-    double p = 1.0 / 40320.0;
-    p = fma(p, x, 1.0 / 5040.0);
-    p = fma(p, x, 1.0 / 720.0);
-    p = fma(p, x, 1.0 / 120.0);
-    p = fma(p, x, 1.0 / 24.0);
-    p = fma(p, x, 1.0 / 6.0);
-    p = fma(p, x, 0.5);
-    p = fma(p, x, 1.0);
-    return fma(p, x, 1.0);
+    const double x2 = x * x, x4 = x2 * x2;
+    const double p01 = 1.0 + x, p23 = fma(x, 1.0 / 6.0, 0.5), p45 = fma(x, 1.0 / 120.0, 1.0 / 24.0),
+                 p67 = fma(x, 1.0 / 5040.0, 1.0 / 720.0);
+    const double lo = fma(x2, p23, p01), hi = fma(x2, p67, p45);
+    return fma(x4, fma(x4, 1.0 / 40320.0, hi), lo);
+}
+
+// exp(x) for |x| <= 2^-10 to degree 4 (relative error < 1e-17), dependency depth 3.
+__device__ __forceinline__ double exp_tiny(double x)
+{
+    const double x2 = x * x;
+    return fma(x2, fma(x2, 1.0 / 24.0, fma(x, 1.0 / 6.0, 0.5)), 1.0 + x);
 }
 
 // Reciprocal for the elimination (and the 2x2 inverses of the boundary system): the fast FP32
@@ -75,84 +91,40 @@ __device__ __forceinline__ double recip(double x)
     return r * fma(-x, r, 2.0);
 }
 
+// Parallel cyclic reduction of a scalar tridiagonal system held by lanes 0 .. n-1 of the
+// calling warp (n a power of two, <= 32; all 32 lanes call it; a lane without a row holds the
+// identity row). Row k: a x_{k-1} + b x_k + c x_{k+1} = r (three right-hand sides r0, r1,
+// r2). cyclic: rows couple to (k +- 1) mod n; else the chain ends at 0 and n - 1. Returns
+// x_k for each right-hand side (after the last step of a cyclic system its remaining
+// couplings reach the row itself and are folded into the diagonal).
 template <typename T>
-struct M2 {
-    T a, b, c, d;  // [[a, b], [c, d]]
-};
-template <typename T>
-__device__ __forceinline__ M2<T> mmul(M2<T> x, M2<T> y)
+__device__ __forceinline__ void warp_scalar_pcr(T a, T b, T c, T r0, T r1, T r2, int n, bool cyclic, T& x0, T& x1,
+                                                T& x2)
 {
-    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
-}
-template <typename T>
-__device__ __forceinline__ M2<T> msub(M2<T> x, M2<T> y)
-{
-    return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d};
-}
-template <typename T>
-__device__ __forceinline__ M2<T> minv(M2<T> x)
-{
-    const T r = recip(x.a * x.d - x.b * x.c);
-    return {x.d * r, -x.b * r, -x.c * r, x.a * r};
-}
-template <typename T>
-__device__ __forceinline__ void mvec(M2<T> x, T v0, T v1, T* o0, T* o1)
-{
-    *o0 = x.a * v0 + x.b * v1;
-    *o1 = x.c * v0 + x.d * v1;
-}
-
-// Block cyclic reduction of the G block rows (thread k < G owns row k) stored as full
-// 2x2 matrices: L3[k] = {Mk(4), Dk(4), Pk(4), rk(2)}, row k: Mk z_{k-1} + Dk z_k + Pk z_{k+1} = rk.
-// After the steps with stride G/2 every row couples only to itself. zsol gets z. (On a
-// bounded grid the corner blocks M_0 and P_{G-1} are zero, so the wrap adds nothing.)
-// The steps alternate between L3 and L3n, one barrier per step.
-template <typename T>
-__device__ void block_pcr(T* L3, T* L3n, T* zsol, int G)
-{
-    const int k = threadIdx.x;
-    auto ld = [](const T* p) { return M2<T>{p[0], p[1], p[2], p[3]}; };
-    auto st = [](T* p, M2<T> m) {
-        p[0] = m.a;
-        p[1] = m.b;
-        p[2] = m.c;
-        p[3] = m.d;
-    };
-    for (int s = 1; s <= G / 2; s <<= 1) {
-        if (k < G) {
-            const T* c = L3 + 14 * k;
-            const T* lm = L3 + 14 * ((k - s + G) % G);
-            const T* lp = L3 + 14 * ((k + s) % G);
-            const M2<T> al = mmul(ld(c), minv(ld(lm + 4)));      // Mk D_{k-s}^-1
-            const M2<T> ga = mmul(ld(c + 8), minv(ld(lp + 4)));  // Pk D_{k+s}^-1
-            T* o = L3n + 14 * k;
-            const M2<T> nM = mmul(al, ld(lm));
-            const M2<T> nP = mmul(ga, ld(lp + 8));
-            st(o, M2<T>{-nM.a, -nM.b, -nM.c, -nM.d});
-            st(o + 8, M2<T>{-nP.a, -nP.b, -nP.c, -nP.d});
-            st(o + 4, msub(msub(ld(c + 4), mmul(al, ld(lm + 8))), mmul(ga, ld(lp))));
-            T ra0, ra1, rg0, rg1;
-            mvec(al, lm[12], lm[13], &ra0, &ra1);
-            mvec(ga, lp[12], lp[13], &rg0, &rg1);
-            o[12] = c[12] - ra0 - rg0;
-            o[13] = c[13] - ra1 - rg1;
-        }
-        __syncthreads();  // the next step reads L3n and overwrites L3, whose reads are done
-        T* t = L3;
-        L3 = L3n;
-        L3n = t;
+    const int k = threadIdx.x & 31;
+    for (int s = 1; s < n; s <<= 1) {
+        const int km = (k - s + n) % n, kp = (k + s) % n;
+        const T am = __shfl_sync(0xFFFFFFFFu, a, km), bm = __shfl_sync(0xFFFFFFFFu, b, km);
+        const T cm = __shfl_sync(0xFFFFFFFFu, c, km), q0m = __shfl_sync(0xFFFFFFFFu, r0, km);
+        const T q1m = __shfl_sync(0xFFFFFFFFu, r1, km), q2m = __shfl_sync(0xFFFFFFFFu, r2, km);
+        const T ap = __shfl_sync(0xFFFFFFFFu, a, kp), bp = __shfl_sync(0xFFFFFFFFu, b, kp);
+        const T cp = __shfl_sync(0xFFFFFFFFu, c, kp), q0p = __shfl_sync(0xFFFFFFFFu, r0, kp);
+        const T q1p = __shfl_sync(0xFFFFFFFFu, r1, kp), q2p = __shfl_sync(0xFFFFFFFFu, r2, kp);
+        const bool hm = k < n && (cyclic || k >= s), hp = k < n && (cyclic || k + s < n);
+        const T al = hm ? a * recip(bm) : T(0);
+        const T ga = hp ? c * recip(bp) : T(0);
+        a = -al * am;
+        c = -ga * cp;
+        b = b - al * cm - ga * ap;
+        r0 = r0 - al * q0m - ga * q0p;
+        r1 = r1 - al * q1m - ga * q1p;
+        r2 = r2 - al * q2m - ga * q2p;
     }
-    if (k < G) {
-        const T* c = L3 + 14 * k;
-        M2<T> Dt = ld(c + 4);
-        const M2<T> Mm = ld(c), Pm = ld(c + 8);
-        Dt = M2<T>{Dt.a + Mm.a + Pm.a, Dt.b + Mm.b + Pm.b, Dt.c + Mm.c + Pm.c, Dt.d + Mm.d + Pm.d};
-        T z0, z1;
-        mvec(minv(Dt), c[12], c[13], &z0, &z1);
-        zsol[2 * k] = z0;
-        zsol[2 * k + 1] = z1;
-    }
-    __syncthreads();
+    const T bt = cyclic ? a + b + c : b;
+    const T rb = recip(bt);
+    x0 = r0 * rb;
+    x1 = r1 * rb;
+    x2 = r2 * rb;
 }
 
 // Parameters of one field solve (one realisation).
@@ -171,6 +143,53 @@ struct FieldDesc {
     int extrap, pad2;
 };
 
+// Parallel cyclic reduction of the 32 rows held by the calling warp (one per lane; a lane
+// without a row holds the identity row). Row i: a x_{i-1} + b x_i + c x_{i+1} = d, with the
+// couplings to rows outside the warp already moved to the columns gc (left) and hc (right).
+// On return every row is decoupled: b x_i = d - gc X_left - hc X_right.
+template <typename T>
+__device__ __forceinline__ void warp_pcr(T& a, T& b, T& c, T& d, T& gc, T& hc)
+{
+    const int lane = threadIdx.x & 31;
+    T rb = recip(b);
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const T am = __shfl_up_sync(0xFFFFFFFFu, a, s), cm = __shfl_up_sync(0xFFFFFFFFu, c, s);
+        const T dm = __shfl_up_sync(0xFFFFFFFFu, d, s), gm = __shfl_up_sync(0xFFFFFFFFu, gc, s);
+        const T hm = __shfl_up_sync(0xFFFFFFFFu, hc, s), rm = __shfl_up_sync(0xFFFFFFFFu, rb, s);
+        const T ap = __shfl_down_sync(0xFFFFFFFFu, a, s), cp = __shfl_down_sync(0xFFFFFFFFu, c, s);
+        const T dp = __shfl_down_sync(0xFFFFFFFFu, d, s), gp = __shfl_down_sync(0xFFFFFFFFu, gc, s);
+        const T hp = __shfl_down_sync(0xFFFFFFFFu, hc, s), rp = __shfl_down_sync(0xFFFFFFFFu, rb, s);
+        const T al = (lane >= s) ? a * rm : T(0);
+        const T ga = (lane + s < 32) ? c * rp : T(0);
+        a = -al * am;
+        c = -ga * cp;
+        b = b - al * cm - ga * ap;
+        d = d - al * dm - ga * dp;
+        gc = gc - al * gm - ga * gp;
+        hc = hc - al * hm - ga * hp;
+        rb = recip(b);
+    }
+    d *= rb;
+    gc *= rb;
+    hc *= rb;
+}
+
+// Values every block pushes into every block's shared memory before the first cluster barrier
+// of a Newton iteration (slot k holds block k's): its first interior row and its last interior
+// row in terms of the block separators around it (x = y - g s_{k-1} - h s_k), its separator
+// row (a, b, c, d of row s_k), and its residual bound (max |F|, min g').
+constexpr int kPush = 12;
+
+// A block's first interior row from its pushed values, given the separators around the block
+// (the owner and its left neighbour evaluate this same function, so the neighbour's halo stays
+// bit-identical to the owner's node).
+template <typename T>
+__device__ __forceinline__ T edge_row(const T* r, T s_left, T s_right)
+{
+    return r[0] - r[1] * s_left - r[2] * s_right;
+}
+
 // Solver body for the realisation of this cluster: B = ncell / G nodes per block, one per
 // thread; threads at or beyond B (a batched launch sized for a larger grid) only take
 // part in the barriers. T is the precision of the linear solve.
@@ -182,23 +201,23 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     const int g = (int)cluster.block_rank();
     const int ncell = d.ncell;
     const int B = ncell / G;
-    const int i = threadIdx.x;
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    const int W = (B + 31) >> 5;  // warps holding rows
     const bool act = i < B;
     const long long* rho = d.rho;
     double* phi = d.phi;
     const double dx = d.dx, nscale = d.nscale, tol = d.tol;
     const int mode = d.mode, maxit = d.maxit;
-    double* ph = sh;                             // [B + 2]
-    double* mymax = ph + B + 2;                  // [1]
-    // two sets of the seven row arrays (A, Bd, C, D, Gs, Hs, Rb: sub-, main and super-diagonal,
-    // right-hand side, the two coupling columns, reciprocal of the diagonal); the reduction
-    // steps alternate between them
-    T* rows = reinterpret_cast<T*>(mymax + 1);   // [2][7][B]
-    T* red = rows + 14 * B;  // [32]
-    T* mine = red + 32;  // [6]
-    T* L3 = mine + 8;    // [G][14]
-    T* L3n = L3 + 14 * G;
-    T* zsol = L3n + 14 * G;  // [2G]
+    double* ph = sh;                              // [B + 2] phi with the halo
+    T* recv = reinterpret_cast<T*>(ph + B + 2);   // [G][kPush] rows pushed by every block
+    T* recvm = recv + kPush * G;                  // [G] every block's max |update|
+    T* wedge = recvm + G;                         // [W][8]: warp w's first interior row (y, g, h),
+                                                  // last interior row (y, g, h), max|F|, min g'
+    T* wsep = wedge + 8 * W;                      // [W][4]: warp w's separator row (a, b, c, d)
+    T* lev2 = wsep + 4 * W;                       // [W][3]: S_w = Y - Gc s_{k-1} - Hc s_k
+    T* svals = lev2 + 3 * W;                      // [G]: every block separator s_k
+    T* wmax = svals + G;                          // [32]: per-warp max |update|
+    T* flag = wmax + 32;                          // [1]: converged by the residual bound
 
     const int mask = ncell - 1;
     const int j = g * B + (act ? i : 0);
@@ -208,26 +227,24 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
     const T o = (T)(-inv_dx2);
     const bool boltz = (mode == PE_POISSON_BOLTZMANN);
     const double nj = act ? (double)__ldg(rho + j) * nscale * ((wl || wr) ? 2.0 : 1.0) : 0.0;
-    double pj = act ? phi[j] : 0.0;
-    if (d.phi_prev && act) {
-        const double pp = d.phi_prev[j];
-        d.phi_prev[j] = pj;
-        if (d.extrap) {
-            pj = 2.0 * pj - pp;
-            phi[j] = pj;
-        }
-    }
-    if (d.phi_prev && d.extrap) {  // extrapolated starts visible to the neighbouring blocks' halos
-        __threadfence();
-        cluster.sync();
-    }
+    // Newton start: phi, or with extrap the extrapolation 2 phi - phi_prev of the last two
+    // solutions. Nothing is written to phi or phi_prev before the first cluster barrier, so the
+    // halo nodes below (the neighbouring blocks' boundary nodes) are read unchanged and
+    // extrapolated here with the owners' arithmetic.
+    const bool hist = d.phi_prev != nullptr, ex = hist && d.extrap;
+    const double p_old = act ? phi[j] : 0.0;
+    double pj = (act && ex) ? 2.0 * p_old - d.phi_prev[j] : p_old;
     double gj = boltz ? exp(pj) : 1.0 + pj;
-    // Halo ph[0], ph[B + 1]: the neighbouring blocks' boundary nodes, read once and then
-    // advanced here with the same damped updates their owners apply (the boundary unknowns of
-    // the reduced system, known to every block), so they stay bit-identical to the owners'
-    // values. Only threads 0 and B - 1 read and write them.
-    if (act && i == 0) ph[0] = phi[(g * B - 1) & mask];
-    if (act && i == B - 1) ph[B + 1] = phi[(g * B + B) & mask];
+    // Halo ph[0], ph[B + 1]: read once and then advanced here with the same damped updates their
+    // owners apply (values of the reduced systems, known to every block), so they stay
+    // bit-identical to the owners' values. Only threads 0 and B - 1 read and write them.
+    if (act && (i == 0 || i == B - 1)) {
+        const int h = (i == 0) ? ((g * B - 1) & mask) : ((g * B + B) & mask);
+        const double v = phi[h];
+        ph[i == 0 ? 0 : B + 1] = ex ? 2.0 * v - d.phi_prev[h] : v;
+    }
+    bool hist_written = false;
+    const int sep = (w == W - 1) ? ((B - 1) & 31) : 31;  // this warp's separator lane
 
     int it = 0;
     bool converged = false;
@@ -235,131 +252,241 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         // ---- FP64 residual with the halo from the neighbouring blocks (mirror ghosts at walls)
         if (act) ph[i + 1] = pj;
         __syncthreads();
-        T* A = rows;
-        T* Bd = A + B;
-        T* C = Bd + B;
-        T* D = C + B;
-        T* Gs = D + B;
-        T* Hs = Gs + B;
-        T* Rb = Hs + B;
+        T a = T(0), b = T(1), c = T(0), rhs = T(0), gc = T(0), hc = T(0);
+        float fabs_r = 0.f, gmin = 3.0e38f;
+        T sa = T(0), sb = T(1), sc = T(0), sd = T(0);  // the separator's row (lane sep)
         if (act) {
             const double pl = wl ? ph[i + 2] : ph[i], pr = wr ? ph[i] : ph[i + 2];
             const double lap = (pl - 2.0 * pj + pr) * inv_dx2;
-            A[i] = (i == 0) ? T(0) : (wr ? T(2) * o : o);
-            C[i] = (i == B - 1) ? T(0) : (wl ? T(2) * o : o);
-            Bd[i] = (T)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
-            Rb[i] = recip(Bd[i]);
-            D[i] = (T)(lap - gj + nj);  // -F_j
-            Gs[i] = (i == 0 && !wl) ? o : T(0);
-            Hs[i] = (i == B - 1 && !wr) ? o : T(0);
-        }
-        __syncthreads();
-        // ---- parallel cyclic reduction of the block rows, three right-hand sides; step s reads
-        // one row set and writes the other, so one barrier per step separates the steps
-        for (int s = 1; s < B; s <<= 1) {
-            T* nx = (A == rows) ? rows + 7 * B : rows;  // the other row set
-            const int im = act ? i - s : -1, ip = act ? i + s : B;
-            const T al = (im >= 0) ? A[i] * Rb[im] : T(0);
-            const T ga = (ip < B) ? C[i] * Rb[ip] : T(0);
-            const T nA = (im >= 0) ? -al * A[im] : T(0);
-            const T nC = (ip < B) ? -ga * C[ip] : T(0);
-            T nB = act ? Bd[i] : T(0), nD = act ? D[i] : T(0), nG = act ? Gs[i] : T(0), nH = act ? Hs[i] : T(0);
-            if (im >= 0) {
-                nB -= al * C[im];
-                nD -= al * D[im];
-                nG -= al * Gs[im];
-                nH -= al * Hs[im];
+            const double r = lap - gj + nj;  // -F_j
+            fabs_r = (float)fabs(r);
+            gmin = boltz ? (float)gj : 1.0f;
+            const T lo = wr ? T(2) * o : o, up = wl ? T(2) * o : o;  // mirror ghosts double a wall row's coupling
+            const T bd = (T)(2.0 * inv_dx2 + (boltz ? gj : 1.0));
+            if (lane == sep) {  // separator: an identity row in the warp's reduction
+                sa = wl ? T(0) : lo;
+                sb = bd;
+                sc = wr ? T(0) : up;
+                sd = (T)r;
+            } else {
+                b = bd;
+                rhs = (T)r;
+                // couplings to the separators around the interior become extra right-hand sides
+                if (lane == 0) gc = wl ? T(0) : lo;
+                else a = lo;
+                if (lane == sep - 1) hc = wr ? T(0) : up;
+                else c = up;
             }
-            if (ip < B) {
-                nB -= ga * A[ip];
-                nD -= ga * D[ip];
-                nG -= ga * Gs[ip];
-                nH -= ga * Hs[ip];
-            }
-            A = nx;
-            Bd = nx + B;
-            C = nx + 2 * B;
-            D = nx + 3 * B;
-            Gs = nx + 4 * B;
-            Hs = nx + 5 * B;
-            Rb = nx + 6 * B;
-            if (act) {
-                A[i] = nA;
-                C[i] = nC;
-                Bd[i] = nB;
-                Rb[i] = recip(nB);
-                D[i] = nD;
-                Gs[i] = nG;
-                Hs[i] = nH;
-            }
-            __syncthreads();
         }
-        const T rb = act ? Rb[i] : T(0);
-        const T y = act ? D[i] * rb : T(0), gsp = act ? Gs[i] * rb : T(0),
-                hsp = act ? Hs[i] * rb : T(0);  // x = y - g X_left - h X_right
-        if (i == 0) {
-            mine[0] = y;
-            mine[1] = gsp;
-            mine[2] = hsp;
-        }
-        if (i == B - 1) {
-            mine[3] = y;
-            mine[4] = gsp;
-            mine[5] = hsp;
-        }
-        cluster.sync();  // #1: every block's boundary rows are visible
-        // ---- cyclic block-tridiagonal system of the blocks' (first, last) unknowns
-        if (i < G) {
-            const T* rem = cluster.map_shared_rank(mine, i);
-            T* r = L3 + 14 * i;
-            // F_k + g0 L_{k-1} + h0 F_{k+1} = y0 ;  L_k + gB L_{k-1} + hB F_{k+1} = yB
-            r[0] = T(0); r[1] = rem[1]; r[2] = T(0); r[3] = rem[4];     // M: picks L_{k-1}
-            r[4] = T(1); r[5] = T(0);   r[6] = T(0); r[7] = T(1);       // D = I
-            r[8] = rem[2]; r[9] = T(0); r[10] = rem[5]; r[11] = T(0);   // P: picks F_{k+1}
-            r[12] = rem[0]; r[13] = rem[3];
-        }
-        __syncthreads();
-        block_pcr<T>(L3, L3n, zsol, G);
-        const T Xl = zsol[2 * ((g - 1 + G) % G) + 1];  // previous block's last unknown
-        const T Xr = zsol[2 * ((g + 1) % G)];          // next block's first unknown
-        // the block's own first and last unknowns are those of the reduced system (equal to
-        // y - g X_left - h X_right up to rounding), so that the neighbours' halos follow them
-        const T dlt = (i == 0) ? zsol[2 * g] : ((i == B - 1) ? zsol[2 * g + 1] : y - gsp * Xl - hsp * Xr);
-        // ---- global max |update| (damping and convergence)
-        T mloc = act ? (dlt < T(0) ? -dlt : dlt) : T(0);
+        // ---- warp interiors: x = rhs - gc S_left - hc S_right
+        warp_pcr(a, b, c, rhs, gc, hc);
+        float fr = fabs_r, gm = gmin;
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            const T oth = __shfl_xor_sync(0xffffffffu, mloc, off);
+            fr = fmaxf(fr, __shfl_xor_sync(0xFFFFFFFFu, fr, off));
+            gm = fminf(gm, __shfl_xor_sync(0xFFFFFFFFu, gm, off));
+        }
+        if (w < W) {
+            T* e = wedge + 8 * w;
+            if (lane == 0) {
+                e[0] = rhs;
+                e[1] = gc;
+                e[2] = hc;
+                e[6] = (T)fr;
+                e[7] = (T)gm;
+            }
+            if (lane == sep - 1) {
+                e[3] = rhs;
+                e[4] = gc;
+                e[5] = hc;
+            }
+            if (lane == sep) {
+                wsep[4 * w] = sa;
+                wsep[4 * w + 1] = sb;
+                wsep[4 * w + 2] = sc;
+                wsep[4 * w + 3] = sd;
+            }
+        }
+        __syncthreads();
+        // ---- warp 0: the block's warp separators S_0 .. S_{W-2} in terms of the block
+        // separators s_{k-1} (left) and s_k (right), then the block's rows for the cluster system
+        if (w == 0) {
+            // row q = lane < W - 1: separator of warp q, between warp q's last interior row and
+            // warp q+1's first interior row
+            T la = T(0), lb = T(1), lc = T(0), r0 = T(0), r1 = T(0), r2 = T(0);
+            if (lane < W - 1) {
+                const T* ep = wedge + 8 * lane;        // warp q
+                const T* en = wedge + 8 * (lane + 1);  // warp q + 1
+                const T* sr = wsep + 4 * lane;
+                la = -sr[0] * ep[4];
+                lb = sr[1] - sr[0] * ep[5] - sr[2] * en[1];
+                lc = -sr[2] * en[2];
+                r0 = sr[3] - sr[0] * ep[3] - sr[2] * en[0];
+                if (lane == 0) {  // S_{-1} = s_{k-1}
+                    r1 = la;
+                    la = T(0);
+                }
+                if (lane == W - 2) {  // S_{W-1} = s_k
+                    r2 = lc;
+                    lc = T(0);
+                }
+            }
+            T Y = T(0), Gc = T(0), Hc = T(0);
+            warp_scalar_pcr(la, lb, lc, r0, r1, r2, W, false, Y, Gc, Hc);
+            if (lane < W - 1) {
+                lev2[3 * lane] = Y;
+                lev2[3 * lane + 1] = Gc;
+                lev2[3 * lane + 2] = Hc;
+            }
+            // the block's first interior row (warp 0, lane 0) and last interior row (warp W-1,
+            // lane sep-1), each in terms of s_{k-1} and s_k
+            const T* e0 = wedge;
+            const T* eL = wedge + 8 * (W - 1);
+            const T Y0 = __shfl_sync(0xFFFFFFFFu, Y, 0), G0 = __shfl_sync(0xFFFFFFFFu, Gc, 0),
+                    H0 = __shfl_sync(0xFFFFFFFFu, Hc, 0);
+            const int ql = W >= 2 ? W - 2 : 0;
+            const T YL = __shfl_sync(0xFFFFFFFFu, Y, ql), GL = __shfl_sync(0xFFFFFFFFu, Gc, ql),
+                    HL = __shfl_sync(0xFFFFFFFFu, Hc, ql);
+            T row[kPush];
+            if (W > 1) {  // first row: x = y - g s_{k-1} - h S_0; last row: x = y - g S_{W-2} - h s_k
+                row[0] = e0[0] - e0[2] * Y0;
+                row[1] = e0[1] - e0[2] * G0;
+                row[2] = -e0[2] * H0;
+                row[3] = eL[3] - eL[4] * YL;
+                row[4] = -eL[4] * GL;
+                row[5] = eL[5] - eL[4] * HL;
+            } else {
+                row[0] = e0[0];
+                row[1] = e0[1];
+                row[2] = e0[2];
+                row[3] = eL[3];
+                row[4] = eL[4];
+                row[5] = eL[5];
+            }
+            const T* sL = wsep + 4 * (W - 1);  // the block separator s_k
+            row[6] = sL[0];
+            row[7] = sL[1];
+            row[8] = sL[2];
+            row[9] = sL[3];
+            // residual bound of the block
+            T fb = lane < W ? wedge[8 * lane + 6] : T(0), gb = lane < W ? wedge[8 * lane + 7] : T(3.0e38f);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T f2 = __shfl_xor_sync(0xFFFFFFFFu, fb, off), g2 = __shfl_xor_sync(0xFFFFFFFFu, gb, off);
+                fb = f2 > fb ? f2 : fb;
+                gb = g2 < gb ? g2 : gb;
+            }
+            row[10] = fb;
+            row[11] = gb;
+            if (lane < G) {  // lane r pushes the block's rows into block r's shared memory
+                T* dst = cluster.map_shared_rank(recv, lane) + kPush * g;
+#pragma unroll
+                for (int c2 = 0; c2 < kPush; ++c2) dst[c2] = row[c2];
+            }
+        }
+        cluster.sync();  // #1: every block's pushed rows are visible in every block
+        if (hist && !hist_written) {  // every block has read its halo: the history may move on
+            if (act) d.phi_prev[j] = p_old;
+            hist_written = true;
+        }
+        // ---- warp 0: the cyclic system of the block separators s_0 .. s_{G-1}, and the residual bound
+        if (w == 0) {
+            T la = T(0), lb = T(1), lc = T(0), r0 = T(0);
+            T fb = T(0), gb = T(3.0e38f);
+            if (lane < G) {
+                // row of s_k: a x_last(k) + b s_k + c x_first(k+1) = d
+                const T* rk = recv + kPush * lane;
+                const T* rn = recv + kPush * ((lane + 1) % G);
+                la = -rk[6] * rk[4];
+                lb = rk[7] - rk[6] * rk[5] - rk[8] * rn[1];
+                lc = -rk[8] * rn[2];
+                r0 = rk[9] - rk[6] * rk[3] - rk[8] * rn[0];
+                fb = rk[10];
+                gb = rk[11];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T f2 = __shfl_xor_sync(0xFFFFFFFFu, fb, off), g2 = __shfl_xor_sync(0xFFFFFFFFu, gb, off);
+                fb = f2 > fb ? f2 : fb;
+                gb = g2 < gb ? g2 : gb;
+            }
+            T sk, u1, u2;
+            warp_scalar_pcr(la, lb, lc, r0, T(0), T(0), G, true, sk, u1, u2);
+            if (lane < G) svals[lane] = sk;
+            // the residual bounds the next update below tol: phi is converged (the same decision
+            // in every block: the same pushed values reduced in the same order)
+            if (lane == 0) flag[0] = (it > 0 && (double)fb < tol * (double)gb) ? T(1) : T(0);
+        }
+        __syncthreads();
+        if (flag[0] != T(0)) {
+            converged = true;
+            break;
+        }
+        const T Sl = svals[(g - 1 + G) % G], Sr = svals[g];  // s_{k-1}, s_k
+        // ---- back substitution: the warp's separators, then its row
+        T dlt = T(0);
+        if (act) {
+            const T Sw_l = (w == 0) ? Sl : lev2[3 * (w - 1)] - lev2[3 * (w - 1) + 1] * Sl - lev2[3 * (w - 1) + 2] * Sr;
+            const T Sw_r = (w == W - 1) ? Sr : lev2[3 * w] - lev2[3 * w + 1] * Sl - lev2[3 * w + 2] * Sr;
+            if (lane == sep) dlt = Sw_r;
+            else if (i == 0)  // the block's first row: the form the left neighbour uses for its halo
+                dlt = edge_row(recv + kPush * g, Sl, Sr);
+            else
+                dlt = rhs - gc * Sw_l - hc * Sw_r;
+        }
+        // ---- global max |update| (damping and convergence): pushed to every block
+        T mloc = dlt < T(0) ? -dlt : dlt;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const T oth = __shfl_xor_sync(0xFFFFFFFFu, mloc, off);
             mloc = oth > mloc ? oth : mloc;
         }
-        if ((i & 31) == 0) red[i >> 5] = mloc;
+        if (lane == 0) wmax[w] = mloc;
         __syncthreads();
-        if (i < 32) {
-            T v = (i < ((blockDim.x + 31) >> 5)) ? red[i] : T(0);
+        if (w == 0) {
+            T v = (lane < ((int)(blockDim.x + 31) >> 5)) ? wmax[lane] : T(0);
+#pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                const T oth = __shfl_xor_sync(0xffffffffu, v, off);
+                const T oth = __shfl_xor_sync(0xFFFFFFFFu, v, off);
                 v = oth > v ? oth : v;
             }
-            if (i == 0) *mymax = (double)v;
+            v = __shfl_sync(0xFFFFFFFFu, v, 0);
+            if (lane < G) cluster.map_shared_rank(recvm, lane)[g] = v;
         }
-        // #2: block maxima visible; level-3 rows no longer read. The next iteration rewrites
-        // mine and mymax only after its barrier #1, which every block reaches after reading them.
+        // #2: every block's maximum is visible; the pushed rows are no longer read. The next
+        // iteration pushes again only after its barrier #1, which every block reaches after
+        // reading these.
         cluster.sync();
-        double m = 0.0;
-        for (int k = 0; k < G; ++k) m = fmax(m, *cluster.map_shared_rank(mymax, k));
+        T mm = T(0);
+        for (int k = 0; k < G; ++k) mm = recvm[k] > mm ? recvm[k] : mm;
+        const double m = (double)mm;
         const double scale = (m > 2.0) ? 2.0 / m : 1.0;
         const double x = act ? scale * (double)dlt : 0.0;
         pj += x;
         if (act) phi[j] = pj;
-        if (act && i == 0) ph[0] += scale * (double)Xl;
-        if (act && i == B - 1) ph[B + 1] += scale * (double)Xr;
-        if (boltz)
-            gj = (fabs(x) <= 0.03125) ? gj * exp_small(x) : exp(pj);
-        else
+        if (act && i == 0) ph[0] += scale * (double)Sl;  // the previous block's last node is s_{k-1}
+        if (act && i == B - 1) {  // the next block's first row, as its owner computes it
+            ph[B + 1] += scale * (double)edge_row(recv + kPush * ((g + 1) % G), Sr, svals[(g + 1) % G]);
+        }
+        if (boltz) {  // |x| <= scale m for every node: the degree follows the cluster-wide bound
+            if (scale * m <= 0.0009765625)
+                gj *= exp_tiny(x);
+            else
+                gj = (fabs(x) <= 0.03125) ? gj * exp_small(x) : exp(pj);
+        } else {
             gj = 1.0 + pj;
+        }
         if (m < tol) {
             converged = true;
             ++it;
             break;
+        }
+    }
+    if (hist && !hist_written) {  // no iteration ran (maxit 0): the start is the solution
+        cluster.sync();           // every block has read its halo
+        if (act) {
+            d.phi_prev[j] = p_old;
+            phi[j] = pj;
         }
     }
     if (act) ph[i + 1] = pj;
@@ -378,11 +505,11 @@ __device__ __forceinline__ void newton_body(const FieldDesc& d, cg::cluster_grou
         }
         if (!converged) raise_flag(d.status, PE_FLAG_NOCONV);
     }
-    cluster.sync();  // no block leaves while another may still read its mymax
+    cluster.sync();  // no block leaves while another may still push into it
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_newton_cluster(FieldDesc d)
+__global__ void __launch_bounds__(kNewtonMaxThreads, 1) k_newton_cluster(FieldDesc d)
 {
     cg::cluster_group cluster = cg::this_cluster();
     newton_body<T>(d, cluster);
@@ -390,7 +517,7 @@ __global__ void __launch_bounds__(1024) k_newton_cluster(FieldDesc d)
 
 // One cluster per realisation: cluster c solves descs[c]; extrap applies to every realisation.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_newton_batch(const FieldDesc* descs, int extrap)
+__global__ void __launch_bounds__(kNewtonMaxThreads, 1) k_newton_batch(const FieldDesc* descs, int extrap)
 {
     cg::cluster_group cluster = cg::this_cluster();
     FieldDesc d = descs[blockIdx.x / cluster.num_blocks()];
@@ -429,14 +556,15 @@ static int cluster_size_for(int ncell)
     int G = cached[dev];
     while (G > 1 && ncell / G < 32) G >>= 1;  // at least 32 nodes per block
     if (ncell < kClusterMinCells) G = 1;
-    while (ncell / G > 1024) G <<= 1;          // at most 1024 nodes (threads) per block
+    while (ncell / G > kNewtonMaxThreads) G <<= 1;  // at most kNewtonMaxThreads nodes (threads) per block
     return G <= kClusterMax ? G : 0;
 }
 
 size_t newton_smem_bytes(int B, int G, bool fp64)
 {
     const size_t t = fp64 ? sizeof(double) : sizeof(float);
-    return sizeof(double) * ((size_t)B + 3) + t * (14 * (size_t)B + 32 + 8 + 30 * (size_t)G) + 16;
+    const size_t W = ((size_t)B + 31) / 32;
+    return sizeof(double) * ((size_t)B + 2) + t * ((kPush + 2) * (size_t)G + 15 * W + 33) + 16;
 }
 
 static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute* attr, int G, int nclusters, int block, size_t smem,
@@ -461,7 +589,7 @@ static int launch_newton_cluster(int G, const long long* rho, int ncell, double 
                                  uint32_t* status, double* phi_prev, int extrap, cudaStream_t s)
 {
     const int B = ncell / G;  // one node per thread
-    if (B > 1024 || B < 2) return PE_EINVAL;
+    if (B > kNewtonMaxThreads || B < 2) return PE_EINVAL;
     const bool fp64 = walls != 0;
     const size_t smem = newton_smem_bytes(B, G, fp64);
     const void* k = fp64 ? (const void*)k_newton_cluster<double> : (const void*)k_newton_cluster<float>;
@@ -483,7 +611,7 @@ int newton_cluster_size(int ncell) { return cluster_size_for(ncell); }
 int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s)
 {
     const int B = max_ncell / G;
-    if (B > 1024 || B < 2 || R < 1) return PE_EINVAL;
+    if (B > kNewtonMaxThreads || B < 2 || R < 1) return PE_EINVAL;
     const size_t smem = newton_smem_bytes(B, G, fp64);
     const void* k = fp64 ? (const void*)k_newton_batch<double> : (const void*)k_newton_batch<float>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
