@@ -47,7 +47,12 @@ KERNEL_BYTES = {
 # summarised in profiles/, each valid while the particle kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
 NCU_TRAFFIC = {
-    "push_sample": {"source_hash": "35e21ff27381b258", "bytes": 270.735360e6 + 145.710336e6},
+    "push_sample": {"source_hash": "036e486a153bb58d", "bytes": 270.727680e6 + 145.672704e6},
+    "push": {"source_hash": "036e486a153bb58d", "bytes": 270.705664e6 + 146.097152e6},
+    "sample": {"source_hash": "036e486a153bb58d", "bytes": 270.664448e6 + 3.045376e6},
+    "deposit": {"source_hash": "036e486a153bb58d", "bytes": 203.015680e6 + 3.054848e6},
+    "push_sample_ps": {"source_hash": "036e486a153bb58d", "bytes": 270.333440e6 + 145.685760e6},
+    "load": {"source_hash": "036e486a153bb58d", "bytes": 0.532224e6 + 207.352576e6},
 }
 
 
