@@ -269,6 +269,33 @@ PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64
                           uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
                           void* stream);
 
+/* The storage slots [first, first + n) of pe_quiet_start's point set of n_total points,
+ * written to local arrays of n particles (local particle k = global slot first + k): the
+ * particles one rank holds when a realisation's particles are split over ranks (Appendix C's
+ * point set is defined for the whole realisation, so every slice of it is loaded exactly as
+ * the unsplit run would). If rho_fx != NULL it is overwritten with the charge deposit of
+ * the slice; the deposits of the slices of a partition of [0, n_total) sum to the deposit of
+ * the whole point set, bit for bit (fixed-point integers). Requires n_total a multiple of
+ * ncell and below 2^32, 0 <= first <= n_total - n, n >= 1; arrays as pe_quiet_start's. */
+PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w, int64_t first,
+                                int64_t n, int64_t n_total, int32_t ncell, const float* prof_n,
+                                const float* prof_u, float v_th, uint64_t seed, int32_t s_w,
+                                int64_t* rho_fx, uint32_t* status, void* stream);
+
+/* The fixed-point shifts of the deposit rule (s_w for weights, s_p for momenta) that a context
+ * of nparticles ions on ncell cells uses: s = 22 - ceil(log2 cap) with the weight cap w_cap
+ * (0: 8 ncell / nparticles) and the momentum cap w_cap v_cap (v_cap 0: 32). A realisation
+ * split over ranks uses the shifts of its total particle count on every rank. */
+/* The initial nodal profiles of pe_load_initial, written to host arrays prof_n[ncell] and
+ * prof_u[ncell] (FP32): PE_PROFILE_SINE, the ion-acoustic wave of Section 4.1,
+ * n = 1 + amplitude cos(2 pi x_j / L), u = amplitude cos(2 pi x_j / L) at x_j = j L / ncell;
+ * PE_PROFILE_SLAB, n = 1 on the nodes 7 ncell / 16 .. 9 ncell / 16 and 0 elsewhere, u = 0. */
+PE_API int pe_initial_profile(int32_t profile, int32_t ncell, double L, double amplitude, float* prof_n,
+                              float* prof_u);
+
+PE_API int pe_fixed_point_shifts(int64_t nparticles, int32_t ncell, double w_cap, double v_cap,
+                                 int32_t* s_w, int32_t* s_p);
+
 /* Quiet-start loading with equal weights on a bounded grid (Appendix C's loading, with the
  * particle count of each cell in proportion to its mass, as for Section 4.2's slab whose
  * vacuum cells hold no ions). The nodal density profile (prof_n, its wall nodes multiplied by

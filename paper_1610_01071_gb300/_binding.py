@@ -132,6 +132,9 @@ SIGNATURES = {
     "pe_ls_project": (ctypes.c_int, [P, i32, i32, f64, f64, P, P, P]),
     "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
     "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
+    "pe_quiet_start_slice": (ctypes.c_int, [P, P, P, P, i64, i64, i64, i32, P, P, f32, u64, i32, P, P, P]),
+    "pe_fixed_point_shifts": (ctypes.c_int, [i64, i32, f64, f64, P, P]),
+    "pe_initial_profile": (ctypes.c_int, [i32, i32, f64, f64, P, P]),
     "pe_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, f32, u64, i32, P, P, P, P]),
     "pe_sort": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P, P]),
     "pe_sort_noalloc": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P]),

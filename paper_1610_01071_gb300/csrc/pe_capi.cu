@@ -107,6 +107,17 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 using namespace pe;
 
+extern "C" PE_API int pe_fixed_point_shifts(int64_t nparticles, int32_t ncell, double w_cap, double v_cap,
+                                            int32_t* s_w, int32_t* s_p)
+{
+    if (nparticles < 1 || ncell < 1 || !s_w || !s_p) return PE_EINVAL;
+    const double wc = w_cap > 0.0 ? w_cap : 8.0 * ncell / (double)nparticles;
+    const double vc = v_cap > 0.0 ? v_cap : 32.0;
+    *s_w = fx_shift(wc);
+    *s_p = fx_shift(wc * vc);
+    return PE_OK;
+}
+
 
 extern "C" PE_API const char* pe_strerror(int code)
 {
@@ -562,6 +573,26 @@ static int measure_phase(pe_ctx* x, double* out)
     return pe_ps_coarsen(dst, 1, x->ncoef, x->s_w, out, x->stream);
 }
 
+extern "C" PE_API int pe_initial_profile(int32_t profile, int32_t ncell, double L, double amplitude, float* prof_n,
+                                         float* prof_u)
+{
+    if ((profile != PE_PROFILE_SINE && profile != PE_PROFILE_SLAB) || ncell < 1 || !(L > 0.0) || !prof_n || !prof_u)
+        return PE_EINVAL;
+    const double dx = L / ncell;
+    for (int j = 0; j < ncell; ++j) {
+        if (profile == PE_PROFILE_SLAB) {  // uniform slab on the central eighth, vacuum elsewhere
+            prof_n[j] = (j >= 7 * ncell / 16 && j <= 9 * ncell / 16) ? 1.0f : 0.0f;
+            prof_u[j] = 0.0f;
+            continue;
+        }
+        const double xj = j * dx;
+        const double pert = amplitude * cos(2.0 * M_PI * xj / L);
+        prof_n[j] = (float)(1.0 + pert);
+        prof_u[j] = (float)pert;
+    }
+    return PE_OK;
+}
+
 extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double amplitude)
 {
     NvtxRange nvtx("pe_load_initial");
@@ -570,17 +601,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     const pe_config& c = x->cfg;
     if (profile == PE_PROFILE_SLAB && !x->walls) return PE_EINVAL;
     std::vector<float> h(2 * (size_t)c.ncell);
-    for (int j = 0; j < c.ncell; ++j) {
-        if (profile == PE_PROFILE_SLAB) {  // uniform slab on the central eighth, vacuum elsewhere
-            h[j] = (j >= 7 * c.ncell / 16 && j <= 9 * c.ncell / 16) ? 1.0f : 0.0f;
-            h[c.ncell + j] = 0.0f;
-            continue;
-        }
-        const double xj = j * x->dx;
-        const double pert = amplitude * cos(2.0 * M_PI * xj / c.L);
-        h[j] = (float)(1.0 + pert);
-        h[c.ncell + j] = (float)pert;
-    }
+    PE_TRY(pe_initial_profile(profile, c.ncell, c.L, amplitude, h.data(), h.data() + c.ncell));
     if (cudaMemcpyAsync(x->prof, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, x->stream) != cudaSuccess)
         return PE_ECUDA;
     if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;  // host buffer goes out of scope

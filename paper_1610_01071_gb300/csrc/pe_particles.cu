@@ -547,7 +547,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<MODE>()) k_particles_batc
 // ------------------------------------------------------------------ quiet start
 
 struct LoadParams {
-    int log2ppc;  // >= 0 when ppc is a power of two: cells store their particles by velocity quantile
+    int64_t first;  // global storage slot of local particle 0 (a slice of the point set)
+    int log2ppc;    // >= 0 when ppc is a power of two: cells store their particles by velocity quantile
     int32_t* cell;
     float* theta;
     float* v;
@@ -597,9 +598,9 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
 {
     extern __shared__ uint32_t smem[];
     int64_t begin, end;
-    block_chunk(P.n, P.chunk, &begin, &end);
+    block_chunk(P.n, P.chunk, &begin, &end);  // local slots; global slot = P.first + local
     const bool dep = P.rho != nullptr;
-    const int c_first = (begin < end) ? (int)((uint64_t)begin / P.ppc) : 0;
+    const int c_first = (begin < end) ? (int)((uint64_t)(P.first + begin) / P.ppc) : 0;
     SmemGrid grho{};
     if (dep) {
         grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     int64_t g0, g1;
     warp_groups(gb0, gb1, &g0, &g1);
     LaneWindow lw;
-    lw.reset(((int)((uint64_t)(g0 << 2) / P.ppc) - 1) & P.mask);
+    lw.reset(((int)((uint64_t)(P.first + (g0 << 2)) / P.ppc) - 1) & P.mask);
     bool ovf = false;
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
         int4 c;
         float4 t, vv, ww;
-        const uint32_t i0 = (uint32_t)(g << 2);
+        const uint32_t i0 = (uint32_t)(P.first + (g << 2));
         load_one(P, i0, c.x, t.x, vv.x, ww.x);
         load_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
         load_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         int c;
         float t, vv, ww;
-        load_one(P, (uint32_t)i, c, t, vv, ww);
+        load_one(P, (uint32_t)(P.first + i), c, t, vv, ww);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;
@@ -1127,20 +1128,23 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
     return launch_particles<kSample>(P, (cudaStream_t)stream);
 }
 
-extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
-                                     const float* prof_n, const float* prof_u, float v_th, uint64_t seed, int32_t s_w,
-                                     int64_t* rho_fx, uint32_t* status, void* stream)
+extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w, int64_t first,
+                                           int64_t n, int64_t n_total, int32_t ncell, const float* prof_n,
+                                           const float* prof_u, float v_th, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                                           uint32_t* status, void* stream)
 {
     if (!is_pow2(ncell) || ncell < 8 || !prof_n || !prof_u || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
-    if (n % ncell != 0 || n == 0 || n >= (int64_t(1) << 32)) return PE_EINVAL;
+    if (n_total % ncell != 0 || n_total == 0 || n_total >= (int64_t(1) << 32)) return PE_EINVAL;
+    if (first < 0 || n < 1 || first > n_total - n) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     LoadParams P{};
+    P.first = first;
     P.cell = cell;
     P.theta = theta;
     P.v = v;
     P.w = w;
     P.n = n;
-    P.ppc = (uint32_t)(n / ncell);
+    P.ppc = (uint32_t)(n_total / ncell);
     P.log2ppc = is_pow2(P.ppc) ? ilog2(P.ppc) : -1;
     P.ncell = ncell;
     P.mask = ncell - 1;
@@ -1150,7 +1154,7 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     P.prof_u = prof_u;
     P.v_th = v_th;
     P.wscale = ldexpf(1.0f, s_w);
-    P.half = (uint32_t)(2147483648.0 / (double)n);
+    P.half = (uint32_t)(2147483648.0 / (double)n_total);
     // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the shift
     uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -1168,6 +1172,14 @@ extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, floa
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
     k_quiet_start<<<grid, block, smem, s>>>(P);
     return launch_status();
+}
+
+extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                     const float* prof_n, const float* prof_u, float v_th, uint64_t seed, int32_t s_w,
+                                     int64_t* rho_fx, uint32_t* status, void* stream)
+{
+    return pe_quiet_start_slice(cell, theta, v, w, 0, n, n, ncell, prof_n, prof_u, v_th, seed, s_w, rho_fx, status,
+                                stream);
 }
 
 extern "C" PE_API int pe_quiet_start_equal(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
