@@ -254,6 +254,10 @@ PE_API int pe_ls_project(const double* samples, int32_t K, int32_t ncoef, double
 PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
                      float* prof_n, float* prof_u, void* stream);
 
+/* pe_refine with FP64 profiles (the lifting of the FP64-particle path). */
+PE_API int pe_refine_f64(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
+                         double* prof_n, double* prof_u, void* stream);
+
 /* Quiet-start loading, Appendix C, on nodal profiles (linear interpolation): the
  * Hammersley point h of n = ppc*ncell: cell = h / ppc, theta = (2 (h mod ppc) + 1) / (2 ppc),
  * w = n(X) / ppc, V = u(X) + v_th Phi^-1(b_h), b_h = (B_h + 1/2) 2^-32 with
@@ -286,6 +290,34 @@ PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w,
  * of nparticles ions on ncell cells uses: s = 22 - ceil(log2 cap) with the weight cap w_cap
  * (0: 8 ncell / nparticles) and the momentum cap w_cap v_cap (v_cap 0: 32). A realisation
  * split over ranks uses the shifts of its total particle count on every rank. */
+/* FP64 particles (Section 2.2 and Appendices B and C as pe_push, pe_sample and pe_quiet_start,
+ * with theta, v and w in double precision): the small workload runs both ways, so that the
+ * error of a run against an FP64 reference separates into the FP32 particles' precision and
+ * the method itself. cell int32[n]; theta, v, w double[n] (any alignment); E and E0 the FP64
+ * nodal fields (pe_field's E); prof_n, prof_u FP64 nodal profiles. The fixed-point rule is
+ * the FP32 particles' (theta_q = rn(theta 2^24), w_q = rn(w 2^s_w), m_q = rn(w V 2^s_p)).
+ * pe_push_f64: kick by kick qm_dt E(X), drift by v dt_over_dx cells; if E0 != NULL it first
+ * writes the co-moving restriction sample of the current state to sample_fx[2][ncell]
+ * (density then momentum, nodal, fixed point): target X + tau Vbar, velocity
+ * Vbar + qm tau E0(X), Vbar = v + (kick - 1/2) qm_dt E(X), with tau_over_dx = tau / dx and
+ * qm_tau = qm tau. If rho_fx != NULL it is overwritten with the deposit of the pushed
+ * particles. pe_sample_f64 writes the sample only. pe_quiet_start_f64 loads the point set of
+ * pe_quiet_start (storage order included), with Phi^-1 in double precision, and the deposit
+ * into rho_fx if not NULL. One thread per particle, 64-bit global atomics: meant for small
+ * particle counts. Errors as pe_push (PE_FLAG_RANGE, PE_FLAG_OVERFLOW in status). */
+PE_API int pe_push_f64(int32_t* cell, double* theta, double* v, const double* w, int64_t n,
+                       const double* E, int32_t ncell, double dt_over_dx, double qm_dt, double kick,
+                       int32_t s_w, int64_t* rho_fx, const double* E0, double tau_over_dx, double qm_tau,
+                       int32_t s_p, int64_t* sample_fx, uint32_t* status, void* stream);
+PE_API int pe_sample_f64(const int32_t* cell, const double* theta, const double* v, const double* w,
+                         int64_t n, const double* E, int32_t ncell, double qm_dt, double kick, int32_t s_w,
+                         const double* E0, double tau_over_dx, double qm_tau, int32_t s_p,
+                         int64_t* sample_fx, uint32_t* status, void* stream);
+PE_API int pe_quiet_start_f64(int32_t* cell, double* theta, double* v, double* w, int64_t n,
+                              int32_t ncell, const double* prof_n, const double* prof_u, double v_th,
+                              uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
+                              void* stream);
+
 /* The initial nodal profiles of pe_load_initial, written to host arrays prof_n[ncell] and
  * prof_u[ncell] (FP32): PE_PROFILE_SINE, the ion-acoustic wave of Section 4.1,
  * n = 1 + amplitude cos(2 pi x_j / L), u = amplitude cos(2 pi x_j / L) at x_j = j L / ncell;

@@ -133,6 +133,10 @@ SIGNATURES = {
     "pe_refine": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
     "pe_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, u64, i32, P, P, P]),
     "pe_quiet_start_slice": (ctypes.c_int, [P, P, P, P, i64, i64, i64, i32, P, P, f32, u64, i32, P, P, P]),
+    "pe_refine_f64": (ctypes.c_int, [P, i32, i32, i32, P, P, P]),
+    "pe_push_f64": (ctypes.c_int, [P, P, P, P, i64, P, i32, f64, f64, f64, i32, P, P, f64, f64, i32, P, P, P]),
+    "pe_sample_f64": (ctypes.c_int, [P, P, P, P, i64, P, i32, f64, f64, i32, P, f64, f64, i32, P, P, P]),
+    "pe_quiet_start_f64": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f64, u64, i32, P, P, P]),
     "pe_fixed_point_shifts": (ctypes.c_int, [i64, i32, f64, f64, P, P]),
     "pe_initial_profile": (ctypes.c_int, [i32, i32, f64, f64, P, P]),
     "pe_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, f32, u64, i32, P, P, P, P]),

@@ -291,8 +291,9 @@ __device__ double* synthesise(const Filter& f, const double* coarse, int nc, int
     return a;
 }
 
+template <typename P>
 __global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, Filter f, int ncell, double scale,
-                                                 float* prof_n, float* prof_u)
+                                                 P* prof_n, P* prof_u)
 {
     extern __shared__ double buf[];
     __shared__ double red[32];
@@ -323,8 +324,8 @@ __global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, F
     double* mf = synthesise(f, coarse + nc, nc, ncell, o1, Z, scale);
     for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
         const double n = nf[j];
-        prof_n[j] = (float)n;
-        prof_u[j] = (n > 1e-12 * nmax) ? (float)(mf[j] / n) : 0.0f;
+        prof_n[j] = (P)n;
+        prof_u[j] = (n > 1e-12 * nmax) ? (P)(mf[j] / n) : P(0);
     }
 }
 
@@ -496,15 +497,28 @@ extern "C" PE_API int pe_ls_project(const double* samples, int32_t K, int32_t nc
     return launch_status();
 }
 
-extern "C" PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell, float* prof_n,
-                                float* prof_u, void* stream)
+template <typename P>
+static int refine_into(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell, P* prof_n, P* prof_u,
+                       void* stream)
 {
     if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || !coarse || !prof_n || !prof_u) return PE_EINVAL;
     if (!wavelet_ok(wavelet)) return PE_EINVAL;
     const size_t smem = 3 * sizeof(double) * (size_t)ncell;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
-    if (ensure_smem((const void*)k_refine, smem) != PE_OK) return PE_ECUDA;
-    k_refine<<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
-                                                      pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u);
+    if (ensure_smem((const void*)k_refine<P>, smem) != PE_OK) return PE_ECUDA;
+    k_refine<P><<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
+                                                         pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u);
     return launch_status();
+}
+
+extern "C" PE_API int pe_refine(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell, float* prof_n,
+                                float* prof_u, void* stream)
+{
+    return refine_into(coarse, n_coarse, wavelet, ncell, prof_n, prof_u, stream);
+}
+
+extern "C" PE_API int pe_refine_f64(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
+                                    double* prof_n, double* prof_u, void* stream)
+{
+    return refine_into(coarse, n_coarse, wavelet, ncell, prof_n, prof_u, stream);
 }
