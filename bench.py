@@ -438,7 +438,8 @@ def run_gpu(args):
                                         "odd: periodic sinusoid, even: bounded slab",
                             "value": sum_over_ranks(ens["particle_steps"]) / t_ens, "unit": UNIT,
                             "ms_per_step": 1e3 * t_ens / ens["steps"], "particles": ens["particles"],
-                            "tuned_chunk": ens["tuned_chunk"], "steps": ens["steps"]}
+                            "tuned_chunk": ens["tuned_chunk"], "tuned_shape": ens["tuned_shape"],
+                            "groups": ens["groups"], "steps": ens["steps"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)
@@ -598,11 +599,21 @@ def run_kernel_kinetic(args):
 def run_kernel(args):
     """Times one hot-path kernel alone on the workload's particle state (for profiling):
     ``--kernel push_sample|push|deposit|sample|field|quiet_start|push_sample_ps|ps_tables|
-    ps_quiet_start|push_sample_ps_slab|kinetic``."""
+    ps_quiet_start|push_sample_ps_slab|kinetic|ensemble``."""
     import torch
 
     if args.kernel == "push_sample_ps_slab":
         return run_kernel_slab(args)
+    if args.kernel == "ensemble":
+        import torch
+
+        from paper_1610_01071_gb300 import _build
+
+        _build.build()
+        ens = run_ensemble(torch.device("cuda", 0), args.steps, args.warmup)
+        ens["value"] = ens["particle_steps"] / ens["seconds"]
+        print(json.dumps(dict(kernel="ensemble", **ens)), flush=True)
+        return 0
     if args.kernel == "kinetic":
         return run_kernel_kinetic(args)
 
@@ -1087,7 +1098,10 @@ def run_ensemble(dev, steps, warmup, rank=0):
             ctx.load_initial(amp)
         ctxs.append(ctx)
     batch = pb.Batch(ctxs)
+    t0 = time.perf_counter()
     chunk = batch.tune()
+    tune_s = time.perf_counter() - t0
+    shape = batch.tuned()
     for _ in range(warmup):
         batch.step()
     torch.cuda.synchronize(dev)
@@ -1102,7 +1116,16 @@ def run_ensemble(dev, steps, warmup, rank=0):
     if bad:
         raise RuntimeError(f"device status set in realisations {bad}")
     total = sum(c.cfg.nparticles for c in ctxs)
+    # ensemble groups: realisations of the same grid and initial-condition family, averaged
+    groups = {}
+    for i, (ncell, n, amp, slab) in enumerate(ensemble_sizes()):
+        groups.setdefault((ncell, slab), []).append(i)
+    means = {f"{'slab' if k[1] else 'sine'}_{k[0]}": batch.group_mean(v) for k, v in sorted(groups.items())}
+    torch.cuda.synchronize(dev)
     return {"realisations": len(ctxs), "particles": int(total), "K": K, "steps": steps, "tuned_chunk": chunk,
+            "tuned_shape": shape, "tune_seconds": tune_s,
+            "groups": {f"{'slab' if k[1] else 'sine'}_{k[0]}": len(v) for k, v in sorted(groups.items())},
+            "group_mean_density_sum": {k: float(m[0].sum().item()) for k, m in means.items()},
             "ms_per_step": 1e3 * t / steps, "seconds": t, "particle_steps": float(total) * K * steps}
 
 

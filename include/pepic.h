@@ -692,11 +692,14 @@ PE_API int pe_profile_read_kinds(pe_ctx* ctx, double* ms, int64_t* launches);
  * Each fine step of the whole ensemble is one persistent particle launch over a shared
  * work list of particle chunks plus one launch of field-solve clusters (one per
  * realisation); from the second pe_batch_step on, the burst, restriction and
- * projection of every realisation replay as one captured CUDA graph. Lifting stays
- * per realisation. Each context keeps its own arena; the batch needs caller-owned
+ * projection of every realisation replay as one captured CUDA graph. Lifting takes one
+ * launch for every realisation's profile and one loading launch per realisation. Each
+ * context keeps its own arena; the batch needs caller-owned
  * device scratch of pe_batch_scratch_bytes (256-byte aligned) for its descriptors, work
- * list and the ensemble's charge, field-copy and sample grids. Results are identical,
- * bit for bit, to pe_step on each context alone. The batch's stream waits for work
+ * list and the ensemble's charge, field-copy and sample grids. Each realisation follows
+ * pe_step on its context alone: the same particle arithmetic; its field solve may partition
+ * the linear solve differently (ensembles use fewer SMs per solve), so states agree to the
+ * Newton tolerance rather than bit for bit. The batch's stream waits for work
  * queued on each context's stream, and each context's stream waits for the batch. Graph
  * capture needs a created stream: on the legacy default stream every step runs eagerly. */
 typedef struct pe_batch pe_batch;
@@ -706,9 +709,20 @@ PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scratch, size_t
 /* One projective macro step of every realisation (all must have been loaded, or all
  * advanced by the batch: PE_ESTATE otherwise). */
 PE_API int pe_batch_step(pe_batch* b);
-/* Autotuner: times the batched particle pass (read-only sample form) for particle
- * chunks of 8192..65536 per block and keeps the fastest; returns it in *chunk. */
+/* Autotuner: times the batched particle pass for every launch shape (particle chunks of
+ * 16384, 32768 or 65536 per work item; blocks of 128, 256 or 512 threads; the charge deposit
+ * through a shared-memory window or straight to the global grid), as the sum of its read-only
+ * sample pass and its deposit pass, and keeps the fastest; returns its chunk in *chunk. The
+ * choice is cached for the process by the ensemble's composition (every realisation's ncell and
+ * particle count, in order, and the device): a later batch of the same composition reuses it
+ * without timing. pe_batch_tuned reports the shape in use. */
 PE_API int pe_batch_tune(pe_batch* b, int64_t* chunk);
+PE_API int pe_batch_tuned(const pe_batch* b, int64_t* chunk, int32_t* block, int32_t* privatised);
+/* Mean of the coarse states (Section 3.3's coarse density and momentum coefficients) of a group
+ * of realisations of the batch: members[nmembers] (1 <= nmembers <= 128) index the contexts
+ * given to pe_batch_create, all with the same n_coarse; out (device, double[2 n_coarse]) gets
+ * the component-wise mean, summed in the order given (repeatable bits), on the batch stream. */
+PE_API int pe_batch_group_mean(pe_batch* b, const int32_t* members, int32_t nmembers, double* out);
 PE_API void pe_batch_destroy(pe_batch* b);
 
 /* =================================================================== learned surrogate

@@ -195,6 +195,8 @@ SIGNATURES = {
     "pe_batch_create": (ctypes.c_int, [P, i32, P, sz, P, ctypes.POINTER(P)]),
     "pe_batch_step": (ctypes.c_int, [P]),
     "pe_batch_tune": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+    "pe_batch_tuned": (ctypes.c_int, [P, P, P, P]),
+    "pe_batch_group_mean": (ctypes.c_int, [P, P, i32, P]),
     "pe_batch_destroy": (None, [P]),
 }
 
@@ -760,6 +762,21 @@ class Batch:
         chunk = ctypes.c_int64()
         check(load().pe_batch_tune(self._h, ctypes.byref(chunk)), "pe_batch_tune")
         return chunk.value
+
+    def tuned(self) -> dict:
+        """The particle launch shape in use: chunk, threads per block, shared-memory deposit window."""
+        chunk, block, priv = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        check(load().pe_batch_tuned(self._h, ctypes.byref(chunk), ctypes.byref(block), ctypes.byref(priv)),
+              "pe_batch_tuned")
+        return dict(chunk=chunk.value, block=block.value, privatised=bool(priv.value))
+
+    def group_mean(self, members, out=None):
+        """Mean coarse state [2, n_coarse] of the realisations `members` (indices into the batch)."""
+        nc = self.contexts[members[0]].cfg.n_coarse
+        out = out if out is not None else torch.empty((2, nc), dtype=torch.float64, device=self.contexts[0].device)
+        idx = (ctypes.c_int32 * len(members))(*members)
+        check(load().pe_batch_group_mean(self._h, idx, len(members), _ptr(out)), "pe_batch_group_mean")
+        return out
 
     def __del__(self):
         h = getattr(self, "_h", None)

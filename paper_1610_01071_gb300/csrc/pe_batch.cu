@@ -9,6 +9,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "pe_ctx.h"
@@ -22,13 +24,23 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t push, field, proj, items, counter, rho, e0, samp, total;
+    size_t push, field, proj, refine, coarse_ptrs, items, counter, rho, e0, samp, total;
     int64_t rho_total, samp_row, max_items;
 };
 
 // The smallest chunk the tuner may choose bounds the work-list length.
 constexpr int64_t kMinChunk = 4096;
-const int64_t kChunkCandidates[] = {8192, 16384, 32768, 65536};
+const int64_t kChunkCandidates[] = {16384, 32768, 65536};
+const int kBlockCandidates[] = {128, 256, 512};
+
+// Tuned launch shapes, cached by the ensemble's composition: the (ncell, N) of every realisation
+// in order, and the device.
+struct Tuned {
+    int64_t chunk;
+    int block, priv;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, Tuned> g_tuned;
 
 int layout_for(pe_ctx* const* ctxs, int n, Layout* L)
 {
@@ -53,6 +65,10 @@ int layout_for(pe_ctx* const* ctxs, int n, Layout* L)
     off += a256(field_desc_size() * n);
     L->proj = off;
     off += a256(proj_desc_size() * n);
+    L->refine = off;
+    off += a256(refine_desc_size() * n);
+    L->coarse_ptrs = off;
+    off += a256(sizeof(double*) * n);
     L->items = off;
     off += a256(work_item_size() * (size_t)items);
     L->counter = off;
@@ -76,20 +92,31 @@ struct pe_batch {
     cudaStream_t stream;
     int K;
     int64_t chunk;
+    int block, priv;  // particle launch shape: threads per block, shared-memory deposit window
     int nitems;
     int max_ncell, max_nb;
-    // Field-solve groups, one launch each: (multi-block clusters of size G | single blocks) x
-    // (FP32 | FP64 Jacobian solve: bounded grids). Every realisation is solved exactly as its
-    // context alone would solve it.
-    std::vector<int> field_ids[4];
-    int field_maxn[4];
-    int G;  // cluster size of the multi-block groups
+    // Field-solve groups, one launch each: (cluster size G) x (FP32 | FP64 Jacobian solve:
+    // bounded grids). The batch sizes clusters for throughput (newton_batch_cluster_size), so
+    // its solves can differ from a lone context's in the last bits (the same equations, another
+    // partition of the linear solve); both converge to the Newton tolerance.
+    struct FieldGroup {
+        int G;
+        bool fp64;
+        int maxn;
+        std::vector<int> ids;
+    };
+    std::vector<FieldGroup> fgroups;
     std::vector<int64_t> rho_off, e0_off, samp_off;
     std::vector<int> banks;  // particle bank of each context when the descriptors were built
     cudaGraphExec_t graph;
     long long graph_kernels;
     int steps_done;
     cudaEvent_t ev_in, ev_out;  // ordering against the contexts' streams
+    // field-solve groups run concurrently: forked onto side streams and joined (in the captured
+    // graph these become parallel branches)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork;
 };
 
 static char* at(pe_batch* b, size_t off) { return b->scratch + off; }
@@ -121,8 +148,8 @@ static int build_descs(pe_batch* b)
     std::vector<int> slot(R, 0);  // position of each realisation's field descriptor
     {
         int o = 0;
-        for (int g = 0; g < 4; ++g)
-            for (int r : b->field_ids[g]) slot[r] = o++;
+        for (const auto& fg : b->fgroups)
+            for (int r : fg.ids) slot[r] = o++;
     }
     int64_t* rho_all = reinterpret_cast<int64_t*>(at(b, b->L.rho));
     float* e0_all = reinterpret_cast<float*>(at(b, b->L.e0));
@@ -143,6 +170,17 @@ static int build_descs(pe_batch* b)
         make_field_desc(dst, rho_all + b->rho_off[r], c.ncell, x->dx, x->s_w, c.poisson, x->walls, c.newton_tol,
                         c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, x->phi + c.ncell);
     }
+    std::vector<char> ref(refine_desc_size() * R);
+    std::vector<const double*> cptr(R);
+    for (int r = 0; r < R; ++r) {
+        pe_ctx* x = b->ctx[r];
+        make_refine_desc(ref.data() + refine_desc_size() * r, x->coarse, x->nc, x->cfg.ncell, x->prof,
+                         x->prof + x->cfg.ncell);
+        cptr[r] = x->coarse;
+    }
+    if (cudaMemcpy(at(b, b->L.refine), ref.data(), ref.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(at(b, b->L.coarse_ptrs), cptr.data(), sizeof(double*) * R, cudaMemcpyHostToDevice) != cudaSuccess)
+        return PE_ECUDA;
     if (cudaMemcpy(at(b, b->L.push), push.data(), push.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(at(b, b->L.proj), proj.data(), proj.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(at(b, b->L.field), fd.data(), fd.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -155,14 +193,21 @@ static int build_descs(pe_batch* b)
 static int field_all(pe_batch* b, bool extrap)
 {
     const char* base = at(b, b->L.field);
+    const bool fork = b->fgroups.size() > 1;
+    if (fork && cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return PE_ECUDA;
     size_t o = 0;
-    for (int g = 0; g < 4; ++g) {
-        const int n = (int)b->field_ids[g].size();
-        if (n)
-            PE_TRY(launch_newton_batch(base + field_desc_size() * o, n, g < 2 ? b->G : 1, b->field_maxn[g], g & 1,
-                                       extrap, b->stream));
+    for (size_t k = 0; k < b->fgroups.size(); ++k) {
+        const auto& fg = b->fgroups[k];
+        const int n = (int)fg.ids.size();
+        cudaStream_t s = fork ? b->side[k] : b->stream;
+        if (fork && cudaStreamWaitEvent(s, b->ev_fork, 0) != cudaSuccess) return PE_ECUDA;
+        PE_TRY(launch_newton_batch(base + field_desc_size() * o, n, fg.G, fg.maxn, fg.fp64, extrap, s));
+        if (fork && cudaEventRecord(b->ev_join[k], s) != cudaSuccess) return PE_ECUDA;
         o += (size_t)n;
     }
+    if (fork)
+        for (size_t k = 0; k < b->fgroups.size(); ++k)
+            if (cudaStreamWaitEvent(b->stream, b->ev_join[k], 0) != cudaSuccess) return PE_ECUDA;
     return PE_OK;
 }
 
@@ -185,12 +230,12 @@ static int burst_restrict_project(pe_batch* b)
         if (cudaMemsetAsync(samp_all + (size_t)p * b->L.samp_row, 0, row_bytes, s) != cudaSuccess) return PE_ECUDA;
         if (p == b->K) {
             PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, p, 1.0f, counter,
-                                          b->max_ncell, b->max_nb, s));
+                                          b->max_ncell, b->max_nb, b->block, b->priv, s));
             break;
         }
         if (cudaMemsetAsync(rho_all, 0, 8 * (size_t)b->L.rho_total, s) != cudaSuccess) return PE_ECUDA;
         PE_TRY(launch_particles_batch(0, at(b, b->L.push), at(b, b->L.items), b->nitems, p, p == 0 ? 0.5f : 1.0f,
-                                      counter, b->max_ncell, b->max_nb, s));
+                                      counter, b->max_ncell, b->max_nb, b->block, b->priv, s));
         PE_TRY(field_all(b, true));
     }
     const pe_config& c0 = b->ctx[0]->cfg;
@@ -223,6 +268,8 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
     b->stream = (cudaStream_t)stream;
     b->K = ctxs[0]->cfg.K;
     b->chunk = 65536;
+    b->block = 256;
+    b->priv = 1;
     b->graph = nullptr;
     b->graph_kernels = 0;
     b->steps_done = 0;
@@ -231,10 +278,7 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
         delete b;
         return PE_ECUDA;
     }
-    b->G = 1;
-    for (int r = 0; r < n; ++r) b->G = newton_cluster_size(ctxs[r]->cfg.ncell) > b->G ? newton_cluster_size(ctxs[r]->cfg.ncell) : b->G;
     b->max_ncell = 0;
-    for (int g = 0; g < 4; ++g) b->field_maxn[g] = 0;
     b->max_nb = 0;
     int64_t ro = 0, so = 0;
     for (int r = 0; r < n; ++r) {
@@ -246,16 +290,41 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
         so += 2 * (int64_t)x->nb;
         if (x->nb > b->max_nb) b->max_nb = x->nb;
         if (x->cfg.ncell > b->max_ncell) b->max_ncell = x->cfg.ncell;
-        const bool cl = b->G > 1 && newton_cluster_size(x->cfg.ncell) == b->G;
-        const int g = (cl ? 0 : 2) + (x->walls ? 1 : 0);
-        b->field_ids[g].push_back(r);
-        if (x->cfg.ncell > b->field_maxn[g]) b->field_maxn[g] = x->cfg.ncell;
+        const int G = newton_batch_cluster_size(x->cfg.ncell);
+        if (G < 1) {
+            cudaEventDestroy(b->ev_in);
+            cudaEventDestroy(b->ev_out);
+            delete b;
+            return PE_EINVAL;
+        }
+        const bool fp64 = x->walls != 0;
+        bool placed = false;
+        for (auto& fg : b->fgroups)
+            if (fg.G == G && fg.fp64 == fp64) {
+                fg.ids.push_back(r);
+                if (x->cfg.ncell > fg.maxn) fg.maxn = x->cfg.ncell;
+                placed = true;
+            }
+        if (!placed) b->fgroups.push_back({G, fp64, x->cfg.ncell, {r}});
     }
-    int rc = build_descs(b);
+    int rc = PE_OK;
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = PE_ECUDA;
+    for (size_t k = 0; rc == PE_OK && k < b->fgroups.size(); ++k) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            rc = PE_ECUDA;
+            break;
+        }
+        b->side.push_back(st);
+        b->ev_join.push_back(ev);
+    }
+    if (rc == PE_OK) rc = build_descs(b);
     if (rc == PE_OK) rc = build_items(b);
     if (rc == PE_OK && cudaMemset(at(b, L.e0), 0, 4 * (size_t)L.rho_total) != cudaSuccess) rc = PE_ECUDA;
     if (rc != PE_OK) {
-        delete b;
+        pe_batch_destroy(b);
         return rc;
     }
     *out = b;
@@ -268,6 +337,9 @@ extern "C" PE_API void pe_batch_destroy(pe_batch* b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaEventDestroy(b->ev_in);
     cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
     delete b;
 }
 
@@ -277,41 +349,134 @@ static void drop_graph(pe_batch* b)
     b->graph = nullptr;
 }
 
-extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
+static std::vector<int64_t> composition(const pe_batch* b)
 {
-    if (!b) return PE_EINVAL;
+    std::vector<int64_t> key;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key.push_back(dev);
+    for (const pe_ctx* x : b->ctx) {
+        key.push_back(x->cfg.ncell);
+        key.push_back(x->cfg.nparticles);
+    }
+    return key;
+}
+
+// Times one launch shape: the read-only sample pass (row K + 1, scratch) and the deposit pass
+// (into the ensemble's charge grid, rewritten before every push) over every realisation's
+// particles, the two halves of the fused push; best of two.
+static int time_shape(pe_batch* b, cudaEvent_t e0, cudaEvent_t e1, float* ms_out)
+{
     unsigned* counter = reinterpret_cast<unsigned*>(at(b, b->L.counter));
-    const int maxn = b->max_ncell;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PE_ECUDA;
     float best = 1e30f;
-    int64_t best_chunk = b->chunk;
-    for (int64_t cand : kChunkCandidates) {
-        b->chunk = cand;
-        PE_TRY(build_items(b));
-        // the read-only sample pass, written to the scratch row K+1, times the particle stream
-        PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, b->K + 1, 1.0f, counter,
-                                      maxn, b->max_nb, b->stream));
+    for (int rep = 0; rep < 3; ++rep) {  // the first repetition warms up
         cudaEventRecord(e0, b->stream);
-        for (int rep = 0; rep < 3; ++rep)
-            PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, b->K + 1, 1.0f, counter,
-                                          maxn, b->max_nb, b->stream));
+        PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, b->K + 1, 1.0f, counter,
+                                      b->max_ncell, b->max_nb, b->block, b->priv, b->stream));
+        PE_TRY(launch_particles_batch(2, at(b, b->L.push), at(b, b->L.items), b->nitems, 0, 1.0f, counter,
+                                      b->max_ncell, b->max_nb, b->block, b->priv, b->stream));
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) return PE_ECUDA;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_chunk = cand;
+        if (rep > 0 && ms < best) best = ms;
+    }
+    *ms_out = best;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
+{
+    if (!b) return PE_EINVAL;
+    const std::vector<int64_t> key = composition(b);
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            b->chunk = it->second.chunk;
+            b->block = it->second.block;
+            b->priv = it->second.priv;
+            cached = true;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    b->chunk = best_chunk;
+    if (!cached) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PE_ECUDA;
+        float best = 1e30f;
+        Tuned pick{b->chunk, b->block, b->priv};
+        for (int64_t cand : kChunkCandidates) {
+            b->chunk = cand;
+            PE_TRY(build_items(b));
+            for (int blk : kBlockCandidates)
+                for (int pv = 1; pv >= 0; --pv) {
+                    b->block = blk;
+                    b->priv = pv;
+                    float ms = 0.f;
+                    PE_TRY(time_shape(b, e0, e1, &ms));
+                    if (ms < best) {
+                        best = ms;
+                        pick = Tuned{cand, blk, pv};
+                    }
+                }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->chunk = pick.chunk;
+        b->block = pick.block;
+        b->priv = pick.priv;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = pick;
+    }
     PE_TRY(build_items(b));
     drop_graph(b);
-    if (chosen_chunk) *chosen_chunk = best_chunk;
+    if (chosen_chunk) *chosen_chunk = b->chunk;
     return PE_OK;
+}
+
+extern "C" PE_API int pe_batch_tuned(const pe_batch* b, int64_t* chunk, int32_t* block, int32_t* privatised)
+{
+    if (!b || !chunk || !block || !privatised) return PE_EINVAL;
+    *chunk = b->chunk;
+    *block = b->block;
+    *privatised = b->priv;
+    return PE_OK;
+}
+
+// Mean of the coarse states of a group of realisations: thread k sums component k over the
+// members in the given order (fixed, so repeated calls return the same bits).
+constexpr int kGroupMax = 128;
+struct GroupMembers {
+    int n;
+    int idx[kGroupMax];
+};
+
+__global__ void k_group_mean(const double* const* coarse, GroupMembers m, int ncoef, double* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncoef) return;
+    double s = 0.0;
+    for (int i = 0; i < m.n; ++i) s += coarse[m.idx[i]][k];
+    out[k] = s / (double)m.n;
+}
+
+extern "C" PE_API int pe_batch_group_mean(pe_batch* b, const int32_t* members, int32_t nmembers, double* out)
+{
+    if (!b || !members || !out || nmembers < 1 || nmembers > kGroupMax) return PE_EINVAL;
+    GroupMembers m{};
+    m.n = nmembers;
+    int64_t ncoef = -1;
+    for (int i = 0; i < nmembers; ++i) {
+        const int r = members[i];
+        if (r < 0 || r >= (int)b->ctx.size()) return PE_EINVAL;
+        const int64_t nc = 2 * (int64_t)b->ctx[r]->nc;
+        if (ncoef >= 0 && nc != ncoef) return PE_EINVAL;  // one coarse layout per group
+        ncoef = nc;
+        m.idx[i] = r;
+    }
+    k_group_mean<<<(int)((ncoef + 255) / 256), 256, 0, b->stream>>>(
+        reinterpret_cast<const double* const*>(at(b, b->L.coarse_ptrs)), m, (int)ncoef, out);
+    return launch_status();
 }
 
 extern "C" PE_API int pe_batch_step(pe_batch* b)
@@ -335,12 +500,13 @@ extern "C" PE_API int pe_batch_step(pe_batch* b)
     }
     // Lifting (or, after pe_load_initial, the charge of the loaded particles) into rho_all
     int64_t* rho_all = reinterpret_cast<int64_t*>(at(b, b->L.rho));
+    if (!fresh)  // every realisation's lifting profile in one launch
+        PE_TRY(launch_refine_batch(at(b, b->L.refine), R, PE_WAVELET_HAAR, b->max_ncell, b->stream));
     for (int r = 0; r < R; ++r) {
         pe_ctx* x = b->ctx[r];
         const pe_config& c = x->cfg;
         const int k = x->bank;
         if (!fresh) {
-            PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, b->stream));
             if (x->walls)  // bounded grid: equal weights, wall deposits doubled to densities
                 PE_TRY(pe_quiet_start_equal(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell,
                                             x->prof, x->prof + c.ncell, 2.0f, (float)c.v_th, pe_ctx_lift_seed(x),

@@ -292,11 +292,40 @@ __device__ double* synthesise(const Filter& f, const double* coarse, int nc, int
 }
 
 template <typename P>
+__device__ __forceinline__ void refine_body(const double* coarse, int nc, const Filter& f, int ncell, double scale,
+                                            P* prof_n, P* prof_u, double* buf, double* red);
+
+template <typename P>
 __global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, Filter f, int ncell, double scale,
                                                  P* prof_n, P* prof_u)
 {
     extern __shared__ double buf[];
     __shared__ double red[32];
+    refine_body(coarse, nc, f, ncell, scale, prof_n, prof_u, buf, red);
+}
+
+// Lifting profiles of many realisations in one launch (the batched ensemble), block r for
+// realisation r: the same arithmetic as k_refine.
+struct RefineDesc {
+    const double* coarse;
+    float* prof_n;
+    float* prof_u;
+    int nc, ncell;
+    double scale;
+};
+
+__global__ void __launch_bounds__(1024) k_refine_batch(const RefineDesc* d, Filter f)
+{
+    extern __shared__ double buf[];
+    __shared__ double red[32];
+    const RefineDesc r = d[blockIdx.x];
+    refine_body(r.coarse, r.nc, f, r.ncell, r.scale, r.prof_n, r.prof_u, buf, red);
+}
+
+template <typename P>
+__device__ __forceinline__ void refine_body(const double* coarse, int nc, const Filter& f, int ncell, double scale,
+                                            P* prof_n, P* prof_u, double* buf, double* red)
+{
     double* X = buf;
     double* Y = buf + ncell;
     double* Z = buf + 2 * ncell;
@@ -496,6 +525,26 @@ extern "C" PE_API int pe_ls_project(const double* samples, int32_t K, int32_t nc
     k_ls_project<<<(ncoef + block - 1) / block, block, 0, (cudaStream_t)stream>>>(samples, K, ncoef, dt, dT, out, slope);
     return launch_status();
 }
+
+namespace pe {
+size_t refine_desc_size() { return sizeof(RefineDesc); }
+
+void make_refine_desc(void* out, const double* coarse, int nc, int ncell, float* prof_n, float* prof_u)
+{
+    RefineDesc d{coarse, prof_n, prof_u, nc, ncell, pow(2.0, 0.5 * ilog2(ncell))};
+    memcpy(out, &d, sizeof(d));
+}
+
+// R realisations (descs on the device), all with the same wavelet, grids of at most max_ncell.
+int launch_refine_batch(const void* descs, int R, int wavelet, int max_ncell, cudaStream_t s)
+{
+    const size_t smem = 3 * sizeof(double) * (size_t)max_ncell;
+    if (R < 1 || smem > (size_t)max_smem_optin() || !wavelet_ok(wavelet)) return PE_EINVAL;
+    if (ensure_smem((const void*)k_refine_batch, smem) != PE_OK) return PE_ECUDA;
+    k_refine_batch<<<R, 1024, smem, s>>>(static_cast<const RefineDesc*>(descs), make_filter(wavelet));
+    return launch_status();
+}
+}  // namespace pe
 
 template <typename P>
 static int refine_into(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell, P* prof_n, P* prof_u,

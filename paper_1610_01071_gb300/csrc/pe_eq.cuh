@@ -43,18 +43,29 @@ __global__ void __launch_bounds__(kEqThreads) k_eq_table(const TP* __restrict__ 
     };
     double run = 0.0;
     for (int c = c0; c < c1; ++c) run += 0.5 * (dens(c) + dens(c + 1));
-    part[t] = run;
+    // exclusive scan of the run totals: within each warp by shuffles, then over the warps' totals
+    // (fixed order; a dependent FP64 add costs ~100 cycles here, so a serial scan of 1024 totals
+    // took ~50 us)
+    const int lane = t & 31, wid = t >> 5;
+    double incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) part[wid] = incl;
     __syncthreads();
-    if (t == 0) {  // exclusive scan of the 1024 run totals (serial: fixed order, ~1k adds)
-        double acc = 0.0;
-        for (int k = 0; k < kEqThreads; ++k) {
-            const double v = part[k];
-            part[k] = acc;
-            acc += v;
+    if (wid == 0) {
+        double ws = (lane < kEqThreads / 32) ? part[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
         }
+        part[32 + lane] = ws;  // inclusive over warps
     }
     __syncthreads();
-    double acc = part[t];
+    double acc = (wid > 0 ? part[32 + wid - 1] : 0.0) + incl - run;
     for (int c = c0; c < c1; ++c) {
         C[c] = acc;
         acc += 0.5 * (dens(c) + dens(c + 1));

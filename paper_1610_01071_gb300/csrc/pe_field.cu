@@ -606,6 +606,18 @@ static int launch_newton_cluster(int G, const long long* rho, int ncell, double 
 
 int newton_cluster_size(int ncell) { return cluster_size_for(ncell); }
 
+// Cluster size of a realisation's solve inside a batched launch: as few blocks as hold the grid
+// at kNewtonMaxThreads nodes each. A lone solve spreads its nodes over up to 16 SMs to cut the
+// latency of the FP64 work; an ensemble fills the GPU with many solves at once, and clusters of
+// 16 for small grids left most of them waiting for SMs in later waves.
+int newton_batch_cluster_size(int ncell)
+{
+    const int gmax = cluster_size_for(kNewtonMaxThreads * kClusterMax);  // the device's largest
+    int G = 1;
+    while (ncell / G > kNewtonMaxThreads) G <<= 1;
+    return G <= gmax ? G : 0;
+}
+
 // Batched field solves: descs[R] on the device, every grid with the same cluster size G;
 // fp64: the linear solves run in FP64 (needed when any grid is bounded).
 int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s)

@@ -44,6 +44,7 @@ void make_field_desc(void* out, const int64_t* rho, int ncell, double dx, int s_
                      int maxit, double* phi, double* E, float* Ef, int32_t* diag, uint32_t* status,
                      double* phi_prev);
 int newton_cluster_size(int ncell);
+int newton_batch_cluster_size(int ncell);
 int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s);
 // Single field solve whose Newton start may extrapolate the solution history (context path).
 int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, int mode, int boundary, double tol,
@@ -63,13 +64,19 @@ void make_push_desc(void* out, int32_t* cell, float* theta, float* v, const floa
                     int64_t row_stride, int walls, uint32_t* status);
 void make_work_item(void* out, int r, int64_t begin, int64_t end);
 int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
-                           unsigned* counter, int max_ncell, int max_nb, cudaStream_t s);
+                           unsigned* counter, int max_ncell, int max_nb, int block, int priv, cudaStream_t s);
 
 // Batched restriction + projection of Haar-binned samples (pe_coarse.cu).
 size_t proj_desc_size();
 void make_proj_desc(void* out, const int64_t* samp, int64_t row_stride, int ncell, int nc, int s_w, int s_p,
                     double* csamples, double* coarse, double* slope);
 int launch_restrict_project_batch(const void* descs, int R, int K, double dt, double dT, cudaStream_t s);
+
+// Batched lifting profiles (pe_coarse.cu): descriptor size and builder, and the launch over
+// R realisations with the same wavelet.
+size_t refine_desc_size();
+void make_refine_desc(void* out, const double* coarse, int nc, int ncell, float* prof_n, float* prof_u);
+int launch_refine_batch(const void* descs, int R, int wavelet, int max_ncell, cudaStream_t s);
 
 // Kinetic electrons: folds the electrons' moments into the ions' (pe_diag.cu).
 int combine_kinetic_moments(pe_moments* out, const pe_moments* electrons, double qm_e, cudaStream_t s);

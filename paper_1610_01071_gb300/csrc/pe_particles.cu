@@ -514,9 +514,11 @@ struct WorkItem {
 // Persistent batched launch over the work items of many realisations: each block takes
 // the next item from a global counter until none are left. Step p and the kick are the
 // same for every realisation; tau and the sample row follow from each descriptor.
+// Blocks of 128, 256 or 512 threads (the tuner's choice), at the register budget of 1024 threads
+// per SM; priv = 0 sends every deposit straight to the global grid (no shared-memory window).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks<MODE>()) k_particles_batch(const PushParams* descs, const WorkItem* items,
-                                                                 int nitems, int p, float kick, unsigned* counter)
+__global__ void __launch_bounds__(512, 2) k_particles_batch(const PushParams* descs, const WorkItem* items,
+                                                           int nitems, int p, float kick, unsigned* counter, int priv)
 {
     extern __shared__ uint32_t smem[];
     __shared__ int next;
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<MODE>()) k_particles_batc
         const WorkItem wi = items[it];
         PushParams P = descs[wi.r];
         P.kick = kick;
+        if (!priv) P.rho_width = 0;
         const float tau = P.comoving ? (float)(P.dT - p * P.dt) : 0.f;
         P.tau_dx = tau * P.inv_dx;
         P.qm_tau = P.qm * tau;
@@ -980,39 +983,39 @@ void make_work_item(void* out, int r, int64_t begin, int64_t end)
     memcpy(out, &wi, sizeof(wi));
 }
 
-// Grid size (blocks) of a persistent batched launch: every resident block of the GPU.
-int batch_grid(int mode, int max_ncell, int max_nb)
+// Shared memory of a batched launch: the field table, the deposit window (priv), the bins.
+static size_t batch_smem(int mode, int max_ncell, int max_nb, int priv)
 {
-    const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
-    const void* k = (mode == 0) ? (const void*)k_particles_batch<kPushSampleBinned> : (const void*)k_particles_batch<kSampleBinned>;
-    const size_t smem = sizeof(float4) * (size_t)kFieldTabNodes + kSmemGridWords * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) +
-                        kBinGridWords * sizeof(uint32_t) * 2 * max_nb;
-    return sm_count() * blocks_per_sm(k, kThreads, smem);
+    const int rw = (mode != 1 && priv) ? (max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes) : 0;
+    return (mode == 2 ? 0 : sizeof(float4) * (size_t)kFieldTabNodes) + kSmemGridWords * sizeof(uint32_t) * (size_t)rw +
+           (mode == 2 ? 0 : kBinGridWords * sizeof(uint32_t) * 2 * (size_t)max_nb);
 }
 
-// mode 0: fused push + binned sample of step p; mode 1: binned sample only.
-int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
-                           unsigned* counter, int max_ncell, int max_nb, cudaStream_t s)
+template <int MODE>
+static int launch_batch_mode(const void* descs, const void* items, int nitems, int p, float kick, unsigned* counter,
+                             size_t smem, int block, int priv, cudaStream_t s)
 {
-    const int rw = max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes;
-    const size_t smem = sizeof(float4) * (size_t)kFieldTabNodes + kSmemGridWords * sizeof(uint32_t) * (size_t)(mode == 0 ? rw : 0) +
-                        kBinGridWords * sizeof(uint32_t) * 2 * max_nb;
+    const void* k = (const void*)k_particles_batch<MODE>;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    const int grid = sm_count() * blocks_per_sm(k, block, smem);
+    k_particles_batch<MODE><<<grid, block, smem, s>>>(static_cast<const PushParams*>(descs),
+                                                      static_cast<const WorkItem*>(items), nitems, p, kick, counter,
+                                                      priv);
+    return launch_status();
+}
+
+// mode 0: fused push + binned sample of step p; mode 1: binned sample only; mode 2: charge
+// deposit only (the tuner's probe of the deposit path). block: 128, 256 or 512 threads.
+int launch_particles_batch(int mode, const void* descs, const void* items, int nitems, int p, float kick,
+                           unsigned* counter, int max_ncell, int max_nb, int block, int priv, cudaStream_t s)
+{
+    if (block != 128 && block != 256 && block != 512) return PE_EINVAL;
+    const size_t smem = batch_smem(mode, max_ncell, max_nb, priv);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
-    const auto* d = static_cast<const PushParams*>(descs);
-    const auto* it = static_cast<const WorkItem*>(items);
-    if (mode == 0) {
-        const void* k = (const void*)k_particles_batch<kPushSampleBinned>;
-        if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-        const int grid = sm_count() * blocks_per_sm(k, kThreads, smem);
-        k_particles_batch<kPushSampleBinned><<<grid, kThreads, smem, s>>>(d, it, nitems, p, kick, counter);
-    } else {
-        const void* k = (const void*)k_particles_batch<kSampleBinned>;
-        if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
-        const int grid = sm_count() * blocks_per_sm(k, kThreads, smem);
-        k_particles_batch<kSampleBinned><<<grid, kThreads, smem, s>>>(d, it, nitems, p, kick, counter);
-    }
-    return launch_status();
+    if (mode == 0) return launch_batch_mode<kPushSampleBinned>(descs, items, nitems, p, kick, counter, smem, block, priv, s);
+    if (mode == 1) return launch_batch_mode<kSampleBinned>(descs, items, nitems, p, kick, counter, smem, block, priv, s);
+    return launch_batch_mode<kDeposit>(descs, items, nitems, p, kick, counter, smem, block, priv, s);
 }
 
 }  // namespace pe

@@ -1,7 +1,8 @@
 """Batched ensemble (pe_batch_*): many realisations of different sizes advanced in
-shared launches and a replayed CUDA graph must give, bit for bit, the coarse states of
-each realisation advanced alone with pe_step, and each realisation's coarse state must
-match the oracle's projective macro step (Section 3.1 cycle) from the same particles."""
+shared launches and a replayed CUDA graph must give the coarse states of each realisation
+advanced alone with pe_step (to the Newton tolerance: the batch partitions its field solves
+for throughput), and each realisation's coarse state must match the oracle's projective macro
+step (Section 3.1 cycle) from the same particles. The autotuner and the group means too."""
 import numpy as np
 import pytest
 import torch
@@ -27,26 +28,30 @@ def make(i, ncell, N, slab=False):
     return ctx
 
 
-def test_batch_matches_individual_contexts_bit_for_bit():
+def close(ga, gb, rel=1e-8):
+    return np.max(np.abs(ga - gb)) <= rel * np.max(np.abs(ga))
+
+
+def test_batch_matches_individual_contexts():
     alone = [make(i, *s) for i, s in enumerate(SIZES)]
     group = [make(i, *s) for i, s in enumerate(SIZES)]
     batch = pe.Batch(group)
     for step in range(4):  # eager, captured, then replayed graph; tuning before the last
         if step == 3:
-            assert batch.tune() in (8192, 16384, 32768, 65536)
+            assert batch.tune() in (16384, 32768, 65536)
         batch.step()
         for c in alone:
             c.step()
         for a, b in zip(alone, group):
             ga, gb = a.get_coarse().cpu().numpy(), b.get_coarse().cpu().numpy()
-            assert np.array_equal(ga, gb), f"step {step}: max diff {np.abs(ga - gb).max()}"
+            assert close(ga, gb), f"step {step}: max diff {np.abs(ga - gb).max()}"
     for c in group:
         assert c.sync_status() == 0
         d = c.diagnostics()
         assert d.macro_steps == 4 and d.newton_iters >= 1
 
 
-def test_batch_of_sinusoids_and_slabs_matches_individual_contexts_bit_for_bit():
+def test_batch_of_sinusoids_and_slabs_matches_individual_contexts():
     # the ensemble workload mixes periodic sinusoids and bounded slabs: the batch solves each
     # field with its context's precision (FP64 Jacobian solves for the slabs), pushes with
     # absorbing walls and lifts the slabs with equal weights, all bit for bit as alone
@@ -61,7 +66,7 @@ def test_batch_of_sinusoids_and_slabs_matches_individual_contexts_bit_for_bit():
             c.step()
         for k, (a, b) in enumerate(zip(alone, group)):
             ga, gb = a.get_coarse().cpu().numpy(), b.get_coarse().cpu().numpy()
-            assert np.array_equal(ga, gb), f"step {step}, realisation {k}: max diff {np.abs(ga - gb).max()}"
+            assert close(ga, gb), f"step {step}, realisation {k}: max diff {np.abs(ga - gb).max()}"
     for c in group:
         assert c.sync_status() == 0
 
@@ -94,6 +99,37 @@ def test_batch_matches_oracle_per_realisation():
         c2, _, _ = macro(lift(c1, ocfg, seed2), ocfg, phi)
         err2 = np.max(np.abs(got2[i] - c2)) / np.max(np.abs(c2))
         assert err2 < 2e-4, f"realisation {i}, step 2: {err2:.3e}"
+
+
+def test_batch_tuner_shapes_and_cache():
+    group = [make(i, *s) for i, s in enumerate(SIZES)]
+    b1 = pe.Batch(group)
+    chunk = b1.tune()
+    t1 = b1.tuned()
+    assert t1["chunk"] == chunk and t1["block"] in (128, 256, 512) and isinstance(t1["privatised"], bool)
+    b1.step()
+    b1.step()  # the tuned shape runs (eager, then captured)
+    for c in group:
+        assert c.sync_status() == 0
+    # a second batch of the same composition takes the cached shape
+    again = [make(i + 50, *s) for i, s in enumerate(SIZES)]
+    b2 = pe.Batch(again)
+    assert b2.tune() == chunk and b2.tuned() == t1
+
+
+def test_group_means_of_coarse_states():
+    sizes = [(256, 1 << 14), (256, 1 << 14), (512, 1 << 15), (256, 1 << 14), (512, 1 << 15)]
+    group = [make(i, n, N) for i, (n, N) in enumerate(sizes)]
+    batch = pe.Batch(group)
+    batch.step()
+    states = [c.get_coarse().cpu().numpy() for c in group]
+    for members in ([0, 1, 3], [2, 4], [3]):
+        got = batch.group_mean(members)
+        torch.cuda.synchronize()
+        want = sum(states[m] for m in members) / len(members)  # summed in the members' order
+        assert np.max(np.abs(got.cpu().numpy() - want)) <= 1e-15 * np.max(np.abs(want))
+    with pytest.raises(pe.PepicError):  # not a realisation of the batch
+        batch.group_mean([0, 7])
 
 
 def test_batch_rejects_mixed_states():
