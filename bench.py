@@ -336,7 +336,7 @@ def run_gpu(args):
         # ---------------- timed region: projective macro steps, inputs resident in HBM
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ctx.profile_read()
-        ctx.profile(True)
+        ctx.profile(True, kinds=("push_sample",))  # the roofline kernel only: events cost stream time
         launches0 = pb.launch_count()
         barrier()
         ev0.record(stream)
@@ -352,12 +352,19 @@ def run_gpu(args):
         st = ctx.sync_status()
         if st != 0:
             raise RuntimeError("device status after the timed region: " + pb.load().pe_strerror(st).decode())
+        # the other kernels of a macro step (field solve, last sample, lifting), timed on
+        # steps after the timed region
+        ctx.profile(True)
+        for _ in range(min(args.steps, 5)):
+            ctx.step()
+        ctx.profile(False)
+        prof_rest = ctx.profile_read_kinds()
         # ---------------- plain (resolved) GPU PIC on the same workload, same context
         ctx.load_initial(cfg["amplitude"])
         ctx.pic_steps(max(3, args.warmup) * K)
         n_plain = max(args.steps, 1) * K
         ctx.profile_read_kinds()
-        ctx.profile(True)
+        ctx.profile(True, kinds=("push",))
         barrier()
         ev0.record(stream)
         ctx.pic_steps(n_plain)
@@ -366,6 +373,10 @@ def run_gpu(args):
         ctx.profile(False)
         prof_plain = ctx.profile_read_kinds()
         t_plain = ev0.elapsed_time(ev1) / 1e3
+        ctx.profile(True, kinds=("field",))
+        ctx.pic_steps(K)
+        ctx.profile(False)
+        prof_plain["field"] = ctx.profile_read_kinds()["field"]
         # ---------------- the deposit alone and the phase-space pass, for their rooflines
         kern = time_kernels(ctx, cfg, pb, stream)
         # ---------------- end to end through the C ABI with host buffers
@@ -397,7 +408,10 @@ def run_gpu(args):
     sim_plain = cfg["dt"] * n_plain / t_plain_max
     peak, peak_kind = peak_hbm()
     src_hash = kernel_source_hash()
-    means = {k: (v["ms"] / v["launches"], v["launches"]) for k, v in prof.items() if v["launches"] and k != "field"}
+    means = {k: (v["ms"] / v["launches"], v["launches"]) for k, v in prof_rest.items()
+             if v["launches"] and k not in ("field", "push_sample")}
+    means["push_sample"] = (prof["push_sample"]["ms"] / max(prof["push_sample"]["launches"], 1),
+                            prof["push_sample"]["launches"])
     means["push"] = (prof_plain["push"]["ms"] / max(prof_plain["push"]["launches"], 1), prof_plain["push"]["launches"])
     means.update(kern)
     roof = {k: roofline_entry(k, ms, n, N, peak, peak_kind, src_hash) for k, (ms, n) in means.items()}
@@ -413,7 +427,7 @@ def run_gpu(args):
                                 "ratio": sim_proj / sim_plain},
         "plain_pic": {"value": ps_plain / t_plain_max, "unit": UNIT, "steps": n_plain,
                       "ms_per_step": 1e3 * t_plain_max / n_plain, "sort_every": 20},
-        "field_solve_us": 1e3 * prof["field"]["ms"] / max(prof["field"]["launches"], 1),
+        "field_solve_us": 1e3 * prof_rest["field"]["ms"] / max(prof_rest["field"]["launches"], 1),
         "field_solve_us_plain_pic": 1e3 * prof_plain["field"]["ms"] / max(prof_plain["field"]["launches"], 1),
         "newton_iters_last": newton_iters,
         # the dominant kernel: the fused pass of the bursts, from its own launches only

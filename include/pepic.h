@@ -669,7 +669,10 @@ PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out);
  * since the last read (push_* = every kind but PE_PROF_FIELD, field_* = PE_PROF_FIELD) and
  * resets them. pe_profile_read_kinds returns the same per kind (ms[PE_PROF_NKINDS],
  * launches[PE_PROF_NKINDS], host arrays) and resets them. Events are host resources created
- * on first use. */
+ * on first use. pe_profile(ctx, 1) times every kind; pe_profile_mask(ctx, kinds) only the
+ * kinds whose bit (1 << PE_PROF_*) is set (0 turns timing off; PE_EINVAL for unknown bits):
+ * each event pair costs a few microseconds of stream time, so a measurement of whole steps
+ * times only the kernels it reports. */
 enum {
     PE_PROF_PUSH_SAMPLE = 0,
     PE_PROF_PUSH = 1,
@@ -681,6 +684,7 @@ enum {
     PE_PROF_NKINDS = 7
 };
 PE_API int pe_profile(pe_ctx* ctx, int32_t enable);
+PE_API int pe_profile_mask(pe_ctx* ctx, int32_t kinds);
 PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches, double* field_ms,
                            int64_t* field_launches);
 PE_API int pe_profile_read_kinds(pe_ctx* ctx, double* ms, int64_t* launches);

@@ -158,6 +158,7 @@ SIGNATURES = {
     "pe_sync_status": (ctypes.c_int, [P]),
     "pe_diagnostics": (ctypes.c_int, [P, ctypes.POINTER(Diag)]),
     "pe_profile": (ctypes.c_int, [P, i32]),
+    "pe_profile_mask": (ctypes.c_int, [P, i32]),
     "pe_profile_read": (ctypes.c_int, [P, P, P, P, P]),
     "pe_profile_read_kinds": (ctypes.c_int, [P, P, P]),
     "pe_launch_count": (i64, []),
@@ -691,8 +692,15 @@ class Context:
         check(load().pe_diagnostics(self._h, ctypes.byref(d)), "pe_diagnostics")
         return d
 
-    def profile(self, enable=True):
-        self._call("pe_profile", int(bool(enable)))
+    def profile(self, enable=True, kinds=None):
+        """Time every launch kind (enable), or only the named kinds (PROFILE_KINDS names)."""
+        if kinds is None:
+            self._call("pe_profile", int(bool(enable)))
+        else:
+            mask = 0
+            for k in kinds:
+                mask |= 1 << PROFILE_KINDS.index(k)
+            self._call("pe_profile_mask", mask if enable else 0)
 
     def profile_read(self):
         """Summed event time (ms) and launch counts of particle kernels and field solves."""

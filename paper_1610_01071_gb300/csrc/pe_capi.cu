@@ -321,7 +321,7 @@ static int record(pe_ctx* x, std::vector<cudaEvent_t>*& pool, size_t slot, int s
 template <class F>
 static int timed(pe_ctx* x, int kind, F&& launch)
 {
-    if (!x->profiling) return launch();
+    if (!((x->profiling >> kind) & 1)) return launch();
     size_t& n = x->prof_n[kind];
     PE_TRY(record(x, x->prof_ev[kind], n, 0));
     PE_TRY(launch());
@@ -333,7 +333,14 @@ static int timed(pe_ctx* x, int kind, F&& launch)
 extern "C" PE_API int pe_profile(pe_ctx* ctx, int32_t enable)
 {
     if (!ctx) return PE_EINVAL;
-    ctx->profiling = enable ? 1 : 0;
+    ctx->profiling = enable ? (1 << PE_PROF_NKINDS) - 1 : 0;
+    return PE_OK;
+}
+
+extern "C" PE_API int pe_profile_mask(pe_ctx* ctx, int32_t kinds)
+{
+    if (!ctx || kinds < 0 || kinds >= (1 << PE_PROF_NKINDS)) return PE_EINVAL;
+    ctx->profiling = kinds;
     return PE_OK;
 }
 
