@@ -99,6 +99,10 @@ def _load():
                 "orc_ps_quiet_start_equal": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
                 "orc_ps_burst_walls": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl,
                                                       i32, i32, i32, dbl, dbl, i32, P, P]),
+                "orc_ps_hist_fine": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, dbl, dbl, i32, P]),
+                "orc_ps_burst_fine": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl, i32, i32, dbl,
+                                                     i32, i32, dbl, dbl, i32, P, P]),
+                "orc_ps_quiet_start_nodes": (None, [i64, i32, i32, P, P, i32, dbl, dbl, u64, P, P, P, P]),
                 "orc_poisson_periodic": (None, [i32, dbl, P, P, P]),
                 "orc_field_kinetic": (None, [i64, P, P, P, i64, P, P, P, i32, dbl, i32, P, P]),
                 "orc_pic_steps_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32,
@@ -505,6 +509,141 @@ def ps_burst(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, bin_shift, vmin, dv,
                                  int(vel_at_integer), int(bin_shift), float(vmin), float(dv), int(nv), _p(phi),
                                  _p(samples))
     return samples, phi, int(fails)
+
+
+# ------------------------------------------------------------------ phase space, wavelet form
+# Section 3.3 as the paper states it (Eqs. waveletapproximation, restriction, interpolation;
+# Appendices A-C): the coarse variable is the array of coarse scaling coefficients
+# C[i, m] (coarse x node i, velocity coefficient m) of the phase-space histogram.
+
+
+def ps_hist_fine(st: State, vbar, E0, ncell, dx, tau, qm, vmin, dv, nvf):
+    """Fine co-moving histogram [ncell, nvf] (FP64): hat weights on the fine nodes in x,
+    nearest cell in v (Appendix B)."""
+    vbar, E0 = _f64(vbar), _f64(E0)
+    H = np.zeros((ncell, nvf))
+    _load().orc_ps_hist_fine(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell, float(dx),
+                             float(tau), float(qm), float(vmin), float(dv), int(nvf), _p(H))
+    return H
+
+
+def ps_burst_fine(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, vmin, dv, nvf, mode=0, tol=1e-11, maxit=50,
+                  vel_at_integer=True):
+    """K fine steps in place with the fine co-moving histograms; returns (samples
+    [(K+1), ncell, nvf], phi, fails)."""
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, ncell, nvf))
+    fails = _load().orc_ps_burst_fine(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                      float(dt), float(qm), int(K), float(dT), int(mode), int(s_w), float(tol),
+                                      int(maxit), int(vel_at_integer), float(vmin), float(dv), int(nvf), _p(phi),
+                                      _p(samples))
+    return samples, phi, int(fails)
+
+
+def restrict_121(f, levels):
+    """Eq. (restriction) along axis 0, `levels` times: coarse node k (fine node 2k) takes
+    (f[2k-1] + 2 f[2k] + f[2k+1]) / 4, periodic."""
+    f = np.asarray(f, dtype=np.float64)
+    for _ in range(levels):
+        left = np.roll(f, 1, axis=0)[0::2]   # f[2k - 1]
+        mid = f[0::2]                         # f[2k]
+        right = np.roll(f, -1, axis=0)[0::2]  # f[2k + 1]
+        f = 0.25 * (left + 2.0 * mid + right)
+    return f
+
+
+def interpolate_x(f, levels):
+    """Eq. (interpolation) along axis 0, `levels` times: fine node 2k takes f[k], fine node
+    2k+1 the mean of f[k] and f[k+1], periodic."""
+    f = np.asarray(f, dtype=np.float64)
+    for _ in range(levels):
+        out = np.empty((2 * f.shape[0],) + f.shape[1:])
+        out[0::2] = f
+        out[1::2] = 0.5 * (f + np.roll(f, -1, axis=0))
+        f = out
+    return f
+
+
+def ps_coarsen_v(H, nvc, wavelet="coif4"):
+    """Periodized DWT along the last axis from nvf cells to nvc scaling coefficients
+    (Section 3.3; Appendix A), details discarded, scaled by 2^(L/2) for L levels so that
+    the coefficients of a row sum to its mass (each analysis level multiplies a row's sum
+    by 1/sqrt 2)."""
+    H = np.asarray(H, dtype=np.float64)
+    nvf = H.shape[-1]
+    L = int(np.log2(nvf // nvc))
+    rows = H.reshape(-1, nvf)
+    out = np.zeros((rows.shape[0], nvc))
+    for r in range(rows.shape[0]):
+        a = rows[r]
+        for _ in range(L):
+            a, _d = dwt_level(a, wavelet)
+        out[r] = a * 2.0 ** (L / 2)
+    return out.reshape(H.shape[:-1] + (nvc,))
+
+
+def ps_refine_v(C, nvf, wavelet="coif4"):
+    """Synthesis along the last axis with zero details from nvc coefficients to nvf cells,
+    scaled by 2^(-L/2): the inverse of ps_coarsen_v on its range."""
+    C = np.asarray(C, dtype=np.float64)
+    nvc = C.shape[-1]
+    L = int(np.log2(nvf // nvc))
+    rows = C.reshape(-1, nvc)
+    out = np.zeros((rows.shape[0], nvf))
+    for r in range(rows.shape[0]):
+        a = rows[r]
+        for _ in range(L):
+            a = idwt_level(a, None, wavelet)
+        out[r] = a * 2.0 ** (-L / 2)
+    return out.reshape(C.shape[:-1] + (nvf,))
+
+
+def ps_wavelet_restrict(hist, bin_shift, nvc, wavelet="coif4"):
+    """Coarse coefficients [.., nxc, nvc] of fine histograms [.., ncell, nvf]: Eq.
+    (restriction) in x (bin_shift levels), then ps_coarsen_v."""
+    hist = np.asarray(hist, dtype=np.float64)
+    if hist.ndim == 2:
+        return ps_coarsen_v(restrict_121(hist, bin_shift), nvc, wavelet)
+    return np.stack([ps_coarsen_v(restrict_121(h, bin_shift), nvc, wavelet) for h in hist])
+
+
+def ps_quiet_start_nodes(N, ncell, bin_shift, mass, cdf, vmin, dv, seed):
+    """Appendix C loading of the wavelet form on coarse-node tables (mass [nxc], cdf
+    [nxc, nvf+1])."""
+    mass, cdf = _f64(mass), _f64(cdf)
+    nvf = cdf.shape[1] - 1
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_ps_quiet_start_nodes(N, ncell, int(bin_shift), _p(mass), _p(cdf), nvf, float(vmin), float(dv),
+                                     seed & 0xFFFFFFFFFFFFFFFF, _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def ps_wavelet_lift(coarse, cfg: dict, seed):
+    """Lifting of the wavelet form (Section 3.3): synthesis in v to the fine velocity cells,
+    the Appendix C reconstruction per coarse node (negative node masses clamped, total kept),
+    then the loading with the linear interpolation in x. Returns (state, pathological flag)."""
+    nvf, wav = cfg["n_v"], cfg.get("wavelet", "coif4")
+    H = ps_refine_v(coarse, nvf, wav)
+    mass, cdf, bad = ps_lift_tables(H)
+    b = int(np.log2(cfg["ncell"] // cfg["n_coarse"]))
+    vmin, dv = -cfg["v_max"], 2.0 * cfg["v_max"] / nvf
+    return ps_quiet_start_nodes(cfg["N"], cfg["ncell"], b, mass, cdf, vmin, dv, seed), bad
+
+
+def efpi_ps_wavelet_macro_step(st: State, cfg: dict, phi, vel_at_integer=True):
+    """One projective step of the wavelet form: burst with fine co-moving histograms, Eq.
+    (restriction) and the DWT in v, least-squares slope, leap (Eqs. extrapolation2 and
+    leastsquares). Returns (coarse [nxc, nvc], coarse samples [(K+1), nxc, nvc], phi)."""
+    ncell, nc, K, nvf, nvc = cfg["ncell"], cfg["n_coarse"], cfg["K"], cfg["n_v"], cfg["n_v_coarse"]
+    dx = cfg["L"] / ncell
+    vmin, dv = -cfg["v_max"], 2.0 * cfg["v_max"] / nvf
+    samples, phi, fails = ps_burst_fine(st, ncell, dx, cfg["dt"], cfg["qm"], K, cfg["dT"], cfg["s_w"], phi, vmin, dv,
+                                        nvf, mode=cfg.get("mode", 0), vel_at_integer=vel_at_integer)
+    b = int(np.log2(ncell // nc))
+    cs = ps_wavelet_restrict(samples, b, nvc, cfg.get("wavelet", "coif4"))
+    coarse, _ = ls_project(cs.reshape(K + 1, nc * nvc), cfg["dt"], cfg["dT"])
+    return coarse.reshape(nc, nvc), cs, phi
 
 
 # ------------------------------------------------------------------ bounded domain (Section 4.2)

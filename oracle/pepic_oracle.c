@@ -1321,3 +1321,134 @@ int orc_ps_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, doubl
     free(vbar);
     return fails;
 }
+
+/* ---------------------------------------------------------------- phase space, wavelet form
+ * Section 3.3 ("A wavelet-based equation-free scheme") as the paper states it: the active
+ * variables are the coarse scaling coefficients of the phase-space histogram of Eq.
+ * (waveletapproximation). Restriction: the fine histogram, hat (CIC) weights on the n_xf fine
+ * nodes in x and nearest grid point on n_vf velocity cells, sampled at the co-moving targets
+ * of Appendix B (Eq. explicitflow and the deposit that follows it); then the 1-2-1 rule of
+ * Eq. (restriction) in x down to the coarse nodes and the periodized DWT in v down to n_vc
+ * coefficients (both in the Python layer). Lifting: synthesis in v, linear interpolation in x
+ * (Eq. interpolation), the CDF reconstruction of Appendix C per coarse node (the Remark there
+ * allows it before the lift in space), and the loading below. FP64 throughout; velocities
+ * outside [vmin, vmin + n_vf dv) are counted in the first or last cell. */
+void orc_ps_hist_fine(int64_t n, const int32_t* cell, const double* theta, const double* vbar, const double* w,
+                      const double* E0, int32_t ncell, double dx, double tau, double qm, double vmin, double dv,
+                      int32_t nvf, double* H)
+{
+    memset(H, 0, sizeof(double) * (size_t)ncell * (size_t)nvf);
+    for (int64_t p = 0; p < n; ++p) {
+        double E0p = orc_gather(E0, ncell, cell[p], theta[p]);
+        int32_t kx = cell[p];
+        double th = theta[p];
+        drift(&kx, &th, tau * vbar[p] / dx, ncell);   /* X~ = X + tau V   (Eq. explicitflow) */
+        double vt = vbar[p] + qm * tau * E0p;         /* V~ = V + qm tau E_n(X)          */
+        double kf = floor((vt - vmin) / dv);          /* k_v = floor((V~ - V_min) / dv)   */
+        int32_t kv = kf < 0.0 ? 0 : (kf >= (double)nvf ? nvf - 1 : (int32_t)kf);
+        H[(size_t)kx * nvf + kv] += (1.0 - th) * w[p];
+        H[(size_t)wrap((int64_t)kx + 1, ncell) * nvf + kv] += th * w[p];
+    }
+}
+
+/* K fine steps in place with the fine co-moving histogram of each of the K + 1 states
+ * (samples: [K+1][ncell][nvf]); the fine steps are orc_ps_burst's. */
+int orc_ps_burst_fine(int64_t n, int32_t* cell, double* theta, double* v, const double* w, int32_t ncell, double dx,
+                      double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                      int32_t vel_at_integer, double vmin, double dv, int32_t nvf, double* phi, double* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)n);
+    size_t row = (size_t)ncell * (size_t)nvf;
+    int fails = field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell);
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = v[i] + (kick - 0.5) * qm * dt * orc_gather(E, ncell, cell[i], theta[i]);
+        orc_ps_hist_fine(n, cell, theta, vbar, w, E0, ncell, dx, dT - p * dt, qm, vmin, dv, nvf,
+                         samples + (size_t)p * row);
+        if (p == K) break;
+        orc_push(n, cell, theta, v, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}
+
+/* Inverse of the CDF G[0..nv] of fine node j at b (Appendix C: lookup, then linear
+ * interpolation inside the cell, i.e. a uniform density there). G is the CDF of the fine
+ * node's histogram: the linear interpolation in x (Eq. interpolation) of the reconstructed
+ * histograms of its two coarse nodes i0, i1 with weights (1 - phi) and phi, i.e. the mixture
+ * of their CDFs weighted by (1 - phi) mass[i0] and phi mass[i1]. */
+static double ps_node_inverse(int32_t nv, const double* F0, const double* F1, double a0, double a1, double b,
+                              double vmin, double dv)
+{
+    double tot = a0 + a1;
+    int32_t k = 0;
+    for (; k < nv - 1; ++k) {
+        double g = (a0 * F0[k + 1] + a1 * F1[k + 1]) / tot;
+        if (g > b) break;
+    }
+    double g0 = (a0 * F0[k] + a1 * F1[k]) / tot;
+    double g1 = (a0 * F0[k + 1] + a1 * F1[k + 1]) / tot;
+    double r = g1 > g0 ? (b - g0) / (g1 - g0) : 0.5;
+    if (r < 0.0) r = 0.0;
+    if (r > 1.0) r = 1.0;
+    return vmin + dv * ((double)k + r);
+}
+
+/* Appendix C loading on the coarse-node tables of the wavelet form: mass[nxc] (the node
+ * values after the clamp of negative ones, orc_ps_lift_tables: Eq. (restriction) averages, so
+ * a coarse node holds mass per fine node) and the reconstructed CDFs cdf[nxc][nvf + 1].
+ * Coarse node i sits at fine node i 2^b. Fine node j has phi_j = (j mod 2^b) / 2^b of the way
+ * from coarse node i0 = j >> b to i1 = i0 + 1 (periodic), density n_j = (1 - phi_j) mass[i0]
+ * + phi_j mass[i1] (the repeated Eq. (interpolation) of the coarse values) and the mixture CDF
+ * of ps_node_inverse. Slot s takes
+ * the Hammersley point, cell and offset of orc_quiet_start; its weight is n(X) / ppc and its
+ * velocity the inverse CDF at b_s, both linear in x between the fine nodes c and c + 1. */
+void orc_ps_quiet_start_nodes(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                              int32_t nvf, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                              double* v, double* w)
+{
+    int64_t ppc = N / ncell;
+    uint32_t half = (uint32_t)(2147483648.0 / (double)N);
+    uint32_t shift = (uint32_t)(orc_splitmix64(seed) >> 32);
+    int m = 0;
+    while (((int64_t)1 << m) < ppc) ++m;
+    int pow2 = ((int64_t)1 << m) == ppc;
+    int32_t nxc = ncell >> bin_shift;
+    double per_node = ldexp(1.0, -bin_shift);
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t i = s;
+        if (pow2 && m > 0) {
+            uint32_t k = (uint32_t)(s & (ppc - 1));
+            uint32_t r = brev32(k) >> (32 - m);
+            i = (s & ~(ppc - 1)) | (int64_t)r;
+        }
+        int32_t c = (int32_t)(i / ppc);
+        double th = (2.0 * (double)(i % ppc) + 1.0) / (2.0 * (double)ppc);
+        uint32_t B = brev32((uint32_t)i) + half + shift;
+        double b = ((double)B + 0.5) * 2.3283064365386963e-10;
+        double vn[2], nn[2];
+        for (int e = 0; e < 2; ++e) {
+            int32_t j = wrap((int64_t)c + e, ncell);
+            int32_t i0 = j >> bin_shift, i1 = (i0 + 1) % nxc;
+            double phi = (double)(j & ((1 << bin_shift) - 1)) * per_node;
+            double a0 = (1.0 - phi) * mass[i0], a1 = phi * mass[i1];
+            nn[e] = a0 + a1;
+            vn[e] = (a0 + a1 > 0.0)
+                        ? ps_node_inverse(nvf, cdf + (size_t)i0 * (nvf + 1), cdf + (size_t)i1 * (nvf + 1), a0, a1, b,
+                                          vmin, dv)
+                        : vmin + dv * (double)nvf * b;
+        }
+        cell[s] = c;
+        theta[s] = th;
+        w[s] = ((1.0 - th) * nn[0] + th * nn[1]) / (double)ppc;
+        v[s] = (1.0 - th) * vn[0] + th * vn[1];
+    }
+}

@@ -230,6 +230,17 @@ int orc_ps_burst_walls(int64_t n, int32_t* cell, double* theta, double* v, doubl
                        int32_t maxit, int32_t vel_at_integer, int32_t bin_shift, double vmin, double dv, int32_t nv,
                        double* phi, int64_t* samples);
 
+/* Phase space, wavelet form (Section 3.3 as stated: fine histogram, 1-2-1 in x, DWT in v). */
+void orc_ps_hist_fine(int64_t n, const int32_t* cell, const double* theta, const double* vbar, const double* w,
+                      const double* E0, int32_t ncell, double dx, double tau, double qm, double vmin, double dv,
+                      int32_t nvf, double* H);
+int orc_ps_burst_fine(int64_t n, int32_t* cell, double* theta, double* v, const double* w, int32_t ncell, double dx,
+                      double dt, double qm, int32_t K, double dT, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                      int32_t vel_at_integer, double vmin, double dv, int32_t nvf, double* phi, double* samples);
+void orc_ps_quiet_start_nodes(int64_t N, int32_t ncell, int32_t bin_shift, const double* mass, const double* cdf,
+                              int32_t nvf, double vmin, double dv, uint64_t seed, int32_t* cell, double* theta,
+                              double* v, double* w);
+
 /* Kinetic electrons (Section 4.1's two-species bursts). */
 void orc_poisson_periodic(int32_t ncell, double dx, const double* r, double* phi, double* E);
 void orc_field_kinetic(int64_t ni, const int32_t* ci, const double* ti, const double* wi, int64_t ne,
