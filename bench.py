@@ -382,7 +382,9 @@ def run_gpu(args):
         # ---------------- end to end through the C ABI with host buffers
         host = torch.empty((2, cfg["n_coarse"]), dtype=torch.float64).pin_memory()
         ctx.load_initial(cfg["amplitude"])
+        ctx.step()  # every timed step then lifts, as in the timed region
         ctx.get_coarse_host(host)
+        ctx.profile(True, kinds=("push_sample",))  # the timed region's event pairs too
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -391,6 +393,8 @@ def run_gpu(args):
             ctx.get_coarse_host(host)
         t_e2e = time.perf_counter() - t0
         barrier()
+        ctx.profile(False)
+        ctx.profile_read_kinds()
         # ---------------- time to solution and accuracy against a resolved plain-PIC run
         acc, want, checks = run_accuracy(dev, cfg, pb) if not args.no_accuracy else (None, None, None)
         sur = run_surrogate(dev, cfg, pb, want, checks) if (acc is not None and not args.no_surrogate) else None
@@ -769,8 +773,14 @@ def run_accuracy(dev, cfg, pb):
            "speedup": t_plain / t_proj, "eps_coarse_density_at_T": eps,
            "status": [ef.sync_status(), ref.sync_status()]}
     runs = []
-    for K in (cfg["K"], cfg["K"] // 2):  # bursts of 20 and of 10 fine steps
-        ps = run_phase_space(dev, cfg, pb, want, checks, K=K)
+    # Haar-bin form with the slope filter: bursts of 20 and 10 at Delta t = 8, bursts of 20 at
+    # Delta t = 10 and 20; the wavelet form of Section 3.3 (1-2-1 rule in x, 256 velocity cells
+    # reduced by Coif4 to 64 coefficients, no filter) at Delta t = 8, 10 and 20
+    wav = dict(n_v=256, n_v_coarse=64, ps_filter=0, wavelet="coif4")
+    variants = [(cfg["K"], 8.0, {}), (cfg["K"] // 2, 8.0, {}), (cfg["K"], 10.0, {}), (cfg["K"], 20.0, {}),
+                (cfg["K"], 8.0, wav), (cfg["K"], 10.0, wav), (cfg["K"] // 2, 10.0, wav), (cfg["K"], 20.0, wav)]
+    for K, dT, kw in variants:
+        ps = run_phase_space(dev, cfg, pb, want, checks, K=K, dT=dT, **kw)
         ps["speedup_vs_plain_pic"] = t_plain / ps["seconds"]
         ps["eps_at_T_end_below_2pct"] = ps["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
         runs.append(ps)
@@ -782,21 +792,35 @@ def run_accuracy(dev, cfg, pb):
     return out, want, checks
 
 
-def run_phase_space(dev, cfg, pb, want, checks, dT=8.0, n_v=64, v_max=8.0, ps_filter=3, K=None):
+def run_phase_space(dev, cfg, pb, want, checks, dT=8.0, n_v=64, v_max=8.0, ps_filter=3, K=None, n_v_coarse=0,
+                    wavelet="haar"):
     """The paper's own coarse variable (Section 3.3): masses of n_coarse x n_v phase-space
-    cells, co-moving restriction, filtered projective step, Appendix C lifting; timed to the
-    end time and compared with the resolved states `want` (coarse density, Section 4.1.1)."""
+    cells (n_v_coarse = 0), or the wavelet form (n_v fine velocity cells reduced to n_v_coarse
+    coefficients, coarse nodes in x), co-moving restriction, projective step (slope filter
+    ps_filter), Appendix C lifting; timed to the end time and compared with the resolved
+    states `want` (coarse density, Section 4.1.1)."""
     import numpy as np
     import torch
 
     nc, ncell = cfg["n_coarse"], cfg["ncell"]
     K = K or cfg["K"]
     c = pb.make_config(ncell, nc, K, cfg["N"], cfg["L"], cfg["dt"], dT, qm=cfg["qm"], v_th=cfg["v_th"],
-                       seed=11, newton_tol=1e-10, coarse="phase_space", n_v=n_v, v_max=v_max, ps_filter=ps_filter)
+                       seed=11, newton_tol=1e-10, coarse="phase_space", n_v=n_v, v_max=v_max, ps_filter=ps_filter,
+                       n_v_coarse=n_v_coarse, wavelet=wavelet)
     ctx = pb.Context(c, device=dev)
     ctx.load_initial(cfg["amplitude"])
     b = int(np.log2(ncell // nc))
     scale = 2.0 ** (-(np.log2(ncell) + b) / 2)  # bin mass -> Haar density coefficient
+
+    def density(coarse):
+        d = coarse.sum(1).cpu().numpy()
+        if n_v_coarse == 0:
+            return d * scale
+        # wavelet form: node values (mass per fine node) -> the lifted profile, linear between
+        # coarse nodes (Eq. interpolation) -> sums over the resolved run's bins of 2^b nodes
+        phi = np.arange(1 << b) / float(1 << b)
+        fine = (1 - phi)[None, :] * d[:, None] + phi[None, :] * np.roll(d, -1)[:, None]
+        return fine.sum(1) * scale
     T_end = cfg["macro_steps"] * cfg["dT"]
     # compare at the resolved-run check times that this macro step lands on exactly
     checks = [m for m in checks if abs((m * cfg["dT"] / dT) - round(m * cfg["dT"] / dT)) < 1e-9]
@@ -812,9 +836,12 @@ def run_phase_space(dev, cfg, pb, want, checks, dT=8.0, n_v=64, v_max=8.0, ps_fi
             t += dT
         torch.cuda.synchronize(dev)
         wall += time.perf_counter() - t0
-        got[m] = (ctx.get_coarse().sum(1) * scale).cpu().numpy()
+        got[m] = density(ctx.get_coarse())
     eps = {str(round(targets[m])): _eps(got[m], want[m].cpu().numpy()) for m in checks}
-    return {"dT": dT, "K": K, "M": dT / (K * cfg["dt"]), "n_v": n_v, "v_max": v_max, "slope_filter": ps_filter,
+    form = ("wavelet form, %s in v: %d cells -> %d coefficients, 1-2-1 rule in x" % (wavelet, n_v, n_v_coarse)
+            if n_v_coarse else "Haar bins x %d velocity cells" % n_v)
+    return {"form": form, "dT": dT, "K": K, "M": dT / (K * cfg["dt"]), "n_v": n_v, "v_max": v_max,
+            "slope_filter": ps_filter,
             "T_end": T_end, "seconds": wall, "sim_time_per_wall_s": T_end / wall, "eps_coarse_density_at_T": eps,
             "status": ctx.sync_status()}
 

@@ -196,6 +196,13 @@ typedef struct pe_sample_args {
     float inv_dv;       /* phase space: 1 / dv, dv = (V_max - V_min) / n_v */
     int32_t boundary;   /* PE_BOUNDARY_*: with walls, a particle whose target X~ lies outside
                            [0, (ncell-1) dx) is not counted (it has left the domain by t_{n+1}) */
+    int32_t x_tent;     /* phase space, periodic: 0 sums the CIC weights over bins of 2^b nodes;
+                           1 samples row i = coarse node i (fine node i 2^b) with the hat of
+                           half-width 2^b, i.e. Eq. (restriction) applied b times to the CIC
+                           histogram: a target at fine position y adds w (1 - f) to node
+                           i = floor(y / 2^b) and w f to node i + 1, f = y / 2^b - i, in fixed
+                           point f_q = rn(fl32((y mod 2^b)) 2^(24-b)); the rows hold 2^b times
+                           the averaged values of that rule */
 } pe_sample_args;
 
 /* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
@@ -495,6 +502,53 @@ PE_API int pe_ps_quiet_start_equal(int32_t* cell, float* theta, float* v, float*
                                    double v_min, double dv, uint64_t seed, int32_t s_w, void* scratch,
                                    int64_t* rho_fx, uint32_t* status, void* stream);
 
+/* ---- Phase-space coarse variable, wavelet form: Section 3.3 as the paper states it. The
+ * active variables are the coarse scaling coefficients C[i][m] of the phase-space histogram:
+ * coarse node i (fine node i 2^b) of Eq. (restriction) applied b times in x, scaling
+ * coefficient m of the periodized DWT in v (Appendix A) at n_vc of the n_vf fine velocity cells.
+ * Restriction: pe_push / pe_sample with n_v = n_vf and x_tent = 1 (the hat rows), then
+ * pe_ps_coarsen_v. Lifting: pe_ps_refine_v, pe_ps_lift_tables on the n_vf-cell rows (Appendix
+ * C's reconstruction per coarse node, which the Appendix's Remark allows before the lift in
+ * space), pe_ps_node_tables (Eq. interpolation to the fine nodes) and
+ * pe_ps_quiet_start_nodes. */
+
+/* Rows sample_fx[nrows][n_vf] (int64, fixed point with shift s_w, hat rows of pe_sample's
+ * x_tent = 1 with bin_shift b) -> coarse[nrows][n_vc] (FP64): row values x 2^-(s_w + 24 + b)
+ * (the averaged values of Eq. restriction), then L = log2(n_vf / n_vc) levels of the
+ * periodized analysis filter of `wavelet` (PE_WAVELET_*) along v with the details discarded,
+ * times 2^(L/2), so that a row's coefficients sum to its mass (Haar: sums of 2^L cells).
+ * n_vf and n_vc powers of two, n_vc <= n_vf <= 4096. One block per row. */
+PE_API int pe_ps_coarsen_v(const int64_t* sample_fx, int64_t nrows, int32_t n_vf, int32_t s_w, int32_t bin_shift,
+                           int32_t wavelet, int32_t n_vc, double* coarse, void* stream);
+
+/* The inverse of pe_ps_coarsen_v on its range: coarse[nrows][n_vc] -> hist[nrows][n_vf] by
+ * L levels of periodized synthesis with zero details, times 2^(-L/2) (FP64, device). */
+PE_API int pe_ps_refine_v(const double* coarse, int64_t nrows, int32_t n_vc, int32_t wavelet, int32_t n_vf,
+                          double* hist, void* stream);
+
+/* Eq. (interpolation) of the coarse-node tables of pe_ps_lift_tables (mass[nxc], cdf[nxc][n_v + 1],
+ * FP64, device) to the ncell fine nodes: fine node j is phi = (j mod 2^b) / 2^b of the way from
+ * coarse node i0 = j >> b to i1 = i0 + 1 (periodic, 2^b = ncell / nxc); its histogram is the
+ * linear interpolation of the two coarse nodes' reconstructed histograms, so
+ * node_dens[j] = (1 - phi) mass[i0] + phi mass[i1] and its CDF is the mixture
+ * ((1 - phi) mass[i0] F_i0 + phi mass[i1] F_i1) / node_dens[j] (uniform if node_dens[j] <= 0).
+ * node_table[ncell][3 n_v + 1] (FP32, evaluated in FP64) is the sampling row of
+ * pe_ps_quiet_start with zero density slopes: the density is uniform inside a velocity cell
+ * (Appendix C: the inverse by lookup and linear interpolation). */
+PE_API int pe_ps_node_tables(const double* mass, const double* cdf, int32_t nxc, int32_t ncell, int32_t n_v,
+                             float* node_table, float* node_dens, void* stream);
+
+/* Appendix C loading of the wavelet form on the fine-node tables of pe_ps_node_tables: the
+ * Hammersley points, quantiles b and storage order of pe_quiet_start; a particle in cell c at
+ * offset theta gets w = ((1 - theta) node_dens[c] + theta node_dens[c+1]) / ppc and
+ * V = (1 - theta) G_c(b) + theta G_{c+1}(b), G_j the inverse of node j's CDF (values linearly
+ * interpolated between the two closest fine nodes). FP32. rho_fx (may be NULL) gets the charge
+ * deposit. */
+PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,
+                                   const float* node_table, const float* node_dens, int32_t n_v, double v_min,
+                                   double dv, uint64_t seed, int32_t s_w, int64_t* rho_fx, uint32_t* status,
+                                   void* stream);
+
 /* =================================================================== context
  * One realisation of the projective-integration cycle (Section 3.1, Figure
  * efpicycle): lift -> N_e fine steps with restriction after each -> least-squares
@@ -530,6 +584,12 @@ typedef struct pe_config {
                              equilibrium with the ions every this many steps (0 = never) */
     double qm_e;          /* kinetic electrons: charge-to-mass ratio (0 = -1800, the paper's value) */
     double v_th_e;        /* kinetic electrons: thermal speed (0 = sqrt(-qm_e), i.e. T_e = 1) */
+    int32_t n_v_coarse;   /* phase space: 0 = the Haar-bin form (n_coarse bins x n_v cells);
+                             > 0 = the wavelet form of Section 3.3 (periodic, Boltzmann electrons,
+                             ps_filter 0): hat rows at n_coarse nodes (Eq. restriction), n_v fine
+                             velocity cells (power of two, <= 1024) reduced by the DWT of
+                             `wavelet` to n_v_coarse coefficients (power of two, 2..n_v); the
+                             coarse state is [n_coarse][n_v_coarse] */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;

@@ -45,7 +45,8 @@ class SampleArgs(ctypes.Structure):
     _fields_ = [("E0f", ctypes.c_void_p), ("tau", ctypes.c_float), ("qm", ctypes.c_float),
                 ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
                 ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p), ("n_v", ctypes.c_int32),
-                ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float), ("boundary", ctypes.c_int32)]
+                ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float), ("boundary", ctypes.c_int32),
+                ("x_tent", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):
@@ -57,7 +58,8 @@ class Config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("w_cap", ctypes.c_double), ("v_cap", ctypes.c_double),
                 ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double),
                 ("ps_filter", ctypes.c_int32), ("boundary", ctypes.c_int32), ("electrons", ctypes.c_int32),
-                ("reset_every", ctypes.c_int32), ("qm_e", ctypes.c_double), ("v_th_e", ctypes.c_double)]
+                ("reset_every", ctypes.c_int32), ("qm_e", ctypes.c_double), ("v_th_e", ctypes.c_double),
+                ("n_v_coarse", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -178,6 +180,10 @@ SIGNATURES = {
     "pe_ps_coarsen": (ctypes.c_int, [P, i32, i64, i32, P, P]),
     "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
     "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
+    "pe_ps_coarsen_v": (ctypes.c_int, [P, i64, i32, i32, i32, i32, i32, P, P]),
+    "pe_ps_refine_v": (ctypes.c_int, [P, i64, i32, i32, i32, P, P]),
+    "pe_ps_node_tables": (ctypes.c_int, [P, P, i32, i32, i32, P, P, P]),
+    "pe_ps_quiet_start_nodes": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
     "pe_ps_quiet_start": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
     "pe_ps_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P,
                                                P]),
@@ -317,12 +323,13 @@ def boltzmann_profile(phi, ncell, ion_moments=None, s_w=0, s_p=0, stream=None):
 
 
 def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0,
-                     boundary="periodic"):
+                     boundary="periodic", x_tent=False):
     """Restriction-sample arguments; n_v > 0 selects the phase-space sample (n_v velocity
-    cells of width dv from v_min) instead of the density and momentum moments."""
+    cells of width dv from v_min) instead of the density and momentum moments; x_tent rows
+    are coarse nodes with the hat weights of the repeated 1-2-1 rule instead of Haar bins."""
     return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
                       int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()), int(n_v), float(v_min),
-                      float(1.0 / dv), PE_BOUNDARY[boundary])
+                      float(1.0 / dv), PE_BOUNDARY[boundary], int(bool(x_tent)))
 
 
 def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
@@ -502,6 +509,55 @@ def ps_quiet_start(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w, with_
     return cell, theta, v, w, rho
 
 
+def ps_coarsen_v(sample_fx, s_w, bin_shift, n_vc, wavelet="coif4", stream=None):
+    """Hat rows of fixed-point phase-space samples (int64 [..., nxc, n_vf]) -> coarse
+    coefficients (FP64 [..., nxc, n_vc]): pe_ps_coarsen_v."""
+    n_vf = sample_fx.shape[-1]
+    nrows = sample_fx.numel() // n_vf
+    out = torch.empty(sample_fx.shape[:-1] + (n_vc,), dtype=torch.float64, device=sample_fx.device)
+    check(load().pe_ps_coarsen_v(_ptr(sample_fx), nrows, n_vf, int(s_w), int(bin_shift), PE_WAVELET[wavelet], n_vc,
+                                 _ptr(out), _stream(stream)), "pe_ps_coarsen_v")
+    return out
+
+
+def ps_refine_v(coarse, n_vf, wavelet="coif4", stream=None):
+    """Coarse coefficients (FP64 [..., n_vc]) -> fine velocity histograms (FP64 [..., n_vf])."""
+    coarse = coarse.contiguous()
+    n_vc = coarse.shape[-1]
+    nrows = coarse.numel() // n_vc
+    out = torch.empty(coarse.shape[:-1] + (n_vf,), dtype=torch.float64, device=coarse.device)
+    check(load().pe_ps_refine_v(_ptr(coarse), nrows, n_vc, PE_WAVELET[wavelet], n_vf, _ptr(out), _stream(stream)),
+          "pe_ps_refine_v")
+    return out
+
+
+def ps_node_tables(mass, cdf, ncell, stream=None):
+    """Fine-node sampling tables (FP32 [ncell, 3 n_v + 1]) and densities (FP32 [ncell]) of the
+    coarse-node tables of ps_lift_tables (pe_ps_node_tables)."""
+    nxc, nv = cdf.shape[0], cdf.shape[1] - 1
+    table = torch.empty((ncell, 3 * nv + 1), dtype=torch.float32, device=mass.device)
+    dens = torch.empty(ncell, dtype=torch.float32, device=mass.device)
+    check(load().pe_ps_node_tables(_ptr(mass), _ptr(cdf), nxc, ncell, nv, _ptr(table), _ptr(dens), _stream(stream)),
+          "pe_ps_node_tables")
+    return table, dens
+
+
+def ps_quiet_start_nodes(n, ncell, table, dens, v_min, dv, seed, s_w, with_rho=True, status=None, stream=None):
+    """Wavelet-form quiet start on fine-node tables (pe_ps_quiet_start_nodes)."""
+    dev = table.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    status = _status(status, dev)
+    check(load().pe_ps_quiet_start_nodes(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, _ptr(table), _ptr(dens),
+                                         (table.shape[1] - 1) // 3, float(v_min), float(dv),
+                                         int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(rho), _ptr(status),
+                                         _stream(stream)), "pe_ps_quiet_start_nodes")
+    return cell, theta, v, w, rho
+
+
 def ps_project(samples, dt, dT, filt=0, stream=None):
     """Filtered phase-space projective step (pe_ps_project) of samples [(K+1), nxc, n_v] (FP64,
     device); returns (out, filtered slope), each [nxc, n_v]."""
@@ -537,19 +593,21 @@ def ps_quiet_start_equal(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w,
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
                 v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic",
-                electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0) -> Config:
+                electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0, n_v_coarse=0) -> Config:
     """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
     masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
     filter of the projected phase-space slope (bit 0 along v, bit 1 along x); boundary:
     "periodic" or "absorbing" (walls at nodes 0 and ncell-1, Section 4.2); electrons:
     "boltzmann" (fluid) or "kinetic" (particles of charge-to-mass ratio qm_e, default -1800,
     thermal speed v_th_e, default sqrt(-qm_e); plain PIC reloads them in Boltzmann equilibrium
-    every reset_every steps if > 0)."""
+    every reset_every steps if > 0); n_v_coarse > 0 selects the wavelet form of the phase-space
+    variable (Section 3.3 as stated: coarse nodes by the 1-2-1 rule in x, n_v fine velocity
+    cells reduced by the DWT of `wavelet` to n_v_coarse coefficients)."""
     return Config(int(ncell), int(n_coarse), PE_WAVELET[wavelet], int(K), int(nparticles), float(L), float(dt),
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
                   int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
                   PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter), PE_BOUNDARY[boundary],
-                  PE_ELECTRONS[electrons], int(reset_every), float(qm_e), float(v_th_e))
+                  PE_ELECTRONS[electrons], int(reset_every), float(qm_e), float(v_th_e), int(n_v_coarse))
 
 
 def layout(cfg: Config) -> Layout:
@@ -614,7 +672,7 @@ class Context:
     def coarse_shape(self):
         """(2, n_coarse) for the moments, (n_coarse, n_v) for the phase-space cells."""
         if self.cfg.coarse_kind == PE_COARSE["phase_space"]:
-            return (self.cfg.n_coarse, self.cfg.n_v)
+            return (self.cfg.n_coarse, self.cfg.n_v_coarse if self.cfg.n_v_coarse > 0 else self.cfg.n_v)
         return (2, self.cfg.n_coarse)
 
     def get_coarse(self):

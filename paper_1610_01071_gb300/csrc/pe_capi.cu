@@ -151,7 +151,13 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.w_cap < 0.0 || c.v_cap < 0.0) return PE_EINVAL;
     if (c.coarse_kind != PE_COARSE_MOMENTS && c.coarse_kind != PE_COARSE_PHASE_SPACE) return PE_EINVAL;
     const bool ps = c.coarse_kind == PE_COARSE_PHASE_SPACE;
-    if (ps && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
+    if (c.n_v_coarse < 0 || (c.n_v_coarse > 0 && !ps)) return PE_EINVAL;
+    const bool psw = ps && c.n_v_coarse > 0;  // the wavelet form
+    if (ps && !psw && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
+    if (psw && (!is_pow2(c.n_v) || c.n_v > 1024 || !is_pow2(c.n_v_coarse) || c.n_v_coarse < 2 ||
+                c.n_v_coarse > c.n_v || !(c.v_max > 0.0) || c.ps_filter != 0 || c.boundary != PE_BOUNDARY_PERIODIC ||
+                c.electrons != PE_ELECTRONS_BOLTZMANN || c.n_coarse < 2))
+        return PE_EINVAL;
     if (c.ps_filter < 0 || c.ps_filter > 3) return PE_EINVAL;
     if (c.boundary != PE_BOUNDARY_PERIODIC && c.boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
     const bool walls = c.boundary == PE_BOUNDARY_ABSORBING;
@@ -164,8 +170,9 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
         return PE_EINVAL;
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
-    const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space coefficients
-    const size_t row_fx = 2 * nc > nps ? 2 * nc : nps, crow = 2 * ncoef > nps ? 2 * ncoef : nps;
+    const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space sample row
+    const size_t npc = psw ? ncoef * (size_t)c.n_v_coarse : nps;         // phase-space coefficients
+    const size_t row_fx = 2 * nc > nps ? 2 * nc : nps, crow = 2 * ncoef > npc ? 2 * ncoef : npc;
     const size_t bank = 4 * align256(4 * N);
     out->bytes[PE_BUF_PARTICLES_A] = bank;
     out->bytes[PE_BUF_PARTICLES_B] = bank;
@@ -187,6 +194,9 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
                                          align256(8 * 2 * ncoef * (size_t)(c.n_v + 1)) +
                                          align256(4 * ncoef * (size_t)(3 * c.n_v + 1)) + 256
                                    : 256) +
+                                (psw ? align256(8 * ncoef * (size_t)c.n_v) + align256(4 * nc * (size_t)(3 * c.n_v + 1)) +
+                                           align256(4 * nc)
+                                     : 0) +
                                 (walls ? align256(PE_PS_EQ_SCRATCH_BYTES(nc)) : 0);
     out->bytes[PE_BUF_ELECTRONS_A] = kin ? bank : 0;
     out->bytes[PE_BUF_ELECTRONS_B] = kin ? bank : 0;
@@ -216,14 +226,18 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->dx = cfg->L / cfg->ncell;
     x->dT_cur = cfg->dT;
     x->nc = cfg->n_coarse;
-    x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
-    x->nb = cfg->ncell >> x->bin_shift;
     x->ps = cfg->coarse_kind == PE_COARSE_PHASE_SPACE;
+    x->psw = x->ps && cfg->n_v_coarse > 0;
+    // Haar moments and both phase-space forms restrict over 2^b nodes in x (bins or hat rows)
+    x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR || x->ps) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
+    x->nb = cfg->ncell >> x->bin_shift;
     x->nv = x->ps ? cfg->n_v : 0;
+    x->nvc = x->psw ? cfg->n_v_coarse : x->nv;
     x->vmin = x->ps ? -cfg->v_max : 0.0;
     x->dv = x->ps ? 2.0 * cfg->v_max / cfg->n_v : 1.0;
-    x->ncoef = x->ps ? (int64_t)x->nc * x->nv : 2 * (int64_t)x->nc;
-    x->row_fx = 2 * (int64_t)x->nb > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nb : x->ncoef;
+    x->ncoef = x->ps ? (int64_t)x->nc * x->nvc : 2 * (int64_t)x->nc;
+    const int64_t nps = x->ps ? (int64_t)x->nc * x->nv : 0;  // phase-space sample row
+    x->row_fx = 2 * (int64_t)x->nb > nps ? 2 * (int64_t)x->nb : nps;
     x->crow = 2 * (int64_t)x->nc > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nc : x->ncoef;
     const double w_cap = cfg->w_cap > 0.0 ? cfg->w_cap : 8.0 * cfg->ncell / (double)cfg->nparticles;
     const double v_cap = cfg->v_cap > 0.0 ? cfg->v_cap : 32.0;
@@ -278,6 +292,14 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
                                              align256(4 * nc_ * (3 * (size_t)x->nv + 1)) + 256
                                        : 256;
         x->eq_scratch = x->walls ? (void*)(ph + ps_bytes) : nullptr;
+        if (x->psw) {  // after the phase-space tables (the wavelet form has no walls)
+            char* q = ph + ps_bytes;
+            x->ps_hist = (double*)q;
+            q += align256(8 * nc_ * (size_t)x->nv);
+            x->ps_node_table = (float*)q;
+            q += align256(4 * (size_t)cfg->ncell * (3 * (size_t)x->nv + 1));
+            x->ps_node_dens = (float*)q;
+        }
     }
     if (cudaMemsetAsync(x->arena + lay.offset[PE_BUF_PHI], 0, lay.bytes[PE_BUF_PHI], x->stream) != cudaSuccess ||
         cudaMemsetAsync(x->status, 0, 64, x->stream) != cudaSuccess) {
@@ -506,6 +528,7 @@ static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
         a.n_v = x->nv;
         a.v_min = (float)x->vmin;
         a.inv_dv = (float)(1.0 / x->dv);
+        a.x_tent = x->psw;  // wavelet form: coarse nodes of the repeated 1-2-1 rule
     }
     return a;
 }
@@ -577,6 +600,7 @@ static int measure_phase(pe_ctx* x, double* out)
     const float kick = x->v_at_integer ? 0.5f : 1.0f;
     PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
                      &a, x->status, x->stream));
+    if (x->psw) return pe_ps_coarsen_v(dst, x->nc, x->nv, x->s_w, x->bin_shift, c.wavelet, x->nvc, out, x->stream);
     return pe_ps_coarsen(dst, 1, x->ncoef, x->s_w, out, x->stream);
 }
 
@@ -683,6 +707,9 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
     NvtxRange nvtx("pe_restrict");
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
+    if (ctx->psw)  // rows of consecutive samples are contiguous: [K+1][n_coarse][n_vf] -> [K+1][n_coarse][n_vc]
+        return pe_ps_coarsen_v(ctx->samples, (int64_t)(c.K + 1) * ctx->nc, ctx->nv, ctx->s_w, ctx->bin_shift, c.wavelet,
+                               ctx->nvc, ctx->csamples, ctx->stream);
     if (ctx->ps) return pe_ps_coarsen(ctx->samples, c.K + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
     return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
                       ctx->csamples, ctx->stream);
@@ -715,7 +742,25 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
     if (!ctx) return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
-    if (x->ps) {
+    if (x->psw) {
+        // Section 3.3 lifting: synthesis in v, Appendix C's reconstruction per coarse node,
+        // Eq. (interpolation) to the fine nodes, quiet start on the fine-node tables
+        PE_TRY(pe_ps_refine_v(x->coarse, x->nc, x->nvc, c.wavelet, x->nv, x->ps_hist, x->stream));
+        PE_TRY(pe_ps_lift_tables(x->ps_hist, x->nc, x->nv, x->ps_mass, x->ps_cdf, x->ps_table, x->ps_scratch,
+                                 x->ps_flags, x->stream));
+        PE_TRY(pe_ps_node_tables(x->ps_mass, x->ps_cdf, x->nc, c.ncell, x->nv, x->ps_node_table, x->ps_node_dens,
+                                 x->stream));
+        const int b = x->bank;
+        PE_TRY(timed(x, PE_PROF_LOAD, [&] {
+            return pe_ps_quiet_start_nodes(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell,
+                                           x->ps_node_table, x->ps_node_dens, x->nv, x->vmin, x->dv, lift_seed(x),
+                                           x->s_w, x->rho, x->status, x->stream);
+        }));
+        x->rho_valid = 1;
+        x->v_at_integer = 1;
+        x->fresh = 1;
+        x->phi_hist = 0;
+    } else if (x->ps) {
         // Appendix C: per-bin CDF reconstruction, then quiet start on the tables
         PE_TRY(pe_ps_lift_tables(x->coarse, x->nc, x->nv, x->ps_mass, x->ps_cdf, x->ps_table, x->ps_scratch, x->ps_flags,
                                  x->stream));

@@ -225,6 +225,58 @@ __global__ void __launch_bounds__(256) k_coarsen(const long long* fx, int ncell,
     for (int k = threadIdx.x; k < n_coarse; k += blockDim.x) out[(size_t)row * n_coarse + k] = a[k];
 }
 
+__device__ void synth_level(const Filter& f, const double* a, int nin, double* b);
+
+// Phase space, wavelet form (Section 3.3): one block per row of nvf fixed-point values (coarse
+// node i of sample p, hat-weighted in x), converted with `scale` and analysed in v by the
+// periodized DWT (approximation branch only) down to nvc coefficients, scaled by 2^(L/2) for L
+// levels so that a row's coefficients sum to its mass.
+__global__ void __launch_bounds__(256) k_ps_coarsen_v(const long long* fx, int nvf, double scale, Filter f, int nvc,
+                                                      double lev, double* out)
+{
+    extern __shared__ double buf[];
+    double* a = buf;
+    double* b = buf + nvf;
+    const long long* src = fx + (size_t)blockIdx.x * nvf;
+    for (int j = threadIdx.x; j < nvf; j += blockDim.x) a[j] = (double)src[j] * scale;
+    __syncthreads();
+    for (int len = nvf; len > nvc; len >>= 1) {
+        const int half = len >> 1;
+        for (int k = threadIdx.x; k < half; k += blockDim.x) {
+            double acc = 0.0;
+            for (int m = 0; m < f.len; ++m) acc += f.h[m] * a[(2 * k + m) & (len - 1)];
+            b[k] = acc;
+        }
+        __syncthreads();
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    for (int k = threadIdx.x; k < nvc; k += blockDim.x) out[(size_t)blockIdx.x * nvc + k] = a[k] * lev;
+}
+
+// Lifting of the wavelet form in v: one block per row of nvc coefficients, periodized synthesis
+// with zero details up to nvf cells, scaled by 2^(-L/2) (the inverse of k_ps_coarsen_v on its range).
+__global__ void __launch_bounds__(256) k_ps_refine_v(const double* coarse, int nvc, Filter f, int nvf, double lev,
+                                                     double* out)
+{
+    extern __shared__ double buf[];
+    double* x = buf;
+    double* y = buf + nvf;
+    for (int k = threadIdx.x; k < nvc; k += blockDim.x) x[k] = coarse[(size_t)blockIdx.x * nvc + k];
+    __syncthreads();
+    double* a = x;
+    double* b = y;
+    for (int len = nvc; len < nvf; len <<= 1) {
+        synth_level(f, a, len, b);
+        __syncthreads();
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    for (int j = threadIdx.x; j < nvf; j += blockDim.x) out[(size_t)blockIdx.x * nvf + j] = a[j] * lev;
+}
+
 // Least-squares slope in the paired form of Eq. (leastsquares) and the forward-Euler leap.
 __global__ void k_ls_project(const double* c, int K, int ncoef, double dt, double dT, double* out, double* slope)
 {
@@ -514,6 +566,37 @@ extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int
                                                                  ldexp(1.0, -(s_w + 24)) * lev,
                                                                  ldexp(1.0, -(s_p + 24)) * lev, make_filter(wavelet),
                                                                  n_coarse, coarse);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_ps_coarsen_v(const int64_t* sample_fx, int64_t nrows, int32_t n_vf, int32_t s_w,
+                                      int32_t bin_shift, int32_t wavelet, int32_t n_vc, double* coarse, void* stream)
+{
+    if (!sample_fx || !coarse || nrows < 0 || nrows > INT32_MAX || !is_pow2(n_vf) || !is_pow2(n_vc) || n_vc > n_vf ||
+        n_vf > 4096 || bin_shift < 0 || bin_shift > 30 || s_w < -60 || s_w > 60 || !wavelet_ok(wavelet))
+        return PE_EINVAL;
+    if (nrows == 0) return PE_OK;
+    const size_t smem = 2 * sizeof(double) * (size_t)n_vf;
+    if (ensure_smem((const void*)k_ps_coarsen_v, smem) != PE_OK) return PE_ECUDA;
+    const int L = ilog2(n_vf / n_vc);
+    k_ps_coarsen_v<<<(unsigned)nrows, 256, smem, (cudaStream_t)stream>>>(
+        reinterpret_cast<const long long*>(sample_fx), n_vf, ldexp(1.0, -(s_w + 24 + bin_shift)),
+        make_filter(wavelet), n_vc, pow(2.0, 0.5 * L), coarse);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_ps_refine_v(const double* coarse, int64_t nrows, int32_t n_vc, int32_t wavelet, int32_t n_vf,
+                                     double* hist, void* stream)
+{
+    if (!coarse || !hist || nrows < 0 || nrows > INT32_MAX || !is_pow2(n_vf) || !is_pow2(n_vc) || n_vc > n_vf ||
+        n_vf > 4096 || !wavelet_ok(wavelet))
+        return PE_EINVAL;
+    if (nrows == 0) return PE_OK;
+    const size_t smem = 2 * sizeof(double) * (size_t)n_vf;
+    if (ensure_smem((const void*)k_ps_refine_v, smem) != PE_OK) return PE_ECUDA;
+    const int L = ilog2(n_vf / n_vc);
+    k_ps_refine_v<<<(unsigned)nrows, 256, smem, (cudaStream_t)stream>>>(coarse, n_vc, make_filter(wavelet), n_vf,
+                                                                         pow(2.0, -0.5 * L), hist);
     return launch_status();
 }
 

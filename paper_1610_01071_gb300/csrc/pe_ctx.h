@@ -24,7 +24,12 @@ struct pe_ctx {
     int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
     int nb;              // sample length per moment: ncell >> bin_shift
     int ps;              // phase-space coarse variable (PE_COARSE_PHASE_SPACE)
-    int nv;              // velocity cells (phase space)
+    int nv;              // velocity cells (phase space; the fine cells n_vf of the wavelet form)
+    int psw;             // phase space, wavelet form: hat rows in x, DWT in v to nvc coefficients
+    int nvc;             // wavelet form: velocity coefficients per coarse node
+    double* ps_hist;     // wavelet form: [n_coarse][nv] lifted histograms
+    float* ps_node_table;  // wavelet form: [ncell][3 nv + 1] fine-node sampling rows
+    float* ps_node_dens;   // wavelet form: [ncell] fine-node densities
     double vmin, dv;     // velocity cells: [vmin + j dv, vmin + (j+1) dv)
     int64_t ncoef;       // active coarse coefficients: 2 n_coarse or n_coarse n_v
     int64_t row_fx;      // int64 words per restriction-sample row

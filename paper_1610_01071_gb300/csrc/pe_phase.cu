@@ -259,6 +259,7 @@ struct PSLoad {
     float per_node, vmin, dv, inv_ppc, two_ppc;
     const double* mass;
     const float* table;
+    const float* node_dens;  // wavelet form: per fine node density and sampling row (else null)
     uint32_t half, shift;
     float wscale;
     unsigned long long* rho;
@@ -303,6 +304,20 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c,
     const uint32_t j = i % P.ppc;
     c = (int)(i / P.ppc);
     th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    if (P.node_dens) {
+        // wavelet form: the fine nodes c and c + 1 carry their own density and sampling row
+        // (k_ps_node_tables); weight and velocity are linear in x between them
+        const int c1 = (c + 1) & P.mask;
+        const float d0 = __ldg(P.node_dens + c), d1 = __ldg(P.node_dens + c1);
+        ww = fmaf(th, d1 - d0, d0) * P.inv_ppc;
+        const uint32_t B = __brev(i) + P.half + P.shift;
+        const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+        const int row = 3 * P.nv + 1;
+        const float v0 = cdf_inverse_f(P.table + (size_t)c * row, P.nv, b, P.vmin, P.dv);
+        const float v1 = cdf_inverse_f(P.table + (size_t)c1 * row, P.nv, b, P.vmin, P.dv);
+        vv = fmaf(th, v1 - v0, v0);
+        return;
+    }
     // linear in x between neighbouring bin centres: phi is the distance from the centre of
     // bin b0 (at or left of the particle) in bin widths
     // (a bin sums the CIC charge of its 2^b nodes: it covers x/dx in [i 2^b - 1/2, (i+1) 2^b - 1/2))
@@ -392,6 +407,37 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
     __syncthreads();
     if (dep) grho.flush();
+}
+
+// Wavelet form, lifting in x (Eq. interpolation) at the fine nodes: fine node j lies phi =
+// (j mod 2^b) / 2^b of the way from coarse node i0 = j >> b to i1 = i0 + 1 (periodic); its
+// histogram is the linear interpolation (1 - phi) H_i0 + phi H_i1 of the reconstructed
+// coarse-node histograms, so its density is a0 + a1 (a0 = (1 - phi) mass[i0], a1 = phi
+// mass[i1]) and its CDF the mixture (a0 F_i0 + a1 F_i1) / (a0 + a1). One block per fine node
+// writes the FP32 sampling row of cdf_inverse_f (CDF, inverse cell masses, zero slopes: the
+// density is uniform inside a velocity cell, Appendix C's lookup with linear interpolation),
+// evaluated in FP64, and the node density.
+__global__ void __launch_bounds__(256) k_ps_node_tables(const double* __restrict__ mass, const double* __restrict__ cdf,
+                                                        int nxc, int bin_shift, int nv, float* __restrict__ table,
+                                                        float* __restrict__ dens)
+{
+    const int j = blockIdx.x;
+    const int i0 = j >> bin_shift, i1 = (i0 + 1) & (nxc - 1);
+    const double phi = ldexp((double)(j & ((1 << bin_shift) - 1)), -bin_shift);
+    const double a0 = (1.0 - phi) * mass[i0], a1 = phi * mass[i1], tot = a0 + a1;
+    const double* F0 = cdf + (size_t)i0 * (nv + 1);
+    const double* F1 = cdf + (size_t)i1 * (nv + 1);
+    float* T = table + (size_t)j * (3 * nv + 1);
+    for (int k = threadIdx.x; k <= nv; k += blockDim.x) {
+        const double g = tot > 0.0 ? (a0 * F0[k] + a1 * F1[k]) / tot : (double)k / nv;
+        T[k] = (float)g;
+        if (k < nv) {
+            const double g1 = tot > 0.0 ? (a0 * F0[k + 1] + a1 * F1[k + 1]) / tot : (double)(k + 1) / nv;
+            T[nv + 1 + k] = g1 > g ? (float)(1.0 / (g1 - g)) : 0.0f;
+            T[2 * nv + 1 + k] = 0.0f;
+        }
+    }
+    if (threadIdx.x == 0) dens[j] = (float)tot;
 }
 
 // Least-squares slope of every phase-space cell (Eq. leastsquares), into raw[nxc][nv].
@@ -770,6 +816,65 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     P.two_ppc = 2.0f * (float)P.ppc;
     P.mass = mass;
     P.table = table;
+    P.half = (uint32_t)(2147483648.0 / (double)n);
+    // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the Cranley-Patterson shift
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    P.shift = (uint32_t)(z >> 32);
+    P.wscale = ldexpf(1.0f, s_w);
+    P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
+    P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
+    P.status = status;
+    const size_t smem = rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const void* k = (const void*)k_ps_quiet_start;
+    if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
+    const int grid = particle_grid(k, 256, smem, n, &P.chunk);
+    if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
+    k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
+    return launch_status(1);
+}
+
+extern "C" PE_API int pe_ps_node_tables(const double* mass, const double* cdf, int32_t nxc, int32_t ncell,
+                                        int32_t n_v, float* node_table, float* node_dens, void* stream)
+{
+    if (!mass || !cdf || !node_table || !node_dens || !is_pow2(ncell) || !is_pow2(nxc) || nxc > ncell || n_v < 1 ||
+        n_v > 4096)
+        return PE_EINVAL;
+    k_ps_node_tables<<<ncell, 256, 0, (cudaStream_t)stream>>>(mass, cdf, nxc, ilog2(ncell / nxc), n_v, node_table,
+                                                              node_dens);
+    return launch_status(1);
+}
+
+extern "C" PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                                              int32_t ncell, const float* node_table, const float* node_dens,
+                                              int32_t n_v, double v_min, double dv, uint64_t seed, int32_t s_w,
+                                              int64_t* rho_fx, uint32_t* status, void* stream)
+{
+    if (!is_pow2(ncell) || ncell < 8 || !node_table || !node_dens || n_v < 1 || n_v > 4096 || !(dv > 0.0))
+        return PE_EINVAL;
+    if (n <= 0 || n % ncell != 0 || n >= (int64_t(1) << 32)) return PE_EINVAL;
+    if (!cell || !theta || !v || !w || !aligned16(cell) || !aligned16(theta) || !aligned16(v) || !aligned16(w))
+        return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PSLoad P{};
+    P.cell = cell;
+    P.theta = theta;
+    P.v = v;
+    P.w = w;
+    P.n = n;
+    P.ppc = (uint32_t)(n / ncell);
+    P.log2ppc = is_pow2(P.ppc) ? ilog2(P.ppc) : -1;
+    P.ncell = ncell;
+    P.mask = ncell - 1;
+    P.nv = n_v;
+    P.vmin = (float)v_min;
+    P.dv = (float)dv;
+    P.inv_ppc = 1.0f / (float)P.ppc;
+    P.two_ppc = 2.0f * (float)P.ppc;
+    P.table = node_table;
+    P.node_dens = node_dens;
     P.half = (uint32_t)(2147483648.0 / (double)n);
     // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the Cranley-Patterson shift
     uint64_t z = seed + 0x9E3779B97F4A7C15ULL;

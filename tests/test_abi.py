@@ -123,3 +123,26 @@ int main(void) {
     assert run.returncode == 0, run.stdout + run.stderr
     version, rc, bad, msg, _ = run.stdout.strip().split("|")
     assert version.startswith("pepic") and rc == "0" and bad == "1" and msg
+
+
+def test_layout_of_the_phase_space_wavelet_form(lib):
+    # n_v fine velocity cells in the sample rows, n_v_coarse coefficients in the coarse state,
+    # and the fine-node sampling tables; configurations outside the form are refused
+    from paper_1610_01071_gb300 import _binding as b
+
+    def cfg(**kw):
+        a = dict(coarse="phase_space", n_v=256, v_max=8.0, n_v_coarse=64, wavelet="coif4")
+        a.update(kw)
+        return b.make_config(4096, 256, 20, 1 << 24, 2048.0, 0.1, 8.0, **a)
+
+    lay = b.layout(cfg())
+    assert lay.bytes[b.BUF["samples_fx"]] == 8 * 256 * 256 * 22  # [K+2][n_coarse][n_vf]
+    assert lay.bytes[b.BUF["coarse"]] == 8 * 256 * 64  # [n_coarse][n_vc]
+    haar = b.layout(cfg(n_v_coarse=0, wavelet="haar"))
+    assert lay.bytes[b.BUF["phase"]] >= haar.bytes[b.BUF["phase"]] + 4 * 4096 * (3 * 256 + 1)
+    for bad in (dict(n_v_coarse=128, n_v=64), dict(n_v=200), dict(ps_filter=1), dict(boundary="absorbing"),
+                dict(electrons="kinetic"), dict(n_v_coarse=1), dict(n_v_coarse=48)):
+        with pytest.raises(RuntimeError):
+            b.layout(cfg(**bad))
+    with pytest.raises(RuntimeError):  # the wavelet form belongs to the phase-space variable
+        b.layout(b.make_config(4096, 256, 20, 1 << 24, 2048.0, 0.1, 8.0, n_v_coarse=16))
