@@ -42,6 +42,9 @@ KERNEL_BYTES = {
     "deposit": (12, "k_particles<deposit> (charge deposit alone: cell, theta, w read)"),
     "load": (16, "k_quiet_start (lifting: quiet-start loading with the deposit fused, write only)"),
     "push_sample_ps": (28, "k_particles<push + phase-space sample> (64 x-bins x 64 velocity cells window)"),
+    "push_sample_psw": (28, "k_particles<push + phase-space sample, hat rows> (wavelet form: 16 coarse nodes x "
+                            "256 velocity cells window)"),
+    "load_psw": (16, "k_ps_quiet_start on fine-node tables (wavelet-form lifting, write only)"),
 }
 # DRAM bytes (read + write) per launch on the 2^24-ion workload from the ncu captures
 # summarised in profiles/, each valid while the particle kernels' device code
@@ -517,6 +520,25 @@ def time_kernels(ctx, cfg, pb, stream, reps=10):
         out["push_sample_ps"] = (k["ms"] / max(k["launches"], 1), k["launches"])
         if int(st.item()) != 0 or ps.sync_status() != 0:
             raise RuntimeError("device status set while timing the deposit / phase-space pass")
+        del ps
+        # the wavelet form of the phase-space variable (hat rows, 256 velocity cells -> 64 Coif4)
+        c = pb.make_config(ncell, cfg["n_coarse"], cfg["K"], N, cfg["L"], cfg["dt"], 10.0, qm=cfg["qm"],
+                           v_th=cfg["v_th"], seed=13, newton_tol=1e-10, coarse="phase_space", n_v=256, v_max=8.0,
+                           n_v_coarse=64, wavelet="coif4")
+        pw = pb.Context(c, device=dev, stream=stream)
+        pw.load_initial(cfg["amplitude"])
+        pw.step()
+        pw.profile_read_kinds()
+        pw.profile(True)
+        for _ in range(2):
+            pw.step()
+        pw.profile(False)
+        kk = pw.profile_read_kinds()
+        out["push_sample_psw"] = (kk["push_sample_ps"]["ms"] / max(kk["push_sample_ps"]["launches"], 1),
+                                  kk["push_sample_ps"]["launches"])
+        out["load_psw"] = (kk["load"]["ms"] / max(kk["load"]["launches"], 1), kk["load"]["launches"])
+        if pw.sync_status() != 0:
+            raise RuntimeError("device status set while timing the wavelet-form passes")
     return out
 
 
@@ -663,6 +685,9 @@ def run_kernel(args):
     samp_ps = torch.zeros((nxc, nv), dtype=torch.int64, device=dev)
     args_ps = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp_ps, bin_shift=bshift, n_v=nv,
                                   v_min=-8.0, dv=16.0 / nv)
+    samp_psw = torch.zeros((nxc, 256), dtype=torch.int64, device=dev)
+    args_psw = pb.make_sample_args(Ef, 10.0, cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp_psw, bin_shift=bshift, n_v=256,
+                                   v_min=-8.0, dv=16.0 / 256, x_tent=True)
     if args.kernel in ("ps_tables", "ps_quiet_start"):
         pb.sample(cell, theta, v, w, Ef, ncell, cfg["dt"], 0.5, args_ps, status=status)
         H = pb.ps_coarsen(samp_ps, d.s_w)
@@ -673,6 +698,9 @@ def run_kernel(args):
     def once():
         if args.kernel == "push_sample_ps":
             pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, sample=args_ps,
+                    status=status)
+        elif args.kernel == "push_sample_psw":
+            pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, sample=args_psw,
                     status=status)
         elif args.kernel == "ps_tables":
             pb.load().pe_ps_lift_tables(pb._ptr(H), nxc, nv, pb._ptr(mass), pb._ptr(cdf), pb._ptr(table),
@@ -710,7 +738,7 @@ def run_kernel(args):
     torch.cuda.synchronize()
     us = 1e3 * e0.elapsed_time(e1) / args.steps
     bytes_per = {"push_sample": 28, "push_sample_nodal": 28, "push": 28, "deposit": 12, "sample": 16, "quiet_start": 16,
-                 "field": 0, "push_sample_ps": 28, "ps_tables": 0, "ps_quiet_start": 16}
+                 "field": 0, "push_sample_ps": 28, "push_sample_psw": 28, "ps_tables": 0, "ps_quiet_start": 16}
     gbs = bytes_per[args.kernel] * N / (us * 1e-6) / 1e9
     print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us, "algorithmic_GBps": gbs,
                       "status": int(status.item())}), flush=True)

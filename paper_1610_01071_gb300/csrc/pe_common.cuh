@@ -229,9 +229,12 @@ struct PSGrid {
         return s + 3 * n;
     }
 
-    __device__ __forceinline__ void add(int key, long long val) const
+    // key = (row << 16) | velocity cell
+    __device__ __forceinline__ void add(int key, long long val) const { add_at(key >> 16, key & 0xFFFF, val); }
+
+    // Adds val at (row xb, velocity cell j) without dividing the key.
+    __device__ __forceinline__ void add_at(int xb, int j, long long val) const
     {
-        const int xb = key / nv, j = key - xb * nv;
         const int d = (xb - base) & xmask;
         if (d < width) {
             const int idx = d * nv + j;
@@ -241,8 +244,17 @@ struct PSGrid {
             if (b) atomicAdd(&d1[idx], b);
             if (c) atomicAdd(&d2[idx], c);
         } else {
-            atomicAdd(&g[key], (unsigned long long)val);
+            atomicAdd(&g[(size_t)xb * nv + j], (unsigned long long)val);
         }
+    }
+
+    // Hat rows: a run with key (xb << 16) | j, W = sum w_q and R = sum w_q f_q adds
+    // W 2^24 - R to row xb and R to row xb + 1 (periodic).
+    __device__ __forceinline__ void add_pair(int key, int32_t w, long long r) const
+    {
+        const int xb = key >> 16, j = key & 0xFFFF;
+        add_at(xb, j, (long long)w * (1ll << 24) - r);
+        add_at((xb + 1) & xmask, j, r);
     }
 
     __device__ __forceinline__ void zero() const
@@ -290,6 +302,63 @@ struct PSAcc {
         }
     }
 };
+
+// Per-lane run of equal (coarse node, velocity cell) keys of the hat rows, over a lane's
+// four particles of a group: W = sum w_q (32 bits: |W| <= 4 2^23) and R = sum w_q f_q.
+struct PSAcc2 {
+    int key;  // (xb << 16) | j; -1 while empty
+    int32_t w;
+    long long r;
+
+    __device__ __forceinline__ void reset()
+    {
+        key = -1;
+        w = 0;
+        r = 0;
+    }
+    __device__ __forceinline__ void add(int k, int32_t wq, long long rq, const PSGrid& gr)
+    {
+        if (k == key) {
+            w += wq;
+            r += rq;
+        } else {
+            if (key >= 0) gr.add_pair(key, w, r);
+            key = k;
+            w = wq;
+            r = rq;
+        }
+    }
+};
+
+// ps_add_warp for the hat rows: runs of equal keys in consecutive lanes summed (W over at most
+// 128 particles stays below 2^30), added by the run's first lane as two rows.
+__device__ __forceinline__ void ps_add_warp2(const PSGrid& gr, int key, int32_t w, long long r)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int nact = __popc(act);
+    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
+        if (key >= 0) gr.add_pair(key, w, r);
+        return;
+    }
+    const int prev = __shfl_up_sync(act, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(act, head);
+    const unsigned after = heads & (0xFFFFFFFEu << lane);
+    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
+    int32_t sw = w;
+    long long sr = r;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t ow = __shfl_down_sync(act, sw, off);
+        const long long orr = __shfl_down_sync(act, sr, off);
+        if (lane + off <= run_end) {
+            sw += ow;
+            sr += orr;
+        }
+    }
+    if (head && key >= 0) gr.add_pair(key, sw, sr);
+}
 
 // Adds (key, val) pairs of the active lanes to a PSGrid, summing runs of equal keys in
 // consecutive lanes first (consecutive particles of a velocity-ordered cell share their

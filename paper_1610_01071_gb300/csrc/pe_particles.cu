@@ -48,8 +48,7 @@ struct PushParams {
     // phase-space sample (PS modes): samp_n is the histogram [(ncell >> bin_shift)][nv]
     int nv, ps_width;
     float vmin, inv_dv;
-    int ps_tent;       // rows are coarse nodes with hat weights (Eq. restriction b times), else bins
-    float tent_scale;  // 2^(24 - bin_shift)
+    float tent_scale;  // hat rows (the TENT modes): 2^(24 - bin_shift)
     // bounded grid (walls at nodes 0 and ncell-1, Section 4.2): a particle whose drift ends
     // outside [0, (ncell-1) dx) is absorbed (weight 0 written to w_out, parked on the wall node
     // with v = 0); particles of weight 0 are not moved; co-moving targets outside are dropped
@@ -65,19 +64,23 @@ enum Mode {
     kPushSampleBinned = 4,
     kSampleBinned = 5,
     kPushSamplePS = 6,  // push + phase-space sample
-    kSamplePS = 7
+    kSamplePS = 7,
+    kPushSamplePSW = 8,  // push + phase-space sample with hat rows (the wavelet form)
+    kSamplePSW = 9
 };
 
 template <int MODE>
 struct ModeTraits {
     static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                 MODE == kPushSamplePS);
+                                 MODE == kPushSamplePS || MODE == kPushSamplePSW);
     static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                  MODE == kPushSamplePS);
+                                  MODE == kPushSamplePS || MODE == kPushSamplePSW);
     static constexpr bool sample = (MODE == kPushSample || MODE == kSample || MODE == kPushSampleBinned ||
-                                    MODE == kSampleBinned || MODE == kPushSamplePS || MODE == kSamplePS);
+                                    MODE == kSampleBinned || MODE == kPushSamplePS || MODE == kSamplePS ||
+                                    MODE == kPushSamplePSW || MODE == kSamplePSW);
     static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
-    static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS);
+    static constexpr bool tent = (MODE == kPushSamplePSW || MODE == kSamplePSW);
+    static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS || tent);
 };
 
 // Fixed-point value rn(x 2^s); records in *ovf whether it left the range |q| <= 2^23.
@@ -140,7 +143,7 @@ struct BinSample {
 template <int MODE, bool WALLS>
 __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft, bool act, int c, float th,
                                         float vv, float ww, BinSample& bs, const SmemGrid& gsn, const SmemGrid& gsm,
-                                        const PSGrid& gps, PSAcc& acc, PSAcc& accr, bool* ovf, int& c_out, float& th_out,
+                                        const PSGrid& gps, PSAcc& acc, PSAcc2& acc2, bool* ovf, int& c_out, float& th_out,
                                         float& v_out, float& w_out, int32_t& wq_out)
 {
     using Tr = ModeTraits<MODE>;
@@ -214,20 +217,17 @@ __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft,
             const float jf = floorf((vt - P.vmin) * P.inv_dv);
             const int j = jf < 0.0f ? 0 : (jf >= (float)P.nv ? P.nv - 1 : (int)jf);
             const int b0 = cs >> P.bin_shift, b1 = cs1 >> P.bin_shift;
-            if (P.ps_tent) {
+            if (Tr::tent) {
                 // hat of half-width 2^b around the coarse nodes (Eq. restriction applied b times
                 // to the CIC histogram): the fraction f of the way from node b0 to the next one
                 const float f = ((float)(cs & ((1 << P.bin_shift) - 1)) + ths) * P.tent_scale;
-                const long long right = (long long)wq * (long long)__float2uint_rn(f);
-                const int i1 = (b0 + 1) & ((P.ncell >> P.bin_shift) - 1);
-                acc.add(b0 * P.nv + j, (long long)wq * (long long)kThetaOne - right, gps);
-                accr.add(i1 * P.nv + j, right, gps);
+                acc2.add((b0 << 16) | j, wq, (long long)wq * (long long)__float2uint_rn(f), gps);
             } else if (b0 == b1) {
-                acc.add(b0 * P.nv + j, (long long)wq * (long long)kThetaOne, gps);
+                acc.add((b0 << 16) | j, (long long)wq * (long long)kThetaOne, gps);
             } else {  // split across a bin edge (rare): the right part goes straight to the grid
                 const FxSplit qn = fx_split(wq, ths);
-                acc.add(b0 * P.nv + j, (long long)qn.left, gps);
-                gps.add(b1 * P.nv + j, (long long)qn.right);
+                acc.add((b0 << 16) | j, (long long)qn.left, gps);
+                gps.add_at(b1, j, (long long)qn.right);
             }
         }
         if (!Tr::ps && counted) {
@@ -399,9 +399,10 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     BinWindow bw;
     bw.begin(0);
     BinSample bs;
-    PSAcc acc, accr;  // runs of the left and (hat rows) right parts
+    PSAcc acc;
+    PSAcc2 acc2;  // hat rows
     acc.reset();
-    accr.reset();
+    acc2.reset();
     bool ovf = false;
 
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
@@ -426,19 +427,19 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int4 co;
         float4 to, vo, wo;
         int32_t q0, q1, q2, q3;
-        const bool e0 = process<MODE, WALLS>(P, ft, act, ca.x, ta.x, va.x, wa.x, bs, gsn, gsm, gps, acc, accr, &ovf, co.x,
+        const bool e0 = process<MODE, WALLS>(P, ft, act, ca.x, ta.x, va.x, wa.x, bs, gsn, gsm, gps, acc, acc2, &ovf, co.x,
                                              to.x, vo.x, wo.x, q0);
         if (kBin) {  // the group's bin window starts at the lowest bin of the lanes' first particles
             bw.begin(warp_low_bin(bs.b, bs.ok, P.ncell >> P.bin_shift));
             if (bs.ok) bw.add(bs.b, q0, bs.mq, bs.tq, bsn, bsm);
         }
-        const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gps, acc, accr, &ovf, co.y,
+        const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gps, acc, acc2, &ovf, co.y,
                                              to.y, vo.y, wo.y, q1);
         if (kBin && bs.ok) bw.add(bs.b, q1, bs.mq, bs.tq, bsn, bsm);
-        const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gps, acc, accr, &ovf, co.z,
+        const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gps, acc, acc2, &ovf, co.z,
                                              to.z, vo.z, wo.z, q2);
         if (kBin && bs.ok) bw.add(bs.b, q2, bs.mq, bs.tq, bsn, bsm);
-        const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gps, acc, accr, &ovf, co.w,
+        const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gps, acc, acc2, &ovf, co.w,
                                              to.w, vo.w, wo.w, q3);
         if (kBin && bs.ok) bw.add(bs.b, q3, bs.mq, bs.tq, bsn, bsm);
         if (kWrite && act) {
@@ -449,11 +450,12 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
                 reinterpret_cast<float4*>(P.w_out)[g] = wo;  // an absorption in this group
         }
         if (kPS) {  // one warp-aggregated add per group of four particles per lane
-            ps_add_warp(gps, acc.key, acc.val);
-            acc.reset();
-            if (P.ps_tent) {
-                ps_add_warp(gps, accr.key, accr.val);
-                accr.reset();
+            if (Tr::tent) {
+                ps_add_warp2(gps, acc2.key, acc2.w, acc2.r);
+                acc2.reset();
+            } else {
+                ps_add_warp(gps, acc.key, acc.val);
+                acc.reset();
             }
         }
         if (kBin) bw.end(bsn, bsm);
@@ -466,7 +468,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int32_t q;
         const float vi = kNeedV ? P.v[i] : 0.f;
         const float wi = P.w[i];
-        const bool e = process<MODE, WALLS>(P, ft, true, P.cell[i], P.theta[i], vi, wi, bs, gsn, gsm, gps, acc, accr, &ovf, co,
+        const bool e = process<MODE, WALLS>(P, ft, true, P.cell[i], P.theta[i], vi, wi, bs, gsn, gsm, gps, acc, acc2, &ovf, co,
                                             to, vo, wo, q);
         if (kWrite) {
             P.cell[i] = co;
@@ -475,11 +477,12 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
             if (WALLS && wo != wi) P.w_out[i] = wo;
         }
         if (kPS) {
-            ps_add_warp(gps, acc.key, acc.val);
-            acc.reset();
-            if (P.ps_tent) {
-                ps_add_warp(gps, accr.key, accr.val);
-                accr.reset();
+            if (Tr::tent) {
+                ps_add_warp2(gps, acc2.key, acc2.w, acc2.r);
+                acc2.reset();
+            } else {
+                ps_add_warp(gps, acc.key, acc.val);
+                acc.reset();
             }
         }
         if (kBin && bs.ok) {  // straight to the grids
@@ -956,6 +959,7 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
     if (s->n_v < 0 || s->n_v > 1024) return false;
     if (s->x_tent != 0 && (s->x_tent != 1 || s->n_v <= 0 || s->boundary != PE_BOUNDARY_PERIODIC)) return false;
+    if (s->n_v > 0 && (ncell >> s->bin_shift) > 32767) return false;  // phase-space keys pack (row << 16) | cell
     if (s->n_v > 0) {
         const int nxc = ncell >> s->bin_shift;
         const size_t w = (size_t)ps_window_rows(nxc, s->n_v);
@@ -1105,8 +1109,8 @@ extern "C" PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w
             P.nv = sample->n_v;
             P.vmin = sample->v_min;
             P.inv_dv = sample->inv_dv;
-            P.ps_tent = sample->x_tent;
             P.tent_scale = ldexpf(1.0f, 24 - P.bin_shift);
+            if (sample->x_tent) return launch_particles<kPushSamplePSW>(P, (cudaStream_t)stream);
             return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream);
         }
         if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream);
@@ -1156,8 +1160,8 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
         P.nv = sample->n_v;
         P.vmin = sample->v_min;
         P.inv_dv = sample->inv_dv;
-        P.ps_tent = sample->x_tent;
         P.tent_scale = ldexpf(1.0f, 24 - P.bin_shift);
+        if (sample->x_tent) return launch_particles<kSamplePSW>(P, (cudaStream_t)stream);
         return launch_particles<kSamplePS>(P, (cudaStream_t)stream);
     }
     if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream);
