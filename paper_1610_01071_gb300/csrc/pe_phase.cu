@@ -260,6 +260,7 @@ struct PSLoad {
     const double* mass;
     const float* table;
     const float* node_dens;  // wavelet form: per fine node density and sampling row (else null)
+    int stage_rows;          // wavelet form: fine-node rows staged in shared memory per block
     uint32_t half, shift;
     float wscale;
     unsigned long long* rho;
@@ -295,7 +296,32 @@ __device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int 
 // the particle. A piecewise-constant (Haar) lift would give the density steps at bin edges,
 // and the field spikes there, multiplied by the co-moving time tau ~ Delta t, spread the next
 // restriction sample in velocity. FP32 (the particle precision) on tables built in FP64.
-__device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+// Inverse of a row with uniform density inside each cell (F[0..nv], then the inverse cell
+// masses): v_min + dv (k + r), k the first index with F[k+1] > b, r = (b - F[k]) / p_k.
+__device__ __forceinline__ float cdf_inverse_lin(const float* T, int nv, float b, float vmin, float dv)
+{
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T[mid + 1] > b)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const float f0 = T[lo], sl = T[nv + 1 + lo];
+    const float r = sl > 0.0f ? fminf(fmaxf((b - f0) * sl, 0.0f), 1.0f) : 0.5f;
+    return fmaf(dv, (float)lo + r, vmin);
+}
+
+// Fine-node rows of the block's cells staged in shared memory (rows c_stage .. c_stage + n - 1,
+// 2 nv + 1 floats each); other nodes read the global table.
+struct NodeStage {
+    const float* rows;
+    int c_stage, n;
+};
+
+__device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns, uint32_t i, int& c, float& th,
+                                            float& vv, float& ww)
 {
     if (P.log2ppc > 0) {
         const uint32_t k = i & (P.ppc - 1u);
@@ -312,9 +338,12 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, uint32_t i, int& c,
         ww = fmaf(th, d1 - d0, d0) * P.inv_ppc;
         const uint32_t B = __brev(i) + P.half + P.shift;
         const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-        const int row = 3 * P.nv + 1;
-        const float v0 = cdf_inverse_f(P.table + (size_t)c * row, P.nv, b, P.vmin, P.dv);
-        const float v1 = cdf_inverse_f(P.table + (size_t)c1 * row, P.nv, b, P.vmin, P.dv);
+        const int row = 3 * P.nv + 1, srow = 2 * P.nv + 1;
+        const int r0 = (c - ns.c_stage) & P.mask, r1 = (c1 - ns.c_stage) & P.mask;
+        const float* T0 = r0 < ns.n ? ns.rows + r0 * srow : P.table + (size_t)c * row;
+        const float* T1 = r1 < ns.n ? ns.rows + r1 * srow : P.table + (size_t)c1 * row;
+        const float v0 = cdf_inverse_lin(T0, P.nv, b, P.vmin, P.dv);
+        const float v1 = cdf_inverse_lin(T1, P.nv, b, P.vmin, P.dv);
         vv = fmaf(th, v1 - v0, v0);
         return;
     }
@@ -359,9 +388,20 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     const bool dep = P.rho != nullptr;
     const int c_first = (begin < end) ? (int)((uint64_t)begin / P.ppc) : 0;
     SmemGrid grho{};
+    uint32_t* s = smem;
     if (dep) {
-        grho.bind(smem, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
         grho.zero();
+    }
+    NodeStage ns{nullptr, 0, 0};
+    if (P.node_dens && P.stage_rows > 0) {
+        float* st = reinterpret_cast<float*>(s);
+        const int rw = 2 * P.nv + 1;
+        for (int i = threadIdx.x; i < P.stage_rows * rw; i += blockDim.x) {
+            const int r = i / rw, k = i - r * rw;
+            st[i] = __ldg(P.table + (size_t)((c_first + r) & P.mask) * (3 * P.nv + 1) + k);
+        }
+        ns = NodeStage{st, c_first, P.stage_rows};
     }
     __syncthreads();
     const int64_t gb0 = begin >> 2, gb1 = end >> 2;
@@ -378,10 +418,10 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
         int4 c;
         float4 t, vv, ww;
         const uint32_t i0 = (uint32_t)(g << 2);
-        ps_load_one(P, i0, c.x, t.x, vv.x, ww.x);
-        ps_load_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
-        ps_load_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
-        ps_load_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        ps_load_one(P, ns, i0, c.x, t.x, vv.x, ww.x);
+        ps_load_one(P, ns, i0 + 1, c.y, t.y, vv.y, ww.y);
+        ps_load_one(P, ns, i0 + 2, c.z, t.z, vv.z, ww.z);
+        ps_load_one(P, ns, i0 + 3, c.w, t.w, vv.w, ww.w);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -396,7 +436,7 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         int c;
         float t, vv, ww;
-        ps_load_one(P, (uint32_t)i, c, t, vv, ww);
+        ps_load_one(P, ns, (uint32_t)i, c, t, vv, ww);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;
@@ -875,6 +915,9 @@ extern "C" PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float
     P.two_ppc = 2.0f * (float)P.ppc;
     P.table = node_table;
     P.node_dens = node_dens;
+    // a block's cells (chunks of <= 65536 particles) and the next node, within 48 KB
+    const int rw_bytes = 4 * (2 * n_v + 1);
+    P.stage_rows = std::min<int64_t>({(int64_t)ncell, (48 * 1024) / rw_bytes, 65536 / (int64_t)P.ppc + 2});
     P.half = (uint32_t)(2147483648.0 / (double)n);
     // splitmix64 (Steele, Lea, Flood 2014) of the seed; its upper half is the Cranley-Patterson shift
     uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
@@ -886,7 +929,8 @@ extern "C" PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float
     P.rho = reinterpret_cast<unsigned long long*>(rho_fx);
     P.rho_width = ncell <= kRhoWindowNodes ? ncell : kRhoWindowNodes;
     P.status = status;
-    const size_t smem = rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0;
+    const size_t smem = (rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0) +
+                        (size_t)P.stage_rows * (size_t)rw_bytes;
     const void* k = (const void*)k_ps_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     const int grid = particle_grid(k, 256, smem, n, &P.chunk);
