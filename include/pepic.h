@@ -749,6 +749,17 @@ PE_API int pe_profile_read(pe_ctx* ctx, double* push_ms, int64_t* push_launches,
                            int64_t* field_launches);
 PE_API int pe_profile_read_kinds(pe_ctx* ctx, double* ms, int64_t* launches);
 
+/* =================================================================== tensor-core GEMM
+ * C[M][N] (FP32, row stride ldc) = A[M][K] B[N][K]^T for BF16 A and B stored with K contiguous
+ * (row strides lda, ldb elements; 16-byte aligned bases, lda and ldb multiples of 8): tcgen05.mma
+ * with the accumulator in tensor memory, operands staged by TMA in the 128-byte swizzle layout,
+ * tiles of 128 x 128 (N % 128 == 0) or 128 x 64 (N % 64 == 0), four stages of K = 64; M and K
+ * may be ragged (zero fill). The GEMM engine of the surrogate's training and inference. A
+ * device-side wait that exceeds its budget sets PE_FLAG_TIMEOUT in status[0] (device) and
+ * skips the product. */
+PE_API int pe_tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int32_t M,
+                           int32_t N, int32_t K, uint32_t* status, void* stream);
+
 /* =================================================================== batch
  * Ensemble of independent realisations advanced together (the same burst length, fine
  * and macro steps; any grid of at least 64 cells, any particle count, Haar wavelet, moment

@@ -181,6 +181,7 @@ SIGNATURES = {
     "pe_ps_project": (ctypes.c_int, [P, i32, i32, i32, f64, f64, i32, P, P, P, P]),
     "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
     "pe_ps_coarsen_v": (ctypes.c_int, [P, i64, i32, i32, i32, i32, i32, P, P]),
+    "pe_tc_gemm_bf16": (ctypes.c_int, [P, i64, P, i64, P, i64, i32, i32, i32, P, P]),
     "pe_ps_refine_v": (ctypes.c_int, [P, i64, i32, i32, i32, P, P]),
     "pe_ps_node_tables": (ctypes.c_int, [P, P, i32, i32, i32, P, P, P]),
     "pe_ps_quiet_start_nodes": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),
@@ -556,6 +557,19 @@ def ps_quiet_start_nodes(n, ncell, table, dens, v_min, dv, seed, s_w, with_rho=T
                                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(s_w), _ptr(rho), _ptr(status),
                                          _stream(stream)), "pe_ps_quiet_start_nodes")
     return cell, theta, v, w, rho
+
+
+def tc_gemm(A, B, status=None, stream=None):
+    """C = A B^T (FP32) for BF16 A [M, K] and B [N, K] on the tensor cores (pe_tc_gemm_bf16)."""
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.shape[1] == B.shape[1]
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    status = _status(status, A.device)
+    check(load().pe_tc_gemm_bf16(_ptr(A), K, _ptr(B), K, _ptr(C), N, M, N, K, _ptr(status), _stream(stream)),
+          "pe_tc_gemm_bf16")
+    return C, status
 
 
 def ps_project(samples, dt, dT, filt=0, stream=None):
