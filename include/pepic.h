@@ -815,12 +815,15 @@ PE_API void pe_batch_destroy(pe_batch* b);
 #define PE_MLP_MAX_LAYERS 8
 enum pe_mlp_buffer {
     PE_MLP_PARAMS = 0,  /* f32[nparams]: W_1, b_1, W_2, b_2, ... (flat) */
-    PE_MLP_PARAMS_BF16, /* bf16 mirror of the parameters */
+    PE_MLP_PARAMS_BF16, /* bf16 mirror of the parameters [nparams], then its per-layer transposes
+                           (W_l^T [d_l][d_{l+1}] at W_l's offset + nparams; the data-gradient
+                           GEMMs read them with K contiguous) */
     PE_MLP_GRADS,       /* f32[nparams] gradients of the last pe_mlp_grad / training step */
     PE_MLP_ADAM_M,      /* f32[nparams] first moments */
     PE_MLP_ADAM_V,      /* f32[nparams] second moments */
     PE_MLP_NORM,        /* f32[4][dmax] mu_in, sd_in, mu_out, sd_out; statistics scratch; step, loss */
-    PE_MLP_WORK,        /* batch workspace (activations, gradients) for max_batch rows */
+    PE_MLP_WORK,        /* batch workspace for max_batch rows: activations and gradients, and their
+                           transposes (the weight-gradient GEMMs contract over the batch) */
     PE_MLP_NBUF
 };
 typedef struct pe_mlp_layout {
@@ -865,6 +868,12 @@ PE_API int pe_mlp_train(pe_mlp* net, const float* X, const float* Y, int64_t npa
 PE_API int pe_mlp_set_params(pe_mlp* net, const float* params);
 /* Parameter count and device addresses of the step counter, parameters and gradients. */
 PE_API int pe_mlp_info(const pe_mlp* net, int64_t* nparams, int64_t* steps_device_ptr, void** params, void** grads);
+/* Every product of the network (forward, data and weight gradients) runs on the tensor-core
+ * GEMM of pe_tc_gemm_bf16 with the bias, GELU, loss or GELU' factor fused into its epilogue.
+ * pe_mlp_sync_status synchronises the network's stream, reads and clears its device status
+ * word: PE_ETIMEOUT if a GEMM's bounded wait expired since the last call (its product was
+ * skipped), else PE_OK. */
+PE_API int pe_mlp_sync_status(pe_mlp* net);
 
 /* Gated surrogate macro step (the a-posteriori check of the learned slope). From the coarse
  * state c at the start of the step: s_mlp = net(c); lift (unless fresh); a probe burst of

@@ -189,6 +189,7 @@ SIGNATURES = {
     "pe_ps_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, i32, P, P, i32, f64, f64, u64, i32, P, P, P,
                                                P]),
     "pe_mlp_layout_for": (ctypes.c_int, [i32, P, i32, ctypes.POINTER(MLPLayout)]),
+    "pe_mlp_sync_status": (ctypes.c_int, [P]),
     "pe_mlp_create": (ctypes.c_int, [i32, P, i32, P, sz, P, ctypes.POINTER(P)]),
     "pe_mlp_destroy": (None, [P]),
     "pe_mlp_init": (ctypes.c_int, [P, u64]),
@@ -920,6 +921,10 @@ class MLP:
     def params_bf16(self):
         return self._view("params_bf16", torch.bfloat16, self.nparams)
 
+    def params_bf16_transposed(self):
+        """The per-layer transposes of the BF16 weights (W_l^T at W_l's offset; biases unused)."""
+        return self._view("params_bf16", torch.bfloat16, 2 * self.nparams)[self.nparams:]
+
     def grads(self):
         return self._view("grads", torch.float32, self.nparams)
 
@@ -972,3 +977,7 @@ class MLP:
               "pe_mlp_train")
         self.stream.synchronize()
         return float(self.loss_dev.item())
+
+    def sync_status(self) -> int:
+        """PE_OK, or PE_ETIMEOUT if a tensor-core GEMM's bounded wait expired (status cleared)."""
+        return int(load().pe_mlp_sync_status(self._h))

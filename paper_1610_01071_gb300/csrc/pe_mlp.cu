@@ -1,15 +1,17 @@
 // Learned coarse-derivative surrogate: a multilayer perceptron c -> dc/dt trained on the
 // least-squares slopes that resolved bursts measure (Section 3.3, Eq. (leastsquares)),
 // with BF16 tensor-core GEMMs accumulating in FP32, GELU hidden layers, MSE loss and
-// Adam. Every layer's forward, data-gradient and weight-gradient product is one launch
-// of the tiled GEMM below (mma.sync m16n8k16 BF16 -> FP32, cp.async double-buffered
-// shared-memory tiles, ldmatrix fragments with the transposing form where an operand is
-// stored with its output index contiguous) with the bias, activation, loss or GELU'
-// factor fused into its epilogue.
+// Adam. Every layer's forward, data-gradient and weight-gradient product is one launch of
+// the tcgen05 GEMM of pe_tc.cuh (TMEM accumulator, TMA-staged operands) with the bias,
+// activation, loss or GELU' factor fused into its epilogue. That kernel takes both operands
+// with K contiguous, so the products that contract over another index read transposed
+// copies kept alongside: the BF16 weights' transposes (rewritten with the mirror by Adam),
+// and the activations' and gradients' transposes (written by the epilogues that produce them).
 //
 // Storage (caller-owned arena, see pe_mlp_layout_for): FP32 master parameters (the flat
-// vector W_1 [d1][d0], b_1, W_2, ...), their BF16 mirror used by the GEMMs, FP32
-// gradients, Adam moments, per-component z-score statistics, and a batch workspace.
+// vector W_1 [d1][d0], b_1, W_2, ...), their BF16 mirror and its per-layer transposes used by
+// the GEMMs, FP32 gradients, Adam moments, per-component z-score statistics, and a batch
+// workspace.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -23,50 +25,16 @@
 #include "pe_common.cuh"
 #include "pe_ctx.h"
 #include "pe_internal.h"
+#include "pe_tc.cuh"
 #include "pepic.h"
 
 namespace pe {
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 32;
-constexpr int kGemmThreads = 128;  // 4 warps, 2 x 2, each a 32 x 32 tile
-constexpr int kPad = 8;            // bf16 elements of row padding (ldmatrix without bank conflicts)
 constexpr int kNormBlocks = 64;    // row blocks of the z-score statistics
 constexpr int kLossSlots = 4096;
 
-enum Layout { kNT = 0, kNN = 1, kTN = 2 };  // A[m][k] B[n][k] | A[m][k] B[k][n] | A[k][m] B[k][n]
 enum Epi { kEpiHidden = 0, kEpiOutInfer = 1, kEpiOutTrain = 2, kEpiDgrad = 3, kEpiWgrad = 4 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -96,157 +64,113 @@ struct GemmArgs {
     float gscale;          // train: 2 / (B D)
 };
 
-// C[M][N] = sum_k A(m, k) B(k, n) with the fused epilogue EPI. M may be ragged (rows
-// beyond M read as zero and are not stored); N % 64 == 0, K % 32 == 0.
-template <int LAYOUT, int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g)
-{
-    constexpr bool a_km = (LAYOUT == kTN);  // A stored [k][m]
-    constexpr bool b_kn = (LAYOUT != kNT);  // B stored [k][n]
-    constexpr int A_ROWS = a_km ? kBK : kBM, A_COLS = (a_km ? kBM : kBK) + kPad;
-    constexpr int B_ROWS = b_kn ? kBK : kBN, B_COLS = (b_kn ? kBN : kBK) + kPad;
-    __shared__ __align__(128) __nv_bfloat16 sA[2][A_ROWS][A_COLS];
-    __shared__ __align__(128) __nv_bfloat16 sB[2][B_ROWS][B_COLS];
-    __shared__ float sloss[kGemmThreads / 32];
+// Epilogue of the tensor-core GEMM for row m, columns n0 .. n0 + 31 of C = A B^T (FP32 from
+// TMEM): the bias + GELU of a hidden layer (Z, Aout and its transpose AoutT), the
+// de-normalised output (inference), the loss and output gradient (training; Y optional, G and
+// its transpose), the data gradient times GELU'(Z) (G and its transpose), or the FP32 weight
+// gradient. Rows beyond M are not stored. finish() folds the training loss of the block into
+// loss_part[block] (every thread calls it).
+template <int EPI>
+struct TcEpi {
+    GemmArgs g;
+    __nv_bfloat16* AoutT;  // transposed BF16 output [N][ldT]
+    int ldT;
+    float lsum;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-
-    auto load_tile = [&](int stage, int k0) {
-        // 256 chunks of 16 bytes per operand tile, two per thread
+    __device__ __forceinline__ void operator()(int m, int n0, const float* v)
+    {
+        if (m >= g.M) return;
+        const size_t o = (size_t)m * g.N + n0;
+        if (EPI == kEpiWgrad) {
+            float4* d = reinterpret_cast<float4*>(g.Y + o);
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int c = tid + r * kGemmThreads;
-            if (!a_km) {
-                const int row = c >> 2, col = (c & 3) * 8;
-                const int m = m0 + row;
-                const bool ok = m < g.M;
-                const __nv_bfloat16* src = g.A + (size_t)(ok ? m : 0) * g.lda + k0 + col;
-                cp_async16(&sA[stage][row][col], src, ok ? 16 : 0);
-            } else {
-                const int row = c >> 3, col = (c & 7) * 8;
-                const __nv_bfloat16* src = g.A + (size_t)(k0 + row) * g.lda + m0 + col;
-                cp_async16(&sA[stage][row][col], src, 16);
-            }
-            if (!b_kn) {
-                const int row = c >> 2, col = (c & 3) * 8;
-                const __nv_bfloat16* src = g.B + (size_t)(n0 + row) * g.ldb + k0 + col;
-                cp_async16(&sB[stage][row][col], src, 16);
-            } else {
-                const int row = c >> 3, col = (c & 7) * 8;
-                const __nv_bfloat16* src = g.B + (size_t)(k0 + row) * g.ldb + n0 + col;
-                cp_async16(&sB[stage][row][col], src, 16);
+            for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const int n = n0 + j;
+            float v0 = v[j], v1 = v[j + 1];
+            if (EPI == kEpiHidden) {
+                v0 += g.bias[n];
+                v1 += g.bias[n + 1];
+                *reinterpret_cast<float2*>(g.Z + o + j) = make_float2(v0, v1);
+                const __nv_bfloat162 a = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+                *reinterpret_cast<__nv_bfloat162*>(g.Aout + o + j) = a;
+                AoutT[(size_t)n * ldT + m] = a.x;
+                AoutT[(size_t)(n + 1) * ldT + m] = a.y;
+            } else if (EPI == kEpiOutInfer) {
+                v0 += g.bias[n];
+                v1 += g.bias[n + 1];
+                const float y0 = fmaf(v0, g.sd[n], g.mu[n]), y1 = fmaf(v1, g.sd[n + 1], g.mu[n + 1]);
+                if (g.Y64) {
+                    g.Y64[o + j] = (double)y0;
+                    g.Y64[o + j + 1] = (double)y1;
+                } else {
+                    *reinterpret_cast<float2*>(g.Y + o + j) = make_float2(y0, y1);
+                }
+            } else if (EPI == kEpiOutTrain) {
+                v0 += g.bias[n];
+                v1 += g.bias[n + 1];
+                const float2 t = *reinterpret_cast<const float2*>(g.T + o + j);
+                const float d0 = v0 - t.x, d1 = v1 - t.y;
+                lsum = fmaf(d0, d0, fmaf(d1, d1, lsum));
+                if (g.Y) *reinterpret_cast<float2*>(g.Y + o + j) = make_float2(v0, v1);
+                const __nv_bfloat162 gr = __floats2bfloat162_rn(g.gscale * d0, g.gscale * d1);
+                *reinterpret_cast<__nv_bfloat162*>(g.Aout + o + j) = gr;
+                AoutT[(size_t)n * ldT + m] = gr.x;
+                AoutT[(size_t)(n + 1) * ldT + m] = gr.y;
+            } else if (EPI == kEpiDgrad) {
+                const float2 z = *reinterpret_cast<const float2*>(g.Z + o + j);
+                const __nv_bfloat162 gr = __floats2bfloat162_rn(v0 * gelu_grad_f(z.x), v1 * gelu_grad_f(z.y));
+                *reinterpret_cast<__nv_bfloat162*>(g.Aout + o + j) = gr;
+                AoutT[(size_t)n * ldT + m] = gr.x;
+                AoutT[(size_t)(n + 1) * ldT + m] = gr.y;
             }
         }
-        cp_async_commit();
-    };
-
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-
-    const int ktiles = g.K / kBK;
-    load_tile(0, 0);
-    for (int kt = 0; kt < ktiles; ++kt) {
-        const int st = kt & 1;
-        if (kt + 1 < ktiles) {
-            load_tile(st ^ 1, (kt + 1) * kBK);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kBK; kk += 16) {
-            uint32_t af[2][4], bfr[2][4];
-            const int mi_ = lane >> 3, r8 = lane & 7;
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                if (!a_km)
-                    ldsm_x4(af[mi], &sA[st][wm + mi * 16 + (mi_ & 1) * 8 + r8][kk + (mi_ >> 1) * 8]);
-                else
-                    ldsm_x4_t(af[mi], &sA[st][kk + (mi_ >> 1) * 8 + r8][wm + mi * 16 + (mi_ & 1) * 8]);
-            }
-#pragma unroll
-            for (int np = 0; np < 2; ++np) {
-                if (!b_kn)
-                    ldsm_x4(bfr[np], &sB[st][wn + np * 16 + (mi_ >> 1) * 8 + r8][kk + (mi_ & 1) * 8]);
-                else
-                    ldsm_x4_t(bfr[np], &sB[st][kk + (mi_ & 1) * 8 + r8][wn + np * 16 + (mi_ >> 1) * 8]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int nj = 0; nj < 4; ++nj)
-                    mma_bf16(acc[mi][nj], af[mi], bfr[nj >> 1][(nj & 1) * 2], bfr[nj >> 1][(nj & 1) * 2 + 1]);
-        }
-        __syncthreads();
     }
 
-    // epilogue: thread holds rows (gid, gid + 8) x cols (2 tig, 2 tig + 1) of each 16 x 8 tile
-    const int gid = lane >> 2, tig = lane & 3;
-    float lsum = 0.0f;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm + mi * 16 + gid + h * 8;
-                const int n = n0 + wn + nj * 8 + 2 * tig;
-                if (m >= g.M) continue;
-                float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
-                const size_t o = (size_t)m * g.N + n;
-                if (EPI == kEpiHidden) {
-                    v0 += g.bias[n];
-                    v1 += g.bias[n + 1];
-                    *reinterpret_cast<float2*>(g.Z + o) = make_float2(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162*>(g.Aout + o) = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
-                } else if (EPI == kEpiOutInfer) {
-                    v0 += g.bias[n];
-                    v1 += g.bias[n + 1];
-                    const float y0 = fmaf(v0, g.sd[n], g.mu[n]), y1 = fmaf(v1, g.sd[n + 1], g.mu[n + 1]);
-                    if (g.Y64) {
-                        g.Y64[o] = (double)y0;
-                        g.Y64[o + 1] = (double)y1;
-                    } else {
-                        *reinterpret_cast<float2*>(g.Y + o) = make_float2(y0, y1);
-                    }
-                } else if (EPI == kEpiOutTrain) {
-                    v0 += g.bias[n];
-                    v1 += g.bias[n + 1];
-                    const float2 t = *reinterpret_cast<const float2*>(g.T + o);
-                    const float d0 = v0 - t.x, d1 = v1 - t.y;
-                    lsum = fmaf(d0, d0, fmaf(d1, d1, lsum));
-                    if (g.Y) *reinterpret_cast<float2*>(g.Y + o) = make_float2(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162*>(g.Aout + o) =
-                        __floats2bfloat162_rn(g.gscale * d0, g.gscale * d1);
-                } else if (EPI == kEpiDgrad) {
-                    const float2 z = *reinterpret_cast<const float2*>(g.Z + o);
-                    *reinterpret_cast<__nv_bfloat162*>(g.Aout + o) =
-                        __floats2bfloat162_rn(v0 * gelu_grad_f(z.x), v1 * gelu_grad_f(z.y));
-                } else {  // weight gradient, FP32
-                    *reinterpret_cast<float2*>(g.Y + o) = make_float2(v0, v1);
-                }
-            }
-    if (EPI == kEpiOutTrain) {
-        lsum = warp_sum_f(lsum);
-        if (lane == 0) sloss[warp] = lsum;
+    __device__ __forceinline__ void finish()
+    {
+        if (EPI != kEpiOutTrain) return;
+        __shared__ float sloss[tc::kThreads / 32];
+        const float w = warp_sum_f(lsum);
+        if ((threadIdx.x & 31) == 0) sloss[threadIdx.x >> 5] = w;
         __syncthreads();
-        if (tid == 0) {
-            float s = 0.0f;
-            for (int w = 0; w < kGemmThreads / 32; ++w) s += sloss[w];
-            g.loss_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int k = 0; k < tc::kThreads / 32; ++k) t += sloss[k];
+            g.loss_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ small kernels
+
+// Weight blocks of the flat parameter vector: layer l's W [rows = d_{l+1}][cols = d_l] at off;
+// its BF16 transpose [d_l][d_{l+1}] sits at the same offset of the transposed mirror.
+struct WeightTable {
+    int64_t off[PE_MLP_MAX_LAYERS];
+    int rows[PE_MLP_MAX_LAYERS], cols[PE_MLP_MAX_LAYERS];
+    int L;
+};
+
+// Writes the BF16 value of flat parameter i into the mirror and, for a weight, into the
+// transposed mirror.
+__device__ __forceinline__ void put_bf16(const WeightTable& wt, int64_t i, float w, __nv_bfloat16* __restrict__ pb,
+                                         __nv_bfloat16* __restrict__ pbT)
+{
+    const __nv_bfloat16 b = __float2bfloat16_rn(w);
+    pb[i] = b;
+    for (int l = 0; l < wt.L; ++l) {
+        const int64_t r = i - wt.off[l];
+        if (r >= 0 && r < (int64_t)wt.rows[l] * wt.cols[l]) {
+            const int row = (int)(r / wt.cols[l]), col = (int)(r - (int64_t)row * wt.cols[l]);
+            pbT[wt.off[l] + (int64_t)col * wt.rows[l] + row] = b;
+            break;
         }
     }
 }
-
-// ------------------------------------------------------------------ small kernels
 
 struct ParamSeg {
     int64_t off, n;
@@ -267,7 +191,8 @@ __device__ __forceinline__ uint64_t splitmix64_seq(uint64_t seed, uint64_t i)
 
 // W = (2u - 1) a with u = (s_i >> 40) 2^-24 from the splitmix64 sequence (flat index i);
 // biases 0. Writes the FP32 master and its BF16 mirror.
-__global__ void k_mlp_init(ParamTable tab, uint64_t seed, float* __restrict__ p, __nv_bfloat16* __restrict__ pb)
+__global__ void k_mlp_init(ParamTable tab, WeightTable wt, uint64_t seed, float* __restrict__ p,
+                           __nv_bfloat16* __restrict__ pb, __nv_bfloat16* __restrict__ pbT)
 {
     for (int s = 0; s < tab.nseg; ++s) {
         const ParamSeg sg = tab.seg[s];
@@ -279,7 +204,7 @@ __global__ void k_mlp_init(ParamTable tab, uint64_t seed, float* __restrict__ p,
                 w = (2.0f * u - 1.0f) * sg.bound;
             }
             p[idx] = w;
-            pb[idx] = __float2bfloat16_rn(w);
+            put_bf16(wt, idx, w, pb, pbT);
         }
     }
 }
@@ -364,7 +289,8 @@ template <typename T>
 __global__ void k_prep(const T* __restrict__ X, const float* __restrict__ Y, int B, int D, int Dout,
                        const int32_t* __restrict__ rows, const int32_t* __restrict__ shifts, int P,
                        const float* __restrict__ mu, const float* __restrict__ sd, const float* __restrict__ mu_o,
-                       const float* __restrict__ sd_o, __nv_bfloat16* __restrict__ xz, float* __restrict__ tz)
+                       const float* __restrict__ sd_o, __nv_bfloat16* __restrict__ xz, __nv_bfloat16* __restrict__ xzT,
+                       int ldT, float* __restrict__ tz)
 {
     const int i = blockIdx.y;
     if (i >= B) return;
@@ -378,7 +304,9 @@ __global__ void k_prep(const T* __restrict__ X, const float* __restrict__ Y, int
         }
         if (k < D) {
             const float x = (float)X[r * D + src];
-            xz[(size_t)i * D + k] = __float2bfloat16_rn((x - mu[k]) / sd[k]);
+            const __nv_bfloat16 b = __float2bfloat16_rn((x - mu[k]) / sd[k]);
+            xz[(size_t)i * D + k] = b;
+            if (xzT) xzT[(size_t)k * ldT + i] = b;
         }
         if (Y && k < Dout) tz[(size_t)i * Dout + k] = (Y[r * Dout + src] - mu_o[k]) / sd_o[k];
     }
@@ -413,9 +341,9 @@ __global__ void k_loss_final(const float* __restrict__ part, int n, float* __res
 // advance it). theta, m, v FP32; the BF16 mirror is rewritten. The decay rates and their
 // complements come in FP64 (0.999 is not a float) and the bias corrections are formed in
 // FP64 once per thread.
-__global__ void k_adam(float* __restrict__ p, __nv_bfloat16* __restrict__ pb, const float* __restrict__ grad,
-                       float* __restrict__ m, float* __restrict__ v, int64_t n, int64_t* __restrict__ step, float lr,
-                       double b1, double b2, float eps)
+__global__ void k_adam(float* __restrict__ p, __nv_bfloat16* __restrict__ pb, __nv_bfloat16* __restrict__ pbT,
+                       WeightTable wt, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, int64_t* __restrict__ step, float lr, double b1, double b2, float eps)
 {
     const int64_t t = *step + 1;
     const float c1 = (float)(1.0 / (1.0 - pow(b1, (double)t))), c2 = (float)(1.0 / (1.0 - pow(b2, (double)t)));
@@ -428,7 +356,7 @@ __global__ void k_adam(float* __restrict__ p, __nv_bfloat16* __restrict__ pb, co
         v[i] = vi;
         const float w = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
         p[i] = w;
-        pb[i] = __float2bfloat16_rn(w);
+        put_bf16(wt, i, w, pb, pbT);
     }
 }
 
@@ -453,6 +381,8 @@ struct pe_mlp {
     cudaStream_t stream;
     float* p;
     __nv_bfloat16* pb;
+    __nv_bfloat16* pbT;  // per-layer transposes of the BF16 weights (same offsets as pb)
+    pe::WeightTable wt;
     float* grad;
     float* am;
     float* av;
@@ -470,6 +400,11 @@ struct pe_mlp {
     float* y;           // [Bm][dL]
     float* tz;          // [Bm][dL]
     __nv_bfloat16* g[2];
+    int ldT;             // row stride of the transposed batch arrays (max_batch rounded up to 64)
+    __nv_bfloat16* xzT;  // [d0][ldT]
+    __nv_bfloat16* aT[PE_MLP_MAX_LAYERS];  // [d_{l+1}][ldT]
+    __nv_bfloat16* gT[2];                  // [dmax][ldT]
+    uint32_t* status;    // device status word (PE_FLAG_TIMEOUT from the GEMM's bounded waits)
     int shift_period;   // period used by the statistics (for reference)
 };
 
@@ -488,8 +423,11 @@ int check_dims(int32_t nlayers, const int32_t* dims, int32_t max_batch)
 }
 
 struct WorkPlan {
-    size_t rows, shifts, xz, z[PE_MLP_MAX_LAYERS], a[PE_MLP_MAX_LAYERS], y, tz, g0, g1, total;
+    size_t rows, shifts, xz, z[PE_MLP_MAX_LAYERS], a[PE_MLP_MAX_LAYERS], y, tz, g0, g1, xzT, aT[PE_MLP_MAX_LAYERS],
+        gT0, gT1, total;
 };
+
+int ld_transposed(int Bm) { return (Bm + 63) & ~63; }
 
 WorkPlan plan_work(int L, const int32_t* dims, int Bm, int dmax)
 {
@@ -511,17 +449,44 @@ WorkPlan plan_work(int L, const int32_t* dims, int Bm, int dmax)
     w.tz = take(4 * (size_t)Bm * dims[L]);
     w.g0 = take(2 * (size_t)Bm * dmax);
     w.g1 = take(2 * (size_t)Bm * dmax);
+    const size_t ldT = (size_t)ld_transposed(Bm);
+    w.xzT = take(2 * ldT * dims[0]);
+    for (int l = 0; l + 1 < L; ++l) w.aT[l] = take(2 * ldT * dims[l + 1]);
+    w.gT0 = take(2 * ldT * dmax);
+    w.gT1 = take(2 * ldT * dmax);
     w.total = o;
     return w;
 }
 
-template <int LAYOUT, int EPI>
-int gemm(const GemmArgs& g, cudaStream_t s)
+// C[M][N] = A[M][K] B[N][K]^T on the tensor cores with the epilogue EPI; A and B stored
+// with K contiguous (row strides lda, ldb). AoutT/ldT: transposed BF16 copy of the output.
+// Returns the number of tiles (one loss partial each).
+template <int EPI>
+int tc_gemm(pe_mlp* h, const GemmArgs& g, __nv_bfloat16* AoutT, cudaStream_t s, int* tiles)
 {
-    dim3 grid(g.N / kBN, (g.M + kBM - 1) / kBM);
-    k_gemm<LAYOUT, EPI><<<grid, kGemmThreads, 0, s>>>(g);
+    const int bn = (g.N % 128 == 0) ? 128 : 64;
+    CUtensorMap ma, mb;
+    PE_TRY(tc_operand_map(&ma, g.A, g.M, g.K, g.lda, tc::kBM));
+    PE_TRY(tc_operand_map(&mb, g.B, g.N, g.K, g.ldb, bn));
+    TcEpi<EPI> e{g, AoutT, h->ldT, 0.0f};
+    dim3 grid(g.N / bn, (g.M + tc::kBM - 1) / tc::kBM);
+    if (tiles) *tiles = (int)(grid.x * grid.y);
+    if (bn == 128) {
+        const void* k = (const void*)tc::k_tc_gemm<128, TcEpi<EPI>>;
+        if (ensure_smem(k, tc::TileCfg<128>::kSmemBytes) != PE_OK) return PE_ECUDA;
+        tc::k_tc_gemm<128, TcEpi<EPI>><<<grid, tc::kThreads, tc::TileCfg<128>::kSmemBytes, s>>>(ma, mb, g.M, g.K, e,
+                                                                                               h->status);
+    } else {
+        const void* k = (const void*)tc::k_tc_gemm<64, TcEpi<EPI>>;
+        if (ensure_smem(k, tc::TileCfg<64>::kSmemBytes) != PE_OK) return PE_ECUDA;
+        tc::k_tc_gemm<64, TcEpi<EPI>><<<grid, tc::kThreads, tc::TileCfg<64>::kSmemBytes, s>>>(ma, mb, g.M, g.K, e,
+                                                                                             h->status);
+    }
     return PE_OK;
 }
+
+// Loss partials of the output layer's GEMM (one per tile).
+int loss_tiles(int Dout, int B) { return (Dout / ((Dout % 128 == 0) ? 128 : 64)) * ((B + tc::kBM - 1) / tc::kBM); }
 
 GemmArgs args0() { GemmArgs g; memset(&g, 0, sizeof(g)); return g; }
 
@@ -544,21 +509,21 @@ int forward(pe_mlp* h, int B, int train, float* y32, double* y64, int* launches)
         if (l + 1 < h->L) {
             g.Z = h->z[l];
             g.Aout = h->a[l];
-            gemm<kNT, kEpiHidden>(g, s);
+            PE_TRY(tc_gemm<kEpiHidden>(h, g, h->aT[l], s, nullptr));
             in = h->a[l];
         } else if (!train) {
             g.Y = y32;
             g.Y64 = y64;
             g.mu = h->norm + 2 * h->dmax;
             g.sd = h->norm + 3 * h->dmax;
-            gemm<kNT, kEpiOutInfer>(g, s);
+            PE_TRY(tc_gemm<kEpiOutInfer>(h, g, nullptr, s, nullptr));
         } else {
             g.T = h->tz;
             g.Y = h->y;
             g.Aout = h->g[(h->L - 1) & 1];
             g.loss_part = h->loss_part;
             g.gscale = 2.0f / ((float)B * (float)g.N);
-            gemm<kNT, kEpiOutTrain>(g, s);
+            PE_TRY(tc_gemm<kEpiOutTrain>(h, g, h->gT[(h->L - 1) & 1], s, nullptr));
         }
         ++*launches;
     }
@@ -572,31 +537,30 @@ int backward(pe_mlp* h, int B, int* launches)
     cudaStream_t s = h->stream;
     for (int l = h->L - 1; l >= 0; --l) {
         const __nv_bfloat16* gl = h->g[l & 1];
-        const __nv_bfloat16* act = l ? h->a[l - 1] : h->xz;
-        GemmArgs w = args0();  // dW_l [d_{l+1}][d_l] = G_l^T act_{l-1}
-        w.A = gl;
-        w.B = act;
+        GemmArgs w = args0();  // dW_l [d_{l+1}][d_l] = G_l^T act_{l-1}: both transposes, K = batch
+        w.A = h->gT[l & 1];
+        w.B = l ? h->aT[l - 1] : h->xzT;
         w.M = h->dims[l + 1];
         w.N = h->dims[l];
         w.K = B;
-        w.lda = h->dims[l + 1];
-        w.ldb = h->dims[l];
+        w.lda = h->ldT;
+        w.ldb = h->ldT;
         w.Y = h->grad + h->w_off[l];
-        gemm<kTN, kEpiWgrad>(w, s);
+        PE_TRY(tc_gemm<kEpiWgrad>(h, w, nullptr, s, nullptr));
         k_bias_grad<<<(h->dims[l + 1] + 255) / 256, 256, 0, s>>>(gl, B, h->dims[l + 1], h->grad + h->b_off[l]);
         *launches += 2;
         if (l == 0) break;
-        GemmArgs d = args0();  // G_{l-1} = (G_l W_l) * GELU'(z_{l-1})
+        GemmArgs d = args0();  // G_{l-1} = (G_l W_l) * GELU'(z_{l-1}): W_l read as its transpose
         d.A = gl;
-        d.B = h->pb + h->w_off[l];
+        d.B = h->pbT + h->w_off[l];
         d.M = B;
         d.N = h->dims[l];
         d.K = h->dims[l + 1];
         d.lda = h->dims[l + 1];
-        d.ldb = h->dims[l];
+        d.ldb = h->dims[l + 1];
         d.Z = h->z[l - 1];
         d.Aout = h->g[(l - 1) & 1];
-        gemm<kNN, kEpiDgrad>(d, s);
+        PE_TRY(tc_gemm<kEpiDgrad>(h, d, h->gT[(l - 1) & 1], s, nullptr));
         ++*launches;
     }
     return PE_OK;
@@ -609,10 +573,10 @@ int grad_pass(pe_mlp* h, const float* X, const float* Y, int64_t npairs, const i
     const int D = h->dims[0], Dout = h->dims[h->L];
     dim3 pg((std::max(D, Dout) + 255) / 256, B);
     k_prep<float><<<pg, 256, 0, s>>>(X, Y, B, D, Dout, rows, shifts, P, h->norm, h->norm + h->dmax,
-                                     h->norm + 2 * h->dmax, h->norm + 3 * h->dmax, h->xz, h->tz);
+                                     h->norm + 2 * h->dmax, h->norm + 3 * h->dmax, h->xz, h->xzT, h->ldT, h->tz);
     ++*launches;
-    forward(h, B, 1, nullptr, nullptr, launches);
-    const int nblk = (Dout / kBN) * ((B + kBM - 1) / kBM);
+    PE_TRY(forward(h, B, 1, nullptr, nullptr, launches));
+    const int nblk = loss_tiles(Dout, B);
     k_loss_final<<<1, 256, 0, s>>>(h->loss_part, nblk, h->loss, 1.0f / ((float)B * (float)Dout));
     ++*launches;
     return backward(h, B, launches);
@@ -631,7 +595,7 @@ extern "C" PE_API int pe_mlp_layout_for(int32_t nlayers, const int32_t* dims, in
     for (int l = 0; l <= nlayers; ++l) dmax = std::max(dmax, (int)dims[l]);
     out->nparams = np;
     out->bytes[PE_MLP_PARAMS] = 4 * (size_t)np;
-    out->bytes[PE_MLP_PARAMS_BF16] = 2 * (size_t)np;
+    out->bytes[PE_MLP_PARAMS_BF16] = 2 * 2 * (size_t)np;  // the mirror, then its per-layer transposes
     out->bytes[PE_MLP_GRADS] = 4 * (size_t)np;
     out->bytes[PE_MLP_ADAM_M] = 4 * (size_t)np;
     out->bytes[PE_MLP_ADAM_V] = 4 * (size_t)np;
@@ -677,6 +641,13 @@ extern "C" PE_API int pe_mlp_create(int32_t nlayers, const int32_t* dims, int32_
     h->stream = (cudaStream_t)stream;
     h->p = (float*)(h->arena + lay.offset[PE_MLP_PARAMS]);
     h->pb = (__nv_bfloat16*)(h->arena + lay.offset[PE_MLP_PARAMS_BF16]);
+    h->pbT = h->pb + h->nparams;
+    h->wt.L = nlayers;
+    for (int l = 0; l < nlayers; ++l) {
+        h->wt.off[l] = h->w_off[l];
+        h->wt.rows[l] = dims[l + 1];
+        h->wt.cols[l] = dims[l];
+    }
     h->grad = (float*)(h->arena + lay.offset[PE_MLP_GRADS]);
     h->am = (float*)(h->arena + lay.offset[PE_MLP_ADAM_M]);
     h->av = (float*)(h->arena + lay.offset[PE_MLP_ADAM_V]);
@@ -689,6 +660,7 @@ extern "C" PE_API int pe_mlp_create(int32_t nlayers, const int32_t* dims, int32_
     nb += 8 * (size_t)kNormBlocks * h->dmax;
     h->step = (int64_t*)nb;
     h->loss = (float*)(nb + 8);
+    h->status = (uint32_t*)(nb + 16);
     h->loss_part = (float*)(nb + 256);
     const WorkPlan w = plan_work(nlayers, dims, max_batch, h->dmax);
     char* wb = h->arena + lay.offset[PE_MLP_WORK];
@@ -703,6 +675,11 @@ extern "C" PE_API int pe_mlp_create(int32_t nlayers, const int32_t* dims, int32_
     h->tz = (float*)(wb + w.tz);
     h->g[0] = (__nv_bfloat16*)(wb + w.g0);
     h->g[1] = (__nv_bfloat16*)(wb + w.g1);
+    h->ldT = ld_transposed(max_batch);
+    h->xzT = (__nv_bfloat16*)(wb + w.xzT);
+    for (int l = 0; l + 1 < nlayers; ++l) h->aT[l] = (__nv_bfloat16*)(wb + w.aT[l]);
+    h->gT[0] = (__nv_bfloat16*)(wb + w.gT0);
+    h->gT[1] = (__nv_bfloat16*)(wb + w.gT1);
     *out = h;
     return PE_OK;
 }
@@ -722,10 +699,10 @@ extern "C" PE_API int pe_mlp_init(pe_mlp* h, uint64_t seed)
     }
     tab.nseg = 2 * h->L;
     cudaStream_t s = h->stream;
-    k_mlp_init<<<2 * sm_count(), 256, 0, s>>>(tab, seed, h->p, h->pb);
+    k_mlp_init<<<2 * sm_count(), 256, 0, s>>>(tab, h->wt, seed, h->p, h->pb, h->pbT);
     const size_t nb = 4 * (size_t)h->nparams;
     if (cudaMemsetAsync(h->am, 0, nb, s) != cudaSuccess || cudaMemsetAsync(h->av, 0, nb, s) != cudaSuccess ||
-        cudaMemsetAsync(h->grad, 0, nb, s) != cudaSuccess || cudaMemsetAsync(h->step, 0, 16, s) != cudaSuccess)
+        cudaMemsetAsync(h->grad, 0, nb, s) != cudaSuccess || cudaMemsetAsync(h->step, 0, 32, s) != cudaSuccess)
         return PE_ECUDA;
     // identity normalisation until pe_mlp_fit_norm
     std::vector<float> id(4 * (size_t)h->dmax, 0.0f);
@@ -765,12 +742,12 @@ extern "C" PE_API int pe_mlp_forward(pe_mlp* h, const void* x, int32_t x_is_f64,
     dim3 pg((D + 255) / 256, B);
     if (x_is_f64)
         k_prep<double><<<pg, 256, 0, s>>>((const double*)x, nullptr, B, D, 0, nullptr, nullptr, 0, h->norm,
-                                          h->norm + h->dmax, nullptr, nullptr, h->xz, nullptr);
+                                          h->norm + h->dmax, nullptr, nullptr, h->xz, nullptr, h->ldT, nullptr);
     else
         k_prep<float><<<pg, 256, 0, s>>>((const float*)x, nullptr, B, D, 0, nullptr, nullptr, 0, h->norm,
-                                         h->norm + h->dmax, nullptr, nullptr, h->xz, nullptr);
+                                         h->norm + h->dmax, nullptr, nullptr, h->xz, nullptr, h->ldT, nullptr);
     int launches = 1;
-    forward(h, B, 0, y_is_f64 ? nullptr : (float*)y, y_is_f64 ? (double*)y : nullptr, &launches);
+    PE_TRY(forward(h, B, 0, y_is_f64 ? nullptr : (float*)y, y_is_f64 ? (double*)y : nullptr, &launches));
     return launch_status(launches);
 }
 
@@ -778,10 +755,9 @@ extern "C" PE_API int pe_mlp_grad(pe_mlp* h, const float* X, const float* Y, int
                                   int32_t B, float* loss)
 {
     if (!h || !X || !Y || B < 32 || B % 32 || B > h->max_batch || (!rows && npairs < B)) return PE_EINVAL;
-    const int nblk = (h->dims[h->L] / kBN) * ((B + kBM - 1) / kBM);
-    if (nblk > kLossSlots) return PE_EINVAL;
+    if (loss_tiles(h->dims[h->L], B) > kLossSlots) return PE_EINVAL;
     int launches = 0;
-    grad_pass(h, X, Y, npairs, rows, nullptr, B, 0, &launches);
+    PE_TRY(grad_pass(h, X, Y, npairs, rows, nullptr, B, 0, &launches));
     if (loss && cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) return PE_ECUDA;
     return launch_status(launches);
 }
@@ -791,8 +767,8 @@ extern "C" PE_API int pe_mlp_adam(pe_mlp* h, double lr, double beta1, double bet
     if (!h || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
         return PE_EINVAL;
     cudaStream_t s = h->stream;
-    k_adam<<<2 * sm_count(), 256, 0, s>>>(h->p, h->pb, h->grad, h->am, h->av, h->nparams, h->step, (float)lr, beta1,
-                                          beta2, (float)eps);
+    k_adam<<<2 * sm_count(), 256, 0, s>>>(h->p, h->pb, h->pbT, h->wt, h->grad, h->am, h->av, h->nparams, h->step,
+                                          (float)lr, beta1, beta2, (float)eps);
     k_step_advance<<<1, 32, 0, s>>>(h->step);
     return launch_status(2);
 }
@@ -805,15 +781,15 @@ extern "C" PE_API int pe_mlp_train(pe_mlp* h, const float* X, const float* Y, in
         return PE_EINVAL;
     const int D = h->dims[0], Dout = h->dims[h->L];
     if (shift_period < 0 || (shift_period > 0 && (D % shift_period || Dout % shift_period))) return PE_EINVAL;
-    if ((Dout / kBN) * ((B + kBM - 1) / kBM) > kLossSlots) return PE_EINVAL;
+    if (loss_tiles(Dout, B) > kLossSlots) return PE_EINVAL;
     cudaStream_t s = h->stream;
     const int nsm = sm_count();  // cached before any capture
     int launches = 0;
     auto one_step = [&]() {
         k_sample_rows<<<(B + 255) / 256, 256, 0, s>>>(seed, h->step, B, npairs, shift_period, h->rows, h->shifts);
         grad_pass(h, X, Y, npairs, h->rows, h->shifts, B, shift_period, &launches);
-        k_adam<<<2 * nsm, 256, 0, s>>>(h->p, h->pb, h->grad, h->am, h->av, h->nparams, h->step, lr, 0.9, 0.999,
-                                       1e-8f);
+        k_adam<<<2 * nsm, 256, 0, s>>>(h->p, h->pb, h->pbT, h->wt, h->grad, h->am, h->av, h->nparams, h->step, lr,
+                                       0.9, 0.999, 1e-8f);
         k_step_advance<<<1, 32, 0, s>>>(h->step);
         launches += 3;
     };
@@ -850,6 +826,16 @@ extern "C" PE_API int pe_mlp_train(pe_mlp* h, const float* X, const float* Y, in
     }
     if (loss && cudaMemcpyAsync(loss, h->loss, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return PE_ECUDA;
     return PE_OK;
+}
+
+extern "C" PE_API int pe_mlp_sync_status(pe_mlp* h)
+{
+    if (!h) return PE_EINVAL;
+    uint32_t st = 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
+    if (cudaMemset(h->status, 0, sizeof(st)) != cudaSuccess) return PE_ECUDA;
+    return (st & PE_FLAG_TIMEOUT) ? PE_ETIMEOUT : PE_OK;
 }
 
 extern "C" PE_API int pe_mlp_info(const pe_mlp* h, int64_t* nparams, int64_t* steps_device_ptr, void** params,
@@ -1027,12 +1013,12 @@ extern "C" PE_API int pe_export_f32(pe_ctx* ctx, int32_t what, float* out)
 namespace pe {
 namespace {
 __global__ void k_set_params(const float* __restrict__ src, int64_t n, float* __restrict__ p,
-                             __nv_bfloat16* __restrict__ pb)
+                             __nv_bfloat16* __restrict__ pb, __nv_bfloat16* __restrict__ pbT, WeightTable wt)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float w = src[i];
         p[i] = w;
-        pb[i] = __float2bfloat16_rn(w);
+        put_bf16(wt, i, w, pb, pbT);
     }
 }
 }  // namespace
@@ -1041,6 +1027,6 @@ __global__ void k_set_params(const float* __restrict__ src, int64_t n, float* __
 extern "C" PE_API int pe_mlp_set_params(pe_mlp* h, const float* params)
 {
     if (!h || !params) return PE_EINVAL;
-    k_set_params<<<2 * sm_count(), 256, 0, h->stream>>>(params, h->nparams, h->p, h->pb);
+    k_set_params<<<2 * sm_count(), 256, 0, h->stream>>>(params, h->nparams, h->p, h->pb, h->pbT, h->wt);
     return launch_status(1);
 }

@@ -52,6 +52,7 @@ struct EpiStoreF32 {
 #pragma unroll
         for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
+    __device__ __forceinline__ void finish() {}
 };
 
 template <int BN>

@@ -167,7 +167,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 // C tile (blockIdx.y, blockIdx.x) of A[M][K] B[N][K]^T; ta / tb: tensor maps of A (dims {K, M},
 // box {64, 128}) and B (dims {K, N}, box {64, BN}), 128-byte swizzle, zero fill beyond the
 // extents (ragged M and K). epi(row, col0, v) receives 32 columns col0.. of one row (the row
-// may be >= M: the functor checks). N % BN == 0.
+// may be >= M: the functor checks); every thread then calls epi.finish() (block-wide
+// reductions of the epilogue). N % BN == 0.
 template <int BN, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int K, Epi epi,
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ok = __all_sync(0xFFFFFFFFu, ok);
     if (!ok && lane == 0) atomicOr(status, PE_FLAG_TIMEOUT);
     tc_fence_after();
+    Epi e = epi;
     if (ok) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
@@ -258,9 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < BN; c += 32) {
             float v[32];
             tmem_ld32(t_row + (uint32_t)c, v);
-            epi(row, n0 + c, v);
+            e(row, n0 + c, v);
         }
     }
+    e.finish();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, BN);

@@ -1,4 +1,4 @@
-"""GPU parity of the learned-surrogate kernels (BF16 tensor-core MLP) and of the gate
+"""GPU parity of the learned-surrogate kernels (BF16 tcgen05 tensor-core MLP) and of the gate
 against the FP64 CPU oracle (oracle/mlp.py), through the C ABI.
 
 Tolerances (BF16 operands, FP32 accumulation):
@@ -47,6 +47,7 @@ def test_init_matches_oracle(dims):
     assert np.array_equal(got, want)
     mirror = net.params_bf16().float().cpu().numpy().astype(np.float64)
     assert np.array_equal(mirror, omlp.bf16_round(want))
+    _check_transposed_mirror(net, dims)
 
 
 @pytest.mark.parametrize("period", [0, 32])
@@ -108,6 +109,18 @@ def test_gradients_match_oracle(dims, B):
             assert rel(got, want) <= 2e-2, l
 
 
+def _check_transposed_mirror(net, dims):
+    # the data-gradient GEMMs read W_l^T: the transposed mirror must hold the mirror's weights
+    m = net.params_bf16().float().cpu().numpy()
+    t = net.params_bf16_transposed().float().cpu().numpy()
+    off = 0
+    for l in range(len(dims) - 1):
+        n = dims[l + 1] * dims[l]
+        W = m[off:off + n].reshape(dims[l + 1], dims[l])
+        assert np.array_equal(t[off:off + n].reshape(dims[l], dims[l + 1]), W.T)
+        off += n + dims[l + 1]
+
+
 def test_adam_matches_oracle():
     dims = [128, 64, 192]
     p = inputs.random_mlp_params(dims, 8)
@@ -126,6 +139,7 @@ def test_adam_matches_oracle():
     gm, gv = (a.cpu().numpy().astype(np.float64) for a in net.adam_state())
     assert np.allclose(gm, m, rtol=1e-5, atol=1e-12) and np.allclose(gv, v, rtol=1e-5, atol=1e-16)
     assert np.array_equal(net.params_bf16().float().cpu().numpy().astype(np.float64), omlp.bf16_round(got))
+    _check_transposed_mirror(net, dims)
 
 
 def test_training_reduces_loss_and_graph_replay_is_deterministic():
@@ -153,6 +167,7 @@ def test_training_reduces_loss_and_graph_replay_is_deterministic():
         b.train(dX, dY, 64, 1, 1e-3, seed=9, shift_period=32)
     s.synchronize()
     assert torch.equal(a.params(), b.params())
+    assert a.sync_status() == 0 and b.sync_status() == 0 and net.sync_status() == 0
 
 
 @pytest.mark.parametrize("Ks,n", [(5, 512), (2, 64), (19, 1000)])
