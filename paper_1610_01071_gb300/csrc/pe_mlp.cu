@@ -312,14 +312,18 @@ __global__ void k_prep(const T* __restrict__ X, const float* __restrict__ Y, int
     }
 }
 
-// Bias gradient db[n] = sum_m G[m][n] (BF16 gradient rows, FP32 sum in row order).
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ G, int M, int N, float* __restrict__ db)
+// Bias gradient db[n] = sum_m G[m][n] from the transposed gradient GT [N][ldT] (row n holds
+// G[0..M)[n] contiguously): one warp per n, lanes over m, FP32 partial sums folded in a
+// fixed order (reproducible).
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ GT, int ldT, int M, int N, float* __restrict__ db)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (n >= N) return;
+    const __nv_bfloat16* row = GT + (size_t)n * ldT;
     float s = 0.0f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(G[(size_t)m * N + n]);
-    db[n] = s;
+    for (int m = lane; m < M; m += 32) s += __bfloat162float(row[m]);
+    s = warp_sum_f(s);
+    if (lane == 0) db[n] = s;
 }
 
 __global__ void k_loss_final(const float* __restrict__ part, int n, float* __restrict__ out, float scale)
@@ -461,10 +465,17 @@ WorkPlan plan_work(int L, const int32_t* dims, int Bm, int dmax)
 // C[M][N] = A[M][K] B[N][K]^T on the tensor cores with the epilogue EPI; A and B stored
 // with K contiguous (row strides lda, ldb). AoutT/ldT: transposed BF16 copy of the output.
 // Returns the number of tiles (one loss partial each).
+// Tile width: 128 columns, or 64 when N needs it or when 128-wide tiles would leave SMs idle.
+int tile_n(int N, int M)
+{
+    if (N % 128 != 0) return 64;
+    return (N / 128) * ((M + tc::kBM - 1) / tc::kBM) < sm_count() ? 64 : 128;
+}
+
 template <int EPI>
 int tc_gemm(pe_mlp* h, const GemmArgs& g, __nv_bfloat16* AoutT, cudaStream_t s, int* tiles)
 {
-    const int bn = (g.N % 128 == 0) ? 128 : 64;
+    const int bn = tile_n(g.N, g.M);
     CUtensorMap ma, mb;
     PE_TRY(tc_operand_map(&ma, g.A, g.M, g.K, g.lda, tc::kBM));
     PE_TRY(tc_operand_map(&mb, g.B, g.N, g.K, g.ldb, bn));
@@ -486,7 +497,7 @@ int tc_gemm(pe_mlp* h, const GemmArgs& g, __nv_bfloat16* AoutT, cudaStream_t s, 
 }
 
 // Loss partials of the output layer's GEMM (one per tile).
-int loss_tiles(int Dout, int B) { return (Dout / ((Dout % 128 == 0) ? 128 : 64)) * ((B + tc::kBM - 1) / tc::kBM); }
+int loss_tiles(int Dout, int B) { return (Dout / tile_n(Dout, B)) * ((B + tc::kBM - 1) / tc::kBM); }
 
 GemmArgs args0() { GemmArgs g; memset(&g, 0, sizeof(g)); return g; }
 
@@ -547,7 +558,8 @@ int backward(pe_mlp* h, int B, int* launches)
         w.ldb = h->ldT;
         w.Y = h->grad + h->w_off[l];
         PE_TRY(tc_gemm<kEpiWgrad>(h, w, nullptr, s, nullptr));
-        k_bias_grad<<<(h->dims[l + 1] + 255) / 256, 256, 0, s>>>(gl, B, h->dims[l + 1], h->grad + h->b_off[l]);
+        k_bias_grad<<<(h->dims[l + 1] + 7) / 8, 256, 0, s>>>(h->gT[l & 1], h->ldT, B, h->dims[l + 1],
+                                                             h->grad + h->b_off[l]);
         *launches += 2;
         if (l == 0) break;
         GemmArgs d = args0();  // G_{l-1} = (G_l W_l) * GELU'(z_{l-1}): W_l read as its transpose
