@@ -932,6 +932,34 @@ def leap_curvature(samples, dt):
     return qn, float(np.sqrt(np.sum(samples[-1] ** 2))), float(np.sqrt(np.sum(var)))
 
 
+def slope_noise(samples, dt):
+    """Norm of the standard errors of the least-squares slopes of a burst's samples
+    [(K+1), ncoef] at t_p = p dt: per component s^2 = (residual sum of squares of the quadratic
+    fit) / (K - 2) and var(slope) = s^2 / sum_p (t_p - tbar)^2; returns sqrt(sum var). K >= 3."""
+    samples = _f64(samples)
+    K = samples.shape[0] - 1
+    t = np.arange(K + 1) * float(dt)
+    coef = np.polyfit(t, samples, 2)
+    fit = np.polyval(coef, t[:, None]) if samples.ndim == 2 else np.polyval(coef, t)
+    rss = np.sum((samples - fit) ** 2, axis=0)
+    tau = t - t.mean()
+    return float(np.sqrt(np.sum(rss / (K - 2) / np.sum(tau * tau))))
+
+
+def burst_length_for_noise(sn, K, leap, cn, tol, K_min, K_max):
+    """Smallest burst length K' in [K_min, K_max] whose slope noise, scaled from the measured
+    sn at K by the least-squares variance law var ~ 1 / (K (K+1) (K+2)), moves a leap of the
+    given length by at most tol relative to cn: leap sn sqrt(K(K+1)(K+2) / (K'(K'+1)(K'+2)))
+    <= tol cn; K_max when none does."""
+    if not (leap > 0 and sn > 0 and cn > 0):
+        return int(K_min)
+    base = float(K) * (K + 1) * (K + 2)
+    for Kp in range(int(K_min), int(K_max) + 1):
+        if leap * sn * np.sqrt(base / (float(Kp) * (Kp + 1) * (Kp + 2))) <= tol * cn:
+            return Kp
+    return int(K_max)
+
+
 def leap_for_tol(qn, cn, Kdt, tol):
     """Leap L >= 0 with qn L (L + K dt) = tol cn (infinite without curvature)."""
     if not qn > 0:

@@ -59,3 +59,27 @@ def test_noise_correction_removes_the_bias_of_the_curvature():
     q = np.full(n, 5.0 * raw / np.sqrt(n))
     qn2, _, _ = orc.leap_curvature(1.0 + np.outer(t * t, q) + noise, dt)
     assert qn2 == pytest.approx(np.linalg.norm(q), rel=0.05)
+
+
+def test_slope_noise_of_white_noise_matches_the_least_squares_law():
+    # samples = a + b t + noise (std sigma) on 4000 components: the estimated slope noise is
+    # sqrt(ncoef 12 sigma^2 / (K (K+1) (K+2) dt^2)) (the variance of a least-squares slope)
+    rng = np.random.default_rng(41)
+    K, dt, sigma, n = 12, 0.1, 0.3, 4000
+    t = np.arange(K + 1) * dt
+    y = 1.0 + 0.5 * t[:, None] + sigma * rng.standard_normal((K + 1, n))
+    want = np.sqrt(n * 12 * sigma ** 2 / (K * (K + 1) * (K + 2) * dt ** 2))
+    assert abs(orc.slope_noise(y, dt) / want - 1) < 0.03
+    # noise-free quadratics have no residual
+    q = 2.0 - 0.3 * t[:, None] + 0.7 * t[:, None] ** 2 * np.ones((1, 5))
+    assert orc.slope_noise(q, dt) < 1e-9
+
+
+def test_burst_length_for_noise_closed_form():
+    # leap sn sqrt(K(K+1)(K+2) / (K'(K'+1)(K'+2))) <= tol cn: with K = 10 (K(K+1)(K+2) = 1320),
+    # leap sn / (tol cn) = 4 needs K'(K'+1)(K'+2) >= 16 * 1320 = 21120: K' = 27 (27*28*29 = 21924;
+    # 26*27*28 = 19656 is short)
+    assert orc.burst_length_for_noise(4.0, 10, 1.0, 1.0, 1.0, 5, 40) == 27
+    assert orc.burst_length_for_noise(4.0, 10, 1.0, 1.0, 1.0, 5, 20) == 20  # capped at K_max
+    assert orc.burst_length_for_noise(0.01, 10, 1.0, 1.0, 1.0, 5, 40) == 5  # quiet: K_min
+    assert orc.burst_length_for_noise(0.0, 10, 1.0, 1.0, 1.0, 5, 40) == 5
