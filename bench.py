@@ -812,10 +812,12 @@ def run_accuracy(dev, cfg, pb):
         ps["speedup_vs_plain_pic"] = t_plain / ps["seconds"]
         ps["eps_at_T_end_below_2pct"] = ps["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
         runs.append(ps)
-    ad = run_phase_space_adaptive(dev, cfg, pb, want, [m for m in checks if m in (steps // 5, steps)])
-    ad["speedup_vs_plain_pic"] = t_plain / ad["seconds"]
-    ad["eps_at_T_end_below_2pct"] = ad["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
-    runs.append(ad)
+    for kk in ((0, 0, 8), (5, cfg["K"], 32)):  # adaptive Delta t; adaptive Delta t and burst length
+        ad = run_phase_space_adaptive(dev, cfg, pb, want, [m for m in checks if m in (steps // 5, steps)],
+                                      K_min=kk[0], K_max=kk[1], M_max=kk[2])
+        ad["speedup_vs_plain_pic"] = t_plain / ad["seconds"]
+        ad["eps_at_T_end_below_2pct"] = ad["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
+        runs.append(ad)
     out["phase_space"] = runs
     return out, want, checks
 
@@ -874,7 +876,7 @@ def run_phase_space(dev, cfg, pb, want, checks, dT=8.0, n_v=64, v_max=8.0, ps_fi
             "status": ctx.sync_status()}
 
 
-def run_phase_space_adaptive(dev, cfg, pb, want, checks, tol=1e-2, M_max=8, K=None):
+def run_phase_space_adaptive(dev, cfg, pb, want, checks, tol=1e-2, M_max=8, K=None, K_min=0, K_max=0):
     """The phase-space run with the curvature-controlled macro step (pe_step_adaptive): Delta t
     in whole bursts of K steps between K dt and M_max K dt, landing on the check times; timed to
     the end time and compared with the resolved states `want` as run_phase_space does."""
@@ -891,7 +893,7 @@ def run_phase_space_adaptive(dev, cfg, pb, want, checks, tol=1e-2, M_max=8, K=No
     b = int(np.log2(ncell // nc))
     scale = 2.0 ** (-(np.log2(ncell) + b) / 2)
     got, t, wall, steps, rejected, dT_next = {}, 0.0, 0.0, 0, 0, 4 * Kdt
-    dts = []
+    dts, Ks = [], []
     for m in checks:
         T = m * cfg["dT"]
         torch.cuda.synchronize(dev)
@@ -899,18 +901,20 @@ def run_phase_space_adaptive(dev, cfg, pb, want, checks, tol=1e-2, M_max=8, K=No
         while t < T - 1e-9:
             if dT_next > T - t + 1e-9:  # land on the check time (a whole number of bursts away)
                 ctx.set_macro_step(T - t)
-            st = ctx.step_adaptive(tol=tol, M_min=1, M_max=M_max, safety=0.8, grow=2.0)
+            st = ctx.step_adaptive(tol=tol, M_min=1, M_max=M_max, safety=0.8, grow=2.0, K_min=K_min, K_max=K_max)
             t += st["dT"]
             dT_next = st["dT_next"]
             steps += 1
             rejected += st["rejected"]
             dts.append(st["dT"])
+            Ks.append(st["K"])
         torch.cuda.synchronize(dev)
         wall += time.perf_counter() - t0
         got[m] = (ctx.get_coarse().sum(1) * scale).cpu().numpy()
     eps = {str(round(m * cfg["dT"])): _eps(got[m], want[m].cpu().numpy()) for m in checks}
     T_end = cfg["macro_steps"] * cfg["dT"]
-    return {"dT": "adaptive", "tol": tol, "K": K, "M_max": M_max, "T_end": T_end, "seconds": wall,
+    return {"dT": "adaptive", "tol": tol, "K": K if not K_max else "adaptive %d..%d" % (K_min, K_max),
+            "mean_K": float(np.mean(Ks)), "M_max": M_max, "T_end": T_end, "seconds": wall,
             "macro_steps": steps, "rejected": rejected, "mean_dT": float(np.mean(dts)), "max_dT": float(np.max(dts)),
             "sim_time_per_wall_s": T_end / wall, "eps_coarse_density_at_T": eps, "status": ctx.sync_status()}
 

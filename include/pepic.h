@@ -921,11 +921,13 @@ PE_API int pe_gate(const double* samples, int32_t K_probe, int32_t ncoef, double
  * a burst's samples[(K+1)][ncoef] at t_p = p dt (c ~ a + b t + q t^2) and its sampling
  * variance var_i (the fit's residual variance, K - 2 degrees of freedom, over the sum of the
  * squared quadratic basis); out[0] = sqrt(max(0, ||q||^2 - sum var_i)), the curvature with the
- * particle noise's bias removed, out[1] = ||c_K||_2, out[2] = sqrt(sum var_i) (device,
- * double[3]). On a quadratic trajectory the least-squares slope is the derivative at the
- * burst's midpoint, so the forward-Euler leap of length L from c_K errs by exactly
- * q L (L + K dt): e(L) = out[0] L (L + K dt) / out[1] estimates the relative error of a leap.
- * K >= 2 (K = 2 leaves no residual: no noise correction). scratch: device, double[3 * 1024]
+ * particle noise's bias removed, out[1] = ||c_K||_2, out[2] = sqrt(sum var_i), out[3] =
+ * sqrt(sum s_i^2 / sum_p (t_p - tbar)^2) the norm of the least-squares slopes' standard errors
+ * (s_i^2 the same residual variance) (device, double[4]). On a quadratic trajectory the
+ * least-squares slope is the derivative at the burst's midpoint, so the forward-Euler leap of
+ * length L from c_K errs by exactly q L (L + K dt): e(L) = out[0] L (L + K dt) / out[1]
+ * estimates the relative error of a leap, and L out[3] / out[1] the part the slope's noise
+ * adds. K >= 2 (K = 2 leaves no residual: no noise terms). scratch: device, double[4 * 1024]
  * (per-block partial sums). Every sum in a fixed order: repeated calls give identical bits. */
 PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, double dt, double* scratch,
                              double* out, void* stream);
@@ -937,13 +939,22 @@ PE_API int pe_leap_curvature(const double* samples, int32_t K, int32_t ncoef, do
  * coarse state is lifted again (same seed) and the step rerun with the M of the tolerance
  * (at most M - 1). Otherwise the step is projected, and the next step takes
  * M = floor((K dt + safety L_tol) / (K dt)) bursts, L_tol the leap with e(L_tol) = tol,
- * clamped to [M_min, min(M_max, floor(grow M))]. Synchronises once per burst (the decision). */
+ * clamped to [M_min, min(M_max, floor(grow M))]. Synchronises once per burst (the decision).
+ * Adaptive burst length (K_max > 0): the burst length K itself (at most the configured K,
+ * which sizes the sample buffers) is chosen for the next step as the smallest K' in
+ * [K_min, K_max] whose slope noise, scaled from the measured out[3] at K by the least-squares
+ * law var ~ 1 / (K (K+1) (K+2)), moves the leap just taken by at most noise_frac tol relative to
+ * ||c_K||; the next Delta t is then M' K' dt with M' from the curvature rule in units of K' dt.
+ * K_max = 0 keeps the burst length. */
 typedef struct pe_adapt_cfg {
     double tol;      /* bound on the estimated relative error of one leap, e.g. 1e-4 */
     int32_t M_min;   /* smallest macro step in bursts (>= 1; 1 means no leap) */
     int32_t M_max;   /* largest macro step in bursts */
     double safety;   /* fraction of L_tol taken for the next step, in (0, 1] */
     double grow;     /* the next M is at most grow times the current one (>= 1) */
+    int32_t K_min;   /* adaptive burst length: shortest burst (>= 3) */
+    int32_t K_max;   /* adaptive burst length: longest burst (<= the configured K); 0: fixed K */
+    double noise_frac; /* share of tol granted to the slope noise (in (0, 1]; 0 means 0.5) */
 } pe_adapt_cfg;
 typedef struct pe_adapt_stats {
     double dT;        /* the macro step taken */
@@ -951,10 +962,14 @@ typedef struct pe_adapt_stats {
     double dT_next;   /* the next macro step */
     int32_t rejected; /* bursts rejected and rerun in this step */
     int32_t fine_steps; /* fine steps run in this step */
+    double noise;     /* the slope noise's estimated relative effect on the leap taken */
+    int32_t K;        /* the burst length of this step */
+    int32_t K_next;   /* the burst length of the next step */
 } pe_adapt_stats;
 PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* cfg, pe_adapt_stats* out);
-/* Delta t of the next macro steps (>= K dt); the configured dT until set. Bursts, projections,
- * pe_step and pe_step_surrogate use it; a batch refuses contexts whose Delta t was changed. */
+/* Delta t of the next macro steps (>= K dt, K the current burst length); the configured dT until
+ * set. Bursts, projections, pe_step and pe_step_surrogate use it; a batch refuses contexts whose
+ * Delta t or burst length was changed. */
 PE_API int pe_set_macro_step(pe_ctx* ctx, double dT);
 
 /* FP32 copy of the coarse state (what = 0) or of the last slope (what = 1) into out[2 n_coarse]

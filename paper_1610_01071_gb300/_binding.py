@@ -103,12 +103,14 @@ class GateStats(ctypes.Structure):
 
 class AdaptCfg(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("M_min", ctypes.c_int32), ("M_max", ctypes.c_int32),
-                ("safety", ctypes.c_double), ("grow", ctypes.c_double)]
+                ("safety", ctypes.c_double), ("grow", ctypes.c_double), ("K_min", ctypes.c_int32),
+                ("K_max", ctypes.c_int32), ("noise_frac", ctypes.c_double)]
 
 
 class AdaptStats(ctypes.Structure):
     _fields_ = [("dT", ctypes.c_double), ("err", ctypes.c_double), ("dT_next", ctypes.c_double),
-                ("rejected", ctypes.c_int32), ("fine_steps", ctypes.c_int32)]
+                ("rejected", ctypes.c_int32), ("fine_steps", ctypes.c_int32), ("noise", ctypes.c_double),
+                ("K", ctypes.c_int32), ("K_next", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -304,11 +306,11 @@ def ps_mean_velocity(cdf, v_min, dv, bin_shift, ncell, stream=None):
 
 
 def leap_curvature(samples, dt, stream=None):
-    """(noise-corrected ||q||, ||c_K||, noise of q) of coarse samples [(K+1), ncoef]
-    (pe_leap_curvature), as a device tensor."""
+    """(noise-corrected ||q||, ||c_K||, noise of q, noise of the least-squares slope) of coarse
+    samples [(K+1), ncoef] (pe_leap_curvature), as a device tensor."""
     K1, n = samples.shape
-    out = torch.empty(3, dtype=torch.float64, device=samples.device)
-    scratch = torch.empty(3 * 1024, dtype=torch.float64, device=samples.device)
+    out = torch.empty(4, dtype=torch.float64, device=samples.device)
+    scratch = torch.empty(4 * 1024, dtype=torch.float64, device=samples.device)
     check(load().pe_leap_curvature(_ptr(samples), K1 - 1, n, float(dt), _ptr(scratch), _ptr(out), _stream(stream)),
           "pe_leap_curvature")
     return out
@@ -730,9 +732,12 @@ class Context:
         self._call("pe_step_surrogate", net._h, ctypes.byref(g), ctypes.byref(st))
         return st.as_dict()
 
-    def step_adaptive(self, tol=1e-4, M_min=1, M_max=16, safety=0.8, grow=2.0) -> dict:
-        """Macro step with the curvature-controlled Delta t (pe_step_adaptive); returns its statistics."""
-        a = AdaptCfg(float(tol), int(M_min), int(M_max), float(safety), float(grow))
+    def step_adaptive(self, tol=1e-4, M_min=1, M_max=16, safety=0.8, grow=2.0, K_min=0, K_max=0,
+                      noise_frac=0.5) -> dict:
+        """Macro step with the curvature-controlled Delta t (pe_step_adaptive) and, with K_max > 0,
+        the noise-controlled burst length; returns its statistics."""
+        a = AdaptCfg(float(tol), int(M_min), int(M_max), float(safety), float(grow), int(K_min), int(K_max),
+                     float(noise_frac))
         st = AdaptStats()
         self._call("pe_step_adaptive", ctypes.byref(a), ctypes.byref(st))
         return st.as_dict()

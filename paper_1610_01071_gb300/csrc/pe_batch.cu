@@ -489,7 +489,7 @@ extern "C" PE_API int pe_batch_step(pe_batch* b)
         pe_ctx* x = b->ctx[r];
         if ((x->fresh != 0) != fresh) return PE_ESTATE;  // all realisations must be in the same state
         if (x->bank != b->banks[r]) return PE_ESTATE;      // particles moved banks (plain PIC sort)
-        if (x->dT_cur != x->cfg.dT) return PE_ESTATE;     // the ensemble steps by the configured Delta t
+        if (x->dT_cur != x->cfg.dT || x->K_cur != x->cfg.K) return PE_ESTATE;  // the configured step and burst
     }
     // The batch stream waits for work already queued on the contexts' streams.
     for (int r = 0; r < R; ++r) {

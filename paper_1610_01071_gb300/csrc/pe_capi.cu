@@ -225,6 +225,7 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->stream = (cudaStream_t)stream;
     x->dx = cfg->L / cfg->ncell;
     x->dT_cur = cfg->dT;
+    x->K_cur = cfg->K;
     x->nc = cfg->n_coarse;
     x->ps = cfg->coarse_kind == PE_COARSE_PHASE_SPACE;
     x->psw = x->ps && cfg->n_v_coarse > 0;
@@ -658,7 +659,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
 int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
 {
     const pe_config& c = x->cfg;
-    if (p_begin < 0 || p_end < p_begin || p_end > c.K) return PE_EINVAL;
+    if (p_begin < 0 || p_end < p_begin || p_end > x->K_cur) return PE_EINVAL;
     const int b = x->bank;
     if (p_begin == 0) {
         if (!x->rho_valid) PE_TRY(deposit_current(x));
@@ -699,7 +700,7 @@ extern "C" PE_API int pe_burst(pe_ctx* ctx)
 {
     NvtxRange nvtx("pe_burst");
     if (!ctx) return PE_EINVAL;
-    return pe_ctx_burst_range(ctx, 0, ctx->cfg.K, 1);
+    return pe_ctx_burst_range(ctx, 0, ctx->K_cur, 1);
 }
 
 extern "C" PE_API int pe_restrict(pe_ctx* ctx)
@@ -708,10 +709,10 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
     if (!ctx) return PE_EINVAL;
     const pe_config& c = ctx->cfg;
     if (ctx->psw)  // rows of consecutive samples are contiguous: [K+1][n_coarse][n_vf] -> [K+1][n_coarse][n_vc]
-        return pe_ps_coarsen_v(ctx->samples, (int64_t)(c.K + 1) * ctx->nc, ctx->nv, ctx->s_w, ctx->bin_shift, c.wavelet,
-                               ctx->nvc, ctx->csamples, ctx->stream);
-    if (ctx->ps) return pe_ps_coarsen(ctx->samples, c.K + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
-    return pe_coarsen(ctx->samples, c.K + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
+        return pe_ps_coarsen_v(ctx->samples, (int64_t)(ctx->K_cur + 1) * ctx->nc, ctx->nv, ctx->s_w, ctx->bin_shift,
+                               c.wavelet, ctx->nvc, ctx->csamples, ctx->stream);
+    if (ctx->ps) return pe_ps_coarsen(ctx->samples, ctx->K_cur + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
+    return pe_coarsen(ctx->samples, ctx->K_cur + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
                       ctx->csamples, ctx->stream);
 }
 
@@ -723,10 +724,11 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
     if (ctx->ps && c.ps_filter) {
         double* work = ctx->csamples + (size_t)(c.K + 1) * (size_t)ctx->crow;  // measurement row as scratch
         const int filt = c.ps_filter | ((ctx->walls && (c.ps_filter & 2)) ? 4 : 0);  // reflecting x at walls
-        PE_TRY(pe_ps_project(ctx->csamples, c.K, ctx->nc, ctx->nv, c.dt, ctx->dT_cur, filt, work, ctx->coarse, ctx->slope,
+        PE_TRY(pe_ps_project(ctx->csamples, ctx->K_cur, ctx->nc, ctx->nv, c.dt, ctx->dT_cur, filt, work, ctx->coarse,
+                             ctx->slope,
                              ctx->stream));
     } else {
-        PE_TRY(pe_ls_project(ctx->csamples, c.K, (int32_t)ctx->ncoef, c.dt, ctx->dT_cur, ctx->coarse, ctx->slope,
+        PE_TRY(pe_ls_project(ctx->csamples, ctx->K_cur, (int32_t)ctx->ncoef, c.dt, ctx->dT_cur, ctx->coarse, ctx->slope,
                              ctx->stream));
     }
     ctx->macro_steps += 1;
@@ -799,7 +801,7 @@ extern "C" PE_API int pe_step(pe_ctx* ctx)
 
 extern "C" PE_API int pe_set_macro_step(pe_ctx* ctx, double dT)
 {
-    if (!ctx || !(dT >= ctx->cfg.K * ctx->cfg.dt * (1.0 - 1e-12)) || !(dT < 1e300)) return PE_EINVAL;
+    if (!ctx || !(dT >= ctx->K_cur * ctx->cfg.dt * (1.0 - 1e-12)) || !(dT < 1e300)) return PE_EINVAL;
     ctx->dT_cur = dT;
     return PE_OK;
 }
@@ -813,6 +815,18 @@ static double leap_for_tol(double qn, double cn, double Kdt, double tol)
     return 0.5 * (-Kdt + sqrt(Kdt * Kdt + 4.0 * r));
 }
 
+// Smallest burst length K' in [K_min, K_max] whose least-squares slope noise, scaled from the
+// measured sn at K by var ~ 1 / (K (K+1) (K+2)), moves a leap of length L by at most
+// tol_noise relative to cn; K_max when none does.
+static int burst_length_for_noise(double sn, int K, double L, double cn, double tol_noise, int K_min, int K_max)
+{
+    if (!(L > 0.0) || !(sn > 0.0) || !(cn > 0.0)) return K_min;
+    const double base = (double)K * (K + 1) * (K + 2);
+    for (int Kp = K_min; Kp <= K_max; ++Kp)
+        if (L * sn * sqrt(base / ((double)Kp * (Kp + 1) * (Kp + 2))) <= tol_noise * cn) return Kp;
+    return K_max;
+}
+
 extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_adapt_stats* out)
 {
     NvtxRange nvtx("pe_step_adaptive");
@@ -821,23 +835,29 @@ extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_ad
         return PE_EINVAL;
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
-    if (c.K < 2) return PE_EINVAL;
-    const double Kdt = c.K * c.dt;
+    const bool adapt_K = a->K_max > 0;
+    if (adapt_K && (a->K_min < 3 || a->K_max < a->K_min || a->K_max > c.K || !(a->noise_frac >= 0.0) ||
+                    !(a->noise_frac <= 1.0)))
+        return PE_EINVAL;
+    if (x->K_cur < 2) return PE_EINVAL;
+    if (adapt_K) x->K_cur = std::min(a->K_max, std::max(a->K_min, x->K_cur));
+    const double noise_frac = a->noise_frac > 0.0 ? a->noise_frac : 0.5;
+    const int K = x->K_cur;
+    const double Kdt = K * c.dt;
     auto bursts = [&](double dT) { return std::max(1, (int)floor(dT / Kdt + 1e-9)); };
     int M = std::min(a->M_max, std::max(a->M_min, bursts(x->dT_cur)));
-    // the moments scratch (64 KB) is free here: partial sums, then the three results
+    // the moments scratch (64 KB) is free here: partial sums, then the four results
     double* part = (double*)(x->arena + x->lay.offset[PE_BUF_DIAG]);
-    double* qc = part + 3 * 1024;
+    double* qc = part + 4 * 1024;
     const int64_t f0 = x->fine_steps;
     int rejected = 0;
-    double err = 0.0, L_tol = 0.0;
+    double err = 0.0, L_tol = 0.0, h[4] = {0.0, 0.0, 0.0, 0.0};
     for (;;) {
         x->dT_cur = M * Kdt;
         if (!x->fresh) PE_TRY(pe_lift(x));
         PE_TRY(pe_burst(x));
         PE_TRY(pe_restrict(x));
-        PE_TRY(pe_leap_curvature(x->csamples, c.K, (int32_t)x->ncoef, c.dt, part, qc, x->stream));
-        double h[3];
+        PE_TRY(pe_leap_curvature(x->csamples, K, (int32_t)x->ncoef, c.dt, part, qc, x->stream));
         if (cudaMemcpyAsync(h, qc, sizeof(h), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess) return PE_ECUDA;
         if (cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
         const double L = x->dT_cur - Kdt;
@@ -852,17 +872,27 @@ extern "C" PE_API int pe_step_adaptive(pe_ctx* ctx, const pe_adapt_cfg* a, pe_ad
         break;
     }
     const double taken = x->dT_cur;
+    const double L_taken = taken - Kdt;
     PE_TRY(pe_project(x));
-    const double Mn = isinf(L_tol) ? (double)a->M_max : floor((Kdt + a->safety * L_tol) / Kdt + 1e-9);
-    const double cap = std::min((double)a->M_max, floor(a->grow * M + 1e-9));
+    int K_next = K;
+    if (adapt_K) K_next = burst_length_for_noise(h[3], K, L_taken, h[1], noise_frac * a->tol, a->K_min, a->K_max);
+    // the next macro step in whole bursts of the next burst length: the leap allowed by the
+    // curvature (L_tol, measured with bursts of K), capped by growth of the current Delta t
+    const double Kdt_n = K_next * c.dt;
+    const double Mn = isinf(L_tol) ? (double)a->M_max : floor((Kdt_n + a->safety * L_tol) / Kdt_n + 1e-9);
+    const double cap = std::min((double)a->M_max, floor(a->grow * taken / Kdt_n + 1e-9));
     const int M_next = (int)std::max((double)a->M_min, std::min(cap, Mn));
-    x->dT_cur = M_next * Kdt;
+    x->K_cur = K_next;
+    x->dT_cur = M_next * Kdt_n;
     if (out) {
         out->dT = taken;
         out->err = err;
         out->dT_next = x->dT_cur;
         out->rejected = rejected;
         out->fine_steps = (int32_t)(x->fine_steps - f0);
+        out->noise = h[1] > 0.0 ? L_taken * h[3] / h[1] : 0.0;
+        out->K = K;
+        out->K_next = K_next;
     }
     return PE_OK;
 }
@@ -951,6 +981,7 @@ struct CheckpointHeader {
     int64_t ncoef, macro_steps, fine_steps;
     double time, dT_cur;
     pe_config cfg;  // a restore needs the same configuration, byte for byte
+    int32_t K_cur, pad;  // burst length of the next bursts
 };
 constexpr uint32_t kCheckpointMagic = 0x50455043u;  // "PEPC"
 
@@ -972,7 +1003,7 @@ extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t byt
     CheckpointHeader h;
     memset(&h, 0, sizeof(h));
     h.magic = kCheckpointMagic;
-    h.version = 1u;
+    h.version = 2u;
     h.ncell = x->cfg.ncell;
     h.phi_hist = x->phi_hist;
     h.ncoef = x->ncoef;
@@ -981,6 +1012,7 @@ extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t byt
     h.time = x->time;
     h.dT_cur = x->dT_cur;
     h.cfg = x->cfg;
+    h.K_cur = x->K_cur;
     char* p = (char*)host_buf;
     memcpy(p, &h, sizeof(h));
     double* d = (double*)(p + sizeof(h));
@@ -1001,9 +1033,9 @@ extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, s
     pe_ctx* x = ctx;
     CheckpointHeader h;
     memcpy(&h, host_buf, sizeof(h));
-    if (h.magic != kCheckpointMagic || h.version != 1u || h.ncell != x->cfg.ncell || h.ncoef != x->ncoef ||
-        h.macro_steps < 1 || !(h.dT_cur >= x->cfg.K * x->cfg.dt * (1.0 - 1e-12)) || !(h.dT_cur < 1e300) ||
-        memcmp(&h.cfg, &x->cfg, sizeof(pe_config)) != 0)
+    if (h.magic != kCheckpointMagic || h.version != 2u || h.ncell != x->cfg.ncell || h.ncoef != x->ncoef ||
+        h.macro_steps < 1 || h.K_cur < 1 || h.K_cur > x->cfg.K || !(h.dT_cur >= h.K_cur * x->cfg.dt * (1.0 - 1e-12)) ||
+        !(h.dT_cur < 1e300) || memcmp(&h.cfg, &x->cfg, sizeof(pe_config)) != 0)
         return PE_EINVAL;
     // the clock and the Newton history drive the lifting seed, the sort and reset cadence and
     // the first solve: a header that passes the checks above but carries an impossible clock
@@ -1022,6 +1054,7 @@ extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, s
     x->fine_steps = h.fine_steps;
     x->time = h.time;
     x->dT_cur = h.dT_cur;
+    x->K_cur = h.K_cur;
     x->phi_hist = h.phi_hist;
     x->fresh = 0;  // the next step lifts from the restored coarse state
     x->coarse_state = 1;

@@ -468,10 +468,12 @@ int launch_restrict_project_batch(const void* descs, int R, int K, double dt, do
 // (m2 the mean of tau^2; the three are orthogonal on the symmetric points):
 // q_i = sum_p g_p c_p,i / G with G = sum_p g_p^2, and its sampling variance
 // var_i = s_i^2 / G, s_i^2 the residual variance of the fit (K - 2 degrees of freedom).
-// Block b sums q_i^2, c_K,i^2 and var_i over its components (a fixed grid-stride partition)
-// into part[3 b ..]; the final block adds the partial sums in block order:
+// Block b sums q_i^2, c_K,i^2, var_i and s_i^2 / T2 (the variance of the least-squares slope,
+// T2 = sum_p (t_p - tbar)^2) over its components (a fixed grid-stride partition) into
+// part[4 b ..]; the final block adds the partial sums in block order:
 // out[0] = sqrt(max(0, sum q_i^2 - sum var_i)) (the curvature with the noise's bias removed),
-// out[1] = ||c_K||_2, out[2] = sqrt(sum var_i). The FP64 work is spread over the SMs.
+// out[1] = ||c_K||_2, out[2] = sqrt(sum var_i), out[3] = sqrt(sum s_i^2 / T2) (the slope noise).
+// The FP64 work is spread over the SMs.
 constexpr int kCurvThreads = 256;
 constexpr int kCurvMaxBlocks = 1024;
 
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(kCurvThreads) k_leap_curvature_part(const doub
         G += g * g;
         T2 += tp * tp;
     }
-    double qq = 0.0, cc = 0.0, vv = 0.0;
+    double qq = 0.0, cc = 0.0, vv = 0.0, ss = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double a = 0.0, b = 0.0, q = 0.0;
         for (int p = 0; p <= K; ++p) {
@@ -508,29 +510,34 @@ __global__ void __launch_bounds__(kCurvThreads) k_leap_curvature_part(const doub
         qq += q * q;
         cc += cK * cK;
         vv += K > 2 ? rr / (K - 2) / G : 0.0;
+        ss += K > 2 ? rr / (K - 2) / T2 : 0.0;
     }
     qq = block_sum_d(qq, red);
     cc = block_sum_d(cc, red);
     vv = block_sum_d(vv, red);
+    ss = block_sum_d(ss, red);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = qq;
-        part[3 * blockIdx.x + 1] = cc;
-        part[3 * blockIdx.x + 2] = vv;
+        part[4 * blockIdx.x] = qq;
+        part[4 * blockIdx.x + 1] = cc;
+        part[4 * blockIdx.x + 2] = vv;
+        part[4 * blockIdx.x + 3] = ss;
     }
 }
 
 __global__ void k_leap_curvature_final(const double* __restrict__ part, int nb, double* __restrict__ out)
 {
     if (threadIdx.x != 0) return;
-    double qq = 0.0, cc = 0.0, vv = 0.0;
+    double qq = 0.0, cc = 0.0, vv = 0.0, ss = 0.0;
     for (int b = 0; b < nb; ++b) {
-        qq += part[3 * b];
-        cc += part[3 * b + 1];
-        vv += part[3 * b + 2];
+        qq += part[4 * b];
+        cc += part[4 * b + 1];
+        vv += part[4 * b + 2];
+        ss += part[4 * b + 3];
     }
     out[0] = sqrt(fmax(0.0, qq - vv));
     out[1] = sqrt(cc);
     out[2] = sqrt(vv);
+    out[3] = sqrt(ss);
 }
 
 }  // namespace pe

@@ -24,6 +24,7 @@ struct pe_ctx {
     int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
     int nb;              // sample length per moment: ncell >> bin_shift
     int ps;              // phase-space coarse variable (PE_COARSE_PHASE_SPACE)
+    int K_cur;           // burst length of the next bursts (the configured K unless adapted)
     int nv;              // velocity cells (phase space; the fine cells n_vf of the wavelet form)
     int psw;             // phase space, wavelet form: hat rows in x, DWT in v to nvc coefficients
     int nvc;             // wavelet form: velocity coefficients per coarse node

@@ -961,7 +961,8 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     const pe_config& c = x->cfg;
     const int n = 2 * x->nc, Ks = gc->K_probe;
     if (x->ps) return PE_EINVAL;  // the surrogate maps the density and momentum coefficients
-    if (h->dims[0] != n || h->dims[h->L] != n || Ks < 2 || Ks >= c.K || !(gc->tol >= 0.0) || !(gc->noise_sigmas >= 0.0))
+    if (h->dims[0] != n || h->dims[h->L] != n || Ks < 2 || Ks >= x->K_cur || !(gc->tol >= 0.0) ||
+        !(gc->noise_sigmas >= 0.0))
         return PE_EINVAL;
     char* buf = x->arena + x->lay.offset[PE_BUF_SURROGATE];
     double* s_mlp = (double*)buf;
@@ -996,8 +997,8 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
         x->fresh = 0;
         return PE_OK;
     }
-    out->fine_steps = c.K;
-    PE_TRY(pe_ctx_burst_range(x, Ks, c.K, 1));
+    out->fine_steps = x->K_cur;
+    PE_TRY(pe_ctx_burst_range(x, Ks, x->K_cur, 1));
     PE_TRY(pe_restrict(x));
     return pe_project(x);
 }

@@ -24,6 +24,8 @@ def test_leap_curvature_matches_oracle(K, n):
     assert got[1] == pytest.approx(cn, rel=1e-12)
     assert got[2] == pytest.approx(nz, rel=1e-9)
     assert got[0] == pytest.approx(qn, rel=1e-9)
+    if K > 2:
+        assert got[3] == pytest.approx(orc.slope_noise(samples, dt), rel=1e-9)
 
 
 def make(seed=3, coarse="moments", dT_bursts=4, v_th=1.0):
@@ -81,3 +83,39 @@ def test_set_macro_step_and_batches():
     with pytest.raises(pe.PepicError):  # the ensemble steps by the configured Delta t only
         b = pe.Batch([ctx])
         b.step()
+
+
+@pytest.mark.parametrize("expect", ["long", "short"])
+def test_adaptive_burst_length_follows_the_noise_rule(expect):
+    """Adaptive burst length: every step's K and the next K lie in [K_min, K_max]; the next K is
+    the oracle rule applied to the step's reported slope noise; Delta t stays a whole number of
+    bursts of the current length. With the tolerance a hundredth of the measured noise effect
+    K goes to K_max, with a thousand times it to K_min."""
+    ctx, Kdt = make(dT_bursts=3)
+    dt, K_min, K_max = 0.1, 4, 10
+    probe = ctx.step_adaptive(tol=1.0, M_min=2, M_max=6)  # fixed K: the noise effect of a 2-burst leap
+    assert probe["K"] == 10 and probe["K_next"] == 10 and probe["noise"] > 0
+    tol = probe["noise"] * (1e-2 if expect == "long" else 1e3)
+    for _ in range(5):
+        st = ctx.step_adaptive(tol=tol, M_min=2, M_max=6, K_min=K_min, K_max=K_max, noise_frac=0.5)
+        K = st["K"]
+        assert K_min <= K <= K_max and K_min <= st["K_next"] <= K_max
+        assert st["fine_steps"] == K * (1 + st["rejected"])
+        M = st["dT"] / (K * dt)
+        assert abs(M - round(M)) < 1e-9
+        Mn = st["dT_next"] / (st["K_next"] * dt)
+        assert abs(Mn - round(Mn)) < 1e-9
+        L = st["dT"] - K * dt
+        if L > 0 and st["noise"] > 0:
+            want = orc.burst_length_for_noise(st["noise"] / L, K, L, 1.0, 0.5 * tol, K_min, K_max)
+            assert st["K_next"] == want
+    assert ctx.sync_status() == 0
+    assert st["K_next"] == (K_max if expect == "long" else K_min)
+    # a checkpoint keeps the adapted burst length
+    img = ctx.checkpoint()
+    ctx2, _ = make(dT_bursts=3)
+    ctx2.restore(img)
+    a = ctx.step_adaptive(tol=tol, M_min=2, M_max=6, K_min=K_min, K_max=K_max)
+    b = ctx2.step_adaptive(tol=tol, M_min=2, M_max=6, K_min=K_min, K_max=K_max)
+    assert a["K"] == b["K"] and a["dT"] == b["dT"]
+    assert torch.equal(ctx.get_coarse(), ctx2.get_coarse())
