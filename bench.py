@@ -50,12 +50,13 @@ KERNEL_BYTES = {
 # summarised in profiles/, each valid while the particle kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
 NCU_TRAFFIC = {
-    "push_sample": {"source_hash": "036e486a153bb58d", "bytes": 270.727680e6 + 145.672704e6},
-    "push": {"source_hash": "036e486a153bb58d", "bytes": 270.705664e6 + 146.097152e6},
-    "sample": {"source_hash": "036e486a153bb58d", "bytes": 270.664448e6 + 3.045376e6},
-    "deposit": {"source_hash": "036e486a153bb58d", "bytes": 203.015680e6 + 3.054848e6},
-    "push_sample_ps": {"source_hash": "036e486a153bb58d", "bytes": 270.333440e6 + 145.685760e6},
-    "load": {"source_hash": "036e486a153bb58d", "bytes": 0.532224e6 + 207.352576e6},
+    "push_sample": {"source_hash": "2b55b1873f4a669a", "bytes": 270.730240e6 + 145.224192e6},
+    "push": {"source_hash": "2b55b1873f4a669a", "bytes": 270.726400e6 + 145.909248e6},
+    "sample": {"source_hash": "2b55b1873f4a669a", "bytes": 270.670080e6 + 3.041280e6},
+    "deposit": {"source_hash": "2b55b1873f4a669a", "bytes": 203.019520e6 + 3.031552e6},
+    "push_sample_ps": {"source_hash": "2b55b1873f4a669a", "bytes": 270.273792e6 + 145.716224e6},
+    "push_sample_psw": {"source_hash": "2b55b1873f4a669a", "bytes": 270.489088e6 + 145.959168e6},
+    "load": {"source_hash": "2b55b1873f4a669a", "bytes": 0.526848e6 + 207.284480e6},
 }
 
 
@@ -656,6 +657,8 @@ def run_kernel(args):
         return 0
     if args.kernel == "kinetic":
         return run_kernel_kinetic(args)
+    if args.kernel == "tc_gemm":
+        return run_kernel_tc_gemm(args)
 
     from paper_1610_01071_gb300 import _binding as pb
     from paper_1610_01071_gb300 import _build
@@ -742,6 +745,36 @@ def run_kernel(args):
     gbs = bytes_per[args.kernel] * N / (us * 1e-6) / 1e9
     print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us, "algorithmic_GBps": gbs,
                       "status": int(status.item())}), flush=True)
+    return 0
+
+
+def run_kernel_tc_gemm(args):
+    """The surrogate's tensor-core product alone: C = A B^T for BF16 A [2048, 512], B [512, 512]
+    (one forward layer of a training batch), timed with CUDA events over --steps launches."""
+    import torch
+
+    from paper_1610_01071_gb300 import _binding as pb
+    from paper_1610_01071_gb300 import _build
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device="cpu").manual_seed(3)
+    M, N, K = 2048, 512, 512
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16).to(dev)
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16).to(dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        pb.tc_gemm(A, B, status=status)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pb.tc_gemm(A, B, status=status)
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel": "tc_gemm", "M": M, "N": N, "K": K, "launch_us": us,
+                      "TFLOPs": 2.0 * M * N * K / (us * 1e-6) / 1e12, "status": int(status.item())}), flush=True)
     return 0
 
 
