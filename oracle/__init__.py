@@ -891,6 +891,29 @@ def boltzmann_electrons(N, ncell, phi, v_th_e, seed, u=None, ions: State = None)
     return State(cell, theta, v, w)
 
 
+def electron_kinetic_energy(electrons: State, E, ncell, dx, dt, qm_e, kick):
+    """The electrons' total kinetic energy sum w Vbar^2 dx / 2 at integer time (Vbar = v +
+    (kick - 1/2) qm_e dt E(X)): the global active variable of Section 4.2's runs."""
+    return moments(electrons, E, np.zeros(ncell), ncell, dx, dt, qm_e, kick, 0, mode=1)["kinetic"]
+
+
+def lift_electron_temperature(we_proj, we_ref):
+    """T_e / T_e0 at a lift from the projected electron kinetic energy we_proj and the energy
+    we_ref of the same electrons at T_e0 (the initial load); the electrons' drift energy, a
+    fraction (V_i / v_th_e)^2 of the thermal one, is counted in both."""
+    return float(we_proj) / float(we_ref)
+
+
+def boltzmann_electrons_te(N, ncell, n_ions, dx, T_e, v_th_e, seed, u=None, tol=1e-12):
+    """Electrons of a lifting at temperature T_e (units of T_e0): the Poisson-Boltzmann potential
+    with n_e = exp(phi / T_e), written for psi = phi / T_e as -T_e psi'' + e^psi = n (Newton at
+    the grid step dx / sqrt(T_e)), then the quiet start on exp(psi) with thermal speed
+    v_th_e sqrt(T_e). Returns (electrons, psi)."""
+    psi, _, fail = newton_pb(n_ions, dx / np.sqrt(T_e), tol=tol)
+    assert fail == 0
+    return boltzmann_electrons(N, ncell, psi, v_th_e * np.sqrt(T_e), seed, u=u), psi
+
+
 def ps_mean_velocity(cdf, vmin, dv, bin_shift, ncell):
     """Nodal mean ion velocity of a phase-space state: per x-bin the mean of its reconstructed
     CDF row over cell centres, then linear between bin midpoints (periodic)."""

@@ -180,3 +180,36 @@ def test_boltzmann_electrons_drift_with_the_ions():
     # up to the O((k dx)^2) smoothing of the CIC deposits and the linear profile interpolation
     kdx = 2 * np.pi / ncell
     assert np.abs(m / d - u).max() < 0.2 * kdx**2 / 2
+
+
+def test_temperature_lift_solves_the_boltzmann_relation_at_t_e():
+    # psi from -T_e psi'' + e^psi = n at the step dx / sqrt(T_e); phi = T_e psi satisfies the
+    # printed relation -phi'' + exp(phi / T_e) = n on the grid step dx (residual ~ Newton tol)
+    ncell, L, Te = 64, 32.0, 0.6
+    dx = L / ncell
+    x = np.arange(ncell) * dx
+    n = 1.0 + 0.3 * np.cos(2 * np.pi * x / L)
+    _, psi = orc.boltzmann_electrons_te(ncell * 64, ncell, n, dx, Te, 2.0, 5)
+    phi = Te * psi
+    lap = (np.roll(phi, -1) - 2 * phi + np.roll(phi, 1)) / dx ** 2
+    assert np.max(np.abs(-lap + np.exp(phi / Te) - n)) < 1e-9
+
+
+def test_temperature_lift_scales_the_thermal_energy():
+    # a uniform ion density gives psi = 0 at any T_e: the same weights and quantiles, velocities
+    # scaled by sqrt(T_e), so the kinetic energy scales by T_e exactly
+    ncell, L, N = 32, 16.0, 32 * 128
+    dx = L / ncell
+    n = np.ones(ncell)
+    e1, _ = orc.boltzmann_electrons_te(N, ncell, n, dx, 1.0, 3.0, 9)
+    e2, psi = orc.boltzmann_electrons_te(N, ncell, n, dx, 1.7, 3.0, 9)
+    assert np.max(np.abs(psi)) < 1e-12
+    E = np.zeros(ncell)
+    k1 = orc.electron_kinetic_energy(e1, E, ncell, dx, 0.1, -1800.0, 0.5)
+    k2 = orc.electron_kinetic_energy(e2, E, ncell, dx, 0.1, -1800.0, 0.5)
+    assert k2 / k1 == pytest.approx(1.7, rel=1e-12)
+    assert orc.lift_electron_temperature(k2, k1) == pytest.approx(1.7, rel=1e-12)
+    # the quiet start's thermal energy: sum w v^2 dx / 2 = (sum w dx) v_th^2 / 2 to the
+    # Hammersley quadrature's accuracy
+    q = float(np.sum(e1.w)) * dx
+    assert k1 == pytest.approx(0.5 * q * 9.0, rel=2e-3)
