@@ -1040,11 +1040,11 @@ def run_kinetic(dev, pb, per_reset=150):
     T_end = steps * w["dT"]
     checks = [steps // 3, 2 * steps // 3, steps]
 
-    def make(coarse="phase_space", reset=0):
+    def make(coarse="phase_space", reset=0, te_active=False):
         return pb.make_config(w["ncell"], w["n_coarse"], w["K"], w["N"], w["L"], w["dt"], w["dT"], qm=w["qm"],
                               v_th=w["v_th"], seed=11, sort_every=20, newton_tol=1e-10, coarse=coarse, n_v=w["n_v"],
                               v_max=w["v_max"], ps_filter=3, electrons="kinetic", qm_e=w["qm_e"],
-                              reset_every=reset)
+                              reset_every=reset, te_active=te_active)
 
     wants, plain = {}, {}
     for reset in (0, per_reset):
@@ -1061,21 +1061,27 @@ def run_kinetic(dev, pb, per_reset=150):
         plain[reset] = {"seconds": time.perf_counter() - t0, "status": ref.sync_status()}
         wants[reset] = want
     t_plain = plain[0]["seconds"]
-    ctx = pb.Context(make(), device=dev)
-    ctx.load_initial(w["amplitude"])
     b = int(np.log2(w["ncell"] // w["n_coarse"]))
     scale = 2.0 ** (-(np.log2(w["ncell"]) + b) / 2)  # bin mass -> Haar density coefficient
-    got, wall, done = {}, 0.0, 0
-    for m in checks:
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(m - done):
-            ctx.step()
-        done = m
-        torch.cuda.synchronize(dev)
-        wall += time.perf_counter() - t0
-        got[m] = (ctx.get_coarse().sum(1) * scale).cpu().numpy()
     key = {m: str(round(m * w["dT"])) for m in checks}
+
+    def projective(te_active):
+        ctx = pb.Context(make(te_active=te_active), device=dev)
+        ctx.load_initial(w["amplitude"])
+        got, wall, done = {}, 0.0, 0
+        for m in checks:
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(m - done):
+                ctx.step()
+            done = m
+            torch.cuda.synchronize(dev)
+            wall += time.perf_counter() - t0
+            got[m] = (ctx.get_coarse().sum(1) * scale).cpu().numpy()
+        return got, wall, ctx.sync_status(), ctx.diagnostics().T_e
+
+    got, wall, status, _ = projective(False)
+    got_te, wall_te, status_te, te_end = projective(True)
     eps_plain = {key[m]: _eps(got[m], wants[0][m].cpu().numpy()) for m in checks}
     eps_reset = {key[m]: _eps(got[m], wants[per_reset][m].cpu().numpy()) for m in checks}
     eps_pic = {key[m]: _eps(wants[per_reset][m].cpu().numpy(), wants[0][m].cpu().numpy()) for m in checks}
@@ -1090,7 +1096,13 @@ def run_kinetic(dev, pb, per_reset=150):
                            "speedup_vs_plain_pic": t_plain / wall,
                            "particle_steps_per_s": particles * w["K"] * steps / wall,
                            "eps_vs_plain_pic": eps_plain, "eps_vs_reset_pic": eps_reset,
-                           "status": ctx.sync_status()},
+                           "status": status},
+            "projective_electron_energy_active": {
+                "coarse": "phase_space + electrons' kinetic energy", "seconds": wall_te,
+                "speedup_vs_plain_pic": t_plain / wall_te, "T_e_at_end": te_end,
+                "eps_vs_plain_pic": {key[m]: _eps(got_te[m], wants[0][m].cpu().numpy()) for m in checks},
+                "eps_vs_reset_pic": {key[m]: _eps(got_te[m], wants[per_reset][m].cpu().numpy()) for m in checks},
+                "status": status_te},
             "eps_reset_pic_vs_plain_pic": eps_pic,
             "status_plain_pic": [plain[0]["status"], plain[per_reset]["status"]]}
 

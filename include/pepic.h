@@ -590,6 +590,12 @@ typedef struct pe_config {
                              velocity cells (power of two, <= 1024) reduced by the DWT of
                              `wavelet` to n_v_coarse coefficients (power of two, 2..n_v); the
                              coarse state is [n_coarse][n_v_coarse] */
+    int32_t te_active;    /* kinetic electrons: 1 projects the electrons' total kinetic energy as a
+                             global active variable (Section 4.2): sampled at every burst step,
+                             least-squares leap, and each lift loads the Boltzmann electrons at
+                             T_e / T_e0 = projected energy / energy at the initial load (their
+                             Poisson-Boltzmann potential with n_e = exp(phi / T_e), thermal speed
+                             v_th_e sqrt(T_e)); 0 keeps T_e = T_e0 */
 } pe_config;
 
 typedef struct pe_ctx pe_ctx;
@@ -638,6 +644,8 @@ typedef struct pe_diag {
     uint32_t status;        /* device status word (after sync) */
     int32_t electron_bank;  /* kinetic electrons: which PE_BUF_ELECTRONS_* holds them */
     int32_t e_v_at_integer; /* kinetic electrons: 1 if their stored v is at integer time */
+    double T_e;             /* kinetic electrons: T_e / T_e0 of the last lift (1 unless te_active) */
+    double W_e;             /* te_active: the electrons' projected kinetic energy of the last leap */
 } pe_diag;
 
 /* Validates cfg and fills the arena layout. PE_EINVAL on a bad configuration. */

@@ -59,7 +59,7 @@ class Config(ctypes.Structure):
                 ("coarse_kind", ctypes.c_int32), ("n_v", ctypes.c_int32), ("v_max", ctypes.c_double),
                 ("ps_filter", ctypes.c_int32), ("boundary", ctypes.c_int32), ("electrons", ctypes.c_int32),
                 ("reset_every", ctypes.c_int32), ("qm_e", ctypes.c_double), ("v_th_e", ctypes.c_double),
-                ("n_v_coarse", ctypes.c_int32)]
+                ("n_v_coarse", ctypes.c_int32), ("te_active", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -71,7 +71,8 @@ class Diag(ctypes.Structure):
     _fields_ = [("macro_steps", ctypes.c_int64), ("fine_steps", ctypes.c_int64), ("time", ctypes.c_double),
                 ("particle_bank", ctypes.c_int32), ("v_at_integer", ctypes.c_int32), ("s_w", ctypes.c_int32),
                 ("s_p", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_uint32),
-                ("electron_bank", ctypes.c_int32), ("e_v_at_integer", ctypes.c_int32)]
+                ("electron_bank", ctypes.c_int32), ("e_v_at_integer", ctypes.c_int32), ("T_e", ctypes.c_double),
+                ("W_e", ctypes.c_double)]
 
 
 class Moments(ctypes.Structure):
@@ -610,7 +611,7 @@ def ps_quiet_start_equal(n, ncell, bin_shift, mass, table, v_min, dv, seed, s_w,
 def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wavelet="haar", comoving=True,
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
                 v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic",
-                electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0, n_v_coarse=0) -> Config:
+                electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0, n_v_coarse=0, te_active=False) -> Config:
     """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
     masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
     filter of the projected phase-space slope (bit 0 along v, bit 1 along x); boundary:
@@ -624,7 +625,8 @@ def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wav
                   float(dT), float(qm), float(v_th), int(bool(comoving)), PE_POISSON[poisson], float(newton_tol),
                   int(newton_maxit), int(sort_every), int(seed) & 0xFFFFFFFFFFFFFFFF, float(w_cap), float(v_cap),
                   PE_COARSE[coarse], int(n_v), float(v_max), int(ps_filter), PE_BOUNDARY[boundary],
-                  PE_ELECTRONS[electrons], int(reset_every), float(qm_e), float(v_th_e), int(n_v_coarse))
+                  PE_ELECTRONS[electrons], int(reset_every), float(qm_e), float(v_th_e), int(n_v_coarse),
+                  int(bool(te_active)))
 
 
 def layout(cfg: Config) -> Layout:

@@ -168,6 +168,8 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (kin && (walls || c.poisson != PE_POISSON_BOLTZMANN || !(c.qm_e <= 0.0) || !(c.v_th_e >= 0.0) ||
                 c.reset_every < 0))
         return PE_EINVAL;
+    if (c.te_active != 0 && (c.te_active != 1 || !kin)) return PE_EINVAL;  // an electron temperature needs electrons
+    const bool te = c.te_active == 1;
     memset(out, 0, sizeof(*out));
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space sample row
@@ -200,7 +202,9 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
                                 (walls ? align256(PE_PS_EQ_SCRATCH_BYTES(nc)) : 0);
     out->bytes[PE_BUF_ELECTRONS_A] = kin ? bank : 0;
     out->bytes[PE_BUF_ELECTRONS_B] = kin ? bank : 0;
-    out->bytes[PE_BUF_RHO_E] = kin ? 8 * 3 * nc : 0;  // electron deposit + ion moments [2][ncell]
+    // electron deposit + ion moments [2][ncell]; te_active: K + 2 energy samples, the projected
+    // energy and its slope
+    out->bytes[PE_BUF_RHO_E] = kin ? 8 * 3 * nc + (te ? 8 * (size_t)(c.K + 4) : 0) : 0;
     size_t off = 0;
     for (int b = 0; b < PE_NBUF; ++b) {
         out->offset[b] = off;
@@ -265,7 +269,10 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
             x->ew[b] = (float*)(base + 3 * align256(4 * N));
         }
         x->rho_e = (int64_t*)(x->arena + lay.offset[PE_BUF_RHO_E]);
+        x->te_active = cfg->te_active;
+        if (x->te_active) x->we = (double*)(x->rho_e + 3 * (size_t)cfg->ncell);
     }
+    x->te = 1.0;
     x->phi = (double*)(x->arena + lay.offset[PE_BUF_PHI]);
     x->E = (double*)(x->arena + lay.offset[PE_BUF_E]);
     x->Ef = (float*)(x->arena + lay.offset[PE_BUF_EF]);
@@ -458,7 +465,29 @@ static uint64_t electron_seed(uint64_t s) { return s ^ 0xD1B54A32D192ED03ULL; }
 // phase-space lift), or a moment sample of the ion particles (a plain-PIC reset).
 enum ElectronDrift { kDriftProfile, kDriftPhaseSpace, kDriftParticles };
 
-static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed, ElectronDrift drift)
+// The electrons' total kinetic energy sum w Vbar^2 dx / 2 (pe_compute_moments' kinetic term, Vbar
+// at integer time in the current field) into we[row] (device): the global active variable of
+// Section 4.2.
+static int electron_energy_sample(pe_ctx* x, int row)
+{
+    const pe_config& c = x->cfg;
+    char* scratch = x->arena + x->lay.offset[PE_BUF_DIAG];
+    pe_moments* res = (pe_moments*)(scratch + PE_MOMENTS_SCRATCH_BYTES);
+    const int e = x->ebank;
+    const float kick = x->e_v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(pe_compute_moments(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, nullptr, x->E,
+                              c.ncell, x->dx, c.dt, (float)(x->qm_e * c.dt), kick, x->s_w, 1, scratch, res, x->status,
+                              x->stream));
+    return cudaMemcpyAsync(x->we + row, &res->kinetic, sizeof(double), cudaMemcpyDeviceToDevice, x->stream) ==
+                   cudaSuccess
+               ? PE_OK
+               : PE_ECUDA;
+}
+
+// Electrons at temperature te (units of T_e0): the Poisson-Boltzmann potential with
+// n_e = exp(phi / te) is solved for psi = phi / te, -te psi'' + e^psi = n_i, i.e. the same
+// Newton at the grid step dx / sqrt(te); the quiet start loads exp(psi) with v_th_e sqrt(te).
+static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed, ElectronDrift drift, double te = 1.0)
 {
     const pe_config& c = x->cfg;
     float* u = x->prof + c.ncell;
@@ -482,14 +511,14 @@ static int load_boltzmann_electrons(pe_ctx* x, uint64_t seed, ElectronDrift drif
     } else if (drift == kDriftPhaseSpace) {
         PE_TRY(pe_ps_mean_velocity(x->ps_cdf, x->nc, x->nv, x->vmin, x->dv, x->bin_shift, c.ncell, u, x->stream));
     }
-    PE_TRY(field_solve_history(x->rho, c.ncell, x->dx, x->s_w, PE_POISSON_BOLTZMANN, PE_BOUNDARY_PERIODIC,
-                               c.newton_tol, c.newton_maxit, x->phi, x->E, x->Ef, x->diag, x->status, nullptr, 0,
-                               x->stream));
+    PE_TRY(field_solve_history(x->rho, c.ncell, x->dx / sqrt(te), x->s_w, PE_POISSON_BOLTZMANN,
+                               PE_BOUNDARY_PERIODIC, c.newton_tol, c.newton_maxit, x->phi, x->E, x->Ef, x->diag,
+                               x->status, nullptr, 0, x->stream));
     PE_TRY(pe_boltzmann_profile(x->phi, mom, x->s_w, x->s_p, c.ncell, x->prof, mom ? u : nullptr, x->stream));
     const int e = x->ebank;
     PE_TRY(timed(x, PE_PROF_LOAD, [&] {
         return pe_quiet_start(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, c.ncell, x->prof, u,
-                              (float)x->v_th_e, seed, x->s_w, x->rho_e, x->status, x->stream);
+                              (float)(x->v_th_e * sqrt(te)), seed, x->s_w, x->rho_e, x->status, x->stream);
     }));
     x->e_v_at_integer = 1;
     return PE_OK;
@@ -646,7 +675,17 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
     PE_TRY(quiet_start_from_profile(x, c.seed, 1.0f));
     if (x->kinetic) {
         x->ebank = 0;
+        x->te = 1.0;
         PE_TRY(load_boltzmann_electrons(x, electron_seed(c.seed), kDriftProfile));
+        if (x->te_active) {  // the reference energy of T_e = T_e0
+            PE_TRY(electron_energy_sample(x, c.K + 2));
+            double w = 0.0;
+            if (cudaMemcpyAsync(&w, x->we + (c.K + 2), sizeof(w), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
+                cudaStreamSynchronize(x->stream) != cudaSuccess)
+                return PE_ECUDA;
+            x->we_ref = w;
+            x->we_last = w;
+        }
     }
     if (x->ps) return measure_phase(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
@@ -671,6 +710,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     float kick = x->v_at_integer ? 0.5f : 1.0f;
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
     for (int p = p_begin; p < p_end; ++p) {
+        if (x->te_active) PE_TRY(electron_energy_sample(x, p));
         const double tau = c.comoving ? x->dT_cur - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
         PE_TRY(timed(x, x->ps ? PE_PROF_PUSH_SAMPLE_PS : PE_PROF_PUSH_SAMPLE, [&] {
@@ -685,6 +725,7 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
         x->fine_steps += 1;
     }
     if (final_sample) {
+        if (x->te_active) PE_TRY(electron_energy_sample(x, p_end));
         const double tau = c.comoving ? x->dT_cur - p_end * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p_end));
         PE_TRY(timed(x, PE_PROF_SAMPLE, [&] {
@@ -731,6 +772,9 @@ extern "C" PE_API int pe_project(pe_ctx* ctx)
         PE_TRY(pe_ls_project(ctx->csamples, ctx->K_cur, (int32_t)ctx->ncoef, c.dt, ctx->dT_cur, ctx->coarse, ctx->slope,
                              ctx->stream));
     }
+    if (ctx->te_active)  // the electrons' energy: the same least-squares leap, into we[K+2] (slope we[K+3])
+        PE_TRY(pe_ls_project(ctx->we, ctx->K_cur, 1, c.dt, ctx->dT_cur, ctx->we + (c.K + 2), ctx->we + (c.K + 3),
+                             ctx->stream));
     ctx->macro_steps += 1;
     ctx->coarse_state = 1;
     ctx->time += ctx->dT_cur;
@@ -784,8 +828,19 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
         PE_TRY(pe_refine(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell, x->stream));
         PE_TRY(quiet_start_from_profile(x, lift_seed(x), 2.0f));  // refined restriction: wall nodes hold deposits
     }
-    if (x->kinetic)
-        PE_TRY(load_boltzmann_electrons(x, electron_seed(lift_seed(x)), x->ps ? kDriftPhaseSpace : kDriftProfile));
+    if (x->kinetic) {
+        if (x->te_active) {  // T_e / T_e0 = projected energy / energy at the initial load
+            double w = 0.0;
+            if (cudaMemcpyAsync(&w, x->we + (c.K + 2), sizeof(w), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
+                cudaStreamSynchronize(x->stream) != cudaSuccess)
+                return PE_ECUDA;
+            x->we_last = w;
+            const double t = (x->we_ref > 0.0) ? w / x->we_ref : 1.0;
+            x->te = (t > 1e-3 && t < 1e3) ? t : (t >= 1e3 ? 1e3 : 1e-3);  // NaN and negatives clamp low
+        }
+        PE_TRY(load_boltzmann_electrons(x, electron_seed(lift_seed(x)), x->ps ? kDriftPhaseSpace : kDriftProfile,
+                                        x->te));
+    }
     return PE_OK;
 }
 
@@ -982,6 +1037,7 @@ struct CheckpointHeader {
     double time, dT_cur;
     pe_config cfg;  // a restore needs the same configuration, byte for byte
     int32_t K_cur, pad;  // burst length of the next bursts
+    double te, we_ref, we_proj;  // electrons' temperature state (te_active)
 };
 constexpr uint32_t kCheckpointMagic = 0x50455043u;  // "PEPC"
 
@@ -1013,6 +1069,14 @@ extern "C" PE_API int pe_checkpoint_save(pe_ctx* ctx, void* host_buf, size_t byt
     h.dT_cur = x->dT_cur;
     h.cfg = x->cfg;
     h.K_cur = x->K_cur;
+    h.te = x->te;
+    h.we_ref = x->we_ref;
+    if (x->te_active) {
+        if (cudaMemcpyAsync(&h.we_proj, x->we + (x->cfg.K + 2), sizeof(double), cudaMemcpyDeviceToHost, x->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(x->stream) != cudaSuccess)
+            return PE_ECUDA;
+    }
     char* p = (char*)host_buf;
     memcpy(p, &h, sizeof(h));
     double* d = (double*)(p + sizeof(h));
@@ -1055,6 +1119,15 @@ extern "C" PE_API int pe_checkpoint_restore(pe_ctx* ctx, const void* host_buf, s
     x->time = h.time;
     x->dT_cur = h.dT_cur;
     x->K_cur = h.K_cur;
+    x->te = h.te;
+    x->we_ref = h.we_ref;
+    if (x->te_active) {
+        x->we_last = h.we_proj;
+        if (cudaMemcpyAsync(x->we + (x->cfg.K + 2), &h.we_proj, sizeof(double), cudaMemcpyHostToDevice, x->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(x->stream) != cudaSuccess)
+            return PE_ECUDA;
+    }
     x->phi_hist = h.phi_hist;
     x->fresh = 0;  // the next step lifts from the restored coarse state
     x->coarse_state = 1;
@@ -1123,6 +1196,8 @@ extern "C" PE_API int pe_diagnostics(pe_ctx* ctx, pe_diag* out)
     out->s_p = ctx->s_p;
     out->electron_bank = ctx->ebank;
     out->e_v_at_integer = ctx->e_v_at_integer;
+    out->T_e = ctx->te;
+    out->W_e = ctx->we_last;
     int32_t d[2] = {0, 0};
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PE_ECUDA;
     if (cudaMemcpy(d, ctx->diag, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;

@@ -25,6 +25,11 @@ struct pe_ctx {
     int nb;              // sample length per moment: ncell >> bin_shift
     int ps;              // phase-space coarse variable (PE_COARSE_PHASE_SPACE)
     int K_cur;           // burst length of the next bursts (the configured K unless adapted)
+    int te_active;       // kinetic electrons: their kinetic energy is an active variable
+    double* we;          // te_active: [K+2] sampled energies, then the projected energy and its slope
+    double te;           // T_e / T_e0 of the last lift
+    double we_ref;       // the electrons' kinetic energy at the initial load (T_e = T_e0)
+    double we_last;      // the projected energy read at the last lift
     int nv;              // velocity cells (phase space; the fine cells n_vf of the wavelet form)
     int psw;             // phase space, wavelet form: hat rows in x, DWT in v to nvc coefficients
     int nvc;             // wavelet form: velocity coefficients per coarse node

@@ -319,3 +319,57 @@ def test_kinetic_full_size_properties():
     ctx.step()
     assert ctx.sync_status() == 0
     assert np.all(np.isfinite(ctx.get_coarse().cpu().numpy()))
+
+
+def test_electron_energy_is_sampled_projected_and_lifted():
+    """The electrons' kinetic energy as a global active variable (Section 4.2; te_active): the
+    burst samples it at every step (the oracle's energy of the same two-species trajectory,
+    1e-5), the leap projects it by the least-squares rule (1e-12 on the sampled values), and
+    the lift loads the electrons at T_e = projected / initial energy: their potential solves
+    -T_e psi'' + e^psi = n_i and their energy is the projected one to the quiet start's
+    quadrature (2e-3). A checkpoint keeps the temperature state."""
+    cfg = KIN
+    seed = 13
+    ncell, K = cfg["ncell"], cfg["K"]
+    dx, dt = cfg["L"] / ncell, cfg["dt"]
+    dT = cfg["M"] * K * dt
+    ctx = make_kinetic(cfg, seed=seed, te_active=True)
+    ctx.load_initial(cfg["amp"])
+    d0 = ctx.diagnostics()
+    assert d0.T_e == 1.0
+    ions = oracle_ions(cfg, seed)
+    elec = oracle_electrons(cfg, ions, d0.s_w, electron_seed(seed), u=sine_u(cfg))
+    W0 = orc.electron_kinetic_energy(elec, np.zeros(ncell), ncell, dx, dt, QM_E, 0.5)
+    assert d0.W_e == pytest.approx(W0, rel=1e-5)
+    ctx.step()
+    assert ctx.sync_status() == 0
+    we = ctx.view("rho_e", torch.float64).cpu().numpy()[3 * ncell:3 * ncell + K + 4]
+    want = []
+    for p in range(K + 1):
+        _, E = orc.field_kinetic(ions, elec, ncell, dx, d0.s_w)
+        want.append(orc.electron_kinetic_energy(elec, E, ncell, dx, dt, QM_E, 0.5 if p == 0 else 1.0))
+        if p < K:
+            orc.pic_steps_kinetic(ions, elec, ncell, dx, dt, 1.0, QM_E, 1, d0.s_w, vel_at_integer=(p == 0))
+    np.testing.assert_allclose(we[:K + 1], want, rtol=1e-5)
+    proj, _ = orc.ls_project(we[:K + 1].reshape(K + 1, 1), dt, dT)
+    assert we[K + 2] == pytest.approx(proj[0], rel=1e-12)
+    ctx.lift()
+    assert ctx.sync_status() == 0
+    d = ctx.diagnostics()
+    assert d.T_e == pytest.approx(we[K + 2] / d0.W_e, rel=1e-12) and d.W_e == we[K + 2]
+    psi = ctx.view("phi", torch.float64, ncell).cpu().numpy()
+    gi = state_of(ctx, "ions")
+    n_i = orc.deposit_fx(gi.cell, gi.theta.astype(np.float64), gi.w.astype(np.float64), ncell, d.s_w) * 2.0 ** -(
+        d.s_w + 24)
+    lap = (np.roll(psi, -1) - 2 * psi + np.roll(psi, 1)) / dx ** 2
+    assert np.max(np.abs(-d.T_e * lap + np.exp(psi) - n_i)) < 1e-6 * np.max(n_i)
+    We = orc.electron_kinetic_energy(state_of(ctx, "electrons"), np.zeros(ncell), ncell, dx, dt, QM_E, 0.5)
+    assert We == pytest.approx(we[K + 2], rel=2e-3)
+    ctx.step()  # a checkpoint holds a coarse state: the one after a projection
+    img = ctx.checkpoint()
+    ctx2 = make_kinetic(cfg, seed=seed, te_active=True)
+    ctx2.restore(img)
+    ctx.lift()
+    ctx2.lift()
+    assert ctx.diagnostics().T_e == ctx2.diagnostics().T_e
+    assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
