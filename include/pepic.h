@@ -423,6 +423,15 @@ PE_API int pe_compute_moments(const int32_t* cell, const float* theta, const flo
                       float qm_dt, float kick, int32_t s_w, int32_t mode, void* scratch, pe_moments* out,
                       uint32_t* status, void* stream);
 
+/* Kinetic energy sum w Vbar^2 dx / 2 of one species (Vbar = v + (kick - 1/2) qm_dt E(X) at
+ * integer time, E gathered from Ef), into out (device double): the global active variable of
+ * Section 4.2 for the kinetic electrons. FP32 per-thread sums over a fixed grid-stride partition,
+ * FP64 beyond (about 1e-6 relative; reproducible). scratch: device, double[1024]. An
+ * out-of-range cell is skipped and sets PE_FLAG_RANGE. */
+PE_API int pe_kinetic_energy(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
+                             const float* Ef, int32_t ncell, double dx, float qm_dt, float kick, double* scratch,
+                             double* out, uint32_t* status, void* stream);
+
 /* Error measure of Section 4.1.1 between two coarse states (or any FP64 vectors):
  * out = sqrt( sum_i (a_i - b_i)^2 / sum_i (a_i^2 + b_i^2) ), 0 when both vanish. a, b, out
  * in device memory; one block, fixed summation order. */

@@ -185,6 +185,7 @@ SIGNATURES = {
     "pe_ps_lift_tables": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P]),
     "pe_ps_coarsen_v": (ctypes.c_int, [P, i64, i32, i32, i32, i32, i32, P, P]),
     "pe_tc_gemm_bf16": (ctypes.c_int, [P, i64, P, i64, P, i64, i32, i32, i32, P, P]),
+    "pe_kinetic_energy": (ctypes.c_int, [P, P, P, P, i64, P, i32, f64, f32, f32, P, P, P, P]),
     "pe_ps_refine_v": (ctypes.c_int, [P, i64, i32, i32, i32, P, P]),
     "pe_ps_node_tables": (ctypes.c_int, [P, P, i32, i32, i32, P, P, P]),
     "pe_ps_quiet_start_nodes": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, i32, f64, f64, u64, i32, P, P, P]),

@@ -471,17 +471,11 @@ enum ElectronDrift { kDriftProfile, kDriftPhaseSpace, kDriftParticles };
 static int electron_energy_sample(pe_ctx* x, int row)
 {
     const pe_config& c = x->cfg;
-    char* scratch = x->arena + x->lay.offset[PE_BUF_DIAG];
-    pe_moments* res = (pe_moments*)(scratch + PE_MOMENTS_SCRATCH_BYTES);
+    double* scratch = (double*)(x->arena + x->lay.offset[PE_BUF_DIAG]);
     const int e = x->ebank;
     const float kick = x->e_v_at_integer ? 0.5f : 1.0f;
-    PE_TRY(pe_compute_moments(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, nullptr, x->E,
-                              c.ncell, x->dx, c.dt, (float)(x->qm_e * c.dt), kick, x->s_w, 1, scratch, res, x->status,
-                              x->stream));
-    return cudaMemcpyAsync(x->we + row, &res->kinetic, sizeof(double), cudaMemcpyDeviceToDevice, x->stream) ==
-                   cudaSuccess
-               ? PE_OK
-               : PE_ECUDA;
+    return pe_kinetic_energy(x->ecell[e], x->etheta[e], x->ev[e], x->ew[e], c.nparticles, x->Ef, c.ncell, x->dx,
+                             (float)(x->qm_e * c.dt), kick, scratch, x->we + row, x->status, x->stream);
 }
 
 // Electrons at temperature te (units of T_e0): the Poisson-Boltzmann potential with

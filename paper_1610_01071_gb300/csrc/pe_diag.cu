@@ -222,6 +222,70 @@ int moments_blocks(int64_t n)
 
 using namespace pe;
 
+namespace pe {
+namespace {
+// Kinetic energy sum w Vbar^2 dx / 2 of one species: FP32 per-thread sums over a fixed
+// grid-stride partition, FP64 from the warp sums on (the FP64 pipe is narrow on this part), block
+// partials folded in block order by one thread: reproducible.
+constexpr int kEnergyBlocks = 1024;
+
+__global__ void __launch_bounds__(kDiagThreads) k_energy_part(const int32_t* __restrict__ cell,
+                                                              const float* __restrict__ theta,
+                                                              const float* __restrict__ v, const float* __restrict__ w,
+                                                              int64_t n, const float* __restrict__ Ef, int ncell,
+                                                              float hk, double* __restrict__ part,
+                                                              uint32_t* __restrict__ status)
+{
+    float k = 0.0f;
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int c = cell[i];
+        if ((unsigned)c >= (unsigned)ncell) {
+            bad = true;
+            continue;
+        }
+        const int c1 = (c + 1 == ncell) ? 0 : c + 1;
+        const float Ec = __ldg(Ef + c), Ec1 = __ldg(Ef + c1);
+        const float vb = fmaf(hk, fmaf(theta[i], Ec1 - Ec, Ec), v[i]);
+        k = fmaf(w[i] * vb, vb, k);
+    }
+    if (bad) raise_flag(status, PE_FLAG_RANGE);
+    __shared__ double sk[kDiagThreads / 32];
+    const double kw = warp_sum((double)k);
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = kw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int j = 0; j < kDiagThreads / 32; ++j) t += sk[j];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_energy_final(const double* __restrict__ part, int nb, double half_dx, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += part[b];
+    *out = t * half_dx;
+}
+}  // namespace
+}  // namespace pe
+
+extern "C" PE_API int pe_kinetic_energy(const int32_t* cell, const float* theta, const float* v, const float* w,
+                                        int64_t n, const float* Ef, int32_t ncell, double dx, float qm_dt, float kick,
+                                        double* scratch, double* out, uint32_t* status, void* stream)
+{
+    if (n < 0 || ncell < 2 || !(dx > 0.0) || !scratch || !out || !status) return PE_EINVAL;
+    if (n > 0 && (!cell || !theta || !v || !w || !Ef)) return PE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)std::min<int64_t>(kEnergyBlocks, std::max<int64_t>(1, (n + 4095) / 4096));
+    k_energy_part<<<nb, kDiagThreads, 0, s>>>(cell, theta, v, w, n, Ef, ncell, (kick - 0.5f) * qm_dt, scratch,
+                                              status);
+    k_energy_final<<<1, 32, 0, s>>>(scratch, nb, 0.5 * dx, out);
+    return launch_status(2);
+}
+
 extern "C" PE_API int pe_compute_moments(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
                                  const float* Ef, const double* phi, const double* E, int32_t ncell, double dx,
                                  double dt, float qm_dt, float kick, int32_t s_w, int32_t mode, void* scratch,
