@@ -502,22 +502,39 @@ extern "C" PE_API int pe_batch_step(pe_batch* b)
     int64_t* rho_all = reinterpret_cast<int64_t*>(at(b, b->L.rho));
     if (!fresh)  // every realisation's lifting profile in one launch
         PE_TRY(launch_refine_batch(at(b, b->L.refine), R, PE_WAVELET_HAAR, b->max_ncell, b->stream));
+    // The realisations' loadings are independent: spread over the side streams so that small
+    // ones overlap (each is a few short launches), then joined.
+    const int nside = (int)std::min<size_t>(b->side.size(), (size_t)R);
+    const bool fork = nside > 1;
+    if (fork) {
+        if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return PE_ECUDA;
+        for (int k = 0; k < nside; ++k)
+            if (cudaStreamWaitEvent(b->side[k], b->ev_fork, 0) != cudaSuccess) return PE_ECUDA;
+    }
     for (int r = 0; r < R; ++r) {
         pe_ctx* x = b->ctx[r];
         const pe_config& c = x->cfg;
         const int k = x->bank;
+        cudaStream_t ls = fork ? b->side[r % nside] : b->stream;
         if (!fresh) {
             if (x->walls)  // bounded grid: equal weights, wall deposits doubled to densities
                 PE_TRY(pe_quiet_start_equal(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell,
                                             x->prof, x->prof + c.ncell, 2.0f, (float)c.v_th, pe_ctx_lift_seed(x),
-                                            x->s_w, x->eq_scratch, rho_all + b->rho_off[r], x->status, b->stream));
+                                            x->s_w, x->eq_scratch, rho_all + b->rho_off[r], x->status, ls));
             else
                 PE_TRY(pe_quiet_start(x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles, c.ncell, x->prof,
                                       x->prof + c.ncell, (float)c.v_th, pe_ctx_lift_seed(x), x->s_w,
-                                      rho_all + b->rho_off[r], x->status, b->stream));
+                                      rho_all + b->rho_off[r], x->status, ls));
         } else {
             PE_TRY(pe_deposit(x->cell[k], x->theta[k], x->w[k], c.nparticles, c.ncell, x->s_w,
-                              rho_all + b->rho_off[r], x->status, b->stream));
+                              rho_all + b->rho_off[r], x->status, ls));
+        }
+    }
+    if (fork) {
+        for (int k = 0; k < nside; ++k) {
+            if (cudaEventRecord(b->ev_join[k], b->side[k]) != cudaSuccess ||
+                cudaStreamWaitEvent(b->stream, b->ev_join[k], 0) != cudaSuccess)
+                return PE_ECUDA;
         }
     }
     // Burst + restriction + projection: eager on the first call, then a captured graph
