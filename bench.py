@@ -45,6 +45,8 @@ KERNEL_BYTES = {
     "push_sample_psw": (28, "k_particles<push + phase-space sample, hat rows> (wavelet form: 16 coarse nodes x "
                             "256 velocity cells window)"),
     "load_psw": (16, "k_ps_quiet_start on fine-node tables (wavelet-form lifting, write only)"),
+    "push_sample_slab": (28, "k_particles<push + binned moment sample, walls> on the slab (2^25 ions, 8192 cells)"),
+    "push_sample_ps_slab": (28, "k_particles<push + phase-space sample, walls> on the slab (2^25 ions)"),
 }
 # DRAM bytes (read + write) per launch on the 2^24-ion workload from the ncu captures
 # summarised in profiles/, each valid while the particle kernels' device code
@@ -423,6 +425,18 @@ def run_gpu(args):
     means["push"] = (prof_plain["push"]["ms"] / max(prof_plain["push"]["launches"], 1), prof_plain["push"]["launches"])
     means.update(kern)
     roof = {k: roofline_entry(k, ms, n, N, peak, peak_kind, src_hash) for k, (ms, n) in means.items()}
+    slab_roof = []
+    if slab is not None:  # the bounded-grid workload's fused passes (2^25 ions), timed inside its bursts
+        from paper_1610_01071_gb300 import inputs as _inp
+
+        n_slab = _inp.workload("slab")["N"]
+        for r in slab["projective"]:
+            if r["coarse"] == "moments" or r["K"] == 30:
+                kk = r["pass_kind"] + "_slab"
+                if r["pass_launches"] and kk not in [e.get("key") for e in slab_roof]:
+                    e = roofline_entry(kk, r["pass_ms"], r["pass_launches"], n_slab, peak, peak_kind, src_hash)
+                    e["key"] = kk
+                    slab_roof.append(e)
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -440,7 +454,7 @@ def run_gpu(args):
         "newton_iters_last": newton_iters,
         # the dominant kernel: the fused pass of the bursts, from its own launches only
         "roofline": roof["push_sample"],
-        "roofline_kernels": [roof[k] for k in KERNEL_BYTES if k in roof and k != "push_sample"],
+        "roofline_kernels": [roof[k] for k in KERNEL_BYTES if k in roof and k != "push_sample"] + slab_roof,
         "e2e": {"value": ps_proj / t_e2e_max, "unit": UNIT, "h2d_bytes_per_step": 8 * 2 * cfg["n_coarse"],
                 "d2h_bytes_per_step": 8 * 2 * cfg["n_coarse"]},
         "gpu_launches": launches,
@@ -998,6 +1012,9 @@ def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 2
         b = int(np.log2(w["ncell"] // w["n_coarse"]))
         scale = 2.0 ** (-(np.log2(w["ncell"]) + b) / 2)  # bin mass -> Haar density coefficient
         got, t, wall = {}, 0.0, 0.0
+        kind = "push_sample_ps" if coarse == "phase_space" else "push_sample"
+        ctx.profile_read_kinds()
+        ctx.profile(True, kinds=(kind,))  # the fused pass of the bursts, for its roofline
         for T in checks_t:
             torch.cuda.synchronize(dev)
             t1 = time.perf_counter()
@@ -1008,9 +1025,12 @@ def run_slab(dev, pb, variants=(("phase_space", 6.0, 30), ("phase_space", 6.0, 2
             wall += time.perf_counter() - t1
             c = ctx.get_coarse()
             got[T] = (c.sum(1) * scale if coarse == "phase_space" else c[0]).cpu().numpy()
+        ctx.profile(False)
+        pk = ctx.profile_read_kinds()[kind]
         eps = {str(round(T)): _eps(got[T], want[T].cpu().numpy()) for T in checks_t}
         ctx.lift()
         return {"coarse": coarse, "dT": dT, "K": K, "M": dT / (K * w["dt"]), "seconds": wall,
+                "pass_kind": kind, "pass_ms": pk["ms"] / max(pk["launches"], 1), "pass_launches": pk["launches"],
                 "speedup_vs_plain_pic": t_plain / wall,
                 "particle_steps_per_s": float(w["N"]) * K * round(T_end / dT) / wall,
                 "eps_coarse_density_at_T": eps, "charge_left": ctx.moments()["charge"] / q0,
