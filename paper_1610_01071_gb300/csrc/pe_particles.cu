@@ -919,7 +919,17 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     const bool rho = ModeTraits<MODE>::rho;
     const bool samp = ModeTraits<MODE>::sample;
     const bool bin = ModeTraits<MODE>::binned;
-    P.rho_width = rho ? (P.ncell <= kRhoWindowNodes ? P.ncell : kRhoWindowNodes) : 0;
+    // charge window: 64 nodes before the chunk's first cell, then the chunk's cells at a uniform
+    // density (chunks of <= 65536 particles) twice over; no wider than needed, so that the shared
+    // memory left to L1 stays large (the streaming loads' in-flight capacity)
+    if (rho) {
+        const int64_t span = (int64_t)65536 * P.ncell / (P.n > 0 ? P.n : 1) + 1;
+        int w = 128;
+        while (w < 128 + 2 * span && w < kRhoWindowNodes) w <<= 1;
+        P.rho_width = P.ncell <= w ? P.ncell : w;
+    } else {
+        P.rho_width = 0;
+    }
     P.samp_width = (samp && !bin) ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
     const int nb = bin ? (P.ncell >> P.bin_shift) : 0;
     const bool ps = ModeTraits<MODE>::ps;
