@@ -54,29 +54,79 @@ __device__ int edge_low(int N, double* F)
             break;
         }
     if (k0 < 0) return 0;
-    int km = k0 - 1, kp = k0 + 1;
     // S = F[0] + ... + F[kp-1] summed left to right; it depends on kp only, so it is carried
     // from one kp to the next (the same additions in the same order as summing afresh)
     int s_kp = 0;
     double S = 0.0;
-    for (;;) {
-        if (kp > N || km < 0) return 1;
-        for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
+    // the admissibility test of the range [km, kp) with the operations of the printed rule
+    auto top_of = [&](int km, int kp, double& dF) {
         const double L = (double)(kp - km);
-        const double dF = div_(mul_(2.0, S), mul_(L, sub_(L, 1.0)));
-        const double top = mul_(sub_(L, 1.0), dF);
-        if (top >= 0.0 && top <= F[kp]) {
+        dF = div_(mul_(2.0, S), mul_(L, sub_(L, 1.0)));
+        return mul_(sub_(L, 1.0), dF);
+    };
+    // For each kp the procedure tries km = k0 - 1, k0 - 2, ..., 0 and takes the first that
+    // passes. top = (L - 1) dF is 2 S / L up to rounding (L = kp - km), monotone in km: for
+    // S > 0 it passes from some km down, for S < 0 nowhere, for S = 0 everywhere or nowhere. So
+    // the first passing km is found by bisection on the exact test and then confirmed by the
+    // test itself on its neighbours (2 S / L moves by a factor (L+1)/L >= 1 + 1/N per step, far
+    // beyond the rounding, so only neighbours of the threshold can disagree with the bisection):
+    // the same km as the linear scan, in O(log N) tests.
+    for (int kp = k0 + 1; kp <= N; ++kp) {
+        for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
+        const int hi = k0 - 1;  // first km tried
+        if (hi < 0) return 1;
+        double dF = 0.0;
+        int km = -1;
+        if (S > 0.0) {
+            // smallest L passing <=> largest km passing; test(km) is false for km above it
+            int lo_ok = -1, a = 0, b = hi;  // search the largest km in [0, hi] with the test true
+            double t0;
+            {
+                t0 = top_of(0, kp, dF);
+                if (t0 >= 0.0 && t0 <= F[kp]) lo_ok = 0;
+            }
+            // km = 0 (the largest L) fails clearly: no km passes for this kp
+            if (lo_ok < 0 && t0 > F[kp] * (1.0 + 1e-12) + 1e-300) continue;
+            if (lo_ok == 0) {
+                while (a < b) {  // invariant: test(a) true
+                    const int m = (a + b + 1) >> 1;
+                    const double t = top_of(m, kp, dF);
+                    if (t >= 0.0 && t <= F[kp])
+                        a = m;
+                    else
+                        b = m - 1;
+                }
+                // confirm with the scan order's own tests near the threshold
+                int start = a + 3 < hi ? a + 3 : hi;
+                for (int k = start; k >= 0; --k) {
+                    const double t = top_of(k, kp, dF);
+                    if (t >= 0.0 && t <= F[kp]) {
+                        km = k;
+                        break;
+                    }
+                }
+            } else {
+                // no km in [0, hi] passes by monotonicity; confirm on the last few of the scan
+                for (int k = (hi < 3 ? hi : 3); k >= 0; --k) {
+                    const double t = top_of(k, kp, dF);
+                    if (t >= 0.0 && t <= F[kp]) {
+                        km = k;
+                        break;
+                    }
+                }
+            }
+        } else if (S == 0.0) {
+            const double t = top_of(hi, kp, dF);
+            if (t >= 0.0 && t <= F[kp]) km = hi;
+        }
+        if (km >= 0) {
+            top_of(km, kp, dF);
             for (int k = 0; k < km; ++k) F[k] = 0.0;
             for (int k = km; k < kp; ++k) F[k] = mul_((double)(k - km), dF);
             return 0;
         }
-        if (km > 0) {
-            km -= 1;
-        } else {
-            kp += 1;
-            km = k0 - 1;
-        }
     }
+    return 1;
 }
 
 // Interior reconstruction from the low indices (Appendix C): at the first descent k0, k1 the
