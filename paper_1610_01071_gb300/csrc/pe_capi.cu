@@ -703,13 +703,20 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
     }
     float kick = x->v_at_integer ? 0.5f : 1.0f;
     const float dt_dx = (float)(c.dt / x->dx), qm_dt = (float)(c.qm * c.dt);
+    // the sample rows of the range accumulate from zero: cleared at once here, not per pass
+    const int last_row = final_sample ? p_end : p_end - 1;
+    if (last_row >= p_begin &&
+        cudaMemsetAsync(sample_row(x, p_begin), 0, sizeof(int64_t) * (size_t)x->row_fx * (size_t)(last_row - p_begin + 1),
+                        x->stream) != cudaSuccess)
+        return PE_ECUDA;
     for (int p = p_begin; p < p_end; ++p) {
         if (x->te_active) PE_TRY(electron_energy_sample(x, p));
         const double tau = c.comoving ? x->dT_cur - p * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p));
+        if (cudaMemsetAsync(x->rho, 0, sizeof(int64_t) * (size_t)c.ncell, x->stream) != cudaSuccess) return PE_ECUDA;
         PE_TRY(timed(x, x->ps ? PE_PROF_PUSH_SAMPLE_PS : PE_PROF_PUSH_SAMPLE, [&] {
-            return pe_push_ex(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
-                              kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream);
+            return push_pass(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, dt_dx, qm_dt,
+                             kick, x->s_w, c.boundary, x->rho, &a, x->status, x->stream, false);
         }));
         if (x->kinetic) PE_TRY(push_electrons(x));
         PE_TRY(field_solve(x, 1));
@@ -723,8 +730,8 @@ int pe_ctx_burst_range(pe_ctx* x, int p_begin, int p_end, int final_sample)
         const double tau = c.comoving ? x->dT_cur - p_end * c.dt : 0.0;
         pe_sample_args a = sample_args(x, tau, sample_row(x, p_end));
         PE_TRY(timed(x, PE_PROF_SAMPLE, [&] {
-            return pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick, &a,
-                             x->status, x->stream);
+            return sample_pass(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, qm_dt, kick, &a,
+                               x->status, x->stream, false);
         }));
     }
     x->fresh = 0;

@@ -57,6 +57,15 @@ int field_solve_history(const int64_t* rho_fx, int ncell, double dx, int s_w, in
 // max_chunk or 65536) per block, filling whole waves of resident blocks; returns the block count.
 int particle_grid(const void* kernel, int block, size_t smem, int64_t n, int64_t* chunk, int64_t max_chunk = 0);
 
+// pe_push_ex and pe_sample with their zeroing of the charge grid and of the sample row made
+// optional (zero = false: the caller has zeroed both, e.g. all sample rows of a burst at once).
+int push_pass(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef, int32_t ncell,
+              float dt_over_dx, float qm_dt, float kick, int32_t s_w, int32_t boundary, int64_t* rho_fx,
+              const pe_sample_args* sample, uint32_t* status, void* stream, bool zero);
+int sample_pass(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n, const float* Ef,
+                int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample, uint32_t* status, void* stream,
+                bool zero);
+
 // Batched particle passes (pe_particles.cu).
 size_t push_desc_size();
 size_t work_item_size();

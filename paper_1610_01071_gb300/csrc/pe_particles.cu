@@ -913,7 +913,7 @@ static int ps_window_rows(int nxc, int nv)
 }
 
 template <int MODE>
-static int launch_particles(PushParams& P, cudaStream_t s)
+static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
 {
     const int block = kThreads;
     const bool rho = ModeTraits<MODE>::rho;
@@ -944,9 +944,12 @@ static int launch_particles(PushParams& P, cudaStream_t s)
     const void* k = P.walls ? (const void*)k_particles<MODE, true> : (const void*)k_particles<MODE, false>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = particle_grid(k, block, smem, P.n, &P.chunk, P.max_chunk);
-    if (rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess) return PE_ECUDA;
+    // the pass accumulates into a zeroed charge grid and sample row (zeroed by the caller when !zero)
+    if (zero && rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess)
+        return PE_ECUDA;
     const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : 2 * (size_t)(P.ncell >> P.bin_shift);
-    if (samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess) return PE_ECUDA;
+    if (zero && samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess)
+        return PE_ECUDA;
     if (P.n == 0) return PE_OK;
     if (P.walls)
         k_particles<MODE, true><<<grid, block, smem, s>>>(P);
@@ -1082,10 +1085,11 @@ extern "C" PE_API int pe_deposit(const int32_t* cell, const float* theta, const 
     return launch_particles<kDeposit>(P, (cudaStream_t)stream);
 }
 
-extern "C" PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef,
-                                 int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w,
-                                 int32_t boundary, int64_t* rho_fx, const pe_sample_args* sample, uint32_t* status,
-                                 void* stream)
+namespace pe {
+
+int push_pass(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef, int32_t ncell,
+              float dt_over_dx, float qm_dt, float kick, int32_t s_w, int32_t boundary, int64_t* rho_fx,
+              const pe_sample_args* sample, uint32_t* status, void* stream, bool zero)
 {
     if (!is_pow2(ncell) || ncell < 8 || !rho_fx || !Ef || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
     if (boundary != PE_BOUNDARY_PERIODIC && boundary != PE_BOUNDARY_ABSORBING) return PE_EINVAL;
@@ -1120,28 +1124,18 @@ extern "C" PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w
             P.vmin = sample->v_min;
             P.inv_dv = sample->inv_dv;
             P.tent_scale = ldexpf(1.0f, 24 - P.bin_shift);
-            if (sample->x_tent) return launch_particles<kPushSamplePSW>(P, (cudaStream_t)stream);
-            return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream);
+            if (sample->x_tent) return launch_particles<kPushSamplePSW>(P, (cudaStream_t)stream, zero);
+            return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream, zero);
         }
-        if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream);
-        return launch_particles<kPushSample>(P, (cudaStream_t)stream);
+        if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream, zero);
+        return launch_particles<kPushSample>(P, (cudaStream_t)stream, zero);
     }
-    return launch_particles<kPush>(P, (cudaStream_t)stream);
+    return launch_particles<kPush>(P, (cudaStream_t)stream, zero);
 }
 
-extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
-                              int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w, int64_t* rho_fx,
-                              const pe_sample_args* sample, uint32_t* status, void* stream)
-{
-    if (sample && sample->boundary != PE_BOUNDARY_PERIODIC) return PE_EINVAL;
-    // periodic: the weights are only read
-    return pe_push_ex(cell, theta, v, const_cast<float*>(w), n, Ef, ncell, dt_over_dx, qm_dt, kick, s_w,
-                      PE_BOUNDARY_PERIODIC, rho_fx, sample, status, stream);
-}
-
-extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
-                                const float* Ef, int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample,
-                                uint32_t* status, void* stream)
+int sample_pass(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n, const float* Ef,
+                int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample, uint32_t* status, void* stream,
+                bool zero)
 {
     if (!is_pow2(ncell) || ncell < 8 || !Ef || !particles_ok(cell, theta, v, w, n) || !sample_ok(sample, ncell))
         return PE_EINVAL;
@@ -1171,11 +1165,39 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
         P.vmin = sample->v_min;
         P.inv_dv = sample->inv_dv;
         P.tent_scale = ldexpf(1.0f, 24 - P.bin_shift);
-        if (sample->x_tent) return launch_particles<kSamplePSW>(P, (cudaStream_t)stream);
-        return launch_particles<kSamplePS>(P, (cudaStream_t)stream);
+        if (sample->x_tent) return launch_particles<kSamplePSW>(P, (cudaStream_t)stream, zero);
+        return launch_particles<kSamplePS>(P, (cudaStream_t)stream, zero);
     }
-    if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream);
-    return launch_particles<kSample>(P, (cudaStream_t)stream);
+    if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream, zero);
+    return launch_particles<kSample>(P, (cudaStream_t)stream, zero);
+}
+
+}  // namespace pe
+
+extern "C" PE_API int pe_push_ex(int32_t* cell, float* theta, float* v, float* w, int64_t n, const float* Ef,
+                                 int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w,
+                                 int32_t boundary, int64_t* rho_fx, const pe_sample_args* sample, uint32_t* status,
+                                 void* stream)
+{
+    return push_pass(cell, theta, v, w, n, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, boundary, rho_fx, sample, status,
+                     stream, true);
+}
+
+extern "C" PE_API int pe_push(int32_t* cell, float* theta, float* v, const float* w, int64_t n, const float* Ef,
+                              int32_t ncell, float dt_over_dx, float qm_dt, float kick, int32_t s_w, int64_t* rho_fx,
+                              const pe_sample_args* sample, uint32_t* status, void* stream)
+{
+    if (sample && sample->boundary != PE_BOUNDARY_PERIODIC) return PE_EINVAL;
+    // periodic: the weights are only read
+    return pe_push_ex(cell, theta, v, const_cast<float*>(w), n, Ef, ncell, dt_over_dx, qm_dt, kick, s_w,
+                      PE_BOUNDARY_PERIODIC, rho_fx, sample, status, stream);
+}
+
+extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const float* v, const float* w, int64_t n,
+                                const float* Ef, int32_t ncell, float qm_dt, float kick, const pe_sample_args* sample,
+                                uint32_t* status, void* stream)
+{
+    return sample_pass(cell, theta, v, w, n, Ef, ncell, qm_dt, kick, sample, status, stream, true);
 }
 
 extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w, int64_t first,

@@ -5,7 +5,7 @@
 // (pe_push / pe_sample with n_v > 0); this file holds the rest of the cycle:
 //   - pe_ps_coarsen: fixed-point samples -> FP64 masses;
 //   - pe_ps_lift_tables: per bin the mass and the momentum-conserving reconstruction of the
-//     velocity CDF (Appendix C), one thread per bin, in FP64 with every operation rounded
+//     velocity CDF (Appendix C), one warp per bin, in FP64 with every operation rounded
 //     separately (no contraction) so the tables are reproducible bit for bit;
 //   - pe_ps_quiet_start: the Hammersley loading of Appendix C on those tables, with the
 //     charge deposit of the new particles fused;
@@ -41,173 +41,223 @@ __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
 
-// Edge reconstruction of the entries below 0 of F[0..N] (Appendix C): with k0 the largest
-// index where F < 0, a ramp (k - k_-) dF on [k_-, k_+) (zero below) whose slope keeps the sum
-// of F below k_+ (the histogram's first moment); the range grows (k_- down, then k_+ up with
-// k_- back at k0 - 1) until 0 <= (k_+ - k_- - 1) dF <= F[k_+]. Returns 1 if none exists.
-__device__ int edge_low(int N, double* F)
+// Reconstruction of a CDF row F[0..N] (Appendix C) by one warp, the row in shared memory. Each
+// step tests candidate ranges in a fixed order and keeps the first that passes; the warp tests
+// up to 32 candidates at once, each with exactly the operations (each rounded separately) of
+// the serial test, and keeps the first passing one in the serial order, so the result is that
+// of the serial procedure bit for bit. The sums S that the tests need are running sums, left to
+// right; lane 0 extends them one candidate at a time into the warp's slots Sc[0..31].
+constexpr unsigned kFull = 0xffffffffu;
+
+// Smallest k in [from, to) with F[k] >= x, or to.
+__device__ __forceinline__ int warp_first_geq(const double* F, int from, int to, double x, int lane)
 {
-    int k0 = -1;
-    for (int k = N; k >= 0; --k)
-        if (F[k] < 0.0) {
-            k0 = k;
-            break;
+    for (int base = from; base < to; base += 32) {
+        const int k = base + lane;
+        const unsigned m = __ballot_sync(kFull, k < to && F[k] >= x);
+        if (m) return base + __ffs(m) - 1;
+    }
+    return to;
+}
+
+// Largest k in [0, top] with F[k] <= x, or -1.
+__device__ __forceinline__ int warp_last_leq(const double* F, int top, double x, int lane)
+{
+    for (; top >= 0; top -= 32) {
+        const int k = top - lane;
+        const unsigned m = __ballot_sync(kFull, k >= 0 && F[k] <= x);
+        if (m) return top - (__ffs(m) - 1);
+    }
+    return -1;
+}
+
+// Largest k in [0, top] with F[k] < 0, or -1.
+__device__ __forceinline__ int warp_last_negative(const double* F, int top, int lane)
+{
+    for (; top >= 0; top -= 32) {
+        const int k = top - lane;
+        const unsigned m = __ballot_sync(kFull, k >= 0 && F[k] < 0.0);
+        if (m) return top - (__ffs(m) - 1);
+    }
+    return -1;
+}
+
+// Smallest k in [from, N) with F[k] > F[k + 1], or -1.
+__device__ __forceinline__ int warp_first_descent(const double* F, int from, int N, int lane)
+{
+    for (int base = from; base < N; base += 32) {
+        const int k = base + lane;
+        const unsigned m = __ballot_sync(kFull, k < N && F[k] > F[k + 1]);
+        if (m) return base + __ffs(m) - 1;
+    }
+    return -1;
+}
+
+// First index of the minimum of F over [from, to].
+__device__ __forceinline__ int warp_argmin(const double* F, int from, int to, int lane)
+{
+    int best = -1;
+    double bv = 0.0;
+    for (int k = from + lane; k <= to; k += 32) {
+        const double f = F[k];
+        if (best < 0 || f < bv) {
+            best = k;
+            bv = f;
         }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const int ob = __shfl_xor_sync(kFull, best, o);
+        const double ov = __shfl_xor_sync(kFull, bv, o);
+        if (ob >= 0 && (best < 0 || ov < bv || (ov == bv && ob < best))) {
+            best = ob;
+            bv = ov;
+        }
+    }
+    return best;
+}
+
+// Lane 0 extends the running sum S = F[s_k] + F[s_k + 1] + ... (left to right) up to each of the
+// cnt candidates k_+ = base, base + 1, ..., storing the sum below each in Sc[l].
+__device__ __forceinline__ void running_sums(const double* F, int base, int cnt, double& S, int& s_k, double* Sc,
+                                             int lane)
+{
+    if (lane == 0)
+        for (int l = 0; l < cnt; ++l) {
+            for (; s_k < base + l; ++s_k) S = add_(S, F[s_k]);
+            Sc[l] = S;
+        }
+    __syncwarp();
+}
+
+// Edge reconstruction of the entries below 0 of F (Appendix C): with k0 the largest index where
+// F < 0, a ramp (k - k_-) dF on [k_-, k_+) (zero below) whose slope keeps the sum of F below
+// k_+ (the histogram's first moment); the range grows (k_- down from k0 - 1 to 0, then k_+ up
+// with k_- back at k0 - 1) until 0 <= (k_+ - k_- - 1) dF <= F[k_+]. Returns 1 (on every lane)
+// if none exists.
+// The test's top (L - 1) dF is 2 S / L up to rounding (L = k_+ - k_-, S the sum below k_+),
+// smallest at k_- = 0: where it clearly exceeds F[k_+] there (relative margin 1e-12, far
+// beyond the rounding) no k_- passes, and that k_+ is skipped without its scan.
+__device__ int edge_low_warp(int N, double* F, double* Sc, int lane)
+{
+    const int k0 = warp_last_negative(F, N, lane);
     if (k0 < 0) return 0;
-    // S = F[0] + ... + F[kp-1] summed left to right; it depends on kp only, so it is carried
-    // from one kp to the next (the same additions in the same order as summing afresh)
-    int s_kp = 0;
-    double S = 0.0;
-    // the admissibility test of the range [km, kp) with the operations of the printed rule
-    auto top_of = [&](int km, int kp, double& dF) {
+    const int hi = k0 - 1;  // first k_- of each scan
+    if (hi < 0) return 1;
+    auto top_of = [](double S, int km, int kp, double& dF) {
         const double L = (double)(kp - km);
         dF = div_(mul_(2.0, S), mul_(L, sub_(L, 1.0)));
         return mul_(sub_(L, 1.0), dF);
     };
-    // For each kp the procedure tries km = k0 - 1, k0 - 2, ..., 0 and takes the first that
-    // passes. top = (L - 1) dF is 2 S / L up to rounding (L = kp - km), monotone in km: for
-    // S > 0 it passes from some km down, for S < 0 nowhere, for S = 0 everywhere or nowhere. So
-    // the first passing km is found by bisection on the exact test and then confirmed by the
-    // test itself on its neighbours (2 S / L moves by a factor (L+1)/L >= 1 + 1/N per step, far
-    // beyond the rounding, so only neighbours of the threshold can disagree with the bisection):
-    // the same km as the linear scan, in O(log N) tests.
-    for (int kp = k0 + 1; kp <= N; ++kp) {
-        for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
-        const int hi = k0 - 1;  // first km tried
-        if (hi < 0) return 1;
-        double dF = 0.0;
-        int km = -1;
-        if (S > 0.0) {
-            // smallest L passing <=> largest km passing; test(km) is false for km above it
-            int lo_ok = -1, a = 0, b = hi;  // search the largest km in [0, hi] with the test true
-            double t0;
-            {
-                t0 = top_of(0, kp, dF);
-                if (t0 >= 0.0 && t0 <= F[kp]) lo_ok = 0;
+    double S = 0.0;  // lane 0: F[0] + ... + F[s_k - 1]
+    int s_k = 0;
+    for (int base = k0 + 1; base <= N; base += 32) {
+        const int cnt = min(32, N + 1 - base);
+        running_sums(F, base, cnt, S, s_k, Sc, lane);
+        // candidates k_+ = base + lane: can any k_- pass?
+        bool cand = false;
+        if (lane < cnt) {
+            const int kp = base + lane;
+            const double s = Sc[lane];
+            double dF;
+            if (s > 0.0) {
+                const double t0 = top_of(s, 0, kp, dF);
+                cand = (t0 >= 0.0 && t0 <= F[kp]) || !(t0 > F[kp] * (1.0 + 1e-12) + 1e-300);
+            } else if (s == 0.0) {
+                const double t = top_of(s, hi, kp, dF);
+                cand = t >= 0.0 && t <= F[kp];
             }
-            // km = 0 (the largest L) fails clearly: no km passes for this kp
-            if (lo_ok < 0 && t0 > F[kp] * (1.0 + 1e-12) + 1e-300) continue;
-            if (lo_ok == 0) {
-                while (a < b) {  // invariant: test(a) true
-                    const int m = (a + b + 1) >> 1;
-                    const double t = top_of(m, kp, dF);
-                    if (t >= 0.0 && t <= F[kp])
-                        a = m;
-                    else
-                        b = m - 1;
+        }
+        unsigned m = __ballot_sync(kFull, cand);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const int kp = base + l;
+            const double s = Sc[l];
+            // the scan k_- = hi, hi - 1, ..., 0: the first that passes
+            int km = -1;
+            for (int top = hi; top >= 0 && km < 0; top -= 32) {
+                const int k = top - lane;
+                bool ok = false;
+                if (k >= 0) {
+                    double dF;
+                    const double t = top_of(s, k, kp, dF);
+                    ok = t >= 0.0 && t <= F[kp];
                 }
-                // confirm with the scan order's own tests near the threshold
-                int start = a + 3 < hi ? a + 3 : hi;
-                for (int k = start; k >= 0; --k) {
-                    const double t = top_of(k, kp, dF);
-                    if (t >= 0.0 && t <= F[kp]) {
-                        km = k;
-                        break;
-                    }
-                }
-            } else {
-                // no km in [0, hi] passes by monotonicity; confirm on the last few of the scan
-                for (int k = (hi < 3 ? hi : 3); k >= 0; --k) {
-                    const double t = top_of(k, kp, dF);
-                    if (t >= 0.0 && t <= F[kp]) {
-                        km = k;
-                        break;
-                    }
-                }
+                const unsigned mk = __ballot_sync(kFull, ok);
+                if (mk) km = top - (__ffs(mk) - 1);
             }
-        } else if (S == 0.0) {
-            const double t = top_of(hi, kp, dF);
-            if (t >= 0.0 && t <= F[kp]) km = hi;
+            if (km >= 0) {
+                double dF;
+                top_of(s, km, kp, dF);
+                for (int k = lane; k < kp; k += 32) F[k] = k < km ? 0.0 : mul_((double)(k - km), dF);
+                __syncwarp();
+                return 0;
+            }
         }
-        if (km >= 0) {
-            top_of(km, kp, dF);
-            for (int k = 0; k < km; ++k) F[k] = 0.0;
-            for (int k = km; k < kp; ++k) F[k] = mul_((double)(k - km), dF);
-            return 0;
-        }
+        __syncwarp();  // Sc is rewritten by the next chunk
     }
     return 1;
 }
 
-// Interior reconstruction from the low indices (Appendix C): at the first descent k0, k1 the
-// first later index with F[k1] >= F[k0], k_+ the first minimum on (k0, k1], k_- the last
-// earlier index with F <= F[k_+]; a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) keeping the sum
-// of F over [k_-, k_+); k_+ grows until dF >= 0 and the ramp ends at or below F[k_+]. A
-// descent with no admissible range is filled by a running max and 1 is returned.
-__device__ int interior_fwd(int N, double* F)
+// Interior reconstruction from the low indices (Appendix C), descent after descent: at the
+// first descent k0 (F[k0] > F[k0 + 1]; the search resumes at the previous k_-), k1 is the first
+// later index with F[k1] >= F[k0] (or N), k_+ the first minimum on (k0, k1], k_- the last
+// earlier index with F <= F[k_+] (or 0); a ramp F[k_-] + (k - k_-) dF on (k_-, k_+) keeps the
+// sum of F over [k_-, k_+); k_+ grows until dF >= 0 and the ramp ends at or below F[k_+]. A
+// descent with no admissible range is filled by a running max and 1 is returned (on every lane).
+__device__ int interior_fwd_warp(int N, double* F, double* Sc, int lane)
 {
     int bad = 0, start = 0;
     for (;;) {
-        int k0 = -1;
-        for (int k = start; k < N; ++k)
-            if (F[k] > F[k + 1]) {
-                k0 = k;
-                break;
-            }
+        const int k0 = warp_first_descent(F, start, N, lane);
         if (k0 < 0) return bad;
-        int k1 = k0 + 1;
-        while (k1 < N && F[k1] < F[k0]) ++k1;
-        int kp = k0 + 1;
-        for (int k = k0 + 1; k <= k1; ++k)
-            if (F[k] < F[kp]) kp = k;
-        int km = 0;
-        for (int k = k0 - 1; k >= 0; --k)
-            if (F[k] <= F[kp]) {
-                km = k;
-                break;
+        const int k1 = warp_first_geq(F, k0 + 1, N, F[k0], lane);
+        const int kmin = warp_argmin(F, k0 + 1, k1, lane);
+        const int kl = warp_last_leq(F, k0 - 1, F[kmin], lane);
+        const int km = kl < 0 ? 0 : kl;
+        const double Fkm = F[km];
+        double S = 0.0;  // lane 0: F[km] + ... + F[s_k - 1]
+        int s_k = km;
+        int found = -1;
+        double dF_found = 0.0;
+        for (int base = kmin, chunk = 8; base <= N && found < 0; base += chunk, chunk = 32) {
+            const int cnt = min(chunk, N + 1 - base);
+            running_sums(F, base, cnt, S, s_k, Sc, lane);
+            bool ok = false;
+            double dF = 0.0;
+            if (lane < cnt) {
+                const int kp = base + lane;
+                const double L = (double)(kp - km);
+                dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(Sc[lane], L), Fkm));
+                const double end = add_(Fkm, mul_(sub_(L, 1.0), dF));
+                ok = dF >= 0.0 && end <= F[kp];
             }
-        bool done = false;
-        double S = 0.0;  // F[km] + ... + F[kp-1], left to right, extended as kp grows
-        int s_kp = km;
-        for (; kp <= N; ++kp) {
-            for (; s_kp < kp; ++s_kp) S = add_(S, F[s_kp]);
-            const double L = (double)(kp - km);
-            const double dF = mul_(div_(2.0, sub_(L, 1.0)), sub_(div_(S, L), F[km]));
-            const double end = add_(F[km], mul_(sub_(L, 1.0), dF));
-            if (dF >= 0.0 && end <= F[kp]) {
-                for (int k = km + 1; k < kp; ++k) F[k] = add_(F[km], mul_((double)(k - km), dF));
-                done = true;
-                break;
+            const unsigned m = __ballot_sync(kFull, ok);
+            if (m) {
+                const int l = __ffs(m) - 1;
+                found = base + l;
+                dF_found = __shfl_sync(kFull, dF, l);
             }
+            __syncwarp();  // Sc is rewritten by the next chunk
         }
-        if (!done) {
+        if (found >= 0) {
+            for (int k = km + 1 + lane; k < found; k += 32) F[k] = add_(Fkm, mul_((double)(k - km), dF_found));
+        } else {
             bad = 1;
-            for (int k = k0 + 1; k <= N; ++k)
-                if (F[k] < F[k - 1]) F[k] = F[k - 1];
+            if (lane == 0)
+                for (int k = k0 + 1; k <= N; ++k)
+                    if (F[k] < F[k - 1]) F[k] = F[k - 1];
         }
+        __syncwarp();
         start = km;
     }
 }
 
-__device__ __forceinline__ void mirror(int N, const double* F, double* G)
+// G[k] = 1 - F[N - k] over the warp.
+__device__ __forceinline__ void mirror_warp(int N, const double* F, double* G, int lane)
 {
-    for (int k = 0; k <= N; ++k) G[k] = sub_(1.0, F[N - k]);
-}
-
-// Reconstruction of one CDF row F[0..N] (Appendix C), in three parts so that the two
-// interior passes, which are independent, can run on two lanes: reconstruct_edges fixes both
-// edges of F (clamped if an edge had no admissible range) and leaves P = F and G = mirror(F);
-// interior_fwd then runs on P and on G; reconstruct_join sets F = (P + mirror(G)) / 2.
-__device__ int reconstruct_edges(int N, double* F, double* G, double* P)
-{
-    int bad = 0;
-    F[0] = 0.0;
-    F[N] = 1.0;
-    bad |= edge_low(N, F);
-    mirror(N, F, G);
-    bad |= edge_low(N, G);
-    mirror(N, G, F);
-    if (bad)
-        for (int k = 0; k <= N; ++k) F[k] = F[k] < 0.0 ? 0.0 : (F[k] > 1.0 ? 1.0 : F[k]);
-    for (int k = 0; k <= N; ++k) P[k] = F[k];
-    mirror(N, F, G);
-    return bad;
-}
-
-__device__ void reconstruct_join(int N, double* F, const double* G, const double* P)
-{
-    mirror(N, G, F);
-    for (int k = 0; k <= N; ++k) F[k] = mul_(0.5, add_(P[k], F[k]));
+    for (int k = lane; k <= N; k += 32) G[k] = sub_(1.0, F[N - k]);
+    __syncwarp();
 }
 
 }  // namespace
@@ -216,67 +266,85 @@ __device__ void reconstruct_join(int N, double* F, const double* G, const double
 namespace pe {
 namespace {
 
-// Lifting tables, per bin (one thread per bin, up to 32 bins per block so the bins spread over
-// the SMs): the raw mass, the reconstructed FP64 CDF row (uniform where the raw mass is not
-// positive), and the FP32 sampling row used by the particle loader: F[0..nv], the inverse
-// cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells' relative density
-// slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1]. The reconstruction, whose
-// loops reread the row many times, works on three rows per thread in shared memory.
-__global__ void __launch_bounds__(64) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
-                                              double* __restrict__ mass, double* __restrict__ cdf,
-                                              float* __restrict__ table, int32_t* __restrict__ flags)
+// Lifting tables, one warp per bin: the raw mass, the reconstructed FP64 CDF row (uniform
+// where the raw mass is not positive), and the FP32 sampling row used by the particle loader:
+// F[0..nv], the inverse cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells'
+// relative density slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1].
+// The reconstruction (Appendix C) works on three rows per warp in shared memory (plus 32 slots
+// of running sums): the running sum of the masses is one serial chain (lane 0, left to right);
+// the divisions, mirrors, searches, candidate tests and stores are spread over the lanes, every
+// element getting the FP64 operations (each rounded separately) of a serial host evaluation,
+// so the CDF rows are reproducible bit for bit.
+__global__ void __launch_bounds__(128) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
+                                               double* __restrict__ mass, double* __restrict__ cdf,
+                                               float* __restrict__ table, int32_t* __restrict__ flags)
 {
     extern __shared__ double rows[];
-    // two lanes per bin (neighbours in one warp): lane 0 does the serial parts, the two
-    // interior passes run one per lane
-    const int half = threadIdx.x & 1, local = threadIdx.x >> 1;
-    const int i = blockIdx.x * (blockDim.x >> 1) + local;
-    const bool valid = i < nxc;
-    double* F = rows + (size_t)local * 3 * (nv + 1);
-    double* G = F + nv + 1;
-    double* Pr = G + nv + 1;
-    int bad = 0, positive = 0;
-    if (valid && half == 0) {
-        const double* h = H + (size_t)i * nv;
-        double s = 0.0;
-        for (int j = 0; j < nv; ++j) s = add_(s, h[j]);
-        mass[i] = s;
-        if (s > 0.0) {
-            positive = 1;
-            double r = 0.0;
-            F[0] = 0.0;
-            for (int j = 0; j < nv; ++j) {
-                r = add_(r, h[j]);
-                F[j + 1] = div_(r, s);
-            }
-            bad = reconstruct_edges(nv, F, G, Pr);
-        } else {
-            for (int j = 0; j <= nv; ++j) F[j] = div_((double)j, (double)nv);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int i = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= nxc) return;  // whole warps
+    const int N = nv;
+    double* F = rows + (size_t)wib * (3 * (N + 1) + 32);
+    double* G = F + N + 1;
+    double* P = G + N + 1;
+    double* Sc = P + N + 1;
+    const double* h = H + (size_t)i * nv;
+    for (int j = lane; j < nv; j += 32) P[j] = h[j];
+    __syncwarp();
+    // running sum r_j = h_0 + ... + h_j from 0.0, left to right; its last value is the mass
+    double s = 0.0;
+    if (lane == 0) {
+        double r = 0.0;
+        for (int j = 0; j < nv; ++j) {
+            r = add_(r, P[j]);
+            F[j + 1] = r;
         }
+        s = r;
+        mass[i] = s;
     }
-    // the lanes of this warp that exist (blocks smaller than a warp for wide rows; the block
-    // size is even, so both lanes of a pair exist)
-    const int wfirst = threadIdx.x & ~31, wlanes = min(32, (int)blockDim.x - wfirst);
-    const unsigned wmask = wlanes == 32 ? 0xffffffffu : ((1u << wlanes) - 1u);
-    __syncwarp(wmask);
-    positive = __shfl_sync(wmask, positive, (threadIdx.x & 31) & ~1);
-    if (valid && positive) bad |= interior_fwd(nv, half == 0 ? Pr : G);
-    __syncwarp(wmask);
-    bad |= __shfl_xor_sync(wmask, bad, 1);
-    if (!valid || half != 0) return;
-    if (positive) {
-        reconstruct_join(nv, F, G, Pr);
-        if (bad && flags) atomicOr(flags, 1);
+    s = __shfl_sync(kFull, s, 0);
+    __syncwarp();
+    int bad = 0;
+    if (s > 0.0) {
+        for (int k = lane; k <= N; k += 32) F[k] = k == 0 ? 0.0 : (k == N ? 1.0 : div_(F[k], s));
+        __syncwarp();
+        // edges: the low one, then the high one as the low edge of the mirror
+        bad |= edge_low_warp(N, F, Sc, lane);
+        mirror_warp(N, F, G, lane);
+        bad |= edge_low_warp(N, G, Sc, lane);
+        mirror_warp(N, G, F, lane);
+        for (int k = lane; k <= N; k += 32) {
+            double f = F[k];
+            if (bad) f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+            F[k] = f;
+            P[k] = f;
+        }
+        __syncwarp();
+        mirror_warp(N, F, G, lane);
+        // interior: forward on P, forward on the mirror G (the high indices), then the mean
+        bad |= interior_fwd_warp(N, P, Sc, lane);
+        bad |= interior_fwd_warp(N, G, Sc, lane);
+        for (int k = lane; k <= N; k += 32) F[k] = mul_(0.5, add_(P[k], sub_(1.0, G[N - k])));
+        __syncwarp();
+        if (bad && lane == 0 && flags) atomicOr(flags, 1);
+    } else {
+        for (int k = lane; k <= N; k += 32) F[k] = div_((double)k, (double)nv);
+        __syncwarp();
     }
     double* out = cdf + (size_t)i * (nv + 1);
-    for (int k = 0; k <= nv; ++k) out[k] = F[k];
     float* T = table + (size_t)i * (3 * nv + 1);
-    for (int k = 0; k <= nv; ++k) T[k] = (float)F[k];
-    for (int k = 0; k < nv; ++k) {
+    for (int k = lane; k <= N; k += 32) {
+        out[k] = F[k];
+        T[k] = (float)F[k];
+    }
+    // sampling rows: one FP64 reciprocal per cell (the slope's division by 4 p_k as a product
+    // with it; both are rounded to FP32)
+    for (int k = lane; k < nv; k += 32) {
         const double p = F[k + 1] - F[k];
         const double pl = k > 0 ? F[k] - F[k - 1] : 0.0, pr = k + 1 < nv ? F[k + 2] - F[k + 1] : 0.0;
-        const double sg = p > 0.0 ? (pr - pl) / (4.0 * p) : 0.0;
-        T[nv + 1 + k] = p > 0.0 ? (float)(1.0 / p) : 0.0f;
+        const double r = p > 0.0 ? 1.0 / p : 0.0;
+        const double sg = (pr - pl) * (0.25 * r);
+        T[nv + 1 + k] = (float)r;
         T[2 * nv + 1 + k] = (float)(sg > 1.0 ? 1.0 : (sg < -1.0 ? -1.0 : sg));
     }
 }
@@ -815,15 +883,16 @@ extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_
     if (!H || !mass || !cdf || !table || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
-    // three FP64 rows of n_v + 1 per bin, two threads per bin. The FP64 pipe of an SM is the
-    // bound (the divisions of the CDF and of the sampling rows), so few bins per block spread
-    // the bins over many SMs: 4 per block (fewer for wide rows, <= 192 KB)
-    const size_t row3 = 3 * sizeof(double) * ((size_t)n_v + 1);
-    int per_block = (int)std::min<size_t>(4, (size_t)(192 * 1024) / row3);
+    // three FP64 rows of n_v + 1 and 32 running sums per bin, one warp per bin. The serial
+    // chains (running sums) and the FP64 divisions set the time, so the bins spread over all
+    // SMs: about two warps per SM, 1 to 4 per block (fewer for wide rows, <= 192 KB)
+    const size_t row3 = sizeof(double) * (3 * ((size_t)n_v + 1) + 32);
+    int per_block = std::max(1, std::min(4, nxc / (2 * sm_count())));
+    per_block = (int)std::min<size_t>((size_t)per_block, (size_t)(192 * 1024) / row3);
     if (per_block < 1) return PE_EINVAL;
     const size_t smem = row3 * (size_t)per_block;
     if (ensure_smem((const void*)k_ps_cdf, smem) != PE_OK) return PE_ECUDA;
-    k_ps_cdf<<<(nxc + per_block - 1) / per_block, 2 * per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
+    k_ps_cdf<<<(nxc + per_block - 1) / per_block, 32 * per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
     k_ps_mass<<<1, 1024, 0, s>>>(nxc, mass);
     return launch_status(2);
 }
