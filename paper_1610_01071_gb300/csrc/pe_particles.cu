@@ -582,7 +582,7 @@ struct LoadParams {
     int64_t chunk;
     uint32_t ppc;
     int ncell, mask;
-    float inv_ppc, two_ppc;
+    float inv_ppc, two_ppc, inv_two_ppc;
     const float* prof_n;
     const float* prof_u;
     float v_th, wscale;
@@ -601,9 +601,16 @@ __device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c
         const uint32_t k = i & (P.ppc - 1u);
         i = (i & ~(P.ppc - 1u)) | (__brev(k) >> (32 - P.log2ppc));
     }
-    const uint32_t j = i % P.ppc;
-    c = (int)(i / P.ppc);
-    th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    uint32_t j;
+    if (P.log2ppc >= 0) {  // ppc = 2^m: shifts, and theta scaled by the exact 1 / (2 ppc)
+        j = i & (P.ppc - 1u);
+        c = (int)(i >> P.log2ppc);
+        th = (float)(2u * j + 1u) * P.inv_two_ppc;
+    } else {
+        j = i % P.ppc;
+        c = (int)(i / P.ppc);
+        th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    }
     const int c1 = (c + 1) & P.mask;
     const float n0 = __ldg(P.prof_n + c), n1 = __ldg(P.prof_n + c1);
     const float u0 = __ldg(P.prof_u + c), u1 = __ldg(P.prof_u + c1);
@@ -1222,6 +1229,7 @@ extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v
     P.mask = ncell - 1;
     P.inv_ppc = 1.0f / (float)P.ppc;
     P.two_ppc = 2.0f * (float)P.ppc;
+    P.inv_two_ppc = 1.0f / P.two_ppc;
     P.prof_n = prof_n;
     P.prof_u = prof_u;
     P.v_th = v_th;

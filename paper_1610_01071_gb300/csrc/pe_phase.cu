@@ -266,80 +266,94 @@ __device__ __forceinline__ void mirror_warp(int N, const double* F, double* G, i
 namespace pe {
 namespace {
 
-// Lifting tables, one warp per bin: the raw mass, the reconstructed FP64 CDF row (uniform
+// Synchronises the two warps of bin slot q of the block (named barrier 1 + q, 64 threads).
+__device__ __forceinline__ void pair_sync(int q)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
+}
+
+// Lifting tables, two warps per bin: the raw mass, the reconstructed FP64 CDF row (uniform
 // where the raw mass is not positive), and the FP32 sampling row used by the particle loader:
 // F[0..nv], the inverse cell masses 1 / (F[k+1] - F[k]) (0 for an empty cell) and the cells'
 // relative density slopes sigma_k = (p_{k+1} - p_{k-1}) / (4 p_k) clamped to [-1, 1].
-// The reconstruction (Appendix C) works on three rows per warp in shared memory (plus 32 slots
-// of running sums): the running sum of the masses is one serial chain (lane 0, left to right);
-// the divisions, mirrors, searches, candidate tests and stores are spread over the lanes, every
-// element getting the FP64 operations (each rounded separately) of a serial host evaluation,
-// so the CDF rows are reproducible bit for bit.
-__global__ void __launch_bounds__(128) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
+// The reconstruction (Appendix C) works on three rows per bin in shared memory (plus 32 slots
+// of running sums per warp): the running sum of the masses is one serial chain (lane 0 of the
+// first warp, left to right) and the edges are fixed by the first warp; the two interior
+// passes (on P and on the mirror G) run one per warp; the divisions, mirrors, searches,
+// candidate tests and stores are spread over the lanes. Every element gets the FP64 operations
+// (each rounded separately) of a serial host evaluation, so the CDF rows are reproducible bit
+// for bit.
+__global__ void __launch_bounds__(256) k_ps_cdf(const double* __restrict__ H, int nxc, int nv,
                                                double* __restrict__ mass, double* __restrict__ cdf,
                                                float* __restrict__ table, int32_t* __restrict__ flags)
 {
     extern __shared__ double rows[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int i = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (i >= nxc) return;  // whole warps
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 6, half = (threadIdx.x >> 5) & 1;
+    const int t64 = threadIdx.x & 63;
+    const int i = blockIdx.x * (blockDim.x >> 6) + q;
+    if (i >= nxc) return;  // whole pairs of warps
     const int N = nv;
-    double* F = rows + (size_t)wib * (3 * (N + 1) + 32);
+    double* F = rows + (size_t)q * (3 * (N + 1) + 66);
     double* G = F + N + 1;
     double* P = G + N + 1;
-    double* Sc = P + N + 1;
+    double* Sc = P + N + 1 + 32 * half;        // this warp's running sums
+    double* shared_s = P + N + 1 + 64;         // the mass, for the second warp
+    int* shared_bad = reinterpret_cast<int*>(shared_s + 1);
     const double* h = H + (size_t)i * nv;
-    for (int j = lane; j < nv; j += 32) P[j] = h[j];
-    __syncwarp();
+    for (int j = t64; j < nv; j += 64) P[j] = h[j];
+    if (t64 == 0) *shared_bad = 0;
+    pair_sync(q);
     // running sum r_j = h_0 + ... + h_j from 0.0, left to right; its last value is the mass
-    double s = 0.0;
-    if (lane == 0) {
+    if (t64 == 0) {
         double r = 0.0;
         for (int j = 0; j < nv; ++j) {
             r = add_(r, P[j]);
             F[j + 1] = r;
         }
-        s = r;
-        mass[i] = s;
+        *shared_s = r;
+        mass[i] = r;
     }
-    s = __shfl_sync(kFull, s, 0);
-    __syncwarp();
-    int bad = 0;
+    pair_sync(q);
+    const double s = *shared_s;
     if (s > 0.0) {
-        for (int k = lane; k <= N; k += 32) F[k] = k == 0 ? 0.0 : (k == N ? 1.0 : div_(F[k], s));
-        __syncwarp();
-        // edges: the low one, then the high one as the low edge of the mirror
-        bad |= edge_low_warp(N, F, Sc, lane);
-        mirror_warp(N, F, G, lane);
-        bad |= edge_low_warp(N, G, Sc, lane);
-        mirror_warp(N, G, F, lane);
-        for (int k = lane; k <= N; k += 32) {
-            double f = F[k];
-            if (bad) f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
-            F[k] = f;
-            P[k] = f;
+        for (int k = t64; k <= N; k += 64) F[k] = k == 0 ? 0.0 : (k == N ? 1.0 : div_(F[k], s));
+        pair_sync(q);
+        if (half == 0) {
+            // edges: the low one, then the high one as the low edge of the mirror
+            int bad = edge_low_warp(N, F, Sc, lane);
+            mirror_warp(N, F, G, lane);
+            bad |= edge_low_warp(N, G, Sc, lane);
+            mirror_warp(N, G, F, lane);
+            for (int k = lane; k <= N; k += 32) {
+                double f = F[k];
+                if (bad) f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+                F[k] = f;
+                P[k] = f;
+            }
+            __syncwarp();
+            mirror_warp(N, F, G, lane);
+            if (bad && lane == 0) *shared_bad = 1;
         }
-        __syncwarp();
-        mirror_warp(N, F, G, lane);
-        // interior: forward on P, forward on the mirror G (the high indices), then the mean
-        bad |= interior_fwd_warp(N, P, Sc, lane);
-        bad |= interior_fwd_warp(N, G, Sc, lane);
-        for (int k = lane; k <= N; k += 32) F[k] = mul_(0.5, add_(P[k], sub_(1.0, G[N - k])));
-        __syncwarp();
-        if (bad && lane == 0 && flags) atomicOr(flags, 1);
+        pair_sync(q);
+        // interior: forward on P (first warp) and on the mirror G (the high indices, second warp)
+        const int bad = interior_fwd_warp(N, half == 0 ? P : G, Sc, lane);
+        if (bad && lane == 0) atomicOr(shared_bad, 1);
+        pair_sync(q);
+        for (int k = t64; k <= N; k += 64) F[k] = mul_(0.5, add_(P[k], sub_(1.0, G[N - k])));
+        if (t64 == 0 && *shared_bad && flags) atomicOr(flags, 1);
     } else {
-        for (int k = lane; k <= N; k += 32) F[k] = div_((double)k, (double)nv);
-        __syncwarp();
+        for (int k = t64; k <= N; k += 64) F[k] = div_((double)k, (double)nv);
     }
+    pair_sync(q);
     double* out = cdf + (size_t)i * (nv + 1);
     float* T = table + (size_t)i * (3 * nv + 1);
-    for (int k = lane; k <= N; k += 32) {
+    for (int k = t64; k <= N; k += 64) {
         out[k] = F[k];
         T[k] = (float)F[k];
     }
     // sampling rows: one FP64 reciprocal per cell (the slope's division by 4 p_k as a product
     // with it; both are rounded to FP32)
-    for (int k = lane; k < nv; k += 32) {
+    for (int k = t64; k < nv; k += 64) {
         const double p = F[k + 1] - F[k];
         const double pl = k > 0 ? F[k] - F[k - 1] : 0.0, pr = k + 1 < nv ? F[k + 2] - F[k + 1] : 0.0;
         const double r = p > 0.0 ? 1.0 / p : 0.0;
@@ -374,7 +388,7 @@ struct PSLoad {
     int64_t n, chunk;
     uint32_t ppc;
     int log2ppc, ncell, mask, bin_shift, nv;
-    float per_node, vmin, dv, inv_ppc, two_ppc;
+    float per_node, vmin, dv, inv_ppc, two_ppc, inv_two_ppc;
     const double* mass;
     const float* table;
     const float* node_dens;  // wavelet form: per fine node density and sampling row (else null)
@@ -445,9 +459,16 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns
         const uint32_t k = i & (P.ppc - 1u);
         i = (i & ~(P.ppc - 1u)) | (__brev(k) >> (32 - P.log2ppc));
     }
-    const uint32_t j = i % P.ppc;
-    c = (int)(i / P.ppc);
-    th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    uint32_t j;
+    if (P.log2ppc >= 0) {  // ppc = 2^m: shifts, and theta scaled by the exact 1 / (2 ppc)
+        j = i & (P.ppc - 1u);
+        c = (int)(i >> P.log2ppc);
+        th = (float)(2u * j + 1u) * P.inv_two_ppc;
+    } else {
+        j = i % P.ppc;
+        c = (int)(i / P.ppc);
+        th = __fdiv_rn((float)(2u * j + 1u), P.two_ppc);
+    }
     if (P.node_dens) {
         // wavelet form: the fine nodes c and c + 1 carry their own density and sampling row
         // (k_ps_node_tables); weight and velocity are linear in x between them
@@ -883,16 +904,16 @@ extern "C" PE_API int pe_ps_lift_tables(const double* H, int32_t nxc, int32_t n_
     if (!H || !mass || !cdf || !table || nxc < 1 || n_v < 1 || n_v > 1024) return PE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags && cudaMemsetAsync(flags, 0, sizeof(int32_t), s) != cudaSuccess) return PE_ECUDA;
-    // three FP64 rows of n_v + 1 and 32 running sums per bin, one warp per bin. The serial
-    // chains (running sums) and the FP64 divisions set the time, so the bins spread over all
-    // SMs: about two warps per SM, 1 to 4 per block (fewer for wide rows, <= 192 KB)
-    const size_t row3 = sizeof(double) * (3 * ((size_t)n_v + 1) + 32);
-    int per_block = std::max(1, std::min(4, nxc / (2 * sm_count())));
+    // three FP64 rows of n_v + 1, 2 x 32 running sums and the mass per bin, two warps per bin.
+    // The serial chains (running sums) and the FP64 divisions set the time, so the bins spread
+    // over all SMs: about one bin per SM, 1 to 4 per block (fewer for wide rows, <= 192 KB)
+    const size_t row3 = sizeof(double) * (3 * ((size_t)n_v + 1) + 66);
+    int per_block = std::max(1, std::min(4, nxc / sm_count()));
     per_block = (int)std::min<size_t>((size_t)per_block, (size_t)(192 * 1024) / row3);
     if (per_block < 1) return PE_EINVAL;
     const size_t smem = row3 * (size_t)per_block;
     if (ensure_smem((const void*)k_ps_cdf, smem) != PE_OK) return PE_ECUDA;
-    k_ps_cdf<<<(nxc + per_block - 1) / per_block, 32 * per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
+    k_ps_cdf<<<(nxc + per_block - 1) / per_block, 64 * per_block, smem, s>>>(H, nxc, n_v, mass, cdf, table, flags);
     k_ps_mass<<<1, 1024, 0, s>>>(nxc, mass);
     return launch_status(2);
 }
@@ -973,6 +994,7 @@ extern "C" PE_API int pe_ps_quiet_start(int32_t* cell, float* theta, float* v, f
     P.dv = (float)dv;
     P.inv_ppc = 1.0f / (float)P.ppc;
     P.two_ppc = 2.0f * (float)P.ppc;
+    P.inv_two_ppc = 1.0f / P.two_ppc;
     P.mass = mass;
     P.table = table;
     P.half = (uint32_t)(2147483648.0 / (double)n);
@@ -1032,6 +1054,7 @@ extern "C" PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float
     P.dv = (float)dv;
     P.inv_ppc = 1.0f / (float)P.ppc;
     P.two_ppc = 2.0f * (float)P.ppc;
+    P.inv_two_ppc = 1.0f / P.two_ppc;
     P.table = node_table;
     P.node_dens = node_dens;
     // a block's cells (chunks of <= 65536 particles) and the next node, within 48 KB
