@@ -60,7 +60,9 @@ std::vector<KernelInfo> g_smem_set, g_occ;
 
 int ensure_smem(const void* kernel, size_t smem)
 {
-    if (smem <= 48 * 1024) return PE_OK;
+    // below 48 KB less the kernel's static shared memory no attribute is needed; the static size
+    // is not known here, so every non-zero request goes through the per-kernel record
+    if (smem == 0) return PE_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
     std::lock_guard<std::mutex> lk(g_kmu);

@@ -81,6 +81,10 @@ struct ModeTraits {
     static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
     static constexpr bool tent = (MODE == kPushSamplePSW || MODE == kSamplePSW);
     static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS || tent);
+    // particle streams staged through shared memory (cp.async, one group ahead): the phase-space
+    // passes (three blocks an SM) and the deposit gain from it; the other passes, at four blocks
+    // an SM with their loads already in flight, run faster on direct loads and a larger L1
+    static constexpr bool stage = ps || MODE == kDeposit;
 };
 
 // Fixed-point value rn(x 2^s); records in *ovf whether it left the range |q| <= 2^23.
@@ -119,6 +123,27 @@ __device__ __forceinline__ float2 lds_f2(uint32_t a)
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
     return v;
 }
+
+__device__ __forceinline__ int4 lds_i4(uint32_t a)
+{
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// 16-byte asynchronous copy global -> shared (cached in L2 only) and its group controls: each
+// lane copies its own next group of particles and waits only for its own copies.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Staging of the particle streams: per warp two slots (the group being processed and the next
+// one, in flight), each holding the four arrays' 16-byte vectors of the 32 lanes.
+constexpr int kStageSlotBytes = 4 * 32 * 16;
+constexpr int kStageWarpBytes = 2 * kStageSlotBytes;
 
 // True when cell c + k (k = fl, an integer-valued float) lies between the walls,
 // [0, ncell - 1); NaN counts as outside.
@@ -379,6 +404,9 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         s = gps.bind(s, P.samp_n, ((c_first >> P.bin_shift) - P.ps_width / 2) & (nxc - 1), P.ps_width, nxc, P.nv);
         gps.zero();
     }
+    // this warp's staging slots, after the grids (16-byte aligned)
+    const uint32_t stage = ((smem_u32(s) + 15u) & ~15u) + (uint32_t)(threadIdx.x >> 5) * (uint32_t)kStageWarpBytes +
+                           16u * (uint32_t)(threadIdx.x & 31);
     if (kRho) grho.zero();
     if (kSamp) {
         gsn.zero();
@@ -412,13 +440,37 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     // one 16-byte group (four particles) per lane per iteration: a single inlined copy of the
     // particle step keeps the kernel small enough for the instruction cache. The loop bound is
     // the same for the whole warp (the deposit and sample windows are warp-uniform); lanes past
-    // the end of the slice process nothing.
-    for (int64_t gs = g0; gs < g1; gs += 32) {
+    // the end of the slice process nothing. Each lane's next group is copied to shared memory
+    // (cp.async) while the current one is processed, so the streams' latency overlaps the work;
+    // a slot is refilled one iteration after it was read (its values long in registers).
+    auto fetch = [&](int64_t g, uint32_t slot) {
+        cp_async16(slot, cell4 + g);
+        cp_async16(slot + 512u, th4 + g);
+        if (kNeedV) cp_async16(slot + 1024u, v4 + g);
+        cp_async16(slot + 1536u, w4 + g);
+    };
+    if (Tr::stage) {
+        if (g0 + lane < g1) fetch(g0 + lane, stage);
+        cp_async_commit();
+    }
+    uint32_t it = 0;
+    for (int64_t gs = g0; gs < g1; gs += 32, ++it) {
         const int64_t g = gs + lane;
         const bool act = g < g1;
         int4 ca = make_int4(0, 0, 0, 0);
         float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), va = ta, wa = ta;
-        if (act) {
+        if (Tr::stage) {
+            const uint32_t cur = stage + (it & 1u) * (uint32_t)kStageSlotBytes;
+            cp_async_wait_all();
+            if (act) {
+                ca = lds_i4(cur);
+                ta = lds_f4(cur + 512u);
+                if (kNeedV) va = lds_f4(cur + 1024u);
+                wa = lds_f4(cur + 1536u);
+            }
+            if (g + 32 < g1) fetch(g + 32, stage + ((it + 1u) & 1u) * (uint32_t)kStageSlotBytes);
+            cp_async_commit();
+        } else if (act) {
             ca = cell4[g];
             ta = th4[g];
             if (kNeedV) va = v4[g];
@@ -911,12 +963,20 @@ int particle_grid(const void* kernel, int block, size_t smem, int64_t n, int64_t
 }
 
 // Rows of the block-private phase-space window: up to kPSWindowBins, halved while the window
-// (three 32-bit digit counters per cell) would exceed 48 KB.
+// (three 32-bit digit counters per cell) would exceed 24 KB, so that three blocks and their
+// staging slots fit on an SM (targets outside the window go to the global histogram).
 static int ps_window_rows(int nxc, int nv)
 {
     int w = nxc <= kPSWindowBins ? nxc : kPSWindowBins;
-    while (w > 1 && (size_t)3 * sizeof(uint32_t) * (size_t)w * (size_t)nv > 48 * 1024) w >>= 1;
+    while (w > 1 && (size_t)3 * sizeof(uint32_t) * (size_t)w * (size_t)nv > 24 * 1024) w >>= 1;
     return w;
+}
+
+// Shared memory of a particle pass: the grids (smem bytes), rounded up to 16 bytes, then the
+// staging slots of the block's warps (passes that stage their streams).
+static size_t with_stage(size_t smem, int block, bool staged)
+{
+    return staged ? ((smem + 15) & ~size_t(15)) + (size_t)(block / 32) * kStageWarpBytes : smem;
 }
 
 template <int MODE>
@@ -947,6 +1007,7 @@ static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
     size_t smem = tab + kSmemGridWords * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) +
                   kBinGridWords * sizeof(uint32_t) * 2 * nb +
                   3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
+    smem = with_stage(smem, block, ModeTraits<MODE>::stage);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     const void* k = P.walls ? (const void*)k_particles<MODE, true> : (const void*)k_particles<MODE, false>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
@@ -1037,11 +1098,13 @@ void make_work_item(void* out, int r, int64_t begin, int64_t end)
 }
 
 // Shared memory of a batched launch: the field table, the deposit window (priv), the bins.
-static size_t batch_smem(int mode, int max_ncell, int max_nb, int priv)
+static size_t batch_smem(int mode, int max_ncell, int max_nb, int priv, int block)
 {
     const int rw = (mode != 1 && priv) ? (max_ncell <= kRhoWindowNodes ? max_ncell : kRhoWindowNodes) : 0;
-    return (mode == 2 ? 0 : sizeof(float4) * (size_t)kFieldTabNodes) + kSmemGridWords * sizeof(uint32_t) * (size_t)rw +
-           (mode == 2 ? 0 : kBinGridWords * sizeof(uint32_t) * 2 * (size_t)max_nb);
+    return with_stage((mode == 2 ? 0 : sizeof(float4) * (size_t)kFieldTabNodes) +
+                          kSmemGridWords * sizeof(uint32_t) * (size_t)rw +
+                          (mode == 2 ? 0 : kBinGridWords * sizeof(uint32_t) * 2 * (size_t)max_nb),
+                      block, mode == 2);
 }
 
 template <int MODE>
@@ -1063,7 +1126,7 @@ int launch_particles_batch(int mode, const void* descs, const void* items, int n
                            unsigned* counter, int max_ncell, int max_nb, int block, int priv, cudaStream_t s)
 {
     if (block != 128 && block != 256 && block != 512) return PE_EINVAL;
-    const size_t smem = batch_smem(mode, max_ncell, max_nb, priv);
+    const size_t smem = batch_smem(mode, max_ncell, max_nb, priv, block);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
     if (mode == 0) return launch_batch_mode<kPushSampleBinned>(descs, items, nitems, p, kick, counter, smem, block, priv, s);

@@ -364,18 +364,27 @@ __global__ void __launch_bounds__(256) k_ps_cdf(const double* __restrict__ H, in
 }
 
 // Negative masses clamped to 0, the others rescaled to keep the total (summed by one thread
-// in bin order, as the host evaluation does).
+// in bin order, as the host evaluation does). The masses are staged in shared memory a block
+// at a time, so the serial sums wait on FP64 adds only, not on global loads.
 __global__ void __launch_bounds__(1024) k_ps_mass(int nxc, double* __restrict__ mass)
 {
+    __shared__ double stage[1024];
     __shared__ double sscale;
-    if (threadIdx.x == 0) {
-        double tot = 0.0, pos = 0.0;
-        for (int i = 0; i < nxc; ++i) {
-            tot = add_(tot, mass[i]);
-            pos = add_(pos, mass[i] > 0.0 ? mass[i] : 0.0);
+    double tot = 0.0, pos = 0.0;
+    for (int i0 = 0; i0 < nxc; i0 += blockDim.x) {
+        const int n = min((int)blockDim.x, nxc - i0);
+        if ((int)threadIdx.x < n) stage[threadIdx.x] = mass[i0 + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < n; ++i) {
+                const double m = stage[i];
+                tot = add_(tot, m);
+                pos = add_(pos, m > 0.0 ? m : 0.0);
+            }
         }
-        sscale = pos > 0.0 ? div_(tot, pos) : 0.0;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) sscale = pos > 0.0 ? div_(tot, pos) : 0.0;
     __syncthreads();
     for (int i = threadIdx.x; i < nxc; i += blockDim.x) mass[i] = mass[i] > 0.0 ? mul_(mass[i], sscale) : 0.0;
 }
@@ -400,19 +409,69 @@ struct PSLoad {
     uint32_t* status;
 };
 
-// V = v_min + dv (k + t) on a bin's FP32 sampling row: k the first index with F[k+1] > b
-// (binary search; nv - 1 if none), t the position inside the cell where the cell's linear
-// density reaches the fraction r = (b - F[k]) / (F[k+1] - F[k]) of its mass.
-__device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int nv, float b, float vmin, float dv)
+template <bool LDG>
+__device__ __forceinline__ float ld_row(const float* p)
 {
-    int lo = 0, hi = nv - 1;
+    if (LDG) return __ldg(p);
+    return *p;
+}
+
+// First index k in [lo, nv - 1] with T[k + 1] > b (nv - 1 if none), for a row T[0..nv] that is
+// non-decreasing, given that no index below lo qualifies (lo = 0 for a fresh search): the two
+// indices from lo are tried first (consecutive quantiles of a velocity-ordered cell land in the
+// same or the next cells), then the rest is bisected. The result is the full bisection's.
+template <bool LDG>
+__device__ __forceinline__ int cdf_search(const float* T, int nv, float b, int lo)
+{
+    int hi = nv - 1;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (lo < hi) {
+            if (ld_row<LDG>(T + lo + 1) > b) return lo;
+            ++lo;
+        }
+    }
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (__ldg(T + mid + 1) > b)
+        if (ld_row<LDG>(T + mid + 1) > b)
             hi = mid;
         else
             lo = mid + 1;
     }
+    return lo;
+}
+
+// Search state of one lane across its particles: the rows last searched, the indices found
+// and the quantile they were found for. A later search of the same row for a quantile at or
+// above it starts from the index found (no lower index qualifies, the row being
+// non-decreasing); any other search starts from 0.
+struct SearchHint {
+    const float* row0;
+    const float* row1;
+    int k0, k1;
+    float b;
+
+    __device__ __forceinline__ void reset()
+    {
+        row0 = row1 = nullptr;
+        k0 = k1 = 0;
+        b = 0.0f;
+    }
+    __device__ __forceinline__ int start(const float* T, float bq) const
+    {
+        if (bq < b) return 0;
+        return T == row0 ? k0 : (T == row1 ? k1 : 0);
+    }
+};
+
+// V = v_min + dv (k + t) on a bin's FP32 sampling row: k the first index with F[k+1] > b
+// (nv - 1 if none; cdf_search from lo0), t the position inside the cell where the cell's
+// linear density reaches the fraction r = (b - F[k]) / (F[k+1] - F[k]) of its mass.
+__device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int nv, float b, float vmin, float dv,
+                                               int lo0 = 0, int* found = nullptr)
+{
+    const int lo = cdf_search<true>(T, nv, b, lo0);
+    if (found) *found = lo;
     const float f0 = __ldg(T + lo), sl = __ldg(T + nv + 1 + lo), sg = __ldg(T + 2 * nv + 1 + lo);
     const float r = sl > 0.0f ? fminf(fmaxf((b - f0) * sl, 0.0f), 1.0f) : 0.5f;
     // linear density 1 + sigma (2t - 1) inside the cell: t solves t + sigma (t^2 - t) = r
@@ -430,16 +489,11 @@ __device__ __forceinline__ float cdf_inverse_f(const float* __restrict__ T, int 
 // restriction sample in velocity. FP32 (the particle precision) on tables built in FP64.
 // Inverse of a row with uniform density inside each cell (F[0..nv], then the inverse cell
 // masses): v_min + dv (k + r), k the first index with F[k+1] > b, r = (b - F[k]) / p_k.
-__device__ __forceinline__ float cdf_inverse_lin(const float* T, int nv, float b, float vmin, float dv)
+__device__ __forceinline__ float cdf_inverse_lin(const float* T, int nv, float b, float vmin, float dv, int lo0,
+                                                 int* found)
 {
-    int lo = 0, hi = nv - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (T[mid + 1] > b)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
+    const int lo = cdf_search<false>(T, nv, b, lo0);
+    *found = lo;
     const float f0 = T[lo], sl = T[nv + 1 + lo];
     const float r = sl > 0.0f ? fminf(fmaxf((b - f0) * sl, 0.0f), 1.0f) : 0.5f;
     return fmaf(dv, (float)lo + r, vmin);
@@ -452,8 +506,8 @@ struct NodeStage {
     int c_stage, n;
 };
 
-__device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns, uint32_t i, int& c, float& th,
-                                            float& vv, float& ww)
+__device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns, SearchHint& hint, uint32_t i,
+                                            int& c, float& th, float& vv, float& ww)
 {
     if (P.log2ppc > 0) {
         const uint32_t k = i & (P.ppc - 1u);
@@ -481,8 +535,10 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns
         const int r0 = (c - ns.c_stage) & P.mask, r1 = (c1 - ns.c_stage) & P.mask;
         const float* T0 = r0 < ns.n ? ns.rows + r0 * srow : P.table + (size_t)c * row;
         const float* T1 = r1 < ns.n ? ns.rows + r1 * srow : P.table + (size_t)c1 * row;
-        const float v0 = cdf_inverse_lin(T0, P.nv, b, P.vmin, P.dv);
-        const float v1 = cdf_inverse_lin(T1, P.nv, b, P.vmin, P.dv);
+        int k0, k1;
+        const float v0 = cdf_inverse_lin(T0, P.nv, b, P.vmin, P.dv, hint.start(T0, b), &k0);
+        const float v1 = cdf_inverse_lin(T1, P.nv, b, P.vmin, P.dv, hint.start(T1, b), &k1);
+        hint = SearchHint{T0, T1, k0, k1, b};
         vv = fmaf(th, v1 - v0, v0);
         return;
     }
@@ -514,8 +570,14 @@ __device__ __forceinline__ void ps_load_one(const PSLoad& P, const NodeStage& ns
     const uint32_t B = __brev(i) + P.half + P.shift;
     const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const int row = 3 * P.nv + 1;
-    const float v0 = cdf_inverse_f(P.table + (size_t)b0 * row, P.nv, b, P.vmin, P.dv);
-    const float v1 = (b1 == b0) ? v0 : cdf_inverse_f(P.table + (size_t)b1 * row, P.nv, b, P.vmin, P.dv);
+    const float* T0 = P.table + (size_t)b0 * row;
+    const float* T1 = P.table + (size_t)b1 * row;
+    int k0, k1;
+    const float v0 = cdf_inverse_f(T0, P.nv, b, P.vmin, P.dv, hint.start(T0, b), &k0);
+    float v1 = v0;
+    k1 = k0;
+    if (b1 != b0) v1 = cdf_inverse_f(T1, P.nv, b, P.vmin, P.dv, hint.start(T1, b), &k1);
+    hint = SearchHint{T0, T1, k0, k1, b};
     vv = fmaf(phi, v1 - v0, v0);
 }
 
@@ -553,14 +615,16 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     float4* th4 = reinterpret_cast<float4*>(P.theta);
     float4* v4 = reinterpret_cast<float4*>(P.v);
     float4* w4 = reinterpret_cast<float4*>(P.w);
+    SearchHint hint;
+    hint.reset();
     for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
         int4 c;
         float4 t, vv, ww;
         const uint32_t i0 = (uint32_t)(g << 2);
-        ps_load_one(P, ns, i0, c.x, t.x, vv.x, ww.x);
-        ps_load_one(P, ns, i0 + 1, c.y, t.y, vv.y, ww.y);
-        ps_load_one(P, ns, i0 + 2, c.z, t.z, vv.z, ww.z);
-        ps_load_one(P, ns, i0 + 3, c.w, t.w, vv.w, ww.w);
+        ps_load_one(P, ns, hint, i0, c.x, t.x, vv.x, ww.x);
+        ps_load_one(P, ns, hint, i0 + 1, c.y, t.y, vv.y, ww.y);
+        ps_load_one(P, ns, hint, i0 + 2, c.z, t.z, vv.z, ww.z);
+        ps_load_one(P, ns, hint, i0 + 3, c.w, t.w, vv.w, ww.w);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -575,7 +639,7 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         int c;
         float t, vv, ww;
-        ps_load_one(P, ns, (uint32_t)i, c, t, vv, ww);
+        ps_load_one(P, ns, hint, (uint32_t)i, c, t, vv, ww);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;
@@ -595,26 +659,33 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
 // mass[i1]) and its CDF the mixture (a0 F_i0 + a1 F_i1) / (a0 + a1). One block per fine node
 // writes the FP32 sampling row of cdf_inverse_f (CDF, inverse cell masses, zero slopes: the
 // density is uniform inside a velocity cell, Appendix C's lookup with linear interpolation),
-// evaluated in FP64, and the node density.
+// evaluated in FP64, and the node density. The mixture is scaled by one FP64 reciprocal of the
+// density per node (FP64 divisions are slow on this GPU) and each CDF value is formed once, in
+// shared memory, for both of its neighbouring cells; the inverse cell masses are FP32
+// reciprocals of the FP64 differences (both roundings are below the FP32 table's resolution).
 __global__ void __launch_bounds__(256) k_ps_node_tables(const double* __restrict__ mass, const double* __restrict__ cdf,
                                                         int nxc, int bin_shift, int nv, float* __restrict__ table,
                                                         float* __restrict__ dens)
 {
+    extern __shared__ double gs[];  // nv + 1 CDF values of this node
     const int j = blockIdx.x;
     const int i0 = j >> bin_shift, i1 = (i0 + 1) & (nxc - 1);
     const double phi = ldexp((double)(j & ((1 << bin_shift) - 1)), -bin_shift);
     const double a0 = (1.0 - phi) * mass[i0], a1 = phi * mass[i1], tot = a0 + a1;
+    const double inv = tot > 0.0 ? 1.0 / tot : 0.0, inv_nv = 1.0 / (double)nv;
     const double* F0 = cdf + (size_t)i0 * (nv + 1);
     const double* F1 = cdf + (size_t)i1 * (nv + 1);
     float* T = table + (size_t)j * (3 * nv + 1);
     for (int k = threadIdx.x; k <= nv; k += blockDim.x) {
-        const double g = tot > 0.0 ? (a0 * F0[k] + a1 * F1[k]) / tot : (double)k / nv;
+        const double g = tot > 0.0 ? (a0 * F0[k] + a1 * F1[k]) * inv : (double)k * inv_nv;
+        gs[k] = g;
         T[k] = (float)g;
-        if (k < nv) {
-            const double g1 = tot > 0.0 ? (a0 * F0[k + 1] + a1 * F1[k + 1]) / tot : (double)(k + 1) / nv;
-            T[nv + 1 + k] = g1 > g ? (float)(1.0 / (g1 - g)) : 0.0f;
-            T[2 * nv + 1 + k] = 0.0f;
-        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const double d = gs[k + 1] - gs[k];
+        T[nv + 1 + k] = d > 0.0 ? __frcp_rn((float)d) : 0.0f;
+        T[2 * nv + 1 + k] = 0.0f;
     }
     if (threadIdx.x == 0) dens[j] = (float)tot;
 }
@@ -1023,7 +1094,7 @@ extern "C" PE_API int pe_ps_node_tables(const double* mass, const double* cdf, i
     if (!mass || !cdf || !node_table || !node_dens || !is_pow2(ncell) || !is_pow2(nxc) || nxc > ncell || n_v < 1 ||
         n_v > 4096)
         return PE_EINVAL;
-    k_ps_node_tables<<<ncell, 256, 0, (cudaStream_t)stream>>>(mass, cdf, nxc, ilog2(ncell / nxc), n_v, node_table,
+    k_ps_node_tables<<<ncell, 256, sizeof(double) * ((size_t)n_v + 1), (cudaStream_t)stream>>>(mass, cdf, nxc, ilog2(ncell / nxc), n_v, node_table,
                                                               node_dens);
     return launch_status(1);
 }
