@@ -652,6 +652,92 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start(PSLoad P)
     if (dep) grho.flush();
 }
 
+// Wavelet-form loading when ppc = 2^m, m >= 2: the same slots, values and deposit as
+// k_ps_quiet_start on fine-node tables, with the work a lane's group of four slots shares done
+// once. The four slots lie in one cell c (ppc a multiple of four), so they share the nodes'
+// densities and sampling rows; their quantiles increase with the slot inside the cell (the
+// slot's bit-reversed position index gives the Hammersley point), so each row's search resumes
+// from the previous slot's index until the quantile wraps around.
+__device__ __forceinline__ const float* node_row(const PSLoad& P, const NodeStage& ns, int c)
+{
+    const int r = (c - ns.c_stage) & P.mask;
+    return r < ns.n ? ns.rows + r * (2 * P.nv + 1) : P.table + (size_t)c * (3 * P.nv + 1);
+}
+
+__global__ void __launch_bounds__(256) k_ps_quiet_start_nodes(PSLoad P)
+{
+    extern __shared__ uint32_t smem[];
+    int64_t begin, end;
+    block_chunk(P.n, P.chunk, &begin, &end);
+    const int m = P.log2ppc;
+    const int c_first = (begin < end) ? (int)((uint64_t)begin >> m) : 0;
+    SmemGrid grho{};
+    uint32_t* s = smem;
+    const bool dep = P.rho != nullptr;
+    if (dep) {
+        s = grho.bind(s, P.rho, P.rho_width < P.ncell ? ((c_first - 64) & P.mask) : 0, P.rho_width, P.mask);
+        grho.zero();
+    }
+    NodeStage ns{nullptr, 0, 0};
+    if (P.stage_rows > 0) {
+        float* st = reinterpret_cast<float*>(s);
+        const int rw = 2 * P.nv + 1;
+        for (int i = threadIdx.x; i < P.stage_rows * rw; i += blockDim.x) {
+            const int r = i / rw, k = i - r * rw;
+            st[i] = __ldg(P.table + (size_t)((c_first + r) & P.mask) * (3 * P.nv + 1) + k);
+        }
+        ns = NodeStage{st, c_first, P.stage_rows};
+    }
+    __syncthreads();
+    const int64_t gb0 = begin >> 2, gb1 = end >> 2;  // ppc >= 4 divides n: no ragged tail
+    int64_t g0, g1;
+    warp_groups(gb0, gb1, &g0, &g1);
+    LaneWindow lw;
+    lw.reset(((int)((uint64_t)(g0 << 2) >> m) - 1) & P.mask);
+    bool ovf = false;
+    int c_prev = -1;
+    int k0 = 0, k1 = 0;
+    float b_prev = 2.0f;
+    for (int64_t g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+        const uint32_t i0 = (uint32_t)(g << 2);
+        const int c = (int)(i0 >> m), c1 = (c + 1) & P.mask;
+        const uint32_t kin = i0 & (P.ppc - 1u);
+        const float d0 = __ldg(P.node_dens + c), d1 = __ldg(P.node_dens + c1);
+        const float* T0 = node_row(P, ns, c);
+        const float* T1 = node_row(P, ns, c1);
+        if (c != c_prev) {  // a new cell: the searches start over
+            c_prev = c;
+            b_prev = 2.0f;
+        }
+        float th[4], vq[4], wq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t j = __brev(kin + (uint32_t)q) >> (32 - m);
+            th[q] = (float)(2u * j + 1u) * P.inv_two_ppc;
+            wq[q] = fmaf(th[q], d1 - d0, d0) * P.inv_ppc;
+            const uint32_t B = __brev(((uint32_t)c << m) | j) + P.half + P.shift;
+            const float b = fmaf(__uint2float_rn(B), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+            if (b < b_prev) k0 = k1 = 0;  // the quantile wrapped (or a new cell)
+            b_prev = b;
+            const float v0 = cdf_inverse_lin(T0, P.nv, b, P.vmin, P.dv, k0, &k0);
+            const float v1 = cdf_inverse_lin(T1, P.nv, b, P.vmin, P.dv, k1, &k1);
+            vq[q] = fmaf(th[q], v1 - v0, v0);
+        }
+        reinterpret_cast<int4*>(P.cell)[g] = make_int4(c, c, c, c);
+        reinterpret_cast<float4*>(P.theta)[g] = make_float4(th[0], th[1], th[2], th[3]);
+        reinterpret_cast<float4*>(P.v)[g] = make_float4(vq[0], vq[1], vq[2], vq[3]);
+        reinterpret_cast<float4*>(P.w)[g] = make_float4(wq[0], wq[1], wq[2], wq[3]);
+        if (dep) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lw.add(c, fx_split(fx_weight_q(wq[q], P.wscale, &ovf), th[q]), grho);
+        }
+    }
+    if (dep) lw.flush(grho);
+    if (ovf) raise_flag(P.status, PE_FLAG_OVERFLOW);
+    __syncthreads();
+    if (dep) grho.flush();
+}
+
 // Wavelet form, lifting in x (Eq. interpolation) at the fine nodes: fine node j lies phi =
 // (j mod 2^b) / 2^b of the way from coarse node i0 = j >> b to i1 = i0 + 1 (periodic); its
 // histogram is the linear interpolation (1 - phi) H_i0 + phi H_i1 of the reconstructed
@@ -1144,11 +1230,15 @@ extern "C" PE_API int pe_ps_quiet_start_nodes(int32_t* cell, float* theta, float
     P.status = status;
     const size_t smem = (rho_fx ? kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width : 0) +
                         (size_t)P.stage_rows * (size_t)rw_bytes;
-    const void* k = (const void*)k_ps_quiet_start;
+    const bool four = P.log2ppc >= 2;  // a lane's four slots in one cell
+    const void* k = four ? (const void*)k_ps_quiet_start_nodes : (const void*)k_ps_quiet_start;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     const int grid = particle_grid(k, 256, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
-    k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
+    if (four)
+        k_ps_quiet_start_nodes<<<grid, 256, smem, s>>>(P);
+    else
+        k_ps_quiet_start<<<grid, 256, smem, s>>>(P);
     return launch_status(1);
 }
 
