@@ -110,6 +110,11 @@ def _load():
                 "orc_burst_kinetic": (None, [i64, P, P, P, P, i64, P, P, P, P, i32, dbl, dbl, dbl, dbl, i32, dbl,
                                              i32, i32, i32, dbl, dbl, i32, P, P, P]),
                 "orc_boltzmann_electrons": (None, [i64, i32, P, P, dbl, u64, P, P, P, P]),
+                "orc_restrict_second_moment": (None, [i64, P, P, P, P, P, i32, dbl, dbl, dbl, P]),
+                "orc_burst_pressure": (ctypes.c_int, [i64, P, P, P, P, i32, dbl, dbl, dbl, i32, dbl,
+                                                      i32, i32, i32, dbl, i32, i32, P, P]),
+                "orc_lift_profile_pressure": (None, [i32, P, P, P, P, P]),
+                "orc_quiet_start_thermal": (None, [i64, i32, P, P, P, u64, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -988,3 +993,76 @@ def leap_for_tol(qn, cn, Kdt, tol):
     if not qn > 0:
         return float("inf")
     return 0.5 * (-Kdt + np.sqrt(Kdt * Kdt + 4.0 * tol * cn / qn))
+
+
+# ------------------------------------------------------------------ ion pressure (Section 3.2)
+# EFREE's active ion variables are n, V and P. The restriction adds the second velocity moment
+# S = sum_p w V~^2 S_j(X~) to the density and momentum samples; the coarse state is the
+# wavelet scaling coefficients of the three, [3][n_coarse]; the lift loads Maxwellians of the
+# local temperature T = S / n - u^2.
+
+
+def restrict_second_moment(st: State, vbar, E0, ncell, dx, tau, qm):
+    vbar, E0 = _f64(vbar), _f64(E0)
+    sec = np.zeros(ncell)
+    _load().orc_restrict_second_moment(st.n, _p(st.cell), _p(st.theta), _p(vbar), _p(st.w), _p(E0), ncell,
+                                       float(dx), float(tau), float(qm), _p(sec))
+    return sec
+
+
+def burst_pressure(st: State, ncell, dx, dt, qm, K, dT, s_w, phi, comoving=True, mode=0, tol=1e-11,
+                   maxit=50, vel_at_integer=True):
+    """Runs K steps in place on st; returns (samples [(K+1),3,ncell], phi, fails)."""
+    phi = _f64(phi).copy()
+    samples = np.zeros((K + 1, 3, ncell))
+    fails = _load().orc_burst_pressure(st.n, _p(st.cell), _p(st.theta), _p(st.v), _p(st.w), ncell, float(dx),
+                                       float(dt), float(qm), int(K), float(dT), int(comoving), int(mode),
+                                       int(s_w), float(tol), int(maxit), int(vel_at_integer), _p(phi),
+                                       _p(samples))
+    return samples, phi, int(fails)
+
+
+def lift_profile_pressure(n, m, s):
+    """Returns (n clamped, u, T) of the lifting (orc_lift_profile_pressure)."""
+    n = _f64(n).copy()
+    m, s = _f64(m), _f64(s)
+    u, T = np.zeros_like(n), np.zeros_like(n)
+    _load().orc_lift_profile_pressure(n.shape[0], _p(n), _p(m), _p(s), _p(u), _p(T))
+    return n, u, T
+
+
+def quiet_start_thermal(N, ncell, nprof, uprof, tprof, seed):
+    nprof, uprof, tprof = _f64(nprof), _f64(uprof), _f64(tprof)
+    cell = np.zeros(N, np.int32)
+    theta, v, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().orc_quiet_start_thermal(N, ncell, _p(nprof), _p(uprof), _p(tprof), seed & 0xFFFFFFFFFFFFFFFF,
+                                    _p(cell), _p(theta), _p(v), _p(w))
+    return State(cell, theta, v, w)
+
+
+def efpi_macro_step_pressure(st: State, cfg: dict, phi, vel_at_integer=True):
+    """efpi_macro_step with the ion pressure active: burst with three-moment co-moving
+    samples, coarsening of each, least-squares slope and leap. Returns (coarse [3,nc],
+    samples_c [(K+1),3,nc], phi)."""
+    ncell, nc, K = cfg["ncell"], cfg["n_coarse"], cfg["K"]
+    dx = cfg["L"] / ncell
+    samples, phi, fails = burst_pressure(st, ncell, dx, cfg["dt"], cfg["qm"], K, cfg["dT"], cfg["s_w"], phi,
+                                         comoving=cfg.get("comoving", True), mode=cfg.get("mode", 0),
+                                         vel_at_integer=vel_at_integer)
+    wav = cfg.get("wavelet", "haar")
+    cs = np.zeros((K + 1, 3, nc))
+    for p in range(K + 1):
+        for m in range(3):
+            cs[p, m] = coarsen(samples[p, m], nc, wav)
+    coarse, _ = ls_project(cs.reshape(K + 1, 3 * nc), cfg["dt"], cfg["dT"])
+    return coarse.reshape(3, nc), cs, phi
+
+
+def lift_pressure(coarse, cfg: dict, seed):
+    """Lifting of the three moments: refine each with zero details, n clamped, u = nV / n,
+    T = S / n - u^2 clamped at 0, quiet start at the local temperature."""
+    ncell = cfg["ncell"]
+    wav = cfg.get("wavelet", "haar")
+    nf, mf, sf = (refine(coarse[k], ncell, wav) for k in range(3))
+    nf, uf, Tf = lift_profile_pressure(nf, mf, sf)
+    return quiet_start_thermal(cfg["N"], ncell, nf, uf, Tf, seed)

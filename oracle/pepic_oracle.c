@@ -1452,3 +1452,95 @@ void orc_ps_quiet_start_nodes(int64_t N, int32_t ncell, int32_t bin_shift, const
         v[s] = (1.0 - th) * vn[0] + th * vn[1];
     }
 }
+
+/* ---------------------------------------------------------------- ion pressure (Section 3.2)
+ * EFREE's third ion variable: besides n and nV the ions' second velocity moment is active,
+ * S_j = sum_p w_p V~_p^2 S_j(X~_p), restricted along the same approximate characteristics
+ * (Appendix B) and with the same CIC weights as the density and the momentum. At the lift the
+ * pressure is P = S - (nV)^2 / n and the temperature (velocity variance) T = P / n. */
+
+void orc_restrict_second_moment(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                                const double* w, const double* E0, int32_t ncell, double dx, double tau,
+                                double qm, double* sec)
+{
+    memset(sec, 0, sizeof(double) * (size_t)ncell);
+    for (int64_t p = 0; p < n; ++p) {
+        double E0p = orc_gather(E0, ncell, cell[p], theta[p]);
+        int32_t c = cell[p];
+        double th = theta[p];
+        drift(&c, &th, tau * vbar[p] / dx, ncell);      /* X~ = X + tau V  */
+        double vt = vbar[p] + qm * tau * E0p;            /* V~ = V + qm tau E_n(X) */
+        int32_t c1 = wrap((int64_t)c + 1, ncell);
+        double e = w[p] * vt * vt;
+        sec[c] += e * (1.0 - th);
+        sec[c1] += e * th;
+    }
+}
+
+/* orc_burst with the three moments: samples[(K+1)][3][ncell] = density, momentum, second
+ * moment of each sample p = 0..K. */
+int orc_burst_pressure(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+                       int32_t ncell, double dx, double dt, double qm, int32_t K, double dT,
+                       int32_t comoving, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                       int32_t vel_at_integer, double* phi, double* samples)
+{
+    double* E = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* E0 = (double*)malloc(sizeof(double) * (size_t)ncell);
+    double* vbar = (double*)malloc(sizeof(double) * (size_t)n);
+    int fails = field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    memcpy(E0, E, sizeof(double) * (size_t)ncell); /* E_n, stored at burst start */
+    double kick = vel_at_integer ? 0.5 : 1.0;
+    for (int32_t p = 0; p <= K; ++p) {
+        for (int64_t i = 0; i < n; ++i)
+            vbar[i] = v[i] + (kick - 0.5) * qm * dt * orc_gather(E, ncell, cell[i], theta[i]);
+        double tau = comoving ? dT - p * dt : 0.0;
+        double* row = samples + (size_t)p * 3 * ncell;
+        orc_restrict_sample(n, cell, theta, vbar, w, E0, ncell, dx, tau, qm, row, row + ncell);
+        orc_restrict_second_moment(n, cell, theta, vbar, w, E0, ncell, dx, tau, qm, row + 2 * (size_t)ncell);
+        if (p == K) break;
+        orc_push(n, cell, theta, v, E, ncell, dx, dt, qm, kick);
+        kick = 1.0;
+        fails += field_from_particles(n, cell, theta, w, ncell, dx, mode, s_w, tol, maxit, phi, E);
+    }
+    free(E);
+    free(E0);
+    free(vbar);
+    return fails;
+}
+
+/* Lifting profiles of the three moments: n clamped and rescaled and u = nV / n as in
+ * orc_lift_profile, then T = S / n - u^2 where n is above the same floor, clamped at 0 (a
+ * projected second moment can fall below the kinetic part n u^2); T = 0 where n is not. */
+void orc_lift_profile_pressure(int32_t ncell, double* n, const double* m, const double* s, double* u, double* T)
+{
+    double nmax = 0.0;
+    orc_lift_profile(ncell, n, m, u);
+    for (int32_t j = 0; j < ncell; ++j) nmax = fmax(nmax, n[j]);
+    for (int32_t j = 0; j < ncell; ++j) {
+        double t = (n[j] > 1e-12 * nmax) ? s[j] / n[j] - u[j] * u[j] : 0.0;
+        T[j] = t > 0.0 ? t : 0.0;
+    }
+}
+
+/* Appendix C's loading (orc_quiet_start: the same positions, weights, quantiles and storage
+ * order) with a local temperature: V = u(X) + sqrt(T(X)) Phi^-1(b), T linear between the nodes
+ * like n and u. */
+void orc_quiet_start_thermal(int64_t N, int32_t ncell, const double* nprof, const double* uprof,
+                             const double* tprof, uint64_t seed, int32_t* cell, double* theta, double* v,
+                             double* w)
+{
+    double* z = (double*)malloc(sizeof(double) * (size_t)N);
+    double* u0 = (double*)calloc((size_t)ncell, sizeof(double));
+    /* the loader with u = 0 and v_th = 1 gives each slot its cell, offset, weight and Phi^-1(b) */
+    orc_quiet_start(N, ncell, nprof, u0, 1.0, seed, cell, theta, z, w);
+    for (int64_t s = 0; s < N; ++s) {
+        int32_t c = cell[s];
+        int32_t c1 = wrap((int64_t)c + 1, ncell);
+        double th = theta[s];
+        double uX = (1.0 - th) * uprof[c] + th * uprof[c1];
+        double TX = (1.0 - th) * tprof[c] + th * tprof[c1];
+        v[s] = uX + sqrt(TX) * z[s];
+    }
+    free(z);
+    free(u0);
+}

@@ -258,6 +258,24 @@ void orc_burst_kinetic(int64_t ni, int32_t* ci, double* ti, double* vi, const do
 void orc_boltzmann_electrons(int64_t N, int32_t ncell, const double* phi, const double* u, double v_th_e,
                              uint64_t seed, int32_t* cell, double* theta, double* v, double* w);
 
+/* ---- ion pressure (Section 3.2, EFREE's n, V, P): the second velocity moment as a third
+ * restriction sample and the lifting at a local temperature. */
+/* sec[j] = sum_p w_p V~_p^2 S_j(X~_p), with X~, V~ as in orc_restrict_sample. */
+void orc_restrict_second_moment(int64_t n, const int32_t* cell, const double* theta, const double* vbar,
+                                const double* w, const double* E0, int32_t ncell, double dx, double tau,
+                                double qm, double* sec);
+/* orc_burst with samples[(K+1)][3][ncell]: density, momentum, second moment. */
+int orc_burst_pressure(int64_t n, int32_t* cell, double* theta, double* v, const double* w,
+                       int32_t ncell, double dx, double dt, double qm, int32_t K, double dT,
+                       int32_t comoving, int32_t mode, int32_t s_w, double tol, int32_t maxit,
+                       int32_t vel_at_integer, double* phi, double* samples);
+/* orc_lift_profile, then T = max(S / n - u^2, 0) (0 where n is below the floor). */
+void orc_lift_profile_pressure(int32_t ncell, double* n, const double* m, const double* s, double* u, double* T);
+/* orc_quiet_start with V = u(X) + sqrt(T(X)) Phi^-1(b). */
+void orc_quiet_start_thermal(int64_t N, int32_t ncell, const double* nprof, const double* uprof,
+                             const double* tprof, uint64_t seed, int32_t* cell, double* theta, double* v,
+                             double* w);
+
 #ifdef __cplusplus
 }
 #endif
