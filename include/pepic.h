@@ -70,6 +70,8 @@ extern "C" {
 
 #define PE_COARSE_MOMENTS 0     /* density and momentum, wavelet in x (Section 3.2 variables) */
 #define PE_COARSE_PHASE_SPACE 1 /* phase-space cell masses (Section 3.3), Haar in x and v */
+#define PE_COARSE_MOMENTS_PRESSURE 2 /* density, momentum and the second velocity moment, wavelet
+                                        in x (Section 3.2: EFREE's ion n, V and P = n T active) */
 
 #define PE_PROFILE_SINE 0 /* n = 1 + a cos(2 pi x / L), u = a cos(2 pi x / L) (Section 4.1) */
 #define PE_PROFILE_SLAB 1 /* n = 1 on the nodes 7 ncell/16 .. 9 ncell/16, 0 elsewhere; u = 0
@@ -203,6 +205,13 @@ typedef struct pe_sample_args {
                            i = floor(y / 2^b) and w f to node i + 1, f = y / 2^b - i, in fixed
                            point f_q = rn(fl32((y mod 2^b)) 2^(24-b)); the rows hold 2^b times
                            the averaged values of that rule */
+    int32_t second_moment; /* 1: a third nodal moment, the ions' second velocity moment
+                              S_j = sum_p w V~^2 S_j(X~) (Section 3.2: EFREE's pressure
+                              P = S - (nV)^2 / n is active), in fixed point
+                              e_q = rn(fl32(fl32(w V~) V~) 2^s_e) split like the density; then
+                              sample_fx is int64[3][ncell] (density, momentum, S); needs
+                              bin_shift = 0, n_v = 0 and a periodic grid */
+    int32_t s_e;           /* second-moment fixed-point shift: |w V~^2| 2^s_e must stay <= 2^22 */
 } pe_sample_args;
 
 /* Leapfrog gather + push, Section 2.2, fused with the charge deposit of the new
@@ -334,6 +343,35 @@ PE_API int pe_initial_profile(int32_t profile, int32_t ncell, double L, double a
 
 PE_API int pe_fixed_point_shifts(int64_t nparticles, int32_t ncell, double w_cap, double v_cap,
                                  int32_t* s_w, int32_t* s_p);
+
+/* Shift of the second-moment sample (pe_sample_args.s_e) for the same caps: the largest
+ * |w V~^2| = w_cap v_cap^2 maps below 2^23 (w_cap, v_cap 0 = the defaults of
+ * pe_fixed_point_shifts). */
+PE_API int pe_second_moment_shift(int64_t nparticles, int32_t ncell, double w_cap, double v_cap, int32_t* s_e);
+
+/* Ion pressure as an active variable (Section 3.2, EFREE: ion n, V and P = n T are active,
+ * the ions shifted Maxwellians). pe_coarsen for samples of the three nodal moments,
+ * sample_fx int64[nsamples][3][ncell] (density at 2^-(s_w+24), momentum at 2^-(s_p+24),
+ * second moment at 2^-(s_e+24)): each row is analysed like pe_coarsen's with bin_shift 0 into
+ * coarse[nsamples][3][n_coarse]. */
+PE_API int pe_coarsen_pressure(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
+                               int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse, double* coarse,
+                               void* stream);
+
+/* Lifting profiles of the three moments (Section 3.2 lifting, zero details): coarse[3][n_coarse]
+ * is synthesised to the nodes as in pe_refine; n is clamped at 0 and rescaled to keep its sum,
+ * u = nV / n and T = max(S / n - u^2, 0) where n > 1e-12 max n (u = T = 0 elsewhere). Writes
+ * prof_n, prof_u, prof_T (float[ncell] each). ncell <= 4096 (four FP64 rows in shared memory). */
+PE_API int pe_refine_pressure(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
+                              float* prof_n, float* prof_u, float* prof_T, void* stream);
+
+/* pe_quiet_start at a local temperature: the same cells, offsets, weights, quantiles and
+ * storage order, with V = u(X) + sqrt(T(X)) Phi^-1(b_h), T linear between the nodes like n and
+ * u (prof_T >= 0; a uniform T = v_th^2 gives pe_quiet_start's particles). */
+PE_API int pe_quiet_start_thermal(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                                  int32_t ncell, const float* prof_n, const float* prof_u,
+                                  const float* prof_T, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                                  uint32_t* status, void* stream);
 
 /* Quiet-start loading with equal weights on a bounded grid (Appendix C's loading, with the
  * particle count of each cell in proportion to its mass, as for Section 4.2's slab whose
@@ -582,7 +620,10 @@ typedef struct pe_config {
     uint64_t seed;        /* lifting shift seeds: splitmix64(seed + macro step) */
     double w_cap;         /* largest particle weight (fixed-point range); 0 = 8 ncell / N */
     double v_cap;         /* largest |V~| in restriction samples; 0 = 32 */
-    int32_t coarse_kind;  /* PE_COARSE_MOMENTS or PE_COARSE_PHASE_SPACE */
+    int32_t coarse_kind;  /* PE_COARSE_MOMENTS, PE_COARSE_PHASE_SPACE or PE_COARSE_MOMENTS_PRESSURE
+                             (the last: periodic grids, Boltzmann electrons, ncell <= 4096; nodal
+                             samples of three moments, lifting at the local temperature; the
+                             coarse state is [3][n_coarse]) */
     int32_t n_v;          /* phase space: velocity cells (2..256) */
     double v_max;         /* phase space: velocity range [-v_max, v_max) */
     int32_t ps_filter;    /* phase space: 1-2-1 filter of the projected slope; bit 0 in v, bit 1 in x */
@@ -618,11 +659,14 @@ enum pe_buffer {
     PE_BUF_E,               /* f64[ncell] field */
     PE_BUF_EF,              /* f32[ncell] field copy for the particle kernels */
     PE_BUF_E0F,             /* f32[ncell] field at burst start */
-    PE_BUF_SAMPLES_FX,      /* int64[K+2][row] restriction samples (row: 2 bins or n_coarse n_v) */
+    PE_BUF_SAMPLES_FX,      /* int64[K+2][row] restriction samples (row: 2 bins, 3 ncell nodes with
+                               the pressure, or n_coarse n_v) */
     PE_BUF_COARSE_SAMPLES,  /* f64[K+2][ncoef] */
-    PE_BUF_COARSE,          /* f64[ncoef] current coarse state: [2][n_coarse] or [n_coarse][n_v] */
+    PE_BUF_COARSE,          /* f64[ncoef] current coarse state: [2][n_coarse], [3][n_coarse] (pressure)
+                               or [n_coarse][n_v] */
     PE_BUF_SLOPE,           /* f64[ncoef] last least-squares slope */
-    PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u) */
+    PE_BUF_PROFILE,         /* f32[2][ncell] lifting profiles (n, u); [3][ncell] (n, u, T) with the
+                               pressure */
     PE_BUF_SORT,            /* int32[2 ncell + 64] sort scratch */
     PE_BUF_STATUS,          /* uint32[4] status word; int32[4] Newton diag after it */
     PE_BUF_DIAG,            /* pe_moments scratch + one pe_moments result */

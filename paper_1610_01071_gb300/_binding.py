@@ -28,7 +28,7 @@ BUF = dict(particles_a=0, particles_b=1, rho=2, phi=3, E=4, Ef=5, E0f=6, samples
            coarse=9, slope=10, profile=11, sort=12, status=13, diag=14, surrogate=15, phase=16, electrons_a=17,
            electrons_b=18, rho_e=19)
 PE_ELECTRONS = {"boltzmann": 0, "kinetic": 1}
-PE_COARSE = {"moments": 0, "phase_space": 1}
+PE_COARSE = {"moments": 0, "phase_space": 1, "moments_pressure": 2}
 PE_MLP_NBUF = 7
 MLP_BUF = dict(params=0, params_bf16=1, grads=2, adam_m=3, adam_v=4, norm=5, work=6)
 PE_MOMENTS_SCRATCH_BYTES = 65536
@@ -46,7 +46,7 @@ class SampleArgs(ctypes.Structure):
                 ("inv_dx", ctypes.c_float), ("s_w", ctypes.c_int32), ("s_p", ctypes.c_int32),
                 ("bin_shift", ctypes.c_int32), ("sample_fx", ctypes.c_void_p), ("n_v", ctypes.c_int32),
                 ("v_min", ctypes.c_float), ("inv_dv", ctypes.c_float), ("boundary", ctypes.c_int32),
-                ("x_tent", ctypes.c_int32)]
+                ("x_tent", ctypes.c_int32), ("second_moment", ctypes.c_int32), ("s_e", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):
@@ -143,6 +143,10 @@ SIGNATURES = {
     "pe_sample_f64": (ctypes.c_int, [P, P, P, P, i64, P, i32, f64, f64, i32, P, f64, f64, i32, P, P, P]),
     "pe_quiet_start_f64": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f64, u64, i32, P, P, P]),
     "pe_fixed_point_shifts": (ctypes.c_int, [i64, i32, f64, f64, P, P]),
+    "pe_second_moment_shift": (ctypes.c_int, [i64, i32, f64, f64, P]),
+    "pe_coarsen_pressure": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, i32, P, P]),
+    "pe_refine_pressure": (ctypes.c_int, [P, i32, i32, i32, P, P, P, P]),
+    "pe_quiet_start_thermal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, u64, i32, P, P, P]),
     "pe_initial_profile": (ctypes.c_int, [i32, i32, f64, f64, P, P]),
     "pe_quiet_start_equal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f32, f32, u64, i32, P, P, P, P]),
     "pe_sort": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, P, P, P, P]),
@@ -329,13 +333,15 @@ def boltzmann_profile(phi, ncell, ion_moments=None, s_w=0, s_p=0, stream=None):
 
 
 def make_sample_args(E0f, tau, qm, inv_dx, s_w, s_p, sample_fx, bin_shift=0, n_v=0, v_min=0.0, dv=1.0,
-                     boundary="periodic", x_tent=False):
+                     boundary="periodic", x_tent=False, s_e=None):
     """Restriction-sample arguments; n_v > 0 selects the phase-space sample (n_v velocity
     cells of width dv from v_min) instead of the density and momentum moments; x_tent rows
-    are coarse nodes with the hat weights of the repeated 1-2-1 rule instead of Haar bins."""
+    are coarse nodes with the hat weights of the repeated 1-2-1 rule instead of Haar bins;
+    s_e (not None) adds the second velocity moment as a third nodal row."""
     return SampleArgs(ctypes.c_void_p(E0f.data_ptr()), float(tau), float(qm), float(inv_dx), int(s_w), int(s_p),
                       int(bin_shift), ctypes.c_void_p(sample_fx.data_ptr()), int(n_v), float(v_min),
-                      float(1.0 / dv), PE_BOUNDARY[boundary], int(bool(x_tent)))
+                      float(1.0 / dv), PE_BOUNDARY[boundary], int(bool(x_tent)), int(s_e is not None),
+                      int(s_e or 0))
 
 
 def push(cell, theta, v, w, Ef, ncell, dt_over_dx, qm_dt, kick, s_w, rho=None, sample=None, status=None,
@@ -369,6 +375,46 @@ def coarsen(sample_fx, nsamples, ncell, s_w, s_p, n_coarse, wavelet="haar", out=
     check(load().pe_coarsen(_ptr(sample_fx), nsamples, ncell, s_w, s_p, PE_WAVELET[wavelet], n_coarse, bin_shift,
                             _ptr(out), _stream(stream)), "pe_coarsen")
     return out
+
+
+def second_moment_shift(nparticles, ncell, w_cap=0.0, v_cap=0.0):
+    s_e = ctypes.c_int32()
+    check(load().pe_second_moment_shift(int(nparticles), int(ncell), float(w_cap), float(v_cap), ctypes.byref(s_e)),
+          "pe_second_moment_shift")
+    return s_e.value
+
+
+def coarsen_pressure(sample_fx, nsamples, ncell, s_w, s_p, s_e, n_coarse, wavelet="haar", out=None, stream=None):
+    """Three nodal moments [nsamples][3][ncell] -> [nsamples][3][n_coarse] (pe_coarsen_pressure)."""
+    out = out if out is not None else torch.empty((nsamples, 3, n_coarse), dtype=torch.float64,
+                                                  device=sample_fx.device)
+    check(load().pe_coarsen_pressure(_ptr(sample_fx), nsamples, ncell, s_w, s_p, s_e, PE_WAVELET[wavelet], n_coarse,
+                                     _ptr(out), _stream(stream)), "pe_coarsen_pressure")
+    return out
+
+
+def refine_pressure(coarse, ncell, wavelet="haar", stream=None):
+    """coarse: [3, n_coarse] float64. Returns float32 (n, u, T) profiles."""
+    nc = coarse.shape[-1]
+    prof = [torch.empty(ncell, dtype=torch.float32, device=coarse.device) for _ in range(3)]
+    check(load().pe_refine_pressure(_ptr(coarse), nc, PE_WAVELET[wavelet], ncell, *[_ptr(p) for p in prof],
+                                    _stream(stream)), "pe_refine_pressure")
+    return tuple(prof)
+
+
+def quiet_start_thermal(n, ncell, prof_n, prof_u, prof_T, seed, s_w, with_rho=True, status=None, stream=None):
+    """pe_quiet_start at the local temperature prof_T (pe_quiet_start_thermal)."""
+    dev = prof_n.device
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty_like(theta)
+    w = torch.empty_like(theta)
+    rho = torch.empty(ncell, dtype=torch.int64, device=dev) if with_rho else None
+    status = _status(status, dev)
+    check(load().pe_quiet_start_thermal(_ptr(cell), _ptr(theta), _ptr(v), _ptr(w), n, ncell, _ptr(prof_n),
+                                        _ptr(prof_u), _ptr(prof_T), int(seed) & 0xFFFFFFFFFFFFFFFF, s_w, _ptr(rho),
+                                        _ptr(status), _stream(stream)), "pe_quiet_start_thermal")
+    return cell, theta, v, w, rho
 
 
 def ls_project(samples, dt, dT, stream=None):
@@ -613,7 +659,8 @@ def make_config(ncell, n_coarse, K, nparticles, L, dt, dT, qm=1.0, v_th=1.0, wav
                 poisson="boltzmann", newton_tol=1e-10, newton_maxit=50, sort_every=0, seed=0, w_cap=0.0,
                 v_cap=0.0, coarse="moments", n_v=64, v_max=8.0, ps_filter=0, boundary="periodic",
                 electrons="boltzmann", reset_every=0, qm_e=0.0, v_th_e=0.0, n_v_coarse=0, te_active=False) -> Config:
-    """coarse="moments": density and momentum coefficients (2 n_coarse); "phase_space": the
+    """coarse="moments": density and momentum coefficients (2 n_coarse); "moments_pressure": those and
+    the second velocity moment's (3 n_coarse; the ion pressure of Section 3.2 active); "phase_space": the
     masses of n_coarse x n_v phase-space cells over velocities [-v_max, v_max); ps_filter: 1-2-1
     filter of the projected phase-space slope (bit 0 along v, bit 1 along x); boundary:
     "periodic" or "absorbing" (walls at nodes 0 and ncell-1, Section 4.2); electrons:
@@ -693,6 +740,8 @@ class Context:
         """(2, n_coarse) for the moments, (n_coarse, n_v) for the phase-space cells."""
         if self.cfg.coarse_kind == PE_COARSE["phase_space"]:
             return (self.cfg.n_coarse, self.cfg.n_v_coarse if self.cfg.n_v_coarse > 0 else self.cfg.n_v)
+        if self.cfg.coarse_kind == PE_COARSE["moments_pressure"]:
+            return (3, self.cfg.n_coarse)
         return (2, self.cfg.n_coarse)
 
     def get_coarse(self):

@@ -49,7 +49,7 @@ int layout_for(pe_ctx* const* ctxs, int n, Layout* L)
     int64_t rho = 0, row = 0, items = 0;
     for (int r = 0; r < n; ++r) {
         const pe_ctx* x = ctxs[r];
-        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps || x->kinetic)
+        if (!x || x->cfg.K != K || x->cfg.wavelet != PE_WAVELET_HAAR || x->cfg.ncell < 64 || x->ps || x->pres || x->kinetic)
             return PE_EINVAL;
         rho += x->cfg.ncell;
         row += 2 * (int64_t)x->nb;

@@ -120,6 +120,15 @@ extern "C" PE_API int pe_fixed_point_shifts(int64_t nparticles, int32_t ncell, d
     return PE_OK;
 }
 
+extern "C" PE_API int pe_second_moment_shift(int64_t nparticles, int32_t ncell, double w_cap, double v_cap, int32_t* s_e)
+{
+    if (nparticles < 1 || ncell < 1 || !s_e) return PE_EINVAL;
+    const double wc = w_cap > 0.0 ? w_cap : 8.0 * ncell / (double)nparticles;
+    const double vc = v_cap > 0.0 ? v_cap : 32.0;
+    *s_e = fx_shift(wc * vc * vc);
+    return PE_OK;
+}
+
 
 extern "C" PE_API const char* pe_strerror(int code)
 {
@@ -151,8 +160,15 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     if (c.poisson != PE_POISSON_BOLTZMANN && c.poisson != PE_POISSON_LINEARIZED) return PE_EINVAL;
     if (c.newton_maxit < 1 || !(c.newton_tol > 0.0) || c.sort_every < 0) return PE_EINVAL;
     if (c.w_cap < 0.0 || c.v_cap < 0.0) return PE_EINVAL;
-    if (c.coarse_kind != PE_COARSE_MOMENTS && c.coarse_kind != PE_COARSE_PHASE_SPACE) return PE_EINVAL;
+    if (c.coarse_kind != PE_COARSE_MOMENTS && c.coarse_kind != PE_COARSE_PHASE_SPACE &&
+        c.coarse_kind != PE_COARSE_MOMENTS_PRESSURE)
+        return PE_EINVAL;
     const bool ps = c.coarse_kind == PE_COARSE_PHASE_SPACE;
+    // ion pressure: nodal samples of three moments, lifting at the local temperature (periodic
+    // grids, Boltzmann electrons; four FP64 rows of the grid in shared memory at the lift)
+    const bool pres = c.coarse_kind == PE_COARSE_MOMENTS_PRESSURE;
+    if (pres && (c.boundary != PE_BOUNDARY_PERIODIC || c.electrons != PE_ELECTRONS_BOLTZMANN || c.ncell > 4096))
+        return PE_EINVAL;
     if (c.n_v_coarse < 0 || (c.n_v_coarse > 0 && !ps)) return PE_EINVAL;
     const bool psw = ps && c.n_v_coarse > 0;  // the wavelet form
     if (ps && !psw && (c.wavelet != PE_WAVELET_HAAR || c.n_v < 2 || c.n_v > 256 || !(c.v_max > 0.0))) return PE_EINVAL;
@@ -176,7 +192,8 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     const size_t N = (size_t)c.nparticles, nc = (size_t)c.ncell, ncoef = (size_t)c.n_coarse;
     const size_t nps = ps ? ncoef * (size_t)c.n_v : 0;                 // phase-space sample row
     const size_t npc = psw ? ncoef * (size_t)c.n_v_coarse : nps;         // phase-space coefficients
-    const size_t row_fx = 2 * nc > nps ? 2 * nc : nps, crow = 2 * ncoef > npc ? 2 * ncoef : npc;
+    const size_t row_fx = pres ? 3 * nc : (2 * nc > nps ? 2 * nc : nps);
+    const size_t crow = pres ? 3 * ncoef : (2 * ncoef > npc ? 2 * ncoef : npc);
     const size_t bank = 4 * align256(4 * N);
     out->bytes[PE_BUF_PARTICLES_A] = bank;
     out->bytes[PE_BUF_PARTICLES_B] = bank;
@@ -189,7 +206,7 @@ extern "C" PE_API int pe_layout_for(const pe_config* cfg, pe_layout* out)
     out->bytes[PE_BUF_COARSE_SAMPLES] = 8 * crow * (size_t)(c.K + 2);
     out->bytes[PE_BUF_COARSE] = 8 * crow;
     out->bytes[PE_BUF_SLOPE] = 8 * crow;
-    out->bytes[PE_BUF_PROFILE] = 4 * 2 * nc;
+    out->bytes[PE_BUF_PROFILE] = 4 * (pres ? 3 : 2) * nc;
     out->bytes[PE_BUF_SORT] = 4 * (2 * nc + 64);
     out->bytes[PE_BUF_STATUS] = 64;
     out->bytes[PE_BUF_DIAG] = PE_MOMENTS_SCRATCH_BYTES + 256;
@@ -235,21 +252,24 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->nc = cfg->n_coarse;
     x->ps = cfg->coarse_kind == PE_COARSE_PHASE_SPACE;
     x->psw = x->ps && cfg->n_v_coarse > 0;
-    // Haar moments and both phase-space forms restrict over 2^b nodes in x (bins or hat rows)
-    x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR || x->ps) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
+    x->pres = cfg->coarse_kind == PE_COARSE_MOMENTS_PRESSURE;
+    // Haar moments and both phase-space forms restrict over 2^b nodes in x (bins or hat rows);
+    // the three moments of the pressure variable are sampled on the nodes
+    x->bin_shift = ((cfg->wavelet == PE_WAVELET_HAAR && !x->pres) || x->ps) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
     x->nb = cfg->ncell >> x->bin_shift;
     x->nv = x->ps ? cfg->n_v : 0;
     x->nvc = x->psw ? cfg->n_v_coarse : x->nv;
     x->vmin = x->ps ? -cfg->v_max : 0.0;
     x->dv = x->ps ? 2.0 * cfg->v_max / cfg->n_v : 1.0;
-    x->ncoef = x->ps ? (int64_t)x->nc * x->nvc : 2 * (int64_t)x->nc;
+    x->ncoef = x->ps ? (int64_t)x->nc * x->nvc : (x->pres ? 3 : 2) * (int64_t)x->nc;
     const int64_t nps = x->ps ? (int64_t)x->nc * x->nv : 0;  // phase-space sample row
-    x->row_fx = 2 * (int64_t)x->nb > nps ? 2 * (int64_t)x->nb : nps;
-    x->crow = 2 * (int64_t)x->nc > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nc : x->ncoef;
+    x->row_fx = x->pres ? 3 * (int64_t)x->nb : (2 * (int64_t)x->nb > nps ? 2 * (int64_t)x->nb : nps);
+    x->crow = x->pres ? x->ncoef : (2 * (int64_t)x->nc > (x->ps ? x->ncoef : 0) ? 2 * (int64_t)x->nc : x->ncoef);
     const double w_cap = cfg->w_cap > 0.0 ? cfg->w_cap : 8.0 * cfg->ncell / (double)cfg->nparticles;
     const double v_cap = cfg->v_cap > 0.0 ? cfg->v_cap : 32.0;
     x->s_w = fx_shift(w_cap);
     x->s_p = fx_shift(w_cap * v_cap);
+    x->s_e = fx_shift(w_cap * v_cap * v_cap);
     const size_t N = (size_t)cfg->nparticles;
     for (int b = 0; b < 2; ++b) {
         char* base = x->arena + lay.offset[PE_BUF_PARTICLES_A + b];
@@ -550,6 +570,8 @@ static pe_sample_args sample_args(pe_ctx* x, double tau, int64_t* dst)
     a.s_p = x->s_p;
     a.sample_fx = dst;
     a.boundary = x->cfg.boundary;
+    a.second_moment = x->pres;  // Section 3.2: the pressure's second moment beside n and nV
+    a.s_e = x->s_e;
     if (x->ps) {  // Section 3.3 phase-space histogram instead of the moments
         a.n_v = x->nv;
         a.v_min = (float)x->vmin;
@@ -598,6 +620,7 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
     pe_sample_args a = sample_args(x, 0.0, dst);
     a.E0f = x->Ef;  // tau = 0: the frame field is not used
     a.n_v = 0;      // the measurement is always the density and momentum coefficients
+    a.second_moment = 0;
     const int b = x->bank;
     const float kick = x->v_at_integer ? 0.5f : 1.0f;
     PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
@@ -610,6 +633,23 @@ extern "C" PE_API int pe_measure(pe_ctx* ctx, double* out, int32_t out_on_device
         return PE_ECUDA;
     if (!out_on_device && cudaStreamSynchronize(x->stream) != cudaSuccess) return PE_ECUDA;
     return PE_OK;
+}
+
+// Density, momentum and second-moment coefficients of the current particles (the pressure
+// variable's [3][n_coarse], tau = 0) into out (device).
+static int measure_pressure(pe_ctx* x, double* out)
+{
+    const pe_config& c = x->cfg;
+    if (!x->rho_valid) PE_TRY(deposit_current(x));
+    PE_TRY(field_solve(x));
+    int64_t* dst = sample_row(x, c.K + 1);
+    pe_sample_args a = sample_args(x, 0.0, dst);
+    a.E0f = x->Ef;
+    const int b = x->bank;
+    const float kick = x->v_at_integer ? 0.5f : 1.0f;
+    PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
+                     &a, x->status, x->stream));
+    return pe_coarsen_pressure(dst, 1, c.ncell, x->s_w, x->s_p, x->s_e, c.wavelet, x->nc, out, x->stream);
 }
 
 // Phase-space cell masses of the current particles (co-moving sample with tau = 0) into
@@ -684,6 +724,7 @@ extern "C" PE_API int pe_load_initial(pe_ctx* ctx, int32_t profile, double ampli
         }
     }
     if (x->ps) return measure_phase(x, x->coarse);
+    if (x->pres) return measure_pressure(x, x->coarse);
     return pe_measure(x, x->coarse, 1);
 }
 
@@ -756,6 +797,9 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
         return pe_ps_coarsen_v(ctx->samples, (int64_t)(ctx->K_cur + 1) * ctx->nc, ctx->nv, ctx->s_w, ctx->bin_shift,
                                c.wavelet, ctx->nvc, ctx->csamples, ctx->stream);
     if (ctx->ps) return pe_ps_coarsen(ctx->samples, ctx->K_cur + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
+    if (ctx->pres)  // Section 3.2: n, nV and the second moment, each to its scaling coefficients
+        return pe_coarsen_pressure(ctx->samples, ctx->K_cur + 1, c.ncell, ctx->s_w, ctx->s_p, ctx->s_e, c.wavelet,
+                                   ctx->nc, ctx->csamples, ctx->stream);
     return pe_coarsen(ctx->samples, ctx->K_cur + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
                       ctx->csamples, ctx->stream);
 }
@@ -822,6 +866,21 @@ extern "C" PE_API int pe_lift(pe_ctx* ctx)
             return pe_ps_quiet_start(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->bin_shift,
                                      x->ps_mass, x->ps_table, x->nv, x->vmin, x->dv, lift_seed(x), x->s_w, x->rho,
                                      x->status, x->stream);
+        }));
+        x->rho_valid = 1;
+        x->v_at_integer = 1;
+        x->fresh = 1;
+        x->phi_hist = 0;
+    } else if (x->pres) {
+        // Section 3.2 lifting with the pressure active: n, u and T = P / n on the nodes, then
+        // Maxwellians of the local temperature (periodic grids)
+        PE_TRY(pe_refine_pressure(x->coarse, x->nc, c.wavelet, c.ncell, x->prof, x->prof + c.ncell,
+                                  x->prof + 2 * (size_t)c.ncell, x->stream));
+        const int b = x->bank;
+        PE_TRY(timed(x, PE_PROF_LOAD, [&] {
+            return pe_quiet_start_thermal(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, c.ncell, x->prof,
+                                          x->prof + c.ncell, x->prof + 2 * (size_t)c.ncell, lift_seed(x), x->s_w,
+                                          x->rho, x->status, x->stream);
         }));
         x->rho_valid = 1;
         x->v_at_integer = 1;

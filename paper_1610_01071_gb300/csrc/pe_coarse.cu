@@ -198,15 +198,17 @@ static Filter make_filter(int wavelet)
 }
 
 // One block per (sample, moment) row: fine values -> level-J_f scaling coefficients ->
-// periodized analysis (approximation branch only) down to n_coarse coefficients.
-__global__ void __launch_bounds__(256) k_coarsen(const long long* fx, int ncell, double scale_n, double scale_m,
-                                                 Filter f, int n_coarse, double* out)
+// periodized analysis (approximation branch only) down to n_coarse coefficients. Rows cycle
+// through nmom moments (density, momentum and, with the pressure, the second moment).
+__global__ void __launch_bounds__(256) k_coarsen(const long long* fx, int ncell, int nmom, double scale_n,
+                                                 double scale_m, double scale_e, Filter f, int n_coarse, double* out)
 {
     extern __shared__ double buf[];
     double* a = buf;
     double* b = buf + ncell;
     const int row = blockIdx.x;
-    const double scale = (row & 1) ? scale_m : scale_n;
+    const int mom = row % nmom;
+    const double scale = mom == 0 ? scale_n : (mom == 1 ? scale_m : scale_e);
     const long long* src = fx + (size_t)row * ncell;
     for (int j = threadIdx.x; j < ncell; j += blockDim.x) a[j] = (double)src[j] * scale;
     __syncthreads();
@@ -345,7 +347,8 @@ __device__ double* synthesise(const Filter& f, const double* coarse, int nc, int
 
 template <typename P>
 __device__ __forceinline__ void refine_body(const double* coarse, int nc, const Filter& f, int ncell, double scale,
-                                            P* prof_n, P* prof_u, double* buf, double* red);
+                                            P* prof_n, P* prof_u, double* buf, double* red,
+                                            const double** nf_out = nullptr, const double** mf_out = nullptr);
 
 template <typename P>
 __global__ void __launch_bounds__(1024) k_refine(const double* coarse, int nc, Filter f, int ncell, double scale,
@@ -376,7 +379,8 @@ __global__ void __launch_bounds__(1024) k_refine_batch(const RefineDesc* d, Filt
 
 template <typename P>
 __device__ __forceinline__ void refine_body(const double* coarse, int nc, const Filter& f, int ncell, double scale,
-                                            P* prof_n, P* prof_u, double* buf, double* red)
+                                            P* prof_n, P* prof_u, double* buf, double* red, const double** nf_out,
+                                            const double** mf_out)
 {
     double* X = buf;
     double* Y = buf + ncell;
@@ -407,6 +411,40 @@ __device__ __forceinline__ void refine_body(const double* coarse, int nc, const 
         const double n = nf[j];
         prof_n[j] = (P)n;
         prof_u[j] = (n > 1e-12 * nmax) ? (P)(mf[j] / n) : P(0);
+    }
+    if (nf_out) *nf_out = nf;
+    if (mf_out) *mf_out = mf;
+}
+
+// Lifting profiles with the ion pressure (Section 3.2): n and u as k_refine, then the second
+// moment S synthesised into the two rows left free (four FP64 rows of ncell in shared memory)
+// and T = max(S / n - u^2, 0) with u = nV / n in FP64, where n is above the floor of u.
+__global__ void __launch_bounds__(1024) k_refine_pressure(const double* coarse, int nc, Filter f, int ncell,
+                                                          double scale, float* prof_n, float* prof_u, float* prof_t)
+{
+    extern __shared__ double buf[];
+    __shared__ double red[32];
+    const double* nf = nullptr;
+    const double* mf = nullptr;
+    refine_body(coarse, nc, f, ncell, scale, prof_n, prof_u, buf, red, &nf, &mf);
+    double* X = buf;
+    double* Y = buf + ncell;
+    double* Z = buf + 2 * ncell;
+    double* W = buf + 3 * ncell;
+    double* o1 = (nf == X) ? Y : X;
+    double* free1 = (mf == o1) ? Z : o1;  // the row of the momentum's pair it does not hold
+    double nmax = 0.0;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) nmax = fmax(nmax, nf[j]);
+    nmax = block_max_d(nmax, red);
+    const double* sf = synthesise(f, coarse + 2 * nc, nc, ncell, free1, W, scale);
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) {
+        const double n = nf[j];
+        double t = 0.0;
+        if (n > 1e-12 * nmax) {
+            const double u = mf[j] / n;
+            t = sf[j] / n - u * u;
+        }
+        prof_t[j] = (float)(t > 0.0 ? t : 0.0);
     }
 }
 
@@ -569,9 +607,28 @@ extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int
     if (ensure_smem((const void*)k_coarsen, smem) != PE_OK) return PE_ECUDA;
     // fine values are level-J_f scaling coefficients 2^{-J_f/2} f; b Haar levels of a bin sum add 2^{-b/2}
     const double lev = pow(2.0, -0.5 * (ilog2(ncell) + bin_shift));
-    k_coarsen<<<2 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), nb,
+    k_coarsen<<<2 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), nb, 2,
                                                                  ldexp(1.0, -(s_w + 24)) * lev,
-                                                                 ldexp(1.0, -(s_p + 24)) * lev, make_filter(wavelet),
+                                                                 ldexp(1.0, -(s_p + 24)) * lev, 0.0,
+                                                                 make_filter(wavelet), n_coarse, coarse);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_coarsen_pressure(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
+                                          int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse, double* coarse,
+                                          void* stream)
+{
+    if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || nsamples < 1 || !sample_fx || !coarse)
+        return PE_EINVAL;
+    if (!wavelet_ok(wavelet)) return PE_EINVAL;
+    const size_t smem = 2 * sizeof(double) * (size_t)ncell;
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    if (ensure_smem((const void*)k_coarsen, smem) != PE_OK) return PE_ECUDA;
+    const double lev = pow(2.0, -0.5 * ilog2(ncell));
+    k_coarsen<<<3 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), ncell, 3,
+                                                                 ldexp(1.0, -(s_w + 24)) * lev,
+                                                                 ldexp(1.0, -(s_p + 24)) * lev,
+                                                                 ldexp(1.0, -(s_e + 24)) * lev, make_filter(wavelet),
                                                                  n_coarse, coarse);
     return launch_status();
 }
@@ -647,6 +704,21 @@ static int refine_into(const double* coarse, int32_t n_coarse, int32_t wavelet, 
     if (ensure_smem((const void*)k_refine<P>, smem) != PE_OK) return PE_ECUDA;
     k_refine<P><<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
                                                          pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u);
+    return launch_status();
+}
+
+extern "C" PE_API int pe_refine_pressure(const double* coarse, int32_t n_coarse, int32_t wavelet, int32_t ncell,
+                                         float* prof_n, float* prof_u, float* prof_T, void* stream)
+{
+    if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || ncell > 4096 || !coarse || !prof_n || !prof_u ||
+        !prof_T)
+        return PE_EINVAL;
+    if (!wavelet_ok(wavelet)) return PE_EINVAL;
+    const size_t smem = 4 * sizeof(double) * (size_t)ncell;
+    if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
+    if (ensure_smem((const void*)k_refine_pressure, smem) != PE_OK) return PE_ECUDA;
+    k_refine_pressure<<<1, 1024, smem, (cudaStream_t)stream>>>(coarse, n_coarse, make_filter(wavelet), ncell,
+                                                               pow(2.0, 0.5 * ilog2(ncell)), prof_n, prof_u, prof_T);
     return launch_status();
 }
 

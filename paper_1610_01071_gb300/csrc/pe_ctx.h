@@ -24,6 +24,8 @@ struct pe_ctx {
     int bin_shift;       // Haar: restriction samples summed over coarse bins; else 0
     int nb;              // sample length per moment: ncell >> bin_shift
     int ps;              // phase-space coarse variable (PE_COARSE_PHASE_SPACE)
+    int pres;            // ion pressure active (PE_COARSE_MOMENTS_PRESSURE): three nodal moments
+    int s_e;             // second-moment fixed-point shift (pres)
     int K_cur;           // burst length of the next bursts (the configured K unless adapted)
     int te_active;       // kinetic electrons: their kinetic energy is an active variable
     double* we;          // te_active: [K+2] sampled energies, then the projected energy and its slope

@@ -107,6 +107,7 @@ inline int launch_status(int kernels = 1)
 constexpr int kFullGridMax = 8192;     // largest grid the context API accepts
 constexpr int kRhoWindowNodes = 1024;  // charge deposit: window around the block's cells
 constexpr int kWindowNodes = 4096;     // restriction samples: window (co-moving spread)
+constexpr int kWindowNodesE = 1024;    // the same with the second moment (three rows in shared memory)
 // TMA tensor map of a K-major BF16 GEMM operand: rows x K elements, row stride ld elements,
 // box {64, box_rows}, 128-byte swizzle, zero fill (pe_tc.cu).
 int tc_operand_map(::CUtensorMap_st* map, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows);

@@ -960,7 +960,7 @@ extern "C" PE_API int pe_step_surrogate(pe_ctx* ctx, pe_mlp* h, const pe_gate_cf
     pe_ctx* x = ctx;
     const pe_config& c = x->cfg;
     const int n = 2 * x->nc, Ks = gc->K_probe;
-    if (x->ps) return PE_EINVAL;  // the surrogate maps the density and momentum coefficients
+    if (x->ps || x->pres) return PE_EINVAL;  // the surrogate maps the density and momentum coefficients
     if (x->te_active) return PE_EINVAL;  // an accepted leap would not project the electrons' energy
     if (h->dims[0] != n || h->dims[h->L] != n || Ks < 2 || Ks >= x->K_cur || !(gc->tol >= 0.0) ||
         !(gc->noise_sigmas >= 0.0))

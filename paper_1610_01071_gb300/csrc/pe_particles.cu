@@ -49,6 +49,9 @@ struct PushParams {
     int nv, ps_width;
     float vmin, inv_dv;
     float tent_scale;  // hat rows (the TENT modes): 2^(24 - bin_shift)
+    // second velocity moment (the E modes): samp_e[ncell], fixed point at escale = 2^s_e
+    unsigned long long* samp_e;
+    float escale;
     // bounded grid (walls at nodes 0 and ncell-1, Section 4.2): a particle whose drift ends
     // outside [0, (ncell-1) dx) is absorbed (weight 0 written to w_out, parked on the wall node
     // with v = 0); particles of weight 0 are not moved; co-moving targets outside are dropped
@@ -66,18 +69,22 @@ enum Mode {
     kPushSamplePS = 6,  // push + phase-space sample
     kSamplePS = 7,
     kPushSamplePSW = 8,  // push + phase-space sample with hat rows (the wavelet form)
-    kSamplePSW = 9
+    kSamplePSW = 9,
+    kPushSampleE = 10,  // push + nodal sample of density, momentum and second moment
+    kSampleE = 11
 };
 
 template <int MODE>
 struct ModeTraits {
     static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                 MODE == kPushSamplePS || MODE == kPushSamplePSW);
+                                 MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE);
     static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                  MODE == kPushSamplePS || MODE == kPushSamplePSW);
+                                  MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE);
     static constexpr bool sample = (MODE == kPushSample || MODE == kSample || MODE == kPushSampleBinned ||
                                     MODE == kSampleBinned || MODE == kPushSamplePS || MODE == kSamplePS ||
-                                    MODE == kPushSamplePSW || MODE == kSamplePSW);
+                                    MODE == kPushSamplePSW || MODE == kSamplePSW || MODE == kPushSampleE ||
+                                    MODE == kSampleE);
+    static constexpr bool energy = (MODE == kPushSampleE || MODE == kSampleE);  // third nodal moment
     static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
     static constexpr bool tent = (MODE == kPushSamplePSW || MODE == kSamplePSW);
     static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS || tent);
@@ -168,7 +175,7 @@ struct BinSample {
 template <int MODE, bool WALLS>
 __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft, bool act, int c, float th,
                                         float vv, float ww, BinSample& bs, const SmemGrid& gsn, const SmemGrid& gsm,
-                                        const PSGrid& gps, PSAcc& acc, PSAcc2& acc2, bool* ovf, int& c_out, float& th_out,
+                                        const SmemGrid& gse, const PSGrid& gps, PSAcc& acc, PSAcc2& acc2, bool* ovf, int& c_out, float& th_out,
                                         float& v_out, float& w_out, int32_t& wq_out)
 {
     using Tr = ModeTraits<MODE>;
@@ -272,6 +279,12 @@ __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft,
                 gsn.add(cs1, qn.right);
                 gsm.add(cs, qp.left);
                 gsm.add(cs1, qp.right);
+                if (Tr::energy) {  // Section 3.2: the second moment w V~^2 with the same split
+                    const int32_t eq = fx_weight(__fmul_rn(__fmul_rn(ww, vt), vt), P.escale, ovf);
+                    const FxSplit qe = fx_split(eq, ths);
+                    gse.add(cs, qe.left);
+                    gse.add(cs1, qe.right);
+                }
             }
         }
     }
@@ -366,7 +379,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 
     const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
 
-    SmemGrid grho{}, gsn{}, gsm{};
+    SmemGrid grho{}, gsn{}, gsm{}, gse{};
     BinGrid bsn{}, bsm{};
     PSGrid gps{};
     constexpr bool kPS = Tr::ps;
@@ -393,6 +406,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         const int sb = P.samp_width < P.ncell ? ((c_first - P.samp_width / 2) & P.mask) : 0;
         s = gsn.bind(s, P.samp_n, sb, P.samp_width, P.mask);
         s = gsm.bind(s, P.samp_m, sb, P.samp_width, P.mask);
+        if (Tr::energy) s = gse.bind(s, P.samp_e, sb, P.samp_width, P.mask);
     }
     if (kBin) {
         const int nb = P.ncell >> P.bin_shift;
@@ -411,6 +425,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     if (kSamp) {
         gsn.zero();
         gsm.zero();
+        if (Tr::energy) gse.zero();
     }
     if (kBin) {
         bsn.zero();
@@ -479,19 +494,19 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int4 co;
         float4 to, vo, wo;
         int32_t q0, q1, q2, q3;
-        const bool e0 = process<MODE, WALLS>(P, ft, act, ca.x, ta.x, va.x, wa.x, bs, gsn, gsm, gps, acc, acc2, &ovf, co.x,
+        const bool e0 = process<MODE, WALLS>(P, ft, act, ca.x, ta.x, va.x, wa.x, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.x,
                                              to.x, vo.x, wo.x, q0);
         if (kBin) {  // the group's bin window starts at the lowest bin of the lanes' first particles
             bw.begin(warp_low_bin(bs.b, bs.ok, P.ncell >> P.bin_shift));
             if (bs.ok) bw.add(bs.b, q0, bs.mq, bs.tq, bsn, bsm);
         }
-        const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gps, acc, acc2, &ovf, co.y,
+        const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.y,
                                              to.y, vo.y, wo.y, q1);
         if (kBin && bs.ok) bw.add(bs.b, q1, bs.mq, bs.tq, bsn, bsm);
-        const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gps, acc, acc2, &ovf, co.z,
+        const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.z,
                                              to.z, vo.z, wo.z, q2);
         if (kBin && bs.ok) bw.add(bs.b, q2, bs.mq, bs.tq, bsn, bsm);
-        const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gps, acc, acc2, &ovf, co.w,
+        const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.w,
                                              to.w, vo.w, wo.w, q3);
         if (kBin && bs.ok) bw.add(bs.b, q3, bs.mq, bs.tq, bsn, bsm);
         if (kWrite && act) {
@@ -520,7 +535,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         int32_t q;
         const float vi = kNeedV ? P.v[i] : 0.f;
         const float wi = P.w[i];
-        const bool e = process<MODE, WALLS>(P, ft, true, P.cell[i], P.theta[i], vi, wi, bs, gsn, gsm, gps, acc, acc2, &ovf, co,
+        const bool e = process<MODE, WALLS>(P, ft, true, P.cell[i], P.theta[i], vi, wi, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co,
                                             to, vo, wo, q);
         if (kWrite) {
             P.cell[i] = co;
@@ -553,6 +568,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     if (kSamp) {
         gsn.flush();
         gsm.flush();
+        if (Tr::energy) gse.flush();
     }
     if (kBin) {
         bsn.flush();
@@ -567,7 +583,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 template <int MODE>
 constexpr int min_blocks()
 {
-    return ModeTraits<MODE>::ps ? 3 : 4;
+    return (ModeTraits<MODE>::ps || ModeTraits<MODE>::energy) ? 3 : 4;
 }
 
 template <int MODE, bool WALLS>
@@ -637,6 +653,7 @@ struct LoadParams {
     float inv_ppc, two_ppc, inv_two_ppc;
     const float* prof_n;
     const float* prof_u;
+    const float* prof_t;  // THERMAL loads: nodal temperature (velocity variance), linear in X
     float v_th, wscale;
     uint32_t half, shift;
     unsigned long long* rho;
@@ -644,6 +661,7 @@ struct LoadParams {
     uint32_t* status;
 };
 
+template <bool THERMAL>
 __device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
 {
     // Storage slot i holds Hammersley point h. With ppc = 2^m the cell's slots are filled
@@ -675,9 +693,15 @@ __device__ __forceinline__ void load_one(const LoadParams& P, uint32_t i, int& c
     const uint32_t bs = upper ? ~Bi : Bi;  // distance to the nearer end of (0, 1), in 2^-32 units
     const float b = fmaf(__uint2float_rn(bs), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float z = normcdfinvf(b);
-    vv = fmaf(P.v_th, upper ? -z : z, uX);
+    float vt = P.v_th;
+    if (THERMAL) {  // Section 3.2: a Maxwellian of the local temperature T(X)
+        const float t0 = __ldg(P.prof_t + c), t1 = __ldg(P.prof_t + c1);
+        vt = sqrtf(fmaf(th, t1 - t0, t0));
+    }
+    vv = fmaf(vt, upper ? -z : z, uX);
 }
 
+template <bool THERMAL>
 __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
 {
     extern __shared__ uint32_t smem[];
@@ -706,10 +730,10 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
         int4 c;
         float4 t, vv, ww;
         const uint32_t i0 = (uint32_t)(P.first + (g << 2));
-        load_one(P, i0, c.x, t.x, vv.x, ww.x);
-        load_one(P, i0 + 1, c.y, t.y, vv.y, ww.y);
-        load_one(P, i0 + 2, c.z, t.z, vv.z, ww.z);
-        load_one(P, i0 + 3, c.w, t.w, vv.w, ww.w);
+        load_one<THERMAL>(P, i0, c.x, t.x, vv.x, ww.x);
+        load_one<THERMAL>(P, i0 + 1, c.y, t.y, vv.y, ww.y);
+        load_one<THERMAL>(P, i0 + 2, c.z, t.z, vv.z, ww.z);
+        load_one<THERMAL>(P, i0 + 3, c.w, t.w, vv.w, ww.w);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -724,7 +748,7 @@ __global__ void __launch_bounds__(256) k_quiet_start(LoadParams P)
     for (int64_t i = (gb1 << 2) + threadIdx.x; i < end; i += blockDim.x) {
         int c;
         float t, vv, ww;
-        load_one(P, (uint32_t)(P.first + i), c, t, vv, ww);
+        load_one<THERMAL>(P, (uint32_t)(P.first + i), c, t, vv, ww);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;
@@ -998,13 +1022,17 @@ static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
         P.rho_width = 0;
     }
     P.samp_width = (samp && !bin) ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
+    // three nodal moments: a narrower window (co-moving targets beyond it go to the global rows),
+    // so that three blocks fit on an SM
+    if (ModeTraits<MODE>::energy) P.samp_width = P.ncell <= kWindowNodesE ? P.ncell : kWindowNodesE;
     const int nb = bin ? (P.ncell >> P.bin_shift) : 0;
     const bool ps = ModeTraits<MODE>::ps;
     const int nxc = P.ncell >> P.bin_shift;
     P.ps_width = ps ? ps_window_rows(nxc, P.nv) : 0;
     if (ps) P.samp_width = 0;
     const size_t tab = MODE == kDeposit ? 0 : (samp ? sizeof(float4) : sizeof(float2)) * (size_t)kFieldTabNodes;
-    size_t smem = tab + kSmemGridWords * sizeof(uint32_t) * (size_t)(P.rho_width + 2 * P.samp_width) +
+    const int nmom = ModeTraits<MODE>::energy ? 3 : 2;
+    size_t smem = tab + kSmemGridWords * sizeof(uint32_t) * (size_t)(P.rho_width + nmom * P.samp_width) +
                   kBinGridWords * sizeof(uint32_t) * 2 * nb +
                   3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
     smem = with_stage(smem, block, ModeTraits<MODE>::stage);
@@ -1015,7 +1043,7 @@ static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
     // the pass accumulates into a zeroed charge grid and sample row (zeroed by the caller when !zero)
     if (zero && rho && cudaMemsetAsync(P.rho, 0, sizeof(int64_t) * (size_t)P.ncell, s) != cudaSuccess)
         return PE_ECUDA;
-    const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : 2 * (size_t)(P.ncell >> P.bin_shift);
+    const size_t samp_words = ps ? (size_t)nxc * (size_t)P.nv : (size_t)nmom * (size_t)(P.ncell >> P.bin_shift);
     if (zero && samp && cudaMemsetAsync(P.samp_n, 0, sizeof(int64_t) * samp_words, s) != cudaSuccess)
         return PE_ECUDA;
     if (P.n == 0) return PE_OK;
@@ -1039,6 +1067,9 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
     if (s->boundary != PE_BOUNDARY_PERIODIC && s->boundary != PE_BOUNDARY_ABSORBING) return false;
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
     if (s->n_v < 0 || s->n_v > 1024) return false;
+    if (s->second_moment != 0 && (s->second_moment != 1 || s->bin_shift != 0 || s->n_v != 0 ||
+                                  s->boundary != PE_BOUNDARY_PERIODIC || s->s_e < -64 || s->s_e > 64))
+        return false;
     if (s->x_tent != 0 && (s->x_tent != 1 || s->n_v <= 0 || s->boundary != PE_BOUNDARY_PERIODIC)) return false;
     if (s->n_v > 0 && (ncell >> s->bin_shift) > 32767) return false;  // phase-space keys pack (row << 16) | cell
     if (s->n_v > 0) {
@@ -1198,6 +1229,11 @@ int push_pass(int32_t* cell, float* theta, float* v, float* w, int64_t n, const 
             return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream, zero);
         }
         if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream, zero);
+        if (sample->second_moment) {
+            P.samp_e = P.samp_n + 2 * (size_t)ncell;
+            P.escale = ldexpf(1.0f, sample->s_e);
+            return launch_particles<kPushSampleE>(P, (cudaStream_t)stream, zero);
+        }
         return launch_particles<kPushSample>(P, (cudaStream_t)stream, zero);
     }
     return launch_particles<kPush>(P, (cudaStream_t)stream, zero);
@@ -1239,6 +1275,11 @@ int sample_pass(const int32_t* cell, const float* theta, const float* v, const f
         return launch_particles<kSamplePS>(P, (cudaStream_t)stream, zero);
     }
     if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream, zero);
+    if (sample->second_moment) {
+        P.samp_e = P.samp_n + 2 * (size_t)ncell;
+        P.escale = ldexpf(1.0f, sample->s_e);
+        return launch_particles<kSampleE>(P, (cudaStream_t)stream, zero);
+    }
     return launch_particles<kSample>(P, (cudaStream_t)stream, zero);
 }
 
@@ -1270,10 +1311,12 @@ extern "C" PE_API int pe_sample(const int32_t* cell, const float* theta, const f
     return sample_pass(cell, theta, v, w, n, Ef, ncell, qm_dt, kick, sample, status, stream, true);
 }
 
-extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w, int64_t first,
-                                           int64_t n, int64_t n_total, int32_t ncell, const float* prof_n,
-                                           const float* prof_u, float v_th, uint64_t seed, int32_t s_w, int64_t* rho_fx,
-                                           uint32_t* status, void* stream)
+// Appendix C's loading of the slots [first, first + n); prof_t != NULL loads at the local
+// temperature instead of v_th.
+static int quiet_start_launch(int32_t* cell, float* theta, float* v, float* w, int64_t first, int64_t n,
+                              int64_t n_total, int32_t ncell, const float* prof_n, const float* prof_u,
+                              const float* prof_t, float v_th, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                              uint32_t* status, void* stream)
 {
     if (!is_pow2(ncell) || ncell < 8 || !prof_n || !prof_u || !particles_ok(cell, theta, v, w, n)) return PE_EINVAL;
     if (n_total % ncell != 0 || n_total == 0 || n_total >= (int64_t(1) << 32)) return PE_EINVAL;
@@ -1295,6 +1338,7 @@ extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v
     P.inv_two_ppc = 1.0f / P.two_ppc;
     P.prof_n = prof_n;
     P.prof_u = prof_u;
+    P.prof_t = prof_t;
     P.v_th = v_th;
     P.wscale = ldexpf(1.0f, s_w);
     P.half = (uint32_t)(2147483648.0 / (double)n_total);
@@ -1309,12 +1353,34 @@ extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v
     P.status = status;
     const int block = 256;
     size_t smem = kSmemGridWords * sizeof(uint32_t) * (size_t)P.rho_width;
-    const void* k = (const void*)k_quiet_start;
+    const void* k = prof_t ? (const void*)k_quiet_start<true> : (const void*)k_quiet_start<false>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
     int grid = particle_grid(k, block, smem, n, &P.chunk);
     if (rho_fx && cudaMemsetAsync(rho_fx, 0, sizeof(int64_t) * (size_t)ncell, s) != cudaSuccess) return PE_ECUDA;
-    k_quiet_start<<<grid, block, smem, s>>>(P);
+    if (prof_t)
+        k_quiet_start<true><<<grid, block, smem, s>>>(P);
+    else
+        k_quiet_start<false><<<grid, block, smem, s>>>(P);
     return launch_status();
+}
+
+extern "C" PE_API int pe_quiet_start_slice(int32_t* cell, float* theta, float* v, float* w, int64_t first,
+                                           int64_t n, int64_t n_total, int32_t ncell, const float* prof_n,
+                                           const float* prof_u, float v_th, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                                           uint32_t* status, void* stream)
+{
+    return quiet_start_launch(cell, theta, v, w, first, n, n_total, ncell, prof_n, prof_u, nullptr, v_th, seed, s_w,
+                              rho_fx, status, stream);
+}
+
+extern "C" PE_API int pe_quiet_start_thermal(int32_t* cell, float* theta, float* v, float* w, int64_t n,
+                                             int32_t ncell, const float* prof_n, const float* prof_u,
+                                             const float* prof_T, uint64_t seed, int32_t s_w, int64_t* rho_fx,
+                                             uint32_t* status, void* stream)
+{
+    if (!prof_T) return PE_EINVAL;
+    return quiet_start_launch(cell, theta, v, w, 0, n, n, ncell, prof_n, prof_u, prof_T, 0.0f, seed, s_w, rho_fx,
+                              status, stream);
 }
 
 extern "C" PE_API int pe_quiet_start(int32_t* cell, float* theta, float* v, float* w, int64_t n, int32_t ncell,

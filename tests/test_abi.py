@@ -146,3 +146,29 @@ def test_layout_of_the_phase_space_wavelet_form(lib):
             b.layout(cfg(**bad))
     with pytest.raises(RuntimeError):  # the wavelet form belongs to the phase-space variable
         b.layout(b.make_config(4096, 256, 20, 1 << 24, 2048.0, 0.1, 8.0, n_v_coarse=16))
+
+
+def test_layout_of_the_pressure_variable(lib):
+    # three nodal moment rows per sample, [3][n_coarse] coarse state, (n, u, T) profiles; the
+    # kind is refused on bounded grids, with kinetic electrons and above 4096 cells
+    from paper_1610_01071_gb300 import _binding as b
+
+    def cfg(**kw):
+        a = dict(ncell=4096, n_coarse=256, K=20, nparticles=1 << 24, L=2048.0, dt=0.1, dT=20.0,
+                 coarse="moments_pressure")
+        a.update(kw)
+        return b.make_config(**a)
+
+    lay = b.layout(cfg())
+    assert lay.bytes[b.BUF["samples_fx"]] == 8 * 3 * 4096 * 22  # [K+2][3][ncell]
+    assert lay.bytes[b.BUF["coarse"]] == 8 * 3 * 256
+    assert lay.bytes[b.BUF["profile"]] == 4 * 3 * 4096
+    for bad in (dict(boundary="absorbing"), dict(electrons="kinetic"),
+                dict(ncell=8192, nparticles=1 << 25, n_coarse=512, L=4096.0)):
+        with pytest.raises(RuntimeError):
+            b.layout(cfg(**bad))
+    s_e = ctypes.c_int32()
+    assert lib.pe_second_moment_shift(ctypes.c_int64(1 << 24), 4096, ctypes.c_double(0.0), ctypes.c_double(0.0),
+                                      ctypes.byref(s_e)) == 0
+    # the largest |w V~^2| = (8 ncell / N) 32^2 = 2 maps to 2^22
+    assert s_e.value == 21
