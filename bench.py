@@ -866,7 +866,43 @@ def run_accuracy(dev, cfg, pb):
         ad["eps_at_T_end_below_2pct"] = ad["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
         runs.append(ad)
     out["phase_space"] = runs
+    # the ion pressure active (Section 3.2, EFREE's n, V, P): three nodal moments, lifting at the
+    # local temperature, bursts of K at Delta t = 20, 10 and 8
+    out["pressure"] = [run_pressure(dev, cfg, pb, want, checks, dT=dT) for dT in (cfg["dT"], 10.0, 8.0)]
+    for r in out["pressure"]:
+        r["speedup_vs_plain_pic"] = t_plain / r["seconds"]
+        r["eps_at_T_end_below_2pct"] = r["eps_coarse_density_at_T"][str(round(steps * cfg["dT"]))] <= 0.02
     return out, want, checks
+
+
+def run_pressure(dev, cfg, pb, want, checks, dT=20.0, K=None):
+    """The moment variable with the ion pressure active (coarse kind moments_pressure): density,
+    momentum and second-moment coefficients projected, Maxwellians of the local temperature at
+    each lift; timed to the end time and compared with the resolved states `want` (coarse
+    density, Section 4.1.1) at the check times this macro step lands on."""
+    import torch
+
+    K = K or cfg["K"]
+    c = pb.make_config(cfg["ncell"], cfg["n_coarse"], K, cfg["N"], cfg["L"], cfg["dt"], dT, qm=cfg["qm"],
+                       v_th=cfg["v_th"], wavelet=cfg["wavelet"], seed=11, newton_tol=1e-10, coarse="moments_pressure")
+    ctx = pb.Context(c, device=dev)
+    ctx.load_initial(cfg["amplitude"])
+    checks = [m for m in checks if abs((m * cfg["dT"] / dT) - round(m * cfg["dT"] / dT)) < 1e-9]
+    targets = {m: m * cfg["dT"] for m in checks}
+    got, t, wall = {}, 0.0, 0.0
+    for m in checks:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        while t < targets[m] - 1e-9:
+            ctx.step()
+            t += dT
+        torch.cuda.synchronize(dev)
+        wall += time.perf_counter() - t0
+        got[m] = ctx.get_coarse()[0].cpu().numpy()
+    T_end = cfg["macro_steps"] * cfg["dT"]
+    eps = {str(round(targets[m])): _eps(got[m], want[m].cpu().numpy()) for m in checks}
+    return {"coarse": "moments + ion pressure", "dT": dT, "K": K, "T_end": T_end, "seconds": wall,
+            "sim_time_per_wall_s": T_end / wall, "eps_coarse_density_at_T": eps, "status": ctx.sync_status()}
 
 
 def run_phase_space(dev, cfg, pb, want, checks, dT=8.0, n_v=64, v_max=8.0, ps_filter=3, K=None, n_v_coarse=0,

@@ -152,7 +152,10 @@ def test_initial_coarse_state_has_the_three_moments():
     dens, mom = orc.restrict_sample(st, st.v, np.zeros(SMALL["ncell"]), SMALL["ncell"], 0.5, 0.0, 1.0)
     sec = orc.restrict_second_moment(st, st.v, np.zeros(SMALL["ncell"]), SMALL["ncell"], 0.5, 0.0, 1.0)
     want = np.stack([orc.coarsen(f, SMALL["n_coarse"]) for f in (dens, mom, sec)])
-    assert np.allclose(got, want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
+    assert np.allclose(got[:2], want[:2], rtol=1e-5, atol=1e-5 * np.abs(want).max())
+    # the second moment's fixed point resolves 2^-s_e per particle (v_cap^2 = 1024 of headroom):
+    # here s_e = 17, i.e. 2e-3 of a typical w V^2, random over the ~256 ions of a node
+    assert np.max(np.abs(got[2] - want[2])) < 1e-4 * np.abs(want[2]).max()
     assert ctx.sync_status() == 0
 
 
