@@ -208,9 +208,10 @@ typedef struct pe_sample_args {
     int32_t second_moment; /* 1: a third nodal moment, the ions' second velocity moment
                               S_j = sum_p w V~^2 S_j(X~) (Section 3.2: EFREE's pressure
                               P = S - (nV)^2 / n is active), in fixed point
-                              e_q = rn(fl32(fl32(w V~) V~) 2^s_e) split like the density; then
-                              sample_fx is int64[3][ncell] (density, momentum, S); needs
-                              bin_shift = 0, n_v = 0 and a periodic grid */
+                              e_q = rn(fl32(fl32(w V~) V~) 2^s_e) split like the density (and
+                              summed over bins like it when bin_shift > 0); then sample_fx is
+                              int64[3][ncell >> bin_shift] (density, momentum, S); needs n_v = 0
+                              and a periodic grid */
     int32_t s_e;           /* second-moment fixed-point shift: |w V~^2| 2^s_e must stay <= 2^22 */
 } pe_sample_args;
 
@@ -350,13 +351,13 @@ PE_API int pe_fixed_point_shifts(int64_t nparticles, int32_t ncell, double w_cap
 PE_API int pe_second_moment_shift(int64_t nparticles, int32_t ncell, double w_cap, double v_cap, int32_t* s_e);
 
 /* Ion pressure as an active variable (Section 3.2, EFREE: ion n, V and P = n T are active,
- * the ions shifted Maxwellians). pe_coarsen for samples of the three nodal moments,
- * sample_fx int64[nsamples][3][ncell] (density at 2^-(s_w+24), momentum at 2^-(s_p+24),
- * second moment at 2^-(s_e+24)): each row is analysed like pe_coarsen's with bin_shift 0 into
- * coarse[nsamples][3][n_coarse]. */
+ * the ions shifted Maxwellians). pe_coarsen for samples of the three moments,
+ * sample_fx int64[nsamples][3][ncell >> bin_shift] (density at 2^-(s_w+24), momentum at
+ * 2^-(s_p+24), second moment at 2^-(s_e+24)): each row is analysed like pe_coarsen's (bin sums
+ * over 2^bin_shift nodes with the Haar wavelet only) into coarse[nsamples][3][n_coarse]. */
 PE_API int pe_coarsen_pressure(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
-                               int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse, double* coarse,
-                               void* stream);
+                               int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse, int32_t bin_shift,
+                               double* coarse, void* stream);
 
 /* Lifting profiles of the three moments (Section 3.2 lifting, zero details): coarse[3][n_coarse]
  * is synthesised to the nodes as in pe_refine; n is clamped at 0 and rescaled to keep its sum,

@@ -144,7 +144,7 @@ SIGNATURES = {
     "pe_quiet_start_f64": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, f64, u64, i32, P, P, P]),
     "pe_fixed_point_shifts": (ctypes.c_int, [i64, i32, f64, f64, P, P]),
     "pe_second_moment_shift": (ctypes.c_int, [i64, i32, f64, f64, P]),
-    "pe_coarsen_pressure": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, i32, P, P]),
+    "pe_coarsen_pressure": (ctypes.c_int, [P, i32, i32, i32, i32, i32, i32, i32, i32, P, P]),
     "pe_refine_pressure": (ctypes.c_int, [P, i32, i32, i32, P, P, P, P]),
     "pe_quiet_start_thermal": (ctypes.c_int, [P, P, P, P, i64, i32, P, P, P, u64, i32, P, P, P]),
     "pe_initial_profile": (ctypes.c_int, [i32, i32, f64, f64, P, P]),
@@ -384,12 +384,13 @@ def second_moment_shift(nparticles, ncell, w_cap=0.0, v_cap=0.0):
     return s_e.value
 
 
-def coarsen_pressure(sample_fx, nsamples, ncell, s_w, s_p, s_e, n_coarse, wavelet="haar", out=None, stream=None):
-    """Three nodal moments [nsamples][3][ncell] -> [nsamples][3][n_coarse] (pe_coarsen_pressure)."""
+def coarsen_pressure(sample_fx, nsamples, ncell, s_w, s_p, s_e, n_coarse, wavelet="haar", out=None, stream=None,
+                     bin_shift=0):
+    """Three moments [nsamples][3][ncell >> bin_shift] -> [nsamples][3][n_coarse] (pe_coarsen_pressure)."""
     out = out if out is not None else torch.empty((nsamples, 3, n_coarse), dtype=torch.float64,
                                                   device=sample_fx.device)
     check(load().pe_coarsen_pressure(_ptr(sample_fx), nsamples, ncell, s_w, s_p, s_e, PE_WAVELET[wavelet], n_coarse,
-                                     _ptr(out), _stream(stream)), "pe_coarsen_pressure")
+                                     int(bin_shift), _ptr(out), _stream(stream)), "pe_coarsen_pressure")
     return out
 
 

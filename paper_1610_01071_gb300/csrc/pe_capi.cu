@@ -253,9 +253,9 @@ extern "C" PE_API int pe_create(const pe_config* cfg, void* arena, size_t arena_
     x->ps = cfg->coarse_kind == PE_COARSE_PHASE_SPACE;
     x->psw = x->ps && cfg->n_v_coarse > 0;
     x->pres = cfg->coarse_kind == PE_COARSE_MOMENTS_PRESSURE;
-    // Haar moments and both phase-space forms restrict over 2^b nodes in x (bins or hat rows);
-    // the three moments of the pressure variable are sampled on the nodes
-    x->bin_shift = ((cfg->wavelet == PE_WAVELET_HAAR && !x->pres) || x->ps) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
+    // Haar moments (with or without the pressure) and both phase-space forms restrict over 2^b
+    // nodes in x (bins or hat rows)
+    x->bin_shift = (cfg->wavelet == PE_WAVELET_HAAR || x->ps) ? ilog2(cfg->ncell / cfg->n_coarse) : 0;
     x->nb = cfg->ncell >> x->bin_shift;
     x->nv = x->ps ? cfg->n_v : 0;
     x->nvc = x->psw ? cfg->n_v_coarse : x->nv;
@@ -649,7 +649,8 @@ static int measure_pressure(pe_ctx* x, double* out)
     const float kick = x->v_at_integer ? 0.5f : 1.0f;
     PE_TRY(pe_sample(x->cell[b], x->theta[b], x->v[b], x->w[b], c.nparticles, x->Ef, c.ncell, (float)(c.qm * c.dt), kick,
                      &a, x->status, x->stream));
-    return pe_coarsen_pressure(dst, 1, c.ncell, x->s_w, x->s_p, x->s_e, c.wavelet, x->nc, out, x->stream);
+    return pe_coarsen_pressure(dst, 1, c.ncell, x->s_w, x->s_p, x->s_e, c.wavelet, x->nc, x->bin_shift, out,
+                               x->stream);
 }
 
 // Phase-space cell masses of the current particles (co-moving sample with tau = 0) into
@@ -799,7 +800,7 @@ extern "C" PE_API int pe_restrict(pe_ctx* ctx)
     if (ctx->ps) return pe_ps_coarsen(ctx->samples, ctx->K_cur + 1, ctx->ncoef, ctx->s_w, ctx->csamples, ctx->stream);
     if (ctx->pres)  // Section 3.2: n, nV and the second moment, each to its scaling coefficients
         return pe_coarsen_pressure(ctx->samples, ctx->K_cur + 1, c.ncell, ctx->s_w, ctx->s_p, ctx->s_e, c.wavelet,
-                                   ctx->nc, ctx->csamples, ctx->stream);
+                                   ctx->nc, ctx->bin_shift, ctx->csamples, ctx->stream);
     return pe_coarsen(ctx->samples, ctx->K_cur + 1, c.ncell, ctx->s_w, ctx->s_p, c.wavelet, ctx->nc, ctx->bin_shift,
                       ctx->csamples, ctx->stream);
 }

@@ -615,17 +615,20 @@ extern "C" PE_API int pe_coarsen(const int64_t* sample_fx, int32_t nsamples, int
 }
 
 extern "C" PE_API int pe_coarsen_pressure(const int64_t* sample_fx, int32_t nsamples, int32_t ncell, int32_t s_w,
-                                          int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse, double* coarse,
-                                          void* stream)
+                                          int32_t s_p, int32_t s_e, int32_t wavelet, int32_t n_coarse,
+                                          int32_t bin_shift, double* coarse, void* stream)
 {
     if (!is_pow2(ncell) || !is_pow2(n_coarse) || n_coarse > ncell || nsamples < 1 || !sample_fx || !coarse)
         return PE_EINVAL;
     if (!wavelet_ok(wavelet)) return PE_EINVAL;
-    const size_t smem = 2 * sizeof(double) * (size_t)ncell;
+    if (bin_shift < 0 || (bin_shift > 0 && wavelet != PE_WAVELET_HAAR) || (ncell >> bin_shift) < n_coarse)
+        return PE_EINVAL;
+    const int nb = ncell >> bin_shift;  // input length per row
+    const size_t smem = 2 * sizeof(double) * (size_t)nb;
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
     if (ensure_smem((const void*)k_coarsen, smem) != PE_OK) return PE_ECUDA;
-    const double lev = pow(2.0, -0.5 * ilog2(ncell));
-    k_coarsen<<<3 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), ncell, 3,
+    const double lev = pow(2.0, -0.5 * (ilog2(ncell) + bin_shift));
+    k_coarsen<<<3 * nsamples, 256, smem, (cudaStream_t)stream>>>(reinterpret_cast<const long long*>(sample_fx), nb, 3,
                                                                  ldexp(1.0, -(s_w + 24)) * lev,
                                                                  ldexp(1.0, -(s_p + 24)) * lev,
                                                                  ldexp(1.0, -(s_e + 24)) * lev, make_filter(wavelet),

@@ -577,6 +577,50 @@ struct BinWindow {
     }
 };
 
+// BinWindow with a third moment (the second velocity moment of the pressure variable): the
+// same window and transfers for e_q, summed and added by lanes 4, 5 and a third transfer.
+struct BinWindow3 {
+    BinWindow w;
+    int32_t e0, e1;
+    long long te;
+
+    __device__ __forceinline__ void begin(int k)
+    {
+        w.begin(k);
+        e0 = e1 = 0;
+        te = 0;
+    }
+
+    __device__ __forceinline__ void add(int b, int32_t wq, int32_t mq, int32_t eq, uint32_t tq, const BinGrid& gn,
+                                        const BinGrid& gm, const BinGrid& ge)
+    {
+        const int d = (b - w.K) & (gn.nb - 1);
+        if (d == 0) {
+            e0 += eq;
+            te += (long long)eq * (long long)tq;
+        } else if (d == 1 && tq == 0u) {
+            e1 += eq;
+        } else {
+            ge.add_whole(b, eq);
+            if (tq) ge.add_transfer(b, (long long)eq * (long long)tq);
+        }
+        w.add(b, wq, mq, tq, gn, gm);
+    }
+
+    __device__ __forceinline__ void end(const BinGrid& gn, const BinGrid& gm, const BinGrid& ge) const
+    {
+        w.end(gn, gm);
+        const int lane = threadIdx.x & 31;
+        const int32_t E0 = __reduce_add_sync(0xFFFFFFFFu, e0), E1 = __reduce_add_sync(0xFFFFFFFFu, e1);
+        const int32_t v = lane == 0 ? E0 : E1;
+        if (lane < 2 && v != 0) ge.add_whole((w.K + lane) & (gn.nb - 1), v);
+        if (__any_sync(0xFFFFFFFFu, te != 0)) {
+            const long long TE = warp_sum64(0xFFFFFFFFu, te);
+            if (lane == 0) ge.add_transfer(w.K, TE);
+        }
+    }
+};
+
 // Warp-uniform base bin of a group: the lowest of the lanes' bins b (where ok), compared
 // periodically around lane 0's bin; all 32 lanes, converged.
 __device__ __forceinline__ int warp_low_bin(int b, bool ok, int nb)

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <climits>
+#include <type_traits>
 
 #include "pe_common.cuh"
 #include "pe_eq.cuh"
@@ -71,21 +72,28 @@ enum Mode {
     kPushSamplePSW = 8,  // push + phase-space sample with hat rows (the wavelet form)
     kSamplePSW = 9,
     kPushSampleE = 10,  // push + nodal sample of density, momentum and second moment
-    kSampleE = 11
+    kSampleE = 11,
+    kPushSampleBinnedE = 12,  // push + Haar-binned sample of the three moments
+    kSampleBinnedE = 13
 };
 
 template <int MODE>
 struct ModeTraits {
     static constexpr bool rho = (MODE == kDeposit || MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                 MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE);
+                                 MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE ||
+                                 MODE == kPushSampleBinnedE);
     static constexpr bool push = (MODE == kPush || MODE == kPushSample || MODE == kPushSampleBinned ||
-                                  MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE);
+                                  MODE == kPushSamplePS || MODE == kPushSamplePSW || MODE == kPushSampleE ||
+                                  MODE == kPushSampleBinnedE);
     static constexpr bool sample = (MODE == kPushSample || MODE == kSample || MODE == kPushSampleBinned ||
                                     MODE == kSampleBinned || MODE == kPushSamplePS || MODE == kSamplePS ||
                                     MODE == kPushSamplePSW || MODE == kSamplePSW || MODE == kPushSampleE ||
-                                    MODE == kSampleE);
-    static constexpr bool energy = (MODE == kPushSampleE || MODE == kSampleE);  // third nodal moment
-    static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned);
+                                    MODE == kSampleE || MODE == kPushSampleBinnedE || MODE == kSampleBinnedE);
+    // third moment (the second velocity moment), nodal or binned
+    static constexpr bool energy = (MODE == kPushSampleE || MODE == kSampleE || MODE == kPushSampleBinnedE ||
+                                    MODE == kSampleBinnedE);
+    static constexpr bool binned = (MODE == kPushSampleBinned || MODE == kSampleBinned || MODE == kPushSampleBinnedE ||
+                                    MODE == kSampleBinnedE);
     static constexpr bool tent = (MODE == kPushSamplePSW || MODE == kSamplePSW);
     static constexpr bool ps = (MODE == kPushSamplePS || MODE == kSamplePS || tent);
     // particle streams staged through shared memory (cp.async, one group ahead): the phase-space
@@ -168,6 +176,7 @@ __device__ __forceinline__ bool inside_walls(const PushParams& P, int c, float f
 struct BinSample {
     int b;
     int32_t mq;
+    int32_t eq;  // second moment (the energy modes)
     uint32_t tq;
     bool ok;
 };
@@ -186,6 +195,7 @@ __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft,
     wq_out = 0;
     bs.b = 0;
     bs.mq = 0;
+    if (Tr::energy) bs.eq = 0;
     bs.tq = 0u;
     bs.ok = false;
     if (!act) return false;  // a lane past the end of its warp's slice
@@ -270,6 +280,7 @@ __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft,
                 const int bm = (1 << P.bin_shift) - 1;
                 bs.b = cs >> P.bin_shift;
                 bs.mq = mq;
+                if (Tr::energy) bs.eq = fx_weight(__fmul_rn(__fmul_rn(ww, vt), vt), P.escale, ovf);
                 bs.tq = ((cs & bm) == bm) ? __float2uint_rn(ths * kThetaOneF) : 0u;
                 bs.ok = true;
             } else {
@@ -380,7 +391,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     const int c_first = (begin < end) ? (P.cell[begin] & P.mask) : 0;
 
     SmemGrid grho{}, gsn{}, gsm{}, gse{};
-    BinGrid bsn{}, bsm{};
+    BinGrid bsn{}, bsm{}, bse{};
     PSGrid gps{};
     constexpr bool kPS = Tr::ps;
     uint32_t* s = smem;
@@ -411,6 +422,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     if (kBin) {
         const int nb = P.ncell >> P.bin_shift;
         s = bsn.bind(s, P.samp_n, nb);
+        if (Tr::energy) s = bse.bind(s, P.samp_e, nb);
         s = bsm.bind(s, P.samp_m, nb);
     }
     if (kPS) {
@@ -428,6 +440,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         if (Tr::energy) gse.zero();
     }
     if (kBin) {
+        if (Tr::energy) bse.zero();
         bsn.zero();
         bsm.zero();
     }
@@ -439,9 +452,16 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
     const int lane = threadIdx.x & 31;
     WarpWindow win;
     win.reset(((g0 < g1 ? P.cell[g0 << 2] : c_first) - 1) & P.mask);  // the same address in every lane
-    BinWindow bw;
+    typename std::conditional<Tr::energy, BinWindow3, BinWindow>::type bw;
     bw.begin(0);
     BinSample bs;
+    // adds this lane's binned sample of one particle (weight q) through the warp's bin window
+    auto bin_add = [&](int32_t q) {
+        if constexpr (Tr::energy)
+            bw.add(bs.b, q, bs.mq, bs.eq, bs.tq, bsn, bsm, bse);
+        else
+            bw.add(bs.b, q, bs.mq, bs.tq, bsn, bsm);
+    };
     PSAcc acc;
     PSAcc2 acc2;  // hat rows
     acc.reset();
@@ -498,17 +518,17 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
                                              to.x, vo.x, wo.x, q0);
         if (kBin) {  // the group's bin window starts at the lowest bin of the lanes' first particles
             bw.begin(warp_low_bin(bs.b, bs.ok, P.ncell >> P.bin_shift));
-            if (bs.ok) bw.add(bs.b, q0, bs.mq, bs.tq, bsn, bsm);
+            if (bs.ok) bin_add(q0);
         }
         const bool e1 = process<MODE, WALLS>(P, ft, act, ca.y, ta.y, va.y, wa.y, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.y,
                                              to.y, vo.y, wo.y, q1);
-        if (kBin && bs.ok) bw.add(bs.b, q1, bs.mq, bs.tq, bsn, bsm);
+        if (kBin && bs.ok) bin_add(q1);
         const bool e2 = process<MODE, WALLS>(P, ft, act, ca.z, ta.z, va.z, wa.z, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.z,
                                              to.z, vo.z, wo.z, q2);
-        if (kBin && bs.ok) bw.add(bs.b, q2, bs.mq, bs.tq, bsn, bsm);
+        if (kBin && bs.ok) bin_add(q2);
         const bool e3 = process<MODE, WALLS>(P, ft, act, ca.w, ta.w, va.w, wa.w, bs, gsn, gsm, gse, gps, acc, acc2, &ovf, co.w,
                                              to.w, vo.w, wo.w, q3);
-        if (kBin && bs.ok) bw.add(bs.b, q3, bs.mq, bs.tq, bsn, bsm);
+        if (kBin && bs.ok) bin_add(q3);
         if (kWrite && act) {
             cell4[g] = co;
             th4[g] = to;
@@ -525,7 +545,10 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
                 acc.reset();
             }
         }
-        if (kBin) bw.end(bsn, bsm);
+        if constexpr (kBin && Tr::energy)
+            bw.end(bsn, bsm, bse);
+        else if constexpr (kBin)
+            bw.end(bsn, bsm);
         if (kRho) deposit_group(win, grho, P.ncell, P.mask, co, to, q0, q1, q2, q3, e0, e1, e2, e3);
     }
     if (kRho) win.flush_first(grho, 4);
@@ -555,9 +578,11 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         if (kBin && bs.ok) {  // straight to the grids
             bsn.add_whole(bs.b, q);
             bsm.add_whole(bs.b, bs.mq);
+            if (Tr::energy) bse.add_whole(bs.b, bs.eq);
             if (bs.tq) {
                 bsn.add_transfer(bs.b, (long long)q * (long long)bs.tq);
                 bsm.add_transfer(bs.b, (long long)bs.mq * (long long)bs.tq);
+                if (Tr::energy) bse.add_transfer(bs.b, (long long)bs.eq * (long long)bs.tq);
             }
         }
         if (kRho && e) deposit_direct(grho, co, to, q, P.mask);
@@ -571,6 +596,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         if (Tr::energy) gse.flush();
     }
     if (kBin) {
+        if (Tr::energy) bse.flush();
         bsn.flush();
         bsm.flush();
     }
@@ -1024,7 +1050,7 @@ static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
     P.samp_width = (samp && !bin) ? (P.ncell <= kWindowNodes ? P.ncell : kWindowNodes) : 0;
     // three nodal moments: a narrower window (co-moving targets beyond it go to the global rows),
     // so that three blocks fit on an SM
-    if (ModeTraits<MODE>::energy) P.samp_width = P.ncell <= kWindowNodesE ? P.ncell : kWindowNodesE;
+    if (ModeTraits<MODE>::energy && !bin) P.samp_width = P.ncell <= kWindowNodesE ? P.ncell : kWindowNodesE;
     const int nb = bin ? (P.ncell >> P.bin_shift) : 0;
     const bool ps = ModeTraits<MODE>::ps;
     const int nxc = P.ncell >> P.bin_shift;
@@ -1033,7 +1059,7 @@ static int launch_particles(PushParams& P, cudaStream_t s, bool zero = true)
     const size_t tab = MODE == kDeposit ? 0 : (samp ? sizeof(float4) : sizeof(float2)) * (size_t)kFieldTabNodes;
     const int nmom = ModeTraits<MODE>::energy ? 3 : 2;
     size_t smem = tab + kSmemGridWords * sizeof(uint32_t) * (size_t)(P.rho_width + nmom * P.samp_width) +
-                  kBinGridWords * sizeof(uint32_t) * 2 * nb +
+                  kBinGridWords * sizeof(uint32_t) * (size_t)nmom * nb +
                   3 * sizeof(uint32_t) * (size_t)P.ps_width * (size_t)P.nv;
     smem = with_stage(smem, block, ModeTraits<MODE>::stage);
     if (smem > (size_t)max_smem_optin()) return PE_EINVAL;
@@ -1067,8 +1093,8 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
     if (s->boundary != PE_BOUNDARY_PERIODIC && s->boundary != PE_BOUNDARY_ABSORBING) return false;
     if (s->bin_shift < 0 || (1 << s->bin_shift) > ncell) return false;
     if (s->n_v < 0 || s->n_v > 1024) return false;
-    if (s->second_moment != 0 && (s->second_moment != 1 || s->bin_shift != 0 || s->n_v != 0 ||
-                                  s->boundary != PE_BOUNDARY_PERIODIC || s->s_e < -64 || s->s_e > 64))
+    if (s->second_moment != 0 && (s->second_moment != 1 || s->n_v != 0 || s->boundary != PE_BOUNDARY_PERIODIC ||
+                                  s->s_e < -64 || s->s_e > 64))
         return false;
     if (s->x_tent != 0 && (s->x_tent != 1 || s->n_v <= 0 || s->boundary != PE_BOUNDARY_PERIODIC)) return false;
     if (s->n_v > 0 && (ncell >> s->bin_shift) > 32767) return false;  // phase-space keys pack (row << 16) | cell
@@ -1078,7 +1104,8 @@ static bool sample_ok(const pe_sample_args* s, int ncell)
         return s->inv_dv > 0.0f && 3 * sizeof(uint32_t) * w * (size_t)s->n_v <= 160 * 1024;
     }
     if (s->bin_shift == 0) return true;
-    return (kBinGridWords * 2 * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
+    const size_t nmom = s->second_moment ? 3 : 2;
+    return (kBinGridWords * nmom * (size_t)(ncell >> s->bin_shift)) * sizeof(uint32_t) <= 96 * 1024;  // bins fit in shared memory
 }
 
 // ------------------------------------------------------------------ batched launches
@@ -1228,12 +1255,13 @@ int push_pass(int32_t* cell, float* theta, float* v, float* w, int64_t n, const 
             if (sample->x_tent) return launch_particles<kPushSamplePSW>(P, (cudaStream_t)stream, zero);
             return launch_particles<kPushSamplePS>(P, (cudaStream_t)stream, zero);
         }
-        if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream, zero);
-        if (sample->second_moment) {
-            P.samp_e = P.samp_n + 2 * (size_t)ncell;
+        if (sample->second_moment) {  // rows [3][ncell >> bin_shift]
+            P.samp_e = P.samp_n + 2 * (size_t)(ncell >> P.bin_shift);
             P.escale = ldexpf(1.0f, sample->s_e);
+            if (P.bin_shift > 0) return launch_particles<kPushSampleBinnedE>(P, (cudaStream_t)stream, zero);
             return launch_particles<kPushSampleE>(P, (cudaStream_t)stream, zero);
         }
+        if (P.bin_shift > 0) return launch_particles<kPushSampleBinned>(P, (cudaStream_t)stream, zero);
         return launch_particles<kPushSample>(P, (cudaStream_t)stream, zero);
     }
     return launch_particles<kPush>(P, (cudaStream_t)stream, zero);
@@ -1274,12 +1302,13 @@ int sample_pass(const int32_t* cell, const float* theta, const float* v, const f
         if (sample->x_tent) return launch_particles<kSamplePSW>(P, (cudaStream_t)stream, zero);
         return launch_particles<kSamplePS>(P, (cudaStream_t)stream, zero);
     }
-    if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream, zero);
-    if (sample->second_moment) {
-        P.samp_e = P.samp_n + 2 * (size_t)ncell;
+    if (sample->second_moment) {  // rows [3][ncell >> bin_shift]
+        P.samp_e = P.samp_n + 2 * (size_t)(ncell >> P.bin_shift);
         P.escale = ldexpf(1.0f, sample->s_e);
+        if (P.bin_shift > 0) return launch_particles<kSampleBinnedE>(P, (cudaStream_t)stream, zero);
         return launch_particles<kSampleE>(P, (cudaStream_t)stream, zero);
     }
+    if (P.bin_shift > 0) return launch_particles<kSampleBinned>(P, (cudaStream_t)stream, zero);
     return launch_particles<kSample>(P, (cudaStream_t)stream, zero);
 }
 

@@ -48,11 +48,20 @@ def test_second_moment_sample_matches_oracle(tau, ncell, N):
     out2 = torch.empty(2 * ncell, dtype=torch.int64, device=DEV)
     pe.sample(dc, dt_, dv, dw, Ef, ncell, qm * dt, 1.0, pe.make_sample_args(E0f, tau, qm, 1 / dx, s_w, s_p, out2))
     assert np.array_equal(g[:2 * ncell], out2.cpu().numpy())
+    # Haar bins: exact bin sums of the nodal fixed-point rows, all three moments
+    for bsh in (1, 4):
+        outb = torch.empty(3 * (ncell >> bsh), dtype=torch.int64, device=DEV)
+        pe.sample(dc, dt_, dv, dw, Ef, ncell, qm * dt, 1.0,
+                  pe.make_sample_args(E0f, tau, qm, 1 / dx, s_w, s_p, outb, bin_shift=bsh, s_e=s_e), status=st)
+        want_b = g.reshape(3, ncell >> bsh, 1 << bsh).sum(axis=-1).reshape(-1)
+        assert np.array_equal(outb.cpu().numpy(), want_b)
+    assert int(st.item()) == 0
 
 
-def test_fused_push_second_moment_equals_sample_pass():
+@pytest.mark.parametrize("bin_shift", [0, 3])
+def test_fused_push_second_moment_equals_sample_pass(bin_shift):
     # the fused pass samples the current particles before moving them: its rows equal those of
-    # the sample-only pass on the same state
+    # the sample-only pass on the same state (nodal and Haar-binned)
     ncell, N, dx, dt, qm = 512, (1 << 17) + 1, 0.5, 0.1, 1.0
     c, t, v, w = inputs.random_particles(N, ncell, seed=2)
     s_w = orc.fx_shift(2.0 * ncell / N)
@@ -62,20 +71,29 @@ def test_fused_push_second_moment_equals_sample_pass():
     Ef, = to_dev(E.astype(np.float32))
     a = to_dev(c, t, v, w)
     b = [x.clone() for x in a]
-    out_s = torch.empty(3 * ncell, dtype=torch.int64, device=DEV)
+    out_s = torch.empty(3 * (ncell >> bin_shift), dtype=torch.int64, device=DEV)
     out_p = torch.empty_like(out_s)
-    pe.sample(*a, Ef, ncell, qm * dt, 0.5, pe.make_sample_args(Ef, 5.0, qm, 1 / dx, s_w, s_p, out_s, s_e=s_e))
-    pe.push(*b, Ef, ncell, dt / dx, qm * dt, 0.5, s_w, sample=pe.make_sample_args(Ef, 5.0, qm, 1 / dx, s_w, s_p, out_p,
-                                                                                   s_e=s_e))
+    pe.sample(*a, Ef, ncell, qm * dt, 0.5,
+              pe.make_sample_args(Ef, 5.0, qm, 1 / dx, s_w, s_p, out_s, bin_shift=bin_shift, s_e=s_e))
+    pe.push(*b, Ef, ncell, dt / dx, qm * dt, 0.5, s_w,
+            sample=pe.make_sample_args(Ef, 5.0, qm, 1 / dx, s_w, s_p, out_p, bin_shift=bin_shift, s_e=s_e))
     assert torch.equal(out_s, out_p)
+    # the pushed particles are those of the plain push
+    c2 = to_dev(c, t, v, w)
+    pe.push(*c2, Ef, ncell, dt / dx, qm * dt, 0.5, s_w)
+    for x, y in zip(b, c2):
+        assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("wav,ncell,nc", [("haar", 128, 16), ("haar", 4096, 256), ("coif4", 512, 32)])
-def test_coarsen_pressure_matches_oracle(wav, ncell, nc):
+@pytest.mark.parametrize("wav,ncell,nc,bsh", [("haar", 128, 16, 0), ("haar", 4096, 256, 0), ("coif4", 512, 32, 0),
+                                              ("haar", 4096, 256, 4), ("haar", 128, 16, 2)])
+def test_coarsen_pressure_matches_oracle(wav, ncell, nc, bsh):
     rng = np.random.default_rng(ncell + 1)
     nsamp, s_w, s_p, s_e = 4, 30, 25, 21
     fx = rng.integers(-(1 << 50), 1 << 50, size=(nsamp, 3, ncell), dtype=np.int64)
-    out = pe.coarsen_pressure(*to_dev(fx), nsamp, ncell, s_w, s_p, s_e, nc, wavelet=wav).cpu().numpy()
+    rows = fx.reshape(nsamp, 3, ncell >> bsh, 1 << bsh).sum(axis=-1)  # bin sums when bsh > 0
+    out = pe.coarsen_pressure(*to_dev(rows), nsamp, ncell, s_w, s_p, s_e, nc, wavelet=wav,
+                              bin_shift=bsh).cpu().numpy()
     for p in range(nsamp):
         for m, s in ((0, s_w), (1, s_p), (2, s_e)):
             want = orc.coarsen(fx[p, m] * 2.0 ** -(s + 24), nc, wav)
