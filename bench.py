@@ -45,6 +45,9 @@ KERNEL_BYTES = {
     "push_sample_psw": (28, "k_particles<push + phase-space sample, hat rows> (wavelet form: 16 coarse nodes x "
                             "256 velocity cells window)"),
     "load_psw": (16, "k_ps_quiet_start on fine-node tables (wavelet-form lifting, write only)"),
+    "push_sample_pressure": (28, "k_particles<push + binned sample of density, momentum and second moment> "
+                                 "(ion pressure active)"),
+    "load_thermal": (16, "k_quiet_start<thermal> (lifting at the local temperature, deposit fused, write only)"),
     "push_sample_slab": (28, "k_particles<push + binned moment sample, walls> on the slab (2^25 ions, 8192 cells)"),
     "push_sample_ps_slab": (28, "k_particles<push + phase-space sample, walls> on the slab (2^25 ions)"),
 }
@@ -554,6 +557,24 @@ def time_kernels(ctx, cfg, pb, stream, reps=10):
         out["load_psw"] = (kk["load"]["ms"] / max(kk["load"]["launches"], 1), kk["load"]["launches"])
         if pw.sync_status() != 0:
             raise RuntimeError("device status set while timing the wavelet-form passes")
+        del pw
+        # the moment variable with the ion pressure (three Haar-binned moments, thermal lifting)
+        c = pb.make_config(ncell, cfg["n_coarse"], cfg["K"], N, cfg["L"], cfg["dt"], cfg["dT"], qm=cfg["qm"],
+                           v_th=cfg["v_th"], seed=13, newton_tol=1e-10, coarse="moments_pressure")
+        pp = pb.Context(c, device=dev, stream=stream)
+        pp.load_initial(cfg["amplitude"])
+        pp.step()
+        pp.profile_read_kinds()
+        pp.profile(True)
+        for _ in range(2):
+            pp.step()
+        pp.profile(False)
+        kk = pp.profile_read_kinds()
+        out["push_sample_pressure"] = (kk["push_sample"]["ms"] / max(kk["push_sample"]["launches"], 1),
+                                       kk["push_sample"]["launches"])
+        out["load_thermal"] = (kk["load"]["ms"] / max(kk["load"]["launches"], 1), kk["load"]["launches"])
+        if pp.sync_status() != 0:
+            raise RuntimeError("device status set while timing the pressure variable's passes")
     return out
 
 
@@ -653,8 +674,8 @@ def run_kernel_kinetic(args):
 
 def run_kernel(args):
     """Times one hot-path kernel alone on the workload's particle state (for profiling):
-    ``--kernel push_sample|push|deposit|sample|field|quiet_start|push_sample_ps|ps_tables|
-    ps_quiet_start|push_sample_ps_slab|kinetic|ensemble``."""
+    ``--kernel push_sample|push|deposit|sample|field|quiet_start|push_sample_ps|push_sample_psw|
+    push_sample_pressure|ps_tables|ps_quiet_start|push_sample_ps_slab|kinetic|ensemble|tc_gemm``."""
     import torch
 
     if args.kernel == "push_sample_ps_slab":
@@ -705,6 +726,9 @@ def run_kernel(args):
     samp_psw = torch.zeros((nxc, 256), dtype=torch.int64, device=dev)
     args_psw = pb.make_sample_args(Ef, 10.0, cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp_psw, bin_shift=bshift, n_v=256,
                                    v_min=-8.0, dv=16.0 / 256, x_tent=True)
+    samp3 = torch.zeros(3 * (ncell >> bshift), dtype=torch.int64, device=dev)
+    args_e = pb.make_sample_args(Ef, cfg["dT"], cfg["qm"], 1.0 / dx, d.s_w, d.s_p, samp3, bin_shift=bshift,
+                                 s_e=pb.second_moment_shift(N, ncell))
     if args.kernel in ("ps_tables", "ps_quiet_start"):
         pb.sample(cell, theta, v, w, Ef, ncell, cfg["dt"], 0.5, args_ps, status=status)
         H = pb.ps_coarsen(samp_ps, d.s_w)
@@ -729,6 +753,9 @@ def run_kernel(args):
         elif args.kernel in ("push_sample", "push_sample_nodal"):
             pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho,
                     sample=args_s if args.kernel == "push_sample" else args_f, status=status)
+        elif args.kernel == "push_sample_pressure":
+            pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, sample=args_e,
+                    status=status)
         elif args.kernel == "push":
             pb.push(cell, theta, v, w, Ef, ncell, cfg["dt"] / dx, cfg["dt"], 1.0, d.s_w, rho=rho, status=status)
         elif args.kernel == "deposit":
@@ -755,7 +782,8 @@ def run_kernel(args):
     torch.cuda.synchronize()
     us = 1e3 * e0.elapsed_time(e1) / args.steps
     bytes_per = {"push_sample": 28, "push_sample_nodal": 28, "push": 28, "deposit": 12, "sample": 16, "quiet_start": 16,
-                 "field": 0, "push_sample_ps": 28, "push_sample_psw": 28, "ps_tables": 0, "ps_quiet_start": 16}
+                 "field": 0, "push_sample_ps": 28, "push_sample_psw": 28, "ps_tables": 0, "ps_quiet_start": 16,
+                 "push_sample_pressure": 28}
     gbs = bytes_per[args.kernel] * N / (us * 1e-6) / 1e9
     print(json.dumps({"kernel": args.kernel, "particles": N, "ncell": ncell, "launch_us": us, "algorithmic_GBps": gbs,
                       "status": int(status.item())}), flush=True)
