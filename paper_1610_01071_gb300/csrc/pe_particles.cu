@@ -609,7 +609,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
 template <int MODE>
 constexpr int min_blocks()
 {
-    return (ModeTraits<MODE>::ps || ModeTraits<MODE>::energy) ? 3 : 4;
+    return (ModeTraits<MODE>::ps || (ModeTraits<MODE>::energy && !ModeTraits<MODE>::binned)) ? 3 : 4;
 }
 
 template <int MODE, bool WALLS>
