@@ -55,13 +55,14 @@ KERNEL_BYTES = {
 # summarised in profiles/, each valid while the particle kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
 NCU_TRAFFIC = {
-    "push_sample": {"source_hash": "2b55b1873f4a669a", "bytes": 270.730240e6 + 145.224192e6},
-    "push": {"source_hash": "2b55b1873f4a669a", "bytes": 270.726400e6 + 145.909248e6},
-    "sample": {"source_hash": "2b55b1873f4a669a", "bytes": 270.670080e6 + 3.041280e6},
-    "deposit": {"source_hash": "2b55b1873f4a669a", "bytes": 203.019520e6 + 3.031552e6},
-    "push_sample_ps": {"source_hash": "2b55b1873f4a669a", "bytes": 270.273792e6 + 145.716224e6},
-    "push_sample_psw": {"source_hash": "2b55b1873f4a669a", "bytes": 270.489088e6 + 145.959168e6},
-    "load": {"source_hash": "2b55b1873f4a669a", "bytes": 0.526848e6 + 207.284480e6},
+    "push_sample": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.713344e6 + 145.194496e6},
+    "push": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.702080e6 + 145.757184e6},
+    "sample": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.666240e6 + 2.987008e6},
+    "deposit": {"source_hash": "20cdee557ce6ddd2", "bytes": 203.015424e6 + 2.981120e6},
+    "push_sample_ps": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.275328e6 + 145.240064e6},
+    "push_sample_psw": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.507776e6 + 145.187584e6},
+    "push_sample_pressure": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.769152e6 + 145.245696e6},
+    "load": {"source_hash": "20cdee557ce6ddd2", "bytes": 0.576512e6 + 207.280640e6},
 }
 
 
