@@ -23,10 +23,12 @@
  *   launch error). Faults found on the device (particle cell out of range,
  *   fixed-point overflow, Newton non-convergence) are OR-ed into a caller-owned
  *   device status word (uint32) as PE_FLAG_* bits and never trap; the caller reads
- *   it after synchronising (the context API does this in pe_sync_status). No kernel
- *   spins on a flag or a counter: the only device-side waits are block and cluster
- *   barriers that every thread reaches. PE_FLAG_TIMEOUT / PE_ETIMEOUT are reserved for a
- *   bounded wait that runs out; no current kernel has one.
+ *   it after synchronising (the context API does this in pe_sync_status). The only
+ *   spin-waits are the tensor-core GEMM's mbarrier waits (pe_tc_gemm_bf16 and the
+ *   surrogate's products): each is bounded by a clock budget, after which the kernel sets
+ *   PE_FLAG_TIMEOUT, waits (bounded again) for its copies in flight, frees its tensor
+ *   memory and returns (PE_ETIMEOUT from pe_mlp_sync_status). Every other device-side wait
+ *   is a block or cluster barrier that every thread reaches.
  */
 #ifndef PEPIC_H
 #define PEPIC_H
@@ -52,7 +54,7 @@ extern "C" {
 #define PE_EOVERFLOW 4 /* a weight or momentum exceeded its fixed-point range */
 #define PE_ERANGE 5    /* a particle cell index was outside [0, ncell) */
 #define PE_ESTATE 6    /* call out of order for the context state */
-#define PE_ETIMEOUT 7  /* a bounded device-side wait timed out (reserved: no current kernel waits) */
+#define PE_ETIMEOUT 7  /* a bounded device-side wait timed out (the tensor-core GEMM's mbarrier waits) */
 
 #define PE_FLAG_NOCONV 1u
 #define PE_FLAG_OVERFLOW 2u
