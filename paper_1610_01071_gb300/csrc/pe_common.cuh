@@ -278,30 +278,57 @@ struct PSGrid {
     }
 };
 
-// Per-lane run of equal phase-space keys over consecutive particles of a lane (a lane's
-// four particles of a 16-byte group are neighbours in a velocity-ordered cell, so they
-// usually share their phase-space cell): adds accumulate while the key repeats; a new key
-// sends the finished run to the grid directly.
-struct PSAcc {
+// Per-lane run of equal phase-space keys over consecutive particles of a lane (a lane's four
+// particles of a 16-byte group are neighbours in a velocity-ordered cell, so they usually share
+// their phase-space cell), for particles whose two CIC nodes lie in one bin: W = sum w_q
+// (|W| <= 4 2^23); the entry gets W 2^24. A new key sends the finished run to the grid.
+struct PSAccW {
     int key;
-    long long val;
+    int32_t w;
 
     __device__ __forceinline__ void reset()
     {
         key = -1;
-        val = 0;
+        w = 0;
     }
-    __device__ __forceinline__ void add(int k, long long q, const PSGrid& gr)
+    __device__ __forceinline__ void add(int k, int32_t q, const PSGrid& gr)
     {
         if (k == key) {
-            val += q;
+            w += q;
         } else {
-            if (key >= 0) gr.add(key, val);
+            if (key >= 0) gr.add(key, (long long)w * (long long)kThetaOne);
             key = k;
-            val = q;
+            w = q;
         }
     }
 };
+
+// Adds the lanes' runs (key, W) to a PSGrid, summing runs of equal keys in consecutive lanes
+// first: a segmented suffix sum over the run in 32 bits (W over at most 128 particles stays
+// below 2^30), added once by its first lane as W 2^24. key < 0 marks a lane with nothing to add.
+// When the active lanes are not a prefix of the warp, every lane adds on its own.
+__device__ __forceinline__ void ps_add_warp_w(const PSGrid& gr, int key, int32_t w)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int nact = __popc(act);
+    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
+        if (key >= 0) gr.add(key, (long long)w * (long long)kThetaOne);
+        return;
+    }
+    const int prev = __shfl_up_sync(act, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(act, head);
+    const unsigned after = heads & (0xFFFFFFFEu << lane);
+    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
+    int32_t sw = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t o = __shfl_down_sync(act, sw, off);
+        if (lane + off <= run_end) sw += o;
+    }
+    if (head && key >= 0) gr.add(key, (long long)sw * (long long)kThetaOne);
+}
 
 // Per-lane run of equal (coarse node, velocity cell) keys of the hat rows, over a lane's
 // four particles of a group: W = sum w_q (32 bits: |W| <= 4 2^23) and R = sum w_q f_q.
@@ -330,7 +357,7 @@ struct PSAcc2 {
     }
 };
 
-// ps_add_warp for the hat rows: runs of equal keys in consecutive lanes summed (W over at most
+// ps_add_warp_w for the hat rows: runs of equal keys in consecutive lanes summed (W over at most
 // 128 particles stays below 2^30), added by the run's first lane as two rows.
 __device__ __forceinline__ void ps_add_warp2(const PSGrid& gr, int key, int32_t w, long long r)
 {
@@ -358,34 +385,6 @@ __device__ __forceinline__ void ps_add_warp2(const PSGrid& gr, int key, int32_t 
         }
     }
     if (head && key >= 0) gr.add_pair(key, sw, sr);
-}
-
-// Adds (key, val) pairs of the active lanes to a PSGrid, summing runs of equal keys in
-// consecutive lanes first (consecutive particles of a velocity-ordered cell share their
-// phase-space cell): a segmented suffix sum over the run, added once by its first lane.
-// key < 0 marks a lane with nothing to add. When the active lanes are not a prefix of the
-// warp, every lane adds on its own.
-__device__ __forceinline__ void ps_add_warp(const PSGrid& gr, int key, long long val)
-{
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int nact = __popc(act);
-    if (act != (nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u))) {
-        if (key >= 0) gr.add(key, val);
-        return;
-    }
-    const int prev = __shfl_up_sync(act, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const unsigned heads = __ballot_sync(act, head);
-    const unsigned after = heads & (0xFFFFFFFEu << lane);
-    const int run_end = after ? (__ffs(after) - 2) : (nact - 1);
-    long long s = val;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const long long o = __shfl_down_sync(act, s, off);
-        if (lane + off <= run_end) s += o;
-    }
-    if (head && key >= 0) gr.add(key, s);
 }
 
 // Block-local restriction sample summed over bins of 2^b nodes (Haar restriction). A

@@ -184,7 +184,7 @@ struct BinSample {
 template <int MODE, bool WALLS>
 __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft, bool act, int c, float th,
                                         float vv, float ww, BinSample& bs, const SmemGrid& gsn, const SmemGrid& gsm,
-                                        const SmemGrid& gse, const PSGrid& gps, PSAcc& acc, PSAcc2& acc2, bool* ovf, int& c_out, float& th_out,
+                                        const SmemGrid& gse, const PSGrid& gps, PSAccW& acc, PSAcc2& acc2, bool* ovf, int& c_out, float& th_out,
                                         float& v_out, float& w_out, int32_t& wq_out)
 {
     using Tr = ModeTraits<MODE>;
@@ -265,10 +265,10 @@ __device__ __forceinline__ bool process(const PushParams& P, const FieldTab& ft,
                 const float f = ((float)(cs & ((1 << P.bin_shift) - 1)) + ths) * P.tent_scale;
                 acc2.add((b0 << 16) | j, wq, (long long)wq * (long long)__float2uint_rn(f), gps);
             } else if (b0 == b1) {
-                acc.add((b0 << 16) | j, (long long)wq * (long long)kThetaOne, gps);
-            } else {  // split across a bin edge (rare): the right part goes straight to the grid
+                acc.add((b0 << 16) | j, wq, gps);
+            } else {  // split across a bin edge (rare): both parts go straight to the grid
                 const FxSplit qn = fx_split(wq, ths);
-                acc.add((b0 << 16) | j, (long long)qn.left, gps);
+                gps.add_at(b0, j, (long long)qn.left);
                 gps.add_at(b1, j, (long long)qn.right);
             }
         }
@@ -462,7 +462,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
         else
             bw.add(bs.b, q, bs.mq, bs.tq, bsn, bsm);
     };
-    PSAcc acc;
+    PSAccW acc;
     PSAcc2 acc2;  // hat rows
     acc.reset();
     acc2.reset();
@@ -541,7 +541,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
                 ps_add_warp2(gps, acc2.key, acc2.w, acc2.r);
                 acc2.reset();
             } else {
-                ps_add_warp(gps, acc.key, acc.val);
+                ps_add_warp_w(gps, acc.key, acc.w);
                 acc.reset();
             }
         }
@@ -571,7 +571,7 @@ __device__ __forceinline__ void particle_chunk(const PushParams& P, int64_t begi
                 ps_add_warp2(gps, acc2.key, acc2.w, acc2.r);
                 acc2.reset();
             } else {
-                ps_add_warp(gps, acc.key, acc.val);
+                ps_add_warp_w(gps, acc.key, acc.w);
                 acc.reset();
             }
         }
