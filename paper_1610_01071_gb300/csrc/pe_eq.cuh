@@ -103,25 +103,50 @@ __device__ __forceinline__ int eq_cell_of(const EqTable& tab, int ncell, long lo
     return lo;
 }
 
+// Per-lane constants of the cell last visited by eq_position: the point's share of its cell's
+// mass, r = ((i + 1/2) M/n - C_c) / m_c, is a_c + (i - first_c) s_c with
+// a_c = ((first_c + 1/2) M/n - C_c) / m_c and s_c = (M/n) / m_c, formed once per cell in FP64
+// and applied in FP32 (r within ~1e-7 of the FP64 quotient). A lane visits thousands of points
+// of one cell in a row, and an FP64 division per point took most of the loaders' time.
+struct EqCellCache {
+    int c;          // cell of the constants; -1 before the first point
+    long long i0;   // first[c]
+    float a, s;
+
+    __device__ __forceinline__ void reset() { c = -1; }
+};
+
 // Position of point i: c is walked forward from a cell at or before the point's; returns the
 // offset t in [0, 1) at which the cell's linear density (the profile's two nodal values, wall
 // nodes times wall_factor) holds the point's share r of the cell mass: t + sig (t^2 - t) = r.
 template <typename TP>
 __device__ __forceinline__ float eq_position(const EqTable& tab, const TP* __restrict__ prof, float wall_factor,
-                                             int ncell, uint32_t i, int& c)
+                                             int ncell, uint32_t i, int& c, EqCellCache& cache)
 {
     while (c < ncell - 2 && __ldg(tab.first + c + 1) <= (long long)i) ++c;
-    const double C0 = __ldg(tab.C + c), C1 = __ldg(tab.C + c + 1);
-    const double MoN = __ldg(tab.MoN);
-    const double mc = C1 - C0;
-    double r = mc > 0.0 ? (((double)i + 0.5) * MoN - C0) / mc : 0.5;
-    r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+    if (c != cache.c) {
+        const double C0 = __ldg(tab.C + c), C1 = __ldg(tab.C + c + 1);
+        const double MoN = __ldg(tab.MoN);
+        const double mc = C1 - C0;
+        const long long i0 = __ldg(tab.first + c);
+        cache.c = c;
+        cache.i0 = i0;
+        if (mc > 0.0) {
+            cache.a = (float)((((double)i0 + 0.5) * MoN - C0) / mc);
+            cache.s = (float)(MoN / mc);
+        } else {
+            cache.a = 0.5f;
+            cache.s = 0.0f;
+        }
+    }
+    float r = fmaf((float)((long long)i - cache.i0), cache.s, cache.a);
+    r = r < 0.0f ? 0.0f : (r > 1.0f ? 1.0f : r);
     float n0 = (float)__ldg(prof + c), n1 = (float)__ldg(prof + c + 1);
     if (c == 0) n0 *= wall_factor;
     if (c + 1 == ncell - 1) n1 *= wall_factor;
     const float sum = n0 + n1;
     const float sig = sum > 0.0f ? (n1 - n0) / sum : 0.0f;
-    const float rf = (float)r;
+    const float rf = r;
     const float om = 1.0f - sig;
     const float den = om + sqrtf(fmaxf(om * om + 4.0f * sig * rf, 0.0f));
     const float t = den > 0.0f ? 2.0f * rf / den : 0.0f;

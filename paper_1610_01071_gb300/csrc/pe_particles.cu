@@ -809,9 +809,10 @@ struct EqParams {
     uint32_t* status;
 };
 
-__device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+__device__ __forceinline__ void eq_one(const EqParams& P, uint32_t i, int& c, float& th, float& vv, float& ww,
+                                         EqCellCache& cache)
 {
-    const float t = eq_position(P.tab, P.prof_n, P.wall_factor, P.ncell, i, c);
+    const float t = eq_position(P.tab, P.prof_n, P.wall_factor, P.ncell, i, c, cache);
     th = t;
     const float u0 = __ldg(P.prof_u + c), u1 = __ldg(P.prof_u + c + 1);
     const float uX = fmaf(t, u1 - u0, u0);
@@ -843,6 +844,8 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
     warp_groups(gb0, gb1, &g0, &g1);
     LaneWindow lw;
     lw.reset((c_first - 1) & P.mask);
+    EqCellCache cache;
+    cache.reset();
     bool ovf = false;
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
@@ -858,10 +861,10 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
         const uint32_t pmin = min(min(p0, p1), min(p2, p3));
         const int cb = eq_cell_of(P.tab, P.ncell, pmin);
         c.x = c.y = c.z = c.w = cb;
-        eq_one(P, p0, c.x, t.x, vv.x, ww.x);
-        eq_one(P, p1, c.y, t.y, vv.y, ww.y);
-        eq_one(P, p2, c.z, t.z, vv.z, ww.z);
-        eq_one(P, p3, c.w, t.w, vv.w, ww.w);
+        eq_one(P, p0, c.x, t.x, vv.x, ww.x, cache);
+        eq_one(P, p1, c.y, t.y, vv.y, ww.y, cache);
+        eq_one(P, p2, c.z, t.z, vv.z, ww.z, cache);
+        eq_one(P, p3, c.w, t.w, vv.w, ww.w, cache);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -877,7 +880,7 @@ __global__ void __launch_bounds__(256) k_quiet_start_equal(EqParams P)
         const uint32_t pi = eq_point_of_slot((uint32_t)i, P.n);
         int c = eq_cell_of(P.tab, P.ncell, pi);
         float t, vv, ww;
-        eq_one(P, pi, c, t, vv, ww);
+        eq_one(P, pi, c, t, vv, ww, cache);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;

@@ -934,9 +934,10 @@ struct PSEqLoad {
     uint32_t* status;
 };
 
-__device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww)
+__device__ __forceinline__ void ps_eq_one(const PSEqLoad& P, uint32_t i, int& c, float& th, float& vv, float& ww,
+                                          EqCellCache& cache)
 {
-    const float t = eq_position(P.tab, P.prof, 1.0f, P.ncell, i, c);
+    const float t = eq_position(P.tab, P.prof, 1.0f, P.ncell, i, c, cache);
     th = t;
     int b0, b1;
     float phi;
@@ -980,6 +981,8 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start_equal(PSEqLoad P)
     warp_groups(gb0, gb1, &g0, &g1);
     LaneWindow lw;
     lw.reset((c_first - 1) & P.mask);
+    EqCellCache cache;
+    cache.reset();
     bool ovf = false;
     int4* cell4 = reinterpret_cast<int4*>(P.cell);
     float4* th4 = reinterpret_cast<float4*>(P.theta);
@@ -993,10 +996,10 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start_equal(PSEqLoad P)
                        p2 = eq_point_of_slot(s0 + 2, P.n), p3 = eq_point_of_slot(s0 + 3, P.n);
         const int cb = eq_cell_of(P.tab, P.ncell, min(min(p0, p1), min(p2, p3)));
         c.x = c.y = c.z = c.w = cb;
-        ps_eq_one(P, p0, c.x, t.x, vv.x, ww.x);
-        ps_eq_one(P, p1, c.y, t.y, vv.y, ww.y);
-        ps_eq_one(P, p2, c.z, t.z, vv.z, ww.z);
-        ps_eq_one(P, p3, c.w, t.w, vv.w, ww.w);
+        ps_eq_one(P, p0, c.x, t.x, vv.x, ww.x, cache);
+        ps_eq_one(P, p1, c.y, t.y, vv.y, ww.y, cache);
+        ps_eq_one(P, p2, c.z, t.z, vv.z, ww.z, cache);
+        ps_eq_one(P, p3, c.w, t.w, vv.w, ww.w, cache);
         cell4[g] = c;
         th4[g] = t;
         v4[g] = vv;
@@ -1012,7 +1015,7 @@ __global__ void __launch_bounds__(256) k_ps_quiet_start_equal(PSEqLoad P)
         const uint32_t pi = eq_point_of_slot((uint32_t)i, P.n);
         int c = eq_cell_of(P.tab, P.ncell, pi);
         float t, vv, ww;
-        ps_eq_one(P, pi, c, t, vv, ww);
+        ps_eq_one(P, pi, c, t, vv, ww, cache);
         P.cell[i] = c;
         P.theta[i] = t;
         P.v[i] = vv;
