@@ -297,7 +297,7 @@ extern "C" PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scra
             delete b;
             return PE_EINVAL;
         }
-        const bool fp64 = x->walls != 0;
+        const bool fp64 = x->walls != 0 && kWallsJacobianFP64;
         bool placed = false;
         for (auto& fg : b->fgroups)
             if (fg.G == G && fg.fp64 == fp64) {

@@ -32,7 +32,8 @@ constexpr int kClusterMinCells = 512;  // grids at least this large use the mult
 // FP32 solve only bounds the final contraction rate (~ cond(J) 2^-24 per iteration).
 // Bounded grids with vacuum regions have exp(phi) ~ 1e-6 there and cond(J) ~ 1e7: the FP32
 // solve still contracts, but slowly (7 Newton iterations instead of 3 on an 8192-node slab from
-// a warm start), so their linear solve runs in FP64 (template parameter T).
+// a warm start); it remains the faster solve (kWallsJacobianFP64 selects the FP64 elimination,
+// template parameter T).
 // On this GPU a dependent FP64 instruction costs ~100 cycles and the FP64 pipe retires
 // ~2 lanes per cycle per SM, so FP64 is used only for per-node work, spread over many
 // warps and SMs, and kept off the serial chains of the tridiagonal elimination.
@@ -590,7 +591,7 @@ static int launch_newton_cluster(int G, const long long* rho, int ncell, double 
 {
     const int B = ncell / G;  // one node per thread
     if (B > kNewtonMaxThreads || B < 2) return PE_EINVAL;
-    const bool fp64 = walls != 0;
+    const bool fp64 = walls != 0 && kWallsJacobianFP64;
     const size_t smem = newton_smem_bytes(B, G, fp64);
     const void* k = fp64 ? (const void*)k_newton_cluster<double> : (const void*)k_newton_cluster<float>;
     if (ensure_smem(k, smem) != PE_OK) return PE_ECUDA;
@@ -619,7 +620,7 @@ int newton_batch_cluster_size(int ncell)
 }
 
 // Batched field solves: descs[R] on the device, every grid with the same cluster size G;
-// fp64: the linear solves run in FP64 (needed when any grid is bounded).
+// fp64: the linear solves run in FP64 (bounded grids with kWallsJacobianFP64).
 int launch_newton_batch(const void* descs, int R, int G, int max_ncell, bool fp64, bool extrap, cudaStream_t s)
 {
     const int B = max_ncell / G;

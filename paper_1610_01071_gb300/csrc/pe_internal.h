@@ -108,6 +108,11 @@ constexpr int kFullGridMax = 8192;     // largest grid the context API accepts
 constexpr int kRhoWindowNodes = 1024;  // charge deposit: window around the block's cells
 constexpr int kWindowNodes = 4096;     // restriction samples: window (co-moving spread)
 constexpr int kWindowNodesE = 1024;    // the same with the second moment (three rows in shared memory)
+// Bounded grids (vacuum regions, exp(phi) ~ 1e-6, cond(J) ~ 1e7) slow the FP32 Jacobian solve's
+// contraction: about 7 Newton updates instead of 3 on the 8192-node slab from a warm start. Each
+// FP32 update costs so much less than an FP64 one that the field solve is still faster (56 against
+// 125 us on the slab), so the FP64 elimination stays compiled but unused (true selects it).
+constexpr bool kWallsJacobianFP64 = false;
 // TMA tensor map of a K-major BF16 GEMM operand: rows x K elements, row stride ld elements,
 // box {64, box_rows}, 128-byte swizzle, zero fill (pe_tc.cu).
 int tc_operand_map(::CUtensorMap_st* map, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows);
