@@ -55,14 +55,14 @@ KERNEL_BYTES = {
 # summarised in profiles/, each valid while the particle kernels' device code
 # (kernel_source_hash) hashes to the value it was taken with.
 NCU_TRAFFIC = {
-    "push_sample": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.713344e6 + 145.194496e6},
-    "push": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.702080e6 + 145.757184e6},
-    "sample": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.666240e6 + 2.987008e6},
-    "deposit": {"source_hash": "20cdee557ce6ddd2", "bytes": 203.015424e6 + 2.981120e6},
-    "push_sample_ps": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.275328e6 + 145.240064e6},
-    "push_sample_psw": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.507776e6 + 145.187584e6},
-    "push_sample_pressure": {"source_hash": "20cdee557ce6ddd2", "bytes": 270.769152e6 + 145.245696e6},
-    "load": {"source_hash": "20cdee557ce6ddd2", "bytes": 0.576512e6 + 207.280640e6},
+    "push_sample": {"source_hash": "173582129c21fd7b", "bytes": 270.715904e6 + 145.457152e6},
+    "push": {"source_hash": "173582129c21fd7b", "bytes": 270.730496e6 + 145.774336e6},
+    "sample": {"source_hash": "173582129c21fd7b", "bytes": 270.679552e6 + 3.367168e6},
+    "deposit": {"source_hash": "173582129c21fd7b", "bytes": 203.015936e6 + 2.963968e6},
+    "push_sample_ps": {"source_hash": "173582129c21fd7b", "bytes": 270.272256e6 + 145.230080e6},
+    "push_sample_psw": {"source_hash": "173582129c21fd7b", "bytes": 270.507520e6 + 145.440768e6},
+    "push_sample_pressure": {"source_hash": "173582129c21fd7b", "bytes": 270.752512e6 + 145.262592e6},
+    "load": {"source_hash": "173582129c21fd7b", "bytes": 0.574720e6 + 207.112192e6},
 }
 
 
