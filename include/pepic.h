@@ -850,8 +850,11 @@ PE_API int pe_batch_create(pe_ctx* const* ctxs, int32_t n, void* scratch, size_t
 PE_API int pe_batch_step(pe_batch* b);
 /* Autotuner: times the batched particle pass for every launch shape (particle chunks of
  * 16384, 32768 or 65536 per work item; blocks of 128, 256 or 512 threads; the charge deposit
- * through a shared-memory window or straight to the global grid), as the sum of its read-only
- * sample pass and its deposit pass, and keeps the fastest; returns its chunk in *chunk. The
+ * through a shared-memory window or straight to the global grid): the burst's fused pass (push,
+ * deposit, binned sample) run with a frozen step (dt/dx = 0, kick 0), which rewrites every
+ * particle unchanged and leaves its deposit in the batch's charge grid (the current particles'
+ * deposit) and its sample in a row that each burst clears; it keeps the fastest and returns its
+ * chunk in *chunk. The
  * choice is cached for the process by the ensemble's composition (every realisation's ncell and
  * particle count, in order, and the device): a later batch of the same composition reuses it
  * without timing. pe_batch_tuned reports the shape in use. */

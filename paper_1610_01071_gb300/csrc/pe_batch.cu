@@ -140,7 +140,9 @@ static int build_items(pe_batch* b)
     return PE_OK;
 }
 
-static int build_descs(pe_batch* b)
+// frozen: push descriptors with dt/dx = 0 (the tuner's probe: with kick 0 a fused pass then
+// rewrites every particle unchanged while doing all of a real pass's work).
+static int build_descs(pe_batch* b, bool frozen = false)
 {
     const int R = (int)b->ctx.size();
     std::vector<char> push(push_desc_size() * R), proj(proj_desc_size() * R);
@@ -161,7 +163,8 @@ static int build_descs(pe_batch* b)
         const int k = x->bank;
         b->banks[r] = k;
         make_push_desc(push.data() + push_desc_size() * r, x->cell[k], x->theta[k], x->v[k], x->w[k], c.nparticles,
-                       x->Ef, c.ncell, (float)(c.dt / x->dx), (float)(c.qm * c.dt), x->s_w, rho_all + b->rho_off[r],
+                       x->Ef, c.ncell, frozen ? 0.0f : (float)(c.dt / x->dx), (float)(c.qm * c.dt), x->s_w,
+                       rho_all + b->rho_off[r],
                        e0_all + b->e0_off[r], c.dT, c.dt, (float)(1.0 / x->dx), (float)c.qm, c.comoving,
                        x->s_p, x->bin_shift, samp_all + b->samp_off[r], b->L.samp_row, x->walls, x->status);
         make_proj_desc(proj.data() + proj_desc_size() * r, samp_all + b->samp_off[r], b->L.samp_row, c.ncell, x->nc,
@@ -365,15 +368,19 @@ static std::vector<int64_t> composition(const pe_batch* b)
 // Times one launch shape: the read-only sample pass (row K + 1, scratch) and the deposit pass
 // (into the ensemble's charge grid, rewritten before every push) over every realisation's
 // particles, the two halves of the fused push; best of two.
+// Time of one fused pass of the burst (push + deposit + binned sample, mode 0) in the current
+// shape, on frozen descriptors with kick 0: the particles are rewritten unchanged, the deposit
+// and sample land in the batch's charge grid and sample row 0, which every burst clears before
+// use. Best of two after a warm-up.
 static int time_shape(pe_batch* b, cudaEvent_t e0, cudaEvent_t e1, float* ms_out)
 {
     unsigned* counter = reinterpret_cast<unsigned*>(at(b, b->L.counter));
+    int64_t* rho_all = reinterpret_cast<int64_t*>(at(b, b->L.rho));
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {  // the first repetition warms up
         cudaEventRecord(e0, b->stream);
-        PE_TRY(launch_particles_batch(1, at(b, b->L.push), at(b, b->L.items), b->nitems, b->K + 1, 1.0f, counter,
-                                      b->max_ncell, b->max_nb, b->block, b->priv, b->stream));
-        PE_TRY(launch_particles_batch(2, at(b, b->L.push), at(b, b->L.items), b->nitems, 0, 1.0f, counter,
+        if (cudaMemsetAsync(rho_all, 0, 8 * (size_t)b->L.rho_total, b->stream) != cudaSuccess) return PE_ECUDA;
+        PE_TRY(launch_particles_batch(0, at(b, b->L.push), at(b, b->L.items), b->nitems, 0, 0.0f, counter,
                                       b->max_ncell, b->max_nb, b->block, b->priv, b->stream));
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) return PE_ECUDA;
@@ -405,16 +412,18 @@ extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PE_ECUDA;
         float best = 1e30f;
         Tuned pick{b->chunk, b->block, b->priv};
+        int rc = build_descs(b, true);
         for (int64_t cand : kChunkCandidates) {
+            if (rc != PE_OK) break;
             b->chunk = cand;
-            PE_TRY(build_items(b));
+            rc = build_items(b);
             for (int blk : kBlockCandidates)
-                for (int pv = 1; pv >= 0; --pv) {
+                for (int pv = 1; pv >= 0 && rc == PE_OK; --pv) {
                     b->block = blk;
                     b->priv = pv;
                     float ms = 0.f;
-                    PE_TRY(time_shape(b, e0, e1, &ms));
-                    if (ms < best) {
+                    rc = time_shape(b, e0, e1, &ms);
+                    if (rc == PE_OK && ms < best) {
                         best = ms;
                         pick = Tuned{cand, blk, pv};
                     }
@@ -422,6 +431,9 @@ extern "C" PE_API int pe_batch_tune(pe_batch* b, int64_t* chosen_chunk)
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        const int rc_descs = build_descs(b);  // the real steps' descriptors again, also after an error
+        if (rc != PE_OK) return rc;
+        if (rc_descs != PE_OK) return rc_descs;
         b->chunk = pick.chunk;
         b->block = pick.block;
         b->priv = pick.priv;

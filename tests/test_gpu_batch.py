@@ -117,6 +117,27 @@ def test_batch_tuner_shapes_and_cache():
     assert b2.tune() == chunk and b2.tuned() == t1
 
 
+def test_batch_tuner_leaves_the_particles_unchanged():
+    # the tuner times the burst's fused pass with a frozen step (dt/dx = 0, kick 0): every particle
+    # is rewritten unchanged, periodic and bounded grids alike; a composition not tuned before
+    sizes = [(512, 3 << 15, False), (1024, 5 << 14, True), (256, 3 << 13, False)]
+    group = [make(i, n, N, slab) for i, (n, N, slab) in enumerate(sizes)]
+    before = []
+    for c in group:
+        before.append([t.clone() for t in c.particles(c.diagnostics().particle_bank)])
+    b = pe.Batch(group)
+    b.tune()
+    torch.cuda.synchronize(DEV)
+    for c, ref in zip(group, before):
+        for x, y in zip(c.particles(c.diagnostics().particle_bank), ref):
+            assert torch.equal(x, y)
+        assert c.sync_status() == 0
+    b.step()  # the real descriptors are back: the step moves the particles
+    for c, ref in zip(group, before):
+        assert c.sync_status() == 0
+        assert not torch.equal(c.particles(c.diagnostics().particle_bank)[1], ref[1])
+
+
 def test_group_means_of_coarse_states():
     sizes = [(256, 1 << 14), (256, 1 << 14), (512, 1 << 15), (256, 1 << 14), (512, 1 << 15)]
     group = [make(i, n, N) for i, (n, N) in enumerate(sizes)]
