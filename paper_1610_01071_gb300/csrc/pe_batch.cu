@@ -95,10 +95,11 @@ struct pe_batch {
     int block, priv;  // particle launch shape: threads per block, shared-memory deposit window
     int nitems;
     int max_ncell, max_nb;
-    // Field-solve groups, one launch each: (cluster size G) x (FP32 | FP64 Jacobian solve:
-    // bounded grids). The batch sizes clusters for throughput (newton_batch_cluster_size), so
-    // its solves can differ from a lone context's in the last bits (the same equations, another
-    // partition of the linear solve); both converge to the Newton tolerance.
+    // Field-solve groups, one launch each: (cluster size G) x (FP32 | FP64 Jacobian solve; FP64
+    // only for bounded grids with kWallsJacobianFP64). The batch sizes clusters for throughput
+    // (newton_batch_cluster_size), so its solves can differ from a lone context's in the last
+    // bits (the same equations, another partition of the linear solve); both converge to the
+    // Newton tolerance.
     struct FieldGroup {
         int G;
         bool fp64;

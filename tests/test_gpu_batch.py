@@ -53,7 +53,7 @@ def test_batch_matches_individual_contexts():
 
 def test_batch_of_sinusoids_and_slabs_matches_individual_contexts():
     # the ensemble workload mixes periodic sinusoids and bounded slabs: the batch solves each
-    # field with its context's precision (FP64 Jacobian solves for the slabs), pushes with
+    # field with its context's precision (the Jacobian solve of the slabs as alone), pushes with
     # absorbing walls and lifts the slabs with equal weights, all bit for bit as alone
     sizes = [(512, 1 << 16, True), (1024, 1 << 17, False), (256, 1 << 14, True), (4096, 1 << 18, True),
              (2048, 1 << 16, False), (128, 1 << 12, True)]
